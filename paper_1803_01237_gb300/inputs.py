@@ -1,0 +1,182 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module holds no arithmetic of the sorting method: it only draws keys.
+Every generator is a pure function of its seed (numpy's Philox4x64 bit
+generator), so the CUDA path and the CPU oracle read identical buffers.
+
+Distributions:
+  * ``uniform``      keys uniform over [0, 2^64)                 (Sec. 7.5 UNIF)
+  * ``gauss_mix``    32 Gaussians (sigma = 2^40, means uniform) cast to u64
+  * ``zipf``         values drawn from 2^12 distinct keys with Zipf(s=1.2)
+  * the six inputs of Sec. 7.5 (UNIF, SKEW1, SKEW2, SKEW3, GAUSS, AllZeros)
+  * ``plummer_morton`` 64-bit Morton keys of a Plummer sphere, 21 bits per
+    axis, with the particle index as a u32 payload (the N-body workload of
+    Sec. 7.4 stands in for the ChaNGa datasets, which are not available)
+  * ``batch_jobs``   many int64 jobs with log-uniform sizes
+  * ``lognormal_job`` lognormal(0, 2) keys scaled to 2^63
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+_CHUNK = 1 << 24
+
+
+def rng(seed: int, stream: int = 0) -> np.random.Generator:
+    """numpy Philox4x64 generator keyed by (seed, stream)."""
+    return np.random.Generator(np.random.Philox(key=[seed & ((1 << 64) - 1), stream & ((1 << 64) - 1)]))
+
+
+def uniform(N: int, seed: int) -> np.ndarray:
+    g = rng(seed, 1)
+    out = np.empty(N, dtype=np.uint64)
+    for a in range(0, N, _CHUNK):
+        b = min(N, a + _CHUNK)
+        out[a:b] = g.bit_generator.random_raw(b - a)
+    return out
+
+
+def gauss_mix(N: int, seed: int, ncomp: int = 32, sigma: float = 2.0 ** 40) -> np.ndarray:
+    g = rng(seed, 2)
+    means = g.bit_generator.random_raw(ncomp).view(np.int64)
+    out = np.empty(N, dtype=np.uint64)
+    for a in range(0, N, _CHUNK):
+        b = min(N, a + _CHUNK)
+        comp = g.integers(0, ncomp, size=b - a)
+        off = np.rint(g.standard_normal(b - a) * sigma).astype(np.int64)
+        with np.errstate(over="ignore"):
+            out[a:b] = (means[comp] + off).view(np.uint64)
+    return out
+
+
+def _zipf_table(g: np.random.Generator, distinct: int, s: float):
+    values = g.bit_generator.random_raw(distinct)
+    while np.unique(values).size != distinct:  # practically never
+        values = g.bit_generator.random_raw(distinct)
+    w = np.arange(1, distinct + 1, dtype=np.float64) ** (-s)
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    return values, cdf
+
+
+def zipf(N: int, seed: int, distinct: int = 1 << 12, s: float = 1.2) -> np.ndarray:
+    g = rng(seed, 3)
+    values, cdf = _zipf_table(g, distinct, s)
+    out = np.empty(N, dtype=np.uint64)
+    for a in range(0, N, _CHUNK):
+        b = min(N, a + _CHUNK)
+        idx = np.searchsorted(cdf, g.random(b - a), side="right")
+        out[a:b] = values[np.minimum(idx, distinct - 1)]
+    return out
+
+
+# --- the input distributions of Sec. 7.5 -------------------------------------
+
+def skew1(N: int, seed: int) -> np.ndarray:
+    """Half uniform over the whole range, half uniform over a range of 1000."""
+    g = rng(seed, 4)
+    out = g.bit_generator.random_raw(N)
+    half = N // 2
+    base = int(g.bit_generator.random_raw(1)[0]) % ((1 << 64) - 1000)
+    out[:half] = np.uint64(base) + g.integers(0, 1000, size=half).astype(np.uint64)
+    g.shuffle(out)
+    return out
+
+
+def skew2(N: int, seed: int) -> np.ndarray:
+    """Uniform over [0, 100] (101 distinct values)."""
+    return rng(seed, 5).integers(0, 101, size=N).astype(np.uint64)
+
+
+def skew3(N: int, seed: int) -> np.ndarray:
+    """Bitwise AND of two uniform keys."""
+    g = rng(seed, 6)
+    return g.bit_generator.random_raw(N) & g.bit_generator.random_raw(N)
+
+
+def gauss(N: int, seed: int) -> np.ndarray:
+    """One Gaussian centred in the key range (sigma = 2^58)."""
+    g = rng(seed, 7)
+    v = np.rint(g.standard_normal(N) * 2.0 ** 58).astype(np.int64)
+    with np.errstate(over="ignore"):
+        return (v.view(np.uint64) + np.uint64(1 << 63))
+
+
+def allzeros(N: int, seed: int = 0) -> np.ndarray:
+    return np.zeros(N, dtype=np.uint64)
+
+
+PAPER_DISTRIBUTIONS = {
+    "UNIF": uniform, "SKEW1": skew1, "SKEW2": skew2, "SKEW3": skew3, "GAUSS": gauss, "AllZeros": allzeros,
+}
+
+SCALE_DISTRIBUTIONS = {"uniform": uniform, "gauss_mix": gauss_mix, "zipf": zipf}
+
+
+# --- N-body workload -----------------------------------------------------------
+
+def _spread3(v: np.ndarray) -> np.ndarray:
+    """Insert two zero bits between the 21 low bits of v (Morton interleave)."""
+    v = v.astype(np.uint64) & np.uint64(0x1FFFFF)
+    v = (v | (v << np.uint64(32))) & np.uint64(0x1F00000000FFFF)
+    v = (v | (v << np.uint64(16))) & np.uint64(0x1F0000FF0000FF)
+    v = (v | (v << np.uint64(8))) & np.uint64(0x100F00F00F00F00F)
+    v = (v | (v << np.uint64(4))) & np.uint64(0x10C30C30C30C30C3)
+    v = (v | (v << np.uint64(2))) & np.uint64(0x1249249249249249)
+    return v
+
+
+def plummer_morton(N: int, seed: int, bits: int = 21):
+    """Morton keys of a Plummer sphere plus the particle index as payload.
+
+    Radius from the Plummer mass profile m(r) = r^3 (1+r^2)^(-3/2): for a mass
+    fraction m ~ U(0, 0.999], r = (m^(-2/3) - 1)^(-1/2); isotropic direction;
+    each axis quantised to ``bits`` bits over [-r_max, r_max] with r_max = r(0.999).
+    """
+    g = rng(seed, 8)
+    r_max = (0.999 ** (-2.0 / 3.0) - 1.0) ** -0.5
+    keys = np.empty(N, dtype=np.uint64)
+    scale = float(1 << bits)
+    for a in range(0, N, _CHUNK):
+        b = min(N, a + _CHUNK)
+        n = b - a
+        m = 0.999 * (1.0 - g.random(n))  # (0, 0.999]
+        r = (m ** (-2.0 / 3.0) - 1.0) ** -0.5
+        ct = 2.0 * g.random(n) - 1.0
+        st = np.sqrt(np.maximum(0.0, 1.0 - ct * ct))
+        ph = 2.0 * math.pi * g.random(n)
+        xyz = (r * st * np.cos(ph), r * st * np.sin(ph), r * ct)
+        q = [np.clip(np.floor((c + r_max) / (2.0 * r_max) * scale), 0, scale - 1).astype(np.uint64) for c in xyz]
+        keys[a:b] = _spread3(q[0]) | (_spread3(q[1]) << np.uint64(1)) | (_spread3(q[2]) << np.uint64(2))
+    payload = np.arange(N, dtype=np.uint64).astype(np.uint32)
+    return keys, payload
+
+
+# --- batched and served jobs ---------------------------------------------------
+
+def batch_jobs(njobs: int, seed: int, lo_log2: int = 10, hi_log2: int = 22, zipf_s: float = 1.1,
+               zipf_distinct: int = 1 << 16):
+    """Independent int64 jobs with sizes log-uniform in [2^lo, 2^hi]; each is
+    uniform or Zipf by a seeded coin.  Returns (list of int64 arrays, kinds)."""
+    g = rng(seed, 9)
+    u = g.random(njobs)
+    sizes = np.floor(2.0 ** (lo_log2 + (hi_log2 - lo_log2) * u)).astype(np.int64)
+    coin = g.random(njobs) < 0.5
+    jobs, kinds = [], []
+    for j in range(njobs):
+        n = int(sizes[j])
+        if coin[j]:
+            jobs.append(uniform(n, seed * 1000003 + j).view(np.int64))
+            kinds.append("uniform")
+        else:
+            jobs.append(zipf(n, seed * 1000003 + j, distinct=zipf_distinct, s=zipf_s).view(np.int64))
+            kinds.append("zipf")
+    return jobs, kinds
+
+
+def lognormal_job(n: int, seed: int, sigma: float = 2.0) -> np.ndarray:
+    """lognormal(0, sigma) keys scaled so the largest is 2^63 - 1."""
+    x = rng(seed, 10).lognormal(0.0, sigma, size=n)
+    return np.floor(x / x.max() * float((1 << 63) - 1024)).astype(np.uint64)
