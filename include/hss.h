@@ -1,0 +1,182 @@
+/*
+ * hss.h -- C ABI of the GB300 Histogram Sort with Sampling library (libhss.so).
+ *
+ * The method is Histogram Sort with Sampling (HSS) of Harsh, Kale and
+ * Solomonik (SPAA'19).  Its p "processors" are p contiguous segments of one
+ * device array: processor s owns input positions [floor(sN/p), floor((s+1)N/p)).
+ *
+ * Conventions shared by every entry point
+ *   - Every buffer belongs to the caller.  Pointers named d_* are device
+ *     pointers on the current device, h_* are host pointers.  The library
+ *     never allocates device memory: scratch comes from the caller's
+ *     workspace (d_work, work_bytes), sized with hss_workspace_bytes().
+ *   - Work is enqueued on `stream` (a cudaStream_t passed as void*, NULL =
+ *     the legacy default stream).  hss_partition and hss_sort block the
+ *     calling thread while the splitter rounds run (one small device-to-host
+ *     read per round decides the next launch); everything else they enqueue
+ *     completes asynchronously unless HSS_FLAG_SYNC or HSS_FLAG_TIMING is set.
+ *   - Keys are 64-bit, unsigned (HSS_KEY_U64) or signed (HSS_KEY_I64).  An
+ *     optional 32-bit payload travels with its key.
+ *   - Ties between equal keys are broken by (processor, position), which is
+ *     the (key, processor, index) implicit tagging of the paper's Sec. 6.1;
+ *     every sort here is therefore stable with respect to input order.
+ *   - Return value: HSS_OK (0) or a negative HSS_ERR_* code.  Device-side
+ *     failures (a bounded wait that ran out) travel through a status word and
+ *     are reported as HSS_ERR_TIMEOUT; nothing traps the GPU.
+ *   - Limits: N < 2^40; 1 <= p <= 2^22 and p*(samples per round) positions
+ *     must fit the workspace; a segment or bucket holds fewer than 2^30 keys.
+ */
+#ifndef HSS_H
+#define HSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HSS_OK 0
+#define HSS_ERR_INVALID (-1)      /* bad argument: null pointer, p = 0, eps <= 0, sizes out of range */
+#define HSS_ERR_WORKSPACE (-2)    /* work_bytes smaller than hss_workspace_bytes() */
+#define HSS_ERR_ROUND_LIMIT (-3)  /* max_rounds reached with splitters unresolved */
+#define HSS_ERR_TIMEOUT (-4)      /* a bounded device-side wait gave up */
+#define HSS_ERR_CUDA (-5)         /* a CUDA runtime call failed */
+#define HSS_ERR_CAPACITY (-6)     /* a round drew more probes than the sample buffer holds */
+
+#define HSS_KEY_U64 0
+#define HSS_KEY_I64 1
+
+#define HSS_MAX_ROUNDS 64
+
+/* params.flags */
+#define HSS_FLAG_SYNC 1u     /* synchronize `stream` before returning */
+#define HSS_FLAG_TIMING 2u   /* record per-phase device times into hss_stats (implies SYNC) */
+
+/* Workspace queries (op argument of hss_workspace_bytes). */
+#define HSS_OP_SORT 0
+#define HSS_OP_PARTITION 1
+#define HSS_OP_LOCAL_SORT 2
+#define HSS_OP_MERGE 3
+#define HSS_OP_EXCHANGE 4
+#define HSS_OP_SORT_HOST 5
+
+/* A cut in the tag order of Sec. 6.1: the key itself (caller's
+ * representation), the processor it lies on and its position in that
+ * processor's locally sorted keys.  Special values of seg:
+ *   -1  a non-member cut: sorts before every key equal to `key`;
+ *   -2  minus infinity;  -3  plus infinity. */
+typedef struct {
+    uint64_t key;
+    int32_t seg;
+    uint32_t spos;
+} hss_cut;
+
+typedef struct {
+    double eps;          /* balance: bucket i's start rank lies within floor(N eps/(2p)) of floor(iN/p) (Sec. 2) */
+    uint64_t seed;       /* Philox key of the Bernoulli sampling */
+    uint32_t p;          /* number of processors = buckets */
+    float oversample;    /* s: expected probes per processor per round (default 5, Sec. 7.2) */
+    uint32_t max_rounds; /* <= HSS_MAX_ROUNDS (0 means HSS_MAX_ROUNDS) */
+    uint32_t flags;      /* HSS_FLAG_* */
+} hss_params;
+
+#define HSS_PHASE_LOCAL_SORT 0
+#define HSS_PHASE_ROUNDS 1
+#define HSS_PHASE_EXCHANGE 2
+#define HSS_PHASE_MERGE 3
+#define HSS_NUM_PHASES 4
+
+typedef struct {
+    uint32_t rounds;                         /* histogram rounds run */
+    int32_t status;                          /* same code as the return value */
+    uint64_t tol;                            /* floor(N eps / (2p)) */
+    uint64_t sample_size[HSS_MAX_ROUNDS];    /* Z_j: probes drawn in round j+1 */
+    uint64_t gamma[HSS_MAX_ROUNDS];          /* |gamma|: keys inside unresolved intervals sampled in round j+1 */
+    uint64_t unresolved[HSS_MAX_ROUNDS + 1]; /* unresolved splitters before round 1 .. after the last round */
+    float ms_phase[HSS_NUM_PHASES];          /* device time per phase (HSS_FLAG_TIMING) */
+    float ms_radix_pass_total;               /* summed device time of the radix digit-pass kernels (HSS_FLAG_TIMING) */
+    uint32_t radix_pass_launches;            /* number of those launches */
+    uint64_t radix_pass_keys;                /* keys moved by those launches, summed */
+    uint32_t kernel_launches;                /* kernels this call launched */
+} hss_stats;
+
+/* Bytes of device workspace needed by operation `op` (HSS_OP_*) for N keys.
+ * prm may be NULL for HSS_OP_LOCAL_SORT, HSS_OP_MERGE and HSS_OP_EXCHANGE
+ * except that p is then taken from `p_if_no_params`. */
+size_t hss_workspace_bytes(int op, uint64_t N, const hss_params* prm, uint32_t p_if_no_params,
+                           int key_type, int has_payload);
+
+/* Local sort (paper Sec. 5 "local sorting", Sec. 6 phase 1): stably sort each
+ * of the p contiguous segments of d_keys by key.  d_keys_out may equal d_keys.
+ * d_payload / d_payload_out are both NULL or both non-NULL. */
+int hss_local_sort(const void* d_keys, const uint32_t* d_payload, int key_type, uint64_t N, uint32_t p,
+                   void* d_keys_out, uint32_t* d_payload_out, void* d_work, size_t work_bytes, void* stream);
+
+/* Histogram of Sec. 3.3 step 2 / Sec. 4.2.2 step 2: for each of ncuts cuts,
+ * its exact global rank (#keys strictly below it in tag order) over the p
+ * locally sorted segments of d_sorted_keys (as produced by hss_local_sort).
+ * Optionally also the per-segment counts, d_seg_pos[s * ncuts + k] (u32).
+ * d_ranks: ncuts u64. */
+int hss_rank_cuts(const void* d_sorted_keys, int key_type, uint64_t N, uint32_t p,
+                  const hss_cut* d_cuts, uint32_t ncuts, uint64_t* d_ranks, uint32_t* d_seg_pos, void* stream);
+
+/* Splitter determination (Sec. 4.2.2, with the Sec. 6 sampling of
+ * probability s*p/|gamma|): local sort, then histogram rounds until every
+ * splitter i has a probe whose rank is within floor(N eps/(2p)) of
+ * floor(iN/p), then the closest probe becomes the splitter.
+ * Outputs: d_splitters[p-1], d_offsets[p+1] (chi(0)=0 .. chi(p)=N; bucket b
+ * holds ranks [chi(b), chi(b+1))).  The locally sorted keys stay at the start
+ * of d_work.  h_stats (nullable) receives the round statistics. */
+int hss_partition(const void* d_keys, int key_type, uint64_t N, const hss_params* prm,
+                  hss_cut* d_splitters, uint64_t* d_offsets,
+                  void* d_work, size_t work_bytes, hss_stats* h_stats, void* stream);
+
+/* Data exchange (Sec. 3.1 step 3, Sec. 6 "data exchange"): move every run of
+ * locally sorted keys to its bucket.  d_seg_pos[s*(p-1)+i] is the number of
+ * keys of segment s below splitter i (hss_rank_cuts output for the p-1
+ * splitters); d_offsets[p+1] as above.  Bucket b of d_bucket_keys holds the
+ * runs of segments 0..p-1 in order. */
+int hss_exchange(const void* d_sorted_keys, const uint32_t* d_sorted_payload, uint64_t N, uint32_t p,
+                 const uint32_t* d_seg_pos, const uint64_t* d_offsets,
+                 void* d_bucket_keys, uint32_t* d_bucket_payload, void* d_work, size_t work_bytes, void* stream);
+
+/* Local merge (Sec. 5 "merges them", Sec. 6 "local merging"): stably merge the
+ * sorted runs inside each bucket [d_offsets[b], d_offsets[b+1]) by key,
+ * giving the globally sorted output. */
+int hss_merge(const void* d_bucket_keys, const uint32_t* d_bucket_payload, int key_type, uint64_t N, uint32_t p,
+              const uint64_t* d_offsets, void* d_keys_out, uint32_t* d_payload_out,
+              void* d_work, size_t work_bytes, void* stream);
+
+/* The whole method: local sort, splitter rounds, exchange, merge.  Writes the
+ * globally sorted keys (and payload) with processor i owning
+ * [d_offsets[i], d_offsets[i+1]).  d_keys_out may equal d_keys. */
+int hss_sort(const void* d_keys, const uint32_t* d_payload, int key_type, uint64_t N, const hss_params* prm,
+             void* d_keys_out, uint32_t* d_payload_out, hss_cut* d_splitters, uint64_t* d_offsets,
+             void* d_work, size_t work_bytes, hss_stats* h_stats, void* stream);
+
+/* hss_sort from host buffers: copies the keys (and payload) to the
+ * workspace, sorts, and copies the sorted keys, payload, splitters and
+ * offsets back to host memory.  Pinned host memory gives full copy speed.
+ * Synchronous.  Workspace: hss_workspace_bytes(HSS_OP_SORT_HOST, ...). */
+int hss_sort_host(const void* h_keys, const uint32_t* h_payload, int key_type, uint64_t N, const hss_params* prm,
+                  void* h_keys_out, uint32_t* h_payload_out, hss_cut* h_splitters, uint64_t* h_offsets,
+                  void* d_work, size_t work_bytes, hss_stats* h_stats, void* stream);
+
+/* The 64-bit Bernoulli words of the sampling phase (Sec. 4.2.1): for
+ * positions spos0 .. spos0+count-1 of sorted segment `seg` in round `round`,
+ * the Philox4x32-10 word each key is compared against.  d_out: count u64. */
+int hss_sample_words(uint64_t seed, uint32_t seg, uint32_t round, uint32_t spos0, uint32_t count,
+                     uint64_t* d_out, void* stream);
+
+/* Kernels launched by this library in this process so far. */
+uint64_t hss_kernel_launch_count(void);
+
+/* Static description of an error code. */
+const char* hss_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSS_H */

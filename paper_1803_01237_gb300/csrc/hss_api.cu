@@ -1,0 +1,382 @@
+// hss_api.cu -- the C ABI of libhss.so (declared in include/hss.h).
+//
+// Orchestrates the hot path of Histogram Sort with Sampling on one device:
+// local sort (segmented radix sort over the p processor segments), the
+// splitter rounds, the exchange of runs to buckets and the per-bucket merge.
+// All scratch comes from the caller's workspace; the library never allocates.
+#include "hss_internal.cuh"
+#include "segsort.cuh"
+#include "rounds.cuh"
+
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <algorithm>
+
+namespace hss {
+
+static std::atomic<uint64_t> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static inline size_t aup(size_t x) { return (x + 255) / 256 * 256; }
+
+struct Layout {
+    size_t keysA = 0, keysB = 0, payA = 0, payB = 0, seg_off = 0, err = 0, sws = 0, rws = 0, dst = 0;
+    size_t io_keys = 0, io_pay = 0, io_spl = 0, io_off = 0;
+    size_t total = 0;
+    bool has_pay = false;
+};
+
+static const uint64_t kMaxN = 1ull << 40;
+static const uint32_t kMaxP = 1u << 22;
+
+static Layout plan(int op, uint64_t N, uint32_t p, float oversample, bool pay) {
+    Layout L;
+    L.has_pay = pay;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t r = off; off += aup(bytes); return r; };
+    const uint64_t N1 = std::max<uint64_t>(N, 1);
+    switch (op) {
+    case HSS_OP_LOCAL_SORT:
+    case HSS_OP_MERGE:
+        L.keysB = take(N1 * 8);
+        if (pay) L.payB = take(N1 * 4);
+        L.seg_off = take((uint64_t)(p + 1) * 8);
+        L.err = take(256);
+        L.sws = take(segsort_ws_bytes(N1, p));
+        break;
+    case HSS_OP_EXCHANGE:
+        L.seg_off = take((uint64_t)(p + 1) * 8);
+        L.err = take(256);
+        L.dst = take((uint64_t)p * p * 8);
+        break;
+    case HSS_OP_PARTITION:
+    case HSS_OP_SORT:
+    case HSS_OP_SORT_HOST: {
+        L.keysA = take(N1 * 8);
+        L.keysB = take(N1 * 8);
+        if (pay && op != HSS_OP_PARTITION) { L.payA = take(N1 * 4); L.payB = take(N1 * 4); }
+        L.seg_off = take((uint64_t)(p + 1) * 8);
+        L.err = take(256);
+        L.sws = take(segsort_ws_bytes(N1, p));
+        const uint64_t cap = sample_capacity(N, p, oversample);
+        L.rws = take(rounds_ws_bytes(N1, p, cap));
+        if (op != HSS_OP_PARTITION) L.dst = take((uint64_t)p * p * 8);
+        if (op == HSS_OP_SORT_HOST) {
+            L.io_keys = take(N1 * 8);
+            if (pay) L.io_pay = take(N1 * 4);
+            L.io_spl = take((uint64_t)std::max<uint32_t>(p - 1, 1) * sizeof(hss_cut));
+            L.io_off = take((uint64_t)(p + 1) * 8);
+        }
+        break;
+    }
+    default:
+        return L;
+    }
+    L.total = off;
+    return L;
+}
+
+template <typename T>
+static T* at(void* base, size_t off) { return (T*)((char*)base + off); }
+
+static bool params_ok(const hss_params* prm) {
+    if (!prm) return false;
+    if (!(prm->eps > 0.0) || !std::isfinite(prm->eps)) return false;
+    if (prm->p == 0 || prm->p > kMaxP) return false;
+    if (!(prm->oversample > 0.0f) || !std::isfinite(prm->oversample)) return false;
+    if (prm->max_rounds > HSS_MAX_ROUNDS) return false;
+    return true;
+}
+
+static float eff_oversample(const hss_params* prm) { return prm ? prm->oversample : 5.0f; }
+static uint32_t eff_rounds(const hss_params* prm) { return prm->max_rounds == 0 ? HSS_MAX_ROUNDS : prm->max_rounds; }
+
+struct PhaseTimer {
+    bool on = false;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev[HSS_NUM_PHASES + 1] = {};
+    void start(bool enable, cudaStream_t s) {
+        on = enable; st = s;
+        if (!on) return;
+        for (auto& e : ev) cudaEventCreate(&e);
+        cudaEventRecord(ev[0], st);
+    }
+    void mark(int phase_end) { if (on) cudaEventRecord(ev[phase_end + 1], st); }
+    void finish(hss_stats* out, int last_phase) {
+        if (!on) return;
+        cudaEventSynchronize(ev[last_phase + 1]);
+        if (out) {
+            for (int i = 0; i <= last_phase; ++i) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+                out->ms_phase[i] = ms;
+            }
+        }
+        for (auto& e : ev) cudaEventDestroy(e);
+        on = false;
+    }
+};
+
+static int read_dev_err(uint32_t* d_err, cudaStream_t st) {
+    uint32_t h = 0;
+    if (cudaMemcpyAsync(&h, d_err, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return HSS_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return HSS_ERR_CUDA;
+    if (h & kDevErrTimeout) return HSS_ERR_TIMEOUT;
+    if (h & kDevErrBounds) return HSS_ERR_CUDA;
+    return HSS_OK;
+}
+
+// Core of hss_partition / hss_sort.
+static int run_path(const void* d_keys, const uint32_t* d_payload, int key_type, uint64_t N, const hss_params* prm,
+                    void* d_keys_out, uint32_t* d_payload_out, hss_cut* d_splitters, uint64_t* d_offsets,
+                    void* d_work, size_t work_bytes, hss_stats* h_stats, cudaStream_t st, bool sort) {
+    const uint64_t mark = g_launches.load();
+    if (h_stats) std::memset(h_stats, 0, sizeof(*h_stats));
+    if (!params_ok(prm) || (key_type != HSS_KEY_U64 && key_type != HSS_KEY_I64) || N >= kMaxN) return HSS_ERR_INVALID;
+    if ((N > 0 && !d_keys) || !d_offsets || (prm->p > 1 && !d_splitters) || !d_work) return HSS_ERR_INVALID;
+    if (sort && N > 0 && !d_keys_out) return HSS_ERR_INVALID;
+    const bool pay = sort && d_payload != nullptr;
+    if (sort && ((d_payload == nullptr) != (d_payload_out == nullptr))) return HSS_ERR_INVALID;
+    const uint32_t p = prm->p;
+    const float s = prm->oversample;
+    const Layout L = plan(sort ? HSS_OP_SORT : HSS_OP_PARTITION, N, p, s, pay);
+    if (work_bytes < L.total) return HSS_ERR_WORKSPACE;
+
+    uint64_t* keysA = at<uint64_t>(d_work, L.keysA);
+    uint64_t* keysB = at<uint64_t>(d_work, L.keysB);
+    uint32_t* payA = pay ? at<uint32_t>(d_work, L.payA) : nullptr;
+    uint32_t* payB = pay ? at<uint32_t>(d_work, L.payB) : nullptr;
+    uint64_t* seg_off = at<uint64_t>(d_work, L.seg_off);
+    uint32_t* err = at<uint32_t>(d_work, L.err);
+    const uint64_t cap = sample_capacity(N, p, s);
+    SegSortWs sws = segsort_ws_carve(at<void>(d_work, L.sws), std::max<uint64_t>(N, 1), p, err);
+    RoundWs rws = rounds_ws_carve(at<void>(d_work, L.rws), std::max<uint64_t>(N, 1), p, cap, err);
+    const bool i64 = key_type == HSS_KEY_I64;
+    const bool timing = (prm->flags & HSS_FLAG_TIMING) != 0;
+
+    if (cudaMemsetAsync(err, 0, 256, st) != cudaSuccess) return HSS_ERR_CUDA;
+    if (fill_even_offsets(seg_off, N, p, st) != cudaSuccess) return HSS_ERR_CUDA;
+
+    PhaseTimer tm;
+    tm.start(timing, st);
+    SegSortTiming stime;
+    stime.enabled = timing;
+
+    // Local sort (Sec. 5): order-preserving bits into keysA.  With a single
+    // processor the locally sorted segment is already the output.
+    const bool single = sort && p == 1;
+    if (segsort((const uint64_t*)d_keys, single ? (uint64_t*)d_keys_out : keysA, keysB, d_payload,
+                single ? d_payload_out : payA, payB, N, p, seg_off, i64, single && i64, sws, st, &stime) != cudaSuccess)
+        return HSS_ERR_CUDA;
+    tm.mark(HSS_PHASE_LOCAL_SORT);
+
+    // Splitter rounds (Sec. 4.2.2).
+    RoundResult rr;
+    int status = run_rounds(keysA, seg_off, N, p, prm->eps, prm->seed, s, eff_rounds(prm), key_type, d_splitters,
+                            d_offsets, rws, st, &rr);
+    tm.mark(HSS_PHASE_ROUNDS);
+    if (status == HSS_ERR_CUDA) return status;
+
+    if (sort) {
+        if (single) {
+            tm.mark(HSS_PHASE_EXCHANGE);
+            tm.mark(HSS_PHASE_MERGE);
+        } else {
+            uint64_t* dst = at<uint64_t>(d_work, L.dst);
+            // Exchange (Sec. 3.1 step 3): runs to buckets, keysA -> keysB.
+            if (exchange(keysA, payA, N, p, seg_off, rws.Lpos, d_offsets, keysB, payB, dst, err, st) != cudaSuccess)
+                return HSS_ERR_CUDA;
+            tm.mark(HSS_PHASE_EXCHANGE);
+            // Merge (Sec. 6 local merging): stable sort of each bucket's runs.
+            if (segsort(keysB, (uint64_t*)d_keys_out, keysA, payB, d_payload_out, payA, N, p, d_offsets, false, i64, sws,
+                        st, &stime) != cudaSuccess)
+                return HSS_ERR_CUDA;
+            tm.mark(HSS_PHASE_MERGE);
+        }
+    }
+    tm.finish(h_stats, sort ? HSS_PHASE_MERGE : HSS_PHASE_ROUNDS);
+
+    const bool sync = (prm->flags & (HSS_FLAG_SYNC | HSS_FLAG_TIMING)) != 0;
+    if (sync || status == HSS_OK) {
+        // the rounds already synchronised once per round; this read is cheap
+        const int e = read_dev_err(err, st);
+        if (e != HSS_OK && status == HSS_OK) status = e;
+    }
+    if (h_stats) {
+        h_stats->rounds = rr.rounds;
+        h_stats->status = status;
+        h_stats->tol = (uint64_t)std::floor(((double)N * prm->eps) / (2.0 * (double)p));
+        for (uint32_t j = 0; j < rr.rounds && j < HSS_MAX_ROUNDS; ++j) {
+            h_stats->sample_size[j] = rr.sample_size[j];
+            h_stats->gamma[j] = rr.gamma[j];
+        }
+        for (uint32_t j = 0; j <= rr.rounds && j <= HSS_MAX_ROUNDS; ++j) h_stats->unresolved[j] = rr.unresolved[j];
+        h_stats->ms_radix_pass_total = stime.pass_ms;
+        h_stats->radix_pass_launches = stime.pass_launches;
+        h_stats->kernel_launches = (uint32_t)(g_launches.load() - mark);
+    }
+    return status;
+}
+
+}  // namespace hss
+
+using namespace hss;
+
+extern "C" {
+
+size_t hss_workspace_bytes(int op, uint64_t N, const hss_params* prm, uint32_t p_if_no_params, int key_type,
+                           int has_payload) {
+    (void)key_type;
+    const uint32_t p = prm ? prm->p : p_if_no_params;
+    if (p == 0) return 0;
+    const Layout L = plan(op, N, p, eff_oversample(prm), has_payload != 0);
+    return L.total;
+}
+
+int hss_local_sort(const void* d_keys, const uint32_t* d_payload, int key_type, uint64_t N, uint32_t p,
+                   void* d_keys_out, uint32_t* d_payload_out, void* d_work, size_t work_bytes, void* stream) {
+    if ((key_type != HSS_KEY_U64 && key_type != HSS_KEY_I64) || p == 0 || p > kMaxP || N >= kMaxN) return HSS_ERR_INVALID;
+    if (N > 0 && (!d_keys || !d_keys_out)) return HSS_ERR_INVALID;
+    if ((d_payload == nullptr) != (d_payload_out == nullptr) || !d_work) return HSS_ERR_INVALID;
+    const bool pay = d_payload != nullptr;
+    const Layout L = plan(HSS_OP_LOCAL_SORT, N, p, 5.0f, pay);
+    if (work_bytes < L.total) return HSS_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t* err = at<uint32_t>(d_work, L.err);
+    uint64_t* seg_off = at<uint64_t>(d_work, L.seg_off);
+    SegSortWs sws = segsort_ws_carve(at<void>(d_work, L.sws), std::max<uint64_t>(N, 1), p, err);
+    if (cudaMemsetAsync(err, 0, 256, st) != cudaSuccess) return HSS_ERR_CUDA;
+    if (fill_even_offsets(seg_off, N, p, st) != cudaSuccess) return HSS_ERR_CUDA;
+    const bool i64 = key_type == HSS_KEY_I64;
+    if (segsort((const uint64_t*)d_keys, (uint64_t*)d_keys_out, at<uint64_t>(d_work, L.keysB), d_payload, d_payload_out,
+                pay ? at<uint32_t>(d_work, L.payB) : nullptr, N, p, seg_off, i64, i64, sws, st, nullptr) != cudaSuccess)
+        return HSS_ERR_CUDA;
+    return read_dev_err(err, st);
+}
+
+int hss_rank_cuts(const void* d_sorted_keys, int key_type, uint64_t N, uint32_t p, const hss_cut* d_cuts, uint32_t ncuts,
+                  uint64_t* d_ranks, uint32_t* d_seg_pos, void* stream) {
+    (void)N;
+    if ((key_type != HSS_KEY_U64 && key_type != HSS_KEY_I64) || p == 0 || p > kMaxP || N >= kMaxN) return HSS_ERR_INVALID;
+    if (ncuts > 0 && (!d_cuts || !d_ranks || (N > 0 && !d_sorted_keys))) return HSS_ERR_INVALID;
+    if (rank_cuts((const uint64_t*)d_sorted_keys, key_type, N, p, d_cuts, ncuts, d_ranks, d_seg_pos,
+                  (cudaStream_t)stream) != cudaSuccess)
+        return HSS_ERR_CUDA;
+    return HSS_OK;
+}
+
+int hss_partition(const void* d_keys, int key_type, uint64_t N, const hss_params* prm, hss_cut* d_splitters,
+                  uint64_t* d_offsets, void* d_work, size_t work_bytes, hss_stats* h_stats, void* stream) {
+    return run_path(d_keys, nullptr, key_type, N, prm, nullptr, nullptr, d_splitters, d_offsets, d_work, work_bytes, h_stats,
+                    (cudaStream_t)stream, false);
+}
+
+int hss_exchange(const void* d_sorted_keys, const uint32_t* d_sorted_payload, uint64_t N, uint32_t p,
+                 const uint32_t* d_seg_pos, const uint64_t* d_offsets, void* d_bucket_keys, uint32_t* d_bucket_payload,
+                 void* d_work, size_t work_bytes, void* stream) {
+    if (p == 0 || p > kMaxP || N >= kMaxN || !d_offsets || !d_work) return HSS_ERR_INVALID;
+    if (N > 0 && (!d_sorted_keys || !d_bucket_keys || (p > 1 && !d_seg_pos))) return HSS_ERR_INVALID;
+    if ((d_sorted_payload == nullptr) != (d_bucket_payload == nullptr)) return HSS_ERR_INVALID;
+    const Layout L = plan(HSS_OP_EXCHANGE, N, p, 5.0f, d_sorted_payload != nullptr);
+    if (work_bytes < L.total) return HSS_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t* err = at<uint32_t>(d_work, L.err);
+    uint64_t* seg_off = at<uint64_t>(d_work, L.seg_off);
+    if (cudaMemsetAsync(err, 0, 256, st) != cudaSuccess) return HSS_ERR_CUDA;
+    if (fill_even_offsets(seg_off, N, p, st) != cudaSuccess) return HSS_ERR_CUDA;
+    if (p == 1) {
+        if (N > 0 && cudaMemcpyAsync(d_bucket_keys, d_sorted_keys, N * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return HSS_ERR_CUDA;
+        if (N > 0 && d_sorted_payload &&
+            cudaMemcpyAsync(d_bucket_payload, d_sorted_payload, N * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return HSS_ERR_CUDA;
+        return HSS_OK;
+    }
+    if (exchange((const uint64_t*)d_sorted_keys, d_sorted_payload, N, p, seg_off, d_seg_pos, d_offsets,
+                 (uint64_t*)d_bucket_keys, d_bucket_payload, at<uint64_t>(d_work, L.dst), err, st) != cudaSuccess)
+        return HSS_ERR_CUDA;
+    return read_dev_err(err, st);
+}
+
+int hss_merge(const void* d_bucket_keys, const uint32_t* d_bucket_payload, int key_type, uint64_t N, uint32_t p,
+              const uint64_t* d_offsets, void* d_keys_out, uint32_t* d_payload_out, void* d_work, size_t work_bytes,
+              void* stream) {
+    if ((key_type != HSS_KEY_U64 && key_type != HSS_KEY_I64) || p == 0 || p > kMaxP || N >= kMaxN) return HSS_ERR_INVALID;
+    if (!d_offsets || !d_work || (N > 0 && (!d_bucket_keys || !d_keys_out))) return HSS_ERR_INVALID;
+    if ((d_bucket_payload == nullptr) != (d_payload_out == nullptr)) return HSS_ERR_INVALID;
+    const bool pay = d_bucket_payload != nullptr;
+    const Layout L = plan(HSS_OP_MERGE, N, p, 5.0f, pay);
+    if (work_bytes < L.total) return HSS_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t* err = at<uint32_t>(d_work, L.err);
+    SegSortWs sws = segsort_ws_carve(at<void>(d_work, L.sws), std::max<uint64_t>(N, 1), p, err);
+    if (cudaMemsetAsync(err, 0, 256, st) != cudaSuccess) return HSS_ERR_CUDA;
+    const bool i64 = key_type == HSS_KEY_I64;
+    if (segsort((const uint64_t*)d_bucket_keys, (uint64_t*)d_keys_out, at<uint64_t>(d_work, L.keysB), d_bucket_payload,
+                d_payload_out, pay ? at<uint32_t>(d_work, L.payB) : nullptr, N, p, d_offsets, i64, i64, sws, st,
+                nullptr) != cudaSuccess)
+        return HSS_ERR_CUDA;
+    return read_dev_err(err, st);
+}
+
+int hss_sort(const void* d_keys, const uint32_t* d_payload, int key_type, uint64_t N, const hss_params* prm,
+             void* d_keys_out, uint32_t* d_payload_out, hss_cut* d_splitters, uint64_t* d_offsets, void* d_work,
+             size_t work_bytes, hss_stats* h_stats, void* stream) {
+    return run_path(d_keys, d_payload, key_type, N, prm, d_keys_out, d_payload_out, d_splitters, d_offsets, d_work,
+                    work_bytes, h_stats, (cudaStream_t)stream, true);
+}
+
+int hss_sort_host(const void* h_keys, const uint32_t* h_payload, int key_type, uint64_t N, const hss_params* prm,
+                  void* h_keys_out, uint32_t* h_payload_out, hss_cut* h_splitters, uint64_t* h_offsets, void* d_work,
+                  size_t work_bytes, hss_stats* h_stats, void* stream) {
+    if (!params_ok(prm) || !d_work || !h_offsets || (N > 0 && (!h_keys || !h_keys_out))) return HSS_ERR_INVALID;
+    if ((h_payload == nullptr) != (h_payload_out == nullptr)) return HSS_ERR_INVALID;
+    const uint32_t p = prm->p;
+    const bool pay = h_payload != nullptr;
+    const Layout L = plan(HSS_OP_SORT_HOST, N, p, prm->oversample, pay);
+    if (work_bytes < L.total) return HSS_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint64_t* io = at<uint64_t>(d_work, L.io_keys);
+    uint32_t* iop = pay ? at<uint32_t>(d_work, L.io_pay) : nullptr;
+    hss_cut* spl = at<hss_cut>(d_work, L.io_spl);
+    uint64_t* off = at<uint64_t>(d_work, L.io_off);
+    if (N > 0 && cudaMemcpyAsync(io, h_keys, N * 8, cudaMemcpyHostToDevice, st) != cudaSuccess) return HSS_ERR_CUDA;
+    if (pay && N > 0 && cudaMemcpyAsync(iop, h_payload, N * 4, cudaMemcpyHostToDevice, st) != cudaSuccess) return HSS_ERR_CUDA;
+    // run with the SORT layout inside the same workspace (it is a prefix of SORT_HOST's)
+    int rc = run_path(io, iop, key_type, N, prm, io, iop, spl, off, d_work, work_bytes, h_stats, st, true);
+    if (rc == HSS_ERR_CUDA || rc == HSS_ERR_INVALID || rc == HSS_ERR_WORKSPACE) return rc;
+    if (N > 0 && cudaMemcpyAsync(h_keys_out, io, N * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return HSS_ERR_CUDA;
+    if (pay && N > 0 && cudaMemcpyAsync(h_payload_out, iop, N * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return HSS_ERR_CUDA;
+    if (p > 1 && h_splitters &&
+        cudaMemcpyAsync(h_splitters, spl, (uint64_t)(p - 1) * sizeof(hss_cut), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return HSS_ERR_CUDA;
+    if (cudaMemcpyAsync(h_offsets, off, (uint64_t)(p + 1) * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return HSS_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return HSS_ERR_CUDA;
+    return rc;
+}
+
+int hss_sample_words(uint64_t seed, uint32_t seg, uint32_t round, uint32_t spos0, uint32_t count, uint64_t* d_out,
+                     void* stream) {
+    if (count > 0 && !d_out) return HSS_ERR_INVALID;
+    if ((uint64_t)spos0 + count > (1ull << 32)) return HSS_ERR_INVALID;
+    if (sample_words_launch(seed, seg, round, spos0, count, d_out, (cudaStream_t)stream) != cudaSuccess) return HSS_ERR_CUDA;
+    return HSS_OK;
+}
+
+uint64_t hss_kernel_launch_count(void) { return g_launches.load(); }
+
+const char* hss_strerror(int code) {
+    switch (code) {
+    case HSS_OK: return "ok";
+    case HSS_ERR_INVALID: return "invalid argument";
+    case HSS_ERR_WORKSPACE: return "workspace too small";
+    case HSS_ERR_ROUND_LIMIT: return "round limit reached with unresolved splitters";
+    case HSS_ERR_TIMEOUT: return "a bounded device-side wait timed out";
+    case HSS_ERR_CUDA: return "CUDA runtime error";
+    case HSS_ERR_CAPACITY: return "a round drew more probes than the sample buffer holds";
+    default: return "unknown error";
+    }
+}
+
+}  // extern "C"

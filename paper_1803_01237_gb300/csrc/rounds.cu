@@ -1,0 +1,789 @@
+// rounds.cu -- splitter determination of HSS (Sec. 4.2.2) on one GB300.
+//
+// The p processors are the p locally sorted segments of one device array.
+// One round:
+//   sample   every key strictly inside a distinct unresolved splitter
+//            interval is kept with probability q = min(1, s p/|gamma|) by
+//            comparing its Philox4x32-10 word with T = floor(q 2^64); the
+//            draw needs only (segment, position, round), so keys are read
+//            only for the keys that are kept.  A CTA per segment walks the
+//            interval ranges of its segment, marks a bitmap and counts; a
+//            second pass writes the kept keys in (segment, position) order.
+//   sort     the probes, stably by key (the segmented radix sort with one
+//            segment), i.e. in (key, segment, position) tag order.
+//   histogram the exact global rank of every probe: for every segment a
+//            branch-free binary search confined to the probe's interval,
+//            giving also the per-segment counts the next round and the
+//            exchange need.
+//   update   L_i / U_i move to the best-ranked probe at or below / at or above
+//            t_i = floor(iN/p); a splitter resolves when one of them is within
+//            tol = floor(N eps/(2p)) of t_i; the distinct unresolved intervals,
+//            |gamma| and the next threshold are computed on the device.
+// The host reads one small status record per round.
+#include "rounds.cuh"
+
+#include <cmath>
+#include <algorithm>
+
+namespace hss {
+
+static inline uint64_t cdiv(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+static inline size_t aup(size_t x) { return (x + 255) / 256 * 256; }
+
+uint64_t sample_capacity(uint64_t N, uint64_t p, float oversample) {
+    const double want = std::ceil(2.0 * (double)oversample * (double)p) + 4096.0;
+    uint64_t cap = (uint64_t)std::min<double>(want, (double)std::max<uint64_t>(N, 1));
+    return std::max<uint64_t>(cap, 1);
+}
+
+size_t rounds_ws_bytes(uint64_t N, uint64_t p, uint64_t cap) {
+    const uint64_t S = p > 0 ? p - 1 : 0;
+    const uint64_t S1 = std::max<uint64_t>(S, 1);
+    size_t b = 0;
+    b += aup(sizeof(RoundCtl));
+    b += 2 * aup(S1 * sizeof(DCut));
+    b += 2 * aup(p * S1 * sizeof(uint32_t));
+    b += 6 * aup(S1 * sizeof(uint32_t));
+    b += aup((N / 32 + 2) * sizeof(uint32_t));
+    b += aup(p * sizeof(uint32_t)) + aup((p + 1) * sizeof(uint32_t));
+    b += 3 * aup(cap * sizeof(uint64_t));      // skey, skey_sorted, stmp
+    b += 5 * aup(cap * sizeof(uint32_t));      // sseg, sspos, siota, sperm, ptmp
+    b += aup(cap * sizeof(uint64_t)) * 2;      // pkey, prank
+    b += 3 * aup(cap * sizeof(uint32_t));      // pseg, pspos, pint
+    b += aup(p * cap * sizeof(uint32_t));      // probe_pos
+    b += segsort_ws_bytes(cap, 1);
+    return b;
+}
+
+RoundWs rounds_ws_carve(void* base, uint64_t N, uint64_t p, uint64_t cap, uint32_t* err) {
+    const uint64_t S = p > 0 ? p - 1 : 0;
+    const uint64_t S1 = std::max<uint64_t>(S, 1);
+    RoundWs w;
+    char* q = (char*)base;
+    auto take = [&](size_t bytes) { void* r = q; q += aup(bytes); return r; };
+    w.ctl = (RoundCtl*)take(sizeof(RoundCtl));
+    w.Lcut = (DCut*)take(S1 * sizeof(DCut));
+    w.Ucut = (DCut*)take(S1 * sizeof(DCut));
+    w.Lpos = (uint32_t*)take(p * S1 * sizeof(uint32_t));
+    w.Upos = (uint32_t*)take(p * S1 * sizeof(uint32_t));
+    w.res = (uint32_t*)take(S1 * sizeof(uint32_t));
+    w.chgL = (int32_t*)take(S1 * sizeof(uint32_t));
+    w.chgU = (int32_t*)take(S1 * sizeof(uint32_t));
+    w.choose_u = (uint32_t*)take(S1 * sizeof(uint32_t));
+    w.int_rep = (uint32_t*)take(S1 * sizeof(uint32_t));
+    take(S1 * sizeof(uint32_t));
+    w.bitmap = (uint32_t*)take((N / 32 + 2) * sizeof(uint32_t));
+    w.seg_cnt = (uint32_t*)take(p * sizeof(uint32_t));
+    w.seg_cnt_off = (uint32_t*)take((p + 1) * sizeof(uint32_t));
+    w.skey = (uint64_t*)take(cap * sizeof(uint64_t));
+    w.skey_sorted = (uint64_t*)take(cap * sizeof(uint64_t));
+    w.stmp = (uint64_t*)take(cap * sizeof(uint64_t));
+    w.sseg = (uint32_t*)take(cap * sizeof(uint32_t));
+    w.sspos = (uint32_t*)take(cap * sizeof(uint32_t));
+    w.siota = (uint32_t*)take(cap * sizeof(uint32_t));
+    w.sperm = (uint32_t*)take(cap * sizeof(uint32_t));
+    w.ptmp = (uint32_t*)take(cap * sizeof(uint32_t));
+    w.pkey = (uint64_t*)take(cap * sizeof(uint64_t));
+    w.prank = (uint64_t*)take(cap * sizeof(uint64_t));
+    w.pseg = (int32_t*)take(cap * sizeof(uint32_t));
+    w.pspos = (uint32_t*)take(cap * sizeof(uint32_t));
+    w.pint = (uint32_t*)take(cap * sizeof(uint32_t));
+    w.probe_pos = (uint32_t*)take(p * cap * sizeof(uint32_t));
+    w.sws = segsort_ws_carve(q, cap, 1, err);
+    w.cap = cap;
+    return w;
+}
+
+// ---------------------------------------------------------------------------
+// Block scans (blockDim a multiple of 32, at most 1024).
+// ---------------------------------------------------------------------------
+template <typename T, typename Op>
+__device__ __forceinline__ T warp_incl_scan(T x, Op op) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x = op(x, y);
+    }
+    return x;
+}
+
+// Inclusive block scan with identity `id`; returns the inclusive value and
+// sets `total`.  Uses s_warp[32] of T.
+template <typename T, typename Op>
+__device__ __forceinline__ T block_incl_scan(T v, T id, Op op, T* s_warp, T& total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T x = warp_incl_scan(v, op);
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        T y = lane < nw ? s_warp[lane] : id;
+        y = warp_incl_scan(y, op);
+        s_warp[lane] = y;
+    }
+    __syncthreads();
+    T r = w > 0 ? op(s_warp[w - 1], x) : x;
+    total = s_warp[nw - 1];
+    __syncthreads();
+    return r;
+}
+
+struct AddU32 { __device__ uint32_t operator()(uint32_t a, uint32_t b) const { return a + b; } };
+struct AddU64 { __device__ uint64_t operator()(uint64_t a, uint64_t b) const { return a + b; } };
+struct MaxI32 { __device__ int32_t operator()(int32_t a, int32_t b) const { return a > b ? a : b; } };
+
+__device__ __forceinline__ uint64_t ideal_rank(uint64_t i1, uint64_t N, uint64_t p) {
+    return (uint64_t)(((unsigned __int128)i1 * N) / p);  // t_i for splitter number i1 (1-based)
+}
+
+// ---------------------------------------------------------------------------
+// Initial state: every splitter interval is (-inf, +inf).
+// ---------------------------------------------------------------------------
+__global__ void k_rounds_init(const uint64_t* __restrict__ seg_off, uint32_t S, uint64_t N, DCut* Lcut, DCut* Ucut,
+                              uint32_t* Lpos, uint32_t* Upos) {
+    const uint64_t s = blockIdx.x;
+    const uint32_t i = blockIdx.y * blockDim.x + threadIdx.x;
+    if (i >= S) return;
+    const uint32_t n = (uint32_t)(seg_off[s + 1] - seg_off[s]);
+    Lpos[s * S + i] = 0;
+    Upos[s * S + i] = n;
+    if (s == 0) {
+        DCut a; a.okey = 0; a.seg = -2; a.spos = 0; a.rank = 0; a.kind = kNegInf; a.pad = 0;
+        DCut b; b.okey = 0; b.seg = -3; b.spos = 0; b.rank = N; b.kind = kPosInf; b.pad = 0;
+        Lcut[i] = a;
+        Ucut[i] = b;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Resolved flags, distinct unresolved intervals, |gamma| and the threshold.
+// One CTA of 1024 threads walks the splitters in chunks.
+// ---------------------------------------------------------------------------
+__global__ __launch_bounds__(1024) void k_intervals(uint32_t S, uint64_t N, uint32_t p, uint64_t tol, float oversample,
+                                                    const DCut* __restrict__ Lcut, const DCut* __restrict__ Ucut,
+                                                    uint32_t* __restrict__ res, uint32_t* __restrict__ int_rep,
+                                                    RoundCtl* ctl) {
+    __shared__ uint32_t s_u32[32];
+    __shared__ int32_t s_i32[32];
+    __shared__ uint64_t s_u64[32];
+    uint32_t carry_heads = 0, carry_f = 0, carry_unres = 0;
+    int32_t carry_max = -1;
+    uint64_t gamma = 0;
+    for (uint32_t base = 0; base < S; base += blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        const bool valid = i < S;
+        uint32_t head = 0, unres = 0;
+        uint64_t glen = 0;
+        if (valid) {
+            const DCut L = Lcut[i], U = Ucut[i];
+            const uint64_t t = ideal_rank(i + 1, N, p);
+            const bool r = (t - L.rank) <= tol || (U.rank - t) <= tol;
+            res[i] = r ? 1u : 0u;
+            unres = r ? 0u : 1u;
+            head = (i == 0) || !(cut_equal(L, Lcut[i - 1]) && cut_equal(U, Ucut[i - 1]));
+            glen = U.rank - L.rank - (L.kind == kMember ? 1u : 0u);
+        }
+        uint32_t tot;
+        const uint32_t heads_incl = block_incl_scan<uint32_t>(head, 0u, AddU32(), s_u32, tot) + carry_heads;
+        carry_heads += tot;
+        const int32_t rid = (int32_t)heads_incl - 1;
+        int32_t mtot;
+        const int32_t mv = unres ? rid : -1;
+        int32_t mincl = block_incl_scan<int32_t>(mv, -1, MaxI32(), s_i32, mtot);
+        mincl = mincl > carry_max ? mincl : carry_max;
+        int32_t mexcl = __shfl_up_sync(0xffffffffu, mincl, 1);
+        // lane 0 needs the previous warp's last value
+        __shared__ int32_t s_last[32];
+        if ((threadIdx.x & 31) == 31) s_last[threadIdx.x >> 5] = mincl;
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) mexcl = (threadIdx.x == 0) ? carry_max : s_last[(threadIdx.x >> 5) - 1];
+        __syncthreads();
+        carry_max = carry_max > mtot ? carry_max : mtot;
+        const uint32_t f = (valid && unres && mexcl != rid) ? 1u : 0u;
+        uint32_t ftot;
+        const uint32_t fincl = block_incl_scan<uint32_t>(f, 0u, AddU32(), s_u32, ftot);
+        if (f) int_rep[carry_f + fincl - 1] = i;
+        carry_f += ftot;
+        uint32_t utot;
+        block_incl_scan<uint32_t>(unres, 0u, AddU32(), s_u32, utot);
+        carry_unres += utot;
+        uint64_t gtot;
+        block_incl_scan<uint64_t>(f ? glen : 0ull, 0ull, AddU64(), s_u64, gtot);
+        gamma += gtot;
+    }
+    if (threadIdx.x == 0) {
+        ctl->gamma = gamma;
+        ctl->nint = carry_f;
+        ctl->unresolved = carry_unres;
+        double q = gamma == 0 ? 1.0 : ((double)oversample * (double)p) / (double)gamma;
+        if (q >= 1.0) {
+            ctl->take_all = 1u;
+            ctl->T = 0ull;
+        } else {
+            ctl->take_all = 0u;
+            ctl->T = (uint64_t)floor(ldexp(q, 64));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Sampling.
+// ---------------------------------------------------------------------------
+constexpr int kIntChunk = 2048;
+constexpr int kSampThreads = 256;
+
+// Fill the interval ranges of segment s for intervals [u0, u0+nu) and the
+// exclusive prefix of their position-pair counts.  Returns the pair total.
+__device__ uint32_t load_seg_intervals(uint32_t s, uint32_t n_s, uint32_t S, uint32_t u0, uint32_t nu,
+                                       const uint32_t* __restrict__ Lpos, const uint32_t* __restrict__ Upos,
+                                       const DCut* __restrict__ Lcut, const uint32_t* __restrict__ int_rep,
+                                       uint32_t* s_a, uint32_t* s_b, uint32_t* s_pre, uint32_t* s_warp) {
+    constexpr int kPer = kIntChunk / kSampThreads;
+    uint32_t loc[kPer];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const uint32_t u = threadIdx.x * kPer + k;
+        uint32_t np = 0;
+        if (u < nu) {
+            const uint32_t rep = int_rep[u0 + u];
+            const DCut L = Lcut[rep];
+            uint32_t a = Lpos[(uint64_t)s * S + rep];
+            if (L.kind == kMember && (uint32_t)L.seg == s) a += 1;
+            uint32_t b = Upos[(uint64_t)s * S + rep];
+            if (b > n_s) b = n_s;  // defensive: a range never leaves its segment
+            s_a[u] = a;
+            s_b[u] = b;
+            np = b > a ? ((b - 1) >> 1) - (a >> 1) + 1 : 0u;
+        }
+        loc[k] = sum;
+        sum += np;
+    }
+    uint32_t tot;
+    const uint32_t incl = block_incl_scan<uint32_t>(sum, 0u, AddU32(), s_warp, tot);
+    const uint32_t ex = incl - sum;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const uint32_t u = threadIdx.x * kPer + k;
+        if (u < nu) s_pre[u] = ex + loc[k];
+    }
+    if (threadIdx.x == 0) s_pre[nu] = tot;
+    __syncthreads();
+    return tot;
+}
+
+__device__ __forceinline__ uint32_t find_interval(const uint32_t* s_pre, uint32_t nu, uint32_t f) {
+    uint32_t lo = 0, hi = nu;  // last u with s_pre[u] <= f
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s_pre[mid] <= f) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ __launch_bounds__(kSampThreads) void k_sample_mark(
+    const uint64_t* __restrict__ seg_off, uint32_t S, const uint32_t* __restrict__ Lpos, const uint32_t* __restrict__ Upos,
+    const DCut* __restrict__ Lcut, const uint32_t* __restrict__ int_rep, const RoundCtl* __restrict__ ctl,
+    uint64_t seed, uint32_t round, uint32_t* __restrict__ bitmap, uint32_t* __restrict__ seg_cnt) {
+    __shared__ uint32_t s_a[kIntChunk], s_b[kIntChunk], s_pre[kIntChunk + 1];
+    __shared__ uint32_t s_warp[32];
+    const uint32_t s = blockIdx.x;
+    const uint64_t base = seg_off[s];
+    const uint32_t nint = ctl->nint;
+    const uint64_t T = ctl->T;
+    const bool take_all = ctl->take_all != 0;
+    uint32_t cnt = 0;
+    for (uint32_t u0 = 0; u0 < nint; u0 += kIntChunk) {
+        const uint32_t nu = min((uint32_t)kIntChunk, nint - u0);
+        const uint32_t P = load_seg_intervals(s, (uint32_t)(seg_off[s + 1] - base), S, u0, nu, Lpos, Upos, Lcut, int_rep,
+                                              s_a, s_b, s_pre, s_warp);
+        for (uint32_t f = threadIdx.x; f < P; f += kSampThreads) {
+            const uint32_t u = find_interval(s_pre, nu, f);
+            const uint32_t a = s_a[u], b = s_b[u];
+            const uint32_t m = (a >> 1) + (f - s_pre[u]);
+            uint64_t w0, w1;
+            sample_words(seed, s, round, m, w0, w1);
+            const uint32_t p0 = 2 * m, p1 = 2 * m + 1;
+            if (p0 >= a && p0 < b && (take_all || w0 < T)) {
+                const uint64_t g = base + p0;
+                atomicOr(&bitmap[g >> 5], 1u << (g & 31));
+                ++cnt;
+            }
+            if (p1 >= a && p1 < b && (take_all || w1 < T)) {
+                const uint64_t g = base + p1;
+                atomicOr(&bitmap[g >> 5], 1u << (g & 31));
+                ++cnt;
+            }
+        }
+        __syncthreads();
+    }
+    uint32_t tot;
+    block_incl_scan<uint32_t>(cnt, 0u, AddU32(), s_warp, tot);
+    if (threadIdx.x == 0) seg_cnt[s] = tot;
+}
+
+__global__ __launch_bounds__(1024) void k_count_scan(const uint32_t* __restrict__ seg_cnt, uint32_t p, uint32_t* __restrict__ seg_cnt_off,
+                                                     uint64_t cap, RoundCtl* ctl) {
+    __shared__ uint32_t s_warp[32];
+    uint64_t carry = 0;
+    for (uint32_t base = 0; base < p; base += blockDim.x) {
+        const uint32_t s = base + threadIdx.x;
+        const uint32_t v = s < p ? seg_cnt[s] : 0u;
+        uint32_t tot;
+        const uint32_t incl = block_incl_scan<uint32_t>(v, 0u, AddU32(), s_warp, tot);
+        if (s < p) seg_cnt_off[s] = (uint32_t)(carry + incl - v < 0xffffffffull ? carry + incl - v : 0xffffffffull);
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        seg_cnt_off[p] = (uint32_t)(carry < 0xffffffffull ? carry : 0xffffffffull);
+        ctl->Z = carry;
+        ctl->seg_off_z[0] = 0;
+        ctl->seg_off_z[1] = carry < cap ? carry : cap;
+    }
+}
+
+__global__ __launch_bounds__(kSampThreads) void k_sample_write(
+    const uint64_t* __restrict__ skeys, const uint64_t* __restrict__ seg_off, uint32_t S,
+    const uint32_t* __restrict__ Lpos, const uint32_t* __restrict__ Upos, const DCut* __restrict__ Lcut,
+    const uint32_t* __restrict__ int_rep, const RoundCtl* __restrict__ ctl, const uint32_t* __restrict__ bitmap,
+    const uint32_t* __restrict__ seg_cnt, const uint32_t* __restrict__ seg_cnt_off, uint64_t cap,
+    uint64_t* __restrict__ skey, uint32_t* __restrict__ sseg, uint32_t* __restrict__ sspos, uint32_t* __restrict__ siota) {
+    __shared__ uint32_t s_a[kIntChunk], s_b[kIntChunk], s_pre[kIntChunk + 1];
+    __shared__ uint32_t s_warp[32];
+    const uint32_t s = blockIdx.x;
+    if (seg_cnt[s] == 0) return;
+    const uint64_t base = seg_off[s];
+    const uint32_t nint = ctl->nint;
+    uint64_t out = seg_cnt_off[s];
+    for (uint32_t u0 = 0; u0 < nint; u0 += kIntChunk) {
+        const uint32_t nu = min((uint32_t)kIntChunk, nint - u0);
+        const uint32_t P = load_seg_intervals(s, (uint32_t)(seg_off[s + 1] - base), S, u0, nu, Lpos, Upos, Lcut, int_rep,
+                                              s_a, s_b, s_pre, s_warp);
+        for (uint32_t fb = 0; fb < P; fb += kSampThreads) {
+            const uint32_t f = fb + threadIdx.x;
+            bool k0 = false, k1 = false;
+            uint32_t m = 0;
+            if (f < P) {
+                const uint32_t u = find_interval(s_pre, nu, f);
+                const uint32_t a = s_a[u], b = s_b[u];
+                m = (a >> 1) + (f - s_pre[u]);
+                const uint32_t p0 = 2 * m, p1 = 2 * m + 1;
+                if (p0 >= a && p0 < b) { const uint64_t g = base + p0; k0 = (bitmap[g >> 5] >> (g & 31)) & 1u; }
+                if (p1 >= a && p1 < b) { const uint64_t g = base + p1; k1 = (bitmap[g >> 5] >> (g & 31)) & 1u; }
+            }
+            const uint32_t c = (uint32_t)k0 + (uint32_t)k1;
+            uint32_t tot;
+            const uint32_t incl = block_incl_scan<uint32_t>(c, 0u, AddU32(), s_warp, tot);
+            uint64_t o = out + incl - c;
+            if (k0) {
+                if (o < cap) { skey[o] = skeys[base + 2 * m]; sseg[o] = s; sspos[o] = 2 * m; siota[o] = (uint32_t)o; }
+                ++o;
+            }
+            if (k1) {
+                if (o < cap) { skey[o] = skeys[base + 2 * m + 1]; sseg[o] = s; sspos[o] = 2 * m + 1; siota[o] = (uint32_t)o; }
+            }
+            out += tot;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Probes: gather the sorted sample, find each probe's interval.
+// ---------------------------------------------------------------------------
+__global__ void k_probe_build(uint64_t Z, const uint64_t* __restrict__ skey_sorted, const uint32_t* __restrict__ sperm,
+                              const uint32_t* __restrict__ sseg, const uint32_t* __restrict__ sspos,
+                              const DCut* __restrict__ Ucut, const uint32_t* __restrict__ int_rep, const RoundCtl* __restrict__ ctl,
+                              uint64_t* __restrict__ pkey, int32_t* __restrict__ pseg, uint32_t* __restrict__ pspos,
+                              uint32_t* __restrict__ pint, uint64_t* __restrict__ prank) {
+    const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Z) return;
+    const uint32_t j = sperm[k];
+    DCut c;
+    c.okey = skey_sorted[k]; c.seg = (int32_t)sseg[j]; c.spos = sspos[j]; c.rank = 0; c.kind = kMember; c.pad = 0;
+    pkey[k] = c.okey; pseg[k] = c.seg; pspos[k] = c.spos; prank[k] = 0;
+    uint32_t lo = 0, hi = ctl->nint;  // first interval whose upper cut lies above the probe
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (cut_less(c, Ucut[int_rep[mid]])) hi = mid; else lo = mid + 1;
+    }
+    pint[k] = lo;
+}
+
+// Count of keys in a[0..n) below key: strict (<) or not (<=), branch-free.
+__device__ __forceinline__ uint32_t count_below(const uint64_t* __restrict__ a, uint32_t n, uint64_t key, bool strict) {
+    uint32_t base = 0;
+    while (n > 0) {
+        const uint32_t half = n >> 1;
+        const uint64_t v = a[base + half];
+        const bool go = strict ? (v < key) : (v <= key);
+        base = go ? base + half + 1 : base;
+        n = go ? n - half - 1 : half;
+    }
+    return base;
+}
+
+constexpr int kHistSegPerBlock = 64;
+
+__global__ __launch_bounds__(256) void k_histogram(
+    const uint64_t* __restrict__ skeys, const uint64_t* __restrict__ seg_off, uint32_t p, uint32_t S,
+    const uint32_t* __restrict__ Lpos, const uint32_t* __restrict__ Upos, const uint32_t* __restrict__ int_rep,
+    const uint64_t* __restrict__ pkey, const int32_t* __restrict__ pseg, const uint32_t* __restrict__ pspos,
+    const uint32_t* __restrict__ pint, uint64_t Z, uint64_t* __restrict__ prank, uint32_t* __restrict__ probe_pos,
+    uint64_t cap, uint32_t* __restrict__ err) {
+    __shared__ uint64_t s_part[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint64_t k = (uint64_t)blockIdx.x * 32 + lane;
+    const bool valid = k < Z;
+    uint64_t key = 0; int32_t seg = 0; uint32_t spos = 0, rep = 0;
+    if (valid) { key = pkey[k]; seg = pseg[k]; spos = pspos[k]; rep = int_rep[pint[k]]; }
+    uint64_t partial = 0;
+#pragma unroll 2
+    for (int j = 0; j < kHistSegPerBlock / 8; ++j) {
+        const uint32_t s = blockIdx.y * kHistSegPerBlock + j * 8 + w;
+        if (valid && s < p) {
+            uint32_t pos;
+            if ((int32_t)s == seg) {
+                pos = spos;
+            } else {
+                const uint32_t lo = Lpos[(uint64_t)s * S + rep], hi = Upos[(uint64_t)s * S + rep];
+                const uint32_t n = (uint32_t)(seg_off[s + 1] - seg_off[s]);
+                if (lo <= hi && hi <= n) {
+                    pos = lo + count_below(skeys + seg_off[s] + lo, hi - lo, key, (int32_t)s > seg);
+                } else {  // inconsistent interval state: record, do not read out of range
+                    atomicOr(err, kDevErrBounds);
+                    pos = lo;
+                }
+            }
+            probe_pos[(uint64_t)s * cap + k] = pos;
+            partial += pos;
+        }
+    }
+    s_part[w][lane] = partial;
+    __syncthreads();
+    if (w == 0 && valid) {
+        uint64_t sum = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) sum += s_part[i][lane];
+        atomicAdd((unsigned long long*)&prank[k], (unsigned long long)sum);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// L/U update of every splitter from the ranked probes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void offer(DCut& L, DCut& U, int32_t& cl, int32_t& cu, uint64_t t, const DCut& c, int32_t k) {
+    if (c.rank <= t && (c.rank > L.rank || (c.rank == L.rank && cut_less(c, L)))) { L = c; cl = k; }
+    if (c.rank >= t && (c.rank < U.rank || (c.rank == U.rank && cut_less(c, U)))) { U = c; cu = k; }
+}
+
+__global__ void k_update(uint32_t S, uint64_t N, uint32_t p, const uint64_t* __restrict__ pkey, const int32_t* __restrict__ pseg,
+                         const uint32_t* __restrict__ pspos, const uint64_t* __restrict__ prank, uint64_t Z,
+                         DCut* __restrict__ Lcut, DCut* __restrict__ Ucut, int32_t* __restrict__ chgL, int32_t* __restrict__ chgU) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S) return;
+    const uint64_t t = ideal_rank(i + 1, N, p);
+    uint64_t lo = 0, hi = Z;  // first probe with rank > t
+    while (lo < hi) { const uint64_t m = (lo + hi) >> 1; if (prank[m] <= t) lo = m + 1; else hi = m; }
+    const uint64_t kgt = lo;
+    lo = 0; hi = Z;           // first probe with rank >= t
+    while (lo < hi) { const uint64_t m = (lo + hi) >> 1; if (prank[m] < t) lo = m + 1; else hi = m; }
+    const uint64_t kge = lo;
+    DCut L = Lcut[i], U = Ucut[i];
+    int32_t cl = -1, cu = -1;
+    auto probe = [&](uint64_t k) {
+        DCut c; c.okey = pkey[k]; c.seg = pseg[k]; c.spos = pspos[k]; c.rank = prank[k]; c.kind = kMember; c.pad = 0;
+        return c;
+    };
+    if (kgt > 0) offer(L, U, cl, cu, t, probe(kgt - 1), (int32_t)(kgt - 1));
+    if (kge < Z) offer(L, U, cl, cu, t, probe(kge), (int32_t)kge);
+    Lcut[i] = L; Ucut[i] = U; chgL[i] = cl; chgU[i] = cu;
+}
+
+__global__ void k_update_pos(uint32_t S, const int32_t* __restrict__ chgL, const int32_t* __restrict__ chgU,
+                             const uint32_t* __restrict__ probe_pos, uint64_t cap, uint32_t* __restrict__ Lpos,
+                             uint32_t* __restrict__ Upos) {
+    const uint64_t s = blockIdx.x;
+    const uint32_t i = blockIdx.y * blockDim.x + threadIdx.x;
+    if (i >= S) return;
+    const int32_t cl = chgL[i], cu = chgU[i];
+    if (cl >= 0) Lpos[s * S + i] = probe_pos[s * cap + (uint32_t)cl];
+    if (cu >= 0) Upos[s * S + i] = probe_pos[s * cap + (uint32_t)cu];
+}
+
+// ---------------------------------------------------------------------------
+// Final splitters (Sec. 4.2.2 step 5): the closer of L_i, U_i (tie -> L_i).
+// ---------------------------------------------------------------------------
+__global__ void k_finalize(uint32_t S, uint64_t N, uint32_t p, int key_type, const DCut* __restrict__ Lcut,
+                           const DCut* __restrict__ Ucut, hss_cut* __restrict__ spl, uint64_t* __restrict__ offsets,
+                           uint32_t* __restrict__ choose_u) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) { offsets[0] = 0; offsets[p] = N; }
+    if (i >= S) return;
+    const uint64_t t = ideal_rank(i + 1, N, p);
+    const DCut L = Lcut[i], U = Ucut[i];
+    const bool useU = (U.rank - t) < (t - L.rank);
+    const DCut c = useU ? U : L;
+    hss_cut o;
+    const uint64_t flip = key_type == HSS_KEY_I64 ? kSignBit : 0ull;
+    if (c.kind == kMember) { o.key = c.okey ^ flip; o.seg = c.seg; o.spos = c.spos; }
+    else if (c.kind == kNonMember) { o.key = c.okey ^ flip; o.seg = -1; o.spos = 0; }
+    else if (c.kind == kNegInf) { o.key = 0; o.seg = -2; o.spos = 0; }
+    else { o.key = 0; o.seg = -3; o.spos = 0; }
+    spl[i] = o;
+    offsets[i + 1] = c.rank;
+    choose_u[i] = useU ? 1u : 0u;
+}
+
+__global__ void k_final_pos(uint32_t S, const uint32_t* __restrict__ choose_u, uint32_t* __restrict__ Lpos,
+                            const uint32_t* __restrict__ Upos) {
+    const uint64_t s = blockIdx.x;
+    const uint32_t i = blockIdx.y * blockDim.x + threadIdx.x;
+    if (i >= S) return;
+    if (choose_u[i]) Lpos[s * S + i] = Upos[s * S + i];
+}
+
+// ---------------------------------------------------------------------------
+// Host driver of the rounds.
+// ---------------------------------------------------------------------------
+#define HSS_TRY(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return HSS_ERR_CUDA; } while (0)
+
+static void enqueue_sampling(const RoundWs& ws, const uint64_t* d_seg_off, uint64_t N, uint32_t p, uint32_t S,
+                             uint64_t seed, uint32_t round, cudaStream_t st) {
+    cudaMemsetAsync(ws.bitmap, 0, (N / 32 + 2) * sizeof(uint32_t), st);
+    HSS_LAUNCH(k_sample_mark, p, kSampThreads, 0, st, d_seg_off, S, ws.Lpos, ws.Upos, ws.Lcut, ws.int_rep, ws.ctl, seed,
+               round, ws.bitmap, ws.seg_cnt);
+    HSS_LAUNCH(k_count_scan, 1, 1024, 0, st, ws.seg_cnt, p, ws.seg_cnt_off, ws.cap, ws.ctl);
+}
+
+int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uint32_t p, double eps, uint64_t seed,
+               float oversample, uint32_t max_rounds, int key_type, hss_cut* d_splitters, uint64_t* d_offsets,
+               const RoundWs& ws, cudaStream_t st, RoundResult* out) {
+    const uint32_t S = p - 1;
+    const uint64_t tol = (uint64_t)std::floor(((double)N * eps) / (2.0 * (double)p));
+    HSS_TRY(cudaMemsetAsync(ws.ctl, 0, sizeof(RoundCtl), st));
+    if (S == 0) {
+        HSS_LAUNCH(k_finalize, 1, 32, 0, st, 0u, N, p, key_type, ws.Lcut, ws.Ucut, d_splitters, d_offsets, ws.choose_u);
+        HSS_TRY(cudaGetLastError());
+        out->rounds = 0;
+        out->status = HSS_OK;
+        return HSS_OK;
+    }
+    const unsigned sblk = (unsigned)cdiv(S, 256);
+    HSS_LAUNCH(k_rounds_init, dim3(p, sblk), 256, 0, st, d_seg_off, S, N, ws.Lcut, ws.Ucut, ws.Lpos, ws.Upos);
+    HSS_LAUNCH(k_intervals, 1, 1024, 0, st, S, N, p, tol, oversample, ws.Lcut, ws.Ucut, ws.res, ws.int_rep, ws.ctl);
+    enqueue_sampling(ws, d_seg_off, N, p, S, seed, 1, st);
+    HSS_TRY(cudaGetLastError());
+    RoundCtl h;
+    HSS_TRY(cudaMemcpyAsync(&h, ws.ctl, sizeof(h), cudaMemcpyDeviceToHost, st));
+    HSS_TRY(cudaStreamSynchronize(st));
+    out->unresolved[0] = h.unresolved;
+    uint32_t j = 0;
+    int status = HSS_OK;
+    for (;;) {
+        if (h.unresolved == 0) break;
+        if (j >= max_rounds) { status = HSS_ERR_ROUND_LIMIT; break; }
+        ++j;
+        out->sample_size[j - 1] = h.Z;
+        out->gamma[j - 1] = h.gamma;
+        if (h.Z > ws.cap) { status = HSS_ERR_CAPACITY; break; }
+        const uint64_t Z = h.Z;
+        HSS_LAUNCH(k_sample_write, p, kSampThreads, 0, st, skeys, d_seg_off, S, ws.Lpos, ws.Upos, ws.Lcut, ws.int_rep, ws.ctl,
+                   ws.bitmap, ws.seg_cnt, ws.seg_cnt_off, ws.cap, ws.skey, ws.sseg, ws.sspos, ws.siota);
+        if (Z > 0) {
+            HSS_TRY(segsort(ws.skey, ws.skey_sorted, ws.stmp, ws.siota, ws.sperm, ws.ptmp, Z, 1, ws.ctl->seg_off_z, false,
+                            false, ws.sws, st, nullptr));
+            HSS_LAUNCH(k_probe_build, (unsigned)cdiv(Z, 256), 256, 0, st, Z, ws.skey_sorted, ws.sperm, ws.sseg, ws.sspos,
+                       ws.Ucut, ws.int_rep, ws.ctl, ws.pkey, ws.pseg, ws.pspos, ws.pint, ws.prank);
+            HSS_LAUNCH(k_histogram, dim3((unsigned)cdiv(Z, 32), (unsigned)cdiv(p, kHistSegPerBlock)), 256, 0, st, skeys,
+                       d_seg_off, p, S, ws.Lpos, ws.Upos, ws.int_rep, ws.pkey, ws.pseg, ws.pspos, ws.pint, Z, ws.prank,
+                       ws.probe_pos, ws.cap, ws.sws.err);
+            HSS_LAUNCH(k_update, sblk, 256, 0, st, S, N, p, ws.pkey, ws.pseg, ws.pspos, ws.prank, Z, ws.Lcut, ws.Ucut,
+                       ws.chgL, ws.chgU);
+            HSS_LAUNCH(k_update_pos, dim3(p, sblk), 256, 0, st, S, ws.chgL, ws.chgU, ws.probe_pos, ws.cap, ws.Lpos, ws.Upos);
+        }
+        HSS_LAUNCH(k_intervals, 1, 1024, 0, st, S, N, p, tol, oversample, ws.Lcut, ws.Ucut, ws.res, ws.int_rep, ws.ctl);
+        enqueue_sampling(ws, d_seg_off, N, p, S, seed, j + 1, st);
+        HSS_TRY(cudaGetLastError());
+        HSS_TRY(cudaMemcpyAsync(&h, ws.ctl, sizeof(h), cudaMemcpyDeviceToHost, st));
+        HSS_TRY(cudaStreamSynchronize(st));
+        out->unresolved[j] = h.unresolved;
+    }
+    out->rounds = j;
+    out->status = status;
+    HSS_LAUNCH(k_finalize, (unsigned)cdiv(S, 256), 256, 0, st, S, N, p, key_type, ws.Lcut, ws.Ucut, d_splitters, d_offsets,
+               ws.choose_u);
+    HSS_LAUNCH(k_final_pos, dim3(p, sblk), 256, 0, st, S, ws.choose_u, ws.Lpos, ws.Upos);
+    HSS_TRY(cudaGetLastError());
+    return status;
+}
+
+// ---------------------------------------------------------------------------
+// Exchange (Sec. 3.1 step 3 / Sec. 6): runs of the sorted segments to their
+// buckets.  dst(s, b) = chi(b) + sum_{s' < s} |run(s', b)|.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t bucket_pos(const uint32_t* __restrict__ pos, uint32_t S, uint32_t p, uint64_t s,
+                                               uint32_t b, uint32_t n) {
+    return b == 0 ? 0u : (b == p ? n : pos[s * S + (b - 1)]);
+}
+
+__global__ void k_exchange_dst(const uint64_t* __restrict__ seg_off, uint32_t p, const uint32_t* __restrict__ pos,
+                               const uint64_t* __restrict__ offsets, uint64_t* __restrict__ dst, uint32_t* err) {
+    const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= p) return;
+    const uint32_t S = p - 1;
+    uint64_t run = offsets[b];
+    for (uint32_t s = 0; s < p; ++s) {
+        const uint32_t n = (uint32_t)(seg_off[s + 1] - seg_off[s]);
+        const uint32_t lo = bucket_pos(pos, S, p, s, b, n), hi = bucket_pos(pos, S, p, s, b + 1, n);
+        dst[(uint64_t)s * p + b] = run;
+        run += hi - lo;
+    }
+    if (run != offsets[b + 1]) atomicOr(err, kDevErrBounds);
+}
+
+constexpr uint32_t kXchChunk = 4096;
+constexpr uint32_t kXchMaxB = 1024;
+
+__global__ __launch_bounds__(256) void k_exchange_copy(const uint64_t* __restrict__ skeys, const uint32_t* __restrict__ spay,
+                                                       const uint64_t* __restrict__ seg_off, uint32_t p,
+                                                       const uint32_t* __restrict__ pos, const uint64_t* __restrict__ dst,
+                                                       uint64_t* __restrict__ bkeys, uint32_t* __restrict__ bpay, uint64_t N,
+                                                       uint32_t* __restrict__ err) {
+    __shared__ uint32_t s_bnd[kXchMaxB + 1];
+    __shared__ uint32_t s_b0, s_nb;
+    const uint64_t s = blockIdx.x;
+    const uint32_t S = p - 1;
+    const uint64_t base = seg_off[s];
+    const uint32_t n = (uint32_t)(seg_off[s + 1] - base);
+    const uint32_t c0 = blockIdx.y * kXchChunk;
+    if (c0 >= n) return;
+    const uint32_t c1 = min(n, c0 + kXchChunk);
+    if (threadIdx.x == 0) {
+        // buckets b0..b1 whose runs meet [c0, c1): last b with pos(b) <= c0, last b with pos(b) <= c1-1
+        uint32_t lo = 0, hi = p;  // pos(lo) <= c0 < pos(hi) (pos(p) = n > c0)
+        while (hi - lo > 1) { const uint32_t m = (lo + hi) >> 1; if (bucket_pos(pos, S, p, s, m, n) <= c0) lo = m; else hi = m; }
+        const uint32_t b0 = lo;
+        lo = b0; hi = p;
+        while (hi - lo > 1) { const uint32_t m = (lo + hi) >> 1; if (bucket_pos(pos, S, p, s, m, n) <= c1 - 1) lo = m; else hi = m; }
+        s_b0 = b0;
+        s_nb = lo - b0 + 1;
+    }
+    __syncthreads();
+    const uint32_t b0 = s_b0, nb = s_nb;
+    if (nb <= kXchMaxB) {
+        for (uint32_t i = threadIdx.x; i <= nb; i += blockDim.x) s_bnd[i] = bucket_pos(pos, S, p, s, b0 + i, n);
+        __syncthreads();
+        for (uint32_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
+            uint32_t lo = 0, hi = nb;  // last i with s_bnd[i] <= j
+            while (hi - lo > 1) { const uint32_t m = (lo + hi) >> 1; if (s_bnd[m] <= j) lo = m; else hi = m; }
+            const uint64_t d = dst[s * p + b0 + lo] + (j - s_bnd[lo]);
+            if (d >= N) { atomicOr(err, kDevErrBounds); continue; }
+            bkeys[d] = skeys[base + j];
+            if (bpay) bpay[d] = spay[base + j];
+        }
+    } else {
+        for (uint32_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
+            uint32_t lo = b0, hi = b0 + nb;
+            while (hi - lo > 1) { const uint32_t m = (lo + hi) >> 1; if (bucket_pos(pos, S, p, s, m, n) <= j) lo = m; else hi = m; }
+            const uint64_t d = dst[s * p + lo] + (j - bucket_pos(pos, S, p, s, lo, n));
+            if (d >= N) { atomicOr(err, kDevErrBounds); continue; }
+            bkeys[d] = skeys[base + j];
+            if (bpay) bpay[d] = spay[base + j];
+        }
+    }
+}
+
+cudaError_t exchange(const uint64_t* skeys, const uint32_t* spay, uint64_t N, uint32_t p, const uint64_t* d_seg_off,
+                     const uint32_t* pos, const uint64_t* d_offsets, uint64_t* bkeys, uint32_t* bpay,
+                     uint64_t* dst_scratch, uint32_t* err, cudaStream_t st) {
+    if (N == 0) return cudaSuccess;
+    HSS_LAUNCH(k_exchange_dst, (unsigned)cdiv(p, 128), 128, 0, st, d_seg_off, p, pos, d_offsets, dst_scratch, err);
+    const uint64_t maxn = cdiv(N, p) + 1;
+    HSS_LAUNCH(k_exchange_copy, dim3(p, (unsigned)cdiv(maxn, kXchChunk)), 256, 0, st, skeys, spay, d_seg_off, p, pos,
+               dst_scratch, bkeys, bpay, N, err);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Ranks of caller-supplied cuts (hss_rank_cuts).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t seg_count(const uint64_t* __restrict__ a, uint32_t n, uint64_t okey, bool strict, uint64_t flip) {
+    uint32_t base = 0;
+    while (n > 0) {
+        const uint32_t half = n >> 1;
+        const uint64_t v = a[base + half] ^ flip;
+        const bool go = strict ? (v < okey) : (v <= okey);
+        base = go ? base + half + 1 : base;
+        n = go ? n - half - 1 : half;
+    }
+    return base;
+}
+
+__global__ __launch_bounds__(256) void k_rank_cuts(const uint64_t* __restrict__ skeys, uint64_t flip, uint64_t N,
+                                                   uint32_t p, const hss_cut* __restrict__ cuts, uint32_t ncuts,
+                                                   uint64_t* __restrict__ ranks, uint32_t* __restrict__ seg_pos) {
+    __shared__ uint64_t s_part[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t k = blockIdx.x * 32 + lane;
+    const bool valid = k < ncuts;
+    hss_cut c; c.key = 0; c.seg = -2; c.spos = 0;
+    if (valid) c = cuts[k];
+    const uint64_t okey = c.key ^ flip;
+    uint64_t partial = 0;
+    for (int j = 0; j < kHistSegPerBlock / 8; ++j) {
+        const uint32_t s = blockIdx.y * kHistSegPerBlock + j * 8 + w;
+        if (valid && s < p) {
+            const uint64_t lo = ideal_rank(s, N, p), hi = ideal_rank(s + 1, N, p);  // segment bounds
+            const uint32_t n = (uint32_t)(hi - lo);
+            const uint64_t* a = skeys + lo;
+            uint32_t pos;
+            if (c.seg == -2) pos = 0;
+            else if (c.seg == -3) pos = n;
+            else if (c.seg == -1) pos = seg_count(a, n, okey, true, flip);
+            else if ((int32_t)s < c.seg) pos = seg_count(a, n, okey, false, flip);
+            else if ((int32_t)s > c.seg) pos = seg_count(a, n, okey, true, flip);
+            else {
+                const uint32_t lb = seg_count(a, n, okey, true, flip), ub = seg_count(a, n, okey, false, flip);
+                pos = min(max(c.spos, lb), ub);
+            }
+            if (seg_pos) seg_pos[(uint64_t)s * ncuts + k] = pos;
+            partial += pos;
+        }
+    }
+    s_part[w][lane] = partial;
+    __syncthreads();
+    if (w == 0 && valid) {
+        uint64_t sum = 0;
+        for (int i = 0; i < 8; ++i) sum += s_part[i][lane];
+        atomicAdd((unsigned long long*)&ranks[k], (unsigned long long)sum);
+    }
+}
+
+cudaError_t rank_cuts(const uint64_t* skeys, int key_type, uint64_t N, uint32_t p,
+                      const hss_cut* cuts, uint32_t ncuts, uint64_t* ranks, uint32_t* seg_pos, cudaStream_t st) {
+    if (ncuts == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(ranks, 0, ncuts * sizeof(uint64_t), st);
+    if (e != cudaSuccess) return e;
+    HSS_LAUNCH(k_rank_cuts, dim3((unsigned)cdiv(ncuts, 32), (unsigned)cdiv(p, kHistSegPerBlock)), 256, 0, st, skeys,
+               key_type == HSS_KEY_I64 ? kSignBit : 0ull, N, p, cuts, ncuts, ranks, seg_pos);
+    return cudaGetLastError();
+}
+
+__global__ void k_sample_words(uint64_t seed, uint32_t seg, uint32_t round, uint32_t spos0, uint32_t count, uint64_t* out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const uint32_t spos = spos0 + i;
+    uint64_t w0, w1;
+    sample_words(seed, seg, round, spos >> 1, w0, w1);
+    out[i] = (spos & 1u) ? w1 : w0;
+}
+
+cudaError_t sample_words_launch(uint64_t seed, uint32_t seg, uint32_t round, uint32_t spos0, uint32_t count,
+                                uint64_t* out, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    HSS_LAUNCH(k_sample_words, (unsigned)cdiv(count, 256), 256, 0, st, seed, seg, round, spos0, count, out);
+    return cudaGetLastError();
+}
+
+}  // namespace hss

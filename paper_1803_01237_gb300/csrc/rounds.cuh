@@ -1,0 +1,87 @@
+// rounds.cuh -- the splitter-determination rounds of HSS on one device.
+#pragma once
+
+#include "hss_internal.cuh"
+#include "segsort.cuh"
+
+namespace hss {
+
+// Device-resident state of the round loop (one per call).
+struct RoundCtl {
+    uint64_t gamma;        // |gamma| of the region the next round samples
+    uint64_t T;            // threshold of the next round (u < T selects)
+    uint32_t take_all;     // q >= 1: select every key of the region
+    uint32_t nint;         // distinct unresolved intervals
+    uint32_t unresolved;   // unresolved splitters
+    uint32_t round;        // rounds completed
+    uint64_t Z;            // probes drawn by the last sampling pass
+    uint64_t seg_off_z[2]; // {0, min(Z, cap)}: one "segment" for the probe sort
+    uint32_t err;          // device error bits
+    uint32_t pad;
+};
+
+// Workspace of the rounds, carved from the caller's buffer.
+struct RoundWs {
+    RoundCtl* ctl;
+    DCut* Lcut;          // [S]
+    DCut* Ucut;          // [S]
+    uint32_t* Lpos;      // [p][S]  keys of segment s below L_i
+    uint32_t* Upos;      // [p][S]
+    uint32_t* res;       // [S] resolved flags
+    int32_t* chgL;       // [S]
+    int32_t* chgU;       // [S]
+    uint32_t* choose_u;  // [S]
+    uint32_t* int_rep;   // [S] representative splitter of each distinct unresolved interval
+    uint32_t* bitmap;    // [N/32 + 2]
+    uint32_t* seg_cnt;   // [p]
+    uint32_t* seg_cnt_off;  // [p + 1]
+    uint64_t* skey;      // [cap] sampled keys (order-preserving bits) in (seg, spos) order
+    uint32_t* sseg;      // [cap]
+    uint32_t* sspos;     // [cap]
+    uint32_t* siota;     // [cap]
+    uint64_t* skey_sorted;  // [cap]
+    uint32_t* sperm;     // [cap]
+    uint64_t* stmp;      // [cap] sort scratch
+    uint32_t* ptmp;      // [cap]
+    uint64_t* pkey;      // [cap] probes
+    int32_t* pseg;       // [cap]
+    uint32_t* pspos;     // [cap]
+    uint32_t* pint;      // [cap]
+    uint64_t* prank;     // [cap]
+    uint32_t* probe_pos; // [p][cap]
+    SegSortWs sws;       // scratch of the probe sort
+    uint64_t cap;        // sample capacity
+};
+
+size_t rounds_ws_bytes(uint64_t N, uint64_t p, uint64_t cap);
+RoundWs rounds_ws_carve(void* base, uint64_t N, uint64_t p, uint64_t cap, uint32_t* err);
+uint64_t sample_capacity(uint64_t N, uint64_t p, float oversample);
+
+struct RoundResult {
+    uint32_t rounds = 0;
+    int status = 0;
+    uint64_t sample_size[HSS_MAX_ROUNDS] = {};
+    uint64_t gamma[HSS_MAX_ROUNDS] = {};
+    uint64_t unresolved[HSS_MAX_ROUNDS + 1] = {};
+};
+
+// Run the histogram rounds over the p locally sorted segments skeys
+// (order-preserving key bits) and write the splitters, offsets and the final
+// per-segment positions of the splitters (into ws.Lpos).
+int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uint32_t p, double eps, uint64_t seed,
+               float oversample, uint32_t max_rounds, int key_type, hss_cut* d_splitters, uint64_t* d_offsets,
+               const RoundWs& ws, cudaStream_t st, RoundResult* out);
+
+// Exchange: per-(segment, bucket) destinations, then the run copy.
+cudaError_t exchange(const uint64_t* skeys, const uint32_t* spay, uint64_t N, uint32_t p, const uint64_t* d_seg_off,
+                     const uint32_t* pos /*[p][p-1]*/, const uint64_t* d_offsets, uint64_t* bkeys, uint32_t* bpay,
+                     uint64_t* dst_scratch /*[p][p]*/, uint32_t* err, cudaStream_t st);
+
+// Ranks of arbitrary cuts (keys in caller representation).
+cudaError_t rank_cuts(const uint64_t* skeys, int key_type, uint64_t N, uint32_t p,
+                      const hss_cut* cuts, uint32_t ncuts, uint64_t* ranks, uint32_t* seg_pos, cudaStream_t st);
+
+cudaError_t sample_words_launch(uint64_t seed, uint32_t seg, uint32_t round, uint32_t spos0, uint32_t count,
+                                uint64_t* out, cudaStream_t st);
+
+}  // namespace hss

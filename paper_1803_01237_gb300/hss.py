@@ -1,0 +1,341 @@
+"""Thin ctypes binding of libhss.so (include/hss.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Tensors are torch CUDA tensors (device memory and the current
+stream come from torch); 64-bit keys travel as torch.int64 tensors whose bits
+are either unsigned (key_type="u64") or signed (key_type="i64").  There is no
+CPU fallback: if the library is missing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libhss.so")
+
+HSS_OK = 0
+ERRORS = {-1: "HSS_ERR_INVALID", -2: "HSS_ERR_WORKSPACE", -3: "HSS_ERR_ROUND_LIMIT", -4: "HSS_ERR_TIMEOUT",
+          -5: "HSS_ERR_CUDA", -6: "HSS_ERR_CAPACITY"}
+KEY_TYPES = {"u64": 0, "i64": 1}
+OP = {"sort": 0, "partition": 1, "local_sort": 2, "merge": 3, "exchange": 4, "sort_host": 5}
+FLAG_SYNC = 1
+FLAG_TIMING = 2
+MAX_ROUNDS = 64
+NUM_PHASES = 4
+PHASES = ("local_sort", "rounds", "exchange", "merge")
+
+
+class HSSError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({_lib_or_none_strerror(code)})")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("seed", ctypes.c_uint64), ("p", ctypes.c_uint32),
+                ("oversample", ctypes.c_float), ("max_rounds", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_uint32), ("status", ctypes.c_int32), ("tol", ctypes.c_uint64),
+                ("sample_size", ctypes.c_uint64 * MAX_ROUNDS), ("gamma", ctypes.c_uint64 * MAX_ROUNDS),
+                ("unresolved", ctypes.c_uint64 * (MAX_ROUNDS + 1)), ("ms_phase", ctypes.c_float * NUM_PHASES),
+                ("ms_radix_pass_total", ctypes.c_float), ("radix_pass_launches", ctypes.c_uint32),
+                ("radix_pass_keys", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def _lib_or_none_strerror(code):
+    try:
+        return load().hss_strerror(code).decode()
+    except Exception:
+        return "?"
+
+
+def load():
+    """Load libhss.so (building it first if its sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        from . import build as _build
+        if not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libhss.so is missing at {LIB_PATH}: build it with paper_1803_01237_gb300.build")
+        lib = ctypes.CDLL(LIB_PATH)
+        P, U64, U32, I32, SZ = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_size_t
+        lib.hss_workspace_bytes.argtypes = [I32, U64, ctypes.POINTER(Params), U32, I32, I32]
+        lib.hss_workspace_bytes.restype = SZ
+        lib.hss_local_sort.argtypes = [P, P, I32, U64, U32, P, P, P, SZ, P]
+        lib.hss_rank_cuts.argtypes = [P, I32, U64, U32, P, U32, P, P, P]
+        lib.hss_partition.argtypes = [P, I32, U64, ctypes.POINTER(Params), P, P, P, SZ, ctypes.POINTER(Stats), P]
+        lib.hss_exchange.argtypes = [P, P, U64, U32, P, P, P, P, P, SZ, P]
+        lib.hss_merge.argtypes = [P, P, I32, U64, U32, P, P, P, P, SZ, P]
+        lib.hss_sort.argtypes = [P, P, I32, U64, ctypes.POINTER(Params), P, P, P, P, P, SZ, ctypes.POINTER(Stats), P]
+        lib.hss_sort_host.argtypes = [P, P, I32, U64, ctypes.POINTER(Params), P, P, P, P, P, SZ, ctypes.POINTER(Stats), P]
+        lib.hss_sample_words.argtypes = [U64, U32, U32, U32, U32, P, P]
+        lib.hss_kernel_launch_count.argtypes = []
+        lib.hss_kernel_launch_count.restype = U64
+        lib.hss_strerror.argtypes = [I32]
+        lib.hss_strerror.restype = ctypes.c_char_p
+        for name in ("hss_local_sort", "hss_rank_cuts", "hss_partition", "hss_exchange", "hss_merge", "hss_sort",
+                     "hss_sort_host", "hss_sample_words"):
+            getattr(lib, name).restype = I32
+        _lib = lib
+        return lib
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(rc: int, where: str, allow=()):
+    if rc != HSS_OK and rc not in allow:
+        raise HSSError(rc, where)
+    return rc
+
+
+def _as_key_tensor(keys) -> torch.Tensor:
+    if isinstance(keys, np.ndarray):
+        keys = torch.from_numpy(np.ascontiguousarray(keys).view(np.int64))
+    if keys.dtype not in (torch.int64,):
+        raise TypeError("keys must be int64 tensors (u64 keys are passed by bit pattern)")
+    return keys.contiguous()
+
+
+_ws_cache: dict = {}
+
+
+def workspace(nbytes: int, device=None) -> torch.Tensor:
+    """A cached device byte buffer of at least nbytes (grown on demand)."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    buf = _ws_cache.get(dev)
+    if buf is None or buf.numel() < nbytes:
+        _ws_cache.pop(dev, None)
+        buf = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=dev)
+        _ws_cache[dev] = buf
+    return buf
+
+
+def workspace_bytes(op: str, N: int, p: int, key_type: str = "u64", payload: bool = False,
+                    oversample: float = 5.0, eps: float = 0.05) -> int:
+    prm = Params(eps=eps, seed=0, p=p, oversample=oversample, max_rounds=0, flags=0)
+    return int(load().hss_workspace_bytes(OP[op], N, ctypes.byref(prm), p, KEY_TYPES[key_type], int(payload)))
+
+
+def cuts_to_numpy(raw: torch.Tensor):
+    """Unpack an (n, 2) int64 tensor of hss_cut records into (key, seg, spos)."""
+    a = raw.detach().cpu().numpy().reshape(-1, 2)
+    key = a[:, 0].copy()
+    seg = (a[:, 1] & 0xFFFFFFFF).astype(np.uint32).view(np.int32)
+    spos = ((a[:, 1] >> 32) & 0xFFFFFFFF).astype(np.uint32)
+    return key, seg, spos
+
+
+def cuts_from_numpy(key, seg, spos, device) -> torch.Tensor:
+    key = np.asarray(key).astype(np.uint64).view(np.int64)
+    lo = np.asarray(seg, dtype=np.int32).view(np.uint32).astype(np.int64)
+    hi = np.asarray(spos, dtype=np.uint32).astype(np.int64)
+    packed = (lo | (hi << 32)).astype(np.int64)
+    return torch.from_numpy(np.stack([key, packed], axis=1).copy()).to(device)
+
+
+@dataclass
+class Result:
+    keys: torch.Tensor | None
+    payload: torch.Tensor | None
+    splitters: torch.Tensor        # (p-1, 2) int64: packed hss_cut records
+    offsets: torch.Tensor          # (p+1,) int64
+    rounds: int
+    status: int
+    tol: int
+    sample_size: list = field(default_factory=list)
+    gamma: list = field(default_factory=list)
+    unresolved: list = field(default_factory=list)
+    ms_phase: dict = field(default_factory=dict)
+    ms_radix_pass_total: float = 0.0
+    radix_pass_launches: int = 0
+    kernel_launches: int = 0
+
+    def splitter_tags(self):
+        return cuts_to_numpy(self.splitters)
+
+
+def _result(keys, pay, spl, off, st: Stats) -> Result:
+    R = st.rounds
+    return Result(keys=keys, payload=pay, splitters=spl, offsets=off, rounds=R, status=st.status, tol=st.tol,
+                  sample_size=[int(x) for x in st.sample_size[:R]], gamma=[int(x) for x in st.gamma[:R]],
+                  unresolved=[int(x) for x in st.unresolved[:R + 1]],
+                  ms_phase={PHASES[i]: float(st.ms_phase[i]) for i in range(NUM_PHASES)},
+                  ms_radix_pass_total=float(st.ms_radix_pass_total), radix_pass_launches=int(st.radix_pass_launches),
+                  kernel_launches=int(st.kernel_launches))
+
+
+def _params(p, eps, seed, oversample, max_rounds, flags):
+    return Params(eps=float(eps), seed=int(seed) & ((1 << 64) - 1), p=int(p), oversample=float(oversample),
+                  max_rounds=int(max_rounds), flags=int(flags))
+
+
+# ---------------------------------------------------------------------------
+# entry points
+# ---------------------------------------------------------------------------
+def local_sort(keys, p: int, payload=None, key_type: str = "u64", out=None, out_payload=None, stream=None):
+    """Stable sort of each of the p contiguous segments (hss_local_sort)."""
+    lib = load()
+    keys = _as_key_tensor(keys)
+    N = keys.numel()
+    if out is None:
+        out = torch.empty_like(keys)
+    if payload is not None and out_payload is None:
+        out_payload = torch.empty_like(payload)
+    ws = workspace(workspace_bytes("local_sort", N, p, key_type, payload is not None), keys.device)
+    rc = lib.hss_local_sort(_ptr(keys), _ptr(payload), KEY_TYPES[key_type], N, p, _ptr(out), _ptr(out_payload),
+                            _ptr(ws), ws.numel(), _stream(stream))
+    _check(rc, "hss_local_sort")
+    return (out, out_payload) if payload is not None else out
+
+
+def rank_cuts(sorted_keys, p: int, cuts: torch.Tensor, key_type: str = "u64", want_seg_pos: bool = False, stream=None):
+    """Global ranks (and optionally per-segment counts) of cuts (hss_rank_cuts)."""
+    lib = load()
+    sorted_keys = _as_key_tensor(sorted_keys)
+    n = cuts.shape[0]
+    ranks = torch.empty(n, dtype=torch.int64, device=sorted_keys.device)
+    seg_pos = torch.empty((p, n), dtype=torch.int32, device=sorted_keys.device) if want_seg_pos else None
+    rc = lib.hss_rank_cuts(_ptr(sorted_keys), KEY_TYPES[key_type], sorted_keys.numel(), p, _ptr(cuts.contiguous()), n,
+                           _ptr(ranks), _ptr(seg_pos), _stream(stream))
+    _check(rc, "hss_rank_cuts")
+    return (ranks, seg_pos) if want_seg_pos else ranks
+
+
+def partition(keys, p: int, eps: float, seed: int, oversample: float = 5.0, max_rounds: int = 0,
+              key_type: str = "u64", flags: int = 0, stream=None, allow_round_limit: bool = False):
+    """Splitters and bucket offsets (hss_partition).  Returns (Result, ws)
+    where the first N*8 bytes of ws hold the locally sorted keys."""
+    lib = load()
+    keys = _as_key_tensor(keys)
+    N = keys.numel()
+    prm = _params(p, eps, seed, oversample, max_rounds, flags)
+    nb = int(lib.hss_workspace_bytes(OP["partition"], N, ctypes.byref(prm), p, KEY_TYPES[key_type], 0))
+    ws = workspace(nb, keys.device)
+    spl = torch.empty((max(p - 1, 1), 2), dtype=torch.int64, device=keys.device)
+    off = torch.empty(p + 1, dtype=torch.int64, device=keys.device)
+    st = Stats()
+    rc = lib.hss_partition(_ptr(keys), KEY_TYPES[key_type], N, ctypes.byref(prm), _ptr(spl), _ptr(off), _ptr(ws),
+                           ws.numel(), ctypes.byref(st), _stream(stream))
+    _check(rc, "hss_partition", allow=(-3,) if allow_round_limit else ())
+    return _result(None, None, spl[:p - 1], off, st), ws
+
+
+def exchange(sorted_keys, p: int, seg_pos: torch.Tensor, offsets: torch.Tensor, sorted_payload=None, stream=None):
+    """Runs of the locally sorted segments to their buckets (hss_exchange)."""
+    lib = load()
+    sorted_keys = _as_key_tensor(sorted_keys)
+    N = sorted_keys.numel()
+    bk = torch.empty_like(sorted_keys)
+    bp = torch.empty_like(sorted_payload) if sorted_payload is not None else None
+    ws = workspace(workspace_bytes("exchange", N, p), sorted_keys.device)
+    rc = lib.hss_exchange(_ptr(sorted_keys), _ptr(sorted_payload), N, p, _ptr(seg_pos.contiguous()), _ptr(offsets),
+                          _ptr(bk), _ptr(bp), _ptr(ws), ws.numel(), _stream(stream))
+    _check(rc, "hss_exchange")
+    return (bk, bp) if sorted_payload is not None else bk
+
+
+def merge(bucket_keys, p: int, offsets: torch.Tensor, bucket_payload=None, key_type: str = "u64", stream=None):
+    """Stable merge of the runs inside each bucket (hss_merge)."""
+    lib = load()
+    bucket_keys = _as_key_tensor(bucket_keys)
+    N = bucket_keys.numel()
+    out = torch.empty_like(bucket_keys)
+    outp = torch.empty_like(bucket_payload) if bucket_payload is not None else None
+    ws = workspace(workspace_bytes("merge", N, p, key_type, bucket_payload is not None), bucket_keys.device)
+    rc = lib.hss_merge(_ptr(bucket_keys), _ptr(bucket_payload), KEY_TYPES[key_type], N, p, _ptr(offsets), _ptr(out),
+                       _ptr(outp), _ptr(ws), ws.numel(), _stream(stream))
+    _check(rc, "hss_merge")
+    return (out, outp) if bucket_payload is not None else out
+
+
+def sort(keys, p: int, eps: float, seed: int, payload=None, oversample: float = 5.0, max_rounds: int = 0,
+         key_type: str = "u64", flags: int = 0, out=None, out_payload=None, stream=None) -> Result:
+    """The whole method (hss_sort): globally sorted keys, splitters, offsets."""
+    lib = load()
+    keys = _as_key_tensor(keys)
+    N = keys.numel()
+    prm = _params(p, eps, seed, oversample, max_rounds, flags)
+    nb = int(lib.hss_workspace_bytes(OP["sort"], N, ctypes.byref(prm), p, KEY_TYPES[key_type], int(payload is not None)))
+    ws = workspace(nb, keys.device)
+    if out is None:
+        out = torch.empty_like(keys)
+    if payload is not None and out_payload is None:
+        out_payload = torch.empty_like(payload)
+    spl = torch.empty((max(p - 1, 1), 2), dtype=torch.int64, device=keys.device)
+    off = torch.empty(p + 1, dtype=torch.int64, device=keys.device)
+    st = Stats()
+    rc = lib.hss_sort(_ptr(keys), _ptr(payload), KEY_TYPES[key_type], N, ctypes.byref(prm), _ptr(out), _ptr(out_payload),
+                      _ptr(spl), _ptr(off), _ptr(ws), ws.numel(), ctypes.byref(st), _stream(stream))
+    _check(rc, "hss_sort")
+    return _result(out, out_payload, spl[:p - 1], off, st)
+
+
+def sort_host(keys: np.ndarray, p: int, eps: float, seed: int, payload: np.ndarray | None = None,
+              oversample: float = 5.0, max_rounds: int = 0, key_type: str = "u64", flags: int = 0,
+              out: np.ndarray | None = None, out_payload: np.ndarray | None = None, stream=None):
+    """hss_sort_host: host arrays in, host arrays out (copies inside the call)."""
+    lib = load()
+    keys = np.ascontiguousarray(keys)
+    N = keys.shape[0]
+    prm = _params(p, eps, seed, oversample, max_rounds, flags)
+    nb = int(lib.hss_workspace_bytes(OP["sort_host"], N, ctypes.byref(prm), p, KEY_TYPES[key_type],
+                                     int(payload is not None)))
+    ws = workspace(nb)
+    if out is None:
+        out = np.empty_like(keys)
+    if payload is not None and out_payload is None:
+        out_payload = np.empty_like(payload)
+    spl = np.empty((max(p - 1, 1), 2), dtype=np.int64)
+    off = np.empty(p + 1, dtype=np.uint64)
+    st = Stats()
+    rc = lib.hss_sort_host(_ptr(keys), _ptr(payload), KEY_TYPES[key_type], N, ctypes.byref(prm), _ptr(out),
+                           _ptr(out_payload), _ptr(spl), _ptr(off), _ptr(ws), ws.numel(), ctypes.byref(st),
+                           _stream(stream))
+    _check(rc, "hss_sort_host")
+    return out, out_payload, spl[:p - 1], off, st
+
+
+def sample_words(seed: int, seg: int, rnd: int, spos0: int, count: int, device="cuda", stream=None) -> torch.Tensor:
+    """The Philox words of positions spos0.. of segment seg in round rnd."""
+    lib = load()
+    out = torch.empty(count, dtype=torch.int64, device=device)
+    rc = lib.hss_sample_words(int(seed) & ((1 << 64) - 1), seg, rnd, spos0, count, _ptr(out), _stream(stream))
+    _check(rc, "hss_sample_words")
+    return out
+
+
+def launch_count() -> int:
+    return int(load().hss_kernel_launch_count())
+
+
+def strerror(code: int) -> str:
+    return load().hss_strerror(code).decode()

@@ -1,0 +1,104 @@
+"""CPU-side checks of the C ABI: the library builds for sm_103a, loads without a
+GPU, exports every function include/hss.h declares, sizes workspaces and
+rejects invalid arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hss.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1803_01237_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(hss_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_path():
+    names = declared_functions()
+    for must in ("hss_partition", "hss_sort", "hss_local_sort", "hss_rank_cuts", "hss_exchange", "hss_merge",
+                 "hss_workspace_bytes", "hss_strerror"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_built_for_sm_103a():
+    from paper_1803_01237_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+
+
+def test_strerror(lib):
+    lib.hss_strerror.restype = ctypes.c_char_p
+    lib.hss_strerror.argtypes = [ctypes.c_int]
+    assert lib.hss_strerror(0) == b"ok"
+    assert b"workspace" in lib.hss_strerror(-2)
+    assert lib.hss_strerror(12345) == b"unknown error"
+
+
+def test_workspace_sizes_grow_with_n():
+    from paper_1803_01237_gb300 import hss
+    a = hss.workspace_bytes("sort", 1 << 20, 64)
+    b = hss.workspace_bytes("sort", 1 << 22, 64)
+    assert 0 < a < b
+    assert hss.workspace_bytes("sort", 1 << 20, 64, payload=True) > a
+    assert hss.workspace_bytes("partition", 1 << 20, 64) <= a
+    # the sort keeps two key buffers of N u64 at least
+    assert a >= 2 * 8 * (1 << 20)
+
+
+def test_invalid_arguments_rejected_without_device(lib):
+    from paper_1803_01237_gb300 import hss
+    L = hss.load()
+    st = hss.Stats()
+    bad = [hss.Params(eps=0.0, seed=1, p=4, oversample=5.0, max_rounds=0, flags=0),
+           hss.Params(eps=0.05, seed=1, p=0, oversample=5.0, max_rounds=0, flags=0),
+           hss.Params(eps=float("nan"), seed=1, p=4, oversample=5.0, max_rounds=0, flags=0),
+           hss.Params(eps=0.05, seed=1, p=4, oversample=0.0, max_rounds=0, flags=0),
+           hss.Params(eps=0.05, seed=1, p=4, oversample=5.0, max_rounds=65, flags=0)]
+    dummy = ctypes.c_void_p(16)
+    for prm in bad:
+        rc = L.hss_partition(dummy, 0, 100, ctypes.byref(prm), dummy, dummy, dummy, 1 << 30, ctypes.byref(st), None)
+        assert rc == -1
+    ok = hss.Params(eps=0.05, seed=1, p=4, oversample=5.0, max_rounds=0, flags=0)
+    # workspace too small
+    rc = L.hss_partition(dummy, 0, 100, ctypes.byref(ok), dummy, dummy, dummy, 16, ctypes.byref(st), None)
+    assert rc == -2
+    # bad key type
+    rc = L.hss_partition(dummy, 7, 100, ctypes.byref(ok), dummy, dummy, dummy, 1 << 30, ctypes.byref(st), None)
+    assert rc == -1
+    # null keys with N > 0
+    rc = L.hss_partition(None, 0, 100, ctypes.byref(ok), dummy, dummy, dummy, 1 << 30, ctypes.byref(st), None)
+    assert rc == -1
+    # payload without an output payload
+    rc = L.hss_sort(dummy, dummy, 0, 100, ctypes.byref(ok), dummy, None, dummy, dummy, dummy, 1 << 30,
+                    ctypes.byref(st), None)
+    assert rc == -1
+    # local sort: p = 0
+    rc = L.hss_local_sort(dummy, None, 0, 100, 0, dummy, None, dummy, 1 << 30, None)
+    assert rc == -1
+    # sample words: range past 2^32
+    rc = L.hss_sample_words(1, 0, 1, 0xFFFFFFFF, 2, dummy, None)
+    assert rc == -1
+
+
+def test_no_cpu_fallback_in_binding():
+    """The binding is marshalling only: it never imports the oracle."""
+    src = open(os.path.join(ROOT, "paper_1803_01237_gb300", "hss.py")).read()
+    assert "oracle" not in src.replace("# ", "")
+    for f in os.listdir(os.path.join(ROOT, "paper_1803_01237_gb300", "csrc")):
+        assert "oracle" not in open(os.path.join(ROOT, "paper_1803_01237_gb300", "csrc", f)).read().lower()

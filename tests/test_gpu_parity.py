@@ -1,0 +1,261 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer work throughout, so every comparison is bit-exact: the sampling
+words, the locally sorted segments, the probe ranks, the splitters, the
+offsets, the per-round sample sizes and |gamma|, and the sorted output.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1803_01237_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def hss():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests selected but no CUDA device is visible")
+    from paper_1803_01237_gb300 import hss as h
+    h.load()
+    return h
+
+
+def dev(a):
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint64:
+        a = a.view(np.int64)
+    elif a.dtype == np.uint32:
+        a = a.view(np.int32)
+    return torch.from_numpy(a).cuda()
+
+
+def host_u64(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+GENS = {
+    "uniform": inputs.uniform,
+    "gauss_mix": inputs.gauss_mix,
+    "zipf": inputs.zipf,
+    "skew1": inputs.skew1,
+    "skew2": inputs.skew2,
+    "skew3": inputs.skew3,
+    "gauss": inputs.gauss,
+    "allzeros": inputs.allzeros,
+}
+
+
+# ---------------------------------------------------------------------------
+# K2: Philox words
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("seed,seg,rnd,spos0", [(1, 0, 1, 0), (0xDEADBEEFCAFEF00D, 1023, 7, 12345),
+                                                (2**64 - 1, 65535, 64, 2**31 - 7)])
+def test_sample_words_match_oracle(hss, seed, seg, rnd, spos0):
+    n = 257
+    got = hss.sample_words(seed, seg, rnd, spos0, n).cpu().numpy().view(np.uint64)
+    want = np.array([oracle.sample_draw(seed, seg, spos0 + i, rnd) for i in range(n)], dtype=np.uint64)
+    assert np.array_equal(got, want)
+
+
+# ---------------------------------------------------------------------------
+# a2: local sort
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("N,p", [(1000, 1), (50000, 7), (1 << 16, 4), (100003, 3), (200000, 2), (40000, 1),
+                                 (16384 * 2, 2), (16385 * 2, 2), (5, 8), (0, 3)])
+@pytest.mark.parametrize("gen", ["uniform", "zipf", "skew2", "allzeros"])
+def test_local_sort_matches_oracle(hss, N, p, gen):
+    keys = GENS[gen](N, 3)
+    pay = (np.arange(N, dtype=np.uint32) * np.uint32(2654435761)).astype(np.uint32)
+    if N == 0:
+        out, outp = hss.local_sort(dev(keys), p, payload=dev(pay))
+        assert out.numel() == 0 and outp.numel() == 0
+        return
+    out, outp = hss.local_sort(dev(keys), p, payload=dev(pay))
+    want, wantp = oracle.segment_sort(keys, p, payload=pay)
+    assert np.array_equal(host_u64(out), want)
+    assert np.array_equal(outp.cpu().numpy().view(np.uint32), wantp)
+
+
+@pytest.mark.parametrize("N,p", [(30000, 3), (120000, 2)])
+def test_local_sort_signed(hss, N, p):
+    keys = inputs.uniform(N, 9).view(np.int64)
+    out = hss.local_sort(dev(keys), p, key_type="i64")
+    want = oracle.segment_sort(keys, p)
+    assert np.array_equal(out.cpu().numpy(), want)
+
+
+def test_local_sort_in_place(hss):
+    N, p = 70000, 2
+    keys = inputs.uniform(N, 4)
+    d = dev(keys)
+    hss.local_sort(d, p, out=d)
+    assert np.array_equal(host_u64(d), oracle.segment_sort(keys, p))
+
+
+# ---------------------------------------------------------------------------
+# a5: histogram (ranks of cuts)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("gen", ["uniform", "skew2", "allzeros"])
+def test_rank_cuts_match_oracle(hss, gen):
+    N, p = 6000, 9
+    keys = GENS[gen](N, 5)
+    srt = oracle.segment_sort(keys, p)
+    b = oracle.segment_bounds(N, p)
+    g = np.random.default_rng(1)
+    ks, ss, ps, want = [], [], [], []
+    for _ in range(40):
+        s = int(g.integers(0, p)); sp = int(g.integers(0, int(b[s + 1] - b[s])))
+        key = int(srt[int(b[s]) + sp])
+        ks.append(key); ss.append(s); ps.append(sp)
+        want.append(oracle.cut_rank(keys, p, key, seg=s, spos=sp, member=True))
+    for key in [0, 7, int(keys.max())]:
+        ks.append(key); ss.append(-1); ps.append(0)
+        want.append(oracle.cut_rank(keys, p, key, member=False))
+    ks += [0, 0]; ss += [-2, -3]; ps += [0, 0]; want += [0, N]
+    cuts = hss.cuts_from_numpy(np.array(ks, dtype=np.uint64), ss, ps, "cuda")
+    ranks, seg_pos = hss.rank_cuts(dev(srt), p, cuts, want_seg_pos=True)
+    assert list(ranks.cpu().numpy()) == want
+    assert np.array_equal(seg_pos.cpu().numpy().sum(axis=0), np.array(want))
+
+
+# ---------------------------------------------------------------------------
+# a3-a7: partition, bit-exact against the oracle's round-by-round run
+# ---------------------------------------------------------------------------
+def _cmp_partition(res, ref):
+    assert res.rounds == ref.rounds
+    assert res.sample_size == [int(x) for x in ref.sample_size]
+    assert res.gamma == [int(x) for x in ref.gamma]
+    assert res.unresolved == [int(x) for x in ref.unresolved]
+    assert np.array_equal(res.offsets.cpu().numpy().astype(np.uint64), ref.offsets)
+    k, s, sp = res.splitter_tags()
+    want_k = ref.splitter_key.view(np.uint64) if ref.splitter_key.dtype == np.int64 else ref.splitter_key
+    assert np.array_equal(k.view(np.uint64), want_k)
+    assert np.array_equal(s, ref.splitter_seg)
+    assert np.array_equal(sp, ref.splitter_spos)
+
+
+@pytest.mark.parametrize("N,p,eps,seed", [(1 << 20, 64, 0.05, 1), (1 << 16, 16, 0.02, 3), (1 << 18, 4, 0.01, 5),
+                                          (12345, 100, 0.05, 2), (1000, 999, 0.05, 2), (3, 5, 0.05, 1),
+                                          (1, 1, 0.05, 1), (300, 64, 0.01, 1)])
+def test_partition_matches_oracle(hss, N, p, eps, seed):
+    keys = inputs.uniform(N, seed)
+    res, _ = hss.partition(dev(keys), p, eps, seed)
+    ref = oracle.hss(keys, p, eps, seed, sort=False)
+    _cmp_partition(res, ref)
+
+
+@pytest.mark.parametrize("gen", ["gauss_mix", "zipf", "skew1", "skew2", "skew3", "gauss", "allzeros"])
+def test_partition_distributions(hss, gen):
+    N, p, eps, seed = 1 << 17, 32, 0.02, 11
+    keys = GENS[gen](N, seed)
+    res, _ = hss.partition(dev(keys), p, eps, seed)
+    ref = oracle.hss(keys, p, eps, seed, sort=False)
+    _cmp_partition(res, ref)
+
+
+def test_partition_signed(hss):
+    N, p, eps, seed = 50000, 10, 0.05, 4
+    keys = inputs.uniform(N, 4).view(np.int64)
+    res, _ = hss.partition(dev(keys), p, eps, seed, key_type="i64")
+    ref = oracle.hss(keys, p, eps, seed, sort=False)
+    _cmp_partition(res, ref)
+
+
+def test_partition_oversample_and_round_limit(hss):
+    N, p, eps = 1 << 16, 32, 0.002
+    keys = inputs.uniform(N, 2)
+    for s in (1.0, 2.5, 20.0):
+        res, _ = hss.partition(dev(keys), p, eps, 9, oversample=s)
+        ref = oracle.hss(keys, p, eps, 9, oversample=s, sort=False)
+        _cmp_partition(res, ref)
+    res, _ = hss.partition(dev(keys), p, eps, 9, max_rounds=1, allow_round_limit=True)
+    ref = oracle.hss(keys, p, eps, 9, max_rounds=1, sort=False)
+    assert res.status == -3 and ref.status == -3
+    _cmp_partition(res, ref)
+
+
+# ---------------------------------------------------------------------------
+# a8/a9 and the whole path
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("N,p,eps,seed,payload", [(1 << 20, 64, 0.05, 1, False), (1 << 20, 64, 0.05, 1, True),
+                                                  (1 << 18, 4, 0.02, 3, True), (99991, 13, 0.05, 2, True),
+                                                  (1000, 999, 0.05, 2, False), (7, 7, 0.05, 1, True),
+                                                  (1 << 15, 1, 0.05, 1, True), (0, 4, 0.05, 1, False)])
+def test_sort_matches_oracle(hss, N, p, eps, seed, payload):
+    keys = inputs.uniform(N, seed)
+    pay = np.arange(N, dtype=np.uint32) if payload else None
+    res = hss.sort(dev(keys), p, eps, seed, payload=dev(pay) if payload else None)
+    ref = oracle.hss(keys, p, eps, seed, payload=pay)
+    _cmp_partition(res, ref)
+    assert np.array_equal(host_u64(res.keys), ref.out_keys)
+    if payload:
+        assert np.array_equal(res.payload.cpu().numpy().view(np.uint32), ref.out_payload)
+
+
+@pytest.mark.parametrize("gen", ["gauss_mix", "zipf", "skew2", "allzeros", "skew3"])
+def test_sort_distributions(hss, gen):
+    N, p, eps, seed = 1 << 18, 8, 0.02, 5
+    keys = GENS[gen](N, seed)
+    pay = np.arange(N, dtype=np.uint32)
+    res = hss.sort(dev(keys), p, eps, seed, payload=dev(pay))
+    ref = oracle.hss(keys, p, eps, seed, payload=pay)
+    _cmp_partition(res, ref)
+    assert np.array_equal(host_u64(res.keys), ref.out_keys)
+    assert np.array_equal(res.payload.cpu().numpy().view(np.uint32), ref.out_payload)
+
+
+def test_sort_signed(hss):
+    N, p, eps, seed = 1 << 17, 3, 0.05, 6
+    keys = inputs.uniform(N, 6).view(np.int64)
+    res = hss.sort(dev(keys), p, eps, seed, key_type="i64")
+    ref = oracle.hss(keys, p, eps, seed)
+    assert np.array_equal(res.keys.cpu().numpy(), ref.out_keys)
+    _cmp_partition(res, ref)
+
+
+def test_exchange_and_merge_steps(hss):
+    """hss_exchange then hss_merge reproduce the oracle's buckets and output."""
+    N, p, eps, seed = 1 << 17, 16, 0.05, 8
+    keys = inputs.uniform(N, seed)
+    pay = np.arange(N, dtype=np.uint32)
+    ref = oracle.hss(keys, p, eps, seed, payload=pay)
+    srt, srtp = hss.local_sort(dev(keys), p, payload=dev(pay))
+    cuts = hss.cuts_from_numpy(ref.splitter_key, ref.splitter_seg, ref.splitter_spos, "cuda")
+    ranks, seg_pos = hss.rank_cuts(srt, p, cuts, want_seg_pos=True)
+    assert np.array_equal(ranks.cpu().numpy().astype(np.uint64), ref.offsets[1:-1])
+    off = torch.from_numpy(ref.offsets.view(np.int64)).cuda()
+    bk, bp = hss.exchange(srt, p, seg_pos, off, sorted_payload=srtp)
+    # every bucket holds the oracle's bucket as a multiset, runs in segment order
+    bkh, refk = host_u64(bk), ref.out_keys
+    for b in range(p):
+        lo, hi = int(ref.offsets[b]), int(ref.offsets[b + 1])
+        assert np.array_equal(np.sort(bkh[lo:hi]), refk[lo:hi])
+    out, outp = hss.merge(bk, p, off, bucket_payload=bp)
+    assert np.array_equal(host_u64(out), ref.out_keys)
+    assert np.array_equal(outp.cpu().numpy().view(np.uint32), ref.out_payload)
+
+
+def test_sort_host_matches_oracle(hss):
+    N, p, eps, seed = 1 << 18, 16, 0.05, 12
+    keys = inputs.uniform(N, seed)
+    pay = np.arange(N, dtype=np.uint32)
+    out, outp, spl, off, st = hss.sort_host(keys, p, eps, seed, payload=pay)
+    ref = oracle.hss(keys, p, eps, seed, payload=pay)
+    assert np.array_equal(out, ref.out_keys)
+    assert np.array_equal(outp, ref.out_payload)
+    assert np.array_equal(off, ref.offsets)
+
+
+def test_repeatable_and_launch_count(hss):
+    N, p = 1 << 18, 8
+    keys = dev(inputs.uniform(N, 1))
+    a = hss.launch_count()
+    r1 = hss.sort(keys, p, 0.02, 1)
+    k1 = r1.keys.clone()
+    r2 = hss.sort(keys, p, 0.02, 1)
+    assert torch.equal(k1, r2.keys)
+    assert hss.launch_count() - a == r1.kernel_launches + r2.kernel_launches > 0
