@@ -1,0 +1,321 @@
+#!/usr/bin/env python3
+"""Benchmark of the HSS hot path on GB300.
+
+Workload: N = 2^28 uint64 keys drawn uniform from [0, 2^64) (seed 1), p = 1024
+virtual processors of 2^18 keys, eps = 0.02, s = 5 probes per processor per
+round.  One step = one hss_sort call: local sort of every segment, splitter
+rounds, exchange of runs to buckets and per-bucket merge, with the input
+already resident in HBM.  The inputs (2 GiB) are larger than L2, so no flush
+is needed between steps.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload instead (the reference arm).
+
+Multi-GPU: the path does not shard across devices in this build; under
+torchrun every rank runs an independent replica of the workload (weak
+scaling) and `value` counts the keys of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "keys/s and % of HBM roofline (1 GB300) for HSS sort at eps; HSS rounds; batched jobs/s; p99"
+LOG2N, P, EPS, SEED, OVERSAMPLE = 28, 1024, 0.02, 1, 5.0
+WORKLOAD = "HSS sort: N=2^28 uint64 keys uniform over [0,2^64) (seed 1), p=1024 segments of 2^18, eps=0.02, s=5"
+CPU_SAMPLE_LOG2N = 24      # cpu_baseline: first 2^24 keys, same p and eps
+REF_SAMPLE_LOG2N = 22      # reference arm: first 2^22 keys per step
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _traffic_record():
+    """Per-launch DRAM bytes of the radix digit pass from the committed ncu
+    summary, valid only while the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "onesweep_pass_traffic.txt")
+    src = os.path.join(ROOT, "paper_1803_01237_gb300", "csrc", "segsort.cu")
+    if not os.path.exists(path):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    rec = {}
+    for line in open(path):
+        line = line.strip()
+        if "=" in line and not line.startswith("#"):
+            k, v = line.split("=", 1)
+            rec[k.strip()] = v.strip()
+    if rec.get("segsort_sha") != sha:
+        return None
+    try:
+        return float(rec["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"hss_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = [ln.split(",") for ln in open(self.path).read().strip().splitlines() if ln.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(log2n: int):
+    import numpy as np
+    import oracle
+    from paper_1803_01237_gb300 import inputs
+    keys = inputs.uniform(1 << LOG2N, SEED)[: 1 << log2n] if log2n < LOG2N else inputs.uniform(1 << LOG2N, SEED)
+    t0 = time.perf_counter()
+    res = oracle.hss(np.ascontiguousarray(keys), P, EPS, SEED, oversample=OVERSAMPLE)
+    dt = time.perf_counter() - t0
+    assert res.status == 0
+    return {"value": (1 << log2n) / dt, "unit": "keys/s", "cores": 1, "kind": "oracle",
+            "sample": f"first 2^{log2n} keys of the workload (same p={P}, eps={EPS}, seed), single-threaded C oracle, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle on a bounded sample per step."""
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    from paper_1803_01237_gb300 import inputs
+    oracle.build()
+    keys = np.ascontiguousarray(inputs.uniform(1 << LOG2N, SEED)[: 1 << REF_SAMPLE_LOG2N])
+    for _ in range(args.warmup):
+        oracle.hss(keys, P, EPS, SEED, oversample=OVERSAMPLE)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.hss(keys, P, EPS, SEED, oversample=OVERSAMPLE)
+        times.append(time.perf_counter() - t0)
+        assert r.status == 0
+    ms = 1000.0 * sum(times) / len(times)
+    value = (1 << REF_SAMPLE_LOG2N) / (ms / 1000.0)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": 1 << LOG2N, "p": P, "eps": EPS, "distribution": "uniform",
+                   "sample_per_step": f"first 2^{REF_SAMPLE_LOG2N} keys"},
+        "cpu_baseline": {"value": value, "unit": "keys/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first 2^{REF_SAMPLE_LOG2N} keys of the workload per step, same p and eps"},
+        "e2e": {"value": value, "unit": "keys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    from paper_1803_01237_gb300 import hss, inputs
+
+    rank, world, local = _env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    hss.load()
+
+    N = 1 << LOG2N
+    keys_h = inputs.uniform(N, SEED)
+    keys = torch.from_numpy(keys_h.view(np.int64)).to(dev)
+    out = torch.empty_like(keys)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def step(flags=0):
+        return hss.sort(keys, P, EPS, SEED, oversample=OVERSAMPLE, flags=flags, out=out)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = hss.launch_count()
+    pass_ms, pass_launches, phase = 0.0, 0, {}
+    rounds = None
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        r = step(flags=hss.FLAG_TIMING)
+        pass_ms += r.ms_radix_pass_total
+        pass_launches += r.radix_pass_launches
+        for k, v in r.ms_phase.items():
+            phase[k] = phase.get(k, 0.0) + v
+        rounds = r
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    launches = hss.launch_count() - launches0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * N / (ms / 1000.0)
+
+    # correctness spot check of the last output (sorted, offsets in range)
+    o = out[:: max(1, N // (1 << 20))].cpu().numpy().view(np.uint64)
+    sorted_ok = bool(np.all(o[:-1] <= o[1:]))
+
+    # roofline of the dominant kernel: the one-sweep digit pass moves 16 B per key
+    peak, peak_kind = _measured_peaks()
+    avg_pass_ms = pass_ms / max(pass_launches, 1)
+    bytes_per_pass = 16.0 * N
+    achieved = bytes_per_pass / (avg_pass_ms / 1000.0) / 1e9
+    traffic = _traffic_record()
+
+    # end to end: pinned host keys -> hss_sort_host -> host sorted keys
+    e2e = None
+    if not args.no_e2e:
+        hk = torch.empty(N, dtype=torch.int64, pin_memory=True)
+        hk.copy_(torch.from_numpy(keys_h.view(np.int64)))
+        ho = torch.empty(N, dtype=torch.int64, pin_memory=True)
+        hkn, hon = hk.numpy(), ho.numpy()
+        hss.sort_host(hkn, P, EPS, SEED, oversample=OVERSAMPLE, out=hon)
+        n_e2e = max(2, min(args.steps, 5))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            hss.sort_host(hkn, P, EPS, SEED, oversample=OVERSAMPLE, out=hon)
+        e2e_s = (time.perf_counter() - t0) / n_e2e
+        if dist is not None:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * N / e2e_s, "unit": "keys/s", "h2d_bytes_per_step": 8 * N,
+               "d2h_bytes_per_step": 8 * N + 16 * (P - 1) + 8 * (P + 1), "ms_per_step": 1000 * e2e_s,
+               "api": "hss_sort_host (pinned host buffers, copies inside the call)"}
+        del hk, ho
+
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "p": P, "eps": EPS, "oversample": OVERSAMPLE,
+                   "distribution": "uniform", "l2": "inputs (2 GiB keys) larger than L2; no flush between steps",
+                   "parallelism": "replicas only" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "kernel": "k_onesweep (radix digit pass, 16 B/key)",
+                     "peak_source": f"{peak_kind} hbm_gbs", "avg_launch_ms": avg_pass_ms,
+                     "launches": pass_launches},
+        "hss": {"rounds": rounds.rounds, "sample_size": rounds.sample_size, "gamma": rounds.gamma,
+                "tol": rounds.tol, "phase_ms": {k: v / args.steps for k, v in phase.items()},
+                "kernels_per_step": rounds.kernel_launches, "output_sorted": sorted_ok},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(min(CPU_SAMPLE_LOG2N, LOG2N))
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--log2n", type=int, default=None,
+                    help="smaller case of the same kernels (keeps 2^18 keys per segment); for profiling only")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.log2n is not None:
+        global LOG2N, P, WORKLOAD
+        LOG2N = args.log2n
+        P = max(1, 1 << max(0, LOG2N - 18))
+        WORKLOAD = f"HSS sort: N=2^{LOG2N} uint64 keys uniform (seed 1), p={P}, eps=0.02, s=5 (profiling case)"
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -212,10 +212,10 @@ static int run_path(const void* d_keys, const uint32_t* d_payload, int key_type,
             h_stats->gamma[j] = rr.gamma[j];
         }
         for (uint32_t j = 0; j <= rr.rounds && j <= HSS_MAX_ROUNDS; ++j) h_stats->unresolved[j] = rr.unresolved[j];
-        h_stats->ms_radix_pass_total = stime.pass_ms;
-        h_stats->radix_pass_launches = stime.pass_launches;
+        stime.collect(&h_stats->ms_radix_pass_total, &h_stats->radix_pass_launches);
         h_stats->kernel_launches = (uint32_t)(g_launches.load() - mark);
     }
+    if (stime.n) stime.collect(nullptr, nullptr);
     return status;
 }
 

@@ -6,7 +6,7 @@
 #include <cuda_runtime.h>
 #include <cuda/atomic>
 
-#include "../../include/hss.h"
+#include "hss.h"
 
 namespace hss {
 

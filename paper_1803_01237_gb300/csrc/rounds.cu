@@ -342,49 +342,50 @@ __global__ __launch_bounds__(1024) void k_count_scan(const uint32_t* __restrict_
     }
 }
 
+// Write the kept keys of each segment, in position order, at the segment's
+// offset of the sample buffer.  Kept keys are exactly the set bits of the
+// bitmap inside the segment, so the pass scans the segment's bitmap words and
+// skips empty runs of them.
 __global__ __launch_bounds__(kSampThreads) void k_sample_write(
-    const uint64_t* __restrict__ skeys, const uint64_t* __restrict__ seg_off, uint32_t S,
-    const uint32_t* __restrict__ Lpos, const uint32_t* __restrict__ Upos, const DCut* __restrict__ Lcut,
-    const uint32_t* __restrict__ int_rep, const RoundCtl* __restrict__ ctl, const uint32_t* __restrict__ bitmap,
+    const uint64_t* __restrict__ skeys, const uint64_t* __restrict__ seg_off, const uint32_t* __restrict__ bitmap,
     const uint32_t* __restrict__ seg_cnt, const uint32_t* __restrict__ seg_cnt_off, uint64_t cap,
     uint64_t* __restrict__ skey, uint32_t* __restrict__ sseg, uint32_t* __restrict__ sspos, uint32_t* __restrict__ siota) {
-    __shared__ uint32_t s_a[kIntChunk], s_b[kIntChunk], s_pre[kIntChunk + 1];
     __shared__ uint32_t s_warp[32];
     const uint32_t s = blockIdx.x;
-    if (seg_cnt[s] == 0) return;
-    const uint64_t base = seg_off[s];
-    const uint32_t nint = ctl->nint;
+    const uint32_t want = seg_cnt[s];
+    if (want == 0) return;
+    const uint64_t base = seg_off[s], end = seg_off[s + 1];
+    const uint64_t w0 = base >> 5, w1 = (end + 31) >> 5;
     uint64_t out = seg_cnt_off[s];
-    for (uint32_t u0 = 0; u0 < nint; u0 += kIntChunk) {
-        const uint32_t nu = min((uint32_t)kIntChunk, nint - u0);
-        const uint32_t P = load_seg_intervals(s, (uint32_t)(seg_off[s + 1] - base), S, u0, nu, Lpos, Upos, Lcut, int_rep,
-                                              s_a, s_b, s_pre, s_warp);
-        for (uint32_t fb = 0; fb < P; fb += kSampThreads) {
-            const uint32_t f = fb + threadIdx.x;
-            bool k0 = false, k1 = false;
-            uint32_t m = 0;
-            if (f < P) {
-                const uint32_t u = find_interval(s_pre, nu, f);
-                const uint32_t a = s_a[u], b = s_b[u];
-                m = (a >> 1) + (f - s_pre[u]);
-                const uint32_t p0 = 2 * m, p1 = 2 * m + 1;
-                if (p0 >= a && p0 < b) { const uint64_t g = base + p0; k0 = (bitmap[g >> 5] >> (g & 31)) & 1u; }
-                if (p1 >= a && p1 < b) { const uint64_t g = base + p1; k1 = (bitmap[g >> 5] >> (g & 31)) & 1u; }
-            }
-            const uint32_t c = (uint32_t)k0 + (uint32_t)k1;
-            uint32_t tot;
-            const uint32_t incl = block_incl_scan<uint32_t>(c, 0u, AddU32(), s_warp, tot);
-            uint64_t o = out + incl - c;
-            if (k0) {
-                if (o < cap) { skey[o] = skeys[base + 2 * m]; sseg[o] = s; sspos[o] = 2 * m; siota[o] = (uint32_t)o; }
-                ++o;
-            }
-            if (k1) {
-                if (o < cap) { skey[o] = skeys[base + 2 * m + 1]; sseg[o] = s; sspos[o] = 2 * m + 1; siota[o] = (uint32_t)o; }
-            }
-            out += tot;
+    uint32_t found = 0;
+    for (uint64_t wb = w0; wb < w1 && found < want; wb += kSampThreads) {
+        const uint64_t wi = wb + threadIdx.x;
+        uint32_t bits = 0;
+        if (wi < w1) {
+            bits = bitmap[wi];
+            const uint64_t g0 = wi << 5;
+            if (g0 < base) bits &= ~0u << (uint32_t)(base - g0);               // bits of the previous segment
+            if (g0 + 32 > end) bits &= (uint32_t)((1ull << (uint32_t)(end - g0)) - 1ull);  // bits of the next
         }
-        __syncthreads();
+        if (__syncthreads_count(bits != 0u) == 0) continue;
+        const uint32_t c = __popc(bits);
+        uint32_t tot;
+        const uint32_t incl = block_incl_scan<uint32_t>(c, 0u, AddU32(), s_warp, tot);
+        uint64_t o = out + incl - c;
+        while (bits) {
+            const uint32_t b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            const uint64_t g = (wi << 5) + b;
+            if (o < cap) {
+                skey[o] = skeys[g];
+                sseg[o] = s;
+                sspos[o] = (uint32_t)(g - base);
+                siota[o] = (uint32_t)o;
+            }
+            ++o;
+        }
+        out += tot;
+        found += tot;
     }
 }
 
@@ -588,8 +589,8 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
         out->gamma[j - 1] = h.gamma;
         if (h.Z > ws.cap) { status = HSS_ERR_CAPACITY; break; }
         const uint64_t Z = h.Z;
-        HSS_LAUNCH(k_sample_write, p, kSampThreads, 0, st, skeys, d_seg_off, S, ws.Lpos, ws.Upos, ws.Lcut, ws.int_rep, ws.ctl,
-                   ws.bitmap, ws.seg_cnt, ws.seg_cnt_off, ws.cap, ws.skey, ws.sseg, ws.sspos, ws.siota);
+        HSS_LAUNCH(k_sample_write, p, kSampThreads, 0, st, skeys, d_seg_off, ws.bitmap, ws.seg_cnt, ws.seg_cnt_off, ws.cap,
+                   ws.skey, ws.sseg, ws.sspos, ws.siota);
         if (Z > 0) {
             HSS_TRY(segsort(ws.skey, ws.skey_sorted, ws.stmp, ws.siota, ws.sperm, ws.ptmp, Z, 1, ws.ctl->seg_off_z, false,
                             false, ws.sws, st, nullptr));
@@ -627,19 +628,36 @@ __device__ __forceinline__ uint32_t bucket_pos(const uint32_t* __restrict__ pos,
     return b == 0 ? 0u : (b == p ? n : pos[s * S + (b - 1)]);
 }
 
-__global__ void k_exchange_dst(const uint64_t* __restrict__ seg_off, uint32_t p, const uint32_t* __restrict__ pos,
-                               const uint64_t* __restrict__ offsets, uint64_t* __restrict__ dst, uint32_t* err) {
-    const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= p) return;
+// Column scans of the run lengths: CTA x handles 32 buckets; its 32 warps
+// split the segments into 32 groups, sum their group, scan the group sums and
+// write the destinations.
+__global__ __launch_bounds__(1024) void k_exchange_dst(const uint64_t* __restrict__ seg_off, uint32_t p,
+                                                       const uint32_t* __restrict__ pos, const uint64_t* __restrict__ offsets,
+                                                       uint64_t* __restrict__ dst, uint32_t* err) {
+    __shared__ uint64_t s_part[32][33];
+    const uint32_t col = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    const uint32_t b = blockIdx.x * 32 + col;
     const uint32_t S = p - 1;
-    uint64_t run = offsets[b];
-    for (uint32_t s = 0; s < p; ++s) {
-        const uint32_t n = (uint32_t)(seg_off[s + 1] - seg_off[s]);
-        const uint32_t lo = bucket_pos(pos, S, p, s, b, n), hi = bucket_pos(pos, S, p, s, b + 1, n);
-        dst[(uint64_t)s * p + b] = run;
-        run += hi - lo;
+    const uint32_t R = (p + 31) / 32;
+    const uint32_t s0 = min(p, grp * R), s1 = min(p, s0 + R);
+    uint64_t part = 0;
+    if (b < p) {
+        for (uint32_t s = s0; s < s1; ++s) {
+            const uint32_t n = (uint32_t)(seg_off[s + 1] - seg_off[s]);
+            part += bucket_pos(pos, S, p, s, b + 1, n) - bucket_pos(pos, S, p, s, b, n);
+        }
     }
-    if (run != offsets[b + 1]) atomicOr(err, kDevErrBounds);
+    s_part[grp][col] = part;
+    __syncthreads();
+    if (b >= p) return;
+    uint64_t run = offsets[b];
+    for (uint32_t g = 0; g < grp; ++g) run += s_part[g][col];
+    for (uint32_t s = s0; s < s1; ++s) {
+        const uint32_t n = (uint32_t)(seg_off[s + 1] - seg_off[s]);
+        dst[(uint64_t)s * p + b] = run;
+        run += bucket_pos(pos, S, p, s, b + 1, n) - bucket_pos(pos, S, p, s, b, n);
+    }
+    if (s1 == p && s0 < s1 && run != offsets[b + 1]) atomicOr(err, kDevErrBounds);
 }
 
 constexpr uint32_t kXchChunk = 4096;
@@ -698,7 +716,7 @@ cudaError_t exchange(const uint64_t* skeys, const uint32_t* spay, uint64_t N, ui
                      const uint32_t* pos, const uint64_t* d_offsets, uint64_t* bkeys, uint32_t* bpay,
                      uint64_t* dst_scratch, uint32_t* err, cudaStream_t st) {
     if (N == 0) return cudaSuccess;
-    HSS_LAUNCH(k_exchange_dst, (unsigned)cdiv(p, 128), 128, 0, st, d_seg_off, p, pos, d_offsets, dst_scratch, err);
+    HSS_LAUNCH(k_exchange_dst, (unsigned)cdiv(p, 32), 1024, 0, st, d_seg_off, p, pos, d_offsets, dst_scratch, err);
     const uint64_t maxn = cdiv(N, p) + 1;
     HSS_LAUNCH(k_exchange_copy, dim3(p, (unsigned)cdiv(maxn, kXchChunk)), 256, 0, st, skeys, spay, d_seg_off, p, pos,
                dst_scratch, bkeys, bpay, N, err);

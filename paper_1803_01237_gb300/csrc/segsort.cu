@@ -74,52 +74,80 @@ __device__ __forceinline__ uint32_t scan256_exclusive(uint32_t v, uint32_t* s_wa
 }
 
 // ---------------------------------------------------------------------------
-// Stable block ranking of 8-bit digits.  Items are warp-striped: item i of
-// lane l in warp w is element w*32*ITEMS + i*32 + l, so (w, i, l) order is
-// element order.  Invalid items pass digit >= 256 and get no rank.
-// On return rank[i] is the element's position in the digit-sorted tile,
-// s_total[d] the tile count of digit d and s_start[d] its exclusive prefix.
+// Peer mask of an 8-bit digit inside a warp, from eight ballots: the lanes
+// whose digit equals this lane's.  Lanes with valid == false match nobody and
+// are matched by nobody.
 // ---------------------------------------------------------------------------
-template <int WARPS, int ITEMS, typename HistT>
-__device__ __forceinline__ void block_rank(const uint32_t (&dig)[ITEMS], uint32_t (&rank)[ITEMS],
-                                           HistT* s_hist /*[WARPS*256]*/, uint32_t* s_total, uint32_t* s_start,
-                                           uint32_t* s_warp) {
+__device__ __forceinline__ uint32_t warp_peers8(uint32_t d, bool valid) {
+    uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+    for (int b = 0; b < kRadixBits; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const uint32_t m = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? m : ~m;
+    }
+    return valid ? peers : 0u;
+}
+
+// ---------------------------------------------------------------------------
+// Stable block ranking of 8-bit digits, in three steps:
+//   1. counts: every warp counts its digits into its own 256 shared counters
+//      (fire-and-forget shared atomics, no dependency chain);
+//   2. offsets: thread d turns the counts into absolute bases
+//      start[d] + sum of earlier warps' counts of d, and the tile totals;
+//   3. ranks: per item, the lanes holding the same digit (ballot peer mask)
+//      take consecutive slots: the highest such lane adds their number to the
+//      warp's base for that digit and broadcasts the old value.
+// Items are warp-striped: item i of lane l in warp w is element
+// w*32*ITEMS + i*32 + l, so (w, i, l) order is element order and the ranks are
+// stable.  Shared atomics issued by one warp in program order are applied in
+// that order, which the running bases of step 3 rely on.
+// `between` runs after step 2 (used to publish the look-back aggregate).
+// ---------------------------------------------------------------------------
+struct NoOp { __device__ void operator()() const {} };
+
+template <int WARPS, int ITEMS, typename DigitOf, typename Between>
+__device__ __forceinline__ void block_rank(DigitOf digit_of, uint32_t (&rank)[ITEMS], uint32_t* s_cnt /*[WARPS*256]*/,
+                                           uint32_t* s_total, uint32_t* s_start, uint32_t* s_warp, Between between) {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    for (int i = tid; i < WARPS * kRadix; i += WARPS * 32) s_hist[i] = 0;
+    for (int i = tid; i < WARPS * kRadix; i += WARPS * 32) s_cnt[i] = 0;
     __syncthreads();
-    HistT* h = s_hist + w * kRadix;
-    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t* c = s_cnt + w * kRadix;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        const uint32_t d = dig[i];
-        const uint32_t key = d < kRadix ? d : (kRadix + lane);
-        const uint32_t peers = __match_any_sync(0xffffffffu, key);
-        uint32_t base = 0;
-        if (d < kRadix) base = h[d];
-        __syncwarp();
-        const uint32_t cnt = __popc(peers);
-        const int leader = 31 - __clz(peers);
-        rank[i] = base + __popc(peers & lt);
-        if (d < kRadix && lane == leader) h[d] = (HistT)(base + cnt);
-        __syncwarp();
+        const uint32_t d = digit_of(i);
+        if (d < kRadix) atomicAdd(&c[d], 1u);
     }
     __syncthreads();
     uint32_t tot = 0;
     if (tid < kRadix) {
+        uint32_t run = 0;
         for (int ww = 0; ww < WARPS; ++ww) {
-            const uint32_t c = s_hist[ww * kRadix + tid];
-            s_hist[ww * kRadix + tid] = (HistT)tot;
-            tot += c;
+            const uint32_t x = s_cnt[ww * kRadix + tid];
+            s_cnt[ww * kRadix + tid] = run;
+            run += x;
         }
+        tot = run;
         s_total[tid] = tot;
     }
     const uint32_t ex = scan256_exclusive(tot, s_warp);
-    if (tid < kRadix) s_start[tid] = ex;
+    if (tid < kRadix) {
+        s_start[tid] = ex;
+        for (int ww = 0; ww < WARPS; ++ww) s_cnt[ww * kRadix + tid] += ex;
+    }
     __syncthreads();
+    between();
+    const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        const uint32_t d = dig[i];
-        if (d < kRadix) rank[i] += s_start[d] + (uint32_t)h[d];
+        const uint32_t d = digit_of(i);
+        const bool valid = d < kRadix;
+        const uint32_t peers = warp_peers8(d & 255u, valid);
+        const int leader = valid ? 31 - __clz(peers) : lane;
+        uint32_t base = 0;
+        if (valid && lane == leader) base = atomicAdd(&c[d], (uint32_t)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        rank[i] = base + __popc(peers & lt);
     }
 }
 
@@ -215,7 +243,7 @@ __global__ __launch_bounds__(256) void k_digit_scan(const uint64_t* __restrict__
 // segments.
 // ---------------------------------------------------------------------------
 template <bool PAY>
-__global__ __launch_bounds__(kOsThreads, 2) void k_onesweep(
+__global__ __launch_bounds__(kOsThreads, 3) void k_onesweep(
     const uint64_t* __restrict__ kin, uint64_t* __restrict__ kout,
     const uint32_t* __restrict__ pin, uint32_t* __restrict__ pout,
     const uint64_t* __restrict__ seg_off, const uint32_t* __restrict__ tile_start, uint64_t nseg,
@@ -250,24 +278,34 @@ __global__ __launch_bounds__(kOsThreads, 2) void k_onesweep(
 
     uint64_t key[kOsItems];
     uint32_t pay[kOsItems];
-    uint32_t dig[kOsItems];
     uint32_t rank[kOsItems];
+    const uint32_t wbase = w * 32 * kOsItems + lane;
 #pragma unroll
     for (int i = 0; i < kOsItems; ++i) {
-        const uint32_t e = w * 32 * kOsItems + i * 32 + lane;
+        const uint32_t e = wbase + i * 32;
         if (e < count) {
             key[i] = kin[seg_base + tile_lo + e] ^ flip_in;
             if (PAY) pay[i] = pin[seg_base + tile_lo + e];
-            dig[i] = (uint32_t)(key[i] >> shift) & 255u;
         } else {
-            key[i] = 0; if (PAY) pay[i] = 0;
-            dig[i] = kRadix;  // invalid
+            key[i] = 0;
+            if (PAY) pay[i] = 0;
         }
     }
-    block_rank<kOsWarps, kOsItems, uint32_t>(dig, rank, s_hist, s_total, s_start, s_warp);
+    auto digit_of = [&](int i) -> uint32_t {
+        return (wbase + i * 32 < count) ? ((uint32_t)(key[i] >> shift) & 255u) : (uint32_t)kRadix;
+    };
+
+    // Publish this tile's digit counts as soon as they are known, so the next
+    // tile's look-back does not wait for our ranking.
+    uint32_t* cur = status + (uint64_t)(pass & 1) * max_tiles * kRadix;
+    uint32_t* nxt = status + (uint64_t)((pass + 1) & 1) * max_tiles * kRadix;
+    auto publish = [&]() {
+        if (tid < kRadix) st_relaxed(&cur[(uint64_t)t * kRadix + tid], (ti == 0 ? kFlagPre : kFlagAgg) | s_total[tid]);
+    };
+    block_rank<kOsWarps, kOsItems>(digit_of, rank, s_hist, s_total, s_start, s_warp, publish);
 #pragma unroll
     for (int i = 0; i < kOsItems; ++i) {
-        if (dig[i] < kRadix) {
+        if (wbase + i * 32 < count) {
             s_keys[rank[i]] = key[i];
             if (PAY) s_pay[rank[i]] = pay[i];
         }
@@ -275,16 +313,11 @@ __global__ __launch_bounds__(kOsThreads, 2) void k_onesweep(
 
     // Decoupled look-back over the earlier tiles of this segment: thread d
     // owns digit d.
-    uint32_t* cur = status + (uint64_t)(pass & 1) * max_tiles * kRadix;
-    uint32_t* nxt = status + (uint64_t)((pass + 1) & 1) * max_tiles * kRadix;
     if (tid < kRadix) {
         const uint32_t d = tid;
         const uint32_t cnt = s_total[d];
         uint32_t excl = 0;
-        if (ti == 0) {
-            st_relaxed(&cur[(uint64_t)t * kRadix + d], kFlagPre | cnt);
-        } else {
-            st_relaxed(&cur[(uint64_t)t * kRadix + d], kFlagAgg | cnt);
+        if (ti != 0) {
             const uint64_t first = tile_start[s];
             uint64_t tt = t - 1;
             for (;;) {
@@ -338,8 +371,8 @@ __global__ __launch_bounds__(kSmThreads, 1) void k_small_sort(
     uint64_t* s_keys = (uint64_t*)smem;                                   // kSmallCap u64
     uint16_t* s_idx0 = (uint16_t*)(s_keys + kSmallCap);                   // kSmallCap u16
     uint16_t* s_idx1 = s_idx0 + kSmallCap;                                // kSmallCap u16
-    uint16_t* s_hist = s_idx1 + kSmallCap;                                // kSmWarps*256 u16
-    uint32_t* s_total = (uint32_t*)(s_hist + kSmWarps * kRadix);          // 256
+    uint32_t* s_hist = (uint32_t*)(s_idx1 + kSmallCap);                   // kSmWarps*256 u32
+    uint32_t* s_total = s_hist + kSmWarps * kRadix;                       // 256
     uint32_t* s_start = s_total + kRadix;                                 // 256
     uint32_t* s_warp = s_start + kRadix;                                  // 32
     uint64_t* s_red = (uint64_t*)(s_warp + 32);                           // 2*32 u64
@@ -374,22 +407,17 @@ __global__ __launch_bounds__(kSmThreads, 1) void k_small_sort(
         for (int pass = 0; pass < kPasses; ++pass) {
             const int shift = 8 * pass;
             if (((vary >> shift) & 255u) == 0u) continue;  // digit constant: identity pass
-            uint32_t dig[kSmItems], rank[kSmItems], idx[kSmItems];
+            uint32_t rank[kSmItems], idx[kSmItems];
+            const uint32_t wbase = w * 32 * kSmItems + lane;
 #pragma unroll
-            for (int i = 0; i < kSmItems; ++i) {
-                const uint32_t e = w * 32 * kSmItems + i * 32 + lane;
-                if (e < n) {
-                    idx[i] = cur[e];
-                    dig[i] = (uint32_t)(s_keys[idx[i]] >> shift) & 255u;
-                } else {
-                    idx[i] = 0;
-                    dig[i] = kRadix;
-                }
-            }
-            block_rank<kSmWarps, kSmItems, uint16_t>(dig, rank, s_hist, s_total, s_start, s_warp);
+            for (int i = 0; i < kSmItems; ++i) idx[i] = (wbase + i * 32 < n) ? cur[wbase + i * 32] : 0u;
+            auto digit_of = [&](int i) -> uint32_t {
+                return (wbase + i * 32 < n) ? ((uint32_t)(s_keys[idx[i]] >> shift) & 255u) : (uint32_t)kRadix;
+            };
+            block_rank<kSmWarps, kSmItems>(digit_of, rank, s_hist, s_total, s_start, s_warp, NoOp());
 #pragma unroll
             for (int i = 0; i < kSmItems; ++i)
-                if (dig[i] < kRadix && rank[i] < n) nxt[rank[i]] = (uint16_t)idx[i];
+                if (wbase + i * 32 < n && rank[i] < n) nxt[rank[i]] = (uint16_t)idx[i];
             __syncthreads();
             uint16_t* t = cur; cur = nxt; nxt = t;
         }
@@ -403,7 +431,7 @@ __global__ __launch_bounds__(kSmThreads, 1) void k_small_sort(
 }
 
 static size_t small_sort_smem() {
-    return (size_t)kSmallCap * 8 + 2 * (size_t)kSmallCap * 2 + (size_t)kSmWarps * kRadix * 2 + 2 * kRadix * 4 + 32 * 4 +
+    return (size_t)kSmallCap * 8 + 2 * (size_t)kSmallCap * 2 + (size_t)kSmWarps * kRadix * 4 + 2 * kRadix * 4 + 32 * 4 +
            64 * 8;
 }
 
@@ -468,11 +496,11 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp,
             os_attr[PAY ? 1 : 0] = true;
         }
     }
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    if (timing && timing->enabled) {
-        cudaEventCreate(&ev0);
-        cudaEventCreate(&ev1);
-        cudaEventRecord(ev0, st);
+    const bool timed = timing && timing->enabled && timing->n < 8;
+    if (timed) {
+        cudaEventCreate(&timing->ev[timing->n][0]);
+        cudaEventCreate(&timing->ev[timing->n][1]);
+        cudaEventRecord(timing->ev[timing->n][0], st);
     }
     for (int pass = 0; pass < kPasses; ++pass) {
         // pass writes: even -> tmp, odd -> dst; the last (odd) pass lands in dst
@@ -485,16 +513,10 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp,
                    pass == kPasses - 1 ? fout : 0ull);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if (timing && timing->enabled) {
-        cudaEventRecord(ev1, st);
-        cudaEventSynchronize(ev1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, ev0, ev1);
-        timing->pass_ms += ms;
-        timing->pass_launches += kPasses;
-        timing->pass_keys += 0;  // filled by the caller, which knows the large-segment key count
-        cudaEventDestroy(ev0);
-        cudaEventDestroy(ev1);
+    if (timed) {
+        cudaEventRecord(timing->ev[timing->n][1], st);
+        timing->launches[timing->n] = kPasses;
+        timing->n += 1;
     }
     return cudaSuccess;
 }

@@ -20,9 +20,9 @@ constexpr int kOsWarps = kOsThreads / 32;
 constexpr int kOsItems = 16;
 constexpr int kOsTile = kOsThreads * kOsItems;  // 4096 keys per tile
 
-constexpr int kSmThreads = 1024;
+constexpr int kSmThreads = 512;
 constexpr int kSmWarps = kSmThreads / 32;
-constexpr int kSmItems = 16;
+constexpr int kSmItems = 32;
 constexpr int kSmallCap = kSmThreads * kSmItems;  // 16384 keys per on-chip segment
 
 struct SegSortWs {
@@ -41,9 +41,27 @@ SegSortWs segsort_ws_carve(void* base, uint64_t N, uint64_t nseg, uint32_t* err)
 
 struct SegSortTiming {
     bool enabled = false;
-    float pass_ms = 0.f;      // summed onesweep pass time
-    uint32_t pass_launches = 0;
-    uint64_t pass_keys = 0;   // keys moved by the timed passes (upper bound N per pass)
+    int n = 0;                      // recorded (start, end) pairs around digit-pass groups
+    cudaEvent_t ev[8][2] = {};
+    uint32_t launches[8] = {};
+    // Sum the recorded pass times (call after the stream has passed the last
+    // recorded event) and release the events.
+    void collect(float* ms_total, uint32_t* n_launches) {
+        float tot = 0.f;
+        uint32_t nl = 0;
+        for (int i = 0; i < n; ++i) {
+            float ms = 0.f;
+            cudaEventSynchronize(ev[i][1]);
+            cudaEventElapsedTime(&ms, ev[i][0], ev[i][1]);
+            tot += ms;
+            nl += launches[i];
+            cudaEventDestroy(ev[i][0]);
+            cudaEventDestroy(ev[i][1]);
+        }
+        n = 0;
+        if (ms_total) *ms_total = tot;
+        if (n_launches) *n_launches = nl;
+    }
 };
 
 // Stable sort of every segment [seg_off[s], seg_off[s+1]) of src into dst.
