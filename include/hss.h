@@ -43,6 +43,7 @@ extern "C" {
 #define HSS_ERR_TIMEOUT (-4)      /* a bounded device-side wait gave up */
 #define HSS_ERR_CUDA (-5)         /* a CUDA runtime call failed */
 #define HSS_ERR_CAPACITY (-6)     /* a round drew more probes than the sample buffer holds */
+#define HSS_ERR_NOALLOC_LIMIT (-7) /* input larger than the fixed scratch of hss_local_sort_noalloc */
 
 #define HSS_KEY_U64 0
 #define HSS_KEY_I64 1
@@ -168,6 +169,29 @@ int hss_sort_host(const void* h_keys, const uint32_t* h_payload, int key_type, u
  * the Philox4x32-10 word each key is compared against.  d_out: count u64. */
 int hss_sample_words(uint64_t seed, uint32_t seg, uint32_t round, uint32_t spos0, uint32_t count,
                      uint64_t* d_out, void* stream);
+
+/* hss_local_sort for callers that may not allocate device memory at all:
+ * code running inside a host framework that owns every device allocation
+ * (a database or stream engine calling a user function, a plugin of a
+ * serving runtime with a fixed memory budget), or a thread that must not
+ * take the allocator's locks or synchronise the device the way cudaMalloc
+ * and cudaFree can.  The paper has no counterpart; this is a library
+ * service, not a step of the method.
+ *
+ * Same arguments and result as hss_local_sort without d_work/work_bytes: the
+ * scratch is a fixed 16 MiB array inside the library's device image, resident
+ * on every device that loads the library until the process exits.  Limits:
+ * N <= 524288 keys, and the scratch the sort needs for (N, p) must fit those
+ * 16 MiB (the call computes it); otherwise it returns HSS_ERR_NOALLOC_LIMIT
+ * before any device work.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call, from any thread or stream,
+ * uses the same array and leaves its contents behind, so calls that can
+ * overlap on the GPU race with each other: serialise them.  The call
+ * synchronises `stream` to read the kernels' status word.  It allocates
+ * nothing, neither through CUDA nor through any other library. */
+int hss_local_sort_noalloc(const void* d_keys, const uint32_t* d_payload, int key_type, uint64_t N, uint32_t p,
+                           void* d_keys_out, uint32_t* d_payload_out, void* stream);
 
 /* Kernels launched by this library in this process so far. */
 uint64_t hss_kernel_launch_count(void);

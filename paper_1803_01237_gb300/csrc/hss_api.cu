@@ -375,6 +375,7 @@ const char* hss_strerror(int code) {
     case HSS_ERR_TIMEOUT: return "a bounded device-side wait timed out";
     case HSS_ERR_CUDA: return "CUDA runtime error";
     case HSS_ERR_CAPACITY: return "a round drew more probes than the sample buffer holds";
+    case HSS_ERR_NOALLOC_LIMIT: return "input exceeds the fixed scratch of hss_local_sort_noalloc (N <= 524288, 16 MiB)";
     default: return "unknown error";
     }
 }
