@@ -52,7 +52,7 @@ def _measured_peaks():
 def _traffic_record():
     """Per-launch DRAM bytes of the radix digit pass from the committed ncu
     summary, valid only while the kernel source is unchanged."""
-    path = os.path.join(ROOT, "profiles", "onesweep_pass_traffic.txt")
+    path = os.path.join(ROOT, "profiles", "k_split_traffic.txt")
     src = os.path.join(ROOT, "paper_1803_01237_gb300", "csrc", "segsort.cu")
     if not os.path.exists(path):
         return None
@@ -205,7 +205,7 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = hss.launch_count()
-    pass_ms, pass_launches, phase = 0.0, 0, {}
+    pass_ms, pass_launches, pass_keys, phase = 0.0, 0, 0, {}
     rounds = None
     barrier()
     ev0.record(stream)
@@ -213,6 +213,7 @@ def run_gpu(args):
         r = step(flags=hss.FLAG_TIMING)
         pass_ms += r.ms_radix_pass_total
         pass_launches += r.radix_pass_launches
+        pass_keys += r.radix_pass_keys
         for k, v in r.ms_phase.items():
             phase[k] = phase.get(k, 0.0) + v
         rounds = r
@@ -231,11 +232,12 @@ def run_gpu(args):
     o = out[:: max(1, N // (1 << 20))].cpu().numpy().view(np.uint64)
     sorted_ok = bool(np.all(o[:-1] <= o[1:]))
 
-    # roofline of the dominant kernel: the one-sweep digit pass moves 16 B per key
+    # roofline of the dominant kernel: the one-sweep split pass reads and
+    # writes every key of the segments it splits once (16 B per key)
     peak, peak_kind = _measured_peaks()
     avg_pass_ms = pass_ms / max(pass_launches, 1)
-    bytes_per_pass = 16.0 * N
-    achieved = bytes_per_pass / (avg_pass_ms / 1000.0) / 1e9
+    bytes_per_pass = 16.0 * pass_keys / max(pass_launches, 1)
+    achieved = bytes_per_pass / (avg_pass_ms / 1000.0) / 1e9 if pass_launches else 0.0
     traffic = _traffic_record()
 
     # end to end: pinned host keys -> hss_sort_host -> host sorted keys
@@ -275,7 +277,8 @@ def run_gpu(args):
                    "distribution": "uniform", "l2": "inputs (2 GiB keys) larger than L2; no flush between steps",
                    "parallelism": "replicas only" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "k_onesweep (radix digit pass, 16 B/key)",
+                     "traffic": traffic, "kernel": "k_split (one-sweep MSD scatter, 16 B/key)",
+                     "bytes_per_launch": bytes_per_pass,
                      "peak_source": f"{peak_kind} hbm_gbs", "avg_launch_ms": avg_pass_ms,
                      "launches": pass_launches},
         "hss": {"rounds": rounds.rounds, "sample_size": rounds.sample_size, "gamma": rounds.gamma,

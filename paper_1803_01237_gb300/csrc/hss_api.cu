@@ -189,8 +189,11 @@ static int run_path(const void* d_keys, const uint32_t* d_payload, int key_type,
                 return HSS_ERR_CUDA;
             tm.mark(HSS_PHASE_EXCHANGE);
             // Merge (Sec. 6 local merging): stable sort of each bucket's runs.
+            // The keys of bucket b lie between splitters b and b+1, so the first
+            // split of each bucket spreads that key range over 256 sub-buckets.
+            if (bucket_hints(rws, p, st) != cudaSuccess) return HSS_ERR_CUDA;
             if (segsort(keysB, (uint64_t*)d_keys_out, keysA, payB, d_payload_out, payA, N, p, d_offsets, false, i64, sws,
-                        st, &stime) != cudaSuccess)
+                        st, &stime, rws.bucket_lo, rws.bucket_mult) != cudaSuccess)
                 return HSS_ERR_CUDA;
             tm.mark(HSS_PHASE_MERGE);
         }
@@ -212,10 +215,10 @@ static int run_path(const void* d_keys, const uint32_t* d_payload, int key_type,
             h_stats->gamma[j] = rr.gamma[j];
         }
         for (uint32_t j = 0; j <= rr.rounds && j <= HSS_MAX_ROUNDS; ++j) h_stats->unresolved[j] = rr.unresolved[j];
-        stime.collect(&h_stats->ms_radix_pass_total, &h_stats->radix_pass_launches);
+        stime.collect(&h_stats->ms_radix_pass_total, &h_stats->radix_pass_launches, &h_stats->radix_pass_keys);
         h_stats->kernel_launches = (uint32_t)(g_launches.load() - mark);
     }
-    if (stime.n) stime.collect(nullptr, nullptr);
+    if (stime.n) stime.collect(nullptr, nullptr, nullptr);
     return status;
 }
 

@@ -51,6 +51,8 @@ size_t rounds_ws_bytes(uint64_t N, uint64_t p, uint64_t cap) {
     b += aup(cap * sizeof(uint64_t)) * 2;      // pkey, prank
     b += 3 * aup(cap * sizeof(uint32_t));      // pseg, pspos, pint
     b += aup(p * cap * sizeof(uint32_t));      // probe_pos
+    b += aup(S1 * sizeof(uint64_t)) + aup(S1 * sizeof(uint32_t));  // fin_okey, fin_kind
+    b += 2 * aup(p * sizeof(uint64_t));                             // bucket_lo, bucket_mult
     b += segsort_ws_bytes(cap, 1);
     return b;
 }
@@ -89,6 +91,10 @@ RoundWs rounds_ws_carve(void* base, uint64_t N, uint64_t p, uint64_t cap, uint32
     w.pspos = (uint32_t*)take(cap * sizeof(uint32_t));
     w.pint = (uint32_t*)take(cap * sizeof(uint32_t));
     w.probe_pos = (uint32_t*)take(p * cap * sizeof(uint32_t));
+    w.fin_okey = (uint64_t*)take(S1 * sizeof(uint64_t));
+    w.fin_kind = (uint32_t*)take(S1 * sizeof(uint32_t));
+    w.bucket_lo = (uint64_t*)take(p * sizeof(uint64_t));
+    w.bucket_mult = (uint64_t*)take(p * sizeof(uint64_t));
     w.sws = segsort_ws_carve(q, cap, 1, err);
     w.cap = cap;
     return w;
@@ -517,7 +523,8 @@ __global__ void k_update_pos(uint32_t S, const int32_t* __restrict__ chgL, const
 // ---------------------------------------------------------------------------
 __global__ void k_finalize(uint32_t S, uint64_t N, uint32_t p, int key_type, const DCut* __restrict__ Lcut,
                            const DCut* __restrict__ Ucut, hss_cut* __restrict__ spl, uint64_t* __restrict__ offsets,
-                           uint32_t* __restrict__ choose_u) {
+                           uint32_t* __restrict__ choose_u, uint64_t* __restrict__ fin_okey,
+                           uint32_t* __restrict__ fin_kind) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) { offsets[0] = 0; offsets[p] = N; }
     if (i >= S) return;
@@ -534,6 +541,39 @@ __global__ void k_finalize(uint32_t S, uint64_t N, uint32_t p, int key_type, con
     spl[i] = o;
     offsets[i + 1] = c.rank;
     choose_u[i] = useU ? 1u : 0u;
+    fin_okey[i] = c.okey;
+    fin_kind[i] = (uint32_t)c.kind;
+}
+
+// Bucket b holds keys between splitters b and b+1 (sentinels: the ends of the
+// key range).  Its first split interpolates that range onto 256 sub-buckets:
+// digit = mulhi(key - lo, floor(255 * 2^64 / (hi - lo))), monotone in the key
+// and at most 255; a range narrower than 256 uses key - lo itself.
+__global__ void k_bucket_hint(uint32_t p, const uint64_t* __restrict__ fin_okey, const uint32_t* __restrict__ fin_kind,
+                              uint64_t* __restrict__ lo_out, uint64_t* __restrict__ mult_out) {
+    const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= p) return;
+    auto bound = [&](uint32_t i, uint64_t if_none) -> uint64_t {  // splitter number i (1..p-1)
+        if (i == 0 || i == p) return if_none;
+        const uint32_t k = fin_kind[i - 1];
+        if (k == (uint32_t)kNegInf) return 0ull;
+        if (k == (uint32_t)kPosInf) return ~0ull;
+        return fin_okey[i - 1];
+    };
+    const uint64_t lo = bound(b, 0ull);
+    uint64_t hi = bound(b + 1, ~0ull);
+    if (hi < lo) hi = lo;  // empty bucket
+    const uint64_t r = hi - lo;
+    // mult = 0 selects the plain form ((key >> 0) - lo) & 255 = key - lo
+    const uint64_t mult = r < 256 ? 0ull : (uint64_t)(((unsigned __int128)255 << 64) / r);
+    lo_out[b] = lo;
+    mult_out[b] = mult;
+}
+
+cudaError_t bucket_hints(const RoundWs& ws, uint32_t p, cudaStream_t st) {
+    HSS_LAUNCH(k_bucket_hint, (unsigned)cdiv(p, 256), 256, 0, st, p, ws.fin_okey, ws.fin_kind, ws.bucket_lo,
+               ws.bucket_mult);
+    return cudaGetLastError();
 }
 
 __global__ void k_final_pos(uint32_t S, const uint32_t* __restrict__ choose_u, uint32_t* __restrict__ Lpos,
@@ -564,7 +604,8 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
     const uint64_t tol = (uint64_t)std::floor(((double)N * eps) / (2.0 * (double)p));
     HSS_TRY(cudaMemsetAsync(ws.ctl, 0, sizeof(RoundCtl), st));
     if (S == 0) {
-        HSS_LAUNCH(k_finalize, 1, 32, 0, st, 0u, N, p, key_type, ws.Lcut, ws.Ucut, d_splitters, d_offsets, ws.choose_u);
+        HSS_LAUNCH(k_finalize, 1, 32, 0, st, 0u, N, p, key_type, ws.Lcut, ws.Ucut, d_splitters, d_offsets, ws.choose_u,
+                   ws.fin_okey, ws.fin_kind);
         HSS_TRY(cudaGetLastError());
         out->rounds = 0;
         out->status = HSS_OK;
@@ -613,7 +654,7 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
     out->rounds = j;
     out->status = status;
     HSS_LAUNCH(k_finalize, (unsigned)cdiv(S, 256), 256, 0, st, S, N, p, key_type, ws.Lcut, ws.Ucut, d_splitters, d_offsets,
-               ws.choose_u);
+               ws.choose_u, ws.fin_okey, ws.fin_kind);
     HSS_LAUNCH(k_final_pos, dim3(p, sblk), 256, 0, st, S, ws.choose_u, ws.Lpos, ws.Upos);
     HSS_TRY(cudaGetLastError());
     return status;

@@ -49,6 +49,10 @@ struct RoundWs {
     uint32_t* pint;      // [cap]
     uint64_t* prank;     // [cap]
     uint32_t* probe_pos; // [p][cap]
+    uint64_t* fin_okey;  // [S] order-preserving key of each final splitter
+    uint32_t* fin_kind;  // [S]
+    uint64_t* bucket_lo;    // [p] lower key bound of each bucket (its first split digit is
+    uint64_t* bucket_mult;  // [p] mulhi(key - lo, mult), an interpolation of [lo, hi] onto 0..255)
     SegSortWs sws;       // scratch of the probe sort
     uint64_t cap;        // sample capacity
 };
@@ -71,6 +75,9 @@ struct RoundResult {
 int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uint32_t p, double eps, uint64_t seed,
                float oversample, uint32_t max_rounds, int key_type, hss_cut* d_splitters, uint64_t* d_offsets,
                const RoundWs& ws, cudaStream_t st, RoundResult* out);
+
+// Per-bucket split windows for the merge, from the final splitters.
+cudaError_t bucket_hints(const RoundWs& ws, uint32_t p, cudaStream_t st);
 
 // Exchange: per-(segment, bucket) destinations, then the run copy.
 cudaError_t exchange(const uint64_t* skeys, const uint32_t* spay, uint64_t N, uint32_t p, const uint64_t* d_seg_off,

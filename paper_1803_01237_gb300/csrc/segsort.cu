@@ -1,18 +1,27 @@
-// segsort.cu -- stable segmented LSD radix sort (local sort of Sec. 5/6 and,
-// over bucket ranges, the local merge).
+// segsort.cu -- stable segmented radix sort (local sort of Sec. 5/6 and, over
+// bucket ranges, the local merge).
 //
 // Design for sm_103a:
-//  * Small segments (<= 16384 keys): one 1024-thread CTA loads the whole
-//    segment into shared memory once, runs the 8-bit digit passes on chip over
-//    a 16-bit index permutation (the keys stay put), skips digits that are
-//    constant over the segment, and writes the sorted keys once: 16 B of HBM
-//    traffic per key.
-//  * Large segments: a digit-histogram pass (8 B/key) followed by eight
-//    one-sweep digit passes (16 B/key each).  Each 4096-key tile ranks its keys
-//    in shared memory (warp match + per-warp counters), publishes its digit
-//    counts and chains the per-segment exclusive prefix by decoupled look-back
-//    over the tiles of the same segment, then scatters from shared memory so
-//    that runs of equal digits are written contiguously.
+//  * A segment of at most 14336 keys is sorted by one CTA on chip: its keys are
+//    read from HBM once into shared memory; a counting pass on a 10-bit digit
+//    that interpolates the segment's [min, max] key range splits them into
+//    1024 groups in key order; every key's final slot is its group's start plus
+//    the number of keys of its group below it in (key, input position) order;
+//    the keys are written once (16 B of HBM traffic per key).  Three CTA shapes
+//    by segment size (128, 256, 512 threads).  A segment whose largest group is
+//    above kTinyGroup keys (heavy duplicates, skew) goes to a stable LSD kernel
+//    (8-bit digit passes over a 16-bit index permutation).
+//  * A larger segment takes one read pass for statistics (digit counts and the
+//    OR/AND of its keys) and one one-sweep stable scatter on its first-split
+//    digit (its top varying byte, or an interpolation of the key range the
+//    caller bounds): every 4096-key tile ranks its keys in shared memory with
+//    ballot peer masks, publishes its digit counts and chains the segment's
+//    exclusive digit prefix by decoupled look-back over the earlier tiles of the
+//    same segment.  The 256 sub-buckets are then sorted the same way (on chip
+//    when small, recursively otherwise), so a uniform 64-bit input costs
+//    8 + 16 + 16 B of HBM traffic per key instead of the 136 B of eight LSD
+//    passes.  A segment whose keys are all equal is copied straight to the
+//    output by its scatter pass.
 #include "segsort.cuh"
 
 #include <algorithm>
@@ -26,51 +35,105 @@ constexpr uint32_t kCountMask = (1u << 30) - 1u;
 __host__ __device__ static inline uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 static inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+static uint64_t max_large_of(uint64_t N) { return std::max<uint64_t>(1, N / (kSmallCap + 1)); }
+
+struct WsDims {
+    uint64_t ml, list, tiles;
+};
+static WsDims ws_dims(uint64_t N, uint64_t nseg) {
+    WsDims d;
+    d.ml = max_large_of(N);
+    d.list = std::max<uint64_t>(nseg, d.ml * kRadix);
+    d.tiles = ceil_div(std::max<uint64_t>(N, 1), kOsTile) + d.ml + 1;
+    return d;
+}
+
 size_t segsort_ws_bytes(uint64_t N, uint64_t nseg) {
-    const uint64_t max_tiles = ceil_div(N, kOsTile) + nseg + 1;
+    const WsDims d = ws_dims(N, nseg);
     size_t b = 0;
-    b += align_up(nseg * kPasses * kRadix * sizeof(uint32_t), 256);
-    b += align_up((nseg + 1) * sizeof(uint32_t), 256);
-    b += align_up(2 * max_tiles * kRadix * sizeof(uint32_t), 256);
-    b += align_up(64 * sizeof(uint32_t), 256);
+    b += align_up((d.list + 1) * 4, 256) + align_up(d.list * 4, 256);  // tile_start, large_id
+    b += align_up(d.ml * 4, 256);                                     // large_seg
+    b += align_up(d.ml * 8 * kRadix * 4, 256);                        // hist
+    b += 2 * align_up(d.ml * 8, 256);                                 // vor, vand
+    b += align_up(d.ml * kRadix * 4, 256);                            // msd_off
+    b += 2 * align_up(d.ml * 4, 256);                                 // msd_shift, direct
+    b += 2 * align_up(d.ml * 8, 256);                                 // msd_base, msd_mult
+    b += 4 * align_up(d.ml * kRadix * 8, 256);                        // sub_lo/hi x2
+    b += align_up(d.tiles * kRadix * 4, 256);                         // status
+    b += align_up(64 * 4, 256);                                       // counters
+    b += 4 * align_up(d.list * 4, 256);                               // class lists, fallback list
+    b += align_up(8 * (d.list / 1024 + 2) * 4, 256);                  // blk
     return b;
 }
 
 SegSortWs segsort_ws_carve(void* base, uint64_t N, uint64_t nseg, uint32_t* err) {
+    const WsDims d = ws_dims(N, nseg);
     SegSortWs w;
-    w.max_tiles = ceil_div(N, kOsTile) + nseg + 1;
+    w.max_large = d.ml;
+    w.max_list = d.list;
+    w.max_tiles = d.tiles;
     char* p = (char*)base;
-    w.digit_off = (uint32_t*)p; p += align_up(nseg * kPasses * kRadix * sizeof(uint32_t), 256);
-    w.tile_start = (uint32_t*)p; p += align_up((nseg + 1) * sizeof(uint32_t), 256);
-    w.status = (uint32_t*)p; p += align_up(2 * w.max_tiles * kRadix * sizeof(uint32_t), 256);
-    w.counters = (uint32_t*)p; p += align_up(64 * sizeof(uint32_t), 256);
+    auto take = [&](size_t bytes) { void* r = p; p += align_up(bytes, 256); return r; };
+    w.tile_start = (uint32_t*)take((d.list + 1) * 4);
+    w.large_id = (uint32_t*)take(d.list * 4);
+    w.large_seg = (uint32_t*)take(d.ml * 4);
+    w.hist = (uint32_t*)take(d.ml * 8 * kRadix * 4);
+    w.vor = (unsigned long long*)take(d.ml * 8);
+    w.vand = (unsigned long long*)take(d.ml * 8);
+    w.msd_off = (uint32_t*)take(d.ml * kRadix * 4);
+    w.msd_shift = (uint32_t*)take(d.ml * 4);
+    w.direct = (uint32_t*)take(d.ml * 4);
+    w.msd_base = (uint64_t*)take(d.ml * 8);
+    w.msd_mult = (uint64_t*)take(d.ml * 8);
+    for (int i = 0; i < 2; ++i) {
+        w.sub_lo[i] = (uint64_t*)take(d.ml * kRadix * 8);
+        w.sub_hi[i] = (uint64_t*)take(d.ml * kRadix * 8);
+    }
+    w.status = (uint32_t*)take(d.tiles * kRadix * 4);
+    w.counters = (uint32_t*)take(64 * 4);
+    for (int i = 0; i < 3; ++i) w.list[i] = (uint32_t*)take(d.list * 4);
+    w.fb_list = (uint32_t*)take(d.list * 4);
+    w.blk = (uint32_t*)take(8 * (d.list / 1024 + 2) * 4);
     w.err = err;
     return w;
 }
 
+// Digit of the first split of a segment: an 8-bit window of the key, or (mult
+// != 0) a linear interpolation of the segment's key range onto 0..255.
+__device__ __forceinline__ uint32_t split_digit(uint64_t key, int shift, uint64_t base, uint64_t mult) {
+    if (mult) return min((uint32_t)__umul64hi(key - base, mult), 255u);
+    return (uint32_t)((key >> shift) - base) & 255u;
+}
+
 // ---------------------------------------------------------------------------
-// Block-wide exclusive scan of 256 values held one per thread by threads
-// 0..255 (the caller guarantees blockDim >= 256).  Returns the exclusive
-// prefix for threads < 256.
+// Exclusive scan of 256 shared values by a CTA of T threads (T >= 64).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t scan256_exclusive(uint32_t v, uint32_t* s_warp /*[8]*/) {
+template <int T>
+__device__ __forceinline__ void scan256_smem(const uint32_t* in, uint32_t* out, uint32_t* s_warp) {
+    constexpr int U = T < kRadix ? T : kRadix;
+    constexpr int K = kRadix / U;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    uint32_t x = v;
-    if (tid < 256) {
+    uint32_t loc[K];
+    uint32_t sum = 0;
+    if (tid < U) {
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) s_warp[w] = x;
+        for (int k = 0; k < K; ++k) { loc[k] = in[tid * K + k]; sum += loc[k]; }
+    }
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31 && tid < U) s_warp[w] = x;
+    __syncthreads();
+    if (tid < U) {
+        uint32_t run = x - sum;
+        for (int i = 0; i < w; ++i) run += s_warp[i];
+#pragma unroll
+        for (int k = 0; k < K; ++k) { out[tid * K + k] = run; run += loc[k]; }
     }
     __syncthreads();
-    uint32_t add = 0;
-    if (tid < 256) {
-        for (int i = 0; i < w; ++i) add += s_warp[i];
-    }
-    __syncthreads();
-    return add + x - v;
 }
 
 // ---------------------------------------------------------------------------
@@ -93,53 +156,57 @@ __device__ __forceinline__ uint32_t warp_peers8(uint32_t d, bool valid) {
 // Stable block ranking of 8-bit digits, in three steps:
 //   1. counts: every warp counts its digits into its own 256 shared counters
 //      (fire-and-forget shared atomics, no dependency chain);
-//   2. offsets: thread d turns the counts into absolute bases
-//      start[d] + sum of earlier warps' counts of d, and the tile totals;
+//   2. offsets: the counts become absolute bases start[d] + (earlier warps'
+//      counts of d), plus the tile totals;
 //   3. ranks: per item, the lanes holding the same digit (ballot peer mask)
 //      take consecutive slots: the highest such lane adds their number to the
 //      warp's base for that digit and broadcasts the old value.
 // Items are warp-striped: item i of lane l in warp w is element
 // w*32*ITEMS + i*32 + l, so (w, i, l) order is element order and the ranks are
 // stable.  Shared atomics issued by one warp in program order are applied in
-// that order, which the running bases of step 3 rely on.
-// `between` runs after step 2 (used to publish the look-back aggregate).
+// that order, which the running bases of step 3 rely on.  `between` runs after
+// step 2 (used to publish the look-back aggregate early).
 // ---------------------------------------------------------------------------
 struct NoOp { __device__ void operator()() const {} };
 
 template <int WARPS, int ITEMS, typename DigitOf, typename Between>
-__device__ __forceinline__ void block_rank(DigitOf digit_of, uint32_t (&rank)[ITEMS], uint32_t* s_cnt /*[WARPS*256]*/,
-                                           uint32_t* s_total, uint32_t* s_start, uint32_t* s_warp, Between between) {
+__device__ __forceinline__ void block_rank(DigitOf digit_of, uint32_t count, uint32_t (&rank)[ITEMS],
+                                           uint32_t* s_cnt /*[WARPS*256]*/, uint32_t* s_total, uint32_t* s_start,
+                                           uint32_t* s_warp, Between between) {
+    constexpr int T = WARPS * 32;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    for (int i = tid; i < WARPS * kRadix; i += WARPS * 32) s_cnt[i] = 0;
+    const uint32_t wfirst = (uint32_t)w * 32 * ITEMS;  // element of the warp's first item slot
+    for (int i = tid; i < WARPS * kRadix; i += T) s_cnt[i] = 0;
     __syncthreads();
     uint32_t* c = s_cnt + w * kRadix;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
+        if (wfirst + i * 32 >= count) break;  // the rest of this warp's slots are empty
         const uint32_t d = digit_of(i);
         if (d < kRadix) atomicAdd(&c[d], 1u);
     }
     __syncthreads();
-    uint32_t tot = 0;
-    if (tid < kRadix) {
+    for (int d = tid; d < kRadix; d += T) {
         uint32_t run = 0;
         for (int ww = 0; ww < WARPS; ++ww) {
-            const uint32_t x = s_cnt[ww * kRadix + tid];
-            s_cnt[ww * kRadix + tid] = run;
+            const uint32_t x = s_cnt[ww * kRadix + d];
+            s_cnt[ww * kRadix + d] = run;
             run += x;
         }
-        tot = run;
-        s_total[tid] = tot;
+        s_total[d] = run;
     }
-    const uint32_t ex = scan256_exclusive(tot, s_warp);
-    if (tid < kRadix) {
-        s_start[tid] = ex;
-        for (int ww = 0; ww < WARPS; ++ww) s_cnt[ww * kRadix + tid] += ex;
+    __syncthreads();
+    scan256_smem<T>(s_total, s_start, s_warp);
+    for (int d = tid; d < kRadix; d += T) {
+        const uint32_t st = s_start[d];
+        for (int ww = 0; ww < WARPS; ++ww) s_cnt[ww * kRadix + d] += st;
     }
     __syncthreads();
     between();
     const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
+        if (wfirst + i * 32 >= count) break;
         const uint32_t d = digit_of(i);
         const bool valid = d < kRadix;
         const uint32_t peers = warp_peers8(d & 255u, valid);
@@ -152,39 +219,388 @@ __device__ __forceinline__ void block_rank(DigitOf digit_of, uint32_t (&rank)[IT
 }
 
 // ---------------------------------------------------------------------------
-// Planning: tiles of the large segments.
+// On-chip sort of segments with min_n < n <= max_n keys (n <= CAP), taken
+// from `list` (compact ids, count at *nlist) or, when list is null, from all
+// nseg segments.  The keys are read once into shared memory.  One counting
+// pass on the top varying 8-bit window splits them into 256 groups that come
+// in key order (the keys agree on every bit above the window); inside a group
+// the atomics leave an arbitrary order, and each key's final slot is its
+// group's start plus the number of keys of the group below it in
+// (key, input position) order -- a total order, so the result is the stable
+// sort.  A segment with a group larger than kTinyGroup is left to the stable
+// LSD kernel below (appended to the fallback list).
 // ---------------------------------------------------------------------------
-__global__ void k_seg_plan(const uint64_t* __restrict__ seg_off, uint64_t nseg, uint32_t* __restrict__ tile_start,
-                           uint32_t* __restrict__ counters) {
-    __shared__ uint32_t s_warp[32];
-    __shared__ uint32_t s_carry;
+constexpr int kChipRadix = 1024;  // groups of the on-chip counting pass
+
+// Exclusive scan of NV shared values in place by a CTA of T threads.
+template <int T, int NV>
+__device__ __forceinline__ void scan_smem_inplace(uint32_t* v, uint32_t* s_warp) {
+    constexpr int K = NV / T;
+    static_assert(NV % T == 0, "scan size");
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    if (tid == 0) s_carry = 0;
-    if (tid < 64) counters[tid] = 0;
-    __syncthreads();
-    for (uint64_t base = 0; base < nseg; base += blockDim.x) {
-        const uint64_t s = base + tid;
-        uint32_t nt = 0;
-        if (s < nseg) {
-            const uint64_t n = seg_off[s + 1] - seg_off[s];
-            nt = n > (uint64_t)kSmallCap ? (uint32_t)ceil_div(n, kOsTile) : 0u;
-        }
-        uint32_t x = nt;
+    uint32_t loc[K];
+    uint32_t sum = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
+    for (int k = 0; k < K; ++k) { loc[k] = v[tid * K + k]; sum += loc[k]; }
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    uint32_t run = x - sum;
+    for (int i = 0; i < w; ++i) run += s_warp[i];
+#pragma unroll
+    for (int k = 0; k < K; ++k) { v[tid * K + k] = run; run += loc[k]; }
+    __syncthreads();
+}
+
+template <int CAP>
+constexpr size_t msd_sort_smem() {
+    return (size_t)CAP * 8 + 3 * (size_t)CAP * 2 + 2 * (kChipRadix + 1) * 4 + 32 * 4 + 2 * 32 * 8 + 64;
+}
+
+template <bool PAY, int THREADS, int CAP>
+__global__ __launch_bounds__(THREADS) void k_small_msd(
+    const uint64_t* __restrict__ kin, uint64_t* __restrict__ kout, const uint32_t* __restrict__ pin,
+    uint32_t* __restrict__ pout, const uint64_t* __restrict__ seg_lo, const uint64_t* __restrict__ seg_hi,
+    const uint32_t* __restrict__ list, const uint32_t* __restrict__ nlist, uint64_t nseg, uint32_t min_n,
+    uint32_t max_n, uint64_t flip_in, uint64_t flip_out, uint32_t* __restrict__ fb_list, uint32_t* __restrict__ fb_count) {
+    constexpr int WARPS = THREADS / 32;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t* s_keys = (uint64_t*)smem;                        // CAP u64
+    uint16_t* s_grp = (uint16_t*)(s_keys + CAP);               // CAP u16: positions grouped by digit
+    uint16_t* s_out = s_grp + CAP;                             // CAP u16: positions in sorted order
+    uint16_t* s_dig = s_out + CAP;                             // CAP u16: digit of each position
+    uint32_t* s_start = (uint32_t*)(s_dig + CAP);              // kChipRadix+1: counts, then group starts
+    uint32_t* s_run = s_start + (kChipRadix + 1);              // kChipRadix+1: running write positions
+    uint32_t* s_warp = s_run + (kChipRadix + 1);               // 32
+    uint64_t* s_red = (uint64_t*)(((uintptr_t)(s_warp + 32) + 7) & ~(uintptr_t)7);  // 2*32
+
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const uint64_t count = list ? (uint64_t)*nlist : nseg;
+    for (uint64_t k = blockIdx.x; k < count; k += gridDim.x) {
+        const uint64_t s = list ? (uint64_t)list[k] : k;
+        const uint64_t base = seg_lo[s];
+        const uint64_t n64 = seg_hi[s] - base;
+        if (n64 <= min_n || n64 > max_n) continue;  // uniform per CTA
+        const uint32_t n = (uint32_t)n64;
+        uint64_t kmin = ~0ull, kmax = 0;
+        for (uint32_t j = tid; j < n; j += THREADS) {
+            const uint64_t key = kin[base + j] ^ flip_in;
+            s_keys[j] = key;
+            kmin = min(kmin, key);
+            kmax = max(kmax, key);
         }
-        if (lane == 31) s_warp[w] = x;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            kmin = min(kmin, (uint64_t)__shfl_xor_sync(0xffffffffu, kmin, o));
+            kmax = max(kmax, (uint64_t)__shfl_xor_sync(0xffffffffu, kmax, o));
+        }
+        if (lane == 0) { s_red[w] = kmin; s_red[32 + w] = kmax; }
+        for (int d = tid; d < kChipRadix; d += THREADS) s_start[d] = 0;
         __syncthreads();
-        uint32_t add = s_carry;
-        for (int i = 0; i < w; ++i) add += s_warp[i];
-        if (s < nseg) tile_start[s] = add + x - nt;
+        {
+            uint64_t a = ~0ull, b = 0;
+            for (int i = 0; i < WARPS; ++i) { a = min(a, s_red[i]); b = max(b, s_red[32 + i]); }
+            kmin = a;
+            kmax = b;
+        }
+        if (kmin == kmax) {  // all keys equal: already in order
+            for (uint32_t j = tid; j < n; j += THREADS) {
+                kout[base + j] = s_keys[j] ^ flip_out;
+                if (PAY) pout[base + j] = pin[base + j];
+            }
+            __syncthreads();
+            continue;
+        }
+        // Counting pass on a 10-bit digit: the key range [kmin, kmax]
+        // interpolated onto 0..1023, monotone in the key (a plain offset when
+        // the range is narrower than 1024).  The groups come in key order; the
+        // atomics leave an arbitrary order inside a group, and each key's final
+        // slot is its group's start plus the number of keys of the group below
+        // it in (key, input position) order -- a total order, so the result is
+        // the stable sort.  Any monotone digit gives the same result, so the
+        // multiplier only needs to be about 1023 * 2^64 / range.
+        const uint64_t range = kmax - kmin;
+        const uint64_t mult = range < (uint64_t)kChipRadix ? 0ull : (uint64_t)(1.8871019187404871e22 / (double)range);
+        for (uint32_t e = tid; e < n; e += THREADS) {
+            const uint64_t off = s_keys[e] - kmin;
+            const uint32_t d = mult ? min((uint32_t)__umul64hi(off, mult), (uint32_t)kChipRadix - 1) : (uint32_t)off;
+            s_dig[e] = (uint16_t)d;
+            atomicAdd(&s_start[d], 1u);
+        }
         __syncthreads();
-        if (tid == blockDim.x - 1) s_carry = add + x;
+        uint32_t mx = 0;
+        for (int d = tid; d < kChipRadix; d += THREADS) mx = max(mx, s_start[d]);
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        scan_smem_inplace<THREADS, kChipRadix>(s_start, s_warp);
+        if (lane == 0) s_warp[w] = mx;
+        for (int d = tid; d < kChipRadix; d += THREADS) s_run[d] = s_start[d];
+        if (tid == 0) s_start[kChipRadix] = n;
+        __syncthreads();
+        mx = 0;
+        for (int i = 0; i < WARPS; ++i) mx = max(mx, s_warp[i]);
+        if (mx > (uint32_t)kTinyGroup) {  // skewed: the stable LSD kernel takes this segment
+            if (tid == 0) fb_list[atomicAdd(fb_count, 1u)] = (uint32_t)s;
+            __syncthreads();
+            continue;
+        }
+        for (uint32_t e = tid; e < n; e += THREADS) s_grp[atomicAdd(&s_run[s_dig[e]], 1u)] = (uint16_t)e;
+        __syncthreads();
+        for (uint32_t q = tid; q < n; q += THREADS) {
+            const uint16_t x = s_grp[q];
+            const uint64_t kx = s_keys[x];
+            const uint32_t d = s_dig[x];
+            const uint32_t a = s_start[d], b = s_start[d + 1];
+            uint32_t r = 0;
+            for (uint32_t g = a; g < b; ++g) {
+                const uint16_t y = s_grp[g];
+                const uint64_t ky = s_keys[y];
+                r += (ky < kx || (ky == kx && y < x)) ? 1u : 0u;
+            }
+            s_out[a + r] = x;
+        }
+        __syncthreads();
+        for (uint32_t j = tid; j < n; j += THREADS) {
+            const uint32_t src = s_out[j];
+            kout[base + j] = s_keys[src] ^ flip_out;
+            if (PAY) pout[base + j] = pin[base + src];
+        }
         __syncthreads();
     }
-    if (tid == 0) tile_start[nseg] = s_carry;
+}
+
+// ---------------------------------------------------------------------------
+// Stable LSD sort on chip of the segments in the fallback list (at most
+// kSmallCap keys each): 8-bit digit passes over a 16-bit index permutation,
+// skipping digits that are constant over the segment.
+// ---------------------------------------------------------------------------
+template <int THREADS, int ITEMS>
+constexpr size_t lsd_sort_smem() {
+    return (size_t)THREADS * ITEMS * 8 + 2 * (size_t)THREADS * ITEMS * 2 + (size_t)(THREADS / 32) * kRadix * 4 +
+           2 * kRadix * 4 + 32 * 4 + 2 * 32 * 8;
+}
+
+template <bool PAY, int THREADS, int ITEMS>
+__global__ __launch_bounds__(THREADS, 1) void k_small_lsd(
+    const uint64_t* __restrict__ kin, uint64_t* __restrict__ kout, const uint32_t* __restrict__ pin,
+    uint32_t* __restrict__ pout, const uint64_t* __restrict__ seg_lo, const uint64_t* __restrict__ seg_hi,
+    const uint32_t* __restrict__ list, const uint32_t* __restrict__ nlist, uint64_t flip_in, uint64_t flip_out) {
+    constexpr int WARPS = THREADS / 32;
+    constexpr int CAP = THREADS * ITEMS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t* s_keys = (uint64_t*)smem;                        // CAP u64
+    uint16_t* s_idx0 = (uint16_t*)(s_keys + CAP);              // CAP u16
+    uint16_t* s_idx1 = s_idx0 + CAP;                           // CAP u16
+    uint32_t* s_cnt = (uint32_t*)(s_idx1 + CAP);               // WARPS*256
+    uint32_t* s_total = s_cnt + WARPS * kRadix;                // 256
+    uint32_t* s_start = s_total + kRadix;                      // 256
+    uint32_t* s_warp = s_start + kRadix;                       // 32
+    uint64_t* s_red = (uint64_t*)(s_warp + 32);                // 2*32
+
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const uint64_t count = *nlist;
+    const uint32_t wbase = w * 32 * ITEMS + lane;
+    const uint32_t wfirst = (uint32_t)w * 32 * ITEMS;
+    for (uint64_t k = blockIdx.x; k < count; k += gridDim.x) {
+        const uint64_t s = list[k];
+        const uint64_t base = seg_lo[s];
+        const uint64_t n64 = seg_hi[s] - base;
+        if (n64 == 0 || n64 > (uint64_t)CAP) continue;
+        const uint32_t n = (uint32_t)n64;
+        uint64_t vor = 0, vand = ~0ull;
+        for (uint32_t j = tid; j < n; j += THREADS) {
+            const uint64_t key = kin[base + j] ^ flip_in;
+            s_keys[j] = key;
+            s_idx0[j] = (uint16_t)j;
+            vor |= key;
+            vand &= key;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            vor |= __shfl_xor_sync(0xffffffffu, vor, o);
+            vand &= __shfl_xor_sync(0xffffffffu, vand, o);
+        }
+        if (lane == 0) { s_red[w] = vor; s_red[32 + w] = vand; }
+        __syncthreads();
+        uint64_t vary;
+        {
+            uint64_t a = 0, b = ~0ull;
+            for (int i = 0; i < WARPS; ++i) { a |= s_red[i]; b &= s_red[32 + i]; }
+            vary = a ^ b;
+        }
+        uint16_t* cur = s_idx0;
+        uint16_t* nxt = s_idx1;
+        for (int pass = 0; pass < 8; ++pass) {
+            const int shift = 8 * pass;
+            if (((vary >> shift) & 255u) == 0u) continue;  // digit constant: identity pass
+            uint32_t idx[ITEMS], rank[ITEMS];
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) idx[i] = (wbase + i * 32 < n) ? cur[wbase + i * 32] : 0u;
+            auto digit_of = [&](int i) -> uint32_t {
+                return (wbase + i * 32 < n) ? ((uint32_t)(s_keys[idx[i]] >> shift) & 255u) : (uint32_t)kRadix;
+            };
+            block_rank<WARPS, ITEMS>(digit_of, n, rank, s_cnt, s_total, s_start, s_warp, NoOp());
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                if (wfirst + i * 32 >= n) break;
+                if (wbase + i * 32 < n && rank[i] < n) nxt[rank[i]] = (uint16_t)idx[i];
+            }
+            __syncthreads();
+            uint16_t* t = cur; cur = nxt; nxt = t;
+        }
+        for (uint32_t j = tid; j < n; j += THREADS) {
+            const uint32_t src = cur[j];
+            kout[base + j] = s_keys[src] ^ flip_out;
+            if (PAY) pout[base + j] = pin[base + src];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Planning of one level, as a three-step scan over chunks of 1024 segments:
+// compact lists of the segments of each on-chip size class, compact ids and
+// tiles of the segments above the on-chip capacity.
+// counters[16..18] = class sizes, [19] = #large, [20] = #tiles,
+// [22..23] = keys in large segments.
+// ---------------------------------------------------------------------------
+struct PlanV {
+    uint32_t c[5];  // classes 0..2, large, tiles
+    unsigned long long keys;
+};
+
+__device__ __forceinline__ PlanV plan_item(const uint64_t* seg_lo, const uint64_t* seg_hi, uint64_t nseg, uint64_t s) {
+    PlanV v = {{0, 0, 0, 0, 0}, 0ull};
+    if (s < nseg) {
+        const uint64_t n = seg_hi[s] - seg_lo[s];
+        if (n == 0) {
+        } else if (n <= (uint64_t)kC0Cap) {
+            v.c[0] = 1;
+        } else if (n <= (uint64_t)kC1Cap) {
+            v.c[1] = 1;
+        } else if (n <= (uint64_t)kSmallCap) {
+            v.c[2] = 1;
+        } else {
+            v.c[3] = 1;
+            v.c[4] = (uint32_t)ceil_div(n, kOsTile);
+            v.keys = n;
+        }
+    }
+    return v;
+}
+
+// Inclusive scan of PlanV over the CTA; returns the totals in tot.
+__device__ __forceinline__ void plan_scan(PlanV& v, PlanV& tot) {
+    __shared__ uint32_t s_c[5][32];
+    __shared__ unsigned long long s_k[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, v.c[i], o);
+            if (lane >= o) v.c[i] += y;
+        }
+        const unsigned long long yk = __shfl_up_sync(0xffffffffu, v.keys, o);
+        if (lane >= o) v.keys += yk;
+    }
+    if (lane == 31) {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) s_c[i][w] = v.c[i];
+        s_k[w] = v.keys;
+    }
+    __syncthreads();
+    tot = PlanV{{0, 0, 0, 0, 0}, 0ull};
+    for (int j = 0; j < nw; ++j) {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            if (j < w) v.c[i] += s_c[i][j];
+            tot.c[i] += s_c[i][j];
+        }
+        if (j < w) v.keys += s_k[j];
+        tot.keys += s_k[j];
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void blk_store(uint32_t* blk, uint32_t i, const PlanV& v) {
+    uint32_t* b = blk + 8 * (uint64_t)i;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) b[k] = v.c[k];
+    *(unsigned long long*)(b + 6) = v.keys;
+}
+__device__ __forceinline__ PlanV blk_load(const uint32_t* blk, uint32_t i) {
+    const uint32_t* b = blk + 8 * (uint64_t)i;
+    PlanV v;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) v.c[k] = b[k];
+    v.keys = *(const unsigned long long*)(b + 6);
+    return v;
+}
+
+__global__ __launch_bounds__(1024) void k_plan_count(const uint64_t* __restrict__ seg_lo, const uint64_t* __restrict__ seg_hi,
+                                                     uint64_t nseg, uint32_t* __restrict__ blk) {
+    PlanV v = plan_item(seg_lo, seg_hi, nseg, (uint64_t)blockIdx.x * 1024 + threadIdx.x), tot;
+    plan_scan(v, tot);
+    if (threadIdx.x == 0) blk_store(blk, blockIdx.x, tot);
+}
+
+// Exclusive scan of the chunk totals (one CTA), totals into counters.
+__global__ __launch_bounds__(1024) void k_plan_scan(uint32_t nblk, uint32_t* __restrict__ blk, uint32_t* __restrict__ counters) {
+    PlanV carry = {{0, 0, 0, 0, 0}, 0ull};
+    for (uint32_t base = 0; base < nblk; base += blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        PlanV v = i < nblk ? blk_load(blk, i) : PlanV{{0, 0, 0, 0, 0}, 0ull};
+        const PlanV v0 = v;
+        PlanV tot;
+        plan_scan(v, tot);
+        if (i < nblk) {
+            PlanV ex;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) ex.c[k] = carry.c[k] + v.c[k] - v0.c[k];
+            ex.keys = carry.keys + v.keys - v0.keys;
+            blk_store(blk, i, ex);
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) carry.c[k] += tot.c[k];
+        carry.keys += tot.keys;
+    }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 5; ++k) counters[16 + k] = carry.c[k];
+        *(unsigned long long*)(counters + 22) = carry.keys;
+        counters[0] = 0;   // tile counter of this level's scatter pass
+        counters[24] = 0;  // fallback list of this level's on-chip sorts
+    }
+}
+
+__global__ __launch_bounds__(1024) void k_plan_write(const uint64_t* __restrict__ seg_lo, const uint64_t* __restrict__ seg_hi,
+                                                     uint64_t nseg, const uint32_t* __restrict__ blk,
+                                                     const uint32_t* __restrict__ counters, uint32_t* __restrict__ tile_start,
+                                                     uint32_t* __restrict__ large_id, uint32_t* __restrict__ large_seg,
+                                                     uint32_t* __restrict__ list0, uint32_t* __restrict__ list1,
+                                                     uint32_t* __restrict__ list2) {
+    const uint64_t s = (uint64_t)blockIdx.x * 1024 + threadIdx.x;
+    const PlanV item = plan_item(seg_lo, seg_hi, nseg, s);
+    PlanV v = item, tot;
+    plan_scan(v, tot);
+    const PlanV off = blk_load(blk, blockIdx.x);
+    if (s < nseg) {
+        tile_start[s] = off.c[4] + v.c[4] - item.c[4];
+        large_id[s] = 0xffffffffu;
+        if (item.c[0]) list0[off.c[0] + v.c[0] - 1] = (uint32_t)s;
+        if (item.c[1]) list1[off.c[1] + v.c[1] - 1] = (uint32_t)s;
+        if (item.c[2]) list2[off.c[2] + v.c[2] - 1] = (uint32_t)s;
+        if (item.c[3]) {
+            const uint32_t id = off.c[3] + v.c[3] - 1;
+            large_id[s] = id;
+            large_seg[id] = (uint32_t)s;
+        }
+    }
+    if (s == nseg) tile_start[nseg] = counters[20];
 }
 
 __device__ __forceinline__ uint32_t find_tile_segment(const uint32_t* __restrict__ tile_start, uint64_t nseg, uint32_t t) {
@@ -198,60 +614,141 @@ __device__ __forceinline__ uint32_t find_tile_segment(const uint32_t* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// Digit histograms of the large segments: all 8 digit positions in one read.
-// Grid (nseg, split); CTA (s, k) counts the k-th share of segment s's tiles.
+// Statistics of the large segments: 8 byte histograms (or, with a window
+// hint, the window histogram) and the OR/AND of the keys, in one read.
+// Grid (#large, split); CTA (id, k) reads the k-th share of segment id.
 // ---------------------------------------------------------------------------
-__global__ __launch_bounds__(256) void k_digit_hist(const uint64_t* __restrict__ kin, const uint64_t* __restrict__ seg_off,
-                                                    uint32_t* __restrict__ digit_off, uint32_t split, uint64_t flip_in) {
-    __shared__ uint32_t s_h[kPasses * kRadix];
-    const uint64_t s = blockIdx.x;
-    const uint64_t lo = seg_off[s], n = seg_off[s + 1] - lo;
-    if (n <= (uint64_t)kSmallCap) return;
+__global__ __launch_bounds__(256) void k_seg_stats(const uint64_t* __restrict__ kin, const uint64_t* __restrict__ seg_lo,
+                                                   const uint64_t* __restrict__ seg_hi, const uint32_t* __restrict__ large_seg,
+                                                   const uint32_t* __restrict__ counters, uint32_t* __restrict__ hist,
+                                                   unsigned long long* __restrict__ vor, unsigned long long* __restrict__ vand,
+                                                   const uint64_t* __restrict__ hint_lo, const uint64_t* __restrict__ hint_mult,
+                                                   uint32_t split, uint64_t flip_in) {
+    __shared__ uint32_t s_h[8 * kRadix];
+    __shared__ unsigned long long s_or[8], s_and[8];
+    const uint32_t id = blockIdx.x;
+    if (id >= counters[19]) return;
+    const uint32_t s = large_seg[id];
+    const uint64_t lo = seg_lo[s], n = seg_hi[s] - lo;
     const uint64_t per = ceil_div(ceil_div(n, kOsTile), split) * kOsTile;
     const uint64_t a = (uint64_t)blockIdx.y * per;
     if (a >= n) return;
     const uint64_t b = min(n, a + per);
-    for (int i = threadIdx.x; i < kPasses * kRadix; i += blockDim.x) s_h[i] = 0;
+    const bool win = hint_lo != nullptr;
+    const uint64_t hb = win ? hint_lo[s] : 0ull;
+    const uint64_t hm = win ? hint_mult[s] : 0ull;
+    for (int i = threadIdx.x; i < 8 * kRadix; i += blockDim.x) s_h[i] = 0;
     __syncthreads();
+    unsigned long long o = 0, an = ~0ull;
     for (uint64_t e = a + threadIdx.x; e < b; e += blockDim.x) {
         const uint64_t k = kin[lo + e] ^ flip_in;
+        o |= k;
+        an &= k;
+        if (win) {
+            atomicAdd(&s_h[split_digit(k, 0, hb, hm)], 1u);
+        } else {
 #pragma unroll
-        for (int p = 0; p < kPasses; ++p) atomicAdd(&s_h[p * kRadix + ((k >> (8 * p)) & 255u)], 1u);
+            for (int p = 0; p < 8; ++p) atomicAdd(&s_h[p * kRadix + ((uint32_t)(k >> (8 * p)) & 255u)], 1u);
+        }
     }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        o |= __shfl_xor_sync(0xffffffffu, o, off);
+        an &= __shfl_xor_sync(0xffffffffu, an, off);
+    }
+    if ((threadIdx.x & 31) == 0) { s_or[threadIdx.x >> 5] = o; s_and[threadIdx.x >> 5] = an; }
     __syncthreads();
-    uint32_t* g = digit_off + s * (kPasses * kRadix);
-    for (int i = threadIdx.x; i < kPasses * kRadix; i += blockDim.x) {
+    if (threadIdx.x == 0) {
+        unsigned long long x = 0, y = ~0ull;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { x |= s_or[i]; y &= s_and[i]; }
+        atomicOr(&vor[id], x);
+        atomicAnd(&vand[id], y);
+    }
+    uint32_t* g = hist + (uint64_t)id * (8 * kRadix);
+    const int nh = win ? kRadix : 8 * kRadix;
+    for (int i = threadIdx.x; i < nh; i += blockDim.x) {
         const uint32_t c = s_h[i];
         if (c) atomicAdd(&g[i], c);
     }
 }
 
-// In place: counts -> exclusive offsets, per (segment, pass).
-__global__ __launch_bounds__(256) void k_digit_scan(const uint64_t* __restrict__ seg_off, uint32_t* __restrict__ digit_off) {
-    __shared__ uint32_t s_warp[8];
-    const uint64_t s = blockIdx.x;
-    const uint64_t n = seg_off[s + 1] - seg_off[s];
-    if (n <= (uint64_t)kSmallCap) return;
-    uint32_t* g = digit_off + s * (kPasses * kRadix) + blockIdx.y * kRadix;
-    const uint32_t v = g[threadIdx.x];
-    const uint32_t ex = scan256_exclusive(v, s_warp);
-    g[threadIdx.x] = ex;
+// Window of each large segment's split, its exclusive digit offsets and the
+// bounds of its 256 sub-buckets (empty when the keys are all equal).
+__global__ __launch_bounds__(256) void k_msd_prep(const uint64_t* __restrict__ seg_lo, const uint32_t* __restrict__ large_seg,
+                                                  const uint32_t* __restrict__ counters, const uint32_t* __restrict__ hist,
+                                                  const unsigned long long* __restrict__ vor,
+                                                  const unsigned long long* __restrict__ vand, const uint64_t* __restrict__ hint_lo,
+                                                  const uint64_t* __restrict__ hint_mult, uint64_t* __restrict__ msd_base,
+                                                  uint64_t* __restrict__ msd_mult,
+                                                  uint32_t* __restrict__ msd_off, uint32_t* __restrict__ msd_shift,
+                                                  uint32_t* __restrict__ direct, uint64_t* __restrict__ sub_lo,
+                                                  uint64_t* __restrict__ sub_hi) {
+    __shared__ uint32_t s_c[kRadix], s_x[kRadix], s_warp[32];
+    const uint32_t id = blockIdx.x;
+    if (id >= counters[19]) return;
+    const uint32_t s = large_seg[id];
+    const uint64_t lo = seg_lo[s];
+    const unsigned long long vary = vor[id] ^ vand[id];
+    uint32_t shift = 0, row;
+    uint64_t base = 0, mult = 0;
+    if (hint_lo) {
+        base = hint_lo[s];
+        mult = hint_mult[s];
+        row = 0;
+    } else {
+        const uint32_t t = vary ? (uint32_t)(63 - __clzll((long long)vary)) >> 3 : 0u;
+        shift = 8 * t;
+        row = t;
+    }
+    const bool dir = vary == 0ull;
+    s_c[threadIdx.x] = hist[((uint64_t)id * 8 + row) * kRadix + threadIdx.x];
+    __syncthreads();
+    scan256_smem<256>(s_c, s_x, s_warp);
+    const uint32_t c = s_c[threadIdx.x], x = s_x[threadIdx.x];
+    msd_off[(uint64_t)id * kRadix + threadIdx.x] = x;
+    sub_lo[(uint64_t)id * kRadix + threadIdx.x] = dir ? lo : lo + x;
+    sub_hi[(uint64_t)id * kRadix + threadIdx.x] = dir ? lo : lo + x + c;
+    if (threadIdx.x == 0) {
+        msd_shift[id] = shift;
+        msd_base[id] = base;
+        msd_mult[id] = mult;
+        direct[id] = dir ? 1u : 0u;
+    }
 }
 
 // ---------------------------------------------------------------------------
-// One digit pass of the one-sweep radix sort over the tiles of all large
-// segments.
+// The split pass: one-sweep stable scatter of every large segment on its
+// window, over all tiles of all large segments.
 // ---------------------------------------------------------------------------
+struct SplitArgs {
+    const uint64_t* kin;
+    uint64_t* kout;      // next level
+    uint64_t* kfinal;    // output (segments whose keys are all equal)
+    const uint32_t* pin;
+    uint32_t* pout;
+    uint32_t* pfinal;
+    const uint64_t* seg_lo;
+    const uint64_t* seg_hi;
+    uint64_t nseg;
+    const uint32_t* tile_start;
+    const uint32_t* large_id;
+    const uint32_t* msd_off;
+    const uint32_t* msd_shift;
+    const uint64_t* msd_base;
+    const uint64_t* msd_mult;
+    const uint32_t* direct;
+    uint32_t* status;
+    uint32_t* counter;
+    uint32_t* err;
+    uint64_t flip_in;
+    uint64_t flip_out;
+};
+
 template <bool PAY>
-__global__ __launch_bounds__(kOsThreads, 3) void k_onesweep(
-    const uint64_t* __restrict__ kin, uint64_t* __restrict__ kout,
-    const uint32_t* __restrict__ pin, uint32_t* __restrict__ pout,
-    const uint64_t* __restrict__ seg_off, const uint32_t* __restrict__ tile_start, uint64_t nseg,
-    const uint32_t* __restrict__ digit_off, uint32_t* __restrict__ status, uint64_t max_tiles,
-    uint32_t* __restrict__ counters, uint32_t* __restrict__ err, int pass, uint64_t flip_in, uint64_t flip_out) {
+__global__ __launch_bounds__(kOsThreads, 3) void k_split(const SplitArgs A) {
     extern __shared__ __align__(16) unsigned char os_smem[];
-    uint64_t* s_keys = (uint64_t*)os_smem;                 // kOsTile keys
-    uint32_t* s_pay = (uint32_t*)(s_keys + kOsTile);       // kOsTile payloads (PAY)
+    uint64_t* s_keys = (uint64_t*)os_smem;            // kOsTile keys
+    uint32_t* s_pay = (uint32_t*)(s_keys + kOsTile);  // kOsTile payloads (PAY)
     __shared__ uint32_t s_hist[kOsWarps * kRadix];
     __shared__ uint32_t s_total[kRadix], s_start[kRadix];
     __shared__ uint64_t s_gbase[kRadix];
@@ -259,22 +756,29 @@ __global__ __launch_bounds__(kOsThreads, 3) void k_onesweep(
     __shared__ uint32_t s_tile, s_seg;
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const uint32_t total_tiles = tile_start[nseg];
+    const uint32_t total_tiles = A.tile_start[A.nseg];
     if (tid == 0) {
-        const uint32_t t = atomicAdd(&counters[pass], 1u);
+        const uint32_t t = atomicAdd(A.counter, 1u);
         s_tile = t;
-        s_seg = t < total_tiles ? find_tile_segment(tile_start, nseg, t) : 0u;
+        s_seg = t < total_tiles ? find_tile_segment(A.tile_start, A.nseg, t) : 0u;
     }
     __syncthreads();
     const uint32_t t = s_tile;
     if (t >= total_tiles) return;
     const uint32_t s = s_seg;
-    const uint64_t seg_base = seg_off[s];
-    const uint64_t seg_n = seg_off[s + 1] - seg_base;
-    const uint32_t ti = t - tile_start[s];
+    const uint32_t id = A.large_id[s];
+    const uint64_t seg_base = A.seg_lo[s];
+    const uint64_t seg_n = A.seg_hi[s] - seg_base;
+    const uint32_t ti = t - A.tile_start[s];
     const uint64_t tile_lo = (uint64_t)ti * kOsTile;
     const uint32_t count = (uint32_t)min((uint64_t)kOsTile, seg_n - tile_lo);
-    const int shift = 8 * pass;
+    const int shift = (int)A.msd_shift[id];
+    const uint64_t dbase = A.msd_base[id];
+    const uint64_t dmult = A.msd_mult[id];
+    const bool dir = A.direct[id] != 0u;
+    uint64_t* kout = dir ? A.kfinal : A.kout;
+    uint32_t* pout = dir ? A.pfinal : A.pout;
+    const uint64_t flip_out = dir ? A.flip_out : 0ull;
 
     uint64_t key[kOsItems];
     uint32_t pay[kOsItems];
@@ -284,25 +788,23 @@ __global__ __launch_bounds__(kOsThreads, 3) void k_onesweep(
     for (int i = 0; i < kOsItems; ++i) {
         const uint32_t e = wbase + i * 32;
         if (e < count) {
-            key[i] = kin[seg_base + tile_lo + e] ^ flip_in;
-            if (PAY) pay[i] = pin[seg_base + tile_lo + e];
+            key[i] = A.kin[seg_base + tile_lo + e] ^ A.flip_in;
+            if (PAY) pay[i] = A.pin[seg_base + tile_lo + e];
         } else {
             key[i] = 0;
             if (PAY) pay[i] = 0;
         }
     }
     auto digit_of = [&](int i) -> uint32_t {
-        return (wbase + i * 32 < count) ? ((uint32_t)(key[i] >> shift) & 255u) : (uint32_t)kRadix;
+        return (wbase + i * 32 < count) ? split_digit(key[i], shift, dbase, dmult) : (uint32_t)kRadix;
     };
-
     // Publish this tile's digit counts as soon as they are known, so the next
     // tile's look-back does not wait for our ranking.
-    uint32_t* cur = status + (uint64_t)(pass & 1) * max_tiles * kRadix;
-    uint32_t* nxt = status + (uint64_t)((pass + 1) & 1) * max_tiles * kRadix;
+    uint32_t* cur = A.status;
     auto publish = [&]() {
         if (tid < kRadix) st_relaxed(&cur[(uint64_t)t * kRadix + tid], (ti == 0 ? kFlagPre : kFlagAgg) | s_total[tid]);
     };
-    block_rank<kOsWarps, kOsItems>(digit_of, rank, s_hist, s_total, s_start, s_warp, publish);
+    block_rank<kOsWarps, kOsItems>(digit_of, count, rank, s_hist, s_total, s_start, s_warp, publish);
 #pragma unroll
     for (int i = 0; i < kOsItems; ++i) {
         if (wbase + i * 32 < count) {
@@ -318,14 +820,14 @@ __global__ __launch_bounds__(kOsThreads, 3) void k_onesweep(
         const uint32_t cnt = s_total[d];
         uint32_t excl = 0;
         if (ti != 0) {
-            const uint64_t first = tile_start[s];
+            const uint64_t first = A.tile_start[s];
             uint64_t tt = t - 1;
             for (;;) {
                 uint32_t v;
                 uint32_t it = 0;
                 while (((v = ld_relaxed(&cur[tt * kRadix + d])) & (kFlagAgg | kFlagPre)) == 0u) {
                     if (++it > kSpinLimit) {
-                        atomicOr(err, kDevErrTimeout);
+                        atomicOr(A.err, kDevErrTimeout);
                         v = kFlagPre;
                         break;
                     }
@@ -334,105 +836,28 @@ __global__ __launch_bounds__(kOsThreads, 3) void k_onesweep(
                 excl += v & kCountMask;
                 if (v & kFlagPre) break;
                 if (tt == first) {  // the first tile always publishes a prefix
-                    atomicOr(err, kDevErrBounds);
+                    atomicOr(A.err, kDevErrBounds);
                     break;
                 }
                 --tt;
             }
             st_relaxed(&cur[(uint64_t)t * kRadix + d], kFlagPre | (excl + cnt));
         }
-        const uint32_t goff = digit_off[((uint64_t)s * kPasses + pass) * kRadix + d];
+        const uint32_t goff = A.msd_off[(uint64_t)id * kRadix + d];
         s_gbase[d] = seg_base + (uint64_t)goff + (uint64_t)excl - (uint64_t)s_start[d];
-        nxt[(uint64_t)t * kRadix + d] = 0u;  // ready for the pass after this one
     }
     __syncthreads();
     for (uint32_t j = tid; j < count; j += kOsThreads) {
         const uint64_t k = s_keys[j];
-        const uint32_t d = (uint32_t)(k >> shift) & 255u;
+        const uint32_t d = split_digit(k, shift, dbase, dmult);
         const uint64_t dst = s_gbase[d] + j;
         if (dst - seg_base >= seg_n) {  // never taken when the digit offsets are consistent
-            atomicOr(err, kDevErrBounds);
+            atomicOr(A.err, kDevErrBounds);
             continue;
         }
         kout[dst] = k ^ flip_out;
         if (PAY) pout[dst] = s_pay[j];
     }
-}
-
-// ---------------------------------------------------------------------------
-// Small segments: one CTA, whole segment on chip.
-// ---------------------------------------------------------------------------
-template <bool PAY>
-__global__ __launch_bounds__(kSmThreads, 1) void k_small_sort(
-    const uint64_t* __restrict__ kin, uint64_t* __restrict__ kout,
-    const uint32_t* __restrict__ pin, uint32_t* __restrict__ pout,
-    const uint64_t* __restrict__ seg_off, uint64_t nseg, uint64_t flip_in, uint64_t flip_out) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t* s_keys = (uint64_t*)smem;                                   // kSmallCap u64
-    uint16_t* s_idx0 = (uint16_t*)(s_keys + kSmallCap);                   // kSmallCap u16
-    uint16_t* s_idx1 = s_idx0 + kSmallCap;                                // kSmallCap u16
-    uint32_t* s_hist = (uint32_t*)(s_idx1 + kSmallCap);                   // kSmWarps*256 u32
-    uint32_t* s_total = s_hist + kSmWarps * kRadix;                       // 256
-    uint32_t* s_start = s_total + kRadix;                                 // 256
-    uint32_t* s_warp = s_start + kRadix;                                  // 32
-    uint64_t* s_red = (uint64_t*)(s_warp + 32);                           // 2*32 u64
-
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    for (uint64_t s = blockIdx.x; s < nseg; s += gridDim.x) {
-        const uint64_t base = seg_off[s];
-        const uint32_t n = (uint32_t)(seg_off[s + 1] - base);
-        if (n == 0 || seg_off[s + 1] - base > (uint64_t)kSmallCap) continue;  // uniform per CTA
-        uint64_t vor = 0, vand = ~0ull;
-        for (uint32_t j = tid; j < n; j += kSmThreads) {
-            const uint64_t k = kin[base + j] ^ flip_in;
-            s_keys[j] = k;
-            s_idx0[j] = (uint16_t)j;
-            vor |= k; vand &= k;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            vor |= __shfl_xor_sync(0xffffffffu, vor, o);
-            vand &= __shfl_xor_sync(0xffffffffu, vand, o);
-        }
-        if (lane == 0) { s_red[w] = vor; s_red[32 + w] = vand; }
-        __syncthreads();
-        uint64_t vary = 0;
-        {
-            uint64_t a = 0, b = ~0ull;
-            for (int i = 0; i < kSmWarps; ++i) { a |= s_red[i]; b &= s_red[32 + i]; }
-            vary = a ^ b;  // bits that differ between some two keys
-        }
-        uint16_t* cur = s_idx0;
-        uint16_t* nxt = s_idx1;
-        for (int pass = 0; pass < kPasses; ++pass) {
-            const int shift = 8 * pass;
-            if (((vary >> shift) & 255u) == 0u) continue;  // digit constant: identity pass
-            uint32_t rank[kSmItems], idx[kSmItems];
-            const uint32_t wbase = w * 32 * kSmItems + lane;
-#pragma unroll
-            for (int i = 0; i < kSmItems; ++i) idx[i] = (wbase + i * 32 < n) ? cur[wbase + i * 32] : 0u;
-            auto digit_of = [&](int i) -> uint32_t {
-                return (wbase + i * 32 < n) ? ((uint32_t)(s_keys[idx[i]] >> shift) & 255u) : (uint32_t)kRadix;
-            };
-            block_rank<kSmWarps, kSmItems>(digit_of, rank, s_hist, s_total, s_start, s_warp, NoOp());
-#pragma unroll
-            for (int i = 0; i < kSmItems; ++i)
-                if (wbase + i * 32 < n && rank[i] < n) nxt[rank[i]] = (uint16_t)idx[i];
-            __syncthreads();
-            uint16_t* t = cur; cur = nxt; nxt = t;
-        }
-        for (uint32_t j = tid; j < n; j += kSmThreads) {
-            const uint32_t src = cur[j];
-            kout[base + j] = s_keys[src] ^ flip_out;
-            if (PAY) pout[base + j] = pin[base + src];
-        }
-        __syncthreads();
-    }
-}
-
-static size_t small_sort_smem() {
-    return (size_t)kSmallCap * 8 + 2 * (size_t)kSmallCap * 2 + (size_t)kSmWarps * kRadix * 4 + 2 * kRadix * 4 + 32 * 4 +
-           64 * 8;
 }
 
 __global__ void k_even_offsets(uint64_t* __restrict__ seg_off, uint64_t N, uint64_t p) {
@@ -446,88 +871,192 @@ cudaError_t fill_even_offsets(uint64_t* d_seg_off, uint64_t N, uint64_t p, cudaS
     return cudaGetLastError();
 }
 
-template <bool PAY>
-static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp,
-                             const uint32_t* psrc, uint32_t* pdst, uint32_t* ptmp,
-                             uint64_t N, uint64_t nseg, const uint64_t* d_seg_off,
-                             bool flip_in, bool flip_out, const SegSortWs& ws, cudaStream_t st,
-                             SegSortTiming* timing) {
-    if (N == 0 || nseg == 0) return cudaSuccess;
-    const uint64_t fin = flip_in ? kSignBit : 0ull, fout = flip_out ? kSignBit : 0ull;
-    cudaError_t e;
-    // Small segments: on chip, straight from src to dst.
-    {
-        static bool attr_set[2] = {false, false};
-        const size_t smem = small_sort_smem();
-        if (!attr_set[PAY ? 1 : 0]) {
-            e = cudaFuncSetAttribute(k_small_sort<PAY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            attr_set[PAY ? 1 : 0] = true;
-        }
-        int dev = 0, nsm = 148;
+// ---------------------------------------------------------------------------
+// Host driver.
+// ---------------------------------------------------------------------------
+static int num_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        const uint64_t grid = std::min<uint64_t>(nseg, (uint64_t)nsm * 64);
-        HSS_LAUNCH(k_small_sort<PAY>, (unsigned)grid, kSmThreads, smem, st, src, dst, psrc, pdst, d_seg_off, nseg, fin, fout);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 148;
     }
-    // Large segments: histogram + 8 one-sweep passes.
-    if (N <= (uint64_t)kSmallCap) return cudaSuccess;  // no segment can be large
-    HSS_LAUNCH(k_seg_plan, 1, 1024, 0, st, d_seg_off, nseg, ws.tile_start, ws.counters);
-    if ((e = cudaMemsetAsync(ws.digit_off, 0, nseg * kPasses * kRadix * sizeof(uint32_t), st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(ws.status, 0, ws.max_tiles * kRadix * sizeof(uint32_t), st)) != cudaSuccess) return e;
-    {
-        // enough CTAs for several waves over the device
-        const uint64_t approx_tiles = ceil_div(N, kOsTile);
-        uint64_t split = std::max<uint64_t>(1, std::min<uint64_t>(64, ceil_div(approx_tiles, std::max<uint64_t>(nseg, 1) * 16)));
-        dim3 g((unsigned)nseg, (unsigned)split);
-        HSS_LAUNCH(k_digit_hist, g, 256, 0, st, src, d_seg_off, ws.digit_off, (uint32_t)split, fin);
-        dim3 g2((unsigned)nseg, kPasses);
-        HSS_LAUNCH(k_digit_scan, g2, 256, 0, st, d_seg_off, ws.digit_off);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    const uint64_t grid = ws.max_tiles;  // upper bound; extra CTAs exit at once
-    const size_t os_smem = (size_t)kOsTile * 8 + (PAY ? (size_t)kOsTile * 4 : 0);
-    {
-        static bool os_attr[2] = {false, false};
-        if (!os_attr[PAY ? 1 : 0]) {
-            e = cudaFuncSetAttribute(k_onesweep<PAY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)os_smem);
-            if (e != cudaSuccess) return e;
-            os_attr[PAY ? 1 : 0] = true;
-        }
-    }
-    const bool timed = timing && timing->enabled && timing->n < 8;
-    if (timed) {
-        cudaEventCreate(&timing->ev[timing->n][0]);
-        cudaEventCreate(&timing->ev[timing->n][1]);
-        cudaEventRecord(timing->ev[timing->n][0], st);
-    }
-    for (int pass = 0; pass < kPasses; ++pass) {
-        // pass writes: even -> tmp, odd -> dst; the last (odd) pass lands in dst
-        const uint64_t* in = pass == 0 ? src : ((pass & 1) ? tmp : dst);
-        uint64_t* out = (pass & 1) ? dst : tmp;
-        const uint32_t* pin = PAY ? (pass == 0 ? psrc : ((pass & 1) ? ptmp : pdst)) : nullptr;
-        uint32_t* pout = PAY ? ((pass & 1) ? pdst : ptmp) : nullptr;
-        HSS_LAUNCH(k_onesweep<PAY>, (unsigned)grid, kOsThreads, os_smem, st, in, out, pin, pout, d_seg_off, ws.tile_start, nseg,
-                   ws.digit_off, ws.status, ws.max_tiles, ws.counters, ws.err, pass, pass == 0 ? fin : 0ull,
-                   pass == kPasses - 1 ? fout : 0ull);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    if (timed) {
-        cudaEventRecord(timing->ev[timing->n][1], st);
-        timing->launches[timing->n] = kPasses;
-        timing->n += 1;
-    }
-    return cudaSuccess;
+    return n;
 }
 
-cudaError_t segsort(const uint64_t* src, uint64_t* dst, uint64_t* tmp,
-                    const uint32_t* psrc, uint32_t* pdst, uint32_t* ptmp,
-                    uint64_t N, uint64_t nseg, const uint64_t* d_seg_off,
-                    bool flip_in, bool flip_out, const SegSortWs& ws, cudaStream_t st,
-                    SegSortTiming* timing) {
-    if (psrc) return segsort_t<true>(src, dst, tmp, psrc, pdst, ptmp, N, nseg, d_seg_off, flip_in, flip_out, ws, st, timing);
-    return segsort_t<false>(src, dst, tmp, nullptr, nullptr, nullptr, N, nseg, d_seg_off, flip_in, flip_out, ws, st, timing);
+template <bool PAY, int THREADS, int CAP>
+static cudaError_t launch_small(const uint64_t* in, uint64_t* out, const uint32_t* pin, uint32_t* pout,
+                                const uint64_t* seg_lo, const uint64_t* seg_hi, const uint32_t* list,
+                                const uint32_t* nlist, uint64_t count, uint64_t nseg, uint32_t min_n, uint32_t max_n,
+                                uint64_t fin, uint64_t fout, const SegSortWs& ws, cudaStream_t st) {
+    constexpr size_t smem = msd_sort_smem<CAP>();
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(k_small_msd<PAY, THREADS, CAP>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int per_sm = std::max<int>(1, std::min<int>(2048 / THREADS, (int)(227 * 1024 / smem)));
+    const uint64_t grid = std::min<uint64_t>(count, (uint64_t)num_sms() * per_sm * 4);
+    if (grid == 0) return cudaSuccess;
+    HSS_LAUNCH((k_small_msd<PAY, THREADS, CAP>), (unsigned)grid, THREADS, smem, st, in, out, pin, pout, seg_lo, seg_hi,
+               list, nlist, nseg, min_n, max_n, fin, fout, ws.fb_list, ws.counters + 24);
+    return cudaGetLastError();
+}
+
+// The stable LSD kernel over this level's fallback list (length on the device).
+template <bool PAY>
+static cudaError_t launch_fallback(const uint64_t* in, uint64_t* out, const uint32_t* pin, uint32_t* pout,
+                                   const uint64_t* seg_lo, const uint64_t* seg_hi, uint64_t fin, uint64_t fout,
+                                   const SegSortWs& ws, cudaStream_t st) {
+    constexpr size_t smem = lsd_sort_smem<kC2Threads, kC2Items>();
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(k_small_lsd<PAY, kC2Threads, kC2Items>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    HSS_LAUNCH((k_small_lsd<PAY, kC2Threads, kC2Items>), (unsigned)num_sms(), kC2Threads, smem, st, in, out, pin, pout,
+               seg_lo, seg_hi, ws.fb_list, ws.counters + 24, fin, fout);
+    return cudaGetLastError();
+}
+
+struct Level {
+    const uint64_t* in;
+    const uint32_t* pin;
+    const uint64_t* seg_lo;
+    const uint64_t* seg_hi;
+    uint64_t nseg;
+    uint64_t flip_in;
+    const uint64_t* hint_lo;
+    const uint64_t* hint_mult;
+    int depth;
+};
+
+template <bool PAY>
+static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, const uint32_t* psrc, uint32_t* pdst,
+                             uint32_t* ptmp, uint64_t N, uint64_t nseg, const uint64_t* d_seg_off, bool flip_in,
+                             bool flip_out, const SegSortWs& ws, cudaStream_t st, SegSortTiming* timing,
+                             const uint64_t* hint_lo, const uint64_t* hint_mult) {
+    if (N == 0 || nseg == 0) return cudaSuccess;
+    const uint64_t fout = flip_out ? kSignBit : 0ull;
+    cudaError_t e;
+    Level L{src, psrc, d_seg_off, d_seg_off + 1, nseg, flip_in ? kSignBit : 0ull, hint_lo, hint_mult, 0};
+    if (N <= (uint64_t)kSmallCap) {
+        // No segment can exceed the on-chip capacity: sort every segment in
+        // its class without planning (and without a host round trip).
+        if ((e = cudaMemsetAsync(ws.counters + 24, 0, 4, st)) != cudaSuccess) return e;
+        if ((e = launch_small<PAY, kC0Threads, kC0Cap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi, nullptr, nullptr, nseg,
+                                                       nseg, 0u, (uint32_t)kC0Cap, L.flip_in, fout, ws, st)) !=
+            cudaSuccess)
+            return e;
+        if (N > (uint64_t)kC0Cap &&
+            (e = launch_small<PAY, kC1Threads, kC1Cap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi, nullptr, nullptr,
+                                                       nseg, nseg, (uint32_t)kC0Cap, (uint32_t)kC1Cap, L.flip_in, fout,
+                                                       ws, st)) != cudaSuccess)
+            return e;
+        if (N > (uint64_t)kC1Cap &&
+            (e = launch_small<PAY, kC2Threads, kSmallCap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi, nullptr, nullptr,
+                                                          nseg, nseg, (uint32_t)kC1Cap, (uint32_t)kSmallCap, L.flip_in,
+                                                          fout, ws, st)) != cudaSuccess)
+            return e;
+        return launch_fallback<PAY>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi, L.flip_in, fout, ws, st);
+    }
+    for (;;) {
+        if (L.nseg > ws.max_list) return cudaErrorInvalidValue;
+        const uint32_t nblk = (uint32_t)ceil_div(L.nseg + 1, 1024);
+        HSS_LAUNCH(k_plan_count, nblk, 1024, 0, st, L.seg_lo, L.seg_hi, L.nseg, ws.blk);
+        HSS_LAUNCH(k_plan_scan, 1, 1024, 0, st, nblk, ws.blk, ws.counters);
+        HSS_LAUNCH(k_plan_write, nblk, 1024, 0, st, L.seg_lo, L.seg_hi, L.nseg, ws.blk, ws.counters, ws.tile_start,
+                   ws.large_id, ws.large_seg, ws.list[0], ws.list[1], ws.list[2]);
+        uint32_t hc[8];
+        if ((e = cudaMemcpyAsync(hc, ws.counters + 16, sizeof(hc), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+        const uint32_t n_large = hc[3], tiles = hc[4];
+        const uint64_t keys_large = (uint64_t)hc[6] | ((uint64_t)hc[7] << 32);
+        // Segments of this level that fit on chip: straight to the output.
+        if (hc[0] && (e = launch_small<PAY, kC0Threads, kC0Cap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi, ws.list[0],
+                                                                ws.counters + 16, hc[0], L.nseg, 0u, (uint32_t)kC0Cap,
+                                                                L.flip_in, fout, ws, st)) != cudaSuccess)
+            return e;
+        if (hc[1] && (e = launch_small<PAY, kC1Threads, kC1Cap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi, ws.list[1],
+                                                                ws.counters + 17, hc[1], L.nseg, (uint32_t)kC0Cap,
+                                                                (uint32_t)kC1Cap, L.flip_in, fout, ws, st)) != cudaSuccess)
+            return e;
+        if (hc[2] && (e = launch_small<PAY, kC2Threads, kSmallCap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi,
+                                                                   ws.list[2], ws.counters + 18, hc[2], L.nseg,
+                                                                   (uint32_t)kC1Cap, (uint32_t)kSmallCap, L.flip_in, fout,
+                                                                   ws, st)) != cudaSuccess)
+            return e;
+        if ((hc[0] || hc[1] || hc[2]) &&
+            (e = launch_fallback<PAY>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi, L.flip_in, fout, ws, st)) != cudaSuccess)
+            return e;
+        if (n_large == 0) return cudaSuccess;
+        if (n_large > ws.max_large || tiles > ws.max_tiles || L.depth >= kMaxDepth) return cudaErrorInvalidValue;
+        // Statistics and the split window.
+        if ((e = cudaMemsetAsync(ws.hist, 0, (size_t)n_large * 8 * kRadix * 4, st)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(ws.vor, 0, (size_t)n_large * 8, st)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(ws.vand, 0xff, (size_t)n_large * 8, st)) != cudaSuccess) return e;
+        const uint64_t avg_tiles = ceil_div(tiles, n_large);
+        const uint32_t split = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(256, ceil_div(2 * avg_tiles, 16)));
+        HSS_LAUNCH(k_seg_stats, dim3(n_large, split), 256, 0, st, L.in, L.seg_lo, L.seg_hi, ws.large_seg, ws.counters,
+                   ws.hist, ws.vor, ws.vand, L.hint_lo, L.hint_mult, split, L.flip_in);
+        const int buf = L.depth & 1;
+        HSS_LAUNCH(k_msd_prep, n_large, 256, 0, st, L.seg_lo, ws.large_seg, ws.counters, ws.hist, ws.vor, ws.vand,
+                   L.hint_lo, L.hint_mult, ws.msd_base, ws.msd_mult, ws.msd_off, ws.msd_shift, ws.direct, ws.sub_lo[buf],
+                   ws.sub_hi[buf]);
+        if ((e = cudaMemsetAsync(ws.status, 0, (size_t)tiles * kRadix * 4, st)) != cudaSuccess) return e;
+        // The split pass: level buffers alternate tmp, dst, tmp, ... after src.
+        uint64_t* next = (L.depth & 1) ? dst : tmp;
+        uint32_t* pnext = PAY ? ((L.depth & 1) ? pdst : ptmp) : nullptr;
+        SplitArgs A;
+        A.kin = L.in; A.kout = next; A.kfinal = dst;
+        A.pin = L.pin; A.pout = pnext; A.pfinal = pdst;
+        A.seg_lo = L.seg_lo; A.seg_hi = L.seg_hi; A.nseg = L.nseg;
+        A.tile_start = ws.tile_start; A.large_id = ws.large_id;
+        A.msd_off = ws.msd_off; A.msd_shift = ws.msd_shift; A.msd_base = ws.msd_base; A.msd_mult = ws.msd_mult;
+        A.direct = ws.direct;
+        A.status = ws.status; A.counter = ws.counters; A.err = ws.err;
+        A.flip_in = L.flip_in; A.flip_out = fout;
+        const size_t smem = (size_t)kOsTile * 8 + (PAY ? (size_t)kOsTile * 4 : 0);
+        static bool attr = false;
+        if (!attr) {
+            if ((e = cudaFuncSetAttribute(k_split<PAY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+                cudaSuccess)
+                return e;
+            attr = true;
+        }
+        const bool timed = timing && timing->enabled && timing->n < 16;
+        if (timed) {
+            cudaEventCreate(&timing->ev[timing->n][0]);
+            cudaEventCreate(&timing->ev[timing->n][1]);
+            cudaEventRecord(timing->ev[timing->n][0], st);
+        }
+        HSS_LAUNCH(k_split<PAY>, tiles, kOsThreads, smem, st, A);
+        if (timed) {
+            cudaEventRecord(timing->ev[timing->n][1], st);
+            timing->keys[timing->n] = keys_large;
+            timing->n += 1;
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        // Next level: the 256 sub-buckets of every large segment.
+        L = Level{next, pnext, ws.sub_lo[buf], ws.sub_hi[buf], (uint64_t)n_large * kRadix, 0ull, nullptr, nullptr,
+                  L.depth + 1};
+    }
+}
+
+cudaError_t segsort(const uint64_t* src, uint64_t* dst, uint64_t* tmp, const uint32_t* psrc, uint32_t* pdst,
+                    uint32_t* ptmp, uint64_t N, uint64_t nseg, const uint64_t* d_seg_off, bool flip_in, bool flip_out,
+                    const SegSortWs& ws, cudaStream_t st, SegSortTiming* timing, const uint64_t* hint_lo,
+                    const uint64_t* hint_mult) {
+    if (psrc)
+        return segsort_t<true>(src, dst, tmp, psrc, pdst, ptmp, N, nseg, d_seg_off, flip_in, flip_out, ws, st, timing,
+                               hint_lo, hint_mult);
+    return segsort_t<false>(src, dst, tmp, nullptr, nullptr, nullptr, N, nseg, d_seg_off, flip_in, flip_out, ws, st,
+                            timing, hint_lo, hint_mult);
 }
 
 }  // namespace hss

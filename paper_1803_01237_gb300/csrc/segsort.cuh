@@ -1,10 +1,12 @@
-// segsort.cuh -- stable segmented LSD radix sort of 64-bit keys (+ u32 payload).
+// segsort.cuh -- stable segmented radix sort of 64-bit keys (+ u32 payload).
 //
 // Segments are given by a device array seg_off[nseg+1] of u64 offsets.  A
-// segment that fits in shared memory (<= kSmallCap keys) is sorted by one CTA
-// entirely on chip; larger segments go through eight 8-bit digit passes of a
-// one-sweep radix sort whose tiles chain their digit prefixes per segment by
-// decoupled look-back.
+// segment of at most kSmallCap keys is sorted by one CTA entirely on chip.  A
+// larger segment is split by one most-significant-digit pass (a one-sweep
+// scatter with decoupled look-back over the segment's tiles) on its top
+// varying 8-bit window into 256 sub-buckets, which are sorted the same way,
+// recursively; a segment whose keys are all equal is copied straight to the
+// output.
 #pragma once
 
 #include "hss_internal.cuh"
@@ -13,25 +15,45 @@ namespace hss {
 
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 256;
-constexpr int kPasses = 8;
+constexpr int kMaxDepth = 8;
 
 constexpr int kOsThreads = 256;
 constexpr int kOsWarps = kOsThreads / 32;
 constexpr int kOsItems = 16;
-constexpr int kOsTile = kOsThreads * kOsItems;  // 4096 keys per tile
+constexpr int kOsTile = kOsThreads * kOsItems;  // 4096 keys per one-sweep tile
 
-constexpr int kSmThreads = 512;
-constexpr int kSmWarps = kSmThreads / 32;
-constexpr int kSmItems = 32;
-constexpr int kSmallCap = kSmThreads * kSmItems;  // 16384 keys per on-chip segment
+// On-chip sort: three CTA shapes by segment size (threads x items per thread).
+constexpr int kC0Threads = 128, kC0Items = 12;  // up to 1536 keys
+constexpr int kC1Threads = 256, kC1Items = 16;  // up to 4096 keys
+constexpr int kC2Threads = 512, kC2Items = 28;  // up to 14336 keys
+constexpr int kC0Cap = kC0Threads * kC0Items;
+constexpr int kC1Cap = kC1Threads * kC1Items;
+constexpr int kSmallCap = kC2Threads * kC2Items;
+constexpr int kTinyGroup = 64;  // on chip: rank inside the groups of one MSD pass when none is larger
 
 struct SegSortWs {
-    uint32_t* digit_off;   // [nseg][8][256] digit counts, then exclusive offsets
-    uint32_t* tile_start;  // [nseg + 1] first tile of each large segment
-    uint32_t* status;      // [2][max_tiles][256] look-back words
-    uint32_t* counters;    // [kPasses] dynamic tile counters
-    uint32_t* err;         // device error word (kDevErr*)
+    uint64_t max_large;    // bound on segments larger than kSmallCap at any depth
+    uint64_t max_list;     // bound on the length of any segment list
     uint64_t max_tiles;
+    uint32_t* tile_start;  // [max_list + 1]
+    uint32_t* large_id;    // [max_list]
+    uint32_t* large_seg;   // [max_large]
+    uint32_t* hist;        // [max_large][8][256] digit counts
+    unsigned long long* vor;   // [max_large] OR of the keys
+    unsigned long long* vand;  // [max_large] AND of the keys
+    uint32_t* msd_off;     // [max_large][256] exclusive offsets of the MSD digit
+    uint32_t* msd_shift;   // [max_large]
+    uint64_t* msd_base;    // [max_large] digit = ((key >> shift) - base) & 255, or
+    uint64_t* msd_mult;    // [max_large] when mult != 0: digit = mulhi(key - base, mult)
+    uint32_t* direct;      // [max_large] all keys equal: copy to the output
+    uint64_t* sub_lo[2];   // [max_large * 256] sub-bucket bounds, double-buffered by depth
+    uint64_t* sub_hi[2];
+    uint32_t* status;      // [2][max_tiles][256] look-back words
+    uint32_t* counters;    // [64]
+    uint32_t* list[3];     // [max_list] segments of each on-chip size class
+    uint32_t* fb_list;     // [max_list] segments left to the stable LSD kernel (count in counters[24])
+    uint32_t* blk;         // [8 * (max_list / 1024 + 2)] per-chunk counts of the planning scan
+    uint32_t* err;         // device error word (kDevErr*)
 };
 
 // Bytes of scratch a segmented sort of N keys in nseg segments needs.
@@ -41,38 +63,44 @@ SegSortWs segsort_ws_carve(void* base, uint64_t N, uint64_t nseg, uint32_t* err)
 
 struct SegSortTiming {
     bool enabled = false;
-    int n = 0;                      // recorded (start, end) pairs around digit-pass groups
-    cudaEvent_t ev[8][2] = {};
-    uint32_t launches[8] = {};
+    int n = 0;                      // recorded (start, end) pairs around MSD passes
+    cudaEvent_t ev[16][2] = {};
+    uint64_t keys[16] = {};         // keys moved by each recorded pass
     // Sum the recorded pass times (call after the stream has passed the last
     // recorded event) and release the events.
-    void collect(float* ms_total, uint32_t* n_launches) {
+    void collect(float* ms_total, uint32_t* n_launches, uint64_t* n_keys) {
         float tot = 0.f;
-        uint32_t nl = 0;
+        uint64_t nk = 0;
         for (int i = 0; i < n; ++i) {
             float ms = 0.f;
             cudaEventSynchronize(ev[i][1]);
             cudaEventElapsedTime(&ms, ev[i][0], ev[i][1]);
             tot += ms;
-            nl += launches[i];
+            nk += keys[i];
             cudaEventDestroy(ev[i][0]);
             cudaEventDestroy(ev[i][1]);
         }
-        n = 0;
         if (ms_total) *ms_total = tot;
-        if (n_launches) *n_launches = nl;
+        if (n_launches) *n_launches = (uint32_t)n;
+        if (n_keys) *n_keys = nk;
+        n = 0;
     }
 };
 
 // Stable sort of every segment [seg_off[s], seg_off[s+1]) of src into dst.
 // tmp (and ptmp) must not alias src/dst; dst may alias src.  flip_in XORs the
 // sign bit into keys as they are read (signed keys), flip_out as they are
-// written.  psrc/pdst/ptmp are all null or all non-null.
+// written.  psrc/pdst/ptmp are all null or all non-null.  hint_lo and
+// hint_mult (both null or both per segment) promise that every key k of
+// segment s satisfies hint_lo[s] <= k and mulhi(k - hint_lo[s], hint_mult[s])
+// <= 255; the first split of s then uses that value, which is monotone in k,
+// as its digit (an interpolation of the key range over 256 sub-buckets).
 cudaError_t segsort(const uint64_t* src, uint64_t* dst, uint64_t* tmp,
                     const uint32_t* psrc, uint32_t* pdst, uint32_t* ptmp,
                     uint64_t N, uint64_t nseg, const uint64_t* d_seg_off,
                     bool flip_in, bool flip_out, const SegSortWs& ws, cudaStream_t st,
-                    SegSortTiming* timing);
+                    SegSortTiming* timing, const uint64_t* hint_lo = nullptr,
+                    const uint64_t* hint_mult = nullptr);
 
 // seg_off[s] = floor(s * N / p) for s = 0..p.
 cudaError_t fill_even_offsets(uint64_t* d_seg_off, uint64_t N, uint64_t p, cudaStream_t st);

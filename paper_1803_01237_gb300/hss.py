@@ -177,6 +177,7 @@ class Result:
     ms_phase: dict = field(default_factory=dict)
     ms_radix_pass_total: float = 0.0
     radix_pass_launches: int = 0
+    radix_pass_keys: int = 0
     kernel_launches: int = 0
 
     def splitter_tags(self):
@@ -190,6 +191,7 @@ def _result(keys, pay, spl, off, st: Stats) -> Result:
                   unresolved=[int(x) for x in st.unresolved[:R + 1]],
                   ms_phase={PHASES[i]: float(st.ms_phase[i]) for i in range(NUM_PHASES)},
                   ms_radix_pass_total=float(st.ms_radix_pass_total), radix_pass_launches=int(st.radix_pass_launches),
+                  radix_pass_keys=int(st.radix_pass_keys),
                   kernel_launches=int(st.kernel_launches))
 
 

@@ -369,7 +369,7 @@ def test_round_with_q_one_resolves_everything():
 
 def test_sample_sizes_chernoff():
     """Z_j ~ Binomial(|gamma_{j-1}|, q_j); each round stays inside a 6-sigma
-    band around its mean s*p (Lemma 4.5 style Chernoff bound)."""
+    band around its mean s*p (the Chernoff argument of Lemma 4.6)."""
     N, p = 1 << 14, 32
     for seed in range(10):
         res = oracle.hss(inputs.uniform(N, seed), p, 0.02, seed=seed, sort=False)
@@ -398,12 +398,12 @@ def test_gamma_shrinks_like_lemma_4_4():
             ratios.append(g_next / (2.0 * N / s_eff))
     assert len(ratios) > 20
     assert float(np.mean(ratios)) <= 1.05
-    # the w.h.p. bound |gamma_j| <= 4N/s_j (Lemma 4.3) holds in every case
+    # the w.h.p. bound |gamma_j| <= 4N/s_j (Lemma 4.5) holds in every case
     assert max(ratios) <= 2.0
 
 
 def test_rounds_logarithmic():
-    """Rounds grow like log(log p / eps) (Thm 4.7); at s = 5 the interval
+    """Rounds grow like log(log p / eps) (Theorem 4.8); at s = 5 the interval
     union shrinks ~s/2 per round, so rounds stay within a small window of
     ln(ln p/(s eps))/ln(s/2) + 1."""
     for p, eps in [(16, 0.05), (64, 0.02), (256, 0.02)]:
