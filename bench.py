@@ -31,7 +31,9 @@ if ROOT not in sys.path:
 
 METRIC = "keys/s and % of HBM roofline (1 GB300) for HSS sort at eps; HSS rounds; batched jobs/s; p99"
 LOG2N, P, EPS, SEED, OVERSAMPLE = 28, 1024, 0.02, 1, 5.0
-WORKLOAD = "HSS sort: N=2^28 uint64 keys uniform over [0,2^64) (seed 1), p=1024 segments of 2^18, eps=0.02, s=5"
+WORKLOAD = ("HSS sort: N=2^28 uint64 keys, p=1024 segments of 2^18, eps=0.02, s=5; steps cycle over three seeded "
+            "inputs: uniform [0,2^64) (seed 1), 32-Gaussian mixture sigma=2^40 (seed 2), Zipf s=1.2 over 2^12 values (seed 3)")
+DISTS = (("uniform", 1), ("gauss_mix", 2), ("zipf", 3))
 CPU_SAMPLE_LOG2N = 24      # cpu_baseline: first 2^24 keys, same p and eps
 REF_SAMPLE_LOG2N = 22      # reference arm: first 2^22 keys per step
 
@@ -185,7 +187,12 @@ def run_gpu(args):
 
     N = 1 << LOG2N
     keys_h = inputs.uniform(N, SEED)
-    keys = torch.from_numpy(keys_h.view(np.int64)).to(dev)
+    dists = DISTS if LOG2N == 28 and not args.uniform_only else (("uniform", SEED),)
+    dev_inputs = []
+    for name, sd in dists:
+        kh = keys_h if name == "uniform" else inputs.SCALE_DISTRIBUTIONS[name](N, sd)
+        dev_inputs.append((name, torch.from_numpy(kh.view(np.int64)).to(dev)))
+    keys = dev_inputs[0][1]
     out = torch.empty_like(keys)
 
     def barrier():
@@ -193,11 +200,11 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def step(flags=0):
-        return hss.sort(keys, P, EPS, SEED, oversample=OVERSAMPLE, flags=flags, out=out)
+    def step(k, flags=0):
+        return hss.sort(dev_inputs[k % len(dev_inputs)][1], P, EPS, SEED, oversample=OVERSAMPLE, flags=flags, out=out)
 
-    for _ in range(args.warmup):
-        step()
+    for w in range(max(args.warmup, len(dev_inputs))):
+        step(w)
     barrier()
 
     clocks = ClockSampler(local)
@@ -206,16 +213,21 @@ def run_gpu(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = hss.launch_count()
     pass_ms, pass_launches, pass_keys, phase = 0.0, 0, 0, {}
+    per_dist = {name: {"ms": 0.0, "steps": 0, "rounds": []} for name, _ in dev_inputs}
     rounds = None
     barrier()
     ev0.record(stream)
-    for _ in range(args.steps):
-        r = step(flags=hss.FLAG_TIMING)
+    for k in range(args.steps):
+        r = step(k, flags=hss.FLAG_TIMING)
         pass_ms += r.ms_radix_pass_total
         pass_launches += r.radix_pass_launches
         pass_keys += r.radix_pass_keys
-        for k, v in r.ms_phase.items():
-            phase[k] = phase.get(k, 0.0) + v
+        for kk, v in r.ms_phase.items():
+            phase[kk] = phase.get(kk, 0.0) + v
+        pd = per_dist[dev_inputs[k % len(dev_inputs)][0]]
+        pd["ms"] += sum(r.ms_phase.values())
+        pd["steps"] += 1
+        pd["rounds"].append(r.rounds)
         rounds = r
     ev1.record(stream)
     barrier()
@@ -227,6 +239,9 @@ def run_gpu(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = world * N / (ms / 1000.0)
+    dist_report = {name: {"device_ms_per_step": v["ms"] / max(v["steps"], 1),
+                          "keys_per_s_device": N / (v["ms"] / max(v["steps"], 1) / 1000.0) if v["steps"] else None,
+                          "rounds": sorted(set(v["rounds"]))} for name, v in per_dist.items()}
 
     # correctness spot check of the last output (sorted, offsets in range)
     o = out[:: max(1, N // (1 << 20))].cpu().numpy().view(np.uint64)
@@ -260,7 +275,7 @@ def run_gpu(args):
             e2e_s = float(t.item())
         e2e = {"value": world * N / e2e_s, "unit": "keys/s", "h2d_bytes_per_step": 8 * N,
                "d2h_bytes_per_step": 8 * N + 16 * (P - 1) + 8 * (P + 1), "ms_per_step": 1000 * e2e_s,
-               "api": "hss_sort_host (pinned host buffers, copies inside the call)"}
+               "api": "hss_sort_host (pinned host buffers, copies inside the call)", "input": "uniform"}
         del hk, ho
 
     if rank != 0:
@@ -274,13 +289,15 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N, "p": P, "eps": EPS, "oversample": OVERSAMPLE,
-                   "distribution": "uniform", "l2": "inputs (2 GiB keys) larger than L2; no flush between steps",
+                   "distributions": [n for n, _ in dev_inputs],
+                   "l2": "inputs (2 GiB keys per distribution) larger than L2; no flush between steps",
                    "parallelism": "replicas only" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "kernel": "k_split (one-sweep MSD scatter, 16 B/key)",
                      "bytes_per_launch": bytes_per_pass,
                      "peak_source": f"{peak_kind} hbm_gbs", "avg_launch_ms": avg_pass_ms,
                      "launches": pass_launches},
+        "per_distribution": dist_report,
         "hss": {"rounds": rounds.rounds, "sample_size": rounds.sample_size, "gamma": rounds.gamma,
                 "tol": rounds.tol, "phase_ms": {k: v / args.steps for k, v in phase.items()},
                 "kernels_per_step": rounds.kernel_launches, "output_sorted": sorted_ok},
@@ -305,6 +322,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--uniform-only", action="store_true", help="time the uniform input only")
     ap.add_argument("--log2n", type=int, default=None,
                     help="smaller case of the same kernels (keeps 2^18 keys per segment); for profiling only")
     args = ap.parse_args()

@@ -191,7 +191,7 @@ static int run_path(const void* d_keys, const uint32_t* d_payload, int key_type,
             // Merge (Sec. 6 local merging): stable sort of each bucket's runs.
             // The keys of bucket b lie between splitters b and b+1, so the first
             // split of each bucket spreads that key range over 256 sub-buckets.
-            if (bucket_hints(rws, p, st) != cudaSuccess) return HSS_ERR_CUDA;
+            if (bucket_hints(rws, keysA, seg_off, p, st) != cudaSuccess) return HSS_ERR_CUDA;
             if (segsort(keysB, (uint64_t*)d_keys_out, keysA, payB, d_payload_out, payA, N, p, d_offsets, false, i64, sws,
                         st, &stime, rws.bucket_lo, rws.bucket_mult) != cudaSuccess)
                 return HSS_ERR_CUDA;

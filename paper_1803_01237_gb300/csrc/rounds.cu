@@ -53,6 +53,7 @@ size_t rounds_ws_bytes(uint64_t N, uint64_t p, uint64_t cap) {
     b += aup(p * cap * sizeof(uint32_t));      // probe_pos
     b += aup(S1 * sizeof(uint64_t)) + aup(S1 * sizeof(uint32_t));  // fin_okey, fin_kind
     b += 2 * aup(p * sizeof(uint64_t));                             // bucket_lo, bucket_mult
+    b += aup(2 * sizeof(uint64_t));                                 // key_range
     b += segsort_ws_bytes(cap, 1);
     return b;
 }
@@ -95,6 +96,7 @@ RoundWs rounds_ws_carve(void* base, uint64_t N, uint64_t p, uint64_t cap, uint32
     w.fin_kind = (uint32_t*)take(S1 * sizeof(uint32_t));
     w.bucket_lo = (uint64_t*)take(p * sizeof(uint64_t));
     w.bucket_mult = (uint64_t*)take(p * sizeof(uint64_t));
+    w.key_range = (uint64_t*)take(2 * sizeof(uint64_t));
     w.sws = segsort_ws_carve(q, cap, 1, err);
     w.cap = cap;
     return w;
@@ -549,8 +551,40 @@ __global__ void k_finalize(uint32_t S, uint64_t N, uint32_t p, int key_type, con
 // key range).  Its first split interpolates that range onto 256 sub-buckets:
 // digit = mulhi(key - lo, floor(255 * 2^64 / (hi - lo))), monotone in the key
 // and at most 255; a range narrower than 256 uses key - lo itself.
+// Smallest and largest key of the whole input: the first and the last key of
+// the locally sorted segments.  One block.
+__global__ void __launch_bounds__(1024) k_key_range(const uint64_t* __restrict__ skeys,
+                                                    const uint64_t* __restrict__ seg_off, uint32_t p,
+                                                    uint64_t* __restrict__ range) {
+    __shared__ uint64_t s_lo[32], s_hi[32];
+    uint64_t lo = ~0ull, hi = 0ull;
+    for (uint32_t s = threadIdx.x; s < p; s += blockDim.x) {
+        const uint64_t a = seg_off[s], b = seg_off[s + 1];
+        if (a < b) {
+            lo = min(lo, skeys[a]);
+            hi = max(hi, skeys[b - 1]);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0) { s_lo[w] = lo; s_hi[w] = hi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < nw; ++i) { lo = min(lo, s_lo[i]); hi = max(hi, s_hi[i]); }
+        range[0] = lo;
+        range[1] = hi;
+    }
+}
+
+// Interpolation hint of each bucket for the first digit split of the merge:
+// the bucket's keys lie between splitters b and b+1, clipped to the input's
+// key range, and mulhi(key - lo, mult) maps that interval onto 0..255.
 __global__ void k_bucket_hint(uint32_t p, const uint64_t* __restrict__ fin_okey, const uint32_t* __restrict__ fin_kind,
-                              uint64_t* __restrict__ lo_out, uint64_t* __restrict__ mult_out) {
+                              const uint64_t* __restrict__ range, uint64_t* __restrict__ lo_out,
+                              uint64_t* __restrict__ mult_out) {
     const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= p) return;
     auto bound = [&](uint32_t i, uint64_t if_none) -> uint64_t {  // splitter number i (1..p-1)
@@ -560,8 +594,9 @@ __global__ void k_bucket_hint(uint32_t p, const uint64_t* __restrict__ fin_okey,
         if (k == (uint32_t)kPosInf) return ~0ull;
         return fin_okey[i - 1];
     };
-    const uint64_t lo = bound(b, 0ull);
-    uint64_t hi = bound(b + 1, ~0ull);
+    const uint64_t kmin = range[0], kmax = range[1];
+    const uint64_t lo = max(bound(b, 0ull), kmin);
+    uint64_t hi = min(bound(b + 1, ~0ull), kmax);
     if (hi < lo) hi = lo;  // empty bucket
     const uint64_t r = hi - lo;
     // mult = 0 selects the plain form ((key >> 0) - lo) & 255 = key - lo
@@ -570,9 +605,11 @@ __global__ void k_bucket_hint(uint32_t p, const uint64_t* __restrict__ fin_okey,
     mult_out[b] = mult;
 }
 
-cudaError_t bucket_hints(const RoundWs& ws, uint32_t p, cudaStream_t st) {
-    HSS_LAUNCH(k_bucket_hint, (unsigned)cdiv(p, 256), 256, 0, st, p, ws.fin_okey, ws.fin_kind, ws.bucket_lo,
-               ws.bucket_mult);
+cudaError_t bucket_hints(const RoundWs& ws, const uint64_t* skeys, const uint64_t* d_seg_off, uint32_t p,
+                         cudaStream_t st) {
+    HSS_LAUNCH(k_key_range, 1, 1024, 0, st, skeys, d_seg_off, p, ws.key_range);
+    HSS_LAUNCH(k_bucket_hint, (unsigned)cdiv(p, 256), 256, 0, st, p, ws.fin_okey, ws.fin_kind, ws.key_range,
+               ws.bucket_lo, ws.bucket_mult);
     return cudaGetLastError();
 }
 

@@ -52,6 +52,7 @@ struct RoundWs {
     uint64_t* fin_okey;  // [S] order-preserving key of each final splitter
     uint32_t* fin_kind;  // [S]
     uint64_t* bucket_lo;    // [p] lower key bound of each bucket (its first split digit is
+    uint64_t* key_range;    // [2] smallest and largest key of the input
     uint64_t* bucket_mult;  // [p] mulhi(key - lo, mult), an interpolation of [lo, hi] onto 0..255)
     SegSortWs sws;       // scratch of the probe sort
     uint64_t cap;        // sample capacity
@@ -77,7 +78,8 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
                const RoundWs& ws, cudaStream_t st, RoundResult* out);
 
 // Per-bucket split windows for the merge, from the final splitters.
-cudaError_t bucket_hints(const RoundWs& ws, uint32_t p, cudaStream_t st);
+cudaError_t bucket_hints(const RoundWs& ws, const uint64_t* skeys, const uint64_t* d_seg_off, uint32_t p,
+                         cudaStream_t st);
 
 // Exchange: per-(segment, bucket) destinations, then the run copy.
 cudaError_t exchange(const uint64_t* skeys, const uint32_t* spay, uint64_t N, uint32_t p, const uint64_t* d_seg_off,

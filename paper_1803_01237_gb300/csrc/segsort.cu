@@ -222,15 +222,19 @@ __device__ __forceinline__ void block_rank(DigitOf digit_of, uint32_t count, uin
 // On-chip sort of segments with min_n < n <= max_n keys (n <= CAP), taken
 // from `list` (compact ids, count at *nlist) or, when list is null, from all
 // nseg segments.  The keys are read once into shared memory.  One counting
-// pass on the top varying 8-bit window splits them into 256 groups that come
-// in key order (the keys agree on every bit above the window); inside a group
-// the atomics leave an arbitrary order, and each key's final slot is its
-// group's start plus the number of keys of the group below it in
-// (key, input position) order -- a total order, so the result is the stable
-// sort.  A segment with a group larger than kTinyGroup is left to the stable
-// LSD kernel below (appended to the fallback list).
+// pass on a 10-bit digit (the segment's key range interpolated onto 1024
+// groups) splits them into groups that come in key order; inside a group the
+// atomics leave an arbitrary order, and each key's final slot is its group's
+// start plus the number of keys of the group below it in (key, input
+// position) order -- a total order, so the result is the stable sort.
+// Groups larger than kTinyGroup are not ranked that way: when every such
+// group holds one key value (heavy duplicates), its members only need input
+// order, which two ordered warp passes over the positions give; a segment
+// with a larger group of distinct keys is left to the stable LSD kernel below
+// (appended to the fallback list).
 // ---------------------------------------------------------------------------
 constexpr int kChipRadix = 1024;  // groups of the on-chip counting pass
+constexpr int kMaxBig = 64;       // groups above kTinyGroup keys that one segment may hold
 
 // Exclusive scan of NV shared values in place by a CTA of T threads.
 template <int T, int NV>
@@ -257,16 +261,47 @@ __device__ __forceinline__ void scan_smem_inplace(uint32_t* v, uint32_t* s_warp)
     __syncthreads();
 }
 
-template <int CAP>
+// Write a sorted segment: keys from shared memory in the order `order`, and
+// the payload gathered from the segment's input payload.  The output may be
+// the input itself (every second level of the recursion sorts its small
+// buckets in place), so every payload value is gathered into registers before
+// the barrier and stored after it, and the on-chip kernels take their key and
+// payload buffers without __restrict__: with it the compiler may move the
+// gathers past the stores.
+template <bool PAY, int THREADS, int CAP>
+__device__ __forceinline__ void write_sorted(uint64_t* kout, uint32_t* pout, const uint32_t* pin, uint64_t base,
+                                             uint32_t n, const uint64_t* s_keys, const uint16_t* order, uint64_t flip_out) {
+    const int tid = threadIdx.x;
+    if (PAY) {
+        constexpr int PER = (CAP + THREADS - 1) / THREADS;
+        uint32_t pv[PER];
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const uint32_t j = tid + i * THREADS;
+            pv[i] = j < n ? pin[base + order[j]] : 0u;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const uint32_t j = tid + i * THREADS;
+            if (j < n) pout[base + j] = pv[i];
+        }
+    }
+    for (uint32_t j = tid; j < n; j += THREADS) kout[base + j] = s_keys[order[j]] ^ flip_out;
+    __syncthreads();
+}
+
+template <int THREADS, int CAP>
 constexpr size_t msd_sort_smem() {
-    return (size_t)CAP * 8 + 3 * (size_t)CAP * 2 + 2 * (kChipRadix + 1) * 4 + 32 * 4 + 2 * 32 * 8 + 64;
+    return (size_t)CAP * 8 + 3 * (size_t)CAP * 2 + 2 * (kChipRadix + 1) * 4 + 32 * 4 + 2 * 32 * 8 +
+           (size_t)(THREADS / 32) * kMaxBig * 4 + kChipRadix + 64;
 }
 
 template <bool PAY, int THREADS, int CAP>
 __global__ __launch_bounds__(THREADS) void k_small_msd(
-    const uint64_t* __restrict__ kin, uint64_t* __restrict__ kout, const uint32_t* __restrict__ pin,
-    uint32_t* __restrict__ pout, const uint64_t* __restrict__ seg_lo, const uint64_t* __restrict__ seg_hi,
-    const uint32_t* __restrict__ list, const uint32_t* __restrict__ nlist, uint64_t nseg, uint32_t min_n,
+    const uint64_t* kin, uint64_t* kout, const uint32_t* pin, uint32_t* pout, const uint64_t* __restrict__ seg_lo,
+    const uint64_t* __restrict__ seg_hi, const uint32_t* __restrict__ list, const uint32_t* __restrict__ nlist,
+    uint64_t nseg, uint32_t min_n,
     uint32_t max_n, uint64_t flip_in, uint64_t flip_out, uint32_t* __restrict__ fb_list, uint32_t* __restrict__ fb_count) {
     constexpr int WARPS = THREADS / 32;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -278,6 +313,9 @@ __global__ __launch_bounds__(THREADS) void k_small_msd(
     uint32_t* s_run = s_start + (kChipRadix + 1);              // kChipRadix+1: running write positions
     uint32_t* s_warp = s_run + (kChipRadix + 1);               // 32
     uint64_t* s_red = (uint64_t*)(((uintptr_t)(s_warp + 32) + 7) & ~(uintptr_t)7);  // 2*32
+    uint32_t* s_wcnt = (uint32_t*)(s_red + 64);                 // WARPS*kMaxBig: per-warp counts of the big groups
+    uint32_t* s_misc = s_wcnt + WARPS * kMaxBig;                // [0] big groups, [1] a big group holds distinct keys
+    uint8_t* s_bigid = (uint8_t*)(s_misc + 2);                  // kChipRadix: index of a big group, 0xff otherwise
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const uint64_t count = list ? (uint64_t)*nlist : nseg;
@@ -301,6 +339,7 @@ __global__ __launch_bounds__(THREADS) void k_small_msd(
         }
         if (lane == 0) { s_red[w] = kmin; s_red[32 + w] = kmax; }
         for (int d = tid; d < kChipRadix; d += THREADS) s_start[d] = 0;
+        if (tid == 0) { s_misc[0] = 0; s_misc[1] = 0; }
         __syncthreads();
         {
             uint64_t a = ~0ull, b = 0;
@@ -343,10 +382,17 @@ __global__ __launch_bounds__(THREADS) void k_small_msd(
         __syncthreads();
         mx = 0;
         for (int i = 0; i < WARPS; ++i) mx = max(mx, s_warp[i]);
-        if (mx > (uint32_t)kTinyGroup) {  // skewed: the stable LSD kernel takes this segment
-            if (tid == 0) fb_list[atomicAdd(fb_count, 1u)] = (uint32_t)s;
+        const bool big = mx > (uint32_t)kTinyGroup;  // uniform per CTA
+        if (big) {
+            for (int d = tid; d < kChipRadix; d += THREADS)
+                s_bigid[d] = (s_start[d + 1] - s_start[d] > (uint32_t)kTinyGroup)
+                                 ? (uint8_t)min(atomicAdd(&s_misc[0], 1u), 255u) : (uint8_t)0xff;
             __syncthreads();
-            continue;
+            if (s_misc[0] > (uint32_t)kMaxBig) {  // too many big groups: the LSD kernel takes this segment
+                if (tid == 0) fb_list[atomicAdd(fb_count, 1u)] = (uint32_t)s;
+                __syncthreads();
+                continue;
+            }
         }
         for (uint32_t e = tid; e < n; e += THREADS) s_grp[atomicAdd(&s_run[s_dig[e]], 1u)] = (uint16_t)e;
         __syncthreads();
@@ -355,6 +401,10 @@ __global__ __launch_bounds__(THREADS) void k_small_msd(
             const uint64_t kx = s_keys[x];
             const uint32_t d = s_dig[x];
             const uint32_t a = s_start[d], b = s_start[d + 1];
+            if (b - a > (uint32_t)kTinyGroup) {  // big group: only check that it holds one key value
+                if (kx != s_keys[s_grp[a]]) s_misc[1] = 1u;
+                continue;
+            }
             uint32_t r = 0;
             for (uint32_t g = a; g < b; ++g) {
                 const uint16_t y = s_grp[g];
@@ -364,12 +414,59 @@ __global__ __launch_bounds__(THREADS) void k_small_msd(
             s_out[a + r] = x;
         }
         __syncthreads();
-        for (uint32_t j = tid; j < n; j += THREADS) {
-            const uint32_t src = s_out[j];
-            kout[base + j] = s_keys[src] ^ flip_out;
-            if (PAY) pout[base + j] = pin[base + src];
+        if (big) {
+            if (s_misc[1]) {  // a big group of distinct keys: the LSD kernel takes this segment
+                if (tid == 0) fb_list[atomicAdd(fb_count, 1u)] = (uint32_t)s;
+                __syncthreads();
+                continue;
+            }
+            // Members of each big group in input order: warp w walks the
+            // positions [w*C, (w+1)*C) in order; pass A counts the members of
+            // every big group per warp, a scan over the warps turns the counts
+            // into starts, and pass B places each member at its group's start
+            // plus the members before it.
+            const uint32_t nbig = s_misc[0];
+            const uint32_t C = ((n + WARPS - 1) / WARPS + 31) / 32 * 32;
+            const uint32_t lo = min(n, (uint32_t)w * C), hi = min(n, lo + C);
+            const uint32_t lt = (1u << lane) - 1u;
+            uint32_t* wc = s_wcnt + w * kMaxBig;
+            for (uint32_t b = lane; b < nbig; b += 32) wc[b] = 0;
+            __syncwarp();
+            for (uint32_t p0 = lo; p0 < hi; p0 += 32) {
+                const uint32_t e = p0 + lane;
+                const uint32_t g = e < hi ? (uint32_t)s_bigid[s_dig[e]] : 0xffu;
+                const bool valid = g != 0xffu;
+                const uint32_t peers = __match_any_sync(0xffffffffu, valid ? g : 0x100u + lane);
+                if (valid && (peers & lt) == 0u) wc[g] += (uint32_t)__popc(peers);
+                __syncwarp();
+            }
+            __syncthreads();
+            for (uint32_t b = tid; b < nbig; b += THREADS) {
+                uint32_t run = 0;
+                for (int v = 0; v < WARPS; ++v) {
+                    const uint32_t c = s_wcnt[v * kMaxBig + b];
+                    s_wcnt[v * kMaxBig + b] = run;
+                    run += c;
+                }
+            }
+            __syncthreads();
+            for (uint32_t p0 = lo; p0 < hi; p0 += 32) {
+                const uint32_t e = p0 + lane;
+                const uint32_t d = e < hi ? (uint32_t)s_dig[e] : 0u;
+                const uint32_t g = e < hi ? (uint32_t)s_bigid[d] : 0xffu;
+                const bool valid = g != 0xffu;
+                const uint32_t peers = __match_any_sync(0xffffffffu, valid ? g : 0x100u + lane);
+                const uint32_t before = valid ? wc[g] : 0u;
+                __syncwarp();
+                if (valid) {
+                    s_out[s_start[d] + before + (uint32_t)__popc(peers & lt)] = (uint16_t)e;
+                    if ((peers & lt) == 0u) wc[g] = before + (uint32_t)__popc(peers);
+                }
+                __syncwarp();
+            }
+            __syncthreads();
         }
-        __syncthreads();
+        write_sorted<PAY, THREADS, CAP>(kout, pout, pin, base, n, s_keys, s_out, flip_out);
     }
 }
 
@@ -386,9 +483,9 @@ constexpr size_t lsd_sort_smem() {
 
 template <bool PAY, int THREADS, int ITEMS>
 __global__ __launch_bounds__(THREADS, 1) void k_small_lsd(
-    const uint64_t* __restrict__ kin, uint64_t* __restrict__ kout, const uint32_t* __restrict__ pin,
-    uint32_t* __restrict__ pout, const uint64_t* __restrict__ seg_lo, const uint64_t* __restrict__ seg_hi,
-    const uint32_t* __restrict__ list, const uint32_t* __restrict__ nlist, uint64_t flip_in, uint64_t flip_out) {
+    const uint64_t* kin, uint64_t* kout, const uint32_t* pin, uint32_t* pout, const uint64_t* __restrict__ seg_lo,
+    const uint64_t* __restrict__ seg_hi, const uint32_t* __restrict__ list, const uint32_t* __restrict__ nlist,
+    uint64_t flip_in, uint64_t flip_out) {
     constexpr int WARPS = THREADS / 32;
     constexpr int CAP = THREADS * ITEMS;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -452,12 +549,7 @@ __global__ __launch_bounds__(THREADS, 1) void k_small_lsd(
             __syncthreads();
             uint16_t* t = cur; cur = nxt; nxt = t;
         }
-        for (uint32_t j = tid; j < n; j += THREADS) {
-            const uint32_t src = cur[j];
-            kout[base + j] = s_keys[src] ^ flip_out;
-            if (PAY) pout[base + j] = pin[base + src];
-        }
-        __syncthreads();
+        write_sorted<PAY, THREADS, CAP>(kout, pout, pin, base, n, s_keys, cur, flip_out);
     }
 }
 
@@ -890,7 +982,7 @@ static cudaError_t launch_small(const uint64_t* in, uint64_t* out, const uint32_
                                 const uint64_t* seg_lo, const uint64_t* seg_hi, const uint32_t* list,
                                 const uint32_t* nlist, uint64_t count, uint64_t nseg, uint32_t min_n, uint32_t max_n,
                                 uint64_t fin, uint64_t fout, const SegSortWs& ws, cudaStream_t st) {
-    constexpr size_t smem = msd_sort_smem<CAP>();
+    constexpr size_t smem = msd_sort_smem<THREADS, CAP>();
     static bool attr = false;
     if (!attr) {
         const cudaError_t e = cudaFuncSetAttribute(k_small_msd<PAY, THREADS, CAP>,

@@ -108,6 +108,39 @@ def allzeros(N: int, seed: int = 0) -> np.ndarray:
     return np.zeros(N, dtype=np.uint64)
 
 
+def nested_clusters(N: int, seed: int) -> np.ndarray:
+    """A stress input for the radix recursion: a third of the keys uniform
+    over 64 bits, a third in a window of width 2^40, and a third in a window
+    of width 2^20 nested inside it, drawn from 4096 distinct values (many
+    duplicates).  The nested window keeps one digit bin over the on-chip
+    capacity for three levels of the most-significant-digit split."""
+    g = rng(seed, 9)
+    c = np.uint64(0x5A12_3400_0000_0000)
+    n0, n1 = N // 3, N // 3
+    n2 = N - n0 - n1
+    a = g.bit_generator.random_raw(n0).astype(np.uint64)
+    b = c + (g.bit_generator.random_raw(n1).astype(np.uint64) >> np.uint64(24))
+    d = c + np.uint64(1 << 39) + (g.integers(0, 4096, n2, dtype=np.uint64) << np.uint64(8))
+    out = np.concatenate([a, b, d])
+    return out[g.permutation(N)]
+
+
+def duplicate_groups(N: int, seed: int, nvals: int, share: float, adjacent: bool = False) -> np.ndarray:
+    """A share of the keys drawn from nvals values (each repeated many
+    times), the rest uniform over 64 bits.  With ``adjacent`` the repeated
+    values are consecutive integers, so several of them share any coarse
+    digit of the key range."""
+    g = rng(seed, 10)
+    nd = int(N * share)
+    if adjacent:
+        base = np.uint64(g.bit_generator.random_raw(1)[0] >> np.uint64(1))
+        vals = base + np.arange(nvals, dtype=np.uint64)
+    else:
+        vals = g.bit_generator.random_raw(nvals).astype(np.uint64)
+    out = np.concatenate([vals[g.integers(0, nvals, nd)], g.bit_generator.random_raw(N - nd).astype(np.uint64)])
+    return out[g.permutation(N)]
+
+
 PAPER_DISTRIBUTIONS = {
     "UNIF": uniform, "SKEW1": skew1, "SKEW2": skew2, "SKEW3": skew3, "GAUSS": gauss, "AllZeros": allzeros,
 }
@@ -128,28 +161,43 @@ def _spread3(v: np.ndarray) -> np.ndarray:
     return v
 
 
+def _plummer_chunk(seed: int, c: int, n: int, bits: int) -> np.ndarray:
+    g = rng(seed, (8 << 32) | c)
+    r_max = (0.999 ** (-2.0 / 3.0) - 1.0) ** -0.5
+    scale = float(1 << bits)
+    m = 0.999 * (1.0 - g.random(n))  # (0, 0.999]
+    r = (m ** (-2.0 / 3.0) - 1.0) ** -0.5
+    ct = 2.0 * g.random(n) - 1.0
+    st = np.sqrt(np.maximum(0.0, 1.0 - ct * ct))
+    ph = 2.0 * math.pi * g.random(n)
+    xyz = (r * st * np.cos(ph), r * st * np.sin(ph), r * ct)
+    q = [np.clip(np.floor((v + r_max) / (2.0 * r_max) * scale), 0, scale - 1).astype(np.uint64) for v in xyz]
+    return _spread3(q[0]) | (_spread3(q[1]) << np.uint64(1)) | (_spread3(q[2]) << np.uint64(2))
+
+
 def plummer_morton(N: int, seed: int, bits: int = 21):
     """Morton keys of a Plummer sphere plus the particle index as payload.
 
     Radius from the Plummer mass profile m(r) = r^3 (1+r^2)^(-3/2): for a mass
     fraction m ~ U(0, 0.999], r = (m^(-2/3) - 1)^(-1/2); isotropic direction;
     each axis quantised to ``bits`` bits over [-r_max, r_max] with r_max = r(0.999).
+    Chunks of 2^22 particles draw from their own streams, so the chunks are
+    generated on all host cores and the result does not depend on the count.
     """
-    g = rng(seed, 8)
-    r_max = (0.999 ** (-2.0 / 3.0) - 1.0) ** -0.5
+    from concurrent.futures import ThreadPoolExecutor
+    import os
+
+    chunk = 1 << 22
     keys = np.empty(N, dtype=np.uint64)
-    scale = float(1 << bits)
-    for a in range(0, N, _CHUNK):
-        b = min(N, a + _CHUNK)
-        n = b - a
-        m = 0.999 * (1.0 - g.random(n))  # (0, 0.999]
-        r = (m ** (-2.0 / 3.0) - 1.0) ** -0.5
-        ct = 2.0 * g.random(n) - 1.0
-        st = np.sqrt(np.maximum(0.0, 1.0 - ct * ct))
-        ph = 2.0 * math.pi * g.random(n)
-        xyz = (r * st * np.cos(ph), r * st * np.sin(ph), r * ct)
-        q = [np.clip(np.floor((c + r_max) / (2.0 * r_max) * scale), 0, scale - 1).astype(np.uint64) for c in xyz]
-        keys[a:b] = _spread3(q[0]) | (_spread3(q[1]) << np.uint64(1)) | (_spread3(q[2]) << np.uint64(2))
+
+    def work(c):
+        a = c * chunk
+        b = min(N, a + chunk)
+        keys[a:b] = _plummer_chunk(seed, c, b - a, bits)
+
+    nchunks = (N + chunk - 1) // chunk
+    with ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1))) as ex:
+        list(ex.map(work, range(nchunks)))
     payload = np.arange(N, dtype=np.uint64).astype(np.uint32)
     return keys, payload
 

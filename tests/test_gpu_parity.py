@@ -46,6 +46,7 @@ GENS = {
     "skew3": inputs.skew3,
     "gauss": inputs.gauss,
     "allzeros": inputs.allzeros,
+    "nested": inputs.nested_clusters,
 }
 
 
@@ -74,6 +75,35 @@ def test_local_sort_matches_oracle(hss, N, p, gen):
         out, outp = hss.local_sort(dev(keys), p, payload=dev(pay))
         assert out.numel() == 0 and outp.numel() == 0
         return
+    out, outp = hss.local_sort(dev(keys), p, payload=dev(pay))
+    want, wantp = oracle.segment_sort(keys, p, payload=pay)
+    assert np.array_equal(host_u64(out), want)
+    assert np.array_equal(outp.cpu().numpy().view(np.uint32), wantp)
+
+
+@pytest.mark.parametrize("N,p", [(1 << 18, 1), (300001, 2)])
+def test_local_sort_deep_recursion_payload(hss, N, p):
+    """Three levels of digit splits: the second level's small buckets are
+    sorted on chip in place in the output buffer, payload included."""
+    keys = inputs.nested_clusters(N, 11)
+    pay = (np.arange(N, dtype=np.uint32) * np.uint32(2654435761)).astype(np.uint32)
+    out, outp = hss.local_sort(dev(keys), p, payload=dev(pay))
+    want, wantp = oracle.segment_sort(keys, p, payload=pay)
+    assert np.array_equal(host_u64(out), want)
+    assert np.array_equal(outp.cpu().numpy().view(np.uint32), wantp)
+
+
+@pytest.mark.parametrize("N,p,nvals,share,adjacent", [
+    (14000, 1, 3, 0.85, False),    # big groups of one value each, many small groups
+    (14000, 1, 100, 0.99, False),  # more big groups than the on-chip table holds
+    (1500, 1, 2, 0.8, False),      # the smallest on-chip class
+    (4000, 1, 4, 0.5, True),       # adjacent values share a group: distinct keys in a big group
+    (42001, 3, 5, 0.9, False),     # three segments, each split once first
+    (300000, 2, 40, 0.95, False),  # the bench shape in small: split, then on-chip buckets of few values
+])
+def test_local_sort_duplicate_groups(hss, N, p, nvals, share, adjacent):
+    keys = inputs.duplicate_groups(N, 13, nvals, share, adjacent)
+    pay = (np.arange(N, dtype=np.uint32) * np.uint32(2654435761)).astype(np.uint32)
     out, outp = hss.local_sort(dev(keys), p, payload=dev(pay))
     want, wantp = oracle.segment_sort(keys, p, payload=pay)
     assert np.array_equal(host_u64(out), want)
@@ -196,7 +226,7 @@ def test_sort_matches_oracle(hss, N, p, eps, seed, payload):
         assert np.array_equal(res.payload.cpu().numpy().view(np.uint32), ref.out_payload)
 
 
-@pytest.mark.parametrize("gen", ["gauss_mix", "zipf", "skew2", "allzeros", "skew3"])
+@pytest.mark.parametrize("gen", ["gauss_mix", "zipf", "skew2", "allzeros", "skew3", "nested"])
 def test_sort_distributions(hss, gen):
     N, p, eps, seed = 1 << 18, 8, 0.02, 5
     keys = GENS[gen](N, seed)
