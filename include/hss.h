@@ -133,6 +133,23 @@ int hss_partition(const void* d_keys, int key_type, uint64_t N, const hss_params
                   hss_cut* d_splitters, uint64_t* d_offsets,
                   void* d_work, size_t work_bytes, hss_stats* h_stats, void* stream);
 
+/* hss_partition with externally proposed splitters (a learned model of the
+ * key distribution, or the splitters of an earlier call on similar data).
+ * Each of the nprop keys of d_proposal (device, the caller's key type) is a
+ * non-member cut: it sorts before every input key equal to it, and its rank
+ * is the number of input keys strictly below it.  Before the first round the
+ * cuts are histogrammed like probes (Sec. 4.2.2 step 2) and offered to every
+ * splitter's L/U (step 3; equal ranks keep the smaller cut), so good proposals
+ * resolve splitters without sampling while the rounds still decide balance:
+ * the contract on d_offsets is that of hss_partition whatever the proposal.
+ * A splitter may end on a proposed cut (seg = -1 in d_splitters).  The paper
+ * proposes no such step; it is the hook of the learned proposal.  nprop may be
+ * 0; it must not exceed the round sample capacity, min(N, ceil(2 s p) + 4096),
+ * else HSS_ERR_INVALID.  Workspace as hss_partition. */
+int hss_partition_with_proposal(const void* d_keys, int key_type, uint64_t N, const hss_params* prm,
+                                const void* d_proposal, uint32_t nprop, hss_cut* d_splitters, uint64_t* d_offsets,
+                                void* d_work, size_t work_bytes, hss_stats* h_stats, void* stream);
+
 /* Data exchange (Sec. 3.1 step 3, Sec. 6 "data exchange"): move every run of
  * locally sorted keys to its bucket.  d_seg_pos[s*(p-1)+i] is the number of
  * keys of segment s below splitter i (hss_rank_cuts output for the p-1
@@ -155,6 +172,14 @@ int hss_merge(const void* d_bucket_keys, const uint32_t* d_bucket_payload, int k
 int hss_sort(const void* d_keys, const uint32_t* d_payload, int key_type, uint64_t N, const hss_params* prm,
              void* d_keys_out, uint32_t* d_payload_out, hss_cut* d_splitters, uint64_t* d_offsets,
              void* d_work, size_t work_bytes, hss_stats* h_stats, void* stream);
+
+/* hss_sort with proposed splitters: the rounds start from d_proposal[nprop]
+ * exactly as in hss_partition_with_proposal; the rest as hss_sort.  Workspace
+ * as hss_sort. */
+int hss_sort_with_proposal(const void* d_keys, const uint32_t* d_payload, int key_type, uint64_t N,
+                           const hss_params* prm, const void* d_proposal, uint32_t nprop, void* d_keys_out,
+                           uint32_t* d_payload_out, hss_cut* d_splitters, uint64_t* d_offsets, void* d_work,
+                           size_t work_bytes, hss_stats* h_stats, void* stream);
 
 /* hss_sort from host buffers: copies the keys (and payload) to the
  * workspace, sorts, and copies the sorted keys, payload, splitters and

@@ -130,7 +130,8 @@ static int read_dev_err(uint32_t* d_err, cudaStream_t st) {
 // Core of hss_partition / hss_sort.
 static int run_path(const void* d_keys, const uint32_t* d_payload, int key_type, uint64_t N, const hss_params* prm,
                     void* d_keys_out, uint32_t* d_payload_out, hss_cut* d_splitters, uint64_t* d_offsets,
-                    void* d_work, size_t work_bytes, hss_stats* h_stats, cudaStream_t st, bool sort) {
+                    void* d_work, size_t work_bytes, hss_stats* h_stats, cudaStream_t st, bool sort,
+                    const void* d_prop = nullptr, uint32_t nprop = 0) {
     const uint64_t mark = g_launches.load();
     if (h_stats) std::memset(h_stats, 0, sizeof(*h_stats));
     if (!params_ok(prm) || (key_type != HSS_KEY_U64 && key_type != HSS_KEY_I64) || N >= kMaxN) return HSS_ERR_INVALID;
@@ -174,7 +175,7 @@ static int run_path(const void* d_keys, const uint32_t* d_payload, int key_type,
     // Splitter rounds (Sec. 4.2.2).
     RoundResult rr;
     int status = run_rounds(keysA, seg_off, N, p, prm->eps, prm->seed, s, eff_rounds(prm), key_type, d_splitters,
-                            d_offsets, rws, st, &rr);
+                            d_offsets, rws, st, &rr, (const uint64_t*)d_prop, nprop);
     tm.mark(HSS_PHASE_ROUNDS);
     if (status == HSS_ERR_CUDA) return status;
 
@@ -273,6 +274,23 @@ int hss_partition(const void* d_keys, int key_type, uint64_t N, const hss_params
                   uint64_t* d_offsets, void* d_work, size_t work_bytes, hss_stats* h_stats, void* stream) {
     return run_path(d_keys, nullptr, key_type, N, prm, nullptr, nullptr, d_splitters, d_offsets, d_work, work_bytes, h_stats,
                     (cudaStream_t)stream, false);
+}
+
+int hss_partition_with_proposal(const void* d_keys, int key_type, uint64_t N, const hss_params* prm,
+                                const void* d_proposal, uint32_t nprop, hss_cut* d_splitters, uint64_t* d_offsets,
+                                void* d_work, size_t work_bytes, hss_stats* h_stats, void* stream) {
+    if (nprop > 0 && !d_proposal) return HSS_ERR_INVALID;
+    return run_path(d_keys, nullptr, key_type, N, prm, nullptr, nullptr, d_splitters, d_offsets, d_work, work_bytes, h_stats,
+                    (cudaStream_t)stream, false, d_proposal, nprop);
+}
+
+int hss_sort_with_proposal(const void* d_keys, const uint32_t* d_payload, int key_type, uint64_t N, const hss_params* prm,
+                           const void* d_proposal, uint32_t nprop, void* d_keys_out, uint32_t* d_payload_out,
+                           hss_cut* d_splitters, uint64_t* d_offsets, void* d_work, size_t work_bytes, hss_stats* h_stats,
+                           void* stream) {
+    if (nprop > 0 && !d_proposal) return HSS_ERR_INVALID;
+    return run_path(d_keys, d_payload, key_type, N, prm, d_keys_out, d_payload_out, d_splitters, d_offsets, d_work,
+                    work_bytes, h_stats, (cudaStream_t)stream, true, d_proposal, nprop);
 }
 
 int hss_exchange(const void* d_sorted_keys, const uint32_t* d_sorted_payload, uint64_t N, uint32_t p,

@@ -479,6 +479,30 @@ __global__ __launch_bounds__(256) void k_histogram(
 }
 
 // ---------------------------------------------------------------------------
+// Proposed cuts (a learned splitter proposal): non-member cuts (k, -1) that
+// sort before every input key equal to k.  They are ranked and offered to the
+// splitters like probes before the first round.
+// ---------------------------------------------------------------------------
+// Before round 1 every splitter's interval is (-inf, +inf), so every cut is
+// searched over whole segments: interval 0 with representative splitter 0
+// (whose per-segment bounds are still 0 and the segment length), whatever the
+// resolved flags say.
+__global__ void k_prop_load(const uint64_t* __restrict__ prop, uint32_t nprop, uint64_t flip, uint64_t* __restrict__ okey,
+                            RoundCtl* ctl, uint32_t* __restrict__ int_rep) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) { ctl->seg_off_z[0] = 0; ctl->seg_off_z[1] = nprop; int_rep[0] = 0; }
+    if (k < nprop) okey[k] = prop[k] ^ flip;
+}
+
+__global__ void k_prop_probes(uint32_t nprop, const uint64_t* __restrict__ okey_sorted, uint64_t* __restrict__ pkey,
+                              int32_t* __restrict__ pseg, uint32_t* __restrict__ pspos, uint32_t* __restrict__ pint,
+                              uint64_t* __restrict__ prank) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nprop) return;
+    pkey[k] = okey_sorted[k]; pseg[k] = -1; pspos[k] = 0; prank[k] = 0; pint[k] = 0;
+}
+
+// ---------------------------------------------------------------------------
 // L/U update of every splitter from the ranked probes.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void offer(DCut& L, DCut& U, int32_t& cl, int32_t& cu, uint64_t t, const DCut& c, int32_t k) {
@@ -486,8 +510,11 @@ __device__ __forceinline__ void offer(DCut& L, DCut& U, int32_t& cl, int32_t& cu
     if (c.rank >= t && (c.rank < U.rank || (c.rank == U.rank && cut_less(c, U)))) { U = c; cu = k; }
 }
 
+// Probes of one launch are all input keys (kind kMember, distinct ranks) or
+// all proposed non-member cuts (kind kNonMember), whose ranks may repeat: then
+// the best cut of a rank is the first of its run (the smallest tag).
 __global__ void k_update(uint32_t S, uint64_t N, uint32_t p, const uint64_t* __restrict__ pkey, const int32_t* __restrict__ pseg,
-                         const uint32_t* __restrict__ pspos, const uint64_t* __restrict__ prank, uint64_t Z,
+                         const uint32_t* __restrict__ pspos, const uint64_t* __restrict__ prank, uint64_t Z, int32_t pkind,
                          DCut* __restrict__ Lcut, DCut* __restrict__ Ucut, int32_t* __restrict__ chgL, int32_t* __restrict__ chgU) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= S) return;
@@ -501,10 +528,19 @@ __global__ void k_update(uint32_t S, uint64_t N, uint32_t p, const uint64_t* __r
     DCut L = Lcut[i], U = Ucut[i];
     int32_t cl = -1, cu = -1;
     auto probe = [&](uint64_t k) {
-        DCut c; c.okey = pkey[k]; c.seg = pseg[k]; c.spos = pspos[k]; c.rank = prank[k]; c.kind = kMember; c.pad = 0;
+        DCut c; c.okey = pkey[k]; c.seg = pseg[k]; c.spos = pspos[k]; c.rank = prank[k]; c.kind = pkind; c.pad = 0;
         return c;
     };
-    if (kgt > 0) offer(L, U, cl, cu, t, probe(kgt - 1), (int32_t)(kgt - 1));
+    if (kgt > 0) {
+        uint64_t kl = kgt - 1;
+        if (pkind != kMember) {  // first probe of the run with rank prank[kl]
+            const uint64_t r = prank[kl];
+            uint64_t a = 0, b = kl;
+            while (a < b) { const uint64_t m = (a + b) >> 1; if (prank[m] < r) a = m + 1; else b = m; }
+            kl = a;
+        }
+        offer(L, U, cl, cu, t, probe(kl), (int32_t)kl);
+    }
     if (kge < Z) offer(L, U, cl, cu, t, probe(kge), (int32_t)kge);
     Lcut[i] = L; Ucut[i] = U; chgL[i] = cl; chgU[i] = cu;
 }
@@ -636,7 +672,7 @@ static void enqueue_sampling(const RoundWs& ws, const uint64_t* d_seg_off, uint6
 
 int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uint32_t p, double eps, uint64_t seed,
                float oversample, uint32_t max_rounds, int key_type, hss_cut* d_splitters, uint64_t* d_offsets,
-               const RoundWs& ws, cudaStream_t st, RoundResult* out) {
+               const RoundWs& ws, cudaStream_t st, RoundResult* out, const uint64_t* d_prop, uint32_t nprop) {
     const uint32_t S = p - 1;
     const uint64_t tol = (uint64_t)std::floor(((double)N * eps) / (2.0 * (double)p));
     HSS_TRY(cudaMemsetAsync(ws.ctl, 0, sizeof(RoundCtl), st));
@@ -651,6 +687,23 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
     const unsigned sblk = (unsigned)cdiv(S, 256);
     HSS_LAUNCH(k_rounds_init, dim3(p, sblk), 256, 0, st, d_seg_off, S, N, ws.Lcut, ws.Ucut, ws.Lpos, ws.Upos);
     HSS_LAUNCH(k_intervals, 1, 1024, 0, st, S, N, p, tol, oversample, ws.Lcut, ws.Ucut, ws.res, ws.int_rep, ws.ctl);
+    if (nprop > 0) {
+        // Proposed cuts: sorted, ranked in every segment, offered to L/U.
+        if (nprop > ws.cap) return HSS_ERR_INVALID;
+        const uint64_t flip = key_type == HSS_KEY_I64 ? kSignBit : 0ull;
+        HSS_LAUNCH(k_prop_load, (unsigned)cdiv(nprop, 256), 256, 0, st, d_prop, nprop, flip, ws.skey, ws.ctl, ws.int_rep);
+        HSS_TRY(segsort(ws.skey, ws.skey_sorted, ws.stmp, nullptr, nullptr, nullptr, nprop, 1, ws.ctl->seg_off_z, false,
+                        false, ws.sws, st, nullptr));
+        HSS_LAUNCH(k_prop_probes, (unsigned)cdiv(nprop, 256), 256, 0, st, nprop, ws.skey_sorted, ws.pkey, ws.pseg,
+                   ws.pspos, ws.pint, ws.prank);
+        HSS_LAUNCH(k_histogram, dim3((unsigned)cdiv(nprop, 32), (unsigned)cdiv(p, kHistSegPerBlock)), 256, 0, st, skeys,
+                   d_seg_off, p, S, ws.Lpos, ws.Upos, ws.int_rep, ws.pkey, ws.pseg, ws.pspos, ws.pint, (uint64_t)nprop,
+                   ws.prank, ws.probe_pos, ws.cap, ws.sws.err);
+        HSS_LAUNCH(k_update, sblk, 256, 0, st, S, N, p, ws.pkey, ws.pseg, ws.pspos, ws.prank, (uint64_t)nprop,
+                   (int32_t)kNonMember, ws.Lcut, ws.Ucut, ws.chgL, ws.chgU);
+        HSS_LAUNCH(k_update_pos, dim3(p, sblk), 256, 0, st, S, ws.chgL, ws.chgU, ws.probe_pos, ws.cap, ws.Lpos, ws.Upos);
+        HSS_LAUNCH(k_intervals, 1, 1024, 0, st, S, N, p, tol, oversample, ws.Lcut, ws.Ucut, ws.res, ws.int_rep, ws.ctl);
+    }
     enqueue_sampling(ws, d_seg_off, N, p, S, seed, 1, st);
     HSS_TRY(cudaGetLastError());
     RoundCtl h;
@@ -677,8 +730,8 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
             HSS_LAUNCH(k_histogram, dim3((unsigned)cdiv(Z, 32), (unsigned)cdiv(p, kHistSegPerBlock)), 256, 0, st, skeys,
                        d_seg_off, p, S, ws.Lpos, ws.Upos, ws.int_rep, ws.pkey, ws.pseg, ws.pspos, ws.pint, Z, ws.prank,
                        ws.probe_pos, ws.cap, ws.sws.err);
-            HSS_LAUNCH(k_update, sblk, 256, 0, st, S, N, p, ws.pkey, ws.pseg, ws.pspos, ws.prank, Z, ws.Lcut, ws.Ucut,
-                       ws.chgL, ws.chgU);
+            HSS_LAUNCH(k_update, sblk, 256, 0, st, S, N, p, ws.pkey, ws.pseg, ws.pspos, ws.prank, Z, (int32_t)kMember,
+                       ws.Lcut, ws.Ucut, ws.chgL, ws.chgU);
             HSS_LAUNCH(k_update_pos, dim3(p, sblk), 256, 0, st, S, ws.chgL, ws.chgU, ws.probe_pos, ws.cap, ws.Lpos, ws.Upos);
         }
         HSS_LAUNCH(k_intervals, 1, 1024, 0, st, S, N, p, tol, oversample, ws.Lcut, ws.Ucut, ws.res, ws.int_rep, ws.ctl);

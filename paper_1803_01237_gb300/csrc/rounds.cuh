@@ -72,10 +72,13 @@ struct RoundResult {
 
 // Run the histogram rounds over the p locally sorted segments skeys
 // (order-preserving key bits) and write the splitters, offsets and the final
-// per-segment positions of the splitters (into ws.Lpos).
+// per-segment positions of the splitters (into ws.Lpos).  d_prop[nprop]
+// (nullable; keys in the caller's representation, nprop <= ws.cap) are
+// proposed cuts ranked and offered to every splitter before round 1.
 int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uint32_t p, double eps, uint64_t seed,
                float oversample, uint32_t max_rounds, int key_type, hss_cut* d_splitters, uint64_t* d_offsets,
-               const RoundWs& ws, cudaStream_t st, RoundResult* out);
+               const RoundWs& ws, cudaStream_t st, RoundResult* out, const uint64_t* d_prop = nullptr,
+               uint32_t nprop = 0);
 
 // Per-bucket split windows for the merge, from the final splitters.
 cudaError_t bucket_hints(const RoundWs& ws, const uint64_t* skeys, const uint64_t* d_seg_off, uint32_t p,

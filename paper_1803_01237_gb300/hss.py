@@ -83,13 +83,17 @@ def load():
         lib.hss_merge.argtypes = [P, P, I32, U64, U32, P, P, P, P, SZ, P]
         lib.hss_sort.argtypes = [P, P, I32, U64, ctypes.POINTER(Params), P, P, P, P, P, SZ, ctypes.POINTER(Stats), P]
         lib.hss_sort_host.argtypes = [P, P, I32, U64, ctypes.POINTER(Params), P, P, P, P, P, SZ, ctypes.POINTER(Stats), P]
+        lib.hss_partition_with_proposal.argtypes = [P, I32, U64, ctypes.POINTER(Params), P, U32, P, P, P, SZ,
+                                                    ctypes.POINTER(Stats), P]
+        lib.hss_sort_with_proposal.argtypes = [P, P, I32, U64, ctypes.POINTER(Params), P, U32, P, P, P, P, P, SZ,
+                                               ctypes.POINTER(Stats), P]
         lib.hss_sample_words.argtypes = [U64, U32, U32, U32, U32, P, P]
         lib.hss_kernel_launch_count.argtypes = []
         lib.hss_kernel_launch_count.restype = U64
         lib.hss_strerror.argtypes = [I32]
         lib.hss_strerror.restype = ctypes.c_char_p
         for name in ("hss_local_sort", "hss_rank_cuts", "hss_partition", "hss_exchange", "hss_merge", "hss_sort",
-                     "hss_sort_host", "hss_sample_words"):
+                     "hss_sort_host", "hss_sample_words", "hss_partition_with_proposal", "hss_sort_with_proposal"):
             getattr(lib, name).restype = I32
         _lib = lib
         return lib
@@ -249,6 +253,61 @@ def partition(keys, p: int, eps: float, seed: int, oversample: float = 5.0, max_
                            ws.numel(), ctypes.byref(st), _stream(stream))
     _check(rc, "hss_partition", allow=(-3,) if allow_round_limit else ())
     return _result(None, None, spl[:p - 1], off, st), ws
+
+
+def _proposal_tensor(proposal, keys: torch.Tensor):
+    if proposal is None:
+        return None, 0
+    prop = _as_key_tensor(proposal)
+    if prop.device != keys.device:
+        raise ValueError("the proposal must be on the keys' device")
+    return prop, prop.numel()
+
+
+def partition_with_proposal(keys, p: int, eps: float, seed: int, proposal, oversample: float = 5.0,
+                            max_rounds: int = 0, key_type: str = "u64", flags: int = 0, stream=None,
+                            allow_round_limit: bool = False):
+    """hss_partition after ranking the proposed cuts (keys of the caller's
+    type, one device tensor) before round 1.  Returns (Result, ws)."""
+    lib = load()
+    keys = _as_key_tensor(keys)
+    N = keys.numel()
+    prop, nprop = _proposal_tensor(proposal, keys)
+    prm = _params(p, eps, seed, oversample, max_rounds, flags)
+    nb = int(lib.hss_workspace_bytes(OP["partition"], N, ctypes.byref(prm), p, KEY_TYPES[key_type], 0))
+    ws = workspace(nb, keys.device)
+    spl = torch.empty((max(p - 1, 1), 2), dtype=torch.int64, device=keys.device)
+    off = torch.empty(p + 1, dtype=torch.int64, device=keys.device)
+    st = Stats()
+    rc = lib.hss_partition_with_proposal(_ptr(keys), KEY_TYPES[key_type], N, ctypes.byref(prm), _ptr(prop), nprop,
+                                         _ptr(spl), _ptr(off), _ptr(ws), ws.numel(), ctypes.byref(st), _stream(stream))
+    _check(rc, "hss_partition_with_proposal", allow=(-3,) if allow_round_limit else ())
+    return _result(None, None, spl[:p - 1], off, st), ws
+
+
+def sort_with_proposal(keys, p: int, eps: float, seed: int, proposal, payload=None, oversample: float = 5.0,
+                       max_rounds: int = 0, key_type: str = "u64", flags: int = 0, out=None, out_payload=None,
+                       stream=None) -> "Result":
+    """hss_sort after ranking the proposed cuts before round 1."""
+    lib = load()
+    keys = _as_key_tensor(keys)
+    N = keys.numel()
+    prop, nprop = _proposal_tensor(proposal, keys)
+    prm = _params(p, eps, seed, oversample, max_rounds, flags)
+    nb = int(lib.hss_workspace_bytes(OP["sort"], N, ctypes.byref(prm), p, KEY_TYPES[key_type], int(payload is not None)))
+    ws = workspace(nb, keys.device)
+    if out is None:
+        out = torch.empty_like(keys)
+    if payload is not None and out_payload is None:
+        out_payload = torch.empty_like(payload)
+    spl = torch.empty((max(p - 1, 1), 2), dtype=torch.int64, device=keys.device)
+    off = torch.empty(p + 1, dtype=torch.int64, device=keys.device)
+    st = Stats()
+    rc = lib.hss_sort_with_proposal(_ptr(keys), _ptr(payload), KEY_TYPES[key_type], N, ctypes.byref(prm), _ptr(prop),
+                                    nprop, _ptr(out), _ptr(out_payload), _ptr(spl), _ptr(off), _ptr(ws), ws.numel(),
+                                    ctypes.byref(st), _stream(stream))
+    _check(rc, "hss_sort_with_proposal")
+    return _result(out, out_payload, spl[:p - 1], off, st)
 
 
 def exchange(sorted_keys, p: int, seg_pos: torch.Tensor, offsets: torch.Tensor, sorted_payload=None, stream=None):
