@@ -225,6 +225,10 @@ def batch_jobs(njobs: int, seed: int, lo_log2: int = 10, hi_log2: int = 22, zipf
 
 
 def lognormal_job(n: int, seed: int, sigma: float = 2.0) -> np.ndarray:
-    """lognormal(0, sigma) keys scaled so the largest is 2^63 - 1."""
-    x = rng(seed, 10).lognormal(0.0, sigma, size=n)
-    return np.floor(x / x.max() * float((1 << 63) - 1024)).astype(np.uint64)
+    """lognormal(0, sigma) keys on one fixed scale for every job: x / e^(6 sigma)
+    (six standard deviations of log x) times 2^63, clipped at 2^63 - 1024.  The
+    scale does not depend on the job, so jobs of the same stream share one key
+    distribution (the one a learned CDF model is trained on)."""
+    x = rng(seed, 11).lognormal(0.0, sigma, size=n)
+    u = np.minimum(x / math.exp(6.0 * sigma), 1.0)
+    return np.floor(u * float((1 << 63) - 1024)).astype(np.uint64)
