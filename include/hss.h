@@ -218,6 +218,80 @@ int hss_sample_words(uint64_t seed, uint32_t seg, uint32_t round, uint32_t spos0
 int hss_local_sort_noalloc(const void* d_keys, const uint32_t* d_payload, int key_type, uint64_t N, uint32_t p,
                            void* d_keys_out, uint32_t* d_payload_out, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned splitter proposal: a 1-32-32-1 CDF network of the keys.
+ *
+ * The paper proposes no model; its rounds (Sec. 4.2.2) take any candidate
+ * cuts, and hss_partition_with_proposal feeds them the cuts a model of the
+ * key distribution predicts.  The network maps a key to its estimated
+ * empirical CDF value:
+ *   u   = the key's order-preserving bits (int64: sign bit flipped)
+ *   x   = clip((raw(u) - lo) / (hi - lo), 0, 1), raw(u) = u (HSS_CDF_LINEAR)
+ *         or log2(1 + u) (HSS_CDF_LOG), in double precision
+ *   y   = w3 . relu(W2 relu(w1 x + b1) + b2) + b3, float32
+ * trained on (key, rank) pairs of earlier jobs (for instance the splitters
+ * and offsets an HSS call returns: exact ranks of sampled keys) to minimise
+ * (1/n) sum (y - rank/N)^2 with Adam (beta1 0.9, beta2 0.999, eps 1e-8).
+ * The model is one caller-owned device struct; its parameters can be read
+ * and written directly.  All calls are asynchronous on `stream`.
+ * ------------------------------------------------------------------------- */
+#define HSS_CDF_HIDDEN 32
+#define HSS_CDF_NPARAM 1153  /* 32 + 32 + 32*32 + 32 + 32 + 1 */
+#define HSS_CDF_LINEAR 0
+#define HSS_CDF_LOG 1
+
+typedef struct {
+    float theta[HSS_CDF_NPARAM];  /* w1[32], b1[32], W2[32*32] (row i = hidden-2 unit), b2[32], w3[32], b3 */
+    float m[HSS_CDF_NPARAM];      /* Adam first moments */
+    float v[HSS_CDF_NPARAM];      /* Adam second moments */
+    uint32_t step;                /* Adam steps taken */
+    int32_t feature;              /* HSS_CDF_LINEAR or HSS_CDF_LOG */
+    int32_t key_type;             /* HSS_KEY_U64 or HSS_KEY_I64 */
+    int32_t pad;
+    double lo, hi;                /* raw feature bounds of x = 0 and x = 1 */
+} hss_cdf_model;
+
+/* Initialise d_model: feature map from the key bounds lo_key < hi_key (the
+ * caller's key type), Adam state zero, parameters from Philox4x32-10 words of
+ * `seed` (counter (k, 0, 0, 0x43444621) for parameter k, u = (x0 >> 8) 2^-24):
+ * hidden-1 units alternate in sign with |w1| = 4 (1 + u) and knots -b1/w1 at
+ * (i + 0.5)/32; W2 and w3 uniform in +-sqrt(6/32); b2 = 0.1; b3 = 0.5.
+ * HSS_ERR_INVALID for a bad mode or key type, or bounds not increasing. */
+int hss_cdf_init(hss_cdf_model* d_model, uint64_t seed, int feature, int key_type, uint64_t lo_key, uint64_t hi_key,
+                 void* stream);
+
+/* sizeof(hss_cdf_model), for callers without this header's struct. */
+size_t hss_cdf_model_bytes(void);
+
+/* Device scratch (bytes) of hss_cdf_grad / hss_cdf_train for n points. */
+size_t hss_cdf_work_bytes(uint32_t n);
+
+/* Gradient of the loss at the current parameters over n points (d_keys[n]
+ * in the model's key type, d_ranks[n] their ranks among N keys): d_grad[1153]
+ * (float, nullable) and the loss d_loss[1] (nullable).  No update. */
+int hss_cdf_grad(const hss_cdf_model* d_model, const void* d_keys, const uint64_t* d_ranks, uint32_t n, uint64_t N,
+                 float* d_grad, float* d_loss, void* d_work, size_t work_bytes, void* stream);
+
+/* `steps` full-batch Adam steps of learning rate lr on the n points; the loss
+ * before the last step into d_loss (nullable).  Two kernels per step. */
+int hss_cdf_train(hss_cdf_model* d_model, const void* d_keys, const uint64_t* d_ranks, uint32_t n, uint64_t N,
+                  uint32_t steps, float lr, float* d_loss, void* d_work, size_t work_bytes, void* stream);
+
+/* Network output y for n keys: d_y[n] float. */
+int hss_cdf_eval(const hss_cdf_model* d_model, const void* d_keys, uint32_t n, float* d_y, void* stream);
+
+/* Proposed cuts: for each splitter i = 1..p-1 and k = 0..per_splitter-1 the
+ * CDF target tau = i/p + delta (2k/(per_splitter-1) - 1), clipped to [0, 1]
+ * (just i/p when per_splitter = 1); bisection (40 halvings, float32) for the
+ * smallest x in [0, 1] with y(x) >= tau, mapped back through the inverse
+ * feature map to a key (clamped to the key range).  Several cuts per splitter
+ * spread over the model's error band (delta about a few times its RMS error)
+ * bracket the target rank from both sides, so the histogram of the cuts
+ * narrows both L_i and U_i.  d_out_keys[(p-1) per_splitter], splitter-major,
+ * in the model's key type, ready for hss_partition_with_proposal. */
+int hss_cdf_propose(const hss_cdf_model* d_model, uint32_t p, uint32_t per_splitter, double delta, void* d_out_keys,
+                    void* stream);
+
 /* Kernels launched by this library in this process so far. */
 uint64_t hss_kernel_launch_count(void);
 

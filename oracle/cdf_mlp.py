@@ -17,8 +17,9 @@ textbook definitions the CUDA kernels implement in float32:
     (the empirical CDF at the training keys);
   * its gradient by the chain rule (reverse mode, written out by hand);
   * the Adam update (Kingma and Ba, ICLR 2015) with bias correction;
-  * the proposal: for each splitter i = 1..p-1, bisection on x in [0, 1] for
-    the smallest x with y(x) >= i/p, mapped back to a key.
+  * the proposal: for each splitter i = 1..p-1 and each of `per` targets
+    tau = i/p + delta (2k/(per-1) - 1) around it, bisection on x in [0, 1]
+    for the smallest x with y(x) >= tau, mapped back to a key.
 
 Parameter vector (1153 floats), in this order: w1[32], b1[32], W2[32*32]
 (row-major, W2[i, j] = weight from hidden-1 unit j to hidden-2 unit i),
@@ -152,12 +153,25 @@ def train(theta, x, t, steps, lr, m=None, v=None, step0=0):
     return theta, m, v, L
 
 
-def propose(theta, p, mode, lo, hi, key_type="u64", iters=40):
-    """Keys of the p-1 proposed splitters: bisection for the smallest x in
-    [0, 1] with y(x) >= i/p, then the inverse feature map."""
-    out = np.empty(max(p - 1, 0), dtype=np.uint64)
+def targets(p, per, delta):
+    """CDF targets of the proposed cuts: for splitter i = 1..p-1 and
+    k = 0..per-1, i/p + delta (2k/(per-1) - 1) (just i/p when per = 1),
+    clipped to [0, 1]; splitter-major order."""
+    out = []
     for i in range(1, p):
-        tau = i / p
+        for k in range(per):
+            off = 0.0 if per == 1 else delta * (2.0 * k / (per - 1) - 1.0)
+            out.append(min(1.0, max(0.0, i / p + off)))
+    return np.array(out, dtype=np.float64)
+
+
+def propose(theta, p, mode, lo, hi, key_type="u64", iters=40, per=1, delta=0.0):
+    """Keys of the proposed cuts: for each target tau (see targets), bisection
+    for the smallest x in [0, 1] with y(x) >= tau, then the inverse feature
+    map."""
+    tau_all = targets(p, per, delta)
+    out = np.empty(tau_all.shape[0], dtype=np.uint64)
+    for q, tau in enumerate(tau_all):
         a, b = 0.0, 1.0
         for _ in range(iters):
             mid = 0.5 * (a + b)
@@ -165,7 +179,7 @@ def propose(theta, p, mode, lo, hi, key_type="u64", iters=40):
                 a = mid
             else:
                 b = mid
-        out[i - 1] = key_of_feature(b, mode, lo, hi)
+        out[q] = key_of_feature(b, mode, lo, hi)
     if key_type == "i64":
         return (out ^ SIGN).view(np.int64)
     return out

@@ -88,6 +88,17 @@ def load():
         lib.hss_sort_with_proposal.argtypes = [P, P, I32, U64, ctypes.POINTER(Params), P, U32, P, P, P, P, P, SZ,
                                                ctypes.POINTER(Stats), P]
         lib.hss_sample_words.argtypes = [U64, U32, U32, U32, U32, P, P]
+        lib.hss_cdf_model_bytes.argtypes = []
+        lib.hss_cdf_model_bytes.restype = SZ
+        lib.hss_cdf_work_bytes.argtypes = [U32]
+        lib.hss_cdf_work_bytes.restype = SZ
+        lib.hss_cdf_init.argtypes = [P, U64, I32, I32, U64, U64, P]
+        lib.hss_cdf_grad.argtypes = [P, P, P, U32, U64, P, P, P, SZ, P]
+        lib.hss_cdf_train.argtypes = [P, P, P, U32, U64, U32, ctypes.c_float, P, P, SZ, P]
+        lib.hss_cdf_eval.argtypes = [P, P, U32, P, P]
+        lib.hss_cdf_propose.argtypes = [P, U32, U32, ctypes.c_double, P, P]
+        for name in ("hss_cdf_init", "hss_cdf_grad", "hss_cdf_train", "hss_cdf_eval", "hss_cdf_propose"):
+            getattr(lib, name).restype = I32
         lib.hss_kernel_launch_count.argtypes = []
         lib.hss_kernel_launch_count.restype = U64
         lib.hss_strerror.argtypes = [I32]
@@ -400,3 +411,91 @@ def launch_count() -> int:
 
 def strerror(code: int) -> str:
     return load().hss_strerror(code).decode()
+
+
+# ---------------------------------------------------------------------------
+# Learned splitter proposal: the 1-32-32-1 CDF network (hss_cdf_*)
+# ---------------------------------------------------------------------------
+CDF_NPARAM = 1153
+CDF_FEATURES = {"linear": 0, "log": 1}
+
+
+class CDFModel:
+    """A device-resident CDF network (one hss_cdf_model struct in a uint8
+    tensor).  theta/m/v views alias the struct's float arrays."""
+
+    def __init__(self, device=None):
+        lib = load()
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.nbytes = int(lib.hss_cdf_model_bytes())
+        self.buf = torch.zeros(self.nbytes, dtype=torch.uint8, device=dev)
+        self._work = torch.empty(0, dtype=torch.uint8, device=dev)
+        self.key_type = "u64"
+
+    @property
+    def theta(self) -> torch.Tensor:
+        return self.buf[:4 * CDF_NPARAM].view(torch.float32)
+
+    @property
+    def step(self) -> int:
+        return int(self.buf[12 * CDF_NPARAM:12 * CDF_NPARAM + 4].view(torch.int32).item())
+
+    def init(self, seed: int, feature: str, lo_key: int, hi_key: int, key_type: str = "u64", stream=None):
+        self.key_type = key_type
+        rc = load().hss_cdf_init(_ptr(self.buf), seed & ((1 << 64) - 1), CDF_FEATURES[feature], KEY_TYPES[key_type],
+                                 lo_key & ((1 << 64) - 1), hi_key & ((1 << 64) - 1), _stream(stream))
+        _check(rc, "hss_cdf_init")
+        return self
+
+    def _ws(self, n: int) -> torch.Tensor:
+        nb = int(load().hss_cdf_work_bytes(n))
+        if self._work.numel() < nb:
+            self._work = torch.empty(nb, dtype=torch.uint8, device=self.buf.device)
+        return self._work
+
+    def grad(self, keys, ranks, N: int, stream=None):
+        """(gradient[1153], loss) at the current parameters."""
+        keys = _as_key_tensor(keys)
+        ranks = ranks.contiguous()
+        n = keys.numel()
+        g = torch.empty(CDF_NPARAM, dtype=torch.float32, device=self.buf.device)
+        loss = torch.empty(1, dtype=torch.float32, device=self.buf.device)
+        ws = self._ws(n)
+        rc = load().hss_cdf_grad(_ptr(self.buf), _ptr(keys), _ptr(ranks), n, N, _ptr(g), _ptr(loss), _ptr(ws),
+                                 ws.numel(), _stream(stream))
+        _check(rc, "hss_cdf_grad")
+        return g, loss
+
+    def train(self, keys, ranks, N: int, steps: int, lr: float = 0.01, stream=None) -> torch.Tensor:
+        keys = _as_key_tensor(keys)
+        ranks = ranks.contiguous()
+        n = keys.numel()
+        loss = torch.empty(1, dtype=torch.float32, device=self.buf.device)
+        ws = self._ws(n)
+        rc = load().hss_cdf_train(_ptr(self.buf), _ptr(keys), _ptr(ranks), n, N, steps, float(lr), _ptr(loss),
+                                  _ptr(ws), ws.numel(), _stream(stream))
+        _check(rc, "hss_cdf_train")
+        return loss
+
+    def eval(self, keys, stream=None) -> torch.Tensor:
+        keys = _as_key_tensor(keys)
+        y = torch.empty(keys.numel(), dtype=torch.float32, device=self.buf.device)
+        rc = load().hss_cdf_eval(_ptr(self.buf), _ptr(keys), keys.numel(), _ptr(y), _stream(stream))
+        _check(rc, "hss_cdf_eval")
+        return y
+
+    def propose(self, p: int, per_splitter: int = 1, delta: float = 0.0, stream=None) -> torch.Tensor:
+        out = torch.empty(max(p - 1, 0) * per_splitter, dtype=torch.int64, device=self.buf.device)
+        rc = load().hss_cdf_propose(_ptr(self.buf), p, per_splitter, float(delta), _ptr(out), _stream(stream))
+        _check(rc, "hss_cdf_propose")
+        return out
+
+
+def training_pairs(res: "Result"):
+    """(keys, ranks) training points of the CDF network from an HSS result:
+    every final splitter that is an input key or a proposed cut, with its
+    exact rank chi(i) (offsets[i+1]).  Sentinel splitters are dropped."""
+    spl = res.splitters
+    seg = (spl[:, 1] & 0xFFFFFFFF).to(torch.int32)
+    keep = seg >= -1
+    return spl[:, 0][keep].contiguous(), res.offsets[1:-1][keep].contiguous()
