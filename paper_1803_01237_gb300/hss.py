@@ -21,7 +21,8 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libhss.so")
 
 HSS_OK = 0
 ERRORS = {-1: "HSS_ERR_INVALID", -2: "HSS_ERR_WORKSPACE", -3: "HSS_ERR_ROUND_LIMIT", -4: "HSS_ERR_TIMEOUT",
-          -5: "HSS_ERR_CUDA", -6: "HSS_ERR_CAPACITY"}
+          -5: "HSS_ERR_CUDA", -6: "HSS_ERR_CAPACITY", -7: "HSS_ERR_NOALLOC_LIMIT"}
+ERR_INVALID, ERR_WORKSPACE, ERR_ROUND_LIMIT, ERR_TIMEOUT, ERR_CUDA, ERR_CAPACITY = -1, -2, -3, -4, -5, -6
 KEY_TYPES = {"u64": 0, "i64": 1}
 OP = {"sort": 0, "partition": 1, "local_sort": 2, "merge": 3, "exchange": 4, "sort_host": 5}
 FLAG_SYNC = 1
