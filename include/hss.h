@@ -219,6 +219,60 @@ int hss_local_sort_noalloc(const void* d_keys, const uint32_t* d_payload, int ke
                            void* d_keys_out, uint32_t* d_payload_out, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Batches of independent jobs.
+ *
+ * Job j is the n_j = h_sizes[j] keys following job j-1 in d_keys (job 0
+ * starts at 0), split over p_j = h_p[j] processors (1 <= p_j <= max(n_j, 1),
+ * p_j <= 65536).  Each job gets exactly what hss_sort (hss_partition) would
+ * compute for it alone with params prm and seed prm->seed + j; the jobs run
+ * together: one segmented local sort over the segments of all jobs, rounds in
+ * lock step (a job stops sampling once its splitters are resolved or it
+ * fails), one exchange and one merge over all buckets.  A round costs one
+ * 16-byte device-to-host read for the whole batch.
+ *
+ * Outputs, job-major: d_splitters[sum (p_j - 1)], d_offsets[sum (p_j + 1)]
+ * (relative to the job's first key, chi(0) = 0 .. chi(p_j) = n_j), and for
+ * hss_sort_batch the sorted keys (payload) of every job in its own range.
+ * h_job_stats (host, nullable, njobs entries) receives each job's round
+ * statistics.  The return value is the first failing job's code (or a
+ * device error), HSS_OK when every job succeeded.  Synchronous.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    uint32_t rounds;                          /* histogram rounds of this job */
+    int32_t status;                           /* HSS_OK or the job's error */
+    uint64_t tol;                             /* floor(n eps / (2p)) */
+    uint64_t sample_size[HSS_MAX_ROUNDS];
+    uint64_t gamma[HSS_MAX_ROUNDS];
+    uint64_t unresolved[HSS_MAX_ROUNDS + 1];
+} hss_job_stats;
+
+typedef struct {
+    uint32_t njobs;
+    uint32_t max_rounds;       /* most rounds any job took */
+    uint32_t lockstep_rounds;  /* rounds the batch ran */
+    int32_t status;
+    uint64_t total_samples;    /* probes drawn over all jobs and rounds */
+    uint64_t total_keys;
+    uint32_t total_segments;
+    uint32_t kernel_launches;
+    float ms_phase[HSS_NUM_PHASES];  /* with HSS_FLAG_TIMING */
+} hss_batch_stats;
+
+/* Workspace bytes of hss_sort_batch (sort = 1) or hss_partition_batch
+ * (sort = 0); 0 for invalid job lists. */
+size_t hss_batch_workspace_bytes(const uint64_t* h_sizes, const uint32_t* h_p, uint32_t njobs, const hss_params* prm,
+                                 int key_type, int has_payload, int sort);
+
+int hss_sort_batch(const void* d_keys, const uint32_t* d_payload, int key_type, const uint64_t* h_sizes,
+                   const uint32_t* h_p, uint32_t njobs, const hss_params* prm, void* d_keys_out, uint32_t* d_payload_out,
+                   hss_cut* d_splitters, uint64_t* d_offsets, void* d_work, size_t work_bytes, hss_batch_stats* h_stats,
+                   hss_job_stats* h_job_stats, void* stream);
+
+int hss_partition_batch(const void* d_keys, int key_type, const uint64_t* h_sizes, const uint32_t* h_p, uint32_t njobs,
+                        const hss_params* prm, hss_cut* d_splitters, uint64_t* d_offsets, void* d_work,
+                        size_t work_bytes, hss_batch_stats* h_stats, hss_job_stats* h_job_stats, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Learned splitter proposal: a 1-32-32-1 CDF network of the keys.
  *
  * The paper proposes no model; its rounds (Sec. 4.2.2) take any candidate

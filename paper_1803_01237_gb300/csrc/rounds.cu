@@ -21,6 +21,7 @@
 //            |gamma| and the next threshold are computed on the device.
 // The host reads one small status record per round.
 #include "rounds.cuh"
+#include "rounds_dev.cuh"
 
 #include <cmath>
 #include <algorithm>
@@ -103,48 +104,6 @@ RoundWs rounds_ws_carve(void* base, uint64_t N, uint64_t p, uint64_t cap, uint32
 }
 
 // ---------------------------------------------------------------------------
-// Block scans (blockDim a multiple of 32, at most 1024).
-// ---------------------------------------------------------------------------
-template <typename T, typename Op>
-__device__ __forceinline__ T warp_incl_scan(T x, Op op) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        T y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x = op(x, y);
-    }
-    return x;
-}
-
-// Inclusive block scan with identity `id`; returns the inclusive value and
-// sets `total`.  Uses s_warp[32] of T.
-template <typename T, typename Op>
-__device__ __forceinline__ T block_incl_scan(T v, T id, Op op, T* s_warp, T& total) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    T x = warp_incl_scan(v, op);
-    if (lane == 31) s_warp[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        T y = lane < nw ? s_warp[lane] : id;
-        y = warp_incl_scan(y, op);
-        s_warp[lane] = y;
-    }
-    __syncthreads();
-    T r = w > 0 ? op(s_warp[w - 1], x) : x;
-    total = s_warp[nw - 1];
-    __syncthreads();
-    return r;
-}
-
-struct AddU32 { __device__ uint32_t operator()(uint32_t a, uint32_t b) const { return a + b; } };
-struct AddU64 { __device__ uint64_t operator()(uint64_t a, uint64_t b) const { return a + b; } };
-struct MaxI32 { __device__ int32_t operator()(int32_t a, int32_t b) const { return a > b ? a : b; } };
-
-__device__ __forceinline__ uint64_t ideal_rank(uint64_t i1, uint64_t N, uint64_t p) {
-    return (uint64_t)(((unsigned __int128)i1 * N) / p);  // t_i for splitter number i1 (1-based)
-}
-
-// ---------------------------------------------------------------------------
 // Initial state: every splitter interval is (-inf, +inf).
 // ---------------------------------------------------------------------------
 __global__ void k_rounds_init(const uint64_t* __restrict__ seg_off, uint32_t S, uint64_t N, DCut* Lcut, DCut* Ucut,
@@ -171,124 +130,20 @@ __global__ __launch_bounds__(1024) void k_intervals(uint32_t S, uint64_t N, uint
                                                     const DCut* __restrict__ Lcut, const DCut* __restrict__ Ucut,
                                                     uint32_t* __restrict__ res, uint32_t* __restrict__ int_rep,
                                                     RoundCtl* ctl) {
-    __shared__ uint32_t s_u32[32];
-    __shared__ int32_t s_i32[32];
-    __shared__ uint64_t s_u64[32];
-    uint32_t carry_heads = 0, carry_f = 0, carry_unres = 0;
-    int32_t carry_max = -1;
-    uint64_t gamma = 0;
-    for (uint32_t base = 0; base < S; base += blockDim.x) {
-        const uint32_t i = base + threadIdx.x;
-        const bool valid = i < S;
-        uint32_t head = 0, unres = 0;
-        uint64_t glen = 0;
-        if (valid) {
-            const DCut L = Lcut[i], U = Ucut[i];
-            const uint64_t t = ideal_rank(i + 1, N, p);
-            const bool r = (t - L.rank) <= tol || (U.rank - t) <= tol;
-            res[i] = r ? 1u : 0u;
-            unres = r ? 0u : 1u;
-            head = (i == 0) || !(cut_equal(L, Lcut[i - 1]) && cut_equal(U, Ucut[i - 1]));
-            glen = U.rank - L.rank - (L.kind == kMember ? 1u : 0u);
-        }
-        uint32_t tot;
-        const uint32_t heads_incl = block_incl_scan<uint32_t>(head, 0u, AddU32(), s_u32, tot) + carry_heads;
-        carry_heads += tot;
-        const int32_t rid = (int32_t)heads_incl - 1;
-        int32_t mtot;
-        const int32_t mv = unres ? rid : -1;
-        int32_t mincl = block_incl_scan<int32_t>(mv, -1, MaxI32(), s_i32, mtot);
-        mincl = mincl > carry_max ? mincl : carry_max;
-        int32_t mexcl = __shfl_up_sync(0xffffffffu, mincl, 1);
-        // lane 0 needs the previous warp's last value
-        __shared__ int32_t s_last[32];
-        if ((threadIdx.x & 31) == 31) s_last[threadIdx.x >> 5] = mincl;
-        __syncthreads();
-        if ((threadIdx.x & 31) == 0) mexcl = (threadIdx.x == 0) ? carry_max : s_last[(threadIdx.x >> 5) - 1];
-        __syncthreads();
-        carry_max = carry_max > mtot ? carry_max : mtot;
-        const uint32_t f = (valid && unres && mexcl != rid) ? 1u : 0u;
-        uint32_t ftot;
-        const uint32_t fincl = block_incl_scan<uint32_t>(f, 0u, AddU32(), s_u32, ftot);
-        if (f) int_rep[carry_f + fincl - 1] = i;
-        carry_f += ftot;
-        uint32_t utot;
-        block_incl_scan<uint32_t>(unres, 0u, AddU32(), s_u32, utot);
-        carry_unres += utot;
-        uint64_t gtot;
-        block_incl_scan<uint64_t>(f ? glen : 0ull, 0ull, AddU64(), s_u64, gtot);
-        gamma += gtot;
-    }
+    IntervalsOut o;
+    intervals_body(S, N, p, tol, oversample, Lcut, Ucut, res, int_rep, o);
     if (threadIdx.x == 0) {
-        ctl->gamma = gamma;
-        ctl->nint = carry_f;
-        ctl->unresolved = carry_unres;
-        double q = gamma == 0 ? 1.0 : ((double)oversample * (double)p) / (double)gamma;
-        if (q >= 1.0) {
-            ctl->take_all = 1u;
-            ctl->T = 0ull;
-        } else {
-            ctl->take_all = 0u;
-            ctl->T = (uint64_t)floor(ldexp(q, 64));
-        }
+        ctl->gamma = o.gamma;
+        ctl->nint = o.nint;
+        ctl->unresolved = o.unresolved;
+        ctl->take_all = o.take_all;
+        ctl->T = o.T;
     }
 }
 
 // ---------------------------------------------------------------------------
 // Sampling.
 // ---------------------------------------------------------------------------
-constexpr int kIntChunk = 2048;
-constexpr int kSampThreads = 256;
-
-// Fill the interval ranges of segment s for intervals [u0, u0+nu) and the
-// exclusive prefix of their position-pair counts.  Returns the pair total.
-__device__ uint32_t load_seg_intervals(uint32_t s, uint32_t n_s, uint32_t S, uint32_t u0, uint32_t nu,
-                                       const uint32_t* __restrict__ Lpos, const uint32_t* __restrict__ Upos,
-                                       const DCut* __restrict__ Lcut, const uint32_t* __restrict__ int_rep,
-                                       uint32_t* s_a, uint32_t* s_b, uint32_t* s_pre, uint32_t* s_warp) {
-    constexpr int kPer = kIntChunk / kSampThreads;
-    uint32_t loc[kPer];
-    uint32_t sum = 0;
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-        const uint32_t u = threadIdx.x * kPer + k;
-        uint32_t np = 0;
-        if (u < nu) {
-            const uint32_t rep = int_rep[u0 + u];
-            const DCut L = Lcut[rep];
-            uint32_t a = Lpos[(uint64_t)s * S + rep];
-            if (L.kind == kMember && (uint32_t)L.seg == s) a += 1;
-            uint32_t b = Upos[(uint64_t)s * S + rep];
-            if (b > n_s) b = n_s;  // defensive: a range never leaves its segment
-            s_a[u] = a;
-            s_b[u] = b;
-            np = b > a ? ((b - 1) >> 1) - (a >> 1) + 1 : 0u;
-        }
-        loc[k] = sum;
-        sum += np;
-    }
-    uint32_t tot;
-    const uint32_t incl = block_incl_scan<uint32_t>(sum, 0u, AddU32(), s_warp, tot);
-    const uint32_t ex = incl - sum;
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-        const uint32_t u = threadIdx.x * kPer + k;
-        if (u < nu) s_pre[u] = ex + loc[k];
-    }
-    if (threadIdx.x == 0) s_pre[nu] = tot;
-    __syncthreads();
-    return tot;
-}
-
-__device__ __forceinline__ uint32_t find_interval(const uint32_t* s_pre, uint32_t nu, uint32_t f) {
-    uint32_t lo = 0, hi = nu;  // last u with s_pre[u] <= f
-    while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (s_pre[mid] <= f) lo = mid; else hi = mid;
-    }
-    return lo;
-}
-
 __global__ __launch_bounds__(kSampThreads) void k_sample_mark(
     const uint64_t* __restrict__ seg_off, uint32_t S, const uint32_t* __restrict__ Lpos, const uint32_t* __restrict__ Upos,
     const DCut* __restrict__ Lcut, const uint32_t* __restrict__ int_rep, const RoundCtl* __restrict__ ctl,
@@ -419,19 +274,6 @@ __global__ void k_probe_build(uint64_t Z, const uint64_t* __restrict__ skey_sort
     pint[k] = lo;
 }
 
-// Count of keys in a[0..n) below key: strict (<) or not (<=), branch-free.
-__device__ __forceinline__ uint32_t count_below(const uint64_t* __restrict__ a, uint32_t n, uint64_t key, bool strict) {
-    uint32_t base = 0;
-    while (n > 0) {
-        const uint32_t half = n >> 1;
-        const uint64_t v = a[base + half];
-        const bool go = strict ? (v < key) : (v <= key);
-        base = go ? base + half + 1 : base;
-        n = go ? n - half - 1 : half;
-    }
-    return base;
-}
-
 constexpr int kHistSegPerBlock = 64;
 
 __global__ __launch_bounds__(256) void k_histogram(
@@ -505,10 +347,6 @@ __global__ void k_prop_probes(uint32_t nprop, const uint64_t* __restrict__ okey_
 // ---------------------------------------------------------------------------
 // L/U update of every splitter from the ranked probes.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void offer(DCut& L, DCut& U, int32_t& cl, int32_t& cu, uint64_t t, const DCut& c, int32_t k) {
-    if (c.rank <= t && (c.rank > L.rank || (c.rank == L.rank && cut_less(c, L)))) { L = c; cl = k; }
-    if (c.rank >= t && (c.rank < U.rank || (c.rank == U.rank && cut_less(c, U)))) { U = c; cu = k; }
-}
 
 // Probes of one launch are all input keys (kind kMember, distinct ranks) or
 // all proposed non-member cuts (kind kNonMember), whose ranks may repeat: then

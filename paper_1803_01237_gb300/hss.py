@@ -500,3 +500,121 @@ def training_pairs(res: "Result"):
     seg = (spl[:, 1] & 0xFFFFFFFF).to(torch.int32)
     keep = seg >= -1
     return spl[:, 0][keep].contiguous(), res.offsets[1:-1][keep].contiguous()
+
+
+# ---------------------------------------------------------------------------
+# Batches of independent jobs (hss_sort_batch / hss_partition_batch)
+# ---------------------------------------------------------------------------
+class JobStats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_uint32), ("status", ctypes.c_int32), ("tol", ctypes.c_uint64),
+                ("sample_size", ctypes.c_uint64 * MAX_ROUNDS), ("gamma", ctypes.c_uint64 * MAX_ROUNDS),
+                ("unresolved", ctypes.c_uint64 * (MAX_ROUNDS + 1))]
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("njobs", ctypes.c_uint32), ("max_rounds", ctypes.c_uint32), ("lockstep_rounds", ctypes.c_uint32),
+                ("status", ctypes.c_int32), ("total_samples", ctypes.c_uint64), ("total_keys", ctypes.c_uint64),
+                ("total_segments", ctypes.c_uint32), ("kernel_launches", ctypes.c_uint32),
+                ("ms_phase", ctypes.c_float * NUM_PHASES)]
+
+
+@dataclass
+class BatchResult:
+    keys: torch.Tensor | None
+    payload: torch.Tensor | None
+    splitters: torch.Tensor      # (sum (p_j - 1), 2) packed hss_cut records, job-major
+    offsets: torch.Tensor        # (sum (p_j + 1),) job-relative offsets, job-major
+    sizes: list
+    ps: list
+    status: int
+    job_rounds: list
+    job_sample_size: list
+    job_gamma: list
+    job_unresolved: list
+    job_status: list
+    job_tol: list
+    lockstep_rounds: int
+    total_samples: int
+    kernel_launches: int
+    ms_phase: dict
+
+    def job_offsets(self, j: int) -> torch.Tensor:
+        o = sum(p + 1 for p in self.ps[:j])
+        return self.offsets[o:o + self.ps[j] + 1]
+
+    def job_splitters(self, j: int) -> torch.Tensor:
+        o = sum(p - 1 for p in self.ps[:j])
+        return self.splitters[o:o + self.ps[j] - 1]
+
+
+def _batch(keys, sizes, ps, eps, seed, payload, oversample, max_rounds, key_type, flags, sort, out, out_payload,
+           stream):
+    lib = load()
+    if not hasattr(lib, "_batch_bound"):
+        P, U64, U32, I32, SZ = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_size_t
+        lib.hss_batch_workspace_bytes.argtypes = [P, P, U32, ctypes.POINTER(Params), I32, I32, I32]
+        lib.hss_batch_workspace_bytes.restype = SZ
+        lib.hss_sort_batch.argtypes = [P, P, I32, P, P, U32, ctypes.POINTER(Params), P, P, P, P, P, SZ,
+                                       ctypes.POINTER(BatchStats), P, P]
+        lib.hss_sort_batch.restype = I32
+        lib.hss_partition_batch.argtypes = [P, I32, P, P, U32, ctypes.POINTER(Params), P, P, P, SZ,
+                                            ctypes.POINTER(BatchStats), P, P]
+        lib.hss_partition_batch.restype = I32
+        lib._batch_bound = True
+    keys = _as_key_tensor(keys)
+    sizes = np.ascontiguousarray(np.asarray(sizes, dtype=np.uint64))
+    ps = np.ascontiguousarray(np.asarray(ps, dtype=np.uint32))
+    nj = int(sizes.shape[0])
+    if int(sizes.sum()) != keys.numel():
+        raise ValueError("the job sizes must add up to the number of keys")
+    prm = _params(1, eps, seed, oversample, max_rounds, flags)
+    nb = int(lib.hss_batch_workspace_bytes(_ptr(sizes), _ptr(ps), nj, ctypes.byref(prm), KEY_TYPES[key_type],
+                                           int(payload is not None), int(sort)))
+    if nb == 0:
+        raise HSSError(ERR_INVALID, "hss_batch_workspace_bytes")
+    ws = workspace(nb, keys.device)
+    S_tot = int((ps.astype(np.int64) - 1).sum())
+    O_tot = int((ps.astype(np.int64) + 1).sum())
+    spl = torch.empty((max(S_tot, 1), 2), dtype=torch.int64, device=keys.device)
+    off = torch.empty(O_tot, dtype=torch.int64, device=keys.device)
+    st = BatchStats()
+    js = (JobStats * nj)()
+    if sort:
+        if out is None:
+            out = torch.empty_like(keys)
+        if payload is not None and out_payload is None:
+            out_payload = torch.empty_like(payload)
+        rc = lib.hss_sort_batch(_ptr(keys), _ptr(payload), KEY_TYPES[key_type], _ptr(sizes), _ptr(ps), nj,
+                                ctypes.byref(prm), _ptr(out), _ptr(out_payload), _ptr(spl), _ptr(off), _ptr(ws),
+                                ws.numel(), ctypes.byref(st), js, _stream(stream))
+    else:
+        rc = lib.hss_partition_batch(_ptr(keys), KEY_TYPES[key_type], _ptr(sizes), _ptr(ps), nj, ctypes.byref(prm),
+                                     _ptr(spl), _ptr(off), _ptr(ws), ws.numel(), ctypes.byref(st), js,
+                                     _stream(stream))
+    if rc in (ERR_INVALID, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT):
+        raise HSSError(rc, "hss_sort_batch" if sort else "hss_partition_batch")
+    return BatchResult(
+        keys=out if sort else None, payload=out_payload if sort else None, splitters=spl[:S_tot], offsets=off,
+        sizes=[int(x) for x in sizes], ps=[int(x) for x in ps], status=rc,
+        job_rounds=[int(x.rounds) for x in js], job_status=[int(x.status) for x in js],
+        job_tol=[int(x.tol) for x in js],
+        job_sample_size=[[int(v) for v in x.sample_size[:x.rounds]] for x in js],
+        job_gamma=[[int(v) for v in x.gamma[:x.rounds]] for x in js],
+        job_unresolved=[[int(v) for v in x.unresolved[:x.rounds + 1]] for x in js],
+        lockstep_rounds=int(st.lockstep_rounds), total_samples=int(st.total_samples),
+        kernel_launches=int(st.kernel_launches),
+        ms_phase={PHASES[i]: float(st.ms_phase[i]) for i in range(NUM_PHASES)})
+
+
+def sort_batch(keys, sizes, ps, eps: float, seed: int, payload=None, oversample: float = 5.0, max_rounds: int = 0,
+               key_type: str = "u64", flags: int = 0, out=None, out_payload=None, stream=None) -> BatchResult:
+    """hss_sort of every job of a batch (job j: the next sizes[j] keys, ps[j]
+    processors, seed + j), all jobs together."""
+    return _batch(keys, sizes, ps, eps, seed, payload, oversample, max_rounds, key_type, flags, True, out,
+                  out_payload, stream)
+
+
+def partition_batch(keys, sizes, ps, eps: float, seed: int, oversample: float = 5.0, max_rounds: int = 0,
+                    key_type: str = "u64", flags: int = 0, stream=None) -> BatchResult:
+    """hss_partition of every job of a batch, all jobs together."""
+    return _batch(keys, sizes, ps, eps, seed, None, oversample, max_rounds, key_type, flags, False, None, None, stream)
