@@ -314,6 +314,126 @@ def run_gpu(args):
     return 0
 
 
+def run_batch_workload(args):
+    """Config 4: 4096 independent int64 sort jobs, sizes log-uniform in
+    [2^10, 2^22], p = max(4, n / 2^14), eps = 0.05, each uniform or Zipf(1.1)
+    over 2^16 values by a seeded coin.  A step is one hss_sort_batch call over
+    all jobs; the plain form (one hss_sort call per job, in order) is timed
+    once on the same jobs for comparison."""
+    import numpy as np
+    import torch
+    from paper_1803_01237_gb300 import hss, inputs
+
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    hss.load()
+    njobs = args.batch_jobs
+    jobs, kinds = inputs.batch_jobs(njobs, 4, lo_log2=10, hi_log2=22, zipf_s=1.1, zipf_distinct=1 << 16)
+    sizes = [len(x) for x in jobs]
+    ps = [max(1, min(n, max(4, n >> 14))) for n in sizes]
+    keys = torch.from_numpy(np.concatenate(jobs)).to(dev)
+    del jobs
+    out = torch.empty_like(keys)
+    eps, seed = 0.05, 1
+    for _ in range(args.warmup):
+        hss.sort_batch(keys, sizes, ps, eps, seed, key_type="i64", out=out)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = hss.launch_count()
+    ev0.record()
+    for _ in range(args.steps):
+        r = hss.sort_batch(keys, sizes, ps, eps, seed, key_type="i64", out=out)
+    ev1.record()
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    launches = hss.launch_count() - l0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ok = all(s == 0 for s in r.job_status)
+    rounds_b = float(np.mean(r.job_rounds))
+    # plain form: one hss_sort per job (the single-call path), same jobs
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    rounds_p = []
+    for j in range(njobs):
+        kj = keys[int(offs[j]):int(offs[j + 1])]
+        rr = hss.sort(kj, ps[j], eps, seed + j, key_type="i64", out=out[int(offs[j]):int(offs[j + 1])])
+        rounds_p.append(rr.rounds)
+    torch.cuda.synchronize(dev)
+    plain_s = time.perf_counter() - t0
+    line = {
+        "metric": "batched jobs/s (HSS sort of independent int64 jobs)", "value": njobs / (ms / 1000.0),
+        "unit": "jobs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"batched HSS sort: {njobs} int64 jobs, sizes log-uniform [2^10, 2^22], "
+                               "p = max(4, n/2^14), eps = 0.05, uniform or Zipf(1.1) over 2^16 values by a seeded coin",
+                   "jobs": njobs, "keys": int(offs[-1]), "segments": int(sum(ps)),
+                   "l2": "inputs larger than L2; no flush"},
+        "keys_per_s": offs[-1] / (ms / 1000.0),
+        "mean_rounds_per_job": rounds_b, "lockstep_rounds": r.lockstep_rounds, "all_jobs_ok": ok,
+        "phase_ms": r.ms_phase, "gpu_launches": launches,
+        "plain_form": {"jobs_per_s": njobs / plain_s, "keys_per_s": offs[-1] / plain_s, "seconds": plain_s,
+                       "mean_rounds_per_job": float(np.mean(rounds_p)),
+                       "api": "hss_sort per job, host loop, same stream"},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve_workload(args):
+    """Config 5: Poisson arrivals at 2000 partition requests/s, sizes
+    log-uniform in [2^16, 2^26], p in {256, 1024, 4096}, eps = 0.02,
+    lognormal(0, 2) keys on one 2^63 scale; the CDF network trains online on
+    completed jobs and proposes the first cuts of later ones (plain HSS until
+    it is ready).  Keys are device-resident slices of four lognormal pools."""
+    import numpy as np
+    import torch
+    from paper_1803_01237_gb300 import hss, inputs, serve
+
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    hss.load()
+    pool = [torch.from_numpy(inputs.lognormal_job(1 << 26, 500 + b).view(np.int64)).to(dev) for b in range(4)]
+    reqs = serve.poisson_requests(pool, args.serve_requests, rate=args.serve_rate, seed=7, lo_log2=16, hi_log2=26,
+                                  ps=(256, 1024, 4096), eps=0.02)
+    results = {}
+    low_rate = args.serve_low_rate
+    low_reqs = serve.poisson_requests(pool, max(1, min(args.serve_requests, int(low_rate * 5))), rate=low_rate,
+                                      seed=8, lo_log2=16, hi_log2=26, ps=(256, 1024, 4096), eps=0.02)
+    for rate_name, rr in (("offered", reqs), ("sustainable", low_reqs)):
+        for mode in ("plain", "learned"):
+            model = hss.CDFModel(dev).init(3, "log", 1, (1 << 63) - 1) if mode == "learned" else None
+            srv = serve.Server(slots=args.serve_slots, model=model, train=True, train_steps=50, train_interval=0.05)
+            srv.warmup()
+            torch.cuda.synchronize(dev)
+            clocks = ClockSampler(local)
+            clocks.start()
+            st = srv.run(rr, realtime=True)
+            clk = clocks.stop()
+            srv.close()
+            summ = st.summary()
+            summ["rate_per_s"] = args.serve_rate if rate_name == "offered" else low_rate
+            summ["clocks"] = clk
+            results[f"{rate_name}_{mode}"] = summ
+    s_l = results["offered_learned"]
+    line = {
+        "metric": "served partition requests: p99 latency", "value": s_l["p99_ms"], "unit": "ms", "n_gpus": 1,
+        "steps": args.serve_requests, "warmup": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"served HSS partitions: Poisson {args.serve_rate:g}/s, {args.serve_requests} requests, "
+                               "sizes log-uniform [2^16, 2^26], p in {256, 1024, 4096}, eps = 0.02, lognormal(0,2) keys",
+                   "slots": args.serve_slots, "sustainable_rate_per_s": low_rate},
+        "runs": results,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -325,7 +445,19 @@ def main():
     ap.add_argument("--uniform-only", action="store_true", help="time the uniform input only")
     ap.add_argument("--log2n", type=int, default=None,
                     help="smaller case of the same kernels (keeps 2^18 keys per segment); for profiling only")
+    ap.add_argument("--workload", default="sort", choices=["sort", "batch", "serve"],
+                    help="sort: the N=2^28 bench line (default); batch: 4096 independent jobs; serve: Poisson requests")
+    ap.add_argument("--batch-jobs", type=int, default=4096)
+    ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-low-rate", type=float, default=300.0)
     args = ap.parse_args()
+    if args.workload == "batch" and args.impl == "gb300":
+        args.warmup = max(args.warmup, 1)
+        return run_batch_workload(args)
+    if args.workload == "serve" and args.impl == "gb300":
+        return run_serve_workload(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.log2n is not None:

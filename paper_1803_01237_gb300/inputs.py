@@ -208,19 +208,23 @@ def batch_jobs(njobs: int, seed: int, lo_log2: int = 10, hi_log2: int = 22, zipf
                zipf_distinct: int = 1 << 16):
     """Independent int64 jobs with sizes log-uniform in [2^lo, 2^hi]; each is
     uniform or Zipf by a seeded coin.  Returns (list of int64 arrays, kinds)."""
+    from concurrent.futures import ThreadPoolExecutor
+    import os
+
     g = rng(seed, 9)
     u = g.random(njobs)
     sizes = np.floor(2.0 ** (lo_log2 + (hi_log2 - lo_log2) * u)).astype(np.int64)
     coin = g.random(njobs) < 0.5
-    jobs, kinds = [], []
-    for j in range(njobs):
+    kinds = ["uniform" if coin[j] else "zipf" for j in range(njobs)]
+
+    def one(j):  # every job draws from its own streams: generated on all host cores
         n = int(sizes[j])
         if coin[j]:
-            jobs.append(uniform(n, seed * 1000003 + j).view(np.int64))
-            kinds.append("uniform")
-        else:
-            jobs.append(zipf(n, seed * 1000003 + j, distinct=zipf_distinct, s=zipf_s).view(np.int64))
-            kinds.append("zipf")
+            return uniform(n, seed * 1000003 + j).view(np.int64)
+        return zipf(n, seed * 1000003 + j, distinct=zipf_distinct, s=zipf_s).view(np.int64)
+
+    with ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1))) as ex:
+        jobs = list(ex.map(one, range(njobs)))
     return jobs, kinds
 
 

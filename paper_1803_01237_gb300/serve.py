@@ -103,8 +103,10 @@ class _Trainer:
     SCALE = 1 << 40
 
     def __init__(self, model: hss.CDFModel, lock: threading.Lock, steps: int, lr: float, keep_jobs: int,
-                 min_jobs: int, device):
+                 min_jobs: int, device, interval: float = 0.0):
         self.model, self.lock, self.steps, self.lr = model, lock, steps, lr
+        self.interval = interval
+        self.last_train = -1e9
         self.keep_jobs, self.min_jobs = keep_jobs, min_jobs
         self.stream = torch.cuda.Stream(device=device)
         self.shadow = hss.CDFModel(device)
@@ -132,6 +134,12 @@ class _Trainer:
         stop = False
         while not stop:
             items = [self.q.get()]
+            if items[0] is not None and self.ready:
+                # at most one run per interval once the model is serving:
+                # training shares the GPU with the requests
+                wait = self.interval - (time.perf_counter() - self.last_train)
+                if wait > 0:
+                    time.sleep(wait)
             while True:  # every completion queued meanwhile joins this run
                 try:
                     items.append(self.q.get_nowait())
@@ -160,6 +168,7 @@ class _Trainer:
                     self.loss = float(loss.item())
                     self.trainings += 1
                     self.ready = True
+                self.last_train = time.perf_counter()
 
 
 class Server:
@@ -170,11 +179,12 @@ class Server:
     model          CDF network to train online and propose from (None: plain)
     per_splitter   proposed cuts per splitter; delta = 3 sqrt(training loss)
     train          whether completed jobs train the model (False: frozen)
+    train_interval seconds between training runs once the model serves
     """
 
     def __init__(self, slots: int = 4, hbm_budget: int | None = None, model: hss.CDFModel | None = None,
                  per_splitter: int = 16, train: bool = True, train_steps: int = 100, lr: float = 0.01,
-                 keep_jobs: int = 16, min_jobs: int = 2, device=None):
+                 keep_jobs: int = 16, min_jobs: int = 2, train_interval: float = 0.0, device=None):
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.slots = slots
         self.hbm_budget = hbm_budget
@@ -184,7 +194,8 @@ class Server:
         self.trainer = None
         self.frozen_ready = model is not None and not train
         if model is not None and train:
-            self.trainer = _Trainer(model, self.model_lock, train_steps, lr, keep_jobs, min_jobs, self.device)
+            self.trainer = _Trainer(model, self.model_lock, train_steps, lr, keep_jobs, min_jobs, self.device,
+                                    train_interval)
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
         self.slot_ws = [None] * slots
         self.cv = threading.Condition()
@@ -267,6 +278,13 @@ class Server:
         once (a closed loop)."""
         stats = ServeStats()
         reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        # work the caller queued before this call (the keys, a model trained
+        # on the current stream) comes first on every stream the server uses
+        cur = torch.cuda.current_stream(self.device)
+        for st in self.streams:
+            st.wait_stream(cur)
+        if self.trainer is not None:
+            self.trainer.stream.wait_stream(cur)
         threads = []
         t0 = time.perf_counter()
         for req in reqs:
@@ -307,6 +325,9 @@ class Server:
         it was."""
         n = 1 << 14
         keys = torch.arange(n, dtype=torch.int64, device=self.device) * 7919
+        cur = torch.cuda.current_stream(self.device)
+        for st in self.streams:
+            st.wait_stream(cur)
         req = Request(rid=-1, arrival=0.0, keys=keys, p=16, eps=0.05, seed=1, key_type=key_type)
         for slot in range(self.slots):
             stream = self.streams[slot]
