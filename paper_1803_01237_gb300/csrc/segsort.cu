@@ -53,15 +53,15 @@ size_t segsort_ws_bytes(uint64_t N, uint64_t nseg) {
     size_t b = 0;
     b += align_up((d.list + 1) * 4, 256) + align_up(d.list * 4, 256);  // tile_start, large_id
     b += align_up(d.ml * 4, 256);                                     // large_seg
-    b += align_up(d.ml * 8 * kRadix * 4, 256);                        // hist
+    b += align_up(d.ml * 2 * kRadix * 4, 256);                        // hist
     b += 2 * align_up(d.ml * 8, 256);                                 // vor, vand
     b += align_up(d.ml * kRadix * 4, 256);                            // msd_off
-    b += 2 * align_up(d.ml * 4, 256);                                 // msd_shift, direct
+    b += 4 * align_up(d.ml * 4, 256);                                 // msd_shift x2, spec, direct
     b += 2 * align_up(d.ml * 8, 256);                                 // msd_base, msd_mult
     b += 4 * align_up(d.ml * kRadix * 8, 256);                        // sub_lo/hi x2
     b += align_up(d.tiles * kRadix * 4, 256);                         // status
     b += align_up(64 * 4, 256);                                       // counters
-    b += 4 * align_up(d.list * 4, 256);                               // class lists, fallback list
+    b += 5 * align_up(d.list * 4, 256);                               // class lists, fallback, slow lists
     b += align_up(8 * (d.list / 1024 + 2) * 4, 256);                  // blk
     return b;
 }
@@ -77,11 +77,13 @@ SegSortWs segsort_ws_carve(void* base, uint64_t N, uint64_t nseg, uint32_t* err)
     w.tile_start = (uint32_t*)take((d.list + 1) * 4);
     w.large_id = (uint32_t*)take(d.list * 4);
     w.large_seg = (uint32_t*)take(d.ml * 4);
-    w.hist = (uint32_t*)take(d.ml * 8 * kRadix * 4);
+    w.hist = (uint32_t*)take(d.ml * 2 * kRadix * 4);
     w.vor = (unsigned long long*)take(d.ml * 8);
     w.vand = (unsigned long long*)take(d.ml * 8);
     w.msd_off = (uint32_t*)take(d.ml * kRadix * 4);
-    w.msd_shift = (uint32_t*)take(d.ml * 4);
+    w.msd_shift[0] = (uint32_t*)take(d.ml * 4);
+    w.msd_shift[1] = (uint32_t*)take(d.ml * 4);
+    w.spec = (uint32_t*)take(d.ml * 4);
     w.direct = (uint32_t*)take(d.ml * 4);
     w.msd_base = (uint64_t*)take(d.ml * 8);
     w.msd_mult = (uint64_t*)take(d.ml * 8);
@@ -93,6 +95,7 @@ SegSortWs segsort_ws_carve(void* base, uint64_t N, uint64_t nseg, uint32_t* err)
     w.counters = (uint32_t*)take(64 * 4);
     for (int i = 0; i < 3; ++i) w.list[i] = (uint32_t*)take(d.list * 4);
     w.fb_list = (uint32_t*)take(d.list * 4);
+    w.slow_list = (uint32_t*)take(d.list * 4);
     w.blk = (uint32_t*)take(8 * (d.list / 1024 + 2) * 4);
     w.err = err;
     return w;
@@ -291,10 +294,16 @@ __device__ __forceinline__ void write_sorted(uint64_t* kout, uint32_t* pout, con
     __syncthreads();
 }
 
+// Groups of the counting pass by size class: about two keys per group for
+// the smallest segments (a smaller scan per segment), 1024 groups above that
+// (clustered keys in larger segments would otherwise crowd one group).
+template <int CAP>
+constexpr int chip_radix() { return CAP <= kC0Cap ? 512 : kChipRadix; }
+
 template <int THREADS, int CAP>
 constexpr size_t msd_sort_smem() {
-    return (size_t)CAP * 8 + 3 * (size_t)CAP * 2 + 2 * (kChipRadix + 1) * 4 + 32 * 4 + 2 * 32 * 8 +
-           (size_t)(THREADS / 32) * kMaxBig * 4 + kChipRadix + 64;
+    return (size_t)CAP * 8 + 3 * (size_t)CAP * 2 + 2 * (chip_radix<CAP>() + 1) * 4 + 32 * 4 + 2 * 32 * 8 +
+           (size_t)(THREADS / 32) * kMaxBig * 4 + chip_radix<CAP>() + 64;
 }
 
 template <bool PAY, int THREADS, int CAP>
@@ -304,18 +313,19 @@ __global__ __launch_bounds__(THREADS) void k_small_msd(
     uint64_t nseg, uint32_t min_n,
     uint32_t max_n, uint64_t flip_in, uint64_t flip_out, uint32_t* __restrict__ fb_list, uint32_t* __restrict__ fb_count) {
     constexpr int WARPS = THREADS / 32;
+    constexpr int R = chip_radix<CAP>();
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* s_keys = (uint64_t*)smem;                        // CAP u64
     uint16_t* s_grp = (uint16_t*)(s_keys + CAP);               // CAP u16: positions grouped by digit
     uint16_t* s_out = s_grp + CAP;                             // CAP u16: positions in sorted order
     uint16_t* s_dig = s_out + CAP;                             // CAP u16: digit of each position
-    uint32_t* s_start = (uint32_t*)(s_dig + CAP);              // kChipRadix+1: counts, then group starts
-    uint32_t* s_run = s_start + (kChipRadix + 1);              // kChipRadix+1: running write positions
-    uint32_t* s_warp = s_run + (kChipRadix + 1);               // 32
+    uint32_t* s_start = (uint32_t*)(s_dig + CAP);              // R+1: counts, then group starts
+    uint32_t* s_run = s_start + (R + 1);              // R+1: running write positions
+    uint32_t* s_warp = s_run + (R + 1);               // 32
     uint64_t* s_red = (uint64_t*)(((uintptr_t)(s_warp + 32) + 7) & ~(uintptr_t)7);  // 2*32
     uint32_t* s_wcnt = (uint32_t*)(s_red + 64);                 // WARPS*kMaxBig: per-warp counts of the big groups
     uint32_t* s_misc = s_wcnt + WARPS * kMaxBig;                // [0] big groups, [1] a big group holds distinct keys
-    uint8_t* s_bigid = (uint8_t*)(s_misc + 2);                  // kChipRadix: index of a big group, 0xff otherwise
+    uint8_t* s_bigid = (uint8_t*)(s_misc + 2);                  // R: index of a big group, 0xff otherwise
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const uint64_t count = list ? (uint64_t)*nlist : nseg;
@@ -338,7 +348,7 @@ __global__ __launch_bounds__(THREADS) void k_small_msd(
             kmax = max(kmax, (uint64_t)__shfl_xor_sync(0xffffffffu, kmax, o));
         }
         if (lane == 0) { s_red[w] = kmin; s_red[32 + w] = kmax; }
-        for (int d = tid; d < kChipRadix; d += THREADS) s_start[d] = 0;
+        for (int d = tid; d < R; d += THREADS) s_start[d] = 0;
         if (tid == 0) { s_misc[0] = 0; s_misc[1] = 0; }
         __syncthreads();
         {
@@ -364,27 +374,27 @@ __global__ __launch_bounds__(THREADS) void k_small_msd(
         // the stable sort.  Any monotone digit gives the same result, so the
         // multiplier only needs to be about 1023 * 2^64 / range.
         const uint64_t range = kmax - kmin;
-        const uint64_t mult = range < (uint64_t)kChipRadix ? 0ull : (uint64_t)(1.8871019187404871e22 / (double)range);
+        const uint64_t mult = range < (uint64_t)R ? 0ull : (uint64_t)((double)(R - 1) * 18446744073709551616.0 / (double)range);
         for (uint32_t e = tid; e < n; e += THREADS) {
             const uint64_t off = s_keys[e] - kmin;
-            const uint32_t d = mult ? min((uint32_t)__umul64hi(off, mult), (uint32_t)kChipRadix - 1) : (uint32_t)off;
+            const uint32_t d = mult ? min((uint32_t)__umul64hi(off, mult), (uint32_t)R - 1) : (uint32_t)off;
             s_dig[e] = (uint16_t)d;
             atomicAdd(&s_start[d], 1u);
         }
         __syncthreads();
         uint32_t mx = 0;
-        for (int d = tid; d < kChipRadix; d += THREADS) mx = max(mx, s_start[d]);
+        for (int d = tid; d < R; d += THREADS) mx = max(mx, s_start[d]);
         mx = __reduce_max_sync(0xffffffffu, mx);
-        scan_smem_inplace<THREADS, kChipRadix>(s_start, s_warp);
+        scan_smem_inplace<THREADS, R>(s_start, s_warp);
         if (lane == 0) s_warp[w] = mx;
-        for (int d = tid; d < kChipRadix; d += THREADS) s_run[d] = s_start[d];
-        if (tid == 0) s_start[kChipRadix] = n;
+        for (int d = tid; d < R; d += THREADS) s_run[d] = s_start[d];
+        if (tid == 0) s_start[R] = n;
         __syncthreads();
         mx = 0;
         for (int i = 0; i < WARPS; ++i) mx = max(mx, s_warp[i]);
         const bool big = mx > (uint32_t)kTinyGroup;  // uniform per CTA
         if (big) {
-            for (int d = tid; d < kChipRadix; d += THREADS)
+            for (int d = tid; d < R; d += THREADS)
                 s_bigid[d] = (s_start[d + 1] - s_start[d] > (uint32_t)kTinyGroup)
                                  ? (uint8_t)min(atomicAdd(&s_misc[0], 1u), 255u) : (uint8_t)0xff;
             __syncthreads();
@@ -467,6 +477,175 @@ __global__ __launch_bounds__(THREADS) void k_small_msd(
             __syncthreads();
         }
         write_sorted<PAY, THREADS, CAP>(kout, pout, pin, base, n, s_keys, s_out, flip_out);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The same on-chip sort for segments of up to CAP = THREADS * ITEMS keys
+// (ITEMS <= 16) with the keys, digits and group slots held in registers:
+// one counting pass on the 10-bit digit, a scatter that stores each key and
+// its input position at its group slot, and a rank only for keys whose group
+// holds more than one key (a singleton's slot is its final position).  About
+// half the shared-memory traffic of k_small_msd.  A segment with a group
+// larger than kTinyGroup is appended to slow_list for k_small_msd.  It runs
+// the middle size class (up to 4096 keys, 256 threads); for the smallest
+// class the shared-memory kernel measured faster (more CTAs per SM).
+// ---------------------------------------------------------------------------
+template <int CAP>
+constexpr size_t reg_sort_smem() {
+    return (size_t)CAP * 8 + (size_t)CAP * 2 + 2 * (kChipRadix + 1) * 4 + 32 * 4 + 2 * 32 * 8 + 64;
+}
+
+template <bool PAY, int THREADS, int CAP>
+__global__ __launch_bounds__(THREADS) void k_small_reg(
+    const uint64_t* kin, uint64_t* kout, const uint32_t* pin, uint32_t* pout, const uint64_t* __restrict__ seg_lo,
+    const uint64_t* __restrict__ seg_hi, const uint32_t* __restrict__ list, const uint32_t* __restrict__ nlist,
+    uint64_t nseg, uint32_t min_n, uint32_t max_n, uint64_t flip_in, uint64_t flip_out,
+    uint32_t* __restrict__ slow_list, uint32_t* __restrict__ slow_count) {
+    constexpr int ITEMS = CAP / THREADS;
+    static_assert(CAP % THREADS == 0 && ITEMS <= 16 && CAP <= 4096 && kChipRadix <= 4096, "register sort shape");
+    constexpr int WARPS = THREADS / 32;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t* s_key = (uint64_t*)smem;                     // CAP: keys by group slot, then in final order
+    uint16_t* s_idx = (uint16_t*)(s_key + CAP);            // CAP: their input positions
+    uint32_t* s_start = (uint32_t*)(s_idx + CAP);          // kChipRadix+1: counts, then group starts
+    uint32_t* s_run = s_start + (kChipRadix + 1);          // kChipRadix+1: running slots
+    uint32_t* s_warp = s_run + (kChipRadix + 1);           // 32
+    uint64_t* s_red = (uint64_t*)(((uintptr_t)(s_warp + 32) + 7) & ~(uintptr_t)7);  // 2*32
+
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const uint64_t count = list ? (uint64_t)*nlist : nseg;
+    for (uint64_t k = blockIdx.x; k < count; k += gridDim.x) {
+        const uint64_t s = list ? (uint64_t)list[k] : k;
+        const uint64_t base = seg_lo[s];
+        const uint64_t n64 = seg_hi[s] - base;
+        if (n64 <= min_n || n64 > max_n) continue;  // uniform per CTA
+        const uint32_t n = (uint32_t)n64;
+        uint64_t key[ITEMS];
+        uint64_t kmin = ~0ull, kmax = 0;
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const uint32_t e = tid + i * THREADS;
+            key[i] = e < n ? kin[base + e] ^ flip_in : 0ull;
+            if (e < n) { kmin = min(kmin, key[i]); kmax = max(kmax, key[i]); }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            kmin = min(kmin, (uint64_t)__shfl_xor_sync(0xffffffffu, kmin, o));
+            kmax = max(kmax, (uint64_t)__shfl_xor_sync(0xffffffffu, kmax, o));
+        }
+        if (lane == 0) { s_red[w] = kmin; s_red[32 + w] = kmax; }
+        for (int d = tid; d < kChipRadix; d += THREADS) s_start[d] = 0;
+        __syncthreads();
+        {
+            uint64_t a = ~0ull, b = 0;
+            for (int i = 0; i < WARPS; ++i) { a = min(a, s_red[i]); b = max(b, s_red[32 + i]); }
+            kmin = a;
+            kmax = b;
+        }
+        if (kmin == kmax) {  // all keys equal: already in order
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                const uint32_t e = tid + i * THREADS;
+                if (e < n) {
+                    kout[base + e] = key[i] ^ flip_out;
+                    if (PAY) pout[base + e] = pin[base + e];
+                }
+            }
+            __syncthreads();
+            continue;
+        }
+        const uint64_t range = kmax - kmin;
+        const uint64_t mult = range < (uint64_t)kChipRadix ? 0ull : (uint64_t)(1.8871019187404871e22 / (double)range);
+        uint32_t dp[ITEMS];  // digit in bits 0..11, group slot from bit 12
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const uint32_t e = tid + i * THREADS;
+            dp[i] = 0;
+            if (e < n) {
+                const uint64_t off = key[i] - kmin;
+                const uint32_t d = mult ? min((uint32_t)__umul64hi(off, mult), (uint32_t)kChipRadix - 1) : (uint32_t)off;
+                dp[i] = d;
+                atomicAdd(&s_start[d], 1u);
+            }
+        }
+        __syncthreads();
+        uint32_t mx = 0;
+        for (int d = tid; d < kChipRadix; d += THREADS) mx = max(mx, s_start[d]);
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        scan_smem_inplace<THREADS, kChipRadix>(s_start, s_warp);
+        if (lane == 0) s_warp[w] = mx;
+        for (int d = tid; d < kChipRadix; d += THREADS) s_run[d] = s_start[d];
+        if (tid == 0) s_start[kChipRadix] = n;
+        __syncthreads();
+        mx = 0;
+        for (int i = 0; i < WARPS; ++i) mx = max(mx, s_warp[i]);
+        if (mx > (uint32_t)kTinyGroup) {  // skewed: the shared-memory kernel takes this segment
+            if (tid == 0) slow_list[atomicAdd(slow_count, 1u)] = (uint32_t)s;
+            __syncthreads();
+            continue;
+        }
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const uint32_t e = tid + i * THREADS;
+            if (e < n) {
+                const uint32_t slot = atomicAdd(&s_run[dp[i]], 1u);
+                s_key[slot] = key[i];
+                s_idx[slot] = (uint16_t)e;
+                dp[i] |= slot << 12;
+            }
+        }
+        __syncthreads();
+        // Final position: the group start plus the keys of the group below
+        // this one in (key, input position) order; a singleton keeps its slot.
+        uint32_t fin[ITEMS];
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const uint32_t e = tid + i * THREADS;
+            fin[i] = dp[i] >> 12;
+            if (e < n) {
+                const uint32_t d = dp[i] & 4095u;
+                const uint32_t a = s_start[d], b = s_start[d + 1];
+                if (b - a > 1u) {
+                    uint32_t r = 0;
+                    for (uint32_t g = a; g < b; ++g) {
+                        const uint64_t ky = s_key[g];
+                        r += (ky < key[i] || (ky == key[i] && s_idx[g] < e)) ? 1u : 0u;
+                    }
+                    fin[i] = a + r;
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const uint32_t e = tid + i * THREADS;
+            if (e < n && fin[i] != (dp[i] >> 12)) {
+                s_key[fin[i]] = key[i];
+                if (PAY) s_idx[fin[i]] = (uint16_t)e;
+            }
+        }
+        __syncthreads();
+        if (PAY) {  // the output may be the input: gather every payload first
+            uint32_t pv[ITEMS];
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                const uint32_t j = tid + i * THREADS;
+                pv[i] = j < n ? pin[base + s_idx[j]] : 0u;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                const uint32_t j = tid + i * THREADS;
+                if (j < n) pout[base + j] = pv[i];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const uint32_t j = tid + i * THREADS;
+            if (j < n) kout[base + j] = s_key[j] ^ flip_out;
+        }
+        __syncthreads();
     }
 }
 
@@ -666,6 +845,7 @@ __global__ __launch_bounds__(1024) void k_plan_scan(uint32_t nblk, uint32_t* __r
         *(unsigned long long*)(counters + 22) = carry.keys;
         counters[0] = 0;   // tile counter of this level's scatter pass
         counters[24] = 0;  // fallback list of this level's on-chip sorts
+        counters[25] = 0;  // segments the register kernels leave to the shared-memory kernel
     }
 }
 
@@ -710,13 +890,18 @@ __device__ __forceinline__ uint32_t find_tile_segment(const uint32_t* __restrict
 // hint, the window histogram) and the OR/AND of the keys, in one read.
 // Grid (#large, split); CTA (id, k) reads the k-th share of segment id.
 // ---------------------------------------------------------------------------
+// msd_shift flag: the split interpolated the key range (no byte is fixed in
+// its sub-buckets).
+constexpr uint32_t kShiftInterp = 0x100u;
+
 __global__ __launch_bounds__(256) void k_seg_stats(const uint64_t* __restrict__ kin, const uint64_t* __restrict__ seg_lo,
                                                    const uint64_t* __restrict__ seg_hi, const uint32_t* __restrict__ large_seg,
                                                    const uint32_t* __restrict__ counters, uint32_t* __restrict__ hist,
                                                    unsigned long long* __restrict__ vor, unsigned long long* __restrict__ vand,
                                                    const uint64_t* __restrict__ hint_lo, const uint64_t* __restrict__ hint_mult,
+                                                   const uint32_t* __restrict__ prev_shift, uint32_t* __restrict__ spec_out,
                                                    uint32_t split, uint64_t flip_in) {
-    __shared__ uint32_t s_h[8 * kRadix];
+    __shared__ uint32_t s_h[kRadix];
     __shared__ unsigned long long s_or[8], s_and[8];
     const uint32_t id = blockIdx.x;
     if (id >= counters[19]) return;
@@ -724,24 +909,30 @@ __global__ __launch_bounds__(256) void k_seg_stats(const uint64_t* __restrict__ 
     const uint64_t lo = seg_lo[s], n = seg_hi[s] - lo;
     const uint64_t per = ceil_div(ceil_div(n, kOsTile), split) * kOsTile;
     const uint64_t a = (uint64_t)blockIdx.y * per;
+    const bool win = hint_lo != nullptr;
+    // Speculative window: the byte below the parent split's window (a
+    // sub-bucket's keys agree on that window and above), the top byte at the
+    // first level.  The recount pass fixes the segments where it is wrong.
+    int spec = 7;
+    if (prev_shift) {
+        const uint32_t ps = prev_shift[s >> 8];
+        spec = (ps & kShiftInterp) ? 7 : (ps >= 8 ? (int)(ps >> 3) - 1 : 0);
+    }
+    if (blockIdx.y == 0 && threadIdx.x == 0) spec_out[id] = (uint32_t)spec;
     if (a >= n) return;
     const uint64_t b = min(n, a + per);
-    const bool win = hint_lo != nullptr;
     const uint64_t hb = win ? hint_lo[s] : 0ull;
     const uint64_t hm = win ? hint_mult[s] : 0ull;
-    for (int i = threadIdx.x; i < 8 * kRadix; i += blockDim.x) s_h[i] = 0;
+    const int sh = 8 * spec;
+    for (int i = threadIdx.x; i < kRadix; i += blockDim.x) s_h[i] = 0;
     __syncthreads();
     unsigned long long o = 0, an = ~0ull;
     for (uint64_t e = a + threadIdx.x; e < b; e += blockDim.x) {
         const uint64_t k = kin[lo + e] ^ flip_in;
         o |= k;
         an &= k;
-        if (win) {
-            atomicAdd(&s_h[split_digit(k, 0, hb, hm)], 1u);
-        } else {
-#pragma unroll
-            for (int p = 0; p < 8; ++p) atomicAdd(&s_h[p * kRadix + ((uint32_t)(k >> (8 * p)) & 255u)], 1u);
-        }
+        const uint32_t d = win ? split_digit(k, 0, hb, hm) : (uint32_t)(k >> sh) & 255u;
+        atomicAdd(&s_h[d], 1u);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -756,9 +947,44 @@ __global__ __launch_bounds__(256) void k_seg_stats(const uint64_t* __restrict__ 
         atomicOr(&vor[id], x);
         atomicAnd(&vand[id], y);
     }
-    uint32_t* g = hist + (uint64_t)id * (8 * kRadix);
-    const int nh = win ? kRadix : 8 * kRadix;
-    for (int i = threadIdx.x; i < nh; i += blockDim.x) {
+    uint32_t* g = hist + (uint64_t)id * (2 * kRadix);
+    for (int i = threadIdx.x; i < kRadix; i += blockDim.x) {
+        const uint32_t c = s_h[i];
+        if (c) atomicAdd(&g[i], c);
+    }
+}
+
+// Recount of the segments whose top varying byte (from the OR/AND of the
+// statistics pass) is not the speculative one: the histogram of that byte
+// into the second row.  Other CTAs return at once.
+__global__ __launch_bounds__(256) void k_seg_recount(const uint64_t* __restrict__ kin, const uint64_t* __restrict__ seg_lo,
+                                                     const uint64_t* __restrict__ seg_hi,
+                                                     const uint32_t* __restrict__ large_seg,
+                                                     const uint32_t* __restrict__ counters, uint32_t* __restrict__ hist,
+                                                     const unsigned long long* __restrict__ vor,
+                                                     const unsigned long long* __restrict__ vand,
+                                                     const uint32_t* __restrict__ spec, uint32_t split, uint64_t flip_in) {
+    __shared__ uint32_t s_h[kRadix];
+    const uint32_t id = blockIdx.x;
+    if (id >= counters[19]) return;
+    const unsigned long long vary = vor[id] ^ vand[id];
+    if (vary == 0ull) return;
+    const uint32_t t = (uint32_t)(63 - __clzll((long long)vary)) >> 3;
+    if (t == spec[id]) return;  // uniform per CTA
+    const uint32_t s = large_seg[id];
+    const uint64_t lo = seg_lo[s], n = seg_hi[s] - lo;
+    const uint64_t per = ceil_div(ceil_div(n, kOsTile), split) * kOsTile;
+    const uint64_t a = (uint64_t)blockIdx.y * per;
+    if (a >= n) return;
+    const uint64_t b = min(n, a + per);
+    const int sh = 8 * (int)t;
+    for (int i = threadIdx.x; i < kRadix; i += blockDim.x) s_h[i] = 0;
+    __syncthreads();
+    for (uint64_t e = a + threadIdx.x; e < b; e += blockDim.x)
+        atomicAdd(&s_h[(uint32_t)((kin[lo + e] ^ flip_in) >> sh) & 255u], 1u);
+    __syncthreads();
+    uint32_t* g = hist + (uint64_t)id * (2 * kRadix) + kRadix;
+    for (int i = threadIdx.x; i < kRadix; i += blockDim.x) {
         const uint32_t c = s_h[i];
         if (c) atomicAdd(&g[i], c);
     }
@@ -773,6 +999,7 @@ __global__ __launch_bounds__(256) void k_msd_prep(const uint64_t* __restrict__ s
                                                   const uint64_t* __restrict__ hint_mult, uint64_t* __restrict__ msd_base,
                                                   uint64_t* __restrict__ msd_mult,
                                                   uint32_t* __restrict__ msd_off, uint32_t* __restrict__ msd_shift,
+                                                  const uint32_t* __restrict__ spec,
                                                   uint32_t* __restrict__ direct, uint64_t* __restrict__ sub_lo,
                                                   uint64_t* __restrict__ sub_hi) {
     __shared__ uint32_t s_c[kRadix], s_x[kRadix], s_warp[32];
@@ -788,12 +1015,12 @@ __global__ __launch_bounds__(256) void k_msd_prep(const uint64_t* __restrict__ s
         mult = hint_mult[s];
         row = 0;
     } else {
-        const uint32_t t = vary ? (uint32_t)(63 - __clzll((long long)vary)) >> 3 : 0u;
+        const uint32_t t = vary ? (uint32_t)(63 - __clzll((long long)vary)) >> 3 : spec[id];
         shift = 8 * t;
-        row = t;
+        row = t == spec[id] ? 0u : 1u;
     }
     const bool dir = vary == 0ull;
-    s_c[threadIdx.x] = hist[((uint64_t)id * 8 + row) * kRadix + threadIdx.x];
+    s_c[threadIdx.x] = hist[((uint64_t)id * 2 + row) * kRadix + threadIdx.x];
     __syncthreads();
     scan256_smem<256>(s_c, s_x, s_warp);
     const uint32_t c = s_c[threadIdx.x], x = s_x[threadIdx.x];
@@ -801,7 +1028,7 @@ __global__ __launch_bounds__(256) void k_msd_prep(const uint64_t* __restrict__ s
     sub_lo[(uint64_t)id * kRadix + threadIdx.x] = dir ? lo : lo + x;
     sub_hi[(uint64_t)id * kRadix + threadIdx.x] = dir ? lo : lo + x + c;
     if (threadIdx.x == 0) {
-        msd_shift[id] = shift;
+        msd_shift[id] = shift | (hint_lo ? kShiftInterp : 0u);
         msd_base[id] = base;
         msd_mult[id] = mult;
         direct[id] = dir ? 1u : 0u;
@@ -837,7 +1064,7 @@ struct SplitArgs {
 };
 
 template <bool PAY>
-__global__ __launch_bounds__(kOsThreads, 3) void k_split(const SplitArgs A) {
+__global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitArgs A) {
     extern __shared__ __align__(16) unsigned char os_smem[];
     uint64_t* s_keys = (uint64_t*)os_smem;            // kOsTile keys
     uint32_t* s_pay = (uint32_t*)(s_keys + kOsTile);  // kOsTile payloads (PAY)
@@ -864,7 +1091,7 @@ __global__ __launch_bounds__(kOsThreads, 3) void k_split(const SplitArgs A) {
     const uint32_t ti = t - A.tile_start[s];
     const uint64_t tile_lo = (uint64_t)ti * kOsTile;
     const uint32_t count = (uint32_t)min((uint64_t)kOsTile, seg_n - tile_lo);
-    const int shift = (int)A.msd_shift[id];
+    const int shift = (int)(A.msd_shift[id] & 0xffu);
     const uint64_t dbase = A.msd_base[id];
     const uint64_t dmult = A.msd_mult[id];
     const bool dir = A.direct[id] != 0u;
@@ -998,6 +1225,27 @@ static cudaError_t launch_small(const uint64_t* in, uint64_t* out, const uint32_
     return cudaGetLastError();
 }
 
+template <bool PAY, int THREADS, int CAP>
+static cudaError_t launch_small_reg(const uint64_t* in, uint64_t* out, const uint32_t* pin, uint32_t* pout,
+                                    const uint64_t* seg_lo, const uint64_t* seg_hi, const uint32_t* list,
+                                    const uint32_t* nlist, uint64_t count, uint64_t nseg, uint32_t min_n, uint32_t max_n,
+                                    uint64_t fin, uint64_t fout, const SegSortWs& ws, cudaStream_t st) {
+    constexpr size_t smem = reg_sort_smem<CAP>();
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(k_small_reg<PAY, THREADS, CAP>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int per_sm = std::max<int>(1, std::min<int>(2048 / THREADS, (int)(227 * 1024 / smem)));
+    const uint64_t grid = std::min<uint64_t>(count, (uint64_t)num_sms() * per_sm * 4);
+    if (grid == 0) return cudaSuccess;
+    HSS_LAUNCH((k_small_reg<PAY, THREADS, CAP>), (unsigned)grid, THREADS, smem, st, in, out, pin, pout, seg_lo, seg_hi,
+               list, nlist, nseg, min_n, max_n, fin, fout, ws.slow_list, ws.counters + 25);
+    return cudaGetLastError();
+}
+
 // The stable LSD kernel over this level's fallback list (length on the device).
 template <bool PAY>
 static cudaError_t launch_fallback(const uint64_t* in, uint64_t* out, const uint32_t* pin, uint32_t* pout,
@@ -1040,15 +1288,19 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
     if (N <= (uint64_t)kSmallCap) {
         // No segment can exceed the on-chip capacity: sort every segment in
         // its class without planning (and without a host round trip).
-        if ((e = cudaMemsetAsync(ws.counters + 24, 0, 4, st)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(ws.counters + 24, 0, 8, st)) != cudaSuccess) return e;
         if ((e = launch_small<PAY, kC0Threads, kC0Cap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi, nullptr, nullptr, nseg,
                                                        nseg, 0u, (uint32_t)kC0Cap, L.flip_in, fout, ws, st)) !=
             cudaSuccess)
             return e;
         if (N > (uint64_t)kC0Cap &&
-            (e = launch_small<PAY, kC1Threads, kC1Cap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi, nullptr, nullptr,
-                                                       nseg, nseg, (uint32_t)kC0Cap, (uint32_t)kC1Cap, L.flip_in, fout,
-                                                       ws, st)) != cudaSuccess)
+            (e = launch_small_reg<PAY, kC1Threads, kC1Cap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi, nullptr, nullptr,
+                                                           nseg, nseg, (uint32_t)kC0Cap, (uint32_t)kC1Cap, L.flip_in,
+                                                           fout, ws, st)) != cudaSuccess)
+            return e;
+        if ((e = launch_small<PAY, kC1Threads, kC1Cap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi, ws.slow_list,
+                                                       ws.counters + 25, nseg, nseg, 0u, (uint32_t)kC1Cap, L.flip_in,
+                                                       fout, ws, st)) != cudaSuccess)
             return e;
         if (N > (uint64_t)kC1Cap &&
             (e = launch_small<PAY, kC2Threads, kSmallCap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi, nullptr, nullptr,
@@ -1074,9 +1326,15 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
                                                                 ws.counters + 16, hc[0], L.nseg, 0u, (uint32_t)kC0Cap,
                                                                 L.flip_in, fout, ws, st)) != cudaSuccess)
             return e;
-        if (hc[1] && (e = launch_small<PAY, kC1Threads, kC1Cap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi, ws.list[1],
-                                                                ws.counters + 17, hc[1], L.nseg, (uint32_t)kC0Cap,
-                                                                (uint32_t)kC1Cap, L.flip_in, fout, ws, st)) != cudaSuccess)
+        if (hc[1] && (e = launch_small_reg<PAY, kC1Threads, kC1Cap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi,
+                                                                    ws.list[1], ws.counters + 17, hc[1], L.nseg,
+                                                                    (uint32_t)kC0Cap, (uint32_t)kC1Cap, L.flip_in, fout,
+                                                                    ws, st)) != cudaSuccess)
+            return e;
+        if (hc[1] &&
+            (e = launch_small<PAY, kC1Threads, kC1Cap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi, ws.slow_list,
+                                                       ws.counters + 25, hc[1], L.nseg, 0u, (uint32_t)kC1Cap, L.flip_in,
+                                                       fout, ws, st)) != cudaSuccess)
             return e;
         if (hc[2] && (e = launch_small<PAY, kC2Threads, kSmallCap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi,
                                                                    ws.list[2], ws.counters + 18, hc[2], L.nseg,
@@ -1089,17 +1347,21 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
         if (n_large == 0) return cudaSuccess;
         if (n_large > ws.max_large || tiles > ws.max_tiles || L.depth >= kMaxDepth) return cudaErrorInvalidValue;
         // Statistics and the split window.
-        if ((e = cudaMemsetAsync(ws.hist, 0, (size_t)n_large * 8 * kRadix * 4, st)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(ws.hist, 0, (size_t)n_large * 2 * kRadix * 4, st)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(ws.vor, 0, (size_t)n_large * 8, st)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(ws.vand, 0xff, (size_t)n_large * 8, st)) != cudaSuccess) return e;
         const uint64_t avg_tiles = ceil_div(tiles, n_large);
         const uint32_t split = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(256, ceil_div(2 * avg_tiles, 16)));
-        HSS_LAUNCH(k_seg_stats, dim3(n_large, split), 256, 0, st, L.in, L.seg_lo, L.seg_hi, ws.large_seg, ws.counters,
-                   ws.hist, ws.vor, ws.vand, L.hint_lo, L.hint_mult, split, L.flip_in);
         const int buf = L.depth & 1;
+        const uint32_t* prev_shift = L.depth > 0 ? ws.msd_shift[buf ^ 1] : nullptr;
+        HSS_LAUNCH(k_seg_stats, dim3(n_large, split), 256, 0, st, L.in, L.seg_lo, L.seg_hi, ws.large_seg, ws.counters,
+                   ws.hist, ws.vor, ws.vand, L.hint_lo, L.hint_mult, prev_shift, ws.spec, split, L.flip_in);
+        if (!L.hint_lo)
+            HSS_LAUNCH(k_seg_recount, dim3(n_large, split), 256, 0, st, L.in, L.seg_lo, L.seg_hi, ws.large_seg,
+                       ws.counters, ws.hist, ws.vor, ws.vand, ws.spec, split, L.flip_in);
         HSS_LAUNCH(k_msd_prep, n_large, 256, 0, st, L.seg_lo, ws.large_seg, ws.counters, ws.hist, ws.vor, ws.vand,
-                   L.hint_lo, L.hint_mult, ws.msd_base, ws.msd_mult, ws.msd_off, ws.msd_shift, ws.direct, ws.sub_lo[buf],
-                   ws.sub_hi[buf]);
+                   L.hint_lo, L.hint_mult, ws.msd_base, ws.msd_mult, ws.msd_off, ws.msd_shift[buf], ws.spec, ws.direct,
+                   ws.sub_lo[buf], ws.sub_hi[buf]);
         if ((e = cudaMemsetAsync(ws.status, 0, (size_t)tiles * kRadix * 4, st)) != cudaSuccess) return e;
         // The split pass: level buffers alternate tmp, dst, tmp, ... after src.
         uint64_t* next = (L.depth & 1) ? dst : tmp;
@@ -1109,7 +1371,7 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
         A.pin = L.pin; A.pout = pnext; A.pfinal = pdst;
         A.seg_lo = L.seg_lo; A.seg_hi = L.seg_hi; A.nseg = L.nseg;
         A.tile_start = ws.tile_start; A.large_id = ws.large_id;
-        A.msd_off = ws.msd_off; A.msd_shift = ws.msd_shift; A.msd_base = ws.msd_base; A.msd_mult = ws.msd_mult;
+        A.msd_off = ws.msd_off; A.msd_shift = ws.msd_shift[buf]; A.msd_base = ws.msd_base; A.msd_mult = ws.msd_mult;
         A.direct = ws.direct;
         A.status = ws.status; A.counter = ws.counters; A.err = ws.err;
         A.flip_in = L.flip_in; A.flip_out = fout;
@@ -1117,6 +1379,10 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
         static bool attr = false;
         if (!attr) {
             if ((e = cudaFuncSetAttribute(k_split<PAY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+                cudaSuccess)
+                return e;
+            // all of L1 as shared memory: the CTAs per SM are limited by their tiles
+            if ((e = cudaFuncSetAttribute(k_split<PAY>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) !=
                 cudaSuccess)
                 return e;
             attr = true;

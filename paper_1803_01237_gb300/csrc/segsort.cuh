@@ -38,11 +38,12 @@ struct SegSortWs {
     uint32_t* tile_start;  // [max_list + 1]
     uint32_t* large_id;    // [max_list]
     uint32_t* large_seg;   // [max_large]
-    uint32_t* hist;        // [max_large][8][256] digit counts
+    uint32_t* hist;        // [max_large][2][256] digit counts: the speculative window, then a recount
     unsigned long long* vor;   // [max_large] OR of the keys
     unsigned long long* vand;  // [max_large] AND of the keys
     uint32_t* msd_off;     // [max_large][256] exclusive offsets of the MSD digit
-    uint32_t* msd_shift;   // [max_large]
+    uint32_t* msd_shift[2];  // [max_large] split window (bits) of each large segment, by level parity
+    uint32_t* spec;        // [max_large] byte counted speculatively by the statistics pass
     uint64_t* msd_base;    // [max_large] digit = ((key >> shift) - base) & 255, or
     uint64_t* msd_mult;    // [max_large] when mult != 0: digit = mulhi(key - base, mult)
     uint32_t* direct;      // [max_large] all keys equal: copy to the output
@@ -51,7 +52,8 @@ struct SegSortWs {
     uint32_t* status;      // [2][max_tiles][256] look-back words
     uint32_t* counters;    // [64]
     uint32_t* list[3];     // [max_list] segments of each on-chip size class
-    uint32_t* fb_list;     // [max_list] segments left to the stable LSD kernel (count in counters[24])
+    uint32_t* fb_list;
+    uint32_t* slow_list;   // [max_list] segments the register kernels leave to the shared-memory kernel     // [max_list] segments left to the stable LSD kernel (count in counters[24])
     uint32_t* blk;         // [8 * (max_list / 1024 + 2)] per-chunk counts of the planning scan
     uint32_t* err;         // device error word (kDevErr*)
 };
