@@ -79,6 +79,7 @@ def _load():
             lib.oracle_cut_rank.restype = ctypes.c_uint64
             lib.oracle_hss.argtypes = [P, P, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32, ctypes.c_double,
                                        ctypes.c_uint64, ctypes.c_float, ctypes.c_uint32, P, ctypes.c_uint32,
+                                       ctypes.c_int, ctypes.c_uint32,
                                        P, P, P, P, P, P, ctypes.POINTER(_Stats), P, P, P, P, ctypes.c_uint64]
             lib.oracle_hss.restype = ctypes.c_int
             _lib = lib
@@ -179,9 +180,18 @@ class HSSResult:
     samples: list = field(default_factory=list)
 
 
+SCHEDULES = {"proportional": 0, "theory": 1, "equal": 2}
+
+
 def hss(keys, p: int, eps: float, seed: int, oversample: float = 5.0, max_rounds: int = 64,
-        payload=None, sort: bool = True, trace: bool = False, proposal=None) -> HSSResult:
-    """Run the whole method (Sec. 4.2.2 rounds, then exchange and merge)."""
+        payload=None, sort: bool = True, trace: bool = False, proposal=None, schedule: str = "proportional",
+        schedule_k: int = 0) -> HSSResult:
+    """Run the whole method (Sec. 4.2.2 rounds, then exchange and merge).
+
+    schedule: "proportional" (s p / |gamma| per key, Sec. 6), "theory" (the
+    k-round s_j = (2 ln p / eps)^(j/k) schedule of Theorem 4.7, k =
+    schedule_k) or "equal" (s p / nint expected samples per distinct
+    unresolved interval, the HykSort way of Sec. 4.2.2)."""
     lib = _load()
     k, kt = _keys_u64(keys)
     N = int(k.shape[0])
@@ -208,7 +218,7 @@ def hss(keys, p: int, eps: float, seed: int, oversample: float = 5.0, max_rounds
         prop = np.ascontiguousarray(np.asarray(proposal).astype(np.int64 if kt == KEY_I64 else np.uint64)).view(np.uint64)
         nprop = prop.shape[0]
     rc = lib.oracle_hss(_ptr(k), _ptr(pay), N, kt, p, float(eps), int(seed) & ((1 << 64) - 1),
-                        float(oversample), max_rounds, _ptr(prop), nprop,
+                        float(oversample), max_rounds, _ptr(prop), nprop, SCHEDULES[schedule], int(schedule_k),
                         _ptr(spl_key), _ptr(spl_seg), _ptr(spl_spos), _ptr(offsets),
                         _ptr(out_keys), _ptr(out_pay), ctypes.byref(st), _ptr(tl), _ptr(tu), _ptr(tr), _ptr(ts), cap)
     if rc == -1:

@@ -116,6 +116,26 @@ void oracle_threshold(double oversample, uint32_t p, uint64_t gamma, uint64_t* T
     *T = (uint64_t)floor(ldexp(q, 64));
 }
 
+/* Threshold of a sampling probability q: take all when q >= 1, else
+ * T = floor(q 2^64) (a key is kept when its word is below T). */
+void oracle_threshold_q(double q, uint64_t* T, int* take_all)
+{
+    if (q >= 1.0) { *take_all = 1; *T = 0; return; }
+    *take_all = 0;
+    *T = (uint64_t)floor(ldexp(q, 64));
+}
+
+/* The sampling probability of round j (1-based) of the k-round schedule of
+ * Sec. 4.2.2 and Theorem 4.7: s_j = (2 ln p / eps)^(j/k) and every key of the
+ * unresolved region is drawn with probability p s_j / N (rounds past k keep
+ * s_k). */
+double oracle_theory_q(uint32_t p, double eps, uint64_t N, uint32_t j, uint32_t k)
+{
+    const uint32_t jj = j < k ? j : k;
+    const double sj = pow(2.0 * log((double)p) / eps, (double)jj / (double)k);
+    return ((double)p * sj) / (double)N;
+}
+
 uint64_t oracle_tolerance(uint64_t N, uint32_t p, double eps)
 {
     return (uint64_t)floor(((double)N * eps) / (2.0 * (double)p));
@@ -306,13 +326,14 @@ static void offer(ocut* L, ocut* U, uint64_t t, const ocut* c)
  */
 int oracle_hss(const uint64_t* keys, const uint32_t* payload, uint64_t N, int key_type,
                uint32_t p, double eps, uint64_t seed, float oversample, uint32_t max_rounds,
-               const uint64_t* proposal_keys, uint32_t nprop,
+               const uint64_t* proposal_keys, uint32_t nprop, int schedule, uint32_t schedule_k,
                uint64_t* spl_key, int32_t* spl_seg, uint32_t* spl_spos, uint64_t* offsets,
                uint64_t* out_keys, uint32_t* out_payload, oracle_stats* stats,
                uint64_t* trace_lrank, uint64_t* trace_urank, uint8_t* trace_resolved,
                uint64_t* trace_samples, uint64_t trace_cap)
 {
     if (p == 0 || !(eps > 0.0) || max_rounds > ORACLE_MAX_ROUNDS) return -1;
+    if (schedule < 0 || schedule > 2 || (schedule == 1 && schedule_k == 0)) return -1;
     memset(stats, 0, sizeof(*stats));
 
     /* Step 1: processors and targets. */
@@ -359,6 +380,7 @@ int oracle_hss(const uint64_t* keys, const uint32_t* payload, uint64_t N, int ke
         ++j;
         /* |gamma_{j-1}|: keys strictly inside the distinct unresolved intervals. */
         uint64_t gamma = 0;
+        uint32_t nint = 0;                            /* distinct unresolved intervals */
         for (uint32_t i = 0; i < S; ++i) {
             if (res[i]) continue;
             int dup = 0;
@@ -368,9 +390,16 @@ int oracle_hss(const uint64_t* keys, const uint32_t* payload, uint64_t N, int ke
             }
             if (dup) continue;
             gamma += U[i].rank - L[i].rank - (L[i].kind == CUT_MEMBER ? 1u : 0u);
+            ++nint;
         }
+        /* Sampling probability: proportional (Sec. 6: s p / |gamma| for every
+         * key of the region), the k-round schedule of Theorem 4.7, or equal
+         * per interval (HykSort, Sec. 4.2.2 remark): s p / nint expected
+         * samples for each distinct unresolved interval. */
         uint64_t T; int take_all;
-        oracle_threshold((double)oversample, p, gamma, &T, &take_all);
+        if (schedule == 1) oracle_threshold_q(oracle_theory_q(p, eps, N, j, schedule_k), &T, &take_all);
+        else oracle_threshold((double)oversample, p, gamma, &T, &take_all);
+        const double per_int = nint ? ((double)oversample * (double)p) / (double)nint : 0.0;
 
         /* Sampling phase: every key strictly inside an unresolved interval is
          * drawn independently. */
@@ -384,13 +413,18 @@ int oracle_hss(const uint64_t* keys, const uint32_t* payload, uint64_t N, int ke
                 if (!res[i2]) { dup = 1; break; }
             }
             if (dup) continue;
+            uint64_t Ti = T; int all_i = take_all;
+            if (schedule == 2) {
+                const uint64_t len = U[i].rank - L[i].rank - (L[i].kind == CUT_MEMBER ? 1u : 0u);
+                oracle_threshold_q(len ? per_int / (double)len : 1.0, &Ti, &all_i);
+            }
             for (uint32_t s = 0; s < p; ++s) {
                 uint64_t a = seg_lower_bound(&st, s, &L[i]);
                 if (L[i].kind == CUT_MEMBER && (uint32_t)L[i].seg == s) a += 1;   /* strictly above L */
                 uint64_t b = seg_lower_bound(&st, s, &U[i]);                        /* strictly below U */
                 for (uint64_t pos = a; pos < b; ++pos) {
                     uint64_t u = oracle_sample_draw(seed, s, (uint32_t)pos, j);
-                    if (!(take_all || u < T)) continue;
+                    if (!(all_i || u < Ti)) continue;
                     if (Z == cap) { cap *= 2; smp = (ocut*)realloc(smp, sizeof(ocut) * cap); }
                     ocut* c = &smp[Z++];
                     c->kind = CUT_MEMBER; c->okey = okeys[seg_start[s] + pos]; c->seg = (int32_t)s; c->spos = (uint32_t)pos;

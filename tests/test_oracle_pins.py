@@ -440,3 +440,91 @@ def test_proposal_cuts_are_histogrammed():
     _check_result(keys, p, eps, res)
     # exact proposals resolve every splitter before any sampling
     assert res.rounds == 0 and base.rounds >= 1
+
+
+# ---------------------------------------------------------------------------
+# The other sampling schedules: the k-round schedule of Theorem 4.7 and the
+# equal-per-interval (HykSort) sampling the paper contrasts with in Sec. 4.2.2.
+# ---------------------------------------------------------------------------
+def _region(res, r, N, p):
+    L = res.trace_lrank[r].astype(np.int64)
+    U = res.trace_urank[r].astype(np.int64)
+    flags = res.trace_resolved[r]
+    resolved = (flags & 1) != 0
+    lmem = (flags & 2) != 0
+    ints = []
+    done = set()
+    for i in range(p - 1):
+        if resolved[i]:
+            continue
+        lo, hi = int(L[i]) + int(lmem[i]), int(U[i])
+        if (lo, hi) in done:
+            continue
+        done.add((lo, hi))
+        ints.append((lo, hi))
+    return ints
+
+
+@pytest.mark.parametrize("schedule,k", [("theory", 2), ("theory", 3), ("equal", 0)])
+def test_sampling_set_rederived_other_schedules(schedule, k):
+    """Each round samples exactly the keys of the unresolved region whose
+    Philox word is below the schedule's threshold: p s_j / N with
+    s_j = (2 ln p / eps)^(j/k) (Theorem 4.7), or s p / nint spread equally
+    over the nint distinct intervals (HykSort)."""
+    N, p, eps, seed = 1 << 13, 16, 0.02, 5
+    keys = inputs.uniform(N, seed)
+    res = oracle.hss(keys, p, eps, seed=seed, trace=True, schedule=schedule, schedule_k=k)
+    assert res.status == 0 and res.rounds >= 1
+    b, idx = _sorted_pos_to_input_index(keys, p)
+    _, rank_of = _global_order(keys, p)
+    rank_sp = [rank_of[idx[s]] for s in range(p)]
+    for r in range(res.rounds):
+        ints = _region(res, r, N, p)
+        assert sum(hi - lo for lo, hi in ints) == int(res.gamma[r])
+        thr = {}
+        for lo, hi in ints:
+            if schedule == "theory":
+                sj = math.pow(2.0 * math.log(p) / eps, min(r + 1, k) / k)
+                q = (p * sj) / N
+            else:
+                q = (5.0 * p / len(ints)) / (hi - lo) if hi > lo else 1.0
+            thr[(lo, hi)] = (True, 0) if q >= 1.0 else (False, int(math.floor(math.ldexp(q, 64))))
+        want = set()
+        for s in range(p):
+            for spos in range(len(rank_sp[s])):
+                rk = rank_sp[s][spos]
+                for lo, hi in ints:
+                    if lo <= rk < hi:
+                        all_, T = thr[(lo, hi)]
+                        if all_ or oracle.sample_draw(seed, s, spos, r + 1) < T:
+                            want.add((s, spos))
+        got = {(int(sg), int(sp)) for _, sg, sp in res.samples[r]}
+        assert got == want
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4, 5])
+def test_theory_one_round_is_lemma_4_1(seed):
+    """k = 1: every key drawn with probability 2 p ln p / (eps N) puts a key
+    in every target range w.h.p. (Lemma 4.1): one round."""
+    N, p, eps = 1 << 16, 32, 0.05
+    keys = inputs.uniform(N, seed)
+    res = oracle.hss(keys, p, eps, seed=seed, schedule="theory", schedule_k=1)
+    assert res.status == 0 and res.rounds == 1
+    _check_result(keys, p, eps, res)
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_theory_k_rounds_theorem_4_7(k):
+    """With s_j = (2 ln p / eps)^(j/k) the splitters are found after k rounds
+    w.h.p. (Lemma 4.3, Theorem 4.7), and round j draws about p s_j/N of the
+    region (a 6-sigma Chernoff band)."""
+    N, p, eps = 1 << 16, 64, 0.02
+    for seed in (1, 2, 3):
+        keys = inputs.gauss_mix(N, seed)
+        res = oracle.hss(keys, p, eps, seed=seed, schedule="theory", schedule_k=k)
+        assert res.status == 0 and res.rounds <= k
+        _check_result(keys, p, eps, res)
+        for j in range(res.rounds):
+            q = min(1.0, p * math.pow(2.0 * math.log(p) / eps, (j + 1) / k) / N)
+            mean = q * int(res.gamma[j])
+            assert abs(int(res.sample_size[j]) - mean) <= 6.0 * math.sqrt(max(mean * (1 - q), 1e-9)) + 1
