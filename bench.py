@@ -434,6 +434,87 @@ def run_serve_workload(args):
     return 0
 
 
+def run_rounds_workload(args):
+    """Round-count study (the rounds of Sec. 7.1, Fig. 1): histogram rounds
+    of hss_partition against p for oversampling s = 1 and s = 5 at eps = 2%,
+    N = 2^26 uniform keys, p = 2^4 .. 2^14 (the p x (p-1) per-segment cut
+    positions bound p on one device), with the round bound of Theorem 4.8,
+    O(log(log p / eps)), printed beside as log2(log2(p) / eps)."""
+    import math
+    import numpy as np
+    import torch
+    from paper_1803_01237_gb300 import hss, inputs
+
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    hss.load()
+    N, eps = 1 << 26, 0.02
+    keys = torch.from_numpy(inputs.uniform(N, 1).view(np.int64)).to(dev)
+    table = []
+    for lp in range(4, 15):
+        p = 1 << lp
+        row = {"p": p, "log2_log2p_over_eps": math.log2(math.log2(p) / eps)}
+        for s_ in (1.0, 5.0):
+            rounds = []
+            for seed in (1, 2, 3):
+                res, _ = hss.partition(keys, p, eps, seed, oversample=s_)
+                rounds.append(res.rounds)
+            row[f"rounds_s{int(s_)}"] = rounds
+            row[f"mean_rounds_s{int(s_)}"] = float(np.mean(rounds))
+        table.append(row)
+        torch.cuda.empty_cache()
+    line = {"metric": "HSS rounds vs p (s = 1 and s = 5, eps = 0.02)", "value": table[-1]["mean_rounds_s5"],
+            "unit": "rounds", "n_gpus": 1, "steps": len(table), "warmup": 0, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "round-count study: N = 2^26 uniform u64, eps = 0.02, p = 2^4 .. 2^14, "
+                                   "s in {1, 5}, seeds 1-3"},
+            "table": table}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_schedules_workload(args):
+    """Sampling-schedule ablation (Sec. 4.2.2, Theorem 4.7): at the bench
+    shape (N = 2^28, p = 1024, eps = 0.02) on the three inputs, the rounds,
+    the probes drawn over all rounds and the partition time of the
+    proportional schedule (s = 5, the default), the k-round schedule
+    s_j = (2 ln p / eps)^(j/k) for k = 2, 3, 4, and equal sampling per
+    interval (HykSort)."""
+    import numpy as np
+    import torch
+    from paper_1803_01237_gb300 import hss, inputs
+
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    hss.load()
+    N = 1 << LOG2N
+    rows = []
+    for name, sd in DISTS:
+        keys = torch.from_numpy(inputs.SCALE_DISTRIBUTIONS[name](N, sd).view(np.int64)).to(dev)
+        for sched, k in (("proportional", 0), ("theory", 2), ("theory", 3), ("theory", 4), ("equal", 0)):
+            hss.partition(keys, P, EPS, SEED, schedule=sched, schedule_k=k)  # warm
+            torch.cuda.synchronize(dev)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            res, _ = hss.partition(keys, P, EPS, SEED, schedule=sched, schedule_k=k, flags=hss.FLAG_TIMING)
+            ev1.record()
+            torch.cuda.synchronize(dev)
+            rows.append({"input": name, "schedule": sched, "k": k, "rounds": res.rounds,
+                         "probes": int(sum(res.sample_size)), "sample_size": res.sample_size,
+                         "partition_ms": ev0.elapsed_time(ev1), "rounds_ms": res.ms_phase["rounds"]})
+        del keys
+        torch.cuda.empty_cache()
+    line = {"metric": "sampling-schedule ablation: rounds and probes per partition", "value": None,
+            "unit": "rounds", "n_gpus": 1, "steps": len(rows), "warmup": 1, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"hss_partition N=2^{LOG2N}, p={P}, eps={EPS}, seed {SEED}, three inputs"},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -445,7 +526,7 @@ def main():
     ap.add_argument("--uniform-only", action="store_true", help="time the uniform input only")
     ap.add_argument("--log2n", type=int, default=None,
                     help="smaller case of the same kernels (keeps 2^18 keys per segment); for profiling only")
-    ap.add_argument("--workload", default="sort", choices=["sort", "batch", "serve"],
+    ap.add_argument("--workload", default="sort", choices=["sort", "batch", "serve", "rounds", "schedules"],
                     help="sort: the N=2^28 bench line (default); batch: 4096 independent jobs; serve: Poisson requests")
     ap.add_argument("--batch-jobs", type=int, default=4096)
     ap.add_argument("--serve-requests", type=int, default=10000)
@@ -458,6 +539,10 @@ def main():
         return run_batch_workload(args)
     if args.workload == "serve" and args.impl == "gb300":
         return run_serve_workload(args)
+    if args.workload == "rounds" and args.impl == "gb300":
+        return run_rounds_workload(args)
+    if args.workload == "schedules" and args.impl == "gb300":
+        return run_schedules_workload(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.log2n is not None:

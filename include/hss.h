@@ -80,7 +80,24 @@ typedef struct {
     float oversample;    /* s: expected probes per processor per round (default 5, Sec. 7.2) */
     uint32_t max_rounds; /* <= HSS_MAX_ROUNDS (0 means HSS_MAX_ROUNDS) */
     uint32_t flags;      /* HSS_FLAG_* */
+    uint32_t schedule;   /* HSS_SCHEDULE_*: how a round's sampling probability is chosen */
+    uint32_t schedule_k; /* HSS_SCHEDULE_THEORY: the number of rounds k (>= 1) */
 } hss_params;
+
+/* Sampling schedules (single calls; the batch entry points take only the
+ * proportional one):
+ *   PROPORTIONAL  every key of the unresolved region with probability
+ *                 min(1, s p / |gamma|) (Sec. 6: s p probes per round);
+ *   THEORY        round j draws every key of the region with probability
+ *                 min(1, p s_j / N), s_j = (2 ln p / eps)^(min(j,k)/k)
+ *                 (Sec. 4.2.2, Theorem 4.7), computed on the host in IEEE
+ *                 double with the C library's log and pow;
+ *   EQUAL         every distinct unresolved interval gets s p / nint expected
+ *                 probes (probability min(1, (s p / nint) / its length)), the
+ *                 HykSort sampling the paper contrasts with (Sec. 4.2.2). */
+#define HSS_SCHEDULE_PROPORTIONAL 0
+#define HSS_SCHEDULE_THEORY 1
+#define HSS_SCHEDULE_EQUAL 2
 
 #define HSS_PHASE_LOCAL_SORT 0
 #define HSS_PHASE_ROUNDS 1

@@ -648,6 +648,7 @@ int run_batch(const void* d_keys, const uint32_t* d_payload, int key_type, const
     const uint64_t mark = hss_kernel_launch_count();
     if (h_stats) std::memset(h_stats, 0, sizeof(*h_stats));
     if (!prm || !(prm->eps > 0.0) || !(prm->oversample > 0.0f) || njobs == 0 || !h_sizes || !h_p) return HSS_ERR_INVALID;
+    if (prm->schedule != HSS_SCHEDULE_PROPORTIONAL) return HSS_ERR_INVALID;
     if (key_type != HSS_KEY_U64 && key_type != HSS_KEY_I64) return HSS_ERR_INVALID;
     Tables T;
     if (build_tables(h_sizes, h_p, njobs, prm, T) != HSS_OK) return HSS_ERR_INVALID;

@@ -86,10 +86,21 @@ static bool params_ok(const hss_params* prm) {
     if (prm->p == 0 || prm->p > kMaxP) return false;
     if (!(prm->oversample > 0.0f) || !std::isfinite(prm->oversample)) return false;
     if (prm->max_rounds > HSS_MAX_ROUNDS) return false;
+    if (prm->schedule > HSS_SCHEDULE_EQUAL || (prm->schedule == HSS_SCHEDULE_THEORY && prm->schedule_k == 0)) return false;
     return true;
 }
 
-static float eff_oversample(const hss_params* prm) { return prm ? prm->oversample : 5.0f; }
+// Oversampling that sizes the round sample buffers: s, or under the k-round
+// schedule 5 (2 ln p / eps)^(1/k), the bound of Lemma 4.6 on a round's probes
+// per processor (round 1 draws p (2 ln p / eps)^(1/k) of the whole input).
+static float eff_oversample(const hss_params* prm) {
+    if (!prm) return 5.0f;
+    if (prm->schedule == HSS_SCHEDULE_THEORY && prm->schedule_k > 0 && prm->p > 1) {
+        const double r = std::pow(2.0 * std::log((double)prm->p) / prm->eps, 1.0 / (double)prm->schedule_k);
+        return (float)std::max<double>(prm->oversample, 5.0 * r);
+    }
+    return prm->oversample;
+}
 static uint32_t eff_rounds(const hss_params* prm) { return prm->max_rounds == 0 ? HSS_MAX_ROUNDS : prm->max_rounds; }
 
 struct PhaseTimer {
@@ -141,7 +152,8 @@ static int run_path(const void* d_keys, const uint32_t* d_payload, int key_type,
     if (sort && ((d_payload == nullptr) != (d_payload_out == nullptr))) return HSS_ERR_INVALID;
     const uint32_t p = prm->p;
     const float s = prm->oversample;
-    const Layout L = plan(sort ? HSS_OP_SORT : HSS_OP_PARTITION, N, p, s, pay);
+    const float s_cap = eff_oversample(prm);
+    const Layout L = plan(sort ? HSS_OP_SORT : HSS_OP_PARTITION, N, p, s_cap, pay);
     if (work_bytes < L.total) return HSS_ERR_WORKSPACE;
 
     uint64_t* keysA = at<uint64_t>(d_work, L.keysA);
@@ -150,7 +162,7 @@ static int run_path(const void* d_keys, const uint32_t* d_payload, int key_type,
     uint32_t* payB = pay ? at<uint32_t>(d_work, L.payB) : nullptr;
     uint64_t* seg_off = at<uint64_t>(d_work, L.seg_off);
     uint32_t* err = at<uint32_t>(d_work, L.err);
-    const uint64_t cap = sample_capacity(N, p, s);
+    const uint64_t cap = sample_capacity(N, p, s_cap);
     SegSortWs sws = segsort_ws_carve(at<void>(d_work, L.sws), std::max<uint64_t>(N, 1), p, err);
     RoundWs rws = rounds_ws_carve(at<void>(d_work, L.rws), std::max<uint64_t>(N, 1), p, cap, err);
     const bool i64 = key_type == HSS_KEY_I64;
@@ -175,7 +187,7 @@ static int run_path(const void* d_keys, const uint32_t* d_payload, int key_type,
     // Splitter rounds (Sec. 4.2.2).
     RoundResult rr;
     int status = run_rounds(keysA, seg_off, N, p, prm->eps, prm->seed, s, eff_rounds(prm), key_type, d_splitters,
-                            d_offsets, rws, st, &rr, (const uint64_t*)d_prop, nprop);
+                            d_offsets, rws, st, &rr, (const uint64_t*)d_prop, nprop, prm->schedule, prm->schedule_k);
     tm.mark(HSS_PHASE_ROUNDS);
     if (status == HSS_ERR_CUDA) return status;
 
@@ -355,7 +367,7 @@ int hss_sort_host(const void* h_keys, const uint32_t* h_payload, int key_type, u
     if ((h_payload == nullptr) != (h_payload_out == nullptr)) return HSS_ERR_INVALID;
     const uint32_t p = prm->p;
     const bool pay = h_payload != nullptr;
-    const Layout L = plan(HSS_OP_SORT_HOST, N, p, prm->oversample, pay);
+    const Layout L = plan(HSS_OP_SORT_HOST, N, p, eff_oversample(prm), pay);
     if (work_bytes < L.total) return HSS_ERR_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
     uint64_t* io = at<uint64_t>(d_work, L.io_keys);

@@ -45,6 +45,7 @@ size_t rounds_ws_bytes(uint64_t N, uint64_t p, uint64_t cap) {
     b += 2 * aup(S1 * sizeof(DCut));
     b += 2 * aup(p * S1 * sizeof(uint32_t));
     b += 6 * aup(S1 * sizeof(uint32_t));
+    b += aup(S1 * sizeof(uint64_t)) + aup(S1 * sizeof(uint32_t));  // int_T, int_all
     b += aup((N / 32 + 2) * sizeof(uint32_t));
     b += aup(p * sizeof(uint32_t)) + aup((p + 1) * sizeof(uint32_t));
     b += 3 * aup(cap * sizeof(uint64_t));      // skey, skey_sorted, stmp
@@ -75,6 +76,8 @@ RoundWs rounds_ws_carve(void* base, uint64_t N, uint64_t p, uint64_t cap, uint32
     w.chgU = (int32_t*)take(S1 * sizeof(uint32_t));
     w.choose_u = (uint32_t*)take(S1 * sizeof(uint32_t));
     w.int_rep = (uint32_t*)take(S1 * sizeof(uint32_t));
+    w.int_T = (uint64_t*)take(S1 * sizeof(uint64_t));
+    w.int_all = (uint32_t*)take(S1 * sizeof(uint32_t));
     take(S1 * sizeof(uint32_t));
     w.bitmap = (uint32_t*)take((N / 32 + 2) * sizeof(uint32_t));
     w.seg_cnt = (uint32_t*)take(p * sizeof(uint32_t));
@@ -126,18 +129,24 @@ __global__ void k_rounds_init(const uint64_t* __restrict__ seg_off, uint32_t S, 
 // Resolved flags, distinct unresolved intervals, |gamma| and the threshold.
 // One CTA of 1024 threads walks the splitters in chunks.
 // ---------------------------------------------------------------------------
+// schedule THEORY: the next round's threshold comes from the host (T_ovr,
+// all_ovr); EQUAL: per-interval thresholds into int_T / int_all.
 __global__ __launch_bounds__(1024) void k_intervals(uint32_t S, uint64_t N, uint32_t p, uint64_t tol, float oversample,
                                                     const DCut* __restrict__ Lcut, const DCut* __restrict__ Ucut,
                                                     uint32_t* __restrict__ res, uint32_t* __restrict__ int_rep,
-                                                    RoundCtl* ctl) {
+                                                    RoundCtl* ctl, uint32_t schedule, uint64_t T_ovr, uint32_t all_ovr,
+                                                    uint64_t* __restrict__ int_T, uint32_t* __restrict__ int_all) {
     IntervalsOut o;
-    intervals_body(S, N, p, tol, oversample, Lcut, Ucut, res, int_rep, o);
+    const bool equal = schedule == HSS_SCHEDULE_EQUAL;
+    intervals_body(S, N, p, tol, oversample, Lcut, Ucut, res, int_rep, o, equal ? int_T : nullptr,
+                   equal ? int_all : nullptr);
     if (threadIdx.x == 0) {
         ctl->gamma = o.gamma;
         ctl->nint = o.nint;
         ctl->unresolved = o.unresolved;
-        ctl->take_all = o.take_all;
-        ctl->T = o.T;
+        const bool theory = schedule == HSS_SCHEDULE_THEORY;
+        ctl->take_all = theory ? all_ovr : o.take_all;
+        ctl->T = theory ? T_ovr : o.T;
     }
 }
 
@@ -147,7 +156,8 @@ __global__ __launch_bounds__(1024) void k_intervals(uint32_t S, uint64_t N, uint
 __global__ __launch_bounds__(kSampThreads) void k_sample_mark(
     const uint64_t* __restrict__ seg_off, uint32_t S, const uint32_t* __restrict__ Lpos, const uint32_t* __restrict__ Upos,
     const DCut* __restrict__ Lcut, const uint32_t* __restrict__ int_rep, const RoundCtl* __restrict__ ctl,
-    uint64_t seed, uint32_t round, uint32_t* __restrict__ bitmap, uint32_t* __restrict__ seg_cnt) {
+    uint64_t seed, uint32_t round, uint32_t* __restrict__ bitmap, uint32_t* __restrict__ seg_cnt,
+    const uint64_t* __restrict__ int_T, const uint32_t* __restrict__ int_all) {
     __shared__ uint32_t s_a[kIntChunk], s_b[kIntChunk], s_pre[kIntChunk + 1];
     __shared__ uint32_t s_warp[32];
     const uint32_t s = blockIdx.x;
@@ -167,12 +177,18 @@ __global__ __launch_bounds__(kSampThreads) void k_sample_mark(
             uint64_t w0, w1;
             sample_words(seed, s, round, m, w0, w1);
             const uint32_t p0 = 2 * m, p1 = 2 * m + 1;
-            if (p0 >= a && p0 < b && (take_all || w0 < T)) {
+            uint64_t Tu = T;
+            bool all_u = take_all;
+            if (int_T) {  // equal-per-interval schedule
+                Tu = int_T[u0 + u];
+                all_u = int_all[u0 + u] != 0u;
+            }
+            if (p0 >= a && p0 < b && (all_u || w0 < Tu)) {
                 const uint64_t g = base + p0;
                 atomicOr(&bitmap[g >> 5], 1u << (g & 31));
                 ++cnt;
             }
-            if (p1 >= a && p1 < b && (take_all || w1 < T)) {
+            if (p1 >= a && p1 < b && (all_u || w1 < Tu)) {
                 const uint64_t g = base + p1;
                 atomicOr(&bitmap[g >> 5], 1u << (g & 31));
                 ++cnt;
@@ -501,18 +517,36 @@ __global__ void k_final_pos(uint32_t S, const uint32_t* __restrict__ choose_u, u
 #define HSS_TRY(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return HSS_ERR_CUDA; } while (0)
 
 static void enqueue_sampling(const RoundWs& ws, const uint64_t* d_seg_off, uint64_t N, uint32_t p, uint32_t S,
-                             uint64_t seed, uint32_t round, cudaStream_t st) {
+                             uint64_t seed, uint32_t round, cudaStream_t st, bool per_interval) {
     cudaMemsetAsync(ws.bitmap, 0, (N / 32 + 2) * sizeof(uint32_t), st);
     HSS_LAUNCH(k_sample_mark, p, kSampThreads, 0, st, d_seg_off, S, ws.Lpos, ws.Upos, ws.Lcut, ws.int_rep, ws.ctl, seed,
-               round, ws.bitmap, ws.seg_cnt);
+               round, ws.bitmap, ws.seg_cnt, per_interval ? ws.int_T : nullptr, per_interval ? ws.int_all : nullptr);
     HSS_LAUNCH(k_count_scan, 1, 1024, 0, st, ws.seg_cnt, p, ws.seg_cnt_off, ws.cap, ws.ctl);
 }
 
 int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uint32_t p, double eps, uint64_t seed,
                float oversample, uint32_t max_rounds, int key_type, hss_cut* d_splitters, uint64_t* d_offsets,
-               const RoundWs& ws, cudaStream_t st, RoundResult* out, const uint64_t* d_prop, uint32_t nprop) {
+               const RoundWs& ws, cudaStream_t st, RoundResult* out, const uint64_t* d_prop, uint32_t nprop,
+               uint32_t schedule, uint32_t schedule_k) {
     const uint32_t S = p - 1;
     const uint64_t tol = (uint64_t)std::floor(((double)N * eps) / (2.0 * (double)p));
+    const bool per_interval = schedule == HSS_SCHEDULE_EQUAL;
+    // The interval pass before sampling round r; under the k-round schedule
+    // the host supplies round r's threshold: probability p s_r / N,
+    // s_r = (2 ln p / eps)^(min(r,k)/k) (Theorem 4.7), in IEEE double.
+    auto intervals = [&](uint32_t r) {
+        uint64_t Tq = 0;
+        uint32_t allq = 0;
+        if (schedule == HSS_SCHEDULE_THEORY) {
+            const uint32_t rr = r < schedule_k ? r : schedule_k;
+            const double sj = std::pow(2.0 * std::log((double)p) / eps, (double)rr / (double)schedule_k);
+            const double q = ((double)p * sj) / (double)N;
+            if (q >= 1.0) allq = 1u;
+            else Tq = (uint64_t)std::floor(std::ldexp(q, 64));
+        }
+        HSS_LAUNCH(k_intervals, 1, 1024, 0, st, S, N, p, tol, oversample, ws.Lcut, ws.Ucut, ws.res, ws.int_rep, ws.ctl,
+                   schedule, Tq, allq, ws.int_T, ws.int_all);
+    };
     HSS_TRY(cudaMemsetAsync(ws.ctl, 0, sizeof(RoundCtl), st));
     if (S == 0) {
         HSS_LAUNCH(k_finalize, 1, 32, 0, st, 0u, N, p, key_type, ws.Lcut, ws.Ucut, d_splitters, d_offsets, ws.choose_u,
@@ -524,7 +558,7 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
     }
     const unsigned sblk = (unsigned)cdiv(S, 256);
     HSS_LAUNCH(k_rounds_init, dim3(p, sblk), 256, 0, st, d_seg_off, S, N, ws.Lcut, ws.Ucut, ws.Lpos, ws.Upos);
-    HSS_LAUNCH(k_intervals, 1, 1024, 0, st, S, N, p, tol, oversample, ws.Lcut, ws.Ucut, ws.res, ws.int_rep, ws.ctl);
+    intervals(1);
     if (nprop > 0) {
         // Proposed cuts: sorted, ranked in every segment, offered to L/U.
         if (nprop > ws.cap) return HSS_ERR_INVALID;
@@ -540,9 +574,9 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
         HSS_LAUNCH(k_update, sblk, 256, 0, st, S, N, p, ws.pkey, ws.pseg, ws.pspos, ws.prank, (uint64_t)nprop,
                    (int32_t)kNonMember, ws.Lcut, ws.Ucut, ws.chgL, ws.chgU);
         HSS_LAUNCH(k_update_pos, dim3(p, sblk), 256, 0, st, S, ws.chgL, ws.chgU, ws.probe_pos, ws.cap, ws.Lpos, ws.Upos);
-        HSS_LAUNCH(k_intervals, 1, 1024, 0, st, S, N, p, tol, oversample, ws.Lcut, ws.Ucut, ws.res, ws.int_rep, ws.ctl);
+        intervals(1);
     }
-    enqueue_sampling(ws, d_seg_off, N, p, S, seed, 1, st);
+    enqueue_sampling(ws, d_seg_off, N, p, S, seed, 1, st, per_interval);
     HSS_TRY(cudaGetLastError());
     RoundCtl h;
     HSS_TRY(cudaMemcpyAsync(&h, ws.ctl, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -572,8 +606,8 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
                        ws.Lcut, ws.Ucut, ws.chgL, ws.chgU);
             HSS_LAUNCH(k_update_pos, dim3(p, sblk), 256, 0, st, S, ws.chgL, ws.chgU, ws.probe_pos, ws.cap, ws.Lpos, ws.Upos);
         }
-        HSS_LAUNCH(k_intervals, 1, 1024, 0, st, S, N, p, tol, oversample, ws.Lcut, ws.Ucut, ws.res, ws.int_rep, ws.ctl);
-        enqueue_sampling(ws, d_seg_off, N, p, S, seed, j + 1, st);
+        intervals(j + 1);
+        enqueue_sampling(ws, d_seg_off, N, p, S, seed, j + 1, st, per_interval);
         HSS_TRY(cudaGetLastError());
         HSS_TRY(cudaMemcpyAsync(&h, ws.ctl, sizeof(h), cudaMemcpyDeviceToHost, st));
         HSS_TRY(cudaStreamSynchronize(st));

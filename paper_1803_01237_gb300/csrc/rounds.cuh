@@ -32,6 +32,8 @@ struct RoundWs {
     int32_t* chgU;       // [S]
     uint32_t* choose_u;  // [S]
     uint32_t* int_rep;   // [S] representative splitter of each distinct unresolved interval
+    uint64_t* int_T;     // [S] per-interval threshold (equal-per-interval schedule)
+    uint32_t* int_all;   // [S] per-interval take-all flag
     uint32_t* bitmap;    // [N/32 + 2]
     uint32_t* seg_cnt;   // [p]
     uint32_t* seg_cnt_off;  // [p + 1]
@@ -78,7 +80,7 @@ struct RoundResult {
 int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uint32_t p, double eps, uint64_t seed,
                float oversample, uint32_t max_rounds, int key_type, hss_cut* d_splitters, uint64_t* d_offsets,
                const RoundWs& ws, cudaStream_t st, RoundResult* out, const uint64_t* d_prop = nullptr,
-               uint32_t nprop = 0);
+               uint32_t nprop = 0, uint32_t schedule = HSS_SCHEDULE_PROPORTIONAL, uint32_t schedule_k = 0);
 
 // Per-bucket split windows for the merge, from the final splitters.
 cudaError_t bucket_hints(const RoundWs& ws, const uint64_t* skeys, const uint64_t* d_seg_off, uint32_t p,

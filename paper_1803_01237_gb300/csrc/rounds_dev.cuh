@@ -78,10 +78,13 @@ struct IntervalsOut {
 // splitters into int_rep), |gamma| and the next threshold of one job, by one
 // CTA of up to 1024 threads walking the splitters in chunks.  The outputs are
 // valid in thread 0.
+// With int_T non-null, every distinct interval u also gets the threshold of
+// the equal-per-interval schedule: probability (s p / nint) / its length.
 __device__ __forceinline__ void intervals_body(uint32_t S, uint64_t N, uint32_t p, uint64_t tol, float oversample,
                                                const DCut* __restrict__ Lcut, const DCut* __restrict__ Ucut,
                                                uint32_t* __restrict__ res, uint32_t* __restrict__ int_rep,
-                                               IntervalsOut& out) {
+                                               IntervalsOut& out, uint64_t* __restrict__ int_T = nullptr,
+                                               uint32_t* __restrict__ int_all = nullptr) {
     __shared__ uint32_t s_u32[32];
     __shared__ int32_t s_i32[32];
     __shared__ uint64_t s_u64[32];
@@ -129,6 +132,18 @@ __device__ __forceinline__ void intervals_body(uint32_t S, uint64_t N, uint32_t 
         uint64_t gtot;
         block_incl_scan<uint64_t>(f ? glen : 0ull, 0ull, AddU64(), s_u64, gtot);
         gamma += gtot;
+    }
+    if (int_T) {
+        __syncthreads();  // int_rep is complete
+        const double per_int = carry_f ? ((double)oversample * (double)p) / (double)carry_f : 0.0;
+        for (uint32_t u = threadIdx.x; u < carry_f; u += blockDim.x) {
+            const uint32_t rep = int_rep[u];
+            const DCut L = Lcut[rep], U = Ucut[rep];
+            const uint64_t len = U.rank - L.rank - (L.kind == kMember ? 1u : 0u);
+            const double q = len ? per_int / (double)len : 1.0;
+            if (q >= 1.0) { int_all[u] = 1u; int_T[u] = 0ull; }
+            else { int_all[u] = 0u; int_T[u] = (uint64_t)floor(ldexp(q, 64)); }
+        }
     }
     if (threadIdx.x == 0) {
         out.gamma = gamma;

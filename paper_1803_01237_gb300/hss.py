@@ -40,7 +40,11 @@ class HSSError(RuntimeError):
 
 class Params(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("seed", ctypes.c_uint64), ("p", ctypes.c_uint32),
-                ("oversample", ctypes.c_float), ("max_rounds", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+                ("oversample", ctypes.c_float), ("max_rounds", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("schedule", ctypes.c_uint32), ("schedule_k", ctypes.c_uint32)]
+
+
+SCHEDULES = {"proportional": 0, "theory": 1, "equal": 2}
 
 
 class Stats(ctypes.Structure):
@@ -211,9 +215,10 @@ def _result(keys, pay, spl, off, st: Stats) -> Result:
                   kernel_launches=int(st.kernel_launches))
 
 
-def _params(p, eps, seed, oversample, max_rounds, flags):
+def _params(p, eps, seed, oversample, max_rounds, flags, schedule="proportional", schedule_k=0):
     return Params(eps=float(eps), seed=int(seed) & ((1 << 64) - 1), p=int(p), oversample=float(oversample),
-                  max_rounds=int(max_rounds), flags=int(flags))
+                  max_rounds=int(max_rounds), flags=int(flags), schedule=SCHEDULES[schedule],
+                  schedule_k=int(schedule_k))
 
 
 # ---------------------------------------------------------------------------
@@ -249,13 +254,14 @@ def rank_cuts(sorted_keys, p: int, cuts: torch.Tensor, key_type: str = "u64", wa
 
 
 def partition(keys, p: int, eps: float, seed: int, oversample: float = 5.0, max_rounds: int = 0,
-              key_type: str = "u64", flags: int = 0, stream=None, allow_round_limit: bool = False):
+              key_type: str = "u64", flags: int = 0, stream=None, allow_round_limit: bool = False,
+              schedule: str = "proportional", schedule_k: int = 0):
     """Splitters and bucket offsets (hss_partition).  Returns (Result, ws)
     where the first N*8 bytes of ws hold the locally sorted keys."""
     lib = load()
     keys = _as_key_tensor(keys)
     N = keys.numel()
-    prm = _params(p, eps, seed, oversample, max_rounds, flags)
+    prm = _params(p, eps, seed, oversample, max_rounds, flags, schedule, schedule_k)
     nb = int(lib.hss_workspace_bytes(OP["partition"], N, ctypes.byref(prm), p, KEY_TYPES[key_type], 0))
     ws = workspace(nb, keys.device)
     spl = torch.empty((max(p - 1, 1), 2), dtype=torch.int64, device=keys.device)
@@ -351,12 +357,13 @@ def merge(bucket_keys, p: int, offsets: torch.Tensor, bucket_payload=None, key_t
 
 
 def sort(keys, p: int, eps: float, seed: int, payload=None, oversample: float = 5.0, max_rounds: int = 0,
-         key_type: str = "u64", flags: int = 0, out=None, out_payload=None, stream=None) -> Result:
+         key_type: str = "u64", flags: int = 0, out=None, out_payload=None, stream=None,
+         schedule: str = "proportional", schedule_k: int = 0) -> Result:
     """The whole method (hss_sort): globally sorted keys, splitters, offsets."""
     lib = load()
     keys = _as_key_tensor(keys)
     N = keys.numel()
-    prm = _params(p, eps, seed, oversample, max_rounds, flags)
+    prm = _params(p, eps, seed, oversample, max_rounds, flags, schedule, schedule_k)
     nb = int(lib.hss_workspace_bytes(OP["sort"], N, ctypes.byref(prm), p, KEY_TYPES[key_type], int(payload is not None)))
     ws = workspace(nb, keys.device)
     if out is None:

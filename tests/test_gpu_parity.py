@@ -289,3 +289,29 @@ def test_repeatable_and_launch_count(hss):
     r2 = hss.sort(keys, p, 0.02, 1)
     assert torch.equal(k1, r2.keys)
     assert hss.launch_count() - a == r1.kernel_launches + r2.kernel_launches > 0
+
+
+# ---------------------------------------------------------------------------
+# Sampling schedules: the k-round schedule of Theorem 4.7 and the
+# equal-per-interval (HykSort) sampling, bit-exact against the oracle.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("schedule,k", [("theory", 1), ("theory", 3), ("equal", 0)])
+@pytest.mark.parametrize("gen", ["uniform", "gauss_mix", "zipf"])
+def test_schedules_match_oracle(hss, schedule, k, gen):
+    N, p, eps, seed = 1 << 18, 32, 0.02, 7
+    keys = GENS[gen](N, seed)
+    res, _ = hss.partition(dev(keys), p, eps, seed, schedule=schedule, schedule_k=k)
+    ref = oracle.hss(keys, p, eps, seed, sort=False, schedule=schedule, schedule_k=k)
+    _cmp_partition(res, ref)
+
+
+def test_schedule_sort_output(hss):
+    N, p, eps, seed = 200003, 12, 0.01, 3
+    keys = inputs.gauss_mix(N, seed)
+    pay = np.arange(N, dtype=np.uint32)
+    for schedule, k in (("theory", 2), ("equal", 0)):
+        res = hss.sort(dev(keys), p, eps, seed, payload=dev(pay), schedule=schedule, schedule_k=k)
+        ref = oracle.hss(keys, p, eps, seed, payload=pay, schedule=schedule, schedule_k=k)
+        _cmp_partition(res, ref)
+        assert np.array_equal(host_u64(res.keys), ref.out_keys)
+        assert np.array_equal(res.payload.cpu().numpy().view(np.uint32), ref.out_payload)
