@@ -187,7 +187,10 @@ def run_gpu(args):
 
     N = 1 << LOG2N
     keys_h = inputs.uniform(N, SEED)
-    dists = DISTS if LOG2N == 28 and not args.uniform_only else (("uniform", SEED),)
+    if args.dist:
+        dists = tuple(d for d in DISTS if d[0] == args.dist)
+    else:
+        dists = DISTS if LOG2N == 28 and not args.uniform_only else (("uniform", SEED),)
     dev_inputs = []
     for name, sd in dists:
         kh = keys_h if name == "uniform" else inputs.SCALE_DISTRIBUTIONS[name](N, sd)
@@ -524,6 +527,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--uniform-only", action="store_true", help="time the uniform input only")
+    ap.add_argument("--dist", default=None, choices=[d[0] for d in DISTS], help="time one input only")
     ap.add_argument("--log2n", type=int, default=None,
                     help="smaller case of the same kernels (keeps 2^18 keys per segment); for profiling only")
     ap.add_argument("--workload", default="sort", choices=["sort", "batch", "serve", "rounds", "schedules"],

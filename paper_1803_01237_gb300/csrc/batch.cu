@@ -518,14 +518,25 @@ __global__ __launch_bounds__(256) void kb_exchange_copy(const uint64_t* __restri
     if (c0 >= n) return;
     const uint32_t c1 = min(n, c0 + kBXchChunk);
     const uint32_t* P = pos + J.lbase;
-    if (threadIdx.x == 0) {
-        uint32_t lo = 0, hi = p;
-        while (hi - lo > 1) { const uint32_t m = (lo + hi) >> 1; if (bpos(P, S, p, s, m, n) <= c0) lo = m; else hi = m; }
-        const uint32_t b0 = lo;
-        lo = b0; hi = p;
-        while (hi - lo > 1) { const uint32_t m = (lo + hi) >> 1; if (bpos(P, S, p, s, m, n) <= c1 - 1) lo = m; else hi = m; }
-        s_b0 = b0;
-        s_nb = lo - b0 + 1;
+    if (threadIdx.x < 32) {  // 32-way warp searches for the buckets meeting [c0, c1)
+        auto last_le = [&](uint32_t v, uint32_t lo, uint32_t hi) {
+            const uint32_t lane = threadIdx.x & 31;
+            while (hi - lo > 1) {
+                const uint32_t step = (hi - lo + 31) / 32;
+                const uint32_t m = lo + lane * step;
+                const bool ok = m < hi && bpos(P, S, p, s, m, n) <= v;
+                const uint32_t bal = __ballot_sync(0xffffffffu, ok);
+                lo = lo + (31 - __clz(bal)) * step;
+                hi = min(hi, lo + step);
+            }
+            return lo;
+        };
+        const uint32_t b0 = last_le(c0, 0, p);
+        const uint32_t b1 = last_le(c1 - 1, b0, p);
+        if (threadIdx.x == 0) {
+            s_b0 = b0;
+            s_nb = b1 - b0 + 1;
+        }
     }
     __syncthreads();
     const uint32_t b0 = s_b0, nb = s_nb;

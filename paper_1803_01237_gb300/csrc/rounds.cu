@@ -663,6 +663,25 @@ __global__ __launch_bounds__(1024) void k_exchange_dst(const uint64_t* __restric
     if (s1 == p && s0 < s1 && run != offsets[b + 1]) atomicOr(err, kDevErrBounds);
 }
 
+// Largest m in [lo, hi) with bucket_pos(m) <= v, given bucket_pos(lo) <= v,
+// by one full warp: each step splits the range into 32 parts and keeps the
+// last part whose first position is <= v (a few parallel loads instead of a
+// chain of dependent ones).
+__device__ __forceinline__ uint32_t warp_last_le(const uint32_t* __restrict__ pos, uint32_t S, uint32_t p, uint64_t s,
+                                                 uint32_t n, uint32_t v, uint32_t lo, uint32_t hi) {
+    const uint32_t lane = threadIdx.x & 31;
+    while (hi - lo > 1) {
+        const uint32_t step = (hi - lo + 31) / 32;
+        const uint32_t m = lo + lane * step;
+        const bool ok = m < hi && bucket_pos(pos, S, p, s, m, n) <= v;
+        const uint32_t bal = __ballot_sync(0xffffffffu, ok);  // lane 0 always holds
+        const uint32_t last = 31 - __clz(bal);
+        lo = lo + last * step;
+        hi = min(hi, lo + step);
+    }
+    return lo;
+}
+
 constexpr uint32_t kXchChunk = 4096;
 constexpr uint32_t kXchMaxB = 1024;
 
@@ -680,15 +699,14 @@ __global__ __launch_bounds__(256) void k_exchange_copy(const uint64_t* __restric
     const uint32_t c0 = blockIdx.y * kXchChunk;
     if (c0 >= n) return;
     const uint32_t c1 = min(n, c0 + kXchChunk);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
         // buckets b0..b1 whose runs meet [c0, c1): last b with pos(b) <= c0, last b with pos(b) <= c1-1
-        uint32_t lo = 0, hi = p;  // pos(lo) <= c0 < pos(hi) (pos(p) = n > c0)
-        while (hi - lo > 1) { const uint32_t m = (lo + hi) >> 1; if (bucket_pos(pos, S, p, s, m, n) <= c0) lo = m; else hi = m; }
-        const uint32_t b0 = lo;
-        lo = b0; hi = p;
-        while (hi - lo > 1) { const uint32_t m = (lo + hi) >> 1; if (bucket_pos(pos, S, p, s, m, n) <= c1 - 1) lo = m; else hi = m; }
-        s_b0 = b0;
-        s_nb = lo - b0 + 1;
+        const uint32_t b0 = warp_last_le(pos, S, p, s, n, c0, 0, p);
+        const uint32_t b1 = warp_last_le(pos, S, p, s, n, c1 - 1, b0, p);
+        if (threadIdx.x == 0) {
+            s_b0 = b0;
+            s_nb = b1 - b0 + 1;
+        }
     }
     __syncthreads();
     const uint32_t b0 = s_b0, nb = s_nb;

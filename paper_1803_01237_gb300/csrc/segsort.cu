@@ -238,6 +238,7 @@ __device__ __forceinline__ void block_rank(DigitOf digit_of, uint32_t count, uin
 // ---------------------------------------------------------------------------
 constexpr int kChipRadix = 1024;  // groups of the on-chip counting pass
 constexpr int kMaxBig = 64;       // groups above kTinyGroup keys that one segment may hold
+constexpr uint32_t kMixedMax = 256;  // a big group of distinct keys up to this size is ranked on chip
 
 // Exclusive scan of NV shared values in place by a CTA of T threads.
 template <int T, int NV>
@@ -303,7 +304,7 @@ constexpr int chip_radix() { return CAP <= kC0Cap ? 512 : kChipRadix; }
 template <int THREADS, int CAP>
 constexpr size_t msd_sort_smem() {
     return (size_t)CAP * 8 + 3 * (size_t)CAP * 2 + 2 * (chip_radix<CAP>() + 1) * 4 + 32 * 4 + 2 * 32 * 8 +
-           (size_t)(THREADS / 32) * kMaxBig * 4 + chip_radix<CAP>() + 64;
+           (size_t)(THREADS / 32) * kMaxBig * 4 + kMaxBig * 4 + chip_radix<CAP>() + 64;
 }
 
 template <bool PAY, int THREADS, int CAP>
@@ -314,6 +315,10 @@ __global__ __launch_bounds__(THREADS) void k_small_msd(
     uint32_t max_n, uint64_t flip_in, uint64_t flip_out, uint32_t* __restrict__ fb_list, uint32_t* __restrict__ fb_count) {
     constexpr int WARPS = THREADS / 32;
     constexpr int R = chip_radix<CAP>();
+    // Mixed big groups are ranked on chip in the two smaller classes; the
+    // largest class leaves such segments to the LSD kernel (measured faster
+    // there, where its larger groups come from clustered keys).
+    constexpr bool kMixed = CAP <= kC1Cap;
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* s_keys = (uint64_t*)smem;                        // CAP u64
     uint16_t* s_grp = (uint16_t*)(s_keys + CAP);               // CAP u16: positions grouped by digit
@@ -324,8 +329,9 @@ __global__ __launch_bounds__(THREADS) void k_small_msd(
     uint32_t* s_warp = s_run + (R + 1);               // 32
     uint64_t* s_red = (uint64_t*)(((uintptr_t)(s_warp + 32) + 7) & ~(uintptr_t)7);  // 2*32
     uint32_t* s_wcnt = (uint32_t*)(s_red + 64);                 // WARPS*kMaxBig: per-warp counts of the big groups
-    uint32_t* s_misc = s_wcnt + WARPS * kMaxBig;                // [0] big groups, [1] a big group holds distinct keys
-    uint8_t* s_bigid = (uint8_t*)(s_misc + 2);                  // R: index of a big group, 0xff otherwise
+    uint32_t* s_misc = s_wcnt + WARPS * kMaxBig;                // [0] big groups, [1] a mixed group above kMixedMax
+    uint32_t* s_mixed = s_misc + 2;                             // kMaxBig: the big group holds distinct keys
+    uint8_t* s_bigid = (uint8_t*)(s_mixed + kMaxBig);           // R: index of a big group, 0xff otherwise
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const uint64_t count = list ? (uint64_t)*nlist : nseg;
@@ -397,6 +403,8 @@ __global__ __launch_bounds__(THREADS) void k_small_msd(
             for (int d = tid; d < R; d += THREADS)
                 s_bigid[d] = (s_start[d + 1] - s_start[d] > (uint32_t)kTinyGroup)
                                  ? (uint8_t)min(atomicAdd(&s_misc[0], 1u), 255u) : (uint8_t)0xff;
+            if (kMixed)
+                for (int g = tid; g < kMaxBig; g += THREADS) s_mixed[g] = 0u;
             __syncthreads();
             if (s_misc[0] > (uint32_t)kMaxBig) {  // too many big groups: the LSD kernel takes this segment
                 if (tid == 0) fb_list[atomicAdd(fb_count, 1u)] = (uint32_t)s;
@@ -411,8 +419,11 @@ __global__ __launch_bounds__(THREADS) void k_small_msd(
             const uint64_t kx = s_keys[x];
             const uint32_t d = s_dig[x];
             const uint32_t a = s_start[d], b = s_start[d + 1];
-            if (b - a > (uint32_t)kTinyGroup) {  // big group: only check that it holds one key value
-                if (kx != s_keys[s_grp[a]]) s_misc[1] = 1u;
+            if (b - a > (uint32_t)kTinyGroup) {  // big group: only check whether it holds one key value
+                if (kx != s_keys[s_grp[a]]) {
+                    if (kMixed) s_mixed[s_bigid[d]] = 1u;
+                    if (!kMixed || b - a > kMixedMax) s_misc[1] = 1u;
+                }
                 continue;
             }
             uint32_t r = 0;
@@ -425,10 +436,26 @@ __global__ __launch_bounds__(THREADS) void k_small_msd(
         }
         __syncthreads();
         if (big) {
-            if (s_misc[1]) {  // a big group of distinct keys: the LSD kernel takes this segment
+            if (s_misc[1]) {  // a large group of distinct keys: the LSD kernel takes this segment
                 if (tid == 0) fb_list[atomicAdd(fb_count, 1u)] = (uint32_t)s;
                 __syncthreads();
                 continue;
+            }
+            // Big groups of distinct keys (at most kMixedMax): the same rank by
+            // (key, input position), quadratic in the group size.
+            for (uint32_t q = tid; kMixed && q < n; q += THREADS) {
+                const uint16_t x = s_grp[q];
+                const uint32_t d = s_dig[x];
+                const uint32_t a = s_start[d], b = s_start[d + 1];
+                if (b - a <= (uint32_t)kTinyGroup || !s_mixed[s_bigid[d]]) continue;
+                const uint64_t kx = s_keys[x];
+                uint32_t r = 0;
+                for (uint32_t g = a; g < b; ++g) {
+                    const uint16_t y = s_grp[g];
+                    const uint64_t ky = s_keys[y];
+                    r += (ky < kx || (ky == kx && y < x)) ? 1u : 0u;
+                }
+                s_out[a + r] = x;
             }
             // Members of each big group in input order: warp w walks the
             // positions [w*C, (w+1)*C) in order; pass A counts the members of
@@ -444,7 +471,8 @@ __global__ __launch_bounds__(THREADS) void k_small_msd(
             __syncwarp();
             for (uint32_t p0 = lo; p0 < hi; p0 += 32) {
                 const uint32_t e = p0 + lane;
-                const uint32_t g = e < hi ? (uint32_t)s_bigid[s_dig[e]] : 0xffu;
+                uint32_t g = e < hi ? (uint32_t)s_bigid[s_dig[e]] : 0xffu;
+                if (kMixed && g != 0xffu && s_mixed[g]) g = 0xffu;  // ranked above
                 const bool valid = g != 0xffu;
                 const uint32_t peers = __match_any_sync(0xffffffffu, valid ? g : 0x100u + lane);
                 if (valid && (peers & lt) == 0u) wc[g] += (uint32_t)__popc(peers);
@@ -463,7 +491,8 @@ __global__ __launch_bounds__(THREADS) void k_small_msd(
             for (uint32_t p0 = lo; p0 < hi; p0 += 32) {
                 const uint32_t e = p0 + lane;
                 const uint32_t d = e < hi ? (uint32_t)s_dig[e] : 0u;
-                const uint32_t g = e < hi ? (uint32_t)s_bigid[d] : 0xffu;
+                uint32_t g = e < hi ? (uint32_t)s_bigid[d] : 0xffu;
+                if (kMixed && g != 0xffu && s_mixed[g]) g = 0xffu;  // ranked above
                 const bool valid = g != 0xffu;
                 const uint32_t peers = __match_any_sync(0xffffffffu, valid ? g : 0x100u + lane);
                 const uint32_t before = valid ? wc[g] : 0u;
@@ -1248,9 +1277,12 @@ static cudaError_t launch_small_reg(const uint64_t* in, uint64_t* out, const uin
 
 // The stable LSD kernel over this level's fallback list (length on the device).
 template <bool PAY>
+// max_entries bounds the list on the host (the segments that could have
+// been appended): a CTA per entry at most, since each launch of this kernel
+// reconfigures the SMs for its large shared-memory tile.
 static cudaError_t launch_fallback(const uint64_t* in, uint64_t* out, const uint32_t* pin, uint32_t* pout,
                                    const uint64_t* seg_lo, const uint64_t* seg_hi, uint64_t fin, uint64_t fout,
-                                   const SegSortWs& ws, cudaStream_t st) {
+                                   const SegSortWs& ws, cudaStream_t st, uint64_t max_entries) {
     constexpr size_t smem = lsd_sort_smem<kC2Threads, kC2Items>();
     static bool attr = false;
     if (!attr) {
@@ -1259,7 +1291,9 @@ static cudaError_t launch_fallback(const uint64_t* in, uint64_t* out, const uint
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    HSS_LAUNCH((k_small_lsd<PAY, kC2Threads, kC2Items>), (unsigned)num_sms(), kC2Threads, smem, st, in, out, pin, pout,
+    const uint64_t grid = std::min<uint64_t>((uint64_t)num_sms(), max_entries);
+    if (grid == 0) return cudaSuccess;
+    HSS_LAUNCH((k_small_lsd<PAY, kC2Threads, kC2Items>), (unsigned)grid, kC2Threads, smem, st, in, out, pin, pout,
                seg_lo, seg_hi, ws.fb_list, ws.counters + 24, fin, fout);
     return cudaGetLastError();
 }
@@ -1307,7 +1341,7 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
                                                           nseg, nseg, (uint32_t)kC1Cap, (uint32_t)kSmallCap, L.flip_in,
                                                           fout, ws, st)) != cudaSuccess)
             return e;
-        return launch_fallback<PAY>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi, L.flip_in, fout, ws, st);
+        return launch_fallback<PAY>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi, L.flip_in, fout, ws, st, nseg);
     }
     for (;;) {
         if (L.nseg > ws.max_list) return cudaErrorInvalidValue;
@@ -1342,7 +1376,8 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
                                                                    ws, st)) != cudaSuccess)
             return e;
         if ((hc[0] || hc[1] || hc[2]) &&
-            (e = launch_fallback<PAY>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi, L.flip_in, fout, ws, st)) != cudaSuccess)
+            (e = launch_fallback<PAY>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi, L.flip_in, fout, ws, st,
+                                      (uint64_t)hc[0] + hc[1] + hc[2])) != cudaSuccess)
             return e;
         if (n_large == 0) return cudaSuccess;
         if (n_large > ws.max_large || tiles > ws.max_tiles || L.depth >= kMaxDepth) return cudaErrorInvalidValue;
