@@ -35,6 +35,7 @@ WORKLOAD = ("HSS sort: N=2^28 uint64 keys, p=1024 segments of 2^18, eps=0.02, s=
             "inputs: uniform [0,2^64) (seed 1), 32-Gaussian mixture sigma=2^40 (seed 2), Zipf s=1.2 over 2^12 values (seed 3)")
 DISTS = (("uniform", 1), ("gauss_mix", 2), ("zipf", 3))
 CPU_SAMPLE_LOG2N = 24      # cpu_baseline: first 2^24 keys, same p and eps
+PATH_BYTES_PER_KEY = 98.3  # algorithmic bytes of one whole hss_sort step per key (keys only)
 REF_SAMPLE_LOG2N = 22      # reference arm: first 2^22 keys per step
 
 
@@ -300,6 +301,13 @@ def run_gpu(args):
                      "bytes_per_launch": bytes_per_pass,
                      "peak_source": f"{peak_kind} hbm_gbs", "avg_launch_ms": avg_pass_ms,
                      "launches": pass_launches},
+        "path_roofline": {
+            "model": "algorithmic HBM bytes of the whole step per key: local sort 8 (statistics) + 16 (split) + 16 "
+                     "(on-chip sort), rounds ~2.3 (bitmap, probes), exchange 16, merge 8 + 16 + 16",
+            "bytes_per_key": PATH_BYTES_PER_KEY, "achieved_GBs": PATH_BYTES_PER_KEY * world * N / (ms / 1000.0) / 1e9,
+            "peak_GBs": peak, "frac": PATH_BYTES_PER_KEY * world * N / (ms / 1000.0) / 1e9 / peak,
+            "survey_lsd_model_bytes_per_key": 200,
+            "frac_of_lsd_model": 200.0 * world * N / (ms / 1000.0) / 1e9 / peak},
         "per_distribution": dist_report,
         "hss": {"rounds": rounds.rounds, "sample_size": rounds.sample_size, "gamma": rounds.gamma,
                 "tol": rounds.tol, "phase_ms": {k: v / args.steps for k, v in phase.items()},

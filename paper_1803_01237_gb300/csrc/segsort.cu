@@ -1095,8 +1095,9 @@ struct SplitArgs {
 template <bool PAY>
 __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitArgs A) {
     extern __shared__ __align__(16) unsigned char os_smem[];
-    uint64_t* s_keys = (uint64_t*)os_smem;            // kOsTile keys
-    uint32_t* s_pay = (uint32_t*)(s_keys + kOsTile);  // kOsTile payloads (PAY)
+    uint64_t* s_keys = (uint64_t*)os_smem;             // kOsTile keys
+    uint32_t* s_pay = (uint32_t*)(s_keys + kOsTile);   // kOsTile payloads (PAY)
+    uint8_t* s_dg = (uint8_t*)(s_pay + (PAY ? kOsTile : 0));  // kOsTile digits of the staged keys
     __shared__ uint32_t s_hist[kOsWarps * kRadix];
     __shared__ uint32_t s_total[kRadix], s_start[kRadix];
     __shared__ uint64_t s_gbase[kRadix];
@@ -1143,8 +1144,15 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
             if (PAY) pay[i] = 0;
         }
     }
+    // Each key's digit once, byte-packed in four registers.
+    uint32_t dpk[kOsItems / 4];
+#pragma unroll
+    for (int i = 0; i < kOsItems / 4; ++i) dpk[i] = 0;
+#pragma unroll
+    for (int i = 0; i < kOsItems; ++i)
+        dpk[i >> 2] |= split_digit(key[i], shift, dbase, dmult) << (8 * (i & 3));
     auto digit_of = [&](int i) -> uint32_t {
-        return (wbase + i * 32 < count) ? split_digit(key[i], shift, dbase, dmult) : (uint32_t)kRadix;
+        return (wbase + i * 32 < count) ? (dpk[i >> 2] >> (8 * (i & 3))) & 255u : (uint32_t)kRadix;
     };
     // Publish this tile's digit counts as soon as they are known, so the next
     // tile's look-back does not wait for our ranking.
@@ -1157,6 +1165,7 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
     for (int i = 0; i < kOsItems; ++i) {
         if (wbase + i * 32 < count) {
             s_keys[rank[i]] = key[i];
+            s_dg[rank[i]] = (uint8_t)((dpk[i >> 2] >> (8 * (i & 3))) & 255u);
             if (PAY) s_pay[rank[i]] = pay[i];
         }
     }
@@ -1197,7 +1206,7 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
     __syncthreads();
     for (uint32_t j = tid; j < count; j += kOsThreads) {
         const uint64_t k = s_keys[j];
-        const uint32_t d = split_digit(k, shift, dbase, dmult);
+        const uint32_t d = s_dg[j];
         const uint64_t dst = s_gbase[d] + j;
         if (dst - seg_base >= seg_n) {  // never taken when the digit offsets are consistent
             atomicOr(A.err, kDevErrBounds);
@@ -1410,7 +1419,7 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
         A.direct = ws.direct;
         A.status = ws.status; A.counter = ws.counters; A.err = ws.err;
         A.flip_in = L.flip_in; A.flip_out = fout;
-        const size_t smem = (size_t)kOsTile * 8 + (PAY ? (size_t)kOsTile * 4 : 0);
+        const size_t smem = (size_t)kOsTile * 9 + (PAY ? (size_t)kOsTile * 4 : 0);
         static bool attr = false;
         if (!attr) {
             if ((e = cudaFuncSetAttribute(k_split<PAY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
