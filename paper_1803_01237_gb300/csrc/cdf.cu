@@ -25,7 +25,7 @@ constexpr int kH = HSS_CDF_HIDDEN;
 constexpr int kP = HSS_CDF_NPARAM;
 constexpr int kOffB1 = kH, kOffW2 = 2 * kH, kOffB2 = 2 * kH + kH * kH, kOffW3 = kOffB2 + kH, kOffB3 = kOffW3 + kH;
 constexpr int kGradThreads = 256;
-constexpr int kMaxGradBlocks = 128;
+constexpr int kMaxGradBlocks = 32;  // training shares the GPU with the sorts it serves: a few SMs
 constexpr int kPartStride = kP + 3;  // gradient, loss partial, padding
 constexpr int kStage = kH + 1;       // padded row of a staged activation vector
 constexpr uint32_t kInitTag = 0x43444621u;

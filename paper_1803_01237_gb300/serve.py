@@ -216,12 +216,20 @@ class Server:
         ready = self.frozen_ready or (self.trainer is not None and self.trainer.ready)
         if self.model is None or not ready or req.key_type != self.model.key_type:
             return None
+        # Proposed cuts pay off when their bracket around each target rank is
+        # tighter than a sampling round's (about N / (s p) apart): with per
+        # cuts over a band of half-width delta, 2 delta N / (per - 1) < N / (5p),
+        # i.e. p delta < (per - 1) / 10.  Otherwise plain HSS is cheaper (the
+        # histogram of the cuts costs (p - 1) per x p searches).
+        delta = self._delta(req.p)
+        if req.p * delta * 10.0 >= self.per_splitter - 1:
+            return None
         # the proposed cuts may not exceed the round sample capacity
         cap = min(req.keys.numel(), math.ceil(10.0 * req.p) + 4096)
         per = max(1, min(self.per_splitter, cap // max(req.p - 1, 1)))
         try:
             with self.model_lock:
-                prop = self.model.propose(req.p, per, self._delta(req.p), stream=stream)
+                prop = self.model.propose(req.p, per, delta, stream=stream)
                 stream.synchronize()
             return prop
         except hss.HSSError:
