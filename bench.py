@@ -426,8 +426,10 @@ def run_serve_workload(args):
             clocks.start()
             st = srv.run(rr, realtime=True)
             clk = clocks.stop()
+            heldout = ([e for e, _ in srv.trainer.heldout] if srv.trainer is not None else None)
             srv.close()
             summ = st.summary()
+            summ["heldout_errors_last"] = heldout
             summ["rate_per_s"] = args.serve_rate if rate_name == "offered" else low_rate
             summ["clocks"] = clk
             results[f"{rate_name}_{mode}"] = summ

@@ -61,6 +61,48 @@ class Completion:
         return self.done - self.arrival
 
 
+def rounds_from(width: float, p: int, eps: float, s: float = 5.0) -> int:
+    """Expected sampling rounds until every splitter is resolved when each
+    splitter's interval holds a fraction `width` of the N keys, r = width p /
+    eps times the 2 tol = eps N / p window.  None when r <= 1.  One when
+    r <= 2: the bracket alone resolves about 1 / r of the splitters, and the
+    round's s p samples (Sec. 4.2.2) gather on the rest.  Else each round
+    shrinks the intervals by about s, plus one round for the largest of the
+    p - 1 random gaps."""
+    r = width * p / eps
+    if r <= 1.0:
+        return 0
+    if r <= 2.0:
+        return 1
+    return math.ceil(math.log(r) / math.log(s) - 1e-9) + 1
+
+
+def plain_rounds(p: int, eps: float, s: float = 5.0) -> int:
+    """Expected rounds of plain HSS: round 1 spreads s p samples over the
+    whole key range, leaving intervals of about N / (s p) keys; at least three
+    rounds, since round 1 resolves splitters only by chance."""
+    return max(3, 2 + math.ceil(math.log(max(1.0 / (s * eps), 1.0)) / math.log(s) - 1e-9))
+
+
+def plan_proposal(p: int, eps: float, delta: float, per_max: int, s: float = 5.0) -> tuple[int, int, int]:
+    """(per, expected rounds with the proposal, expected plain rounds), per = 0
+    when plain HSS is expected to be cheaper.  Rounds with a proposal count
+    the proposal's own ranking pass as one.
+
+    A proposal of per cuts per splitter spread over +-delta brackets each
+    target within 2 delta N / (per - 1) keys, at the price of ranking
+    (p - 1) per cuts over whole segments (plain round 1 ranks s p).  Taken:
+    the smallest per that reaches the fewest rounds, if it saves a round and
+    its cuts stay within s p x (1 + rounds saved)."""
+    plain = plain_rounds(p, eps, s)
+    best = (0, plain)
+    for per in range(2, per_max + 1):
+        r = 1 + rounds_from(2.0 * delta / (per - 1), p, eps, s)
+        if r < best[1] and (p - 1) * per <= s * p * (1 + plain - r):
+            best = (per, r)
+    return best[0], best[1], plain
+
+
 @dataclass
 class ServeStats:
     completions: list = field(default_factory=list)
@@ -88,9 +130,21 @@ class ServeStats:
             "mean_rounds_with_proposal": sum(with_prop) / len(with_prop) if with_prop else None,
             "mean_rounds_plain": sum(plain) / len(plain) if plain else None,
             "served_with_proposal": len(with_prop),
+            "mean_cuts_per_splitter": (sum(c.proposal.numel() / max(c.p - 1, 1) for c in ok if c.proposal is not None)
+                                       / len(with_prop) if with_prop else None),
             "max_in_flight": self.max_in_flight, "max_bytes_in_flight": self.max_bytes_in_flight,
             "makespan_s": self.makespan,
+            "by_p": {str(pp): self._by_p(ok, pp) for pp in sorted({c.p for c in ok})},
         }
+
+    @staticmethod
+    def _by_p(ok: list, p: int) -> dict:
+        cs = [c for c in ok if c.p == p]
+        lat = sorted(c.latency for c in cs)
+        wp = [c for c in cs if c.proposal is not None]
+        return {"requests": len(cs), "with_proposal": len(wp),
+                "mean_rounds": sum(c.rounds for c in cs) / len(cs),
+                "p50_ms": 1e3 * lat[(len(lat) - 1) // 2]}
 
 
 class _Trainer:
@@ -108,7 +162,7 @@ class _Trainer:
         self.interval = interval
         self.last_train = -1e9
         self.keep_jobs, self.min_jobs = keep_jobs, min_jobs
-        self.stream = torch.cuda.Stream(device=device)
+        self.stream = torch.cuda.Stream(device=device, priority=0)  # the lowest: requests come first
         self.shadow = hss.CDFModel(device)
         self.shadow.key_type = model.key_type
         with torch.cuda.stream(self.stream):
@@ -119,12 +173,26 @@ class _Trainer:
         self.jobs_seen = 0
         self.trainings = 0
         self.loss: float | None = None
+        # held-out error: (max |y(key) - rank/N| of the published model over a
+        # completed job's splitters, measured before it trains on that job, N)
+        self.heldout: list[tuple[float, int]] = []
+        self.keep_heldout = 4
+        self.max_pairs_per_job = 256
+        self.timeline: list[tuple[float, float, int]] = []  # (start, end, points) of each training run
         self.ready = False
         self.thread = threading.Thread(target=self._loop, daemon=True)
         self.thread.start()
 
-    def submit(self, keys: torch.Tensor, ranks: torch.Tensor, N: int, event: torch.cuda.Event):
-        self.q.put((keys, ranks, N, event))
+    def _heldout_dev(self, model: hss.CDFModel, keys: torch.Tensor, ranks: torch.Tensor, N: int) -> torch.Tensor:
+        """max |y(key) - rank / N| over one job's splitters, queued on the
+        trainer's stream (a device scalar)."""
+        y = model.eval(keys, stream=self.stream).to(torch.float64)
+        return (y - ranks.to(torch.float64) / N).abs().max()
+
+    def submit(self, res, N: int, event: torch.cuda.Event):
+        """Queue a completed job's result (its splitters and offsets become
+        training pairs once `event`, recorded after the job, has passed)."""
+        self.q.put((res, N, event))
 
     def stop(self):
         self.q.put(None)
@@ -146,22 +214,36 @@ class _Trainer:
                 except queue.Empty:
                     break
             with torch.cuda.stream(self.stream):
+                pending = []  # held-out errors on the device, read after the run
+                t_start = time.perf_counter()
                 for item in items:
                     if item is None:
                         stop = True
                         continue
-                    keys, ranks, N, ev = item
+                    res, N, ev = item
                     self.stream.wait_event(ev)
+                    res.splitters.record_stream(self.stream)
+                    res.offsets.record_stream(self.stream)
+                    keys, ranks = hss.training_pairs(res)
+                    if keys.numel() > self.max_pairs_per_job:  # evenly spaced quantiles suffice
+                        stride = -(-keys.numel() // self.max_pairs_per_job)
+                        keys, ranks = keys[::stride].contiguous(), ranks[::stride].contiguous()
+                    if self.trainings > 0 and keys.numel() > 0:
+                        pending.append((self._heldout_dev(self.shadow, keys, ranks, N), N))
                     scaled = (ranks.to(torch.float64) * (self.SCALE / N)).to(torch.int64)
                     self.pairs.append((keys, scaled))
                     self.jobs_seen += 1
                 self.pairs = self.pairs[-self.keep_jobs:]
-                if stop or self.jobs_seen < self.min_jobs or not self.pairs:
-                    continue
-                tk = torch.cat([k for k, _ in self.pairs])
-                tr = torch.cat([r for _, r in self.pairs])
-                loss = self.shadow.train(tk, tr, self.SCALE, self.steps, self.lr, stream=self.stream)
+                train = not stop and self.jobs_seen >= self.min_jobs and bool(self.pairs)
+                if train:
+                    tk = torch.cat([k for k, _ in self.pairs])
+                    tr = torch.cat([r for _, r in self.pairs])
+                    loss = self.shadow.train(tk, tr, self.SCALE, self.steps, self.lr, stream=self.stream)
                 self.stream.synchronize()
+                for err, N in pending:
+                    self.heldout = (self.heldout + [(float(err.item()), N)])[-self.keep_heldout:]
+                if not train:
+                    continue
                 with self.lock:
                     self.model.buf.copy_(self.shadow.buf)
                     self.stream.synchronize()
@@ -169,6 +251,7 @@ class _Trainer:
                     self.trainings += 1
                     self.ready = True
                 self.last_train = time.perf_counter()
+                self.timeline.append((t_start, self.last_train, int(tk.numel())))
 
 
 class Server:
@@ -177,26 +260,34 @@ class Server:
     slots          concurrent requests on the device (one stream each)
     hbm_budget     bytes of workspace admitted at once (None: no limit)
     model          CDF network to train online and propose from (None: plain)
-    per_splitter   proposed cuts per splitter; delta = 3 sqrt(training loss)
+    per_splitter   most proposed cuts per splitter (each request takes the
+                   fewest that reach its fewest expected rounds, see plan)
     train          whether completed jobs train the model (False: frozen)
     train_interval seconds between training runs once the model serves
+    delta          band half-width of a frozen model's cuts (a fraction of N;
+                   at least 0.25 / p); a trained model derives it from its
+                   held-out errors over the recent jobs (see _delta)
     """
 
     def __init__(self, slots: int = 4, hbm_budget: int | None = None, model: hss.CDFModel | None = None,
                  per_splitter: int = 16, train: bool = True, train_steps: int = 100, lr: float = 0.01,
-                 keep_jobs: int = 16, min_jobs: int = 2, train_interval: float = 0.0, device=None):
+                 keep_jobs: int = 16, min_jobs: int = 2, train_interval: float = 0.0, delta: float = 0.0,
+                 device=None):
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.slots = slots
         self.hbm_budget = hbm_budget
         self.model = model
         self.per_splitter = per_splitter
+        self.frozen_delta = delta
         self.model_lock = threading.Lock()
         self.trainer = None
         self.frozen_ready = model is not None and not train
         if model is not None and train:
             self.trainer = _Trainer(model, self.model_lock, train_steps, lr, keep_jobs, min_jobs, self.device,
                                     train_interval)
-        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
+        # high-priority streams: the block scheduler serves a request's
+        # kernels before the trainer's, which only fill idle SMs
+        self.streams = [torch.cuda.Stream(device=self.device, priority=-1) for _ in range(slots)]
         self.slot_ws = [None] * slots
         self.cv = threading.Condition()
         self.free_slots = list(range(slots))
@@ -207,26 +298,41 @@ class Server:
         ws = hss.workspace_bytes("partition", n, p, key_type, False, oversample=oversample)
         return ws + 16 * max(p - 1, 1) + 8 * (p + 1) + 8 * nprop
 
-    def _delta(self, p: int) -> float:
-        loss = self.trainer.loss if self.trainer is not None else None
-        base = 3.0 * math.sqrt(loss) if loss is not None else 0.0
+    # a job of n keys drawn from the modelled distribution has its own CDF
+    # within sqrt(ln(2 / alpha) / (2 n)) of it with probability 1 - alpha
+    # (the Dvoretzky-Kiefer-Wolfowitz inequality, Massart's constant)
+    ALPHA = 0.01
+
+    @classmethod
+    def _dkw(cls, n: int) -> float:
+        return math.sqrt(math.log(2.0 / cls.ALPHA) / (2.0 * max(n, 1)))
+
+    def _delta(self, p: int, n: int) -> float:
+        """Half-width of the band of proposed cuts around each target i/p for
+        a job of n keys: 1.25 x (the model's error beyond sampling noise, the
+        largest over the recent held-out jobs, + the job's own sampling noise).
+        A frozen model uses the `delta` it was given; a trained one without
+        held-out jobs yet, 3 x its RMS training error."""
+        t = self.trainer
+        if t is not None and t.heldout:
+            model_err = max(max(0.0, e - self._dkw(m)) for e, m in t.heldout)
+            base = 1.25 * (model_err + self._dkw(n))
+        elif t is not None and t.loss is not None:
+            base = 3.0 * math.sqrt(t.loss)
+        else:
+            base = self.frozen_delta
         return max(base, 0.25 / p)
 
     def _propose(self, req: Request, stream) -> torch.Tensor | None:
         ready = self.frozen_ready or (self.trainer is not None and self.trainer.ready)
         if self.model is None or not ready or req.key_type != self.model.key_type:
             return None
-        # Proposed cuts pay off when their bracket around each target rank is
-        # tighter than a sampling round's (about N / (s p) apart): with per
-        # cuts over a band of half-width delta, 2 delta N / (per - 1) < N / (5p),
-        # i.e. p delta < (per - 1) / 10.  Otherwise plain HSS is cheaper (the
-        # histogram of the cuts costs (p - 1) per x p searches).
-        delta = self._delta(req.p)
-        if req.p * delta * 10.0 >= self.per_splitter - 1:
-            return None
+        delta = self._delta(req.p, req.keys.numel())
         # the proposed cuts may not exceed the round sample capacity
         cap = min(req.keys.numel(), math.ceil(10.0 * req.p) + 4096)
-        per = max(1, min(self.per_splitter, cap // max(req.p - 1, 1)))
+        per, _, _ = plan_proposal(req.p, req.eps, delta, min(self.per_splitter, cap // max(req.p - 1, 1)))
+        if per == 0:
+            return None
         try:
             with self.model_lock:
                 prop = self.model.propose(req.p, per, delta, stream=stream)
@@ -251,14 +357,14 @@ class Server:
                 if res is None:
                     res, _ = self._partition(req, None, stream, slot)
                 stream.synchronize()
-                if self.trainer is not None:
-                    tk, tr = hss.training_pairs(res)
-                    ev = torch.cuda.Event()
-                    ev.record(stream)
-                    self.trainer.submit(tk, tr, req.keys.numel(), ev)
         except Exception as e:  # recorded per request; the server keeps going
             err = repr(e)
-        done = time.perf_counter() - t0
+        done = time.perf_counter() - t0  # the result is ready
+        if self.trainer is not None and res is not None and err is None:
+            # the trainer extracts the pairs on its own stream
+            ev = torch.cuda.Event()
+            ev.record(stream)
+            self.trainer.submit(res, req.keys.numel(), ev)
         c = Completion(rid=req.rid, arrival=req.arrival, admitted=admitted, done=done,
                        rounds=res.rounds if res else -1, status=res.status if res else -1, n=req.keys.numel(),
                        p=req.p, tol=res.tol if res else -1, offsets=res.offsets if res else None,
@@ -353,6 +459,7 @@ class Server:
                 w = hss.CDFModel(self.device)
                 w.buf.copy_(self.model.buf)
                 w.train(tk, tr, n, 2, 0.01, stream=self.trainer.stream)
+                self.trainer._heldout_dev(w, tk[::2].contiguous(), tr[::2].contiguous(), n)
                 self.trainer.stream.synchronize()
 
     def close(self):

@@ -100,14 +100,15 @@ def test_online_training_saves_rounds(mods):
     hss, serve = mods
     pool = _pool(3, 1 << 22, 70)
     m = hss.CDFModel().init(3, "log", 1, (1 << 63) - 1)
-    reqs = serve.poisson_requests(pool, 40, rate=200.0, seed=6, lo_log2=19, hi_log2=22, ps=(128, 256))
+    reqs = serve.poisson_requests(pool, 80, rate=200.0, seed=6, lo_log2=19, hi_log2=22, ps=(16, 32))
     srv = serve.Server(slots=3, model=m, train=True, train_steps=150)
     srv.warmup()
     st = srv.run(reqs, realtime=True)
+    heldout = list(srv.trainer.heldout)
     srv.close()
     s = st.summary()
-    print(s)
-    assert s["completed"] == 40
+    print(s, "held-out errors", heldout)
+    assert s["completed"] == 80
     for c in st.completions:
         _check_contract(c)
     assert s["served_with_proposal"] >= 20
