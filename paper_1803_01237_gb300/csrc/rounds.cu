@@ -170,8 +170,7 @@ __global__ __launch_bounds__(kSampThreads) void k_sample_mark(
         const uint32_t nu = min((uint32_t)kIntChunk, nint - u0);
         const uint32_t P = load_seg_intervals(s, (uint32_t)(seg_off[s + 1] - base), S, u0, nu, Lpos, Upos, Lcut, int_rep,
                                               s_a, s_b, s_pre, s_warp);
-        for (uint32_t f = threadIdx.x; f < P; f += kSampThreads) {
-            const uint32_t u = find_interval(s_pre, nu, f);
+        for_each_pair(s_pre, nu, P, [&](uint32_t u, uint32_t f) {
             const uint32_t a = s_a[u], b = s_b[u];
             const uint32_t m = (a >> 1) + (f - s_pre[u]);
             uint64_t w0, w1;
@@ -193,7 +192,7 @@ __global__ __launch_bounds__(kSampThreads) void k_sample_mark(
                 atomicOr(&bitmap[g >> 5], 1u << (g & 31));
                 ++cnt;
             }
-        }
+        });
         __syncthreads();
     }
     uint32_t tot;

@@ -215,4 +215,20 @@ __device__ __forceinline__ uint32_t find_interval(const uint32_t* s_pre, uint32_
     return lo;
 }
 
+// Visit the pairs f in [0, P) of one interval chunk, body(u, f) with u the
+// interval of pair f.  Each thread takes a contiguous block of pairs, so one
+// search finds the interval of its first pair and the others follow by a
+// forward walk over the (non-decreasing) interval starts.
+template <class Body>
+__device__ __forceinline__ void for_each_pair(const uint32_t* s_pre, uint32_t nu, uint32_t P, Body body) {
+    const uint32_t per = (P + kSampThreads - 1) / kSampThreads;
+    const uint32_t f0 = min(P, threadIdx.x * per), f1 = min(P, f0 + per);
+    if (f0 >= f1) return;
+    uint32_t u = find_interval(s_pre, nu, f0);
+    for (uint32_t f = f0; f < f1; ++f) {
+        while (u + 1 < nu && s_pre[u + 1] <= f) ++u;
+        body(u, f);
+    }
+}
+
 }  // namespace hss
