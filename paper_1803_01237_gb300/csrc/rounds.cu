@@ -681,7 +681,7 @@ __device__ __forceinline__ uint32_t warp_last_le(const uint32_t* __restrict__ po
     return lo;
 }
 
-constexpr uint32_t kXchChunk = 4096;
+constexpr uint32_t kXchChunk = 8192;
 constexpr uint32_t kXchMaxB = 1024;
 
 __global__ __launch_bounds__(256) void k_exchange_copy(const uint64_t* __restrict__ skeys, const uint32_t* __restrict__ spay,
@@ -712,13 +712,30 @@ __global__ __launch_bounds__(256) void k_exchange_copy(const uint64_t* __restric
     if (nb <= kXchMaxB) {
         for (uint32_t i = threadIdx.x; i <= nb; i += blockDim.x) s_bnd[i] = bucket_pos(pos, S, p, s, b0 + i, n);
         __syncthreads();
-        for (uint32_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
-            uint32_t lo = 0, hi = nb;  // last i with s_bnd[i] <= j
-            while (hi - lo > 1) { const uint32_t m = (lo + hi) >> 1; if (s_bnd[m] <= j) lo = m; else hi = m; }
-            const uint64_t d = dst[s * p + b0 + lo] + (j - s_bnd[lo]);
-            if (d >= N) { atomicOr(err, kDevErrBounds); continue; }
-            bkeys[d] = skeys[base + j];
-            if (bpay) bpay[d] = spay[base + j];
+        // Four keys per thread per step, their loads issued together (memory
+        // parallelism); j grows by the CTA width, so the run of j follows
+        // from the previous one by a forward walk (runs are about as long as
+        // a step).
+        uint32_t lo = 0;
+        for (uint32_t j0 = c0 + threadIdx.x; j0 < c1; j0 += 4 * blockDim.x) {
+            uint64_t kv[4];
+            uint32_t pv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t j = j0 + u * blockDim.x;
+                kv[u] = j < c1 ? skeys[base + j] : 0ull;
+                pv[u] = (bpay && j < c1) ? spay[base + j] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t j = j0 + u * blockDim.x;
+                if (j >= c1) break;
+                while (lo + 1 < nb && s_bnd[lo + 1] <= j) ++lo;
+                const uint64_t d = dst[s * p + b0 + lo] + (j - s_bnd[lo]);
+                if (d >= N) { atomicOr(err, kDevErrBounds); continue; }
+                bkeys[d] = kv[u];
+                if (bpay) bpay[d] = pv[u];
+            }
         }
     } else {
         for (uint32_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
