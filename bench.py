@@ -395,6 +395,59 @@ def run_batch_workload(args):
     return 0
 
 
+def run_morton_workload(args):
+    """Config 3: N = 2^30 64-bit Morton keys of a seeded Plummer sphere (21
+    bits per axis) with the particle index as a u32 payload, p = 16384,
+    eps = 0.01.  A step is one hss_sort of keys and payload, both resident
+    in HBM (12 GiB in, 12 GiB out: larger than L2, no flush)."""
+    import numpy as np
+    import torch
+    from paper_1803_01237_gb300 import hss, inputs
+
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    hss.load()
+    N, P, E, SEED = 1 << args.morton_log2n, 16384, 0.01, 7
+    kh, ph = inputs.plummer_morton(N, SEED)
+    keys = torch.from_numpy(kh.view(np.int64)).to(dev)
+    pay = torch.from_numpy(ph.view(np.int32)).to(dev)
+    del kh, ph
+    out, out_p = torch.empty_like(keys), torch.empty_like(pay)
+    for _ in range(args.warmup):
+        hss.sort(keys, P, E, SEED, payload=pay, out=out, out_payload=out_p)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = hss.launch_count()
+    phase = {}
+    ev0.record()
+    for _ in range(args.steps):
+        r = hss.sort(keys, P, E, SEED, payload=pay, out=out, out_payload=out_p, flags=hss.FLAG_TIMING)
+        for k, v in r.ms_phase.items():
+            phase[k] = phase.get(k, 0.0) + v / args.steps
+    ev1.record()
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    launches = hss.launch_count() - l0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    o = out[:: max(1, N // (1 << 20))].cpu().numpy().view(np.uint64)
+    line = {
+        "metric": "keys/s (HSS sort with u32 payload)", "value": N / (ms / 1000.0), "unit": "keys/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"HSS sort of 2^{args.morton_log2n} Morton keys (Plummer sphere, 21 bits per axis) "
+                               "+ u32 payload, p = 16384, eps = 0.01",
+                   "N": N, "p": P, "eps": E, "l2": "inputs larger than L2; no flush"},
+        "hss": {"rounds": r.rounds, "sample_size": r.sample_size, "phase_ms": phase,
+                "output_sorted": bool(np.all(o[:-1] <= o[1:]))},
+        "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serve_workload(args):
     """Config 5: Poisson arrivals at 2000 partition requests/s, sizes
     log-uniform in [2^16, 2^26], p in {256, 1024, 4096}, eps = 0.02,
@@ -540,19 +593,22 @@ def main():
     ap.add_argument("--dist", default=None, choices=[d[0] for d in DISTS], help="time one input only")
     ap.add_argument("--log2n", type=int, default=None,
                     help="smaller case of the same kernels (keeps 2^18 keys per segment); for profiling only")
-    ap.add_argument("--workload", default="sort", choices=["sort", "batch", "serve", "rounds", "schedules"],
+    ap.add_argument("--workload", default="sort", choices=["sort", "batch", "serve", "rounds", "schedules", "morton"],
                     help="sort: the N=2^28 bench line (default); batch: 4096 independent jobs; serve: Poisson requests")
     ap.add_argument("--batch-jobs", type=int, default=4096)
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-low-rate", type=float, default=300.0)
+    ap.add_argument("--morton-log2n", type=int, default=30, help="config 3 size (morton workload)")
     args = ap.parse_args()
     if args.workload == "batch" and args.impl == "gb300":
         args.warmup = max(args.warmup, 1)
         return run_batch_workload(args)
     if args.workload == "serve" and args.impl == "gb300":
         return run_serve_workload(args)
+    if args.workload == "morton" and args.impl == "gb300":
+        return run_morton_workload(args)
     if args.workload == "rounds" and args.impl == "gb300":
         return run_rounds_workload(args)
     if args.workload == "schedules" and args.impl == "gb300":

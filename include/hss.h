@@ -53,6 +53,16 @@ extern "C" {
 /* params.flags */
 #define HSS_FLAG_SYNC 1u     /* synchronize `stream` before returning */
 #define HSS_FLAG_TIMING 2u   /* record per-phase device times into hss_stats (implies SYNC) */
+/* Histogram form of the splitter rounds (Sec. 3.3 step 2; the result is the
+ * same either way).  By default each round chooses: when all its probes
+ * share one interval (round 1) and searching every segment for every probe
+ * (Z p log2(N/p) dependent loads) would cost more than eight reads of the
+ * keys, a staged form ranks blocks of sorted probes against the keys between
+ * the block's first and last probe, staged in shared memory; else every
+ * probe is searched in every segment.  These flags force one form (at most
+ * one may be set, else HSS_ERR_INVALID). */
+#define HSS_FLAG_HIST_PROBE 4u
+#define HSS_FLAG_HIST_STAGED 8u
 
 /* Workspace queries (op argument of hss_workspace_bytes). */
 #define HSS_OP_SORT 0

@@ -87,7 +87,13 @@ static bool params_ok(const hss_params* prm) {
     if (!(prm->oversample > 0.0f) || !std::isfinite(prm->oversample)) return false;
     if (prm->max_rounds > HSS_MAX_ROUNDS) return false;
     if (prm->schedule > HSS_SCHEDULE_EQUAL || (prm->schedule == HSS_SCHEDULE_THEORY && prm->schedule_k == 0)) return false;
+    if ((prm->flags & HSS_FLAG_HIST_PROBE) && (prm->flags & HSS_FLAG_HIST_STAGED)) return false;
     return true;
+}
+static uint32_t hist_mode(const hss_params* prm) {
+    if (prm->flags & HSS_FLAG_HIST_PROBE) return kHistProbe;
+    if (prm->flags & HSS_FLAG_HIST_STAGED) return kHistStaged;
+    return kHistAuto;
 }
 
 // Oversampling that sizes the round sample buffers: s, or under the k-round
@@ -187,7 +193,8 @@ static int run_path(const void* d_keys, const uint32_t* d_payload, int key_type,
     // Splitter rounds (Sec. 4.2.2).
     RoundResult rr;
     int status = run_rounds(keysA, seg_off, N, p, prm->eps, prm->seed, s, eff_rounds(prm), key_type, d_splitters,
-                            d_offsets, rws, st, &rr, (const uint64_t*)d_prop, nprop, prm->schedule, prm->schedule_k);
+                            d_offsets, rws, st, &rr, (const uint64_t*)d_prop, nprop, prm->schedule, prm->schedule_k,
+                            hist_mode(prm));
     tm.mark(HSS_PHASE_ROUNDS);
     if (status == HSS_ERR_CUDA) return status;
 

@@ -335,6 +335,99 @@ __global__ __launch_bounds__(256) void k_histogram(
     }
 }
 
+// The histogram of a round whose probes all share one interval (round 1,
+// and the proposal pass: every interval is then the whole key range).  A CTA
+// ranks kStgProbes consecutive sorted probes in kStgSegs segments.  In each
+// segment their positions lie between the rank of the first probe (strict
+// compare) and that of the last (non-strict), so the keys in between are
+// staged in shared memory once and every probe is searched there.  Same
+// positions as k_histogram; per segment and probe block about one read of
+// the keys between the block's first and last probe, instead of one search
+// of the whole segment in HBM per probe.
+constexpr int kStgThreads = 256;
+constexpr int kStgPer = 4;                          // probes per thread
+constexpr int kStgProbes = kStgThreads * kStgPer;   // probes per CTA
+constexpr int kStgSegs = 8;                         // segments per CTA
+constexpr uint32_t kStgCap = 4096;                  // staged keys (32 KB)
+
+__global__ __launch_bounds__(kStgThreads) void k_histogram_staged(
+    const uint64_t* __restrict__ skeys, const uint64_t* __restrict__ seg_off, uint32_t p, uint32_t S,
+    const uint32_t* __restrict__ Lpos, const uint32_t* __restrict__ Upos, const uint32_t* __restrict__ int_rep,
+    const uint64_t* __restrict__ pkey, const int32_t* __restrict__ pseg, const uint32_t* __restrict__ pspos,
+    uint64_t Z, uint64_t* __restrict__ prank, uint32_t* __restrict__ probe_pos, uint64_t cap,
+    uint32_t* __restrict__ err) {
+    __shared__ uint64_t s_keys[kStgCap];
+    __shared__ uint32_t s_lo[kStgSegs], s_a[kStgSegs], s_b[kStgSegs], s_ok[kStgSegs];
+    const uint64_t k0 = (uint64_t)blockIdx.x * kStgProbes;
+    const uint64_t k1 = min(Z, k0 + (uint64_t)kStgProbes);
+    const uint32_t s0 = blockIdx.y * kStgSegs;
+    const uint32_t rep = int_rep[0];
+    uint64_t key[kStgPer], part[kStgPer];
+    int32_t seg[kStgPer];
+    uint32_t spos[kStgPer];
+#pragma unroll
+    for (int u = 0; u < kStgPer; ++u) {
+        const uint64_t k = k0 + threadIdx.x + (uint64_t)u * kStgThreads;
+        part[u] = 0;
+        key[u] = 0; seg[u] = 0; spos[u] = 0;
+        if (k < k1) { key[u] = pkey[k]; seg[u] = pseg[k]; spos[u] = pspos[k]; }
+    }
+    // bounds of the block's probes in each segment, by 2 kStgSegs threads
+    if (threadIdx.x < 2 * kStgSegs) {
+        const uint32_t i = threadIdx.x >> 1, s = s0 + i;
+        if (s < p) {
+            const uint32_t n = (uint32_t)(seg_off[s + 1] - seg_off[s]);
+            const uint32_t lo = Lpos[(uint64_t)s * S + rep], hi = Upos[(uint64_t)s * S + rep];
+            const bool ok = lo <= hi && hi <= n;
+            uint32_t v = 0;
+            if (ok) {
+                const uint64_t* w = skeys + seg_off[s] + lo;
+                v = (threadIdx.x & 1) ? count_below(w, hi - lo, pkey[k1 - 1], false)
+                                      : count_below(w, hi - lo, pkey[k0], true);
+            }
+            if (threadIdx.x & 1) {
+                s_b[i] = v;
+            } else {
+                s_a[i] = v;
+                s_lo[i] = lo;
+                s_ok[i] = ok ? 1u : 0u;
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = 0; i < kStgSegs; ++i) {
+        const uint32_t s = s0 + i;
+        if (s >= p) break;  // uniform per CTA
+        const uint32_t lo = s_lo[i], a = s_a[i];
+        const bool ok = s_ok[i] != 0u;
+        const uint32_t m = ok ? s_b[i] - a : 0u;
+        const bool staged = m <= kStgCap;
+        const uint64_t* w = skeys + seg_off[s] + lo + a;
+        if (ok && staged)
+            for (uint32_t j = threadIdx.x; j < m; j += kStgThreads) s_keys[j] = w[j];
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kStgPer; ++u) {
+            const uint64_t k = k0 + threadIdx.x + (uint64_t)u * kStgThreads;
+            if (k >= k1) continue;
+            uint32_t pos;
+            if ((int32_t)s == seg[u]) pos = spos[u];
+            else if (!ok) pos = lo;  // inconsistent interval state: recorded below, nothing read
+            else if (staged) pos = lo + a + count_below(s_keys, m, key[u], (int32_t)s > seg[u]);
+            else pos = lo + a + count_below(w, m, key[u], (int32_t)s > seg[u]);
+            probe_pos[(uint64_t)s * cap + k] = pos;
+            part[u] += pos;
+        }
+        if (!ok && threadIdx.x == 0) atomicOr(err, kDevErrBounds);
+        __syncthreads();  // s_keys is rewritten for the next segment
+    }
+#pragma unroll
+    for (int u = 0; u < kStgPer; ++u) {
+        const uint64_t k = k0 + threadIdx.x + (uint64_t)u * kStgThreads;
+        if (k < k1) atomicAdd((unsigned long long*)&prank[k], (unsigned long long)part[u]);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Proposed cuts (a learned splitter proposal): non-member cuts (k, -1) that
 // sort before every input key equal to k.  They are ranked and offered to the
@@ -526,7 +619,7 @@ static void enqueue_sampling(const RoundWs& ws, const uint64_t* d_seg_off, uint6
 int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uint32_t p, double eps, uint64_t seed,
                float oversample, uint32_t max_rounds, int key_type, hss_cut* d_splitters, uint64_t* d_offsets,
                const RoundWs& ws, cudaStream_t st, RoundResult* out, const uint64_t* d_prop, uint32_t nprop,
-               uint32_t schedule, uint32_t schedule_k) {
+               uint32_t schedule, uint32_t schedule_k, uint32_t hist_mode) {
     const uint32_t S = p - 1;
     const uint64_t tol = (uint64_t)std::floor(((double)N * eps) / (2.0 * (double)p));
     const bool per_interval = schedule == HSS_SCHEDULE_EQUAL;
@@ -545,6 +638,24 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
         }
         HSS_LAUNCH(k_intervals, 1, 1024, 0, st, S, N, p, tol, oversample, ws.Lcut, ws.Ucut, ws.res, ws.int_rep, ws.ctl,
                    schedule, Tq, allq, ws.int_T, ws.int_all);
+    };
+    // The histogram of Z probes: staged when they share one interval and
+    // searching every segment for every probe (Z p log2(N/p) dependent loads)
+    // would cost several reads of the keys (the probe-side form otherwise).
+    auto histogram = [&](uint64_t Z, uint32_t nint) -> cudaError_t {
+        const double searches = (double)Z * (double)p * std::log2((double)N / (double)p + 2.0);
+        const bool staged = nint == 1 && hist_mode != kHistProbe &&
+                            (hist_mode == kHistStaged || searches >= 8.0 * (double)N);
+        if (staged) {
+            HSS_LAUNCH(k_histogram_staged, dim3((unsigned)cdiv(Z, kStgProbes), (unsigned)cdiv(p, kStgSegs)), kStgThreads, 0,
+                       st, skeys, d_seg_off, p, S, ws.Lpos, ws.Upos, ws.int_rep, ws.pkey, ws.pseg, ws.pspos, Z, ws.prank,
+                       ws.probe_pos, ws.cap, ws.sws.err);
+        } else {
+            HSS_LAUNCH(k_histogram, dim3((unsigned)cdiv(Z, 32), (unsigned)cdiv(p, kHistSegPerBlock)), 256, 0, st, skeys,
+                       d_seg_off, p, S, ws.Lpos, ws.Upos, ws.int_rep, ws.pkey, ws.pseg, ws.pspos, ws.pint, Z, ws.prank,
+                       ws.probe_pos, ws.cap, ws.sws.err);
+        }
+        return cudaGetLastError();
     };
     HSS_TRY(cudaMemsetAsync(ws.ctl, 0, sizeof(RoundCtl), st));
     if (S == 0) {
@@ -567,9 +678,7 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
                         false, ws.sws, st, nullptr));
         HSS_LAUNCH(k_prop_probes, (unsigned)cdiv(nprop, 256), 256, 0, st, nprop, ws.skey_sorted, ws.pkey, ws.pseg,
                    ws.pspos, ws.pint, ws.prank);
-        HSS_LAUNCH(k_histogram, dim3((unsigned)cdiv(nprop, 32), (unsigned)cdiv(p, kHistSegPerBlock)), 256, 0, st, skeys,
-                   d_seg_off, p, S, ws.Lpos, ws.Upos, ws.int_rep, ws.pkey, ws.pseg, ws.pspos, ws.pint, (uint64_t)nprop,
-                   ws.prank, ws.probe_pos, ws.cap, ws.sws.err);
+        HSS_TRY(histogram((uint64_t)nprop, 1u));
         HSS_LAUNCH(k_update, sblk, 256, 0, st, S, N, p, ws.pkey, ws.pseg, ws.pspos, ws.prank, (uint64_t)nprop,
                    (int32_t)kNonMember, ws.Lcut, ws.Ucut, ws.chgL, ws.chgU);
         HSS_LAUNCH(k_update_pos, dim3(p, sblk), 256, 0, st, S, ws.chgL, ws.chgU, ws.probe_pos, ws.cap, ws.Lpos, ws.Upos);
@@ -598,9 +707,7 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
                             false, ws.sws, st, nullptr));
             HSS_LAUNCH(k_probe_build, (unsigned)cdiv(Z, 256), 256, 0, st, Z, ws.skey_sorted, ws.sperm, ws.sseg, ws.sspos,
                        ws.Ucut, ws.int_rep, ws.ctl, ws.pkey, ws.pseg, ws.pspos, ws.pint, ws.prank);
-            HSS_LAUNCH(k_histogram, dim3((unsigned)cdiv(Z, 32), (unsigned)cdiv(p, kHistSegPerBlock)), 256, 0, st, skeys,
-                       d_seg_off, p, S, ws.Lpos, ws.Upos, ws.int_rep, ws.pkey, ws.pseg, ws.pspos, ws.pint, Z, ws.prank,
-                       ws.probe_pos, ws.cap, ws.sws.err);
+            HSS_TRY(histogram(Z, h.nint));
             HSS_LAUNCH(k_update, sblk, 256, 0, st, S, N, p, ws.pkey, ws.pseg, ws.pspos, ws.prank, Z, (int32_t)kMember,
                        ws.Lcut, ws.Ucut, ws.chgL, ws.chgU);
             HSS_LAUNCH(k_update_pos, dim3(p, sblk), 256, 0, st, S, ws.chgL, ws.chgU, ws.probe_pos, ws.cap, ws.Lpos, ws.Upos);
@@ -682,7 +789,7 @@ __device__ __forceinline__ uint32_t warp_last_le(const uint32_t* __restrict__ po
 }
 
 constexpr uint32_t kXchChunk = 8192;
-constexpr uint32_t kXchMaxB = 1024;
+constexpr uint32_t kXchMaxB = 4096;
 
 __global__ __launch_bounds__(256) void k_exchange_copy(const uint64_t* __restrict__ skeys, const uint32_t* __restrict__ spay,
                                                        const uint64_t* __restrict__ seg_off, uint32_t p,
@@ -714,8 +821,8 @@ __global__ __launch_bounds__(256) void k_exchange_copy(const uint64_t* __restric
         __syncthreads();
         // Four keys per thread per step, their loads issued together (memory
         // parallelism); j grows by the CTA width, so the run of j follows
-        // from the previous one by a forward walk (runs are about as long as
-        // a step).
+        // from the previous one by a galloping search forward (one compare
+        // when runs are about as long as a step, a few when they are short).
         uint32_t lo = 0;
         for (uint32_t j0 = c0 + threadIdx.x; j0 < c1; j0 += 4 * blockDim.x) {
             uint64_t kv[4];
@@ -730,7 +837,13 @@ __global__ __launch_bounds__(256) void k_exchange_copy(const uint64_t* __restric
             for (int u = 0; u < 4; ++u) {
                 const uint32_t j = j0 + u * blockDim.x;
                 if (j >= c1) break;
-                while (lo + 1 < nb && s_bnd[lo + 1] <= j) ++lo;
+                if (lo + 1 < nb && s_bnd[lo + 1] <= j) {  // gallop forward, then bisect
+                    uint32_t at = lo + 1, step = 1;
+                    while (at + step < nb && s_bnd[at + step] <= j) { at += step; step <<= 1; }
+                    uint32_t hi = min(at + step, nb);
+                    while (hi - at > 1) { const uint32_t m = (at + hi) >> 1; if (s_bnd[m] <= j) at = m; else hi = m; }
+                    lo = at;
+                }
                 const uint64_t d = dst[s * p + b0 + lo] + (j - s_bnd[lo]);
                 if (d >= N) { atomicOr(err, kDevErrBounds); continue; }
                 bkeys[d] = kv[u];

@@ -72,6 +72,9 @@ struct RoundResult {
     uint64_t unresolved[HSS_MAX_ROUNDS + 1] = {};
 };
 
+// Histogram form of the rounds: chosen per round, or forced (tests).
+constexpr uint32_t kHistAuto = 0, kHistProbe = 1, kHistStaged = 2;
+
 // Run the histogram rounds over the p locally sorted segments skeys
 // (order-preserving key bits) and write the splitters, offsets and the final
 // per-segment positions of the splitters (into ws.Lpos).  d_prop[nprop]
@@ -80,7 +83,8 @@ struct RoundResult {
 int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uint32_t p, double eps, uint64_t seed,
                float oversample, uint32_t max_rounds, int key_type, hss_cut* d_splitters, uint64_t* d_offsets,
                const RoundWs& ws, cudaStream_t st, RoundResult* out, const uint64_t* d_prop = nullptr,
-               uint32_t nprop = 0, uint32_t schedule = HSS_SCHEDULE_PROPORTIONAL, uint32_t schedule_k = 0);
+               uint32_t nprop = 0, uint32_t schedule = HSS_SCHEDULE_PROPORTIONAL, uint32_t schedule_k = 0,
+               uint32_t hist_mode = kHistAuto);
 
 // Per-bucket split windows for the merge, from the final splitters.
 cudaError_t bucket_hints(const RoundWs& ws, const uint64_t* skeys, const uint64_t* d_seg_off, uint32_t p,

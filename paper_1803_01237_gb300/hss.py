@@ -27,6 +27,8 @@ KEY_TYPES = {"u64": 0, "i64": 1}
 OP = {"sort": 0, "partition": 1, "local_sort": 2, "merge": 3, "exchange": 4, "sort_host": 5}
 FLAG_SYNC = 1
 FLAG_TIMING = 2
+FLAG_HIST_PROBE = 4   # force the probe-side histogram
+FLAG_HIST_STAGED = 8  # force the staged histogram in rounds whose probes share one interval
 MAX_ROUNDS = 64
 NUM_PHASES = 4
 PHASES = ("local_sort", "rounds", "exchange", "merge")

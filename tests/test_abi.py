@@ -71,7 +71,9 @@ def test_invalid_arguments_rejected_without_device(lib):
            hss.Params(eps=0.05, seed=1, p=4, oversample=0.0, max_rounds=0, flags=0),
            hss.Params(eps=0.05, seed=1, p=4, oversample=5.0, max_rounds=65, flags=0),
            hss.Params(eps=0.05, seed=1, p=4, oversample=5.0, max_rounds=0, flags=0, schedule=3),
-           hss.Params(eps=0.05, seed=1, p=4, oversample=5.0, max_rounds=0, flags=0, schedule=1, schedule_k=0)]
+           hss.Params(eps=0.05, seed=1, p=4, oversample=5.0, max_rounds=0, flags=0, schedule=1, schedule_k=0),
+           hss.Params(eps=0.05, seed=1, p=4, oversample=5.0, max_rounds=0,
+                      flags=hss.FLAG_HIST_PROBE | hss.FLAG_HIST_STAGED)]
     dummy = ctypes.c_void_p(16)
     for prm in bad:
         rc = L.hss_partition(dummy, 0, 100, ctypes.byref(prm), dummy, dummy, dummy, 1 << 30, ctypes.byref(st), None)

@@ -315,3 +315,45 @@ def test_schedule_sort_output(hss):
         _cmp_partition(res, ref)
         assert np.array_equal(host_u64(res.keys), ref.out_keys)
         assert np.array_equal(res.payload.cpu().numpy().view(np.uint32), ref.out_payload)
+
+
+# ---------------------------------------------------------------------------
+# a5: both histogram forms (probe-side and staged) give the oracle's rounds
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("N,p,eps,seed", [(1 << 16, 1024, 0.05, 1), (1 << 18, 512, 0.02, 2), (100003, 777, 0.05, 3),
+                                          (1 << 20, 64, 0.05, 4), (5000, 4999, 0.05, 5), (3000, 2, 0.01, 6)])
+@pytest.mark.parametrize("gen", ["uniform", "zipf", "allzeros"])
+@pytest.mark.parametrize("mode", ["probe", "staged"])
+def test_histogram_forms_match_oracle(hss, N, p, eps, seed, gen, mode):
+    """Forced staged or probe-side histograms, large p against N (segments
+    of 1 to 64 keys), duplicates and all-equal keys: same rounds, samples,
+    splitters and offsets as the oracle."""
+    keys = GENS[gen](N, seed) if gen != "allzeros" else inputs.allzeros(N)
+    flags = hss.FLAG_HIST_STAGED if mode == "staged" else hss.FLAG_HIST_PROBE
+    res, _ = hss.partition(dev(keys), p, eps, seed, flags=flags)
+    ref = oracle.hss(keys, p, eps, seed, sort=False)
+    _cmp_partition(res, ref)
+
+
+def test_histogram_auto_large_p_sort(hss):
+    """The automatic choice at large p (staged in round 1) on a sort with payload."""
+    N, p, eps, seed = 1 << 19, 2048, 0.02, 8
+    keys = inputs.gauss_mix(N, seed)
+    pay = np.arange(N, dtype=np.uint32)
+    res = hss.sort(dev(keys), p, eps, seed, payload=dev(pay))
+    ref = oracle.hss(keys, p, eps, seed, payload=pay)
+    _cmp_partition(res, ref)
+    assert np.array_equal(host_u64(res.keys), ref.out_keys)
+    assert np.array_equal(res.payload.cpu().numpy().view(np.uint32), ref.out_payload)
+
+
+def test_histogram_staged_with_proposal(hss):
+    """The proposal pass (all cuts share the first interval) in staged form."""
+    N, p, eps, seed = 1 << 18, 256, 0.02, 9
+    keys = inputs.uniform(N, seed)
+    srt = np.sort(keys)
+    prop = srt[[(i * N) // p + 37 for i in range(1, p)]]
+    for flags in (hss.FLAG_HIST_STAGED, hss.FLAG_HIST_PROBE):
+        res, _ = hss.partition_with_proposal(dev(keys), p, eps, seed, dev(prop), flags=flags)
+        ref = oracle.hss(keys, p, eps, seed, sort=False, proposal=prop)
+        _cmp_partition(res, ref)
