@@ -347,7 +347,7 @@ __global__ __launch_bounds__(256) void k_histogram(
 constexpr int kStgThreads = 256;
 constexpr int kStgPer = 4;                          // probes per thread
 constexpr int kStgProbes = kStgThreads * kStgPer;   // probes per CTA
-constexpr int kStgSegs = 8;                         // segments per CTA
+constexpr int kStgSegs = 32;                        // segments per CTA
 constexpr uint32_t kStgCap = 4096;                  // staged keys (32 KB)
 
 __global__ __launch_bounds__(kStgThreads) void k_histogram_staged(
