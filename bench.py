@@ -306,7 +306,7 @@ def run_gpu(args):
                      "(on-chip sort), rounds ~2.3 (bitmap, probes), exchange 16, merge 8 + 16 + 16",
             "bytes_per_key": PATH_BYTES_PER_KEY, "achieved_GBs": PATH_BYTES_PER_KEY * world * N / (ms / 1000.0) / 1e9,
             "peak_GBs": peak, "frac": PATH_BYTES_PER_KEY * world * N / (ms / 1000.0) / 1e9 / peak,
-            "survey_lsd_model_bytes_per_key": 200,
+            "lsd_model_bytes_per_key": 200,
             "frac_of_lsd_model": 200.0 * world * N / (ms / 1000.0) / 1e9 / peak},
         "per_distribution": dist_report,
         "hss": {"rounds": rounds.rounds, "sample_size": rounds.sample_size, "gamma": rounds.gamma,
