@@ -39,6 +39,17 @@ PATH_BYTES_PER_KEY = 98.3  # algorithmic bytes of one whole hss_sort step per ke
 REF_SAMPLE_LOG2N = 22      # reference arm: first 2^22 keys per step
 
 
+def _max_over_ranks(x: float, dist, device) -> float:
+    """The slowest rank's figure (the job's time): an all-reduce MAX over
+    the ranks; x itself in a single process."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
@@ -237,11 +248,7 @@ def run_gpu(args):
     barrier()
     clk = clocks.stop()
     launches = hss.launch_count() - launches0
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = _max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, dev)
     value = world * N / (ms / 1000.0)
     dist_report = {name: {"device_ms_per_step": v["ms"] / max(v["steps"], 1),
                           "keys_per_s_device": N / (v["ms"] / max(v["steps"], 1) / 1000.0) if v["steps"] else None,
@@ -273,10 +280,7 @@ def run_gpu(args):
         for _ in range(n_e2e):
             hss.sort_host(hkn, P, EPS, SEED, oversample=OVERSAMPLE, out=hon)
         e2e_s = (time.perf_counter() - t0) / n_e2e
-        if dist is not None:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = _max_over_ranks(e2e_s, dist, dev)
         e2e = {"value": world * N / e2e_s, "unit": "keys/s", "h2d_bytes_per_step": 8 * N,
                "d2h_bytes_per_step": 8 * N + 16 * (P - 1) + 8 * (P + 1), "ms_per_step": 1000 * e2e_s,
                "api": "hss_sort_host (pinned host buffers, copies inside the call)", "input": "uniform"}
