@@ -7,8 +7,10 @@ the budget; every slot runs on its own CUDA stream from its own host thread
 on the GPU while later requests keep arriving.  Once the CDF network has
 been trained on the splitters of completed jobs (exact ranks of sampled
 keys), a request starts from the network's proposed cuts
-(hss_partition_with_proposal); before that, or if proposing fails, it runs
-plain HSS.  The histogram rounds decide balance either way, so every result
+(hss_partition_with_proposal) when the plan (plan_proposal: the network's
+held-out error against the request's p, eps and size) expects them to save
+a round; otherwise, before training, or if proposing fails, it runs plain
+HSS.  The histogram rounds decide balance either way, so every result
 satisfies the same contract, and a request computes the same splitters and
 offsets alone or in the mix given the same proposal (which each completion
 records).
