@@ -301,10 +301,15 @@ __device__ __forceinline__ void write_sorted(uint64_t* kout, uint32_t* pout, con
 template <int CAP>
 constexpr int chip_radix() { return CAP <= kC0Cap ? 512 : kChipRadix; }
 
+// The largest class re-splits crowded groups on chip (see k_small_msd).
+template <int CAP>
+constexpr bool chip_resplit() { return CAP > kC1Cap; }
+
 template <int THREADS, int CAP>
 constexpr size_t msd_sort_smem() {
     return (size_t)CAP * 8 + 3 * (size_t)CAP * 2 + 2 * (chip_radix<CAP>() + 1) * 4 + 32 * 4 + 2 * 32 * 8 +
-           (size_t)(THREADS / 32) * kMaxBig * 4 + kMaxBig * 4 + chip_radix<CAP>() + 64;
+           (size_t)(THREADS / 32) * kMaxBig * 4 + kMaxBig * 4 + chip_radix<CAP>() + 64 +
+           (chip_resplit<CAP>() ? (size_t)(chip_radix<CAP>() + 1) * 4 + kMaxBig * 2 : 0);
 }
 
 template <bool PAY, int THREADS, int CAP>
@@ -315,10 +320,13 @@ __global__ __launch_bounds__(THREADS) void k_small_msd(
     uint32_t max_n, uint64_t flip_in, uint64_t flip_out, uint32_t* __restrict__ fb_list, uint32_t* __restrict__ fb_count) {
     constexpr int WARPS = THREADS / 32;
     constexpr int R = chip_radix<CAP>();
-    // Mixed big groups are ranked on chip in the two smaller classes; the
-    // largest class leaves such segments to the LSD kernel (measured faster
-    // there, where its larger groups come from clustered keys).
+    // Mixed big groups are ranked on chip in the two smaller classes (up to
+    // kMixedMax keys).  The largest class, where big groups come from
+    // clustered keys, re-splits each one by a second counting pass that
+    // interpolates the group's own key range; a segment with a sub-group
+    // still above kTinyGroup keys goes to the LSD kernel.
     constexpr bool kMixed = CAP <= kC1Cap;
+    constexpr bool kResplit = chip_resplit<CAP>();
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* s_keys = (uint64_t*)smem;                        // CAP u64
     uint16_t* s_grp = (uint16_t*)(s_keys + CAP);               // CAP u16: positions grouped by digit
@@ -332,6 +340,8 @@ __global__ __launch_bounds__(THREADS) void k_small_msd(
     uint32_t* s_misc = s_wcnt + WARPS * kMaxBig;                // [0] big groups, [1] a mixed group above kMixedMax
     uint32_t* s_mixed = s_misc + 2;                             // kMaxBig: the big group holds distinct keys
     uint8_t* s_bigid = (uint8_t*)(s_mixed + kMaxBig);           // R: index of a big group, 0xff otherwise
+    uint32_t* s_h2 = (uint32_t*)(s_bigid + R);                  // R+1 (kResplit): sub-group starts
+    uint16_t* s_bigd = (uint16_t*)(s_h2 + R + 1);               // kMaxBig (kResplit): digit of each big group
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const uint64_t count = list ? (uint64_t)*nlist : nseg;
@@ -400,10 +410,16 @@ __global__ __launch_bounds__(THREADS) void k_small_msd(
         for (int i = 0; i < WARPS; ++i) mx = max(mx, s_warp[i]);
         const bool big = mx > (uint32_t)kTinyGroup;  // uniform per CTA
         if (big) {
-            for (int d = tid; d < R; d += THREADS)
-                s_bigid[d] = (s_start[d + 1] - s_start[d] > (uint32_t)kTinyGroup)
-                                 ? (uint8_t)min(atomicAdd(&s_misc[0], 1u), 255u) : (uint8_t)0xff;
-            if (kMixed)
+            for (int d = tid; d < R; d += THREADS) {
+                uint8_t id = 0xff;
+                if (s_start[d + 1] - s_start[d] > (uint32_t)kTinyGroup) {
+                    const uint32_t i = atomicAdd(&s_misc[0], 1u);
+                    if (kResplit && i < (uint32_t)kMaxBig) s_bigd[i] = (uint16_t)d;
+                    id = (uint8_t)min(i, 255u);
+                }
+                s_bigid[d] = id;
+            }
+            if (kMixed || kResplit)
                 for (int g = tid; g < kMaxBig; g += THREADS) s_mixed[g] = 0u;
             __syncthreads();
             if (s_misc[0] > (uint32_t)kMaxBig) {  // too many big groups: the LSD kernel takes this segment
@@ -421,8 +437,12 @@ __global__ __launch_bounds__(THREADS) void k_small_msd(
             const uint32_t a = s_start[d], b = s_start[d + 1];
             if (b - a > (uint32_t)kTinyGroup) {  // big group: only check whether it holds one key value
                 if (kx != s_keys[s_grp[a]]) {
-                    if (kMixed) s_mixed[s_bigid[d]] = 1u;
-                    if (!kMixed || b - a > kMixedMax) s_misc[1] = 1u;
+                    if (kResplit) {
+                        s_mixed[s_bigid[d]] = 2u;  // re-split below
+                    } else {
+                        if (kMixed) s_mixed[s_bigid[d]] = 1u;
+                        if (!kMixed || b - a > kMixedMax) s_misc[1] = 1u;
+                    }
                 }
                 continue;
             }
@@ -435,6 +455,71 @@ __global__ __launch_bounds__(THREADS) void k_small_msd(
             s_out[a + r] = x;
         }
         __syncthreads();
+        if (big && kResplit) {
+            // Re-split every big group of distinct keys, one at a time by the
+            // whole CTA: a counting pass on a digit interpolating the group's
+            // own key range (any monotone digit keeps the order), positions
+            // scattered by sub-group into the group's slots of s_out, then
+            // each key ranked inside its sub-group by (key, input position)
+            // into s_grp and copied back to s_out.
+            const uint32_t nbig = s_misc[0];
+            for (uint32_t g = 0; g < nbig; ++g) {
+                if (s_mixed[g] != 2u) continue;  // uniform: read after a barrier
+                const uint32_t dg = s_bigd[g];
+                const uint32_t a = s_start[dg], b = s_start[dg + 1];
+                uint64_t gmin = ~0ull, gmax = 0;
+                for (uint32_t q = a + tid; q < b; q += THREADS) {
+                    const uint64_t kq = s_keys[s_grp[q]];
+                    gmin = min(gmin, kq);
+                    gmax = max(gmax, kq);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    gmin = min(gmin, (uint64_t)__shfl_xor_sync(0xffffffffu, gmin, o));
+                    gmax = max(gmax, (uint64_t)__shfl_xor_sync(0xffffffffu, gmax, o));
+                }
+                if (lane == 0) { s_red[w] = gmin; s_red[32 + w] = gmax; }
+                for (int i = tid; i < R; i += THREADS) s_h2[i] = 0u;
+                __syncthreads();
+                for (int i = 0; i < WARPS; ++i) { gmin = min(gmin, s_red[i]); gmax = max(gmax, s_red[32 + i]); }
+                const uint64_t r2 = gmax - gmin;
+                const uint64_t m2 = r2 < (uint64_t)R ? 0ull : (uint64_t)((double)(R - 1) * 18446744073709551616.0 / (double)r2);
+                auto dig2 = [&](uint64_t kq) -> uint32_t {
+                    const uint64_t off = kq - gmin;
+                    return m2 ? min((uint32_t)__umul64hi(off, m2), (uint32_t)R - 1) : (uint32_t)off;
+                };
+                for (uint32_t q = a + tid; q < b; q += THREADS) atomicAdd(&s_h2[dig2(s_keys[s_grp[q]])], 1u);
+                __syncthreads();
+                for (int i = tid; i < R; i += THREADS)
+                    if (s_h2[i] > (uint32_t)kTinyGroup) s_misc[1] = 1u;  // still crowded: LSD kernel
+                scan_smem_inplace<THREADS, R>(s_h2, s_warp);        // ends with a barrier
+                if (s_misc[1]) break;                               // uniform
+                for (int i = tid; i < R; i += THREADS) s_run[i] = s_h2[i];
+                if (tid == 0) s_h2[R] = b - a;
+                __syncthreads();
+                for (uint32_t q = a + tid; q < b; q += THREADS) {
+                    const uint16_t x = s_grp[q];
+                    s_out[a + atomicAdd(&s_run[dig2(s_keys[x])], 1u)] = x;
+                }
+                __syncthreads();
+                for (uint32_t q = a + tid; q < b; q += THREADS) {
+                    const uint16_t x = s_out[q];
+                    const uint64_t kx = s_keys[x];
+                    const uint32_t d2 = dig2(kx);
+                    const uint32_t lo2 = a + s_h2[d2], hi2 = a + s_h2[d2 + 1];
+                    uint32_t r = 0;
+                    for (uint32_t q2 = lo2; q2 < hi2; ++q2) {
+                        const uint16_t y = s_out[q2];
+                        const uint64_t ky = s_keys[y];
+                        r += (ky < kx || (ky == kx && y < x)) ? 1u : 0u;
+                    }
+                    s_grp[lo2 + r] = x;
+                }
+                __syncthreads();
+                for (uint32_t q = a + tid; q < b; q += THREADS) s_out[q] = s_grp[q];
+                __syncthreads();
+            }
+        }
         if (big) {
             if (s_misc[1]) {  // a large group of distinct keys: the LSD kernel takes this segment
                 if (tid == 0) fb_list[atomicAdd(fb_count, 1u)] = (uint32_t)s;
@@ -472,7 +557,7 @@ __global__ __launch_bounds__(THREADS) void k_small_msd(
             for (uint32_t p0 = lo; p0 < hi; p0 += 32) {
                 const uint32_t e = p0 + lane;
                 uint32_t g = e < hi ? (uint32_t)s_bigid[s_dig[e]] : 0xffu;
-                if (kMixed && g != 0xffu && s_mixed[g]) g = 0xffu;  // ranked above
+                if ((kMixed || kResplit) && g != 0xffu && s_mixed[g]) g = 0xffu;  // ranked above
                 const bool valid = g != 0xffu;
                 const uint32_t peers = __match_any_sync(0xffffffffu, valid ? g : 0x100u + lane);
                 if (valid && (peers & lt) == 0u) wc[g] += (uint32_t)__popc(peers);
@@ -492,7 +577,7 @@ __global__ __launch_bounds__(THREADS) void k_small_msd(
                 const uint32_t e = p0 + lane;
                 const uint32_t d = e < hi ? (uint32_t)s_dig[e] : 0u;
                 uint32_t g = e < hi ? (uint32_t)s_bigid[d] : 0xffu;
-                if (kMixed && g != 0xffu && s_mixed[g]) g = 0xffu;  // ranked above
+                if ((kMixed || kResplit) && g != 0xffu && s_mixed[g]) g = 0xffu;  // ranked above
                 const bool valid = g != 0xffu;
                 const uint32_t peers = __match_any_sync(0xffffffffu, valid ? g : 0x100u + lane);
                 const uint32_t before = valid ? wc[g] : 0u;

@@ -47,6 +47,7 @@ GENS = {
     "gauss": inputs.gauss,
     "allzeros": inputs.allzeros,
     "nested": inputs.nested_clusters,
+    "morton": lambda n, seed: inputs.plummer_morton(n, seed)[0],
 }
 
 
@@ -67,7 +68,7 @@ def test_sample_words_match_oracle(hss, seed, seg, rnd, spos0):
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("N,p", [(1000, 1), (50000, 7), (1 << 16, 4), (100003, 3), (200000, 2), (40000, 1),
                                  (16384 * 2, 2), (16385 * 2, 2), (5, 8), (0, 3)])
-@pytest.mark.parametrize("gen", ["uniform", "zipf", "skew2", "allzeros"])
+@pytest.mark.parametrize("gen", ["uniform", "zipf", "skew2", "allzeros", "morton"])
 def test_local_sort_matches_oracle(hss, N, p, gen):
     keys = GENS[gen](N, 3)
     pay = (np.arange(N, dtype=np.uint32) * np.uint32(2654435761)).astype(np.uint32)
@@ -91,6 +92,22 @@ def test_local_sort_deep_recursion_payload(hss, N, p):
     want, wantp = oracle.segment_sort(keys, p, payload=pay)
     assert np.array_equal(host_u64(out), want)
     assert np.array_equal(outp.cpu().numpy().view(np.uint32), wantp)
+
+
+@pytest.mark.parametrize("N,p", [(1 << 18, 1), (1 << 18, 4), (1 << 20, 16), (300007, 5)])
+def test_local_sort_crowded_groups(hss, N, p):
+    """Morton keys of a Plummer sphere: the dense core crowds the on-chip
+    sort's 10-bit groups, which the largest class re-splits on chip (a
+    second counting pass over each crowded group's own range)."""
+    keys, _ = inputs.plummer_morton(N, 13)
+    pay = (np.arange(N, dtype=np.uint32) * np.uint32(2654435761)).astype(np.uint32)
+    out, outp = hss.local_sort(dev(keys), p, payload=dev(pay))
+    want, wantp = oracle.segment_sort(keys, p, payload=pay)
+    assert np.array_equal(host_u64(out), want)
+    assert np.array_equal(outp.cpu().numpy().view(np.uint32), wantp)
+    out2 = hss.local_sort(dev(keys), p)
+    out2 = out2[0] if isinstance(out2, tuple) else out2
+    assert np.array_equal(host_u64(out2), want)
 
 
 @pytest.mark.parametrize("N,p,nvals,share,adjacent", [
@@ -226,7 +243,7 @@ def test_sort_matches_oracle(hss, N, p, eps, seed, payload):
         assert np.array_equal(res.payload.cpu().numpy().view(np.uint32), ref.out_payload)
 
 
-@pytest.mark.parametrize("gen", ["gauss_mix", "zipf", "skew2", "allzeros", "skew3", "nested"])
+@pytest.mark.parametrize("gen", ["gauss_mix", "zipf", "skew2", "allzeros", "skew3", "nested", "morton"])
 def test_sort_distributions(hss, gen):
     N, p, eps, seed = 1 << 18, 8, 0.02, 5
     keys = GENS[gen](N, seed)
