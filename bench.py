@@ -63,21 +63,52 @@ def _measured_peaks():
     return 6800.0, "fallback"
 
 
+# The sources the split pass's DRAM traffic depends on: its kernel and
+# helpers in segsort.cu, the tile constants in segsort.cuh, and the shared
+# device helpers.  The committed traffic record holds their hash.
+_SPLIT_REGIONS = (("__device__ __forceinline__ uint32_t split_digit(", "// Exclusive scan of 256 shared values"),
+                  ("__device__ __forceinline__ uint32_t warp_peers8(", "// On-chip sort of segments"),
+                  ("struct SplitArgs {", "__global__ void k_even_offsets("))
+
+
+def split_source_hash(segsort_cu: str, segsort_cuh: str, internal_cuh: str):
+    """sha256 (16 hex digits) of the split pass's sources, or None when a
+    marker is missing."""
+    parts = []
+    for a, b in _SPLIT_REGIONS:
+        i = segsort_cu.find(a)
+        j = segsort_cu.find(b, i)
+        if i < 0 or j < 0:
+            return None
+        parts.append(segsort_cu[i:j])
+    i = segsort_cuh.find("constexpr int kRadixBits")
+    j = segsort_cuh.find("\n", segsort_cuh.find("constexpr int kOsTile"))
+    if i < 0 or j < 0:
+        return None
+    parts.append(segsort_cuh[i:j])
+    parts.append(internal_cuh)
+    return hashlib.sha256("".join(parts).encode()).hexdigest()[:16]
+
+
 def _traffic_record():
     """Per-launch DRAM bytes of the radix digit pass from the committed ncu
-    summary, valid only while the kernel source is unchanged."""
+    summary, valid only while the split pass's sources are unchanged."""
     path = os.path.join(ROOT, "profiles", "k_split_traffic.txt")
-    src = os.path.join(ROOT, "paper_1803_01237_gb300", "csrc", "segsort.cu")
+    csrc = os.path.join(ROOT, "paper_1803_01237_gb300", "csrc")
     if not os.path.exists(path):
         return None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    texts = []
+    for name in ("segsort.cu", "segsort.cuh", "hss_internal.cuh"):
+        with open(os.path.join(csrc, name)) as f:
+            texts.append(f.read())
+    sha = split_source_hash(*texts)
     rec = {}
     for line in open(path):
         line = line.strip()
         if "=" in line and not line.startswith("#"):
             k, v = line.split("=", 1)
             rec[k.strip()] = v.strip()
-    if rec.get("segsort_sha") != sha:
+    if sha is None or rec.get("split_source_sha") != sha:
         return None
     try:
         return float(rec["dram_bytes_per_launch_full_size"])
