@@ -121,10 +121,14 @@ def load():
 # helpers
 # ---------------------------------------------------------------------------
 def _ptr(t):
+    """Address for the C library: numpy arrays are host buffers (the host
+    entry point); torch tensors must live in device memory."""
     if t is None:
         return None
     if isinstance(t, np.ndarray):
         return t.ctypes.data_as(ctypes.c_void_p)
+    if not t.is_cuda:
+        raise ValueError("device entry points take CUDA tensors (host arrays go through sort_host)")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -140,10 +144,12 @@ def _check(rc: int, where: str, allow=()):
 
 
 def _as_key_tensor(keys) -> torch.Tensor:
-    if isinstance(keys, np.ndarray):
-        keys = torch.from_numpy(np.ascontiguousarray(keys).view(np.int64))
+    if not isinstance(keys, torch.Tensor):
+        raise TypeError("keys must be a CUDA int64 tensor (host arrays go through sort_host)")
     if keys.dtype not in (torch.int64,):
         raise TypeError("keys must be int64 tensors (u64 keys are passed by bit pattern)")
+    if not keys.is_cuda:
+        raise ValueError("keys must live in device memory (host arrays go through sort_host)")
     return keys.contiguous()
 
 

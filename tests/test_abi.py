@@ -106,3 +106,23 @@ def test_no_cpu_fallback_in_binding():
     assert "oracle" not in src.replace("# ", "")
     for f in os.listdir(os.path.join(ROOT, "paper_1803_01237_gb300", "csrc")):
         assert "oracle" not in open(os.path.join(ROOT, "paper_1803_01237_gb300", "csrc", f)).read().lower()
+
+
+def test_binding_rejects_host_tensors_before_any_device_call():
+    """Device entry points refuse host data up front (no host pointer ever
+    reaches a kernel); the host entry point is sort_host."""
+    import numpy as np
+    import torch
+    from paper_1803_01237_gb300 import hss
+    cpu = torch.zeros(16, dtype=torch.int64)
+    with pytest.raises(ValueError):
+        hss.sort(cpu, 2, 0.05, 1)
+    with pytest.raises(ValueError):
+        hss.partition(cpu, 2, 0.05, 1)
+    with pytest.raises(ValueError):
+        hss.local_sort(cpu, 2)
+    with pytest.raises(TypeError):
+        hss.sort(np.zeros(16, dtype=np.uint64), 2, 0.05, 1)
+    with pytest.raises(ValueError):
+        hss._ptr(cpu)
+    assert hss._ptr(np.zeros(4, dtype=np.uint64)) is not None
