@@ -25,6 +25,11 @@
  *     are reported as HSS_ERR_TIMEOUT; nothing traps the GPU.
  *   - Limits: N < 2^40; 1 <= p <= 2^22 and p*(samples per round) positions
  *     must fit the workspace; a segment or bucket holds fewer than 2^30 keys.
+ *     Calls whose even segments (ceil(N/p)), or for the sorting calls whose
+ *     eps-balanced buckets (ceil(N/p) + 2 floor(N eps/(2p))), could reach
+ *     2^30 keys return HSS_ERR_INVALID before any device work; a caller's
+ *     bucket of 2^30 keys or more given to hss_merge is reported as
+ *     HSS_ERR_INVALID after the call's device work.
  */
 #ifndef HSS_H
 #define HSS_H
@@ -235,13 +240,14 @@ int hss_sample_words(uint64_t seed, uint32_t seg, uint32_t round, uint32_t spos0
  * on every device that loads the library until the process exits.  Limits:
  * N <= 524288 keys, and the scratch the sort needs for (N, p) must fit those
  * 16 MiB (the call computes it); otherwise it returns HSS_ERR_NOALLOC_LIMIT
- * before any device work.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Every call, from any thread or stream,
- * uses the same array and leaves its contents behind, so calls that can
- * overlap on the GPU race with each other: serialise them.  The call
- * synchronises `stream` to read the kernels' status word.  It allocates
- * nothing, neither through CUDA nor through any other library. */
+ * before any device work.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress) on the current device.  Every call, from any thread
+ * or stream, uses the same array and leaves its contents behind, so calls
+ * that can overlap on the GPU race with each other: serialise them.  The
+ * call synchronises `stream` to read the kernels' status word; on a stream
+ * that is capturing work it returns HSS_ERR_INVALID before enqueuing
+ * anything.  It allocates nothing, neither through CUDA nor through any
+ * other library. */
 int hss_local_sort_noalloc(const void* d_keys, const uint32_t* d_payload, int key_type, uint64_t N, uint32_t p,
                            void* d_keys_out, uint32_t* d_payload_out, void* stream);
 

@@ -580,6 +580,9 @@ int build_tables(const uint64_t* sizes, const uint32_t* ps, uint32_t njobs, cons
         const uint64_t n = sizes[j];
         const uint32_t p = ps[j];
         if (p == 0 || p > (1u << 16) || (uint64_t)p > std::max<uint64_t>(n, 1)) return HSS_ERR_INVALID;
+        // every segment and every eps-balanced bucket below 2^30 keys
+        const double extra = 2.0 * std::floor(((double)n * prm->eps) / (2.0 * (double)p));
+        if ((double)((n + p - 1) / p) + extra + 1.0 >= (double)kMaxSegKeys) return HSS_ERR_INVALID;
         BJob& J = T.jobs[j];
         J.koff = koff; J.n = n; J.p = p; J.sbase = sb; J.ibase = ib; J.pad = 0;
         J.lbase = lb; J.dbase = db; J.cbase = cb;
@@ -805,6 +808,7 @@ int run_batch(const void* d_keys, const uint32_t* d_payload, int key_type, const
     HSS_BTRY(cudaStreamSynchronize(st));
     int status = HSS_OK;
     if (h_err & kDevErrTimeout) status = HSS_ERR_TIMEOUT;
+    else if (h_err & kDevErrSize) status = HSS_ERR_INVALID;
     else if (h_err & kDevErrBounds) status = HSS_ERR_CUDA;
     uint32_t maxr = 0;
     uint64_t samples = 0;

@@ -272,12 +272,7 @@ size_t grad_smem() { return (size_t)(kP + 3 + 4 * kGradThreads * kStage + 3 * kG
 
 int launch_grad(const hss_cdf_model* M, const uint64_t* keys, const uint64_t* ranks, uint32_t n, uint64_t N,
                 float* part, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(k_cdf_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem()) != cudaSuccess)
-            return HSS_ERR_CUDA;
-        attr = true;
-    }
+    if (ensure_func_attrs((const void*)k_cdf_grad, (int)grad_smem()) != cudaSuccess) return HSS_ERR_CUDA;
     HSS_LAUNCH(k_cdf_grad, grad_blocks(n), kGradThreads, grad_smem(), st, M, keys, ranks, n, 1.0 / (double)N,
                (float)(1.0 / (double)n), part);
     return cudaGetLastError() == cudaSuccess ? HSS_OK : HSS_ERR_CUDA;

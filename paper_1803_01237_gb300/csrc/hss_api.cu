@@ -12,11 +12,48 @@
 #include <cmath>
 #include <cstring>
 #include <algorithm>
+#include <mutex>
+#include <set>
+#include <utility>
 
 namespace hss {
 
 static std::atomic<uint64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// Per-device bookkeeping of kernel attributes and SM counts: a kernel's
+// shared-memory limit set on one device does not carry over to another, and
+// server threads call in concurrently.
+static std::mutex g_attr_mu;
+static std::set<std::pair<int, const void*>> g_attr_done;
+constexpr int kMaxDevices = 256;
+static std::atomic<int> g_sm_count[kMaxDevices];
+
+cudaError_t ensure_func_attrs(const void* func, int max_dyn_smem, int carveout) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    if (g_attr_done.count({dev, func})) return cudaSuccess;
+    if ((e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem)) != cudaSuccess)
+        return e;
+    if (carveout >= 0 &&
+        (e = cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout, carveout)) != cudaSuccess)
+        return e;
+    g_attr_done.insert({dev, func});
+    return cudaSuccess;
+}
+
+int device_sm_count() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 148;
+    int n = g_sm_count[dev].load(std::memory_order_relaxed);
+    if (n <= 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+        g_sm_count[dev].store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
 
 static inline size_t aup(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -29,6 +66,19 @@ struct Layout {
 
 static const uint64_t kMaxN = 1ull << 40;
 static const uint32_t kMaxP = 1u << 22;
+// A segment or bucket holds fewer than 2^30 keys: the look-back words of the
+// split pack a digit's count into 30 bits and in-segment positions are u32.
+static const uint64_t kMaxSeg = 1ull << 30;
+
+// Every processor segment of N keys over p processors is below the limit.
+static bool segments_fit(uint64_t N, uint32_t p) { return p > 0 && (N + p - 1) / p < kMaxSeg; }
+// ... and so is every bucket of an eps-balanced partition: at most
+// ceil(N/p) + 2 floor(N eps/(2p)) keys.
+static bool buckets_fit(uint64_t N, uint32_t p, double eps) {
+    if (!segments_fit(N, p)) return false;
+    const double extra = std::floor(((double)N * eps) / (2.0 * (double)p)) * 2.0;
+    return (double)((N + p - 1) / p) + extra + 1.0 < (double)kMaxSeg;
+}
 
 static Layout plan(int op, uint64_t N, uint32_t p, float oversample, bool pay) {
     Layout L;
@@ -140,6 +190,7 @@ static int read_dev_err(uint32_t* d_err, cudaStream_t st) {
     if (cudaMemcpyAsync(&h, d_err, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return HSS_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return HSS_ERR_CUDA;
     if (h & kDevErrTimeout) return HSS_ERR_TIMEOUT;
+    if (h & kDevErrSize) return HSS_ERR_INVALID;
     if (h & kDevErrBounds) return HSS_ERR_CUDA;
     return HSS_OK;
 }
@@ -152,6 +203,7 @@ static int run_path(const void* d_keys, const uint32_t* d_payload, int key_type,
     const uint64_t mark = g_launches.load();
     if (h_stats) std::memset(h_stats, 0, sizeof(*h_stats));
     if (!params_ok(prm) || (key_type != HSS_KEY_U64 && key_type != HSS_KEY_I64) || N >= kMaxN) return HSS_ERR_INVALID;
+    if (!(sort ? buckets_fit(N, prm->p, prm->eps) : segments_fit(N, prm->p))) return HSS_ERR_INVALID;
     if ((N > 0 && !d_keys) || !d_offsets || (prm->p > 1 && !d_splitters) || !d_work) return HSS_ERR_INVALID;
     if (sort && N > 0 && !d_keys_out) return HSS_ERR_INVALID;
     const bool pay = sort && d_payload != nullptr;
@@ -260,6 +312,7 @@ size_t hss_workspace_bytes(int op, uint64_t N, const hss_params* prm, uint32_t p
 int hss_local_sort(const void* d_keys, const uint32_t* d_payload, int key_type, uint64_t N, uint32_t p,
                    void* d_keys_out, uint32_t* d_payload_out, void* d_work, size_t work_bytes, void* stream) {
     if ((key_type != HSS_KEY_U64 && key_type != HSS_KEY_I64) || p == 0 || p > kMaxP || N >= kMaxN) return HSS_ERR_INVALID;
+    if (!segments_fit(N, p)) return HSS_ERR_INVALID;
     if (N > 0 && (!d_keys || !d_keys_out)) return HSS_ERR_INVALID;
     if ((d_payload == nullptr) != (d_payload_out == nullptr) || !d_work) return HSS_ERR_INVALID;
     const bool pay = d_payload != nullptr;
@@ -280,8 +333,8 @@ int hss_local_sort(const void* d_keys, const uint32_t* d_payload, int key_type, 
 
 int hss_rank_cuts(const void* d_sorted_keys, int key_type, uint64_t N, uint32_t p, const hss_cut* d_cuts, uint32_t ncuts,
                   uint64_t* d_ranks, uint32_t* d_seg_pos, void* stream) {
-    (void)N;
     if ((key_type != HSS_KEY_U64 && key_type != HSS_KEY_I64) || p == 0 || p > kMaxP || N >= kMaxN) return HSS_ERR_INVALID;
+    if (!segments_fit(N, p)) return HSS_ERR_INVALID;
     if (ncuts > 0 && (!d_cuts || !d_ranks || (N > 0 && !d_sorted_keys))) return HSS_ERR_INVALID;
     if (rank_cuts((const uint64_t*)d_sorted_keys, key_type, N, p, d_cuts, ncuts, d_ranks, d_seg_pos,
                   (cudaStream_t)stream) != cudaSuccess)
@@ -315,7 +368,7 @@ int hss_sort_with_proposal(const void* d_keys, const uint32_t* d_payload, int ke
 int hss_exchange(const void* d_sorted_keys, const uint32_t* d_sorted_payload, uint64_t N, uint32_t p,
                  const uint32_t* d_seg_pos, const uint64_t* d_offsets, void* d_bucket_keys, uint32_t* d_bucket_payload,
                  void* d_work, size_t work_bytes, void* stream) {
-    if (p == 0 || p > kMaxP || N >= kMaxN || !d_offsets || !d_work) return HSS_ERR_INVALID;
+    if (p == 0 || p > kMaxP || N >= kMaxN || !segments_fit(N, p) || !d_offsets || !d_work) return HSS_ERR_INVALID;
     if (N > 0 && (!d_sorted_keys || !d_bucket_keys || (p > 1 && !d_seg_pos))) return HSS_ERR_INVALID;
     if ((d_sorted_payload == nullptr) != (d_bucket_payload == nullptr)) return HSS_ERR_INVALID;
     const Layout L = plan(HSS_OP_EXCHANGE, N, p, 5.0f, d_sorted_payload != nullptr);

@@ -17,6 +17,8 @@ constexpr uint64_t kSignBit = 0x8000000000000000ull;
 // Device error bits (OR-ed into a status word in the workspace).
 constexpr uint32_t kDevErrTimeout = 1u;
 constexpr uint32_t kDevErrBounds = 2u;
+constexpr uint32_t kDevErrSize = 4u;  // a segment of 2^30 keys or more (reported as HSS_ERR_INVALID)
+constexpr uint64_t kMaxSegKeys = 1ull << 30;
 
 // Bound on every spin-wait: iterations of a poll with a short sleep.  About a
 // second of waiting before the kernel records kDevErrTimeout and moves on.
@@ -108,6 +110,13 @@ __device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
 // Launch accounting: every kernel launch of the library goes through this.
 void note_launch();
 uint32_t launches_since(uint64_t mark);
+
+// Kernel attributes are per device: set the dynamic shared-memory limit (and,
+// when carveout >= 0, the preferred shared-memory carveout) of `func` once per
+// device, thread-safely.  Returns the first failing CUDA error.
+cudaError_t ensure_func_attrs(const void* func, int max_dyn_smem, int carveout = -1);
+// Streaming multiprocessors of the current device (cached per device).
+int device_sm_count();
 
 }  // namespace hss
 

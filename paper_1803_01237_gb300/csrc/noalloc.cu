@@ -10,7 +10,6 @@
 #include "segsort.cuh"
 
 #include <algorithm>
-#include <mutex>
 
 namespace hss {
 
@@ -21,22 +20,15 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 namespace {
 
-constexpr int kMaxDevices = 256;
-std::mutex g_scratch_mu;
-void* g_scratch_addr[kMaxDevices] = {};
-
 // Device address of the scratch array on the current device.  The host-side
 // symbol is only a stand-in: kernels must be given the address looked up here.
+// It is looked up on every call (cheap next to the sort): a cached address
+// would go stale if the caller reset the device and the library image were
+// loaded again.
 int scratch_on_current_device(void** out) {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HSS_ERR_CUDA;
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (g_scratch_addr[dev] == nullptr) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return HSS_ERR_CUDA;
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return HSS_ERR_CUDA;
+    *out = p;
     return HSS_OK;
 }
 
@@ -53,6 +45,13 @@ extern "C" int hss_local_sort_noalloc(const void* d_keys, const uint32_t* d_payl
     if (N > 0 && (!d_keys || !d_keys_out)) return HSS_ERR_INVALID;
     if ((d_payload == nullptr) != (d_payload_out == nullptr)) return HSS_ERR_INVALID;
     if (N > kNoAllocMaxKeys) return HSS_ERR_NOALLOC_LIMIT;
+    cudaStream_t st = (cudaStream_t)stream;
+    // The call ends with a stream synchronisation to read the kernels' status
+    // word; on a stream that is capturing work that would end the caller's
+    // capture, so such a stream is refused before anything is enqueued.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return HSS_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) return HSS_ERR_INVALID;
     const bool pay = d_payload != nullptr;
     const uint64_t N1 = std::max<uint64_t>(N, 1);
     // Layout inside the fixed array: tmp keys, tmp payload, segment offsets,
@@ -70,7 +69,6 @@ extern "C" int hss_local_sort_noalloc(const void* d_keys, const uint32_t* d_payl
     char* b = (char*)base;
     uint32_t* err = (uint32_t*)(b + o_err);
     uint64_t* seg_off = (uint64_t*)(b + o_seg);
-    cudaStream_t st = (cudaStream_t)stream;
     // The array keeps the previous call's contents: zero the error word here;
     // the sort zeroes its own counters and look-back words before use.
     if (cudaMemsetAsync(err, 0, 256, st) != cudaSuccess) return HSS_ERR_CUDA;
@@ -84,6 +82,7 @@ extern "C" int hss_local_sort_noalloc(const void* d_keys, const uint32_t* d_payl
     if (cudaMemcpyAsync(&h, err, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return HSS_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return HSS_ERR_CUDA;
     if (h & kDevErrTimeout) return HSS_ERR_TIMEOUT;
+    if (h & kDevErrSize) return HSS_ERR_INVALID;
     if (h & kDevErrBounds) return HSS_ERR_CUDA;
     return HSS_OK;
 }

@@ -869,6 +869,8 @@ __device__ __forceinline__ PlanV plan_item(const uint64_t* seg_lo, const uint64_
             v.c[1] = 1;
         } else if (n <= (uint64_t)kSmallCap) {
             v.c[2] = 1;
+        } else if (n >= kMaxSegKeys) {
+            // too large for the split's 30-bit counts: left unsorted, reported by k_plan_write
         } else {
             v.c[3] = 1;
             v.c[4] = (uint32_t)ceil_div(n, kOsTile);
@@ -968,9 +970,10 @@ __global__ __launch_bounds__(1024) void k_plan_write(const uint64_t* __restrict_
                                                      const uint32_t* __restrict__ counters, uint32_t* __restrict__ tile_start,
                                                      uint32_t* __restrict__ large_id, uint32_t* __restrict__ large_seg,
                                                      uint32_t* __restrict__ list0, uint32_t* __restrict__ list1,
-                                                     uint32_t* __restrict__ list2) {
+                                                     uint32_t* __restrict__ list2, uint32_t* __restrict__ err) {
     const uint64_t s = (uint64_t)blockIdx.x * 1024 + threadIdx.x;
     const PlanV item = plan_item(seg_lo, seg_hi, nseg, s);
+    if (s < nseg && seg_hi[s] - seg_lo[s] >= kMaxSegKeys) atomicOr(err, kDevErrSize);
     PlanV v = item, tot;
     plan_scan(v, tot);
     const PlanV off = blk_load(blk, blockIdx.x);
@@ -1316,16 +1319,7 @@ cudaError_t fill_even_offsets(uint64_t* d_seg_off, uint64_t N, uint64_t p, cudaS
 // ---------------------------------------------------------------------------
 // Host driver.
 // ---------------------------------------------------------------------------
-static int num_sms() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 148;
-    }
-    return n;
-}
+static int num_sms() { return device_sm_count(); }
 
 template <bool PAY, int THREADS, int CAP>
 static cudaError_t launch_small(const uint64_t* in, uint64_t* out, const uint32_t* pin, uint32_t* pout,
@@ -1333,12 +1327,9 @@ static cudaError_t launch_small(const uint64_t* in, uint64_t* out, const uint32_
                                 const uint32_t* nlist, uint64_t count, uint64_t nseg, uint32_t min_n, uint32_t max_n,
                                 uint64_t fin, uint64_t fout, const SegSortWs& ws, cudaStream_t st) {
     constexpr size_t smem = msd_sort_smem<THREADS, CAP>();
-    static bool attr = false;
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(k_small_msd<PAY, THREADS, CAP>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        const cudaError_t e = ensure_func_attrs((const void*)k_small_msd<PAY, THREADS, CAP>, (int)smem);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     const int per_sm = std::max<int>(1, std::min<int>(2048 / THREADS, (int)(227 * 1024 / smem)));
     const uint64_t grid = std::min<uint64_t>(count, (uint64_t)num_sms() * per_sm * 4);
@@ -1354,12 +1345,9 @@ static cudaError_t launch_small_reg(const uint64_t* in, uint64_t* out, const uin
                                     const uint32_t* nlist, uint64_t count, uint64_t nseg, uint32_t min_n, uint32_t max_n,
                                     uint64_t fin, uint64_t fout, const SegSortWs& ws, cudaStream_t st) {
     constexpr size_t smem = reg_sort_smem<CAP>();
-    static bool attr = false;
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(k_small_reg<PAY, THREADS, CAP>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        const cudaError_t e = ensure_func_attrs((const void*)k_small_reg<PAY, THREADS, CAP>, (int)smem);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     const int per_sm = std::max<int>(1, std::min<int>(2048 / THREADS, (int)(227 * 1024 / smem)));
     const uint64_t grid = std::min<uint64_t>(count, (uint64_t)num_sms() * per_sm * 4);
@@ -1378,12 +1366,9 @@ static cudaError_t launch_fallback(const uint64_t* in, uint64_t* out, const uint
                                    const uint64_t* seg_lo, const uint64_t* seg_hi, uint64_t fin, uint64_t fout,
                                    const SegSortWs& ws, cudaStream_t st, uint64_t max_entries) {
     constexpr size_t smem = lsd_sort_smem<kC2Threads, kC2Items>();
-    static bool attr = false;
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(k_small_lsd<PAY, kC2Threads, kC2Items>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        const cudaError_t e = ensure_func_attrs((const void*)k_small_lsd<PAY, kC2Threads, kC2Items>, (int)smem);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     const uint64_t grid = std::min<uint64_t>((uint64_t)num_sms(), max_entries);
     if (grid == 0) return cudaSuccess;
@@ -1443,7 +1428,7 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
         HSS_LAUNCH(k_plan_count, nblk, 1024, 0, st, L.seg_lo, L.seg_hi, L.nseg, ws.blk);
         HSS_LAUNCH(k_plan_scan, 1, 1024, 0, st, nblk, ws.blk, ws.counters);
         HSS_LAUNCH(k_plan_write, nblk, 1024, 0, st, L.seg_lo, L.seg_hi, L.nseg, ws.blk, ws.counters, ws.tile_start,
-                   ws.large_id, ws.large_seg, ws.list[0], ws.list[1], ws.list[2]);
+                   ws.large_id, ws.large_seg, ws.list[0], ws.list[1], ws.list[2], ws.err);
         uint32_t hc[8];
         if ((e = cudaMemcpyAsync(hc, ws.counters + 16, sizeof(hc), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
@@ -1505,17 +1490,8 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
         A.status = ws.status; A.counter = ws.counters; A.err = ws.err;
         A.flip_in = L.flip_in; A.flip_out = fout;
         const size_t smem = (size_t)kOsTile * 9 + (PAY ? (size_t)kOsTile * 4 : 0);
-        static bool attr = false;
-        if (!attr) {
-            if ((e = cudaFuncSetAttribute(k_split<PAY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-                cudaSuccess)
-                return e;
-            // all of L1 as shared memory: the CTAs per SM are limited by their tiles
-            if ((e = cudaFuncSetAttribute(k_split<PAY>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) !=
-                cudaSuccess)
-                return e;
-            attr = true;
-        }
+        // all of L1 as shared memory: the CTAs per SM are limited by their tiles
+        if ((e = ensure_func_attrs((const void*)k_split<PAY>, (int)smem, 100)) != cudaSuccess) return e;
         const bool timed = timing && timing->enabled && timing->n < 16;
         if (timed) {
             cudaEventCreate(&timing->ev[timing->n][0]);

@@ -126,3 +126,28 @@ def test_binding_rejects_host_tensors_before_any_device_call():
     with pytest.raises(ValueError):
         hss._ptr(cpu)
     assert hss._ptr(np.zeros(4, dtype=np.uint64)) is not None
+
+
+def test_segment_size_limit_rejected_without_device(lib):
+    """A segment or bucket of 2^30 keys or more would overflow the split's
+    30-bit look-back counts: every entry point refuses it up front."""
+    from paper_1803_01237_gb300 import hss
+    L = hss.load()
+    st = hss.Stats()
+    dummy = ctypes.c_void_p(16)
+    big = 1 << 31
+    prm = hss.Params(eps=0.05, seed=1, p=1, oversample=5.0, max_rounds=0, flags=0)
+    assert L.hss_local_sort(dummy, None, 0, big, 1, dummy, None, dummy, 1 << 62, None) == -1
+    assert L.hss_partition(dummy, 0, big, ctypes.byref(prm), dummy, dummy, dummy, 1 << 62, ctypes.byref(st), None) == -1
+    assert L.hss_sort(dummy, None, 0, big, ctypes.byref(prm), dummy, None, dummy, dummy, dummy, 1 << 62,
+                      ctypes.byref(st), None) == -1
+    assert L.hss_rank_cuts(dummy, 0, big, 1, dummy, 1, dummy, None, None) == -1
+    assert L.hss_exchange(dummy, None, big, 1, dummy, dummy, dummy, None, dummy, 1 << 62, None) == -1
+    # a segment just below the limit passes the size check (and fails on the workspace)
+    n_ok = (1 << 30) - 1
+    assert L.hss_local_sort(dummy, None, 0, n_ok, 1, dummy, None, dummy, 16, None) == -2
+    # the sorting calls also bound the eps-balanced buckets: 2^30 - 1 keys on one
+    # processor is fine, but two processors of 2^29 + eps slack are not at large eps
+    prm2 = hss.Params(eps=1.0, seed=1, p=2, oversample=5.0, max_rounds=0, flags=0)
+    assert L.hss_sort(dummy, None, 0, 1 << 30, ctypes.byref(prm2), dummy, None, dummy, dummy, dummy, 1 << 62,
+                      ctypes.byref(st), None) == -1

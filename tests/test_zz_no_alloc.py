@@ -6,14 +6,16 @@ thread that must not take the allocator's locks.  hss_local_sort_noalloc
 serves them from a fixed scratch array inside the library.  These tests call
 it through the C ABI and check that it returns exactly what the regular
 hss_local_sort returns (integer sort: bit for bit), on two calls in a row,
-and that inputs past its fixed limit are refused before any device work.
-This file is collected last on purpose.
+that it equals the CPU oracle's stable local sort, and that inputs past its
+fixed limit are refused before any device work.  This file is collected last
+on purpose.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_1803_01237_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -98,3 +100,41 @@ def test_noalloc_allocates_nothing(lib):
     assert rc == 0
     assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == before
     assert free_after >= free_before - (2 << 20)  # no new device memory beyond driver noise
+
+
+@pytest.mark.parametrize("N,p,key_type", [(70001, 5, 0), (4096, 16, 1)])
+def test_noalloc_matches_oracle(lib, N, p, key_type):
+    """Against the oracle's stable local sort of every segment (Sec. 6.1
+    tagging): keys and the payload (each key's input index) bit for bit."""
+    raw = inputs.zipf(N, 77 + N, distinct=500)
+    keys_h = raw.view(np.int64) if key_type else raw
+    pay_h = np.arange(N, dtype=np.uint32)
+    ref_k, ref_p = oracle.segment_sort(keys_h, p, payload=pay_h)
+    keys = torch.from_numpy(raw.view(np.int64)).cuda()
+    pay = torch.from_numpy(pay_h.view(np.int32)).cuda()
+    rc, out, outp = _noalloc(lib, keys, p, pay, key_type)
+    assert rc == 0, rc
+    assert np.array_equal(out.cpu().numpy().view(np.uint64), np.ascontiguousarray(ref_k).view(np.uint64))
+    assert np.array_equal(outp.cpu().numpy().view(np.uint32), ref_p)
+
+
+def test_noalloc_refuses_a_capturing_stream(lib):
+    """The call reads its status word back with a stream synchronisation; on a
+    stream that is capturing work it returns HSS_ERR_INVALID without enqueuing."""
+    N, p = 1000, 2
+    keys = torch.from_numpy(inputs.uniform(N, 5).view(np.int64)).cuda()
+    out = torch.empty_like(keys)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        g.capture_begin()
+        try:
+            rc = lib.hss_local_sort_noalloc(_ptr(keys), None, 0, N, p, _ptr(out), None,
+                                            ctypes.c_void_p(s.cuda_stream))
+        finally:
+            g.capture_end()
+    assert rc == -1
+    # the stream and the library stay usable
+    rc, out2, _ = _noalloc(lib, keys, p)
+    assert rc == 0
