@@ -32,7 +32,7 @@ if ROOT not in sys.path:
 METRIC = "keys/s and % of HBM roofline (1 GB300) for HSS sort at eps; HSS rounds; batched jobs/s; p99"
 LOG2N, P, EPS, SEED, OVERSAMPLE = 28, 1024, 0.02, 1, 5.0
 WORKLOAD = ("HSS sort: N=2^28 uint64 keys, p=1024 segments of 2^18, eps=0.02, s=5; steps cycle over three seeded "
-            "inputs: uniform [0,2^64) (seed 1), 32-Gaussian mixture sigma=2^40 (seed 2), Zipf s=1.2 over 2^12 values (seed 3)")
+            "inputs: uniform [0,2^64) (seed 1), 32-Gaussian mixture sigma=2^40 (seed 2), Zipf s=1.2 over 2^12 values (seed 3); each input sampled with its own seed")
 DISTS = (("uniform", 1), ("gauss_mix", 2), ("zipf", 3))
 CPU_SAMPLE_LOG2N = 24      # cpu_baseline: first 2^24 keys, same p and eps
 PATH_BYTES_PER_KEY = 98.3  # algorithmic bytes of one whole hss_sort step per key (keys only)
@@ -237,7 +237,7 @@ def run_gpu(args):
     dev_inputs = []
     for name, sd in dists:
         kh = keys_h if name == "uniform" else inputs.SCALE_DISTRIBUTIONS[name](N, sd)
-        dev_inputs.append((name, torch.from_numpy(kh.view(np.int64)).to(dev)))
+        dev_inputs.append((name, torch.from_numpy(kh.view(np.int64)).to(dev), sd))
     keys = dev_inputs[0][1]
     out = torch.empty_like(keys)
 
@@ -246,8 +246,9 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def step(k, flags=0):
-        return hss.sort(dev_inputs[k % len(dev_inputs)][1], P, EPS, SEED, oversample=OVERSAMPLE, flags=flags, out=out)
+    def step(k, flags=0):  # each input with its own seed, as in the oracle's records of this workload
+        _, dk, sd = dev_inputs[k % len(dev_inputs)]
+        return hss.sort(dk, P, EPS, sd, oversample=OVERSAMPLE, flags=flags, out=out)
 
     for w in range(max(args.warmup, len(dev_inputs))):
         step(w)
@@ -259,7 +260,7 @@ def run_gpu(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = hss.launch_count()
     pass_ms, pass_launches, pass_keys, phase = 0.0, 0, 0, {}
-    per_dist = {name: {"ms": 0.0, "steps": 0, "rounds": []} for name, _ in dev_inputs}
+    per_dist = {name: {"ms": 0.0, "steps": 0, "rounds": []} for name, _, _ in dev_inputs}
     rounds = None
     barrier()
     ev0.record(stream)
@@ -328,7 +329,7 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N, "p": P, "eps": EPS, "oversample": OVERSAMPLE,
-                   "distributions": [n for n, _ in dev_inputs],
+                   "distributions": [n for n, _, _ in dev_inputs],
                    "l2": "inputs (2 GiB keys per distribution) larger than L2; no flush between steps",
                    "parallelism": "replicas only" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

@@ -492,7 +492,10 @@ int oracle_hss(const uint64_t* keys, const uint32_t* payload, uint64_t N, int ke
      * order, the run of keys in [S(b), S(b+1)); the bucket is then merged by
      * (key, processor, index), i.e. a stable sort of the concatenated runs. */
     if (out_keys) {
-        kv* buf = (kv*)malloc(sizeof(kv) * (N ? N : 1));
+        /* one bucket at a time: the buffer holds the largest bucket */
+        uint64_t maxb = 1;
+        for (uint32_t b = 0; b < p; ++b) if (offsets[b + 1] - offsets[b] > maxb) maxb = offsets[b + 1] - offsets[b];
+        kv* buf = (kv*)malloc(sizeof(kv) * maxb);
         for (uint32_t b = 0; b < p; ++b) {
             uint64_t n = 0, base = offsets[b];
             for (uint32_t s = 0; s < p; ++s) {

@@ -61,7 +61,7 @@ size_t segsort_ws_bytes(uint64_t N, uint64_t nseg) {
     b += 4 * align_up(d.ml * kRadix * 8, 256);                        // sub_lo/hi x2
     b += align_up(d.tiles * kRadix * 4, 256);                         // status
     b += align_up(64 * 4, 256);                                       // counters
-    b += 5 * align_up(d.list * 4, 256);                               // class lists, fallback, slow lists
+    b += 8 * align_up(d.list * 4, 256);                               // class lists, fallback, slow lists
     b += align_up(8 * (d.list / 1024 + 2) * 4, 256);                  // blk
     return b;
 }
@@ -96,6 +96,7 @@ SegSortWs segsort_ws_carve(void* base, uint64_t N, uint64_t nseg, uint32_t* err)
     for (int i = 0; i < 3; ++i) w.list[i] = (uint32_t*)take(d.list * 4);
     w.fb_list = (uint32_t*)take(d.list * 4);
     w.slow_list = (uint32_t*)take(d.list * 4);
+    for (int i = 0; i < 3; ++i) w.slow_keys[i] = (uint32_t*)take(d.list * 4);
     w.blk = (uint32_t*)take(8 * (d.list / 1024 + 2) * 4);
     w.err = err;
     return w;
@@ -764,6 +765,151 @@ __global__ __launch_bounds__(THREADS) void k_small_reg(
 }
 
 // ---------------------------------------------------------------------------
+// Keys alone, on chip, segments of up to CAP = THREADS * ITEMS keys held in
+// registers.  Equal keys are indistinguishable, so no input order has to be
+// kept: a counting pass on a digit interpolating the segment's key range
+// (R groups, monotone in the key) hands every key a slot in its group through
+// one shared counter; keys are scattered into group order; a key in a group
+// of two or more moves to its group's start plus the number of the group's
+// keys below it in (key, slot) order, a total order; a large group holding a
+// single key value needs no ranking.  A segment with a large group of
+// distinct keys is appended to slow_list for the shared-memory kernel.
+// ---------------------------------------------------------------------------
+template <int CAP, int R>
+constexpr size_t keys_sort_smem() {
+    return (size_t)CAP * 8 + (size_t)(R + 1) * 4 + 32 * 4 + 2 * 32 * 8 + 64;
+}
+
+template <int THREADS, int CAP, int R>
+__global__ __launch_bounds__(THREADS) void k_small_keys(
+    const uint64_t* kin, uint64_t* kout, const uint64_t* __restrict__ seg_lo, const uint64_t* __restrict__ seg_hi,
+    const uint32_t* __restrict__ list, const uint32_t* __restrict__ nlist, uint64_t nseg, uint32_t min_n,
+    uint32_t max_n, uint64_t flip_in, uint64_t flip_out, uint32_t* __restrict__ slow_list,
+    uint32_t* __restrict__ slow_count) {
+    constexpr int ITEMS = CAP / THREADS;
+    constexpr int WARPS = THREADS / 32;
+    static_assert(CAP % THREADS == 0 && R % THREADS == 0 && R <= 8192 && CAP <= (1 << 18), "keys sort shape");
+    constexpr uint32_t kDigitMask = 8191u;  // digit in bits 0..12, slot from bit 13
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t* s_key = (uint64_t*)smem;                                              // CAP
+    uint32_t* s_start = (uint32_t*)(s_key + CAP);                                   // R + 1
+    uint32_t* s_warp = s_start + (R + 1);                                           // 32
+    uint64_t* s_red = (uint64_t*)(((uintptr_t)(s_warp + 32) + 7) & ~(uintptr_t)7);  // 2 * 32
+    uint32_t* s_flag = (uint32_t*)(s_red + 64);                                     // [0] mixed large group
+
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const uint64_t count = list ? (uint64_t)*nlist : nseg;
+    for (uint64_t k = blockIdx.x; k < count; k += gridDim.x) {
+        const uint64_t s = list ? (uint64_t)list[k] : k;
+        const uint64_t base = seg_lo[s];
+        const uint64_t n64 = seg_hi[s] - base;
+        if (n64 <= min_n || n64 > max_n) continue;  // uniform per CTA
+        const uint32_t n = (uint32_t)n64;
+        uint64_t key[ITEMS];
+        uint64_t kmin = ~0ull, kmax = 0;
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const uint32_t e = tid + i * THREADS;
+            key[i] = e < n ? kin[base + e] ^ flip_in : 0ull;
+            if (e < n) { kmin = min(kmin, key[i]); kmax = max(kmax, key[i]); }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            kmin = min(kmin, (uint64_t)__shfl_xor_sync(0xffffffffu, kmin, o));
+            kmax = max(kmax, (uint64_t)__shfl_xor_sync(0xffffffffu, kmax, o));
+        }
+        if (lane == 0) { s_red[w] = kmin; s_red[32 + w] = kmax; }
+        for (int d = tid; d < R; d += THREADS) s_start[d] = 0;
+        if (tid == 0) s_flag[0] = 0;
+        __syncthreads();
+        {
+            uint64_t a = ~0ull, b = 0;
+            for (int i = 0; i < WARPS; ++i) { a = min(a, s_red[i]); b = max(b, s_red[32 + i]); }
+            kmin = a;
+            kmax = b;
+        }
+        if (kmin == kmax) {  // all keys equal
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                const uint32_t e = tid + i * THREADS;
+                if (e < n) kout[base + e] = key[i] ^ flip_out;
+            }
+            __syncthreads();
+            continue;
+        }
+        const uint64_t range = kmax - kmin;
+        const uint64_t mult = range < (uint64_t)R ? 0ull : (uint64_t)((double)(R - 1) * 18446744073709551616.0 / (double)range);
+        uint32_t dp[ITEMS];
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const uint32_t e = tid + i * THREADS;
+            dp[i] = 0;
+            if (e < n) {
+                const uint64_t off = key[i] - kmin;
+                const uint32_t d = mult ? min((uint32_t)__umul64hi(off, mult), (uint32_t)R - 1) : (uint32_t)off;
+                dp[i] = d | (atomicAdd(&s_start[d], 1u) << 13);
+            }
+        }
+        __syncthreads();
+        uint32_t mx = 0;
+        for (int d = tid; d < R; d += THREADS) mx = max(mx, s_start[d]);
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        scan_smem_inplace<THREADS, R>(s_start, s_warp);
+        if (lane == 0) s_warp[w] = mx;
+        if (tid == 0) s_start[R] = n;
+        __syncthreads();
+        mx = 0;
+        for (int i = 0; i < WARPS; ++i) mx = max(mx, s_warp[i]);
+        // scatter into group order; dp keeps the digit and now the group slot
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const uint32_t e = tid + i * THREADS;
+            if (e < n) {
+                const uint32_t d = dp[i] & kDigitMask;
+                const uint32_t pos = s_start[d] + (dp[i] >> 13);
+                s_key[pos] = key[i];
+                dp[i] = d | (pos << 13);
+            }
+        }
+        __syncthreads();
+        if (mx > 1u) {
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                const uint32_t e = tid + i * THREADS;
+                if (e >= n) continue;
+                const uint32_t d = dp[i] & kDigitMask, pos = dp[i] >> 13;
+                const uint32_t a = s_start[d], b = s_start[d + 1];
+                if (b - a <= 1u) continue;
+                if (b - a > (uint32_t)kTinyGroup) {  // large group: fine as it is if it holds one value
+                    if (s_key[a] != key[i]) s_flag[0] = 1u;
+                    continue;
+                }
+                uint32_t r = 0;
+                for (uint32_t q = a; q < b; ++q) {
+                    const uint64_t ky = s_key[q];
+                    r += (ky < key[i] || (ky == key[i] && q < pos)) ? 1u : 0u;
+                }
+                dp[i] = d | ((a + r) << 13);
+            }
+            __syncthreads();
+            if (s_flag[0]) {  // uniform: a large group of distinct keys
+                if (tid == 0) slow_list[atomicAdd(slow_count, 1u)] = (uint32_t)s;
+                __syncthreads();
+                continue;
+            }
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                const uint32_t e = tid + i * THREADS;
+                if (e < n) s_key[dp[i] >> 13] = key[i];
+            }
+            __syncthreads();
+        }
+        for (uint32_t j = tid; j < n; j += THREADS) kout[base + j] = s_key[j] ^ flip_out;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Stable LSD sort on chip of the segments in the fallback list (at most
 // kSmallCap keys each): 8-bit digit passes over a 16-bit index permutation,
 // skipping digits that are constant over the segment.
@@ -962,6 +1108,9 @@ __global__ __launch_bounds__(1024) void k_plan_scan(uint32_t nblk, uint32_t* __r
         counters[0] = 0;   // tile counter of this level's scatter pass
         counters[24] = 0;  // fallback list of this level's on-chip sorts
         counters[25] = 0;  // segments the register kernels leave to the shared-memory kernel
+        counters[26] = 0;  // ... and the keys-only kernels, per size class
+        counters[27] = 0;
+        counters[28] = 0;
     }
 }
 
@@ -1186,7 +1335,7 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
     uint64_t* s_keys = (uint64_t*)os_smem;             // kOsTile keys
     uint32_t* s_pay = (uint32_t*)(s_keys + kOsTile);   // kOsTile payloads (PAY)
     uint8_t* s_dg = (uint8_t*)(s_pay + (PAY ? kOsTile : 0));  // kOsTile digits of the staged keys
-    __shared__ uint32_t s_hist[kOsWarps * kRadix];
+    __shared__ uint32_t s_hist[PAY ? kOsWarps * kRadix : 1];
     __shared__ uint32_t s_total[kRadix], s_start[kRadix];
     __shared__ uint64_t s_gbase[kRadix];
     __shared__ uint32_t s_warp[32];
@@ -1248,7 +1397,29 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
     auto publish = [&]() {
         if (tid < kRadix) st_relaxed(&cur[(uint64_t)t * kRadix + tid], (ti == 0 ? kFlagPre : kFlagAgg) | s_total[tid]);
     };
-    block_rank<kOsWarps, kOsItems>(digit_of, count, rank, s_hist, s_total, s_start, s_warp, publish);
+    if constexpr (PAY) {
+        block_rank<kOsWarps, kOsItems>(digit_of, count, rank, s_hist, s_total, s_start, s_warp, publish);
+    } else {
+        // Keys alone: equal keys are indistinguishable, so the order of a
+        // digit's keys inside the tile is free and one shared counter per
+        // digit hands out the slots (one atomic per key instead of the
+        // ballot ranking the payload path needs for stability).
+        for (int d = tid; d < kRadix; d += kOsThreads) s_total[d] = 0;
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kOsItems; ++i) {
+            const uint32_t d = digit_of(i);
+            rank[i] = d < kRadix ? atomicAdd(&s_total[d], 1u) : 0u;
+        }
+        __syncthreads();
+        scan256_smem<kOsThreads>(s_total, s_start, s_warp);
+        publish();
+#pragma unroll
+        for (int i = 0; i < kOsItems; ++i) {
+            const uint32_t d = digit_of(i);
+            if (d < kRadix) rank[i] += s_start[d];
+        }
+    }
 #pragma unroll
     for (int i = 0; i < kOsItems; ++i) {
         if (wbase + i * 32 < count) {
@@ -1357,6 +1528,24 @@ static cudaError_t launch_small_reg(const uint64_t* in, uint64_t* out, const uin
     return cudaGetLastError();
 }
 
+template <int THREADS, int CAP, int R>
+static cudaError_t launch_keys(const uint64_t* in, uint64_t* out, const uint64_t* seg_lo, const uint64_t* seg_hi,
+                               const uint32_t* list, const uint32_t* nlist, uint64_t count, uint64_t nseg,
+                               uint32_t min_n, uint32_t max_n, uint64_t fin, uint64_t fout, uint32_t* slow,
+                               uint32_t* slow_count, cudaStream_t st) {
+    constexpr size_t smem = keys_sort_smem<CAP, R>();
+    {
+        const cudaError_t e = ensure_func_attrs((const void*)k_small_keys<THREADS, CAP, R>, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int per_sm = std::max<int>(1, std::min<int>(2048 / THREADS, (int)(227 * 1024 / smem)));
+    const uint64_t grid = std::min<uint64_t>(count, (uint64_t)num_sms() * per_sm * 4);
+    if (grid == 0) return cudaSuccess;
+    HSS_LAUNCH((k_small_keys<THREADS, CAP, R>), (unsigned)grid, THREADS, smem, st, in, out, seg_lo, seg_hi, list, nlist,
+               nseg, min_n, max_n, fin, fout, slow, slow_count);
+    return cudaGetLastError();
+}
+
 // The stable LSD kernel over this level's fallback list (length on the device).
 template <bool PAY>
 // max_entries bounds the list on the host (the segments that could have
@@ -1435,21 +1624,55 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
         const uint32_t n_large = hc[3], tiles = hc[4];
         const uint64_t keys_large = (uint64_t)hc[6] | ((uint64_t)hc[7] << 32);
         // Segments of this level that fit on chip: straight to the output.
-        if (hc[0] && (e = launch_small<PAY, kC0Threads, kC0Cap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi, ws.list[0],
+        if (!PAY) {
+            // keys alone: the register kernels first, their leftovers to the
+            // shared-memory kernel of the same class
+            const uint32_t* lists[3] = {ws.list[0], ws.list[1], ws.list[2]};
+            for (int c = 0; c < 3; ++c) {
+                if (!hc[c]) continue;
+                const uint32_t lo_n = c == 0 ? 0u : (c == 1 ? (uint32_t)kC0Cap : (uint32_t)kC1Cap);
+                const uint32_t hi_n = c == 0 ? (uint32_t)kC0Cap : (c == 1 ? (uint32_t)kC1Cap : (uint32_t)kSmallCap);
+                uint32_t* slow = ws.slow_keys[c];
+                uint32_t* slow_n = ws.counters + 26 + c;
+                if (c == 0)
+                    e = launch_keys<kC0Threads, kC0Cap, 1024>(L.in, dst, L.seg_lo, L.seg_hi, lists[c], ws.counters + 16,
+                                                            hc[c], L.nseg, lo_n, hi_n, L.flip_in, fout, slow, slow_n, st);
+                else if (c == 1)
+                    e = launch_keys<kC1Threads, kC1Cap, 2048>(L.in, dst, L.seg_lo, L.seg_hi, lists[c], ws.counters + 17,
+                                                            hc[c], L.nseg, lo_n, hi_n, L.flip_in, fout, slow, slow_n, st);
+                else
+                    e = launch_keys<kC2Threads, kSmallCap, 4096>(L.in, dst, L.seg_lo, L.seg_hi, lists[c],
+                                                               ws.counters + 18, hc[c], L.nseg, lo_n, hi_n, L.flip_in,
+                                                               fout, slow, slow_n, st);
+                if (e != cudaSuccess) return e;
+                if (c == 0)
+                    e = launch_small<PAY, kC0Threads, kC0Cap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi, slow, slow_n,
+                                                              hc[c], L.nseg, lo_n, hi_n, L.flip_in, fout, ws, st);
+                else if (c == 1)
+                    e = launch_small<PAY, kC1Threads, kC1Cap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi, slow, slow_n,
+                                                              hc[c], L.nseg, lo_n, hi_n, L.flip_in, fout, ws, st);
+                else
+                    e = launch_small<PAY, kC2Threads, kSmallCap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi, slow,
+                                                                 slow_n, hc[c], L.nseg, lo_n, hi_n, L.flip_in, fout,
+                                                                 ws, st);
+                if (e != cudaSuccess) return e;
+            }
+        }
+        if (PAY && hc[0] && (e = launch_small<PAY, kC0Threads, kC0Cap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi, ws.list[0],
                                                                 ws.counters + 16, hc[0], L.nseg, 0u, (uint32_t)kC0Cap,
                                                                 L.flip_in, fout, ws, st)) != cudaSuccess)
             return e;
-        if (hc[1] && (e = launch_small_reg<PAY, kC1Threads, kC1Cap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi,
+        if (PAY && hc[1] && (e = launch_small_reg<PAY, kC1Threads, kC1Cap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi,
                                                                     ws.list[1], ws.counters + 17, hc[1], L.nseg,
                                                                     (uint32_t)kC0Cap, (uint32_t)kC1Cap, L.flip_in, fout,
                                                                     ws, st)) != cudaSuccess)
             return e;
-        if (hc[1] &&
+        if (PAY && hc[1] &&
             (e = launch_small<PAY, kC1Threads, kC1Cap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi, ws.slow_list,
                                                        ws.counters + 25, hc[1], L.nseg, 0u, (uint32_t)kC1Cap, L.flip_in,
                                                        fout, ws, st)) != cudaSuccess)
             return e;
-        if (hc[2] && (e = launch_small<PAY, kC2Threads, kSmallCap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi,
+        if (PAY && hc[2] && (e = launch_small<PAY, kC2Threads, kSmallCap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi,
                                                                    ws.list[2], ws.counters + 18, hc[2], L.nseg,
                                                                    (uint32_t)kC1Cap, (uint32_t)kSmallCap, L.flip_in, fout,
                                                                    ws, st)) != cudaSuccess)

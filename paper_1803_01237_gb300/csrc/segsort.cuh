@@ -54,6 +54,7 @@ struct SegSortWs {
     uint32_t* list[3];     // [max_list] segments of each on-chip size class
     uint32_t* fb_list;     // [max_list] segments left to the stable LSD kernel (count in counters[24])
     uint32_t* slow_list;   // [max_list] segments the register kernel leaves to the shared-memory kernel (counters[25])
+    uint32_t* slow_keys[3];  // [max_list] per size class: segments the keys-only kernel leaves (counters[26..28])
     uint32_t* blk;         // [8 * (max_list / 1024 + 2)] per-chunk counts of the planning scan
     uint32_t* err;         // device error word (kDevErr*)
 };

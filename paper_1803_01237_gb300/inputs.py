@@ -161,17 +161,47 @@ def _spread3(v: np.ndarray) -> np.ndarray:
     return v
 
 
+def _cbrt(x: np.ndarray) -> np.ndarray:
+    """Cube root of positive doubles by Newton's method from above, with
+    IEEE add, multiply and divide only, so the same bits come out on every
+    machine (library sin/cos/pow differ between platforms by an ulp, enough to
+    move a quantised coordinate across a cell boundary)."""
+    x = np.asarray(x, dtype=np.float64)
+    _, e = np.frexp(x)                                  # x = f 2^e, f in [0.5, 1)
+    y = np.ldexp(np.ones_like(x), -((-e) // 3))          # 2^ceil(e/3) >= cbrt(x)
+    for _ in range(12):                                 # monotone from above; 12 steps reach the ulp
+        y = (2.0 * y + x / (y * y)) / 3.0
+    return y
+
+
+def _plummer_radius(m: np.ndarray) -> np.ndarray:
+    """r = (m^(-2/3) - 1)^(-1/2) for a mass fraction m in (0, 1)."""
+    c = _cbrt(m)
+    return np.sqrt((c * c) / (1.0 - c * c))
+
+
+def _unit_vectors(g: np.random.Generator, n: int) -> np.ndarray:
+    """n isotropic unit vectors: points uniform in the cube [-1, 1]^3 kept
+    when inside the unit ball (and not at its centre), then normalised."""
+    out = np.empty((0, 3), dtype=np.float64)
+    while out.shape[0] < n:
+        v = 2.0 * g.random((2 * (n - out.shape[0]) + 64, 3)) - 1.0
+        s = v[:, 0] * v[:, 0] + v[:, 1] * v[:, 1] + v[:, 2] * v[:, 2]
+        keep = (s <= 1.0) & (s > 1e-12)
+        v = v[keep] / np.sqrt(s[keep])[:, None]
+        out = np.concatenate([out, v])
+    return out[:n]
+
+
 def _plummer_chunk(seed: int, c: int, n: int, bits: int) -> np.ndarray:
     g = rng(seed, (8 << 32) | c)
-    r_max = (0.999 ** (-2.0 / 3.0) - 1.0) ** -0.5
+    r_max = float(_plummer_radius(np.array([0.999]))[0])
     scale = float(1 << bits)
     m = 0.999 * (1.0 - g.random(n))  # (0, 0.999]
-    r = (m ** (-2.0 / 3.0) - 1.0) ** -0.5
-    ct = 2.0 * g.random(n) - 1.0
-    st = np.sqrt(np.maximum(0.0, 1.0 - ct * ct))
-    ph = 2.0 * math.pi * g.random(n)
-    xyz = (r * st * np.cos(ph), r * st * np.sin(ph), r * ct)
-    q = [np.clip(np.floor((v + r_max) / (2.0 * r_max) * scale), 0, scale - 1).astype(np.uint64) for v in xyz]
+    r = _plummer_radius(m)
+    d = _unit_vectors(g, n)
+    q = [np.clip(np.floor((r * d[:, a] + r_max) / (2.0 * r_max) * scale), 0, scale - 1).astype(np.uint64)
+         for a in range(3)]
     return _spread3(q[0]) | (_spread3(q[1]) << np.uint64(1)) | (_spread3(q[2]) << np.uint64(2))
 
 
@@ -179,9 +209,11 @@ def plummer_morton(N: int, seed: int, bits: int = 21):
     """Morton keys of a Plummer sphere plus the particle index as payload.
 
     Radius from the Plummer mass profile m(r) = r^3 (1+r^2)^(-3/2): for a mass
-    fraction m ~ U(0, 0.999], r = (m^(-2/3) - 1)^(-1/2); isotropic direction;
-    each axis quantised to ``bits`` bits over [-r_max, r_max] with r_max = r(0.999).
-    Chunks of 2^22 particles draw from their own streams, so the chunks are
+    fraction m ~ U(0, 0.999], r = (m^(-2/3) - 1)^(-1/2); isotropic direction
+    (rejection from the cube); each axis quantised to ``bits`` bits over
+    [-r_max, r_max] with r_max = r(0.999).  Only IEEE add, multiply, divide
+    and square root are used, so every machine draws the same keys.  Chunks
+    of 2^22 particles draw from their own streams, so the chunks are
     generated on all host cores and the result does not depend on the count.
     """
     from concurrent.futures import ThreadPoolExecutor
@@ -204,6 +236,24 @@ def plummer_morton(N: int, seed: int, bits: int = 21):
 
 # --- batched and served jobs ---------------------------------------------------
 
+def batch_job_plan(njobs: int, seed: int, lo_log2: int = 10, hi_log2: int = 22):
+    """Sizes (log-uniform in [2^lo, 2^hi]) and the uniform-or-Zipf coin of
+    every job of a batch."""
+    g = rng(seed, 9)
+    u = g.random(njobs)
+    sizes = np.floor(2.0 ** (lo_log2 + (hi_log2 - lo_log2) * u)).astype(np.int64)
+    coin = g.random(njobs) < 0.5
+    return sizes, coin
+
+
+def batch_job(j: int, seed: int, n: int, uniform_coin: bool, zipf_s: float = 1.1,
+              zipf_distinct: int = 1 << 16) -> np.ndarray:
+    """Keys of job j of a batch (int64): every job draws from its own streams."""
+    if uniform_coin:
+        return uniform(int(n), seed * 1000003 + j).view(np.int64)
+    return zipf(int(n), seed * 1000003 + j, distinct=zipf_distinct, s=zipf_s).view(np.int64)
+
+
 def batch_jobs(njobs: int, seed: int, lo_log2: int = 10, hi_log2: int = 22, zipf_s: float = 1.1,
                zipf_distinct: int = 1 << 16):
     """Independent int64 jobs with sizes log-uniform in [2^lo, 2^hi]; each is
@@ -211,17 +261,11 @@ def batch_jobs(njobs: int, seed: int, lo_log2: int = 10, hi_log2: int = 22, zipf
     from concurrent.futures import ThreadPoolExecutor
     import os
 
-    g = rng(seed, 9)
-    u = g.random(njobs)
-    sizes = np.floor(2.0 ** (lo_log2 + (hi_log2 - lo_log2) * u)).astype(np.int64)
-    coin = g.random(njobs) < 0.5
+    sizes, coin = batch_job_plan(njobs, seed, lo_log2, hi_log2)
     kinds = ["uniform" if coin[j] else "zipf" for j in range(njobs)]
 
-    def one(j):  # every job draws from its own streams: generated on all host cores
-        n = int(sizes[j])
-        if coin[j]:
-            return uniform(n, seed * 1000003 + j).view(np.int64)
-        return zipf(n, seed * 1000003 + j, distinct=zipf_distinct, s=zipf_s).view(np.int64)
+    def one(j):  # generated on all host cores
+        return batch_job(j, seed, int(sizes[j]), bool(coin[j]), zipf_s, zipf_distinct)
 
     with ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1))) as ex:
         jobs = list(ex.map(one, range(njobs)))

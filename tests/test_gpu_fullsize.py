@@ -1,18 +1,28 @@
 """The CUDA path at the full sizes of the workloads, in the launch
-configuration bench.py times.
+configuration bench.py times, against the oracle's stored records.
 
-The CPU oracle cannot run 2^28 keys in test time, so these tests check what
-holds at any size and what the oracle can compute one item at a time:
-  * the output is the stable sort of the input (against torch's stable sort
-    on the device, with the payload carrying each key's input index);
-  * chi(0) = 0, chi(p) = N, monotone, every |chi(i) - t_i| <= floor(N eps/2p)
-    (Sec. 2), hence every bucket within the balance bound;
-  * a sample of splitters: the oracle sorts only the splitter's segment and
-    finds the input element at the splitter's tag; the globally sorted output
-    holds that element at position chi(i) (S(i) = I(chi(i)));
-  * per-round sample sizes inside a 6-sigma band of q |gamma| (Lemma 4.6).
+tests/golden/make_goldens.py ran the CPU oracle (and nothing else) on the same
+seeded inputs and stored, per case: the round count, every round's sample size
+Z_j, |gamma_j| and unresolved count (Sec. 4.2.2), tol, the offsets
+chi(0..p) and every splitter tag (key, seg, spos) in full, and SHA-256 digests
+of the input and of the globally sorted keys and payload.  Each test
+regenerates the input, checks its digest (the generators use only exact
+arithmetic, so every machine draws the same keys), runs the GPU path and
+compares:
+  * rounds, Z_j, |gamma_j|, unresolved counts, tol, status exactly;
+  * the offsets and the splitter tags element by element;
+  * the sorted keys and payload through their digests (and, as a cheap
+    cross-check that localises a mismatch, sortedness and chi(i) positions).
+
+Workloads: the bench input set (N = 2^28, p = 1024, eps = 0.02; uniform,
+32-Gaussian mixture, Zipf) with the payload = input index and keys alone (the
+bench's own call); the Plummer/Morton workload (N = 2^30 with payload,
+p = 16384, eps = 0.01); the batched workload (4096 int64 jobs of 2^10..2^22
+keys, one hss_sort_batch call), every job against its record.
 """
-import math
+import hashlib
+import json
+import os
 
 import numpy as np
 import pytest
@@ -24,6 +34,8 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
 
 @pytest.fixture(scope="module")
 def hss():
@@ -34,85 +46,155 @@ def hss():
     return h
 
 
-def _check_fullsize(hss, keys_h, p, eps, seed, payload_is_index=True, oversample=5.0):
-    N = keys_h.shape[0]
-    dk = torch.from_numpy(keys_h.view(np.int64)).cuda()
-    dp = torch.arange(N, dtype=torch.int32, device="cuda") if payload_is_index else None
-    res = hss.sort(dk, p, eps, seed, payload=dp, oversample=oversample)
-    torch.cuda.synchronize()
-    assert res.status == 0
-    # 1. stable sort of the input (u64 order = i64 order after flipping the sign bit)
-    sign = torch.tensor(-(1 << 63), dtype=torch.int64, device="cuda")
-    flipped = torch.bitwise_xor(dk, sign)
-    ref_vals, ref_idx = torch.sort(flipped, stable=True)
-    assert torch.equal(torch.bitwise_xor(res.keys, sign), ref_vals)
-    if payload_is_index:
-        assert torch.equal(res.payload.to(torch.int64), ref_idx)
-    del flipped, ref_vals, ref_idx
-    # 2. offsets within the target ranges
-    off = res.offsets.cpu().numpy().astype(np.int64)
-    tol = oracle.tolerance(N, p, eps)
-    assert res.tol == tol
-    t = (np.arange(1, p, dtype=object) * N // p).astype(np.int64)
-    assert off[0] == 0 and off[-1] == N and np.all(np.diff(off) >= 0)
-    assert np.all(np.abs(off[1:-1] - t) <= tol)
-    # 3. sampled splitters are the input elements of rank chi(i)
-    k_spl, seg, spos = res.splitter_tags()
-    out_pay = res.payload.cpu().numpy() if payload_is_index else None
-    out_keys = res.keys.cpu().numpy().view(np.uint64)
-    bounds = oracle.segment_bounds(N, p)
-    g = np.random.default_rng(seed)
-    for i in g.choice(p - 1, size=min(12, p - 1), replace=False):
-        s = int(seg[i])
-        assert s >= 0
-        lo, hi = int(bounds[s]), int(bounds[s + 1])
-        srt, idx = oracle.segment_sort(keys_h[lo:hi], 1, payload=np.arange(lo, hi, dtype=np.uint32))
-        assert srt[int(spos[i])] == np.uint64(k_spl[i])
-        assert out_keys[int(off[i + 1])] == np.uint64(k_spl[i])
-        if payload_is_index:
-            assert int(out_pay[int(off[i + 1])]) == int(idx[int(spos[i])])
-    # 4. sample sizes inside a Chernoff band around q |gamma|
-    for r in range(res.rounds):
-        gam = res.gamma[r]
-        q = min(1.0, oversample * p / gam)
-        mean = q * gam
-        sd = math.sqrt(max(mean * (1 - q), 1e-9))
-        assert abs(res.sample_size[r] - mean) <= 6 * sd + 1
-    return res
+def _sha(a: np.ndarray, n: int = 64) -> str:
+    return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()[:n]
 
 
-@pytest.mark.timeout(600)
-@pytest.mark.parametrize("dist", ["uniform", "gauss_mix", "zipf"])
-def test_bench_workload_fullsize(hss, dist):
-    """N = 2^28 uint64, p = 1024, eps = 0.02: the bench configuration."""
-    N = 1 << 28
-    seed = {"uniform": 1, "gauss_mix": 2, "zipf": 3}[dist]
-    keys = inputs.SCALE_DISTRIBUTIONS[dist](N, seed)
-    res = _check_fullsize(hss, keys, 1024, 0.02, seed)
-    assert res.rounds <= 12
+def _load(name):
+    import gzip
+    path = os.path.join(GOLDEN, f"fullsize_{name}.json")
+    if os.path.exists(path + ".gz"):
+        path += ".gz"
+    if not os.path.exists(path):
+        pytest.fail(f"missing oracle record {path}: run tests/golden/make_goldens.py {name}")
+    rec = json.load(gzip.open(path, "rt") if path.endswith(".gz") else open(path))
+    npz = os.path.join(GOLDEN, f"fullsize_{name}.npz")
+    arr = np.load(npz) if os.path.exists(npz) else None
+    return rec, arr
+
+
+def _compare(res, rec, arr, prefix, N, payload_sha=True):
+    assert res.status == rec["status"]
+    assert res.tol == rec["tol"]
+    assert res.rounds == rec["rounds"]
+    assert res.sample_size == rec["sample_size"]
+    assert res.gamma == rec["gamma"]
+    assert res.unresolved == rec["unresolved"]
+    off = res.offsets.cpu().numpy().astype(np.uint64)
+    want_off = arr[f"{prefix}offsets"]
+    bad = np.nonzero(off != want_off)[0]
+    assert bad.size == 0, f"offsets differ at {bad[:8]} (first: {off[bad[0]]} vs {want_off[bad[0]]})"
+    k, s, sp = res.splitter_tags()
+    for name, got, want in (("key", k.view(np.uint64), arr[f"{prefix}spl_key"]),
+                            ("seg", s.astype(np.int32), arr[f"{prefix}spl_seg"]),
+                            ("spos", sp.astype(np.uint32), arr[f"{prefix}spl_spos"])):
+        bad = np.nonzero(got != want)[0]
+        assert bad.size == 0, f"splitter {name} differs at {bad[:8]}"
+    out = res.keys.cpu().numpy().view(np.uint64)
+    if _sha(out) != rec["out_keys_sha256"]:
+        # localise: sortedness, then the splitter keys at their positions
+        assert np.all(out[:-1] <= out[1:]) if out.dtype == np.uint64 else True, "output not sorted"
+        pos = want_off[1:-1].astype(np.int64)
+        member = arr[f"{prefix}spl_seg"] >= 0
+        assert np.array_equal(out[pos[member]], arr[f"{prefix}spl_key"][member]), "splitters not at chi(i)"
+        pytest.fail("sorted keys differ from the oracle's (digest)")
+    if payload_sha:
+        assert _sha(res.payload.cpu().numpy().view(np.uint32)) == rec["out_payload_sha256"], "payload differs"
 
 
 @pytest.mark.timeout(900)
-def test_plummer_morton_payload_fullsize(hss):
+@pytest.mark.parametrize("dist", ["uniform", "gauss_mix", "zipf"])
+def test_bench_workload_vs_oracle_record(hss, dist):
+    """N = 2^28 uint64, p = 1024, eps = 0.02: the bench configuration, with
+    the input index as payload and with keys alone (the bench's call)."""
+    rec_all, arr = _load("scale")
+    cfg = rec_all["config"]
+    rec = rec_all["cases"][dist]
+    N, p, eps, seed = cfg["N"], cfg["p"], cfg["eps"], cfg["inputs"][dist]
+    keys = inputs.SCALE_DISTRIBUTIONS[dist](N, seed)
+    assert _sha(keys) == rec["input_sha256"], "the input generator drew different keys on this machine"
+    dk = torch.from_numpy(keys.view(np.int64)).cuda()
+    del keys
+    dp = torch.arange(N, dtype=torch.int32, device="cuda")
+    res = hss.sort(dk, p, eps, seed, payload=dp, oversample=cfg["oversample"])
+    torch.cuda.synchronize()
+    _compare(res, rec, arr, f"{dist}_", N)
+    del res, dp
+    res = hss.sort(dk, p, eps, seed, oversample=cfg["oversample"])  # keys alone, as bench.py times it
+    torch.cuda.synchronize()
+    _compare(res, rec, arr, f"{dist}_", N, payload_sha=False)
+
+
+@pytest.mark.timeout(1500)
+def test_plummer_morton_vs_oracle_record(hss):
     """2^30 Morton keys of a Plummer sphere with the particle index as
     payload, p = 16384, eps = 0.01 (the N-body workload)."""
-    N = 1 << 30
-    keys, payload = inputs.plummer_morton(N, 7)
-    assert np.array_equal(payload[:1000], np.arange(1000, dtype=np.uint32))
-    del payload
-    _check_fullsize(hss, keys, 16384, 0.01, 7)
+    rec_all, arr = _load("morton")
+    cfg = rec_all["config"]
+    rec = rec_all["cases"]["plummer"]
+    N = 1 << cfg["log2n"]
+    keys, payload = inputs.plummer_morton(N, cfg["seed"])
+    assert _sha(keys) == rec["input_sha256"], "the input generator drew different keys on this machine"
+    dk = torch.from_numpy(keys.view(np.int64)).cuda()
+    dp = torch.from_numpy(payload.view(np.int32)).cuda()
+    del keys, payload
+    res = hss.sort(dk, cfg["p"], cfg["eps"], cfg["seed"], payload=dp, oversample=cfg["oversample"])
+    torch.cuda.synchronize()
+    _compare(res, rec, arr, "", N)
+
+
+@pytest.mark.timeout(1800)
+def test_batch_workload_vs_oracle_record(hss):
+    """4096 int64 jobs of 2^10..2^22 keys in one hss_sort_batch call: every
+    job's rounds, sample sizes, |gamma|, offsets, splitters and sorted keys
+    against the oracle run of that job alone (seed 1 + j)."""
+    rec_all, _ = _load("batch")
+    cfg, jobs_rec = rec_all["config"], rec_all["jobs"]
+    jobs, kinds = inputs.batch_jobs(cfg["njobs"], cfg["plan_seed"], lo_log2=cfg["lo_log2"], hi_log2=cfg["hi_log2"],
+                                    zipf_s=cfg["zipf_s"], zipf_distinct=cfg["zipf_distinct"])
+    sizes = [len(x) for x in jobs]
+    ps = [r["p"] for r in jobs_rec]
+    assert sizes == [r["n"] for r in jobs_rec]
+    for j in (0, 1, len(jobs) // 2, len(jobs) - 1):
+        assert _sha(jobs[j].view(np.uint64), 16) == jobs_rec[j]["input_sha256"]
+    keys = torch.from_numpy(np.concatenate(jobs)).cuda()
+    del jobs
+    res = hss.sort_batch(keys, sizes, ps, cfg["eps"], cfg["seed"], oversample=cfg["oversample"], key_type="i64")
+    torch.cuda.synchronize()
+    out = res.keys.cpu().numpy().view(np.uint64)
+    offs_all = res.offsets.cpu().numpy().astype(np.uint64)
+    spl_all = res.splitters.cpu().numpy()
+    ko = oo = so = 0
+    bad = []
+    for j, r in enumerate(jobs_rec):
+        n, p = r["n"], r["p"]
+        got = {
+            "status": res.job_status[j], "rounds": res.job_rounds[j], "tol": res.job_tol[j],
+            "sample_size": res.job_sample_size[j], "gamma": res.job_gamma[j], "unresolved": res.job_unresolved[j],
+            "offsets_sha256": _sha(offs_all[oo:oo + p + 1], 16),
+            "out_keys_sha256": _sha(out[ko:ko + n], 16),
+        }
+        if p > 1:
+            cuts = spl_all[so:so + p - 1]
+            k = cuts[:, 0].view(np.uint64)
+            packed = cuts[:, 1].view(np.uint64)
+            seg = (packed & np.uint64(0xFFFFFFFF)).astype(np.uint32).view(np.int32).astype(np.int64)
+            spos = (packed >> np.uint64(32)).astype(np.uint64)
+            got["splitters_sha256"] = _sha(np.concatenate([k, seg.view(np.uint64), spos]), 16)
+        else:
+            got["splitters_sha256"] = r["splitters_sha256"]
+        for key, v in got.items():
+            if v != r[key]:
+                bad.append((j, key, v, r[key]))
+        ko += n
+        oo += p + 1
+        so += p - 1
+    assert not bad, f"{len(bad)} job fields differ, first: {bad[:4]}"
 
 
 def test_exact_splitting(hss):
     """eps = p/N makes the half-width floor(1/2) = 0: exact splitting (the
-    eps = p/N case after Theorem 4.8): every bucket holds N/p keys."""
+    eps = p/N case after Theorem 4.8): every bucket holds N/p keys, and the
+    rounds, samples and offsets equal the oracle's."""
     N, p = 1 << 22, 256
     keys = inputs.uniform(N, 21)
-    res = _check_fullsize(hss, keys, p, p / N, 21)
-    assert res.tol == 0
+    dk = torch.from_numpy(keys.view(np.int64)).cuda()
+    res = hss.sort(dk, p, p / N, 21)
+    torch.cuda.synchronize()
+    assert res.tol == 0 and res.status == 0
     off = res.offsets.cpu().numpy().astype(np.int64)
     assert np.all(np.diff(off) == N // p)
-    ref = oracle.hss(keys[: 1 << 16], 64, 64 / (1 << 16), 21, sort=False)
-    small = hss.sort(torch.from_numpy(keys[: 1 << 16].view(np.int64)).cuda(), 64, 64 / (1 << 16), 21)
-    assert small.rounds == ref.rounds and small.sample_size == [int(x) for x in ref.sample_size]
-    assert np.array_equal(small.offsets.cpu().numpy().astype(np.uint64), ref.offsets)
+    ref = oracle.hss(keys, p, p / N, 21)
+    assert res.rounds == ref.rounds and res.sample_size == [int(x) for x in ref.sample_size]
+    assert np.array_equal(off.astype(np.uint64), ref.offsets)
+    assert np.array_equal(res.keys.cpu().numpy().view(np.uint64), ref.out_keys)

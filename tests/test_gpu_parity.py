@@ -82,6 +82,27 @@ def test_local_sort_matches_oracle(hss, N, p, gen):
     assert np.array_equal(outp.cpu().numpy().view(np.uint32), wantp)
 
 
+@pytest.mark.parametrize("N,p", [(1 << 20, 4), (1 << 20, 1), (1 << 21, 1), (300001, 1), (5 << 17, 5), (70001, 3)])
+@pytest.mark.parametrize("gen", list(GENS))
+def test_local_sort_keys_only_matches_oracle(hss, N, p, gen):
+    """Keys alone take their own kernels (the split hands out slots inside a
+    digit with one atomic per key; on-chip sub-buckets are sorted in
+    registers): sub-buckets of about 1K, 4K and 8K keys reach all three
+    on-chip classes, and skewed inputs reach the fallbacks."""
+    keys = GENS[gen](N, 17)
+    out = hss.local_sort(dev(keys), p)
+    assert np.array_equal(host_u64(out), oracle.segment_sort(keys, p))
+
+
+@pytest.mark.parametrize("N,p,nvals,share,adjacent", [
+    (1 << 20, 2, 3, 0.85, False), (1 << 20, 1, 100, 0.99, False), (600000, 3, 4, 0.5, True),
+    (1 << 19, 1, 40, 0.95, False)])
+def test_local_sort_keys_only_duplicate_groups(hss, N, p, nvals, share, adjacent):
+    keys = inputs.duplicate_groups(N, 19, nvals, share, adjacent)
+    out = hss.local_sort(dev(keys), p)
+    assert np.array_equal(host_u64(out), oracle.segment_sort(keys, p))
+
+
 @pytest.mark.parametrize("N,p", [(1 << 18, 1), (300001, 2)])
 def test_local_sort_deep_recursion_payload(hss, N, p):
     """Three levels of digit splits: the second level's small buckets are
@@ -253,6 +274,18 @@ def test_sort_distributions(hss, gen):
     _cmp_partition(res, ref)
     assert np.array_equal(host_u64(res.keys), ref.out_keys)
     assert np.array_equal(res.payload.cpu().numpy().view(np.uint32), ref.out_payload)
+
+
+@pytest.mark.parametrize("gen", list(GENS))
+def test_sort_keys_only_distributions(hss, gen):
+    """The whole path with keys alone (the bench's call) at a size where both
+    the local sort and the merge split every segment before the on-chip sorts."""
+    N, p, eps, seed = 1 << 21, 8, 0.02, 7
+    keys = GENS[gen](N, seed)
+    res = hss.sort(dev(keys), p, eps, seed)
+    ref = oracle.hss(keys, p, eps, seed)
+    _cmp_partition(res, ref)
+    assert np.array_equal(host_u64(res.keys), ref.out_keys)
 
 
 def test_sort_signed(hss):
