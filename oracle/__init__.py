@@ -1,7 +1,9 @@
 """CPU oracle for Histogram Sort with Sampling (Harsh, Kale, Solomonik, SPAA'19).
 
 TEST INFRASTRUCTURE ONLY.  A plain single-threaded C restatement of the method
-(hss_oracle.c) behind a small numpy wrapper.  Only the test suite, the smoke
+(hss_oracle.c) behind a small numpy wrapper.  Beside it, cpu_baselines.cpp
+holds the benchmark's timed CPU references (HSS on all cores with OpenMP, and
+std::sort); they are checked against the oracle, never the other way round.  Only the test suite, the smoke
 check and the benchmark's CPU-baseline leg may import this package; the
 product library never links or calls it, and the two share no code.
 
@@ -31,6 +33,75 @@ _lock = threading.Lock()
 _lib = None
 
 MAX_ROUNDS = 64
+
+
+_BASE_SRC = os.path.join(_HERE, "cpu_baselines.cpp")
+_BASE_PATH = os.path.join(_OUT_DIR, "libcpu_baselines.so")
+_base = None
+
+
+def build_baselines(force: bool = False) -> str:
+    """Compile the timed CPU baselines (OpenMP HSS, std::sort) with g++."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_BASE_PATH)
+            and os.path.getmtime(_BASE_PATH) >= os.path.getmtime(_BASE_SRC)):
+        return _BASE_PATH
+    tmp = _BASE_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["g++", "-std=c++17", "-O3", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+                           "-o", tmp, _BASE_SRC])
+    os.replace(tmp, _BASE_PATH)
+    return _BASE_PATH
+
+
+def _load_baselines():
+    global _base
+    with _lock:
+        if _base is None:
+            lib = ctypes.CDLL(build_baselines())
+            P = ctypes.c_void_p
+            lib.cpu_baseline_threads.restype = ctypes.c_int
+            lib.cpu_std_sort.argtypes = [P, ctypes.c_uint64]
+            lib.cpu_std_sort.restype = None
+            lib.cpu_hss_omp.argtypes = [P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double, ctypes.c_uint64,
+                                        ctypes.c_float, ctypes.c_uint32, P, P, P, P, P, P, P]
+            lib.cpu_hss_omp.restype = ctypes.c_int
+            _base = lib
+    return _base
+
+
+def baseline_threads() -> int:
+    """Threads the OpenMP baseline uses (OMP_NUM_THREADS or all host cores)."""
+    return int(_load_baselines().cpu_baseline_threads())
+
+
+def std_sort(keys) -> np.ndarray:
+    """std::sort of u64 keys on one core (a timed reference, not the oracle)."""
+    out = np.array(keys, dtype=np.uint64, copy=True)
+    _load_baselines().cpu_std_sort(_ptr(out), out.shape[0])
+    return out
+
+
+def hss_omp(keys, p: int, eps: float, seed: int, oversample: float = 5.0, max_rounds: int = 64, sort: bool = True):
+    """HSS on all host cores (OpenMP), u64 keys alone: the same steps and
+    readings as ``hss``, run in parallel (a timed baseline, not the oracle).
+    Returns (splitter_key, splitter_seg, splitter_spos, offsets, out_keys,
+    rounds, sample_size, status)."""
+    lib = _load_baselines()
+    k = np.ascontiguousarray(keys, dtype=np.uint64)
+    N, S = k.shape[0], max(p - 1, 0)
+    sk = np.zeros(max(S, 1), dtype=np.uint64)
+    ss = np.zeros(max(S, 1), dtype=np.int32)
+    sp = np.zeros(max(S, 1), dtype=np.uint32)
+    off = np.zeros(p + 1, dtype=np.uint64)
+    out = np.empty(max(N, 1), dtype=np.uint64) if sort else None
+    rounds = ctypes.c_uint32(0)
+    z = np.zeros(64, dtype=np.uint64)
+    rc = lib.cpu_hss_omp(_ptr(k), N, p, float(eps), int(seed) & ((1 << 64) - 1), float(oversample), max_rounds,
+                         _ptr(sk), _ptr(ss), _ptr(sp), _ptr(off), _ptr(out), ctypes.byref(rounds), _ptr(z))
+    if rc == -1:
+        raise ValueError("cpu_hss_omp: invalid arguments")
+    R = int(rounds.value)
+    return sk[:S], ss[:S], sp[:S], off, (out[:N] if sort else None), R, z[:R], rc
 
 
 def build(force: bool = False) -> str:

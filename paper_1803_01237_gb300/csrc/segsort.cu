@@ -109,6 +109,21 @@ __device__ __forceinline__ uint32_t split_digit(uint64_t key, int shift, uint64_
     return (uint32_t)((key >> shift) - base) & 255u;
 }
 
+// Multiplier m of an interpolating digit mulhi(x - lo, m) of a key range of
+// width `range` onto 0..R-1: about (R-1) 2^64 / range, in single precision.
+// Any m keeps the digit monotone in the key (callers clamp it to R-1); this
+// one spreads the range evenly.  (Double precision is far slower here and
+// buys nothing.)
+__device__ __forceinline__ uint64_t interp_mult(uint64_t range, uint32_t R) {
+    if (range < (uint64_t)R) return 0ull;
+    return __float2ull_rz((float)(R - 1) * 18446744073709551616.0f / (float)range);
+}
+// The same for 32-bit offsets: mulhi(x - lo, m) onto 0..R-1.
+__device__ __forceinline__ uint32_t interp_mult32(uint32_t range, uint32_t R) {
+    if (range < R) return 0u;
+    return __float2uint_rz((float)(R - 1) * 4294967296.0f / (float)range);
+}
+
 // ---------------------------------------------------------------------------
 // Exclusive scan of 256 shared values by a CTA of T threads (T >= 64).
 // ---------------------------------------------------------------------------
@@ -391,7 +406,7 @@ __global__ __launch_bounds__(THREADS) void k_small_msd(
         // the stable sort.  Any monotone digit gives the same result, so the
         // multiplier only needs to be about 1023 * 2^64 / range.
         const uint64_t range = kmax - kmin;
-        const uint64_t mult = range < (uint64_t)R ? 0ull : (uint64_t)((double)(R - 1) * 18446744073709551616.0 / (double)range);
+        const uint64_t mult = interp_mult(range, (uint32_t)R);
         for (uint32_t e = tid; e < n; e += THREADS) {
             const uint64_t off = s_keys[e] - kmin;
             const uint32_t d = mult ? min((uint32_t)__umul64hi(off, mult), (uint32_t)R - 1) : (uint32_t)off;
@@ -484,7 +499,7 @@ __global__ __launch_bounds__(THREADS) void k_small_msd(
                 __syncthreads();
                 for (int i = 0; i < WARPS; ++i) { gmin = min(gmin, s_red[i]); gmax = max(gmax, s_red[32 + i]); }
                 const uint64_t r2 = gmax - gmin;
-                const uint64_t m2 = r2 < (uint64_t)R ? 0ull : (uint64_t)((double)(R - 1) * 18446744073709551616.0 / (double)r2);
+                const uint64_t m2 = interp_mult(r2, (uint32_t)R);
                 auto dig2 = [&](uint64_t kq) -> uint32_t {
                     const uint64_t off = kq - gmin;
                     return m2 ? min((uint32_t)__umul64hi(off, m2), (uint32_t)R - 1) : (uint32_t)off;
@@ -671,7 +686,7 @@ __global__ __launch_bounds__(THREADS) void k_small_reg(
             continue;
         }
         const uint64_t range = kmax - kmin;
-        const uint64_t mult = range < (uint64_t)kChipRadix ? 0ull : (uint64_t)(1.8871019187404871e22 / (double)range);
+        const uint64_t mult = interp_mult(range, (uint32_t)kChipRadix);
         uint32_t dp[ITEMS];  // digit in bits 0..11, group slot from bit 12
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
@@ -805,48 +820,79 @@ __global__ __launch_bounds__(THREADS) void k_small_keys(
         const uint64_t n64 = seg_hi[s] - base;
         if (n64 <= min_n || n64 > max_n) continue;  // uniform per CTA
         const uint32_t n = (uint32_t)n64;
+        const uint64_t* src = kin + base;
+        // Items past the segment are skipped by a uniform break (n is the
+        // same for the whole CTA), so a short segment costs no predicated work.
         uint64_t key[ITEMS];
-        uint64_t kmin = ~0ull, kmax = 0;
+        uint32_t hmin = ~0u, hmax = 0u;
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
+            if ((uint32_t)(i * THREADS) >= n) break;
             const uint32_t e = tid + i * THREADS;
-            key[i] = e < n ? kin[base + e] ^ flip_in : 0ull;
-            if (e < n) { kmin = min(kmin, key[i]); kmax = max(kmax, key[i]); }
+            key[i] = e < n ? src[e] ^ flip_in : 0ull;
+            const uint32_t h = (uint32_t)(key[i] >> 32);
+            if (e < n) { hmin = min(hmin, h); hmax = max(hmax, h); }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            kmin = min(kmin, (uint64_t)__shfl_xor_sync(0xffffffffu, kmin, o));
-            kmax = max(kmax, (uint64_t)__shfl_xor_sync(0xffffffffu, kmax, o));
-        }
-        if (lane == 0) { s_red[w] = kmin; s_red[32 + w] = kmax; }
+        hmin = __reduce_min_sync(0xffffffffu, hmin);
+        hmax = __reduce_max_sync(0xffffffffu, hmax);
+        if (lane == 0) { s_warp[w] = hmin; s_warp[WARPS + w] = hmax; }
         for (int d = tid; d < R; d += THREADS) s_start[d] = 0;
         if (tid == 0) s_flag[0] = 0;
         __syncthreads();
-        {
-            uint64_t a = ~0ull, b = 0;
-            for (int i = 0; i < WARPS; ++i) { a = min(a, s_red[i]); b = max(b, s_red[32 + i]); }
-            kmin = a;
-            kmax = b;
-        }
-        if (kmin == kmax) {  // all keys equal
+        hmin = ~0u; hmax = 0u;
+#pragma unroll
+        for (int i = 0; i < WARPS; ++i) { hmin = min(hmin, s_warp[i]); hmax = max(hmax, s_warp[WARPS + i]); }
+        // Digit: the high 32 key bits interpolated onto R groups when they
+        // spread over at least 8 R values (the common case, 32-bit work);
+        // else the whole 64-bit key range.  Either is monotone in the key.
+        const bool hi_mode = hmax - hmin >= 8u * (uint32_t)R;
+        uint64_t kmin = 0, mult64 = 0;
+        uint32_t mult32 = 0;
+        if (hi_mode) {
+            mult32 = interp_mult32(hmax - hmin, (uint32_t)R);
+        } else {
+            uint64_t lo = ~0ull, hi = 0ull;
 #pragma unroll
             for (int i = 0; i < ITEMS; ++i) {
-                const uint32_t e = tid + i * THREADS;
-                if (e < n) kout[base + e] = key[i] ^ flip_out;
+                if ((uint32_t)(i * THREADS) >= n) break;
+                if (tid + i * THREADS < n) { lo = min(lo, key[i]); hi = max(hi, key[i]); }
             }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                lo = min(lo, (uint64_t)__shfl_xor_sync(0xffffffffu, lo, o));
+                hi = max(hi, (uint64_t)__shfl_xor_sync(0xffffffffu, hi, o));
+            }
+            __syncthreads();  // s_warp reads above are done
+            if (lane == 0) { s_red[w] = lo; s_red[32 + w] = hi; }
             __syncthreads();
-            continue;
+            lo = ~0ull; hi = 0ull;
+            for (int i = 0; i < WARPS; ++i) { lo = min(lo, s_red[i]); hi = max(hi, s_red[32 + i]); }
+            if (lo == hi) {  // all keys equal
+#pragma unroll
+                for (int i = 0; i < ITEMS; ++i) {
+                    if ((uint32_t)(i * THREADS) >= n) break;
+                    const uint32_t e = tid + i * THREADS;
+                    if (e < n) kout[base + e] = key[i] ^ flip_out;
+                }
+                __syncthreads();
+                continue;
+            }
+            kmin = lo;
+            mult64 = interp_mult(hi - lo, (uint32_t)R);
         }
-        const uint64_t range = kmax - kmin;
-        const uint64_t mult = range < (uint64_t)R ? 0ull : (uint64_t)((double)(R - 1) * 18446744073709551616.0 / (double)range);
         uint32_t dp[ITEMS];
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
+            if ((uint32_t)(i * THREADS) >= n) break;
             const uint32_t e = tid + i * THREADS;
-            dp[i] = 0;
             if (e < n) {
-                const uint64_t off = key[i] - kmin;
-                const uint32_t d = mult ? min((uint32_t)__umul64hi(off, mult), (uint32_t)R - 1) : (uint32_t)off;
+                uint32_t d;
+                if (hi_mode) {
+                    d = min(__umulhi((uint32_t)(key[i] >> 32) - hmin, mult32), (uint32_t)R - 1);
+                } else {
+                    const uint64_t off = key[i] - kmin;
+                    d = mult64 ? min((uint32_t)__umul64hi(off, mult64), (uint32_t)R - 1) : (uint32_t)off;
+                }
                 dp[i] = d | (atomicAdd(&s_start[d], 1u) << 13);
             }
         }
@@ -859,10 +905,12 @@ __global__ __launch_bounds__(THREADS) void k_small_keys(
         if (tid == 0) s_start[R] = n;
         __syncthreads();
         mx = 0;
+#pragma unroll
         for (int i = 0; i < WARPS; ++i) mx = max(mx, s_warp[i]);
         // scatter into group order; dp keeps the digit and now the group slot
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
+            if ((uint32_t)(i * THREADS) >= n) break;
             const uint32_t e = tid + i * THREADS;
             if (e < n) {
                 const uint32_t d = dp[i] & kDigitMask;
@@ -873,8 +921,10 @@ __global__ __launch_bounds__(THREADS) void k_small_keys(
         }
         __syncthreads();
         if (mx > 1u) {
+            bool moved = false;
 #pragma unroll
             for (int i = 0; i < ITEMS; ++i) {
+                if ((uint32_t)(i * THREADS) >= n) break;
                 const uint32_t e = tid + i * THREADS;
                 if (e >= n) continue;
                 const uint32_t d = dp[i] & kDigitMask, pos = dp[i] >> 13;
@@ -889,7 +939,7 @@ __global__ __launch_bounds__(THREADS) void k_small_keys(
                     const uint64_t ky = s_key[q];
                     r += (ky < key[i] || (ky == key[i] && q < pos)) ? 1u : 0u;
                 }
-                dp[i] = d | ((a + r) << 13);
+                if (a + r != pos) { dp[i] = d | ((a + r) << 13); moved = true; }
             }
             __syncthreads();
             if (s_flag[0]) {  // uniform: a large group of distinct keys
@@ -897,14 +947,17 @@ __global__ __launch_bounds__(THREADS) void k_small_keys(
                 __syncthreads();
                 continue;
             }
+            if (moved) {
 #pragma unroll
-            for (int i = 0; i < ITEMS; ++i) {
-                const uint32_t e = tid + i * THREADS;
-                if (e < n) s_key[dp[i] >> 13] = key[i];
+                for (int i = 0; i < ITEMS; ++i) {
+                    if ((uint32_t)(i * THREADS) >= n) break;
+                    if (tid + i * THREADS < n) s_key[dp[i] >> 13] = key[i];
+                }
             }
             __syncthreads();
         }
-        for (uint32_t j = tid; j < n; j += THREADS) kout[base + j] = s_key[j] ^ flip_out;
+        uint64_t* dst = kout + base;
+        for (uint32_t j = tid; j < n; j += THREADS) dst[j] = s_key[j] ^ flip_out;
         __syncthreads();
     }
 }
@@ -1381,51 +1434,58 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
             if (PAY) pay[i] = 0;
         }
     }
-    // Each key's digit once, byte-packed in four registers.
-    uint32_t dpk[kOsItems / 4];
-#pragma unroll
-    for (int i = 0; i < kOsItems / 4; ++i) dpk[i] = 0;
-#pragma unroll
-    for (int i = 0; i < kOsItems; ++i)
-        dpk[i >> 2] |= split_digit(key[i], shift, dbase, dmult) << (8 * (i & 3));
-    auto digit_of = [&](int i) -> uint32_t {
-        return (wbase + i * 32 < count) ? (dpk[i >> 2] >> (8 * (i & 3))) & 255u : (uint32_t)kRadix;
-    };
+    uint32_t* cur = A.status;
     // Publish this tile's digit counts as soon as they are known, so the next
     // tile's look-back does not wait for our ranking.
-    uint32_t* cur = A.status;
     auto publish = [&]() {
         if (tid < kRadix) st_relaxed(&cur[(uint64_t)t * kRadix + tid], (ti == 0 ? kFlagPre : kFlagAgg) | s_total[tid]);
     };
     if constexpr (PAY) {
+        // Each key's digit once, byte-packed in four registers.
+        uint32_t dpk[kOsItems / 4];
+#pragma unroll
+        for (int i = 0; i < kOsItems / 4; ++i) dpk[i] = 0;
+#pragma unroll
+        for (int i = 0; i < kOsItems; ++i)
+            dpk[i >> 2] |= split_digit(key[i], shift, dbase, dmult) << (8 * (i & 3));
+        auto digit_of = [&](int i) -> uint32_t {
+            return (wbase + i * 32 < count) ? (dpk[i >> 2] >> (8 * (i & 3))) & 255u : (uint32_t)kRadix;
+        };
         block_rank<kOsWarps, kOsItems>(digit_of, count, rank, s_hist, s_total, s_start, s_warp, publish);
+#pragma unroll
+        for (int i = 0; i < kOsItems; ++i) {
+            if (wbase + i * 32 < count) {
+                s_keys[rank[i]] = key[i];
+                s_dg[rank[i]] = (uint8_t)((dpk[i >> 2] >> (8 * (i & 3))) & 255u);
+                s_pay[rank[i]] = pay[i];
+            }
+        }
     } else {
         // Keys alone: equal keys are indistinguishable, so the order of a
         // digit's keys inside the tile is free and one shared counter per
         // digit hands out the slots (one atomic per key instead of the
-        // ballot ranking the payload path needs for stability).
+        // ballot ranking the payload path needs for stability).  rank[i]
+        // holds the digit and, from bit 8, the key's slot.
         for (int d = tid; d < kRadix; d += kOsThreads) s_total[d] = 0;
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < kOsItems; ++i) {
-            const uint32_t d = digit_of(i);
-            rank[i] = d < kRadix ? atomicAdd(&s_total[d], 1u) : 0u;
+            if (wbase + i * 32 < count) {
+                const uint32_t d = split_digit(key[i], shift, dbase, dmult);
+                rank[i] = d | (atomicAdd(&s_total[d], 1u) << 8);
+            }
         }
         __syncthreads();
         scan256_smem<kOsThreads>(s_total, s_start, s_warp);
         publish();
 #pragma unroll
         for (int i = 0; i < kOsItems; ++i) {
-            const uint32_t d = digit_of(i);
-            if (d < kRadix) rank[i] += s_start[d];
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < kOsItems; ++i) {
-        if (wbase + i * 32 < count) {
-            s_keys[rank[i]] = key[i];
-            s_dg[rank[i]] = (uint8_t)((dpk[i >> 2] >> (8 * (i & 3))) & 255u);
-            if (PAY) s_pay[rank[i]] = pay[i];
+            if (wbase + i * 32 < count) {
+                const uint32_t d = rank[i] & 255u;
+                const uint32_t pos = s_start[d] + (rank[i] >> 8);
+                s_keys[pos] = key[i];
+                s_dg[pos] = (uint8_t)d;
+            }
         }
     }
 
