@@ -11,10 +11,14 @@
  *     never allocates device memory: scratch comes from the caller's
  *     workspace (d_work, work_bytes), sized with hss_workspace_bytes().
  *   - Work is enqueued on `stream` (a cudaStream_t passed as void*, NULL =
- *     the legacy default stream).  hss_partition and hss_sort block the
- *     calling thread while the splitter rounds run (one small device-to-host
- *     read per round decides the next launch); everything else they enqueue
- *     completes asynchronously unless HSS_FLAG_SYNC or HSS_FLAG_TIMING is set.
+ *     the legacy default stream).  The splitter rounds run on the device (a
+ *     CUDA graph loop, see HSS_FLAG_HOST_ROUNDS), so hss_partition returns
+ *     without waiting for the GPU unless statistics are asked for (h_stats
+ *     non-NULL) or HSS_FLAG_SYNC / HSS_FLAG_TIMING is set; hss_call_stats
+ *     reads them later.  hss_sort waits where its merge plans a level of its
+ *     radix recursion (one small read per level).  Rounds driven from the
+ *     host (large samples, the k-round schedule, HSS_FLAG_HOST_ROUNDS) read
+ *     one small record per round.
  *   - Keys are 64-bit, unsigned (HSS_KEY_U64) or signed (HSS_KEY_I64).  An
  *     optional 32-bit payload travels with its key.
  *   - Ties between equal keys are broken by (processor, position), which is
@@ -68,6 +72,15 @@ extern "C" {
  * one may be set, else HSS_ERR_INVALID). */
 #define HSS_FLAG_HIST_PROBE 4u
 #define HSS_FLAG_HIST_STAGED 8u
+/* Drive the splitter rounds from the host (one small device-to-host read per
+ * round decides the next launch) instead of the device-driven loop.  Without
+ * this flag a call whose round sample fits one on-chip sort (sample capacity
+ * min(N, ceil(2 s p) + 4096) <= 14336) and whose schedule is not the k-round
+ * one runs its rounds as one CUDA graph: a WHILE conditional node whose body
+ * is one round (sample, sort, histogram, L/U update, intervals, next sample)
+ * and whose condition a device kernel sets after each round (all resolved,
+ * round limit, sample capacity).  The results are identical either way. */
+#define HSS_FLAG_HOST_ROUNDS 16u
 
 /* Workspace queries (op argument of hss_workspace_bytes). */
 #define HSS_OP_SORT 0
@@ -220,6 +233,16 @@ int hss_sort_with_proposal(const void* d_keys, const uint32_t* d_payload, int ke
 int hss_sort_host(const void* h_keys, const uint32_t* h_payload, int key_type, uint64_t N, const hss_params* prm,
                   void* h_keys_out, uint32_t* h_payload_out, hss_cut* h_splitters, uint64_t* h_offsets,
                   void* d_work, size_t work_bytes, hss_stats* h_stats, void* stream);
+
+/* Statistics and status of the last hss_partition / hss_sort (or their
+ * _with_proposal forms; op = HSS_OP_PARTITION or HSS_OP_SORT) made on the
+ * workspace d_work with these arguments: a call that returned without waiting
+ * for the GPU leaves its round statistics and device-side status in the
+ * workspace until the next call on it.  Synchronises `stream`; the return
+ * value is that call's status (HSS_OK, HSS_ERR_ROUND_LIMIT, HSS_ERR_CAPACITY,
+ * HSS_ERR_TIMEOUT, ...).  h_stats's device times are not filled. */
+int hss_call_stats(int op, uint64_t N, const hss_params* prm, int key_type, int has_payload, const void* d_work,
+                   size_t work_bytes, hss_stats* h_stats, void* stream);
 
 /* The 64-bit Bernoulli words of the sampling phase (Sec. 4.2.1): for
  * positions spos0 .. spos0+count-1 of sorted segment `seg` in round `round`,

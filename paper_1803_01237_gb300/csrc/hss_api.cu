@@ -19,7 +19,16 @@
 namespace hss {
 
 static std::atomic<uint64_t> g_launches{0};
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local int t_capture_depth = 0;
+static thread_local uint64_t t_captured = 0;
+void note_launch() {
+    if (t_capture_depth > 0) ++t_captured;
+    else g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+void add_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+LaunchCountPause::LaunchCountPause() { ++t_capture_depth; }
+LaunchCountPause::~LaunchCountPause() { --t_capture_depth; }
+uint64_t LaunchCountPause::captured() const { return t_captured; }
 
 // Per-device bookkeeping of kernel attributes and SM counts: a kernel's
 // shared-memory limit set on one device does not carry over to another, and
@@ -244,11 +253,12 @@ static int run_path(const void* d_keys, const uint32_t* d_payload, int key_type,
 
     // Splitter rounds (Sec. 4.2.2).
     RoundResult rr;
+    bool device_loop = false;
     int status = run_rounds(keysA, seg_off, N, p, prm->eps, prm->seed, s, eff_rounds(prm), key_type, d_splitters,
                             d_offsets, rws, st, &rr, (const uint64_t*)d_prop, nprop, prm->schedule, prm->schedule_k,
-                            hist_mode(prm));
+                            hist_mode(prm), (prm->flags & HSS_FLAG_HOST_ROUNDS) == 0, &device_loop);
     tm.mark(HSS_PHASE_ROUNDS);
-    if (status == HSS_ERR_CUDA) return status;
+    if (status == HSS_ERR_CUDA || status == HSS_ERR_INVALID) return status;
 
     if (sort) {
         if (single) {
@@ -272,9 +282,16 @@ static int run_path(const void* d_keys, const uint32_t* d_payload, int key_type,
     }
     tm.finish(h_stats, sort ? HSS_PHASE_MERGE : HSS_PHASE_ROUNDS);
 
-    const bool sync = (prm->flags & (HSS_FLAG_SYNC | HSS_FLAG_TIMING)) != 0;
-    if (sync || status == HSS_OK) {
-        // the rounds already synchronised once per round; this read is cheap
+    // With the device-driven rounds nothing above waited for the GPU (a
+    // partition returns at once; a sort waits only where the merge plans its
+    // levels): the statistics and the device status are read here when asked
+    // for, else later through hss_call_stats.
+    const bool sync = (prm->flags & (HSS_FLAG_SYNC | HSS_FLAG_TIMING)) != 0 || h_stats != nullptr;
+    if (device_loop && sync) {
+        status = read_round_result(rws, &rr, st);
+        add_launches(1 + (uint64_t)rr.rounds * device_round_kernels());
+    }
+    if (sync || (!device_loop && status == HSS_OK)) {
         const int e = read_dev_err(err, st);
         if (e != HSS_OK && status == HSS_OK) status = e;
     }
@@ -447,6 +464,33 @@ int hss_sort_host(const void* h_keys, const uint32_t* h_payload, int key_type, u
     if (cudaMemcpyAsync(h_offsets, off, (uint64_t)(p + 1) * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return HSS_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return HSS_ERR_CUDA;
     return rc;
+}
+
+int hss_call_stats(int op, uint64_t N, const hss_params* prm, int key_type, int has_payload, const void* d_work,
+                   size_t work_bytes, hss_stats* h_stats, void* stream) {
+    if (!params_ok(prm) || !d_work || !h_stats || (op != HSS_OP_SORT && op != HSS_OP_PARTITION)) return HSS_ERR_INVALID;
+    (void)key_type;
+    const uint32_t p = prm->p;
+    const Layout L = plan(op, N, p, eff_oversample(prm), op == HSS_OP_SORT && has_payload != 0);
+    if (work_bytes < L.total) return HSS_ERR_WORKSPACE;
+    std::memset(h_stats, 0, sizeof(*h_stats));
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t* err = at<uint32_t>((void*)d_work, L.err);
+    const uint64_t cap = sample_capacity(N, p, eff_oversample(prm));
+    RoundWs rws = rounds_ws_carve(at<void>((void*)d_work, L.rws), std::max<uint64_t>(N, 1), p, cap, err);
+    RoundResult rr;
+    int status = p > 1 ? read_round_result(rws, &rr, st) : HSS_OK;
+    const int e = read_dev_err(err, st);
+    if (e != HSS_OK && status == HSS_OK) status = e;
+    h_stats->rounds = rr.rounds;
+    h_stats->status = status;
+    h_stats->tol = (uint64_t)std::floor(((double)N * prm->eps) / (2.0 * (double)p));
+    for (uint32_t j = 0; j < rr.rounds && j < HSS_MAX_ROUNDS; ++j) {
+        h_stats->sample_size[j] = rr.sample_size[j];
+        h_stats->gamma[j] = rr.gamma[j];
+    }
+    for (uint32_t j = 0; j <= rr.rounds && j <= HSS_MAX_ROUNDS; ++j) h_stats->unresolved[j] = rr.unresolved[j];
+    return status;
 }
 
 int hss_sample_words(uint64_t seed, uint32_t seg, uint32_t round, uint32_t spos0, uint32_t count, uint64_t* d_out,

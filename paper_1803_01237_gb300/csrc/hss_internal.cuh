@@ -110,6 +110,15 @@ __device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
 // Launch accounting: every kernel launch of the library goes through this.
 void note_launch();
 uint32_t launches_since(uint64_t mark);
+// Kernels that ran inside a graph (counted when their number is known).
+void add_launches(uint64_t n);
+// While one is alive, launches on this thread are being captured into a
+// graph: they are counted apart (captured()), not as launches.
+struct LaunchCountPause {
+    LaunchCountPause();
+    ~LaunchCountPause();
+    uint64_t captured() const;
+};
 
 // Kernel attributes are per device: set the dynamic shared-memory limit (and,
 // when carveout >= 0, the preferred shared-memory carveout) of `func` once per

@@ -25,8 +25,14 @@
 
 #include <cmath>
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 namespace hss {
+
+// Probe count argument meaning "read it from the control record" (the
+// device-driven loop, where the host does not know a round's sample size).
+constexpr uint64_t kZFromCtl = ~0ull;
 
 static inline uint64_t cdiv(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 static inline size_t aup(size_t x) { return (x + 255) / 256 * 256; }
@@ -162,6 +168,10 @@ __global__ __launch_bounds__(kSampThreads) void k_sample_mark(
     __shared__ uint32_t s_warp[32];
     const uint32_t s = blockIdx.x;
     const uint64_t base = seg_off[s];
+    if (round == 0) {  // device-driven loop: the next round and the seed come from the control record
+        round = ctl->round + 1;
+        seed = ctl->seed;
+    }
     const uint32_t nint = ctl->nint;
     const uint64_t T = ctl->T;
     const bool take_all = ctl->take_all != 0;
@@ -276,6 +286,7 @@ __global__ void k_probe_build(uint64_t Z, const uint64_t* __restrict__ skey_sort
                               uint64_t* __restrict__ pkey, int32_t* __restrict__ pseg, uint32_t* __restrict__ pspos,
                               uint32_t* __restrict__ pint, uint64_t* __restrict__ prank) {
     const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (Z == kZFromCtl) Z = ctl->seg_off_z[1];
     if (k >= Z) return;
     const uint32_t j = sperm[k];
     DCut c;
@@ -296,9 +307,14 @@ __global__ __launch_bounds__(256) void k_histogram(
     const uint32_t* __restrict__ Lpos, const uint32_t* __restrict__ Upos, const uint32_t* __restrict__ int_rep,
     const uint64_t* __restrict__ pkey, const int32_t* __restrict__ pseg, const uint32_t* __restrict__ pspos,
     const uint32_t* __restrict__ pint, uint64_t Z, uint64_t* __restrict__ prank, uint32_t* __restrict__ probe_pos,
-    uint64_t cap, uint32_t* __restrict__ err) {
+    uint64_t cap, uint32_t* __restrict__ err, const RoundCtl* __restrict__ ctl) {
     __shared__ uint64_t s_part[8][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (Z == kZFromCtl) {  // device-driven loop: this form runs unless the round is staged
+        if (ctl->staged) return;
+        Z = ctl->seg_off_z[1];
+        if ((uint64_t)blockIdx.x * 32 >= Z) return;
+    }
     const uint64_t k = (uint64_t)blockIdx.x * 32 + lane;
     const bool valid = k < Z;
     uint64_t key = 0; int32_t seg = 0; uint32_t spos = 0, rep = 0;
@@ -355,10 +371,15 @@ __global__ __launch_bounds__(kStgThreads) void k_histogram_staged(
     const uint32_t* __restrict__ Lpos, const uint32_t* __restrict__ Upos, const uint32_t* __restrict__ int_rep,
     const uint64_t* __restrict__ pkey, const int32_t* __restrict__ pseg, const uint32_t* __restrict__ pspos,
     uint64_t Z, uint64_t* __restrict__ prank, uint32_t* __restrict__ probe_pos, uint64_t cap,
-    uint32_t* __restrict__ err) {
+    uint32_t* __restrict__ err, const RoundCtl* __restrict__ ctl) {
     __shared__ uint64_t s_keys[kStgCap];
     __shared__ uint32_t s_lo[kStgSegs], s_a[kStgSegs], s_b[kStgSegs], s_ok[kStgSegs];
+    if (Z == kZFromCtl) {  // device-driven loop: this form runs only when the round is staged
+        if (!ctl->staged) return;
+        Z = ctl->seg_off_z[1];
+    }
     const uint64_t k0 = (uint64_t)blockIdx.x * kStgProbes;
+    if (k0 >= Z) return;
     const uint64_t k1 = min(Z, k0 + (uint64_t)kStgProbes);
     const uint32_t s0 = blockIdx.y * kStgSegs;
     const uint32_t rep = int_rep[0];
@@ -461,9 +482,11 @@ __global__ void k_prop_probes(uint32_t nprop, const uint64_t* __restrict__ okey_
 // the best cut of a rank is the first of its run (the smallest tag).
 __global__ void k_update(uint32_t S, uint64_t N, uint32_t p, const uint64_t* __restrict__ pkey, const int32_t* __restrict__ pseg,
                          const uint32_t* __restrict__ pspos, const uint64_t* __restrict__ prank, uint64_t Z, int32_t pkind,
-                         DCut* __restrict__ Lcut, DCut* __restrict__ Ucut, int32_t* __restrict__ chgL, int32_t* __restrict__ chgU) {
+                         DCut* __restrict__ Lcut, DCut* __restrict__ Ucut, int32_t* __restrict__ chgL, int32_t* __restrict__ chgU,
+                         const RoundCtl* __restrict__ ctl) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= S) return;
+    if (Z == kZFromCtl) Z = ctl->seg_off_z[1];
     const uint64_t t = ideal_rank(i + 1, N, p);
     uint64_t lo = 0, hi = Z;  // first probe with rank > t
     while (lo < hi) { const uint64_t m = (lo + hi) >> 1; if (prank[m] <= t) lo = m + 1; else hi = m; }
@@ -604,6 +627,54 @@ __global__ void k_final_pos(uint32_t S, const uint32_t* __restrict__ choose_u, u
 }
 
 // ---------------------------------------------------------------------------
+// The device-driven round loop: the parameters a round reads from the control
+// record, and the decision taken before every round (the host loop's test:
+// all resolved, the round limit, the sample capacity), which also records the
+// round statistics and sets the WHILE condition of the loop's graph.
+// ---------------------------------------------------------------------------
+__global__ void k_ctl_init(RoundCtl* ctl, uint64_t seed, uint32_t max_rounds) {
+    ctl->seed = seed;
+    ctl->max_rounds = max_rounds;
+    ctl->round = 0;
+    ctl->status = HSS_OK;
+    ctl->staged = 0;
+}
+
+__global__ void k_ctl_record(RoundCtl* ctl, uint32_t rounds, int32_t status, uint64_t last_z) {
+    if (threadIdx.x == 0) {
+        ctl->round = rounds;
+        ctl->status = status;
+        (void)last_z;
+    }
+}
+
+__global__ void k_round_decide(RoundCtl* ctl, uint64_t cap, uint64_t N, uint32_t p, uint32_t hist_mode,
+                               cudaGraphConditionalHandle loop) {
+    const uint32_t j = ctl->round;  // rounds done
+    ctl->hist_unres[j] = ctl->unresolved;
+    uint32_t go = 0;
+    if (ctl->unresolved == 0) {
+    } else if (j >= ctl->max_rounds) {
+        ctl->status = HSS_ERR_ROUND_LIMIT;
+    } else {
+        const uint64_t Z = ctl->Z;
+        ctl->hist_Z[j] = Z;
+        ctl->hist_gamma[j] = ctl->gamma;
+        ctl->round = j + 1;
+        if (Z > cap) {
+            ctl->status = HSS_ERR_CAPACITY;
+        } else {
+            // the histogram form of this round, as the host loop chooses it
+            const double searches = (double)Z * (double)p * log2((double)N / (double)p + 2.0);
+            ctl->staged = (ctl->nint == 1 && hist_mode != kHistProbe &&
+                           (hist_mode == kHistStaged || searches >= 8.0 * (double)N)) ? 1u : 0u;
+            go = 1;
+        }
+    }
+    cudaGraphSetConditional(loop, go);
+}
+
+// ---------------------------------------------------------------------------
 // Host driver of the rounds.
 // ---------------------------------------------------------------------------
 #define HSS_TRY(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return HSS_ERR_CUDA; } while (0)
@@ -616,10 +687,168 @@ static void enqueue_sampling(const RoundWs& ws, const uint64_t* d_seg_off, uint6
     HSS_LAUNCH(k_count_scan, 1, 1024, 0, st, ws.seg_cnt, p, ws.seg_cnt_off, ws.cap, ws.ctl);
 }
 
+bool device_loop_possible(uint64_t cap, uint32_t schedule) {
+    // the probe sort of a round must run without host planning (one segment
+    // of at most the on-chip capacity), and the threshold must come from the
+    // device (the k-round schedule computes it on the host with libm)
+    return cap <= (uint64_t)kSmallCap && schedule != HSS_SCHEDULE_THEORY;
+}
+
+namespace {
+
+// One round of the device-driven loop, enqueued on `st` (captured into the
+// body of the loop's graph): write the sample, sort it, build and rank the
+// probes, update L/U and their positions, recompute the intervals, sample the
+// next round and decide whether it runs.  Every kernel reads the round's
+// sample size, seed and histogram form from the control record.
+cudaError_t enqueue_device_round(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uint32_t p, uint64_t tol,
+                                 float oversample, uint32_t schedule, uint32_t hist_mode, const RoundWs& ws,
+                                 cudaGraphConditionalHandle loop, cudaStream_t st) {
+    const uint32_t S = p - 1;
+    const unsigned sblk = (unsigned)cdiv(S, 256);
+    const uint64_t cap = ws.cap;
+    const bool per_interval = schedule == HSS_SCHEDULE_EQUAL;
+    HSS_LAUNCH(k_sample_write, p, kSampThreads, 0, st, skeys, d_seg_off, ws.bitmap, ws.seg_cnt, ws.seg_cnt_off, cap, ws.skey,
+               ws.sseg, ws.sspos, ws.siota);
+    cudaError_t e = segsort(ws.skey, ws.skey_sorted, ws.stmp, ws.siota, ws.sperm, ws.ptmp, cap, 1, ws.ctl->seg_off_z,
+                            false, false, ws.sws, st, nullptr);
+    if (e != cudaSuccess) return e;
+    HSS_LAUNCH(k_probe_build, (unsigned)cdiv(cap, 256), 256, 0, st, kZFromCtl, ws.skey_sorted, ws.sperm, ws.sseg,
+               ws.sspos, ws.Ucut, ws.int_rep, ws.ctl, ws.pkey, ws.pseg, ws.pspos, ws.pint, ws.prank);
+    HSS_LAUNCH(k_histogram_staged, dim3((unsigned)cdiv(cap, kStgProbes), (unsigned)cdiv(p, kStgSegs)), kStgThreads, 0, st,
+               skeys, d_seg_off, p, S, ws.Lpos, ws.Upos, ws.int_rep, ws.pkey, ws.pseg, ws.pspos, kZFromCtl, ws.prank,
+               ws.probe_pos, cap, ws.sws.err, ws.ctl);
+    HSS_LAUNCH(k_histogram, dim3((unsigned)cdiv(cap, 32), (unsigned)cdiv(p, kHistSegPerBlock)), 256, 0, st, skeys,
+               d_seg_off, p, S, ws.Lpos, ws.Upos, ws.int_rep, ws.pkey, ws.pseg, ws.pspos, ws.pint, kZFromCtl, ws.prank,
+               ws.probe_pos, cap, ws.sws.err, ws.ctl);
+    HSS_LAUNCH(k_update, sblk, 256, 0, st, S, N, p, ws.pkey, ws.pseg, ws.pspos, ws.prank, kZFromCtl, (int32_t)kMember,
+               ws.Lcut, ws.Ucut, ws.chgL, ws.chgU, ws.ctl);
+    HSS_LAUNCH(k_update_pos, dim3(p, sblk), 256, 0, st, S, ws.chgL, ws.chgU, ws.probe_pos, cap, ws.Lpos, ws.Upos);
+    HSS_LAUNCH(k_intervals, 1, 1024, 0, st, S, N, p, tol, oversample, ws.Lcut, ws.Ucut, ws.res, ws.int_rep, ws.ctl,
+               schedule, 0ull, 0u, ws.int_T, ws.int_all);
+    if ((e = cudaMemsetAsync(ws.bitmap, 0, (N / 32 + 2) * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    HSS_LAUNCH(k_sample_mark, p, kSampThreads, 0, st, d_seg_off, S, ws.Lpos, ws.Upos, ws.Lcut, ws.int_rep, ws.ctl, 0ull,
+               0u, ws.bitmap, ws.seg_cnt, per_interval ? ws.int_T : nullptr, per_interval ? ws.int_all : nullptr);
+    HSS_LAUNCH(k_count_scan, 1, 1024, 0, st, ws.seg_cnt, p, ws.seg_cnt_off, cap, ws.ctl);
+    HSS_LAUNCH(k_round_decide, 1, 1, 0, st, ws.ctl, cap, N, p, hist_mode, loop);
+    return cudaGetLastError();
+}
+
+// Executable graphs of the loop, keyed by what the captured kernels were
+// given (the workspace's round state, the sorted keys, the sizes and the
+// sampling form); the seed and the round limit travel in the control record.
+struct LoopKey {
+    int dev;
+    const void* ctl;
+    const uint64_t* skeys;
+    const uint64_t* seg_off;
+    uint64_t N, tol, cap;
+    uint32_t p, schedule, hist_mode;
+    float oversample;
+    bool operator==(const LoopKey& o) const {
+        return dev == o.dev && ctl == o.ctl && skeys == o.skeys && seg_off == o.seg_off && N == o.N && tol == o.tol &&
+               cap == o.cap && p == o.p && schedule == o.schedule && hist_mode == o.hist_mode &&
+               oversample == o.oversample;
+    }
+};
+struct LoopGraph {
+    LoopKey key;
+    cudaGraphExec_t exec;
+    uint64_t used;
+};
+std::mutex g_loop_mu;
+std::vector<LoopGraph> g_loops;
+uint64_t g_loop_clock = 0;
+constexpr size_t kMaxLoopGraphs = 32;
+cudaStream_t g_capture_stream[256] = {};
+uint32_t g_body_kernels = 0;  // kernels one round of the loop launches
+
+// Build (once per key) the graph: the decision kernel, then WHILE(cond) { round }.
+int loop_graph(const LoopKey& k, const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uint32_t p,
+               uint64_t tol, float oversample, uint32_t schedule, uint32_t hist_mode, const RoundWs& ws,
+               cudaGraphExec_t* out) {
+    std::lock_guard<std::mutex> lock(g_loop_mu);
+    for (auto& g : g_loops)
+        if (g.key == k) {
+            g.used = ++g_loop_clock;
+            *out = g.exec;
+            return HSS_OK;
+        }
+    if (k.dev < 0 || k.dev >= 256) return HSS_ERR_CUDA;
+    cudaStream_t& cs = g_capture_stream[k.dev];
+    if (!cs && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return HSS_ERR_CUDA;
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return HSS_ERR_CUDA;
+    auto fail = [&]() { cudaGraphDestroy(g); return HSS_ERR_CUDA; };
+    cudaGraphConditionalHandle loop;
+    if (cudaGraphConditionalHandleCreate(&loop, g, 0, cudaGraphCondAssignDefault) != cudaSuccess) return fail();
+    // the decision before round 1
+    LaunchCountPause pause;
+    if (cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+        return fail();
+    k_round_decide<<<1, 1, 0, cs>>>(ws.ctl, ws.cap, N, p, hist_mode, loop);
+    cudaGraph_t tmp = nullptr;
+    if (cudaStreamEndCapture(cs, &tmp) != cudaSuccess || tmp != g) return fail();
+    cudaGraphNode_t gate = nullptr;
+    size_t n = 1;
+    if (cudaGraphGetNodes(g, &gate, &n) != cudaSuccess || n != 1) return fail();
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = loop;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode = nullptr;
+    if (cudaGraphAddNode(&cnode, g, &gate, nullptr, 1, &cp) != cudaSuccess) return fail();
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+        return fail();
+    const uint64_t before = pause.captured();
+    const cudaError_t ce = enqueue_device_round(skeys, d_seg_off, N, p, tol, oversample, schedule, hist_mode, ws, loop, cs);
+    g_body_kernels = (uint32_t)(pause.captured() - before);
+    tmp = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(cs, &tmp);
+    if (ce != cudaSuccess || ee != cudaSuccess) return fail();
+    cudaGraphExec_t exec = nullptr;
+    if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) return fail();
+    cudaGraphDestroy(g);
+    if (g_loops.size() >= kMaxLoopGraphs) {  // evict the least recently used
+        size_t v = 0;
+        for (size_t i = 1; i < g_loops.size(); ++i)
+            if (g_loops[i].used < g_loops[v].used) v = i;
+        cudaGraphExecDestroy(g_loops[v].exec);
+        g_loops.erase(g_loops.begin() + v);
+    }
+    g_loops.push_back(LoopGraph{k, exec, ++g_loop_clock});
+    *out = exec;
+    return HSS_OK;
+}
+
+}  // namespace
+
+uint32_t device_round_kernels() { return g_body_kernels; }
+
+int read_round_result(const RoundWs& ws, RoundResult* out, cudaStream_t st) {
+    RoundCtl h;
+    if (cudaMemcpyAsync(&h, ws.ctl, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return HSS_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return HSS_ERR_CUDA;
+    out->rounds = h.round;
+    out->status = h.status;
+    for (uint32_t j = 0; j < h.round && j < HSS_MAX_ROUNDS; ++j) {
+        out->sample_size[j] = h.hist_Z[j];
+        out->gamma[j] = h.hist_gamma[j];
+    }
+    // unresolved after round j is recorded by the decision before round j+1
+    // (or by the last decision); a capacity stop leaves the last one unset
+    const uint32_t last = h.status == HSS_ERR_CAPACITY ? (h.round > 0 ? h.round - 1 : 0) : h.round;
+    for (uint32_t j = 0; j <= last && j <= HSS_MAX_ROUNDS; ++j) out->unresolved[j] = h.hist_unres[j];
+    return h.status;
+}
+
 int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uint32_t p, double eps, uint64_t seed,
                float oversample, uint32_t max_rounds, int key_type, hss_cut* d_splitters, uint64_t* d_offsets,
                const RoundWs& ws, cudaStream_t st, RoundResult* out, const uint64_t* d_prop, uint32_t nprop,
-               uint32_t schedule, uint32_t schedule_k, uint32_t hist_mode) {
+               uint32_t schedule, uint32_t schedule_k, uint32_t hist_mode, bool device_loop, bool* used_device_loop) {
+    if (used_device_loop) *used_device_loop = false;
     const uint32_t S = p - 1;
     const uint64_t tol = (uint64_t)std::floor(((double)N * eps) / (2.0 * (double)p));
     const bool per_interval = schedule == HSS_SCHEDULE_EQUAL;
@@ -649,11 +878,11 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
         if (staged) {
             HSS_LAUNCH(k_histogram_staged, dim3((unsigned)cdiv(Z, kStgProbes), (unsigned)cdiv(p, kStgSegs)), kStgThreads, 0,
                        st, skeys, d_seg_off, p, S, ws.Lpos, ws.Upos, ws.int_rep, ws.pkey, ws.pseg, ws.pspos, Z, ws.prank,
-                       ws.probe_pos, ws.cap, ws.sws.err);
+                       ws.probe_pos, ws.cap, ws.sws.err, ws.ctl);
         } else {
             HSS_LAUNCH(k_histogram, dim3((unsigned)cdiv(Z, 32), (unsigned)cdiv(p, kHistSegPerBlock)), 256, 0, st, skeys,
                        d_seg_off, p, S, ws.Lpos, ws.Upos, ws.int_rep, ws.pkey, ws.pseg, ws.pspos, ws.pint, Z, ws.prank,
-                       ws.probe_pos, ws.cap, ws.sws.err);
+                       ws.probe_pos, ws.cap, ws.sws.err, ws.ctl);
         }
         return cudaGetLastError();
     };
@@ -680,9 +909,29 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
                    ws.pspos, ws.pint, ws.prank);
         HSS_TRY(histogram((uint64_t)nprop, 1u));
         HSS_LAUNCH(k_update, sblk, 256, 0, st, S, N, p, ws.pkey, ws.pseg, ws.pspos, ws.prank, (uint64_t)nprop,
-                   (int32_t)kNonMember, ws.Lcut, ws.Ucut, ws.chgL, ws.chgU);
+                   (int32_t)kNonMember, ws.Lcut, ws.Ucut, ws.chgL, ws.chgU, ws.ctl);
         HSS_LAUNCH(k_update_pos, dim3(p, sblk), 256, 0, st, S, ws.chgL, ws.chgU, ws.probe_pos, ws.cap, ws.Lpos, ws.Upos);
         intervals(1);
+    }
+    if (device_loop && device_loop_possible(ws.cap, schedule)) {
+        // Sampling of round 1 on the stream, then the loop's graph: no host
+        // round trip until the caller reads the statistics.
+        int dev = 0;
+        HSS_TRY(cudaGetDevice(&dev));
+        cudaGraphExec_t exec = nullptr;
+        const LoopKey key{dev, ws.ctl, skeys, d_seg_off, N, tol, ws.cap, p, schedule, hist_mode, oversample};
+        const int rc = loop_graph(key, skeys, d_seg_off, N, p, tol, oversample, schedule, hist_mode, ws, &exec);
+        if (rc != HSS_OK) return rc;
+        HSS_LAUNCH(k_ctl_init, 1, 1, 0, st, ws.ctl, seed, max_rounds);
+        enqueue_sampling(ws, d_seg_off, N, p, S, seed, 1, st, per_interval);
+        HSS_TRY(cudaGetLastError());
+        HSS_TRY(cudaGraphLaunch(exec, st));
+        HSS_LAUNCH(k_finalize, (unsigned)cdiv(S, 256), 256, 0, st, S, N, p, key_type, ws.Lcut, ws.Ucut, d_splitters,
+                   d_offsets, ws.choose_u, ws.fin_okey, ws.fin_kind);
+        HSS_LAUNCH(k_final_pos, dim3(p, sblk), 256, 0, st, S, ws.choose_u, ws.Lpos, ws.Upos);
+        HSS_TRY(cudaGetLastError());
+        if (used_device_loop) *used_device_loop = true;
+        return HSS_OK;
     }
     enqueue_sampling(ws, d_seg_off, N, p, S, seed, 1, st, per_interval);
     HSS_TRY(cudaGetLastError());
@@ -709,7 +958,7 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
                        ws.Ucut, ws.int_rep, ws.ctl, ws.pkey, ws.pseg, ws.pspos, ws.pint, ws.prank);
             HSS_TRY(histogram(Z, h.nint));
             HSS_LAUNCH(k_update, sblk, 256, 0, st, S, N, p, ws.pkey, ws.pseg, ws.pspos, ws.prank, Z, (int32_t)kMember,
-                       ws.Lcut, ws.Ucut, ws.chgL, ws.chgU);
+                       ws.Lcut, ws.Ucut, ws.chgL, ws.chgU, ws.ctl);
             HSS_LAUNCH(k_update_pos, dim3(p, sblk), 256, 0, st, S, ws.chgL, ws.chgU, ws.probe_pos, ws.cap, ws.Lpos, ws.Upos);
         }
         intervals(j + 1);
@@ -721,6 +970,12 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
     }
     out->rounds = j;
     out->status = status;
+    {   // the same record the device-driven loop leaves, for hss_call_stats
+        HSS_LAUNCH(k_ctl_record, 1, 64, 0, st, ws.ctl, j, status, out->sample_size[j > 0 ? j - 1 : 0]);
+        HSS_TRY(cudaMemcpyAsync(ws.ctl->hist_Z, out->sample_size, sizeof(out->sample_size), cudaMemcpyHostToDevice, st));
+        HSS_TRY(cudaMemcpyAsync(ws.ctl->hist_gamma, out->gamma, sizeof(out->gamma), cudaMemcpyHostToDevice, st));
+        HSS_TRY(cudaMemcpyAsync(ws.ctl->hist_unres, out->unresolved, sizeof(out->unresolved), cudaMemcpyHostToDevice, st));
+    }
     HSS_LAUNCH(k_finalize, (unsigned)cdiv(S, 256), 256, 0, st, S, N, p, key_type, ws.Lcut, ws.Ucut, d_splitters, d_offsets,
                ws.choose_u, ws.fin_okey, ws.fin_kind);
     HSS_LAUNCH(k_final_pos, dim3(p, sblk), 256, 0, st, S, ws.choose_u, ws.Lpos, ws.Upos);

@@ -13,11 +13,20 @@ struct RoundCtl {
     uint32_t take_all;     // q >= 1: select every key of the region
     uint32_t nint;         // distinct unresolved intervals
     uint32_t unresolved;   // unresolved splitters
-    uint32_t round;        // rounds completed
+    uint32_t round;        // rounds started (device-driven loop)
     uint64_t Z;            // probes drawn by the last sampling pass
     uint64_t seg_off_z[2]; // {0, min(Z, cap)}: one "segment" for the probe sort
-    uint32_t err;          // device error bits
+    // Device-driven loop: the decision kernel keeps the loop state and the
+    // round statistics here, and reads the call's parameters from here (so one
+    // captured graph serves every call on the same workspace).
+    int32_t status;        // HSS_OK, HSS_ERR_ROUND_LIMIT or HSS_ERR_CAPACITY
+    uint32_t staged;       // the next histogram takes the staged form
+    uint64_t seed;         // Philox key of the sampling
+    uint32_t max_rounds;
     uint32_t pad;
+    uint64_t hist_Z[HSS_MAX_ROUNDS];
+    uint64_t hist_gamma[HSS_MAX_ROUNDS];
+    uint64_t hist_unres[HSS_MAX_ROUNDS + 1];
 };
 
 // Workspace of the rounds, carved from the caller's buffer.
@@ -80,11 +89,27 @@ constexpr uint32_t kHistAuto = 0, kHistProbe = 1, kHistStaged = 2;
 // per-segment positions of the splitters (into ws.Lpos).  d_prop[nprop]
 // (nullable; keys in the caller's representation, nprop <= ws.cap) are
 // proposed cuts ranked and offered to every splitter before round 1.
+// With device_loop the rounds run as one CUDA graph (a WHILE conditional node
+// whose body is one round; a device kernel decides whether another round is
+// needed), so the call does not wait for the GPU: out is then left for
+// read_round_result() once the stream has passed the rounds.  The loop is
+// taken only when the round's probe sort needs no host planning (sample
+// capacity <= the on-chip capacity) and the schedule is computed on the device
+// (not the k-round schedule); else the host drives the rounds as before.
 int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uint32_t p, double eps, uint64_t seed,
                float oversample, uint32_t max_rounds, int key_type, hss_cut* d_splitters, uint64_t* d_offsets,
                const RoundWs& ws, cudaStream_t st, RoundResult* out, const uint64_t* d_prop = nullptr,
                uint32_t nprop = 0, uint32_t schedule = HSS_SCHEDULE_PROPORTIONAL, uint32_t schedule_k = 0,
-               uint32_t hist_mode = kHistAuto);
+               uint32_t hist_mode = kHistAuto, bool device_loop = false, bool* used_device_loop = nullptr);
+
+// Whether run_rounds can drive these rounds on the device.
+bool device_loop_possible(uint64_t cap, uint32_t schedule);
+
+// Fill out from the device record of a device-driven run (synchronises
+// `st`).  Returns the status.
+int read_round_result(const RoundWs& ws, RoundResult* out, cudaStream_t st);
+// Kernels one round of the device-driven loop launches.
+uint32_t device_round_kernels();
 
 // Per-bucket split windows for the merge, from the final splitters.
 cudaError_t bucket_hints(const RoundWs& ws, const uint64_t* skeys, const uint64_t* d_seg_off, uint32_t p,

@@ -12,12 +12,12 @@
 //    above kTinyGroup keys (heavy duplicates, skew) goes to a stable LSD kernel
 //    (8-bit digit passes over a 16-bit index permutation).
 //  * A larger segment takes one read pass for statistics (digit counts and the
-//    OR/AND of its keys) and one one-sweep stable scatter on its first-split
+//    OR/AND of its keys) and one stable scatter on its first-split
 //    digit (its top varying byte, or an interpolation of the key range the
-//    caller bounds): every 4096-key tile ranks its keys in shared memory with
-//    ballot peer masks, publishes its digit counts and chains the segment's
-//    exclusive digit prefix by decoupled look-back over the earlier tiles of the
-//    same segment.  The 256 sub-buckets are then sorted the same way (on chip
+//    caller bounds): the statistics pass counts every 4096-key tile's digits,
+//    a scan turns the counts into each tile's destination offsets, and every
+//    tile ranks its keys in shared memory (ballot peer masks with a payload,
+//    one shared atomic per key for keys alone) and writes them out.  The 256 sub-buckets are then sorted the same way (on chip
 //    when small, recursively otherwise), so a uniform 64-bit input costs
 //    8 + 16 + 16 B of HBM traffic per key instead of the 136 B of eight LSD
 //    passes.  A segment whose keys are all equal is copied straight to the
@@ -27,10 +27,6 @@
 #include <algorithm>
 
 namespace hss {
-
-constexpr uint32_t kFlagAgg = 1u << 30;
-constexpr uint32_t kFlagPre = 1u << 31;
-constexpr uint32_t kCountMask = (1u << 30) - 1u;
 
 __host__ __device__ static inline uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 static inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -52,14 +48,14 @@ size_t segsort_ws_bytes(uint64_t N, uint64_t nseg) {
     const WsDims d = ws_dims(N, nseg);
     size_t b = 0;
     b += align_up((d.list + 1) * 4, 256) + align_up(d.list * 4, 256);  // tile_start, large_id
+    b += align_up(d.tiles * 4, 256);                                  // tile_seg
     b += align_up(d.ml * 4, 256);                                     // large_seg
-    b += align_up(d.ml * 2 * kRadix * 4, 256);                        // hist
+    b += align_up(d.tiles * 2 * kRadix * 2, 256);                     // tile_hist
     b += 2 * align_up(d.ml * 8, 256);                                 // vor, vand
-    b += align_up(d.ml * kRadix * 4, 256);                            // msd_off
     b += 4 * align_up(d.ml * 4, 256);                                 // msd_shift x2, spec, direct
     b += 2 * align_up(d.ml * 8, 256);                                 // msd_base, msd_mult
     b += 4 * align_up(d.ml * kRadix * 8, 256);                        // sub_lo/hi x2
-    b += align_up(d.tiles * kRadix * 4, 256);                         // status
+    b += align_up(d.tiles * kRadix * 4, 256);                         // tile_off
     b += align_up(64 * 4, 256);                                       // counters
     b += 8 * align_up(d.list * 4, 256);                               // class lists, fallback, slow lists
     b += align_up(8 * (d.list / 1024 + 2) * 4, 256);                  // blk
@@ -76,11 +72,11 @@ SegSortWs segsort_ws_carve(void* base, uint64_t N, uint64_t nseg, uint32_t* err)
     auto take = [&](size_t bytes) { void* r = p; p += align_up(bytes, 256); return r; };
     w.tile_start = (uint32_t*)take((d.list + 1) * 4);
     w.large_id = (uint32_t*)take(d.list * 4);
+    w.tile_seg = (uint32_t*)take(d.tiles * 4);
     w.large_seg = (uint32_t*)take(d.ml * 4);
-    w.hist = (uint32_t*)take(d.ml * 2 * kRadix * 4);
+    w.tile_hist = (uint16_t*)take(d.tiles * 2 * kRadix * 2);
     w.vor = (unsigned long long*)take(d.ml * 8);
     w.vand = (unsigned long long*)take(d.ml * 8);
-    w.msd_off = (uint32_t*)take(d.ml * kRadix * 4);
     w.msd_shift[0] = (uint32_t*)take(d.ml * 4);
     w.msd_shift[1] = (uint32_t*)take(d.ml * 4);
     w.spec = (uint32_t*)take(d.ml * 4);
@@ -91,7 +87,7 @@ SegSortWs segsort_ws_carve(void* base, uint64_t N, uint64_t nseg, uint32_t* err)
         w.sub_lo[i] = (uint64_t*)take(d.ml * kRadix * 8);
         w.sub_hi[i] = (uint64_t*)take(d.ml * kRadix * 8);
     }
-    w.status = (uint32_t*)take(d.tiles * kRadix * 4);
+    w.tile_off = (uint32_t*)take(d.tiles * kRadix * 4);
     w.counters = (uint32_t*)take(64 * 4);
     for (int i = 0; i < 3; ++i) w.list[i] = (uint32_t*)take(d.list * 4);
     w.fb_list = (uint32_t*)take(d.list * 4);
@@ -184,7 +180,7 @@ __device__ __forceinline__ uint32_t warp_peers8(uint32_t d, bool valid) {
 // w*32*ITEMS + i*32 + l, so (w, i, l) order is element order and the ranks are
 // stable.  Shared atomics issued by one warp in program order are applied in
 // that order, which the running bases of step 3 rely on.  `between` runs after
-// step 2 (used to publish the look-back aggregate early).
+// step 2.
 // ---------------------------------------------------------------------------
 struct NoOp { __device__ void operator()() const {} };
 
@@ -782,45 +778,98 @@ __global__ __launch_bounds__(THREADS) void k_small_reg(
 // ---------------------------------------------------------------------------
 // Keys alone, on chip, segments of up to CAP = THREADS * ITEMS keys held in
 // registers.  Equal keys are indistinguishable, so no input order has to be
-// kept: a counting pass on a digit interpolating the segment's key range
-// (R groups, monotone in the key) hands every key a slot in its group through
-// one shared counter; keys are scattered into group order; a key in a group
-// of two or more moves to its group's start plus the number of the group's
-// keys below it in (key, slot) order, a total order; a large group holding a
-// single key value needs no ranking.  A segment with a large group of
-// distinct keys is appended to slow_list for the shared-memory kernel.
+// kept.  A counting pass on a digit interpolating the segment's key range (R
+// groups, monotone in the key) hands every key a slot in its group through
+// one shared counter, and the keys are scattered into group order; since the
+// groups come in key order, each thread then finishes the sort by insertion
+// sorts of its own R / THREADS consecutive groups (a handful of keys, almost
+// in order).  A segment with a group above kTinyGroup keys
+// holding distinct keys is appended to slow_list for the shared-memory
+// kernel.  With PREFETCH the next segment of the list is copied into a
+// shared staging buffer (cp.async) while the current one is sorted.
 // ---------------------------------------------------------------------------
-template <int CAP, int R>
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <int CAP, int R, bool PREFETCH>
 constexpr size_t keys_sort_smem() {
-    return (size_t)CAP * 8 + (size_t)(R + 1) * 4 + 32 * 4 + 2 * 32 * 8 + 64;
+    return (size_t)CAP * 8 * (PREFETCH ? 2 : 1) + (size_t)(R + 1) * 4 + 32 * 4 + 2 * 32 * 8 + 64;
 }
 
-template <int THREADS, int CAP, int R>
-__global__ __launch_bounds__(THREADS) void k_small_keys(
+// CTAs per SM the register budget must allow: the small classes live on
+// many buckets in flight per SM (their keys are prefetched while the
+// previous bucket is sorted).
+template <int THREADS>
+constexpr int keys_min_blocks() { return THREADS <= 128 ? 8 : (THREADS <= 256 ? 3 : 1); }
+
+template <int THREADS, int CAP, int R, bool PREFETCH>
+__global__ __launch_bounds__(THREADS, keys_min_blocks<THREADS>()) void k_small_keys(
     const uint64_t* kin, uint64_t* kout, const uint64_t* __restrict__ seg_lo, const uint64_t* __restrict__ seg_hi,
     const uint32_t* __restrict__ list, const uint32_t* __restrict__ nlist, uint64_t nseg, uint32_t min_n,
     uint32_t max_n, uint64_t flip_in, uint64_t flip_out, uint32_t* __restrict__ slow_list,
     uint32_t* __restrict__ slow_count) {
     constexpr int ITEMS = CAP / THREADS;
     constexpr int WARPS = THREADS / 32;
-    static_assert(CAP % THREADS == 0 && R % THREADS == 0 && R <= 8192 && CAP <= (1 << 18), "keys sort shape");
+    constexpr int G = R / THREADS;  // groups per thread in the final insertion sort
+    static_assert(CAP % THREADS == 0 && R % THREADS == 0 && R <= 8192 && CAP <= (1 << 18) && WARPS <= 16,
+                  "keys sort shape");
     constexpr uint32_t kDigitMask = 8191u;  // digit in bits 0..12, slot from bit 13
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* s_key = (uint64_t*)smem;                                              // CAP
-    uint32_t* s_start = (uint32_t*)(s_key + CAP);                                   // R + 1
+    uint64_t* s_stage = s_key + CAP;                                                // CAP (PREFETCH)
+    uint32_t* s_start = (uint32_t*)(s_stage + (PREFETCH ? CAP : 0));                // R + 1
     uint32_t* s_warp = s_start + (R + 1);                                           // 32
     uint64_t* s_red = (uint64_t*)(((uintptr_t)(s_warp + 32) + 7) & ~(uintptr_t)7);  // 2 * 32
     uint32_t* s_flag = (uint32_t*)(s_red + 64);                                     // [0] mixed large group
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const uint64_t count = list ? (uint64_t)*nlist : nseg;
+    // Segment descriptors travel one iteration ahead in registers: the loads
+    // of the next segment's list entry and bounds are issued at the top of an
+    // iteration and first used after its first barrier, so their latency
+    // hides behind the current segment's work.
+    struct Desc {
+        uint64_t base;
+        uint32_t n;
+        bool ok;  // exists and belongs to this class
+    };
+    auto load_desc = [&](uint64_t k) -> Desc {
+        Desc d{0ull, 0u, false};
+        if (k < count) {
+            const uint64_t s = list ? (uint64_t)list[k] : k;
+            const uint64_t b = seg_lo[s], n = seg_hi[s] - b;
+            d.base = b;
+            d.n = (uint32_t)n;
+            d.ok = n > min_n && n <= max_n;
+        }
+        return d;
+    };
+    auto prefetch = [&](const Desc& d) {  // copy a segment into the staging buffer
+        if (d.ok)
+            for (uint32_t j = tid; j < d.n; j += THREADS) cp_async8(&s_stage[j], &kin[d.base + j]);
+        cp_async_commit();
+    };
+    Desc nxt = load_desc(blockIdx.x);
+    if (PREFETCH) prefetch(nxt);
     for (uint64_t k = blockIdx.x; k < count; k += gridDim.x) {
+        const Desc cur = nxt;
+        nxt = load_desc(k + gridDim.x);
+        if (!cur.ok) {  // uniform per CTA; such a segment was never prefetched
+            if (PREFETCH) prefetch(nxt);
+            continue;
+        }
         const uint64_t s = list ? (uint64_t)list[k] : k;
-        const uint64_t base = seg_lo[s];
-        const uint64_t n64 = seg_hi[s] - base;
-        if (n64 <= min_n || n64 > max_n) continue;  // uniform per CTA
-        const uint32_t n = (uint32_t)n64;
-        const uint64_t* src = kin + base;
+        const uint64_t base = cur.base;
+        const uint32_t n = cur.n;
+        if (PREFETCH) {
+            cp_async_wait_all();
+            __syncthreads();
+        }
+        const uint64_t* src = PREFETCH ? s_stage : kin + base;
         // Items past the segment are skipped by a uniform break (n is the
         // same for the whole CTA), so a short segment costs no predicated work.
         uint64_t key[ITEMS];
@@ -839,6 +888,7 @@ __global__ __launch_bounds__(THREADS) void k_small_keys(
         for (int d = tid; d < R; d += THREADS) s_start[d] = 0;
         if (tid == 0) s_flag[0] = 0;
         __syncthreads();
+        if (PREFETCH) prefetch(nxt);  // the staging buffer has been read
         hmin = ~0u; hmax = 0u;
 #pragma unroll
         for (int i = 0; i < WARPS; ++i) { hmin = min(hmin, s_warp[i]); hmax = max(hmax, s_warp[WARPS + i]); }
@@ -862,7 +912,6 @@ __global__ __launch_bounds__(THREADS) void k_small_keys(
                 lo = min(lo, (uint64_t)__shfl_xor_sync(0xffffffffu, lo, o));
                 hi = max(hi, (uint64_t)__shfl_xor_sync(0xffffffffu, hi, o));
             }
-            __syncthreads();  // s_warp reads above are done
             if (lane == 0) { s_red[w] = lo; s_red[32 + w] = hi; }
             __syncthreads();
             lo = ~0ull; hi = 0ull;
@@ -907,39 +956,26 @@ __global__ __launch_bounds__(THREADS) void k_small_keys(
         mx = 0;
 #pragma unroll
         for (int i = 0; i < WARPS; ++i) mx = max(mx, s_warp[i]);
-        // scatter into group order; dp keeps the digit and now the group slot
+        // scatter into group order
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             if ((uint32_t)(i * THREADS) >= n) break;
             const uint32_t e = tid + i * THREADS;
             if (e < n) {
                 const uint32_t d = dp[i] & kDigitMask;
-                const uint32_t pos = s_start[d] + (dp[i] >> 13);
-                s_key[pos] = key[i];
-                dp[i] = d | (pos << 13);
+                s_key[s_start[d] + (dp[i] >> 13)] = key[i];
             }
         }
         __syncthreads();
-        if (mx > 1u) {
-            bool moved = false;
+        if (mx > (uint32_t)kTinyGroup) {
+            // a large group is fine as it is if it holds a single value
 #pragma unroll
             for (int i = 0; i < ITEMS; ++i) {
                 if ((uint32_t)(i * THREADS) >= n) break;
-                const uint32_t e = tid + i * THREADS;
-                if (e >= n) continue;
-                const uint32_t d = dp[i] & kDigitMask, pos = dp[i] >> 13;
-                const uint32_t a = s_start[d], b = s_start[d + 1];
-                if (b - a <= 1u) continue;
-                if (b - a > (uint32_t)kTinyGroup) {  // large group: fine as it is if it holds one value
-                    if (s_key[a] != key[i]) s_flag[0] = 1u;
-                    continue;
-                }
-                uint32_t r = 0;
-                for (uint32_t q = a; q < b; ++q) {
-                    const uint64_t ky = s_key[q];
-                    r += (ky < key[i] || (ky == key[i] && q < pos)) ? 1u : 0u;
-                }
-                if (a + r != pos) { dp[i] = d | ((a + r) << 13); moved = true; }
+                if (tid + i * THREADS >= n) continue;
+                const uint32_t d = dp[i] & kDigitMask;
+                const uint32_t a = s_start[d];
+                if (s_start[d + 1] - a > (uint32_t)kTinyGroup && s_key[a] != s_key[a + (dp[i] >> 13)]) s_flag[0] = 1u;
             }
             __syncthreads();
             if (s_flag[0]) {  // uniform: a large group of distinct keys
@@ -947,11 +983,25 @@ __global__ __launch_bounds__(THREADS) void k_small_keys(
                 __syncthreads();
                 continue;
             }
-            if (moved) {
-#pragma unroll
-                for (int i = 0; i < ITEMS; ++i) {
-                    if ((uint32_t)(i * THREADS) >= n) break;
-                    if (tid + i * THREADS < n) s_key[dp[i] >> 13] = key[i];
+        }
+        if (mx > 1u) {
+            // Every group of 2..kTinyGroup keys is sorted in place by the
+            // thread owning it (each thread owns G consecutive groups; the
+            // groups hold a few keys, nearly in order); a large group holding
+            // one value needs nothing.
+            for (int g = tid * G; g < tid * G + G; ++g) {
+                const uint32_t a = s_start[g], b = s_start[g + 1];
+                if (b - a < 2u || b - a > (uint32_t)kTinyGroup) continue;
+                for (uint32_t j = a + 1; j < b; ++j) {
+                    const uint64_t x = s_key[j];
+                    uint32_t i = j;
+                    while (i > a) {
+                        const uint64_t y = s_key[i - 1];
+                        if (y <= x) break;
+                        s_key[i] = y;
+                        --i;
+                    }
+                    s_key[i] = x;
                 }
             }
             __syncthreads();
@@ -960,6 +1010,7 @@ __global__ __launch_bounds__(THREADS) void k_small_keys(
         for (uint32_t j = tid; j < n; j += THREADS) dst[j] = s_key[j] ^ flip_out;
         __syncthreads();
     }
+    if (PREFETCH) cp_async_wait_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -1158,7 +1209,6 @@ __global__ __launch_bounds__(1024) void k_plan_scan(uint32_t nblk, uint32_t* __r
     if (threadIdx.x == 0) {
         for (int k = 0; k < 5; ++k) counters[16 + k] = carry.c[k];
         *(unsigned long long*)(counters + 22) = carry.keys;
-        counters[0] = 0;   // tile counter of this level's scatter pass
         counters[24] = 0;  // fallback list of this level's on-chip sorts
         counters[25] = 0;  // segments the register kernels leave to the shared-memory kernel
         counters[26] = 0;  // ... and the keys-only kernels, per size class
@@ -1172,7 +1222,8 @@ __global__ __launch_bounds__(1024) void k_plan_write(const uint64_t* __restrict_
                                                      const uint32_t* __restrict__ counters, uint32_t* __restrict__ tile_start,
                                                      uint32_t* __restrict__ large_id, uint32_t* __restrict__ large_seg,
                                                      uint32_t* __restrict__ list0, uint32_t* __restrict__ list1,
-                                                     uint32_t* __restrict__ list2, uint32_t* __restrict__ err) {
+                                                     uint32_t* __restrict__ list2, uint32_t* __restrict__ err,
+                                                     uint32_t* __restrict__ tile_seg) {
     const uint64_t s = (uint64_t)blockIdx.x * 1024 + threadIdx.x;
     const PlanV item = plan_item(seg_lo, seg_hi, nseg, s);
     if (s < nseg && seg_hi[s] - seg_lo[s] >= kMaxSegKeys) atomicOr(err, kDevErrSize);
@@ -1189,64 +1240,60 @@ __global__ __launch_bounds__(1024) void k_plan_write(const uint64_t* __restrict_
             const uint32_t id = off.c[3] + v.c[3] - 1;
             large_id[s] = id;
             large_seg[id] = (uint32_t)s;
+            const uint32_t t0 = off.c[4] + v.c[4] - item.c[4];
+            for (uint32_t u = 0; u < item.c[4]; ++u) tile_seg[t0 + u] = (uint32_t)s;
         }
     }
     if (s == nseg) tile_start[nseg] = counters[20];
 }
 
-__device__ __forceinline__ uint32_t find_tile_segment(const uint32_t* __restrict__ tile_start, uint64_t nseg, uint32_t t) {
-    // largest s with tile_start[s] <= t (segments with no tiles share a start value)
-    uint64_t lo = 0, hi = nseg;  // answer in [lo, hi)
-    while (hi - lo > 1) {
-        const uint64_t mid = (lo + hi) >> 1;
-        if (tile_start[mid] <= t) lo = mid; else hi = mid;
-    }
-    return (uint32_t)lo;
-}
-
 // ---------------------------------------------------------------------------
-// Statistics of the large segments: 8 byte histograms (or, with a window
-// hint, the window histogram) and the OR/AND of the keys, in one read.
-// Grid (#large, split); CTA (id, k) reads the k-th share of segment id.
+// Statistics of the large segments, per tile of kOsTile keys: the digit
+// histogram of the tile (on a speculative window, or on the interpolating
+// hint) and the OR/AND of the segment's keys, in one read.  One CTA per tile.
+// From these the split pass gets every tile's destination offsets by a scan
+// (k_msd_prep) instead of a look-back across the tiles of its segment.
 // ---------------------------------------------------------------------------
 // msd_shift flag: the split interpolated the key range (no byte is fixed in
 // its sub-buckets).
 constexpr uint32_t kShiftInterp = 0x100u;
 
-__global__ __launch_bounds__(256) void k_seg_stats(const uint64_t* __restrict__ kin, const uint64_t* __restrict__ seg_lo,
-                                                   const uint64_t* __restrict__ seg_hi, const uint32_t* __restrict__ large_seg,
-                                                   const uint32_t* __restrict__ counters, uint32_t* __restrict__ hist,
-                                                   unsigned long long* __restrict__ vor, unsigned long long* __restrict__ vand,
-                                                   const uint64_t* __restrict__ hint_lo, const uint64_t* __restrict__ hint_mult,
-                                                   const uint32_t* __restrict__ prev_shift, uint32_t* __restrict__ spec_out,
-                                                   uint32_t split, uint64_t flip_in) {
+__device__ __forceinline__ int spec_window(const uint32_t* __restrict__ prev_shift, uint32_t s) {
+    // the byte below the parent split's window (a sub-bucket's keys agree on
+    // that window and above); the top byte at the first level
+    if (!prev_shift) return 7;
+    const uint32_t ps = prev_shift[s >> 8];
+    return (ps & kShiftInterp) ? 7 : (ps >= 8 ? (int)(ps >> 3) - 1 : 0);
+}
+
+__global__ __launch_bounds__(256) void k_tile_stats(const uint64_t* __restrict__ kin, const uint64_t* __restrict__ seg_lo,
+                                                    const uint64_t* __restrict__ seg_hi, uint64_t nseg,
+                                                    const uint32_t* __restrict__ tile_start,
+                                                    const uint32_t* __restrict__ tile_seg,
+                                                    const uint32_t* __restrict__ large_id, uint16_t* __restrict__ tile_hist,
+                                                    unsigned long long* __restrict__ vor, unsigned long long* __restrict__ vand,
+                                                    const uint64_t* __restrict__ hint_lo, const uint64_t* __restrict__ hint_mult,
+                                                    const uint32_t* __restrict__ prev_shift, uint32_t* __restrict__ spec_out,
+                                                    uint64_t flip_in) {
     __shared__ uint32_t s_h[kRadix];
     __shared__ unsigned long long s_or[8], s_and[8];
-    const uint32_t id = blockIdx.x;
-    if (id >= counters[19]) return;
-    const uint32_t s = large_seg[id];
+    const uint32_t t = blockIdx.x;
+    if (t >= tile_start[nseg]) return;  // uniform
+    s_h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t s = tile_seg[t], id = large_id[s];
     const uint64_t lo = seg_lo[s], n = seg_hi[s] - lo;
-    const uint64_t per = ceil_div(ceil_div(n, kOsTile), split) * kOsTile;
-    const uint64_t a = (uint64_t)blockIdx.y * per;
+    const uint32_t ti = t - tile_start[s];
+    const uint64_t a = (uint64_t)ti * kOsTile, b = min(n, a + kOsTile);
     const bool win = hint_lo != nullptr;
-    // Speculative window: the byte below the parent split's window (a
-    // sub-bucket's keys agree on that window and above), the top byte at the
-    // first level.  The recount pass fixes the segments where it is wrong.
-    int spec = 7;
-    if (prev_shift) {
-        const uint32_t ps = prev_shift[s >> 8];
-        spec = (ps & kShiftInterp) ? 7 : (ps >= 8 ? (int)(ps >> 3) - 1 : 0);
-    }
-    if (blockIdx.y == 0 && threadIdx.x == 0) spec_out[id] = (uint32_t)spec;
-    if (a >= n) return;
-    const uint64_t b = min(n, a + per);
+    const int spec = spec_window(prev_shift, s);
+    if (ti == 0 && threadIdx.x == 0) spec_out[id] = (uint32_t)spec;
     const uint64_t hb = win ? hint_lo[s] : 0ull;
     const uint64_t hm = win ? hint_mult[s] : 0ull;
     const int sh = 8 * spec;
-    for (int i = threadIdx.x; i < kRadix; i += blockDim.x) s_h[i] = 0;
-    __syncthreads();
     unsigned long long o = 0, an = ~0ull;
-    for (uint64_t e = a + threadIdx.x; e < b; e += blockDim.x) {
+#pragma unroll 4
+    for (uint64_t e = a + threadIdx.x; e < b; e += 256) {
         const uint64_t k = kin[lo + e] ^ flip_in;
         o |= k;
         an &= k;
@@ -1262,65 +1309,60 @@ __global__ __launch_bounds__(256) void k_seg_stats(const uint64_t* __restrict__ 
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long x = 0, y = ~0ull;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { x |= s_or[i]; y &= s_and[i]; }
+        for (int i = 0; i < 8; ++i) { x |= s_or[i]; y &= s_and[i]; }
         atomicOr(&vor[id], x);
         atomicAnd(&vand[id], y);
     }
-    uint32_t* g = hist + (uint64_t)id * (2 * kRadix);
-    for (int i = threadIdx.x; i < kRadix; i += blockDim.x) {
-        const uint32_t c = s_h[i];
-        if (c) atomicAdd(&g[i], c);
-    }
+    tile_hist[(uint64_t)t * (2 * kRadix) + threadIdx.x] = (uint16_t)s_h[threadIdx.x];
 }
 
-// Recount of the segments whose top varying byte (from the OR/AND of the
-// statistics pass) is not the speculative one: the histogram of that byte
-// into the second row.  Other CTAs return at once.
-__global__ __launch_bounds__(256) void k_seg_recount(const uint64_t* __restrict__ kin, const uint64_t* __restrict__ seg_lo,
-                                                     const uint64_t* __restrict__ seg_hi,
-                                                     const uint32_t* __restrict__ large_seg,
-                                                     const uint32_t* __restrict__ counters, uint32_t* __restrict__ hist,
-                                                     const unsigned long long* __restrict__ vor,
-                                                     const unsigned long long* __restrict__ vand,
-                                                     const uint32_t* __restrict__ spec, uint32_t split, uint64_t flip_in) {
+// Recount of the tiles of segments whose top varying byte (from the OR/AND of
+// the statistics pass) is not the speculative one: the histogram of that byte
+// into the tile's second row.  Other CTAs return at once.
+__global__ __launch_bounds__(256) void k_tile_recount(const uint64_t* __restrict__ kin, const uint64_t* __restrict__ seg_lo,
+                                                      const uint64_t* __restrict__ seg_hi, uint64_t nseg,
+                                                      const uint32_t* __restrict__ tile_start,
+                                                      const uint32_t* __restrict__ tile_seg,
+                                                      const uint32_t* __restrict__ large_id, uint16_t* __restrict__ tile_hist,
+                                                      const unsigned long long* __restrict__ vor,
+                                                      const unsigned long long* __restrict__ vand,
+                                                      const uint32_t* __restrict__ spec, uint64_t flip_in) {
     __shared__ uint32_t s_h[kRadix];
-    const uint32_t id = blockIdx.x;
-    if (id >= counters[19]) return;
+    const uint32_t t = blockIdx.x;
+    if (t >= tile_start[nseg]) return;  // uniform
+    s_h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t s = tile_seg[t], id = large_id[s];
     const unsigned long long vary = vor[id] ^ vand[id];
     if (vary == 0ull) return;
-    const uint32_t t = (uint32_t)(63 - __clzll((long long)vary)) >> 3;
-    if (t == spec[id]) return;  // uniform per CTA
-    const uint32_t s = large_seg[id];
+    const uint32_t w = (uint32_t)(63 - __clzll((long long)vary)) >> 3;
+    if (w == spec[id]) return;  // uniform per CTA
     const uint64_t lo = seg_lo[s], n = seg_hi[s] - lo;
-    const uint64_t per = ceil_div(ceil_div(n, kOsTile), split) * kOsTile;
-    const uint64_t a = (uint64_t)blockIdx.y * per;
-    if (a >= n) return;
-    const uint64_t b = min(n, a + per);
-    const int sh = 8 * (int)t;
-    for (int i = threadIdx.x; i < kRadix; i += blockDim.x) s_h[i] = 0;
-    __syncthreads();
-    for (uint64_t e = a + threadIdx.x; e < b; e += blockDim.x)
+    const uint64_t a = (uint64_t)(t - tile_start[s]) * kOsTile, b = min(n, a + kOsTile);
+    const int sh = 8 * (int)w;
+#pragma unroll 4
+    for (uint64_t e = a + threadIdx.x; e < b; e += 256)
         atomicAdd(&s_h[(uint32_t)((kin[lo + e] ^ flip_in) >> sh) & 255u], 1u);
     __syncthreads();
-    uint32_t* g = hist + (uint64_t)id * (2 * kRadix) + kRadix;
-    for (int i = threadIdx.x; i < kRadix; i += blockDim.x) {
-        const uint32_t c = s_h[i];
-        if (c) atomicAdd(&g[i], c);
-    }
+    tile_hist[(uint64_t)t * (2 * kRadix) + kRadix + threadIdx.x] = (uint16_t)s_h[threadIdx.x];
 }
 
-// Window of each large segment's split, its exclusive digit offsets and the
-// bounds of its 256 sub-buckets (empty when the keys are all equal).
+// Per large segment (thread d = digit d): the split window, the digit totals
+// (summed over the segment's tile histograms), their exclusive offsets, the
+// bounds of the 256 sub-buckets (empty when the keys are all equal), and the
+// destination of every tile's digit-d keys: the digit's offset plus the
+// digit-d keys of the segment's earlier tiles.
 __global__ __launch_bounds__(256) void k_msd_prep(const uint64_t* __restrict__ seg_lo, const uint32_t* __restrict__ large_seg,
-                                                  const uint32_t* __restrict__ counters, const uint32_t* __restrict__ hist,
+                                                  const uint32_t* __restrict__ counters,
+                                                  const uint32_t* __restrict__ tile_start,
+                                                  const uint16_t* __restrict__ tile_hist,
                                                   const unsigned long long* __restrict__ vor,
                                                   const unsigned long long* __restrict__ vand, const uint64_t* __restrict__ hint_lo,
                                                   const uint64_t* __restrict__ hint_mult, uint64_t* __restrict__ msd_base,
-                                                  uint64_t* __restrict__ msd_mult,
-                                                  uint32_t* __restrict__ msd_off, uint32_t* __restrict__ msd_shift,
-                                                  const uint32_t* __restrict__ spec,
-                                                  uint32_t* __restrict__ direct, uint64_t* __restrict__ sub_lo,
-                                                  uint64_t* __restrict__ sub_hi) {
+                                                  uint64_t* __restrict__ msd_mult, uint32_t* __restrict__ msd_shift,
+                                                  const uint32_t* __restrict__ spec, uint32_t* __restrict__ direct,
+                                                  uint64_t* __restrict__ sub_lo, uint64_t* __restrict__ sub_hi,
+                                                  uint32_t* __restrict__ tile_off) {
     __shared__ uint32_t s_c[kRadix], s_x[kRadix], s_warp[32];
     const uint32_t id = blockIdx.x;
     if (id >= counters[19]) return;
@@ -1334,19 +1376,28 @@ __global__ __launch_bounds__(256) void k_msd_prep(const uint64_t* __restrict__ s
         mult = hint_mult[s];
         row = 0;
     } else {
-        const uint32_t t = vary ? (uint32_t)(63 - __clzll((long long)vary)) >> 3 : spec[id];
-        shift = 8 * t;
-        row = t == spec[id] ? 0u : 1u;
+        const uint32_t w = vary ? (uint32_t)(63 - __clzll((long long)vary)) >> 3 : spec[id];
+        shift = 8 * w;
+        row = w == spec[id] ? 0u : 1u;
     }
     const bool dir = vary == 0ull;
-    s_c[threadIdx.x] = hist[((uint64_t)id * 2 + row) * kRadix + threadIdx.x];
+    const uint32_t d = threadIdx.x;
+    const uint32_t t0 = tile_start[s], t1 = tile_start[s + 1];
+    const uint16_t* h = tile_hist + row * kRadix + d;
+    uint32_t total = 0;
+    for (uint32_t t = t0; t < t1; ++t) total += h[(uint64_t)t * (2 * kRadix)];
+    s_c[d] = total;
     __syncthreads();
     scan256_smem<256>(s_c, s_x, s_warp);
-    const uint32_t c = s_c[threadIdx.x], x = s_x[threadIdx.x];
-    msd_off[(uint64_t)id * kRadix + threadIdx.x] = x;
-    sub_lo[(uint64_t)id * kRadix + threadIdx.x] = dir ? lo : lo + x;
-    sub_hi[(uint64_t)id * kRadix + threadIdx.x] = dir ? lo : lo + x + c;
-    if (threadIdx.x == 0) {
+    const uint32_t x = s_x[d];
+    sub_lo[(uint64_t)id * kRadix + d] = dir ? lo : lo + x;
+    sub_hi[(uint64_t)id * kRadix + d] = dir ? lo : lo + x + total;
+    uint32_t run = x;
+    for (uint32_t t = t0; t < t1; ++t) {
+        tile_off[(uint64_t)t * kRadix + d] = run;
+        run += h[(uint64_t)t * (2 * kRadix)];
+    }
+    if (d == 0) {
         msd_shift[id] = shift | (hint_lo ? kShiftInterp : 0u);
         msd_base[id] = base;
         msd_mult[id] = mult;
@@ -1355,8 +1406,9 @@ __global__ __launch_bounds__(256) void k_msd_prep(const uint64_t* __restrict__ s
 }
 
 // ---------------------------------------------------------------------------
-// The split pass: one-sweep stable scatter of every large segment on its
-// window, over all tiles of all large segments.
+// The split pass: stable scatter of every large segment on its window, one
+// CTA per tile of every large segment, each tile to the offsets k_msd_prep
+// assigned it.
 // ---------------------------------------------------------------------------
 struct SplitArgs {
     const uint64_t* kin;
@@ -1369,14 +1421,13 @@ struct SplitArgs {
     const uint64_t* seg_hi;
     uint64_t nseg;
     const uint32_t* tile_start;
+    const uint32_t* tile_seg;
     const uint32_t* large_id;
-    const uint32_t* msd_off;
+    const uint32_t* tile_off;  // [tile][256] destination of the tile's digit-d keys, relative to the segment
     const uint32_t* msd_shift;
     const uint64_t* msd_base;
     const uint64_t* msd_mult;
     const uint32_t* direct;
-    uint32_t* status;
-    uint32_t* counter;
     uint32_t* err;
     uint64_t flip_in;
     uint64_t flip_out;
@@ -1392,19 +1443,12 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
     __shared__ uint32_t s_total[kRadix], s_start[kRadix];
     __shared__ uint64_t s_gbase[kRadix];
     __shared__ uint32_t s_warp[32];
-    __shared__ uint32_t s_tile, s_seg;
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const uint32_t total_tiles = A.tile_start[A.nseg];
-    if (tid == 0) {
-        const uint32_t t = atomicAdd(A.counter, 1u);
-        s_tile = t;
-        s_seg = t < total_tiles ? find_tile_segment(A.tile_start, A.nseg, t) : 0u;
-    }
-    __syncthreads();
-    const uint32_t t = s_tile;
-    if (t >= total_tiles) return;
-    const uint32_t s = s_seg;
+    const uint32_t t = blockIdx.x;
+    if (t >= total_tiles) return;  // uniform
+    const uint32_t s = A.tile_seg[t];
     const uint32_t id = A.large_id[s];
     const uint64_t seg_base = A.seg_lo[s];
     const uint64_t seg_n = A.seg_hi[s] - seg_base;
@@ -1434,12 +1478,6 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
             if (PAY) pay[i] = 0;
         }
     }
-    uint32_t* cur = A.status;
-    // Publish this tile's digit counts as soon as they are known, so the next
-    // tile's look-back does not wait for our ranking.
-    auto publish = [&]() {
-        if (tid < kRadix) st_relaxed(&cur[(uint64_t)t * kRadix + tid], (ti == 0 ? kFlagPre : kFlagAgg) | s_total[tid]);
-    };
     if constexpr (PAY) {
         // Each key's digit once, byte-packed in four registers.
         uint32_t dpk[kOsItems / 4];
@@ -1451,7 +1489,7 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
         auto digit_of = [&](int i) -> uint32_t {
             return (wbase + i * 32 < count) ? (dpk[i >> 2] >> (8 * (i & 3))) & 255u : (uint32_t)kRadix;
         };
-        block_rank<kOsWarps, kOsItems>(digit_of, count, rank, s_hist, s_total, s_start, s_warp, publish);
+        block_rank<kOsWarps, kOsItems>(digit_of, count, rank, s_hist, s_total, s_start, s_warp, NoOp());
 #pragma unroll
         for (int i = 0; i < kOsItems; ++i) {
             if (wbase + i * 32 < count) {
@@ -1477,7 +1515,6 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
         }
         __syncthreads();
         scan256_smem<kOsThreads>(s_total, s_start, s_warp);
-        publish();
 #pragma unroll
         for (int i = 0; i < kOsItems; ++i) {
             if (wbase + i * 32 < count) {
@@ -1489,39 +1526,10 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
         }
     }
 
-    // Decoupled look-back over the earlier tiles of this segment: thread d
-    // owns digit d.
-    if (tid < kRadix) {
-        const uint32_t d = tid;
-        const uint32_t cnt = s_total[d];
-        uint32_t excl = 0;
-        if (ti != 0) {
-            const uint64_t first = A.tile_start[s];
-            uint64_t tt = t - 1;
-            for (;;) {
-                uint32_t v;
-                uint32_t it = 0;
-                while (((v = ld_relaxed(&cur[tt * kRadix + d])) & (kFlagAgg | kFlagPre)) == 0u) {
-                    if (++it > kSpinLimit) {
-                        atomicOr(A.err, kDevErrTimeout);
-                        v = kFlagPre;
-                        break;
-                    }
-                    __nanosleep(64);
-                }
-                excl += v & kCountMask;
-                if (v & kFlagPre) break;
-                if (tt == first) {  // the first tile always publishes a prefix
-                    atomicOr(A.err, kDevErrBounds);
-                    break;
-                }
-                --tt;
-            }
-            st_relaxed(&cur[(uint64_t)t * kRadix + d], kFlagPre | (excl + cnt));
-        }
-        const uint32_t goff = A.msd_off[(uint64_t)id * kRadix + d];
-        s_gbase[d] = seg_base + (uint64_t)goff + (uint64_t)excl - (uint64_t)s_start[d];
-    }
+    // The tile's digit-d keys go to the offsets the statistics scan assigned
+    // to this tile (digit offset plus the earlier tiles' digit-d keys).
+    if (tid < kRadix)
+        s_gbase[tid] = seg_base + (uint64_t)A.tile_off[(uint64_t)t * kRadix + tid] - (uint64_t)s_start[tid];
     __syncthreads();
     for (uint32_t j = tid; j < count; j += kOsThreads) {
         const uint64_t k = s_keys[j];
@@ -1588,21 +1596,22 @@ static cudaError_t launch_small_reg(const uint64_t* in, uint64_t* out, const uin
     return cudaGetLastError();
 }
 
-template <int THREADS, int CAP, int R>
+template <int THREADS, int CAP, int R, bool PREFETCH>
 static cudaError_t launch_keys(const uint64_t* in, uint64_t* out, const uint64_t* seg_lo, const uint64_t* seg_hi,
                                const uint32_t* list, const uint32_t* nlist, uint64_t count, uint64_t nseg,
                                uint32_t min_n, uint32_t max_n, uint64_t fin, uint64_t fout, uint32_t* slow,
                                uint32_t* slow_count, cudaStream_t st) {
-    constexpr size_t smem = keys_sort_smem<CAP, R>();
+    constexpr size_t smem = keys_sort_smem<CAP, R, PREFETCH>();
     {
-        const cudaError_t e = ensure_func_attrs((const void*)k_small_keys<THREADS, CAP, R>, (int)smem);
+        const cudaError_t e = ensure_func_attrs((const void*)k_small_keys<THREADS, CAP, R, PREFETCH>, (int)smem);
         if (e != cudaSuccess) return e;
     }
     const int per_sm = std::max<int>(1, std::min<int>(2048 / THREADS, (int)(227 * 1024 / smem)));
-    const uint64_t grid = std::min<uint64_t>(count, (uint64_t)num_sms() * per_sm * 4);
+    // With prefetching every CTA walks several segments of the list.
+    const uint64_t grid = std::min<uint64_t>(count, (uint64_t)num_sms() * per_sm * (PREFETCH ? 1 : 4));
     if (grid == 0) return cudaSuccess;
-    HSS_LAUNCH((k_small_keys<THREADS, CAP, R>), (unsigned)grid, THREADS, smem, st, in, out, seg_lo, seg_hi, list, nlist,
-               nseg, min_n, max_n, fin, fout, slow, slow_count);
+    HSS_LAUNCH((k_small_keys<THREADS, CAP, R, PREFETCH>), (unsigned)grid, THREADS, smem, st, in, out, seg_lo, seg_hi,
+               list, nlist, nseg, min_n, max_n, fin, fout, slow, slow_count);
     return cudaGetLastError();
 }
 
@@ -1677,7 +1686,7 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
         HSS_LAUNCH(k_plan_count, nblk, 1024, 0, st, L.seg_lo, L.seg_hi, L.nseg, ws.blk);
         HSS_LAUNCH(k_plan_scan, 1, 1024, 0, st, nblk, ws.blk, ws.counters);
         HSS_LAUNCH(k_plan_write, nblk, 1024, 0, st, L.seg_lo, L.seg_hi, L.nseg, ws.blk, ws.counters, ws.tile_start,
-                   ws.large_id, ws.large_seg, ws.list[0], ws.list[1], ws.list[2], ws.err);
+                   ws.large_id, ws.large_seg, ws.list[0], ws.list[1], ws.list[2], ws.err, ws.tile_seg);
         uint32_t hc[8];
         if ((e = cudaMemcpyAsync(hc, ws.counters + 16, sizeof(hc), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
@@ -1695,13 +1704,13 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
                 uint32_t* slow = ws.slow_keys[c];
                 uint32_t* slow_n = ws.counters + 26 + c;
                 if (c == 0)
-                    e = launch_keys<kC0Threads, kC0Cap, 1024>(L.in, dst, L.seg_lo, L.seg_hi, lists[c], ws.counters + 16,
+                    e = launch_keys<kC0Threads, kC0Cap, 512, true>(L.in, dst, L.seg_lo, L.seg_hi, lists[c], ws.counters + 16,
                                                             hc[c], L.nseg, lo_n, hi_n, L.flip_in, fout, slow, slow_n, st);
                 else if (c == 1)
-                    e = launch_keys<kC1Threads, kC1Cap, 2048>(L.in, dst, L.seg_lo, L.seg_hi, lists[c], ws.counters + 17,
+                    e = launch_keys<kC1Threads, kC1Cap, 1024, true>(L.in, dst, L.seg_lo, L.seg_hi, lists[c], ws.counters + 17,
                                                             hc[c], L.nseg, lo_n, hi_n, L.flip_in, fout, slow, slow_n, st);
                 else
-                    e = launch_keys<kC2Threads, kSmallCap, 4096>(L.in, dst, L.seg_lo, L.seg_hi, lists[c],
+                    e = launch_keys<kC2Threads, kSmallCap, 4096, false>(L.in, dst, L.seg_lo, L.seg_hi, lists[c],
                                                                ws.counters + 18, hc[c], L.nseg, lo_n, hi_n, L.flip_in,
                                                                fout, slow, slow_n, st);
                 if (e != cudaSuccess) return e;
@@ -1743,23 +1752,19 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
             return e;
         if (n_large == 0) return cudaSuccess;
         if (n_large > ws.max_large || tiles > ws.max_tiles || L.depth >= kMaxDepth) return cudaErrorInvalidValue;
-        // Statistics and the split window.
-        if ((e = cudaMemsetAsync(ws.hist, 0, (size_t)n_large * 2 * kRadix * 4, st)) != cudaSuccess) return e;
+        // Statistics per tile, the split window and every tile's offsets.
         if ((e = cudaMemsetAsync(ws.vor, 0, (size_t)n_large * 8, st)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(ws.vand, 0xff, (size_t)n_large * 8, st)) != cudaSuccess) return e;
-        const uint64_t avg_tiles = ceil_div(tiles, n_large);
-        const uint32_t split = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(256, ceil_div(2 * avg_tiles, 16)));
         const int buf = L.depth & 1;
         const uint32_t* prev_shift = L.depth > 0 ? ws.msd_shift[buf ^ 1] : nullptr;
-        HSS_LAUNCH(k_seg_stats, dim3(n_large, split), 256, 0, st, L.in, L.seg_lo, L.seg_hi, ws.large_seg, ws.counters,
-                   ws.hist, ws.vor, ws.vand, L.hint_lo, L.hint_mult, prev_shift, ws.spec, split, L.flip_in);
+        HSS_LAUNCH(k_tile_stats, tiles, 256, 0, st, L.in, L.seg_lo, L.seg_hi, L.nseg, ws.tile_start, ws.tile_seg, ws.large_id,
+                   ws.tile_hist, ws.vor, ws.vand, L.hint_lo, L.hint_mult, prev_shift, ws.spec, L.flip_in);
         if (!L.hint_lo)
-            HSS_LAUNCH(k_seg_recount, dim3(n_large, split), 256, 0, st, L.in, L.seg_lo, L.seg_hi, ws.large_seg,
-                       ws.counters, ws.hist, ws.vor, ws.vand, ws.spec, split, L.flip_in);
-        HSS_LAUNCH(k_msd_prep, n_large, 256, 0, st, L.seg_lo, ws.large_seg, ws.counters, ws.hist, ws.vor, ws.vand,
-                   L.hint_lo, L.hint_mult, ws.msd_base, ws.msd_mult, ws.msd_off, ws.msd_shift[buf], ws.spec, ws.direct,
-                   ws.sub_lo[buf], ws.sub_hi[buf]);
-        if ((e = cudaMemsetAsync(ws.status, 0, (size_t)tiles * kRadix * 4, st)) != cudaSuccess) return e;
+            HSS_LAUNCH(k_tile_recount, tiles, 256, 0, st, L.in, L.seg_lo, L.seg_hi, L.nseg, ws.tile_start, ws.tile_seg, ws.large_id,
+                       ws.tile_hist, ws.vor, ws.vand, ws.spec, L.flip_in);
+        HSS_LAUNCH(k_msd_prep, n_large, 256, 0, st, L.seg_lo, ws.large_seg, ws.counters, ws.tile_start, ws.tile_hist,
+                   ws.vor, ws.vand, L.hint_lo, L.hint_mult, ws.msd_base, ws.msd_mult, ws.msd_shift[buf], ws.spec,
+                   ws.direct, ws.sub_lo[buf], ws.sub_hi[buf], ws.tile_off);
         // The split pass: level buffers alternate tmp, dst, tmp, ... after src.
         uint64_t* next = (L.depth & 1) ? dst : tmp;
         uint32_t* pnext = PAY ? ((L.depth & 1) ? pdst : ptmp) : nullptr;
@@ -1767,10 +1772,10 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
         A.kin = L.in; A.kout = next; A.kfinal = dst;
         A.pin = L.pin; A.pout = pnext; A.pfinal = pdst;
         A.seg_lo = L.seg_lo; A.seg_hi = L.seg_hi; A.nseg = L.nseg;
-        A.tile_start = ws.tile_start; A.large_id = ws.large_id;
-        A.msd_off = ws.msd_off; A.msd_shift = ws.msd_shift[buf]; A.msd_base = ws.msd_base; A.msd_mult = ws.msd_mult;
+        A.tile_start = ws.tile_start; A.tile_seg = ws.tile_seg; A.large_id = ws.large_id;
+        A.tile_off = ws.tile_off; A.msd_shift = ws.msd_shift[buf]; A.msd_base = ws.msd_base; A.msd_mult = ws.msd_mult;
         A.direct = ws.direct;
-        A.status = ws.status; A.counter = ws.counters; A.err = ws.err;
+        A.err = ws.err;
         A.flip_in = L.flip_in; A.flip_out = fout;
         const size_t smem = (size_t)kOsTile * 9 + (PAY ? (size_t)kOsTile * 4 : 0);
         // all of L1 as shared memory: the CTAs per SM are limited by their tiles

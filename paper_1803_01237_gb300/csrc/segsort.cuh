@@ -2,8 +2,8 @@
 //
 // Segments are given by a device array seg_off[nseg+1] of u64 offsets.  A
 // segment of at most kSmallCap keys is sorted by one CTA entirely on chip.  A
-// larger segment is split by one most-significant-digit pass (a one-sweep
-// scatter with decoupled look-back over the segment's tiles) on its top
+// larger segment is split by one most-significant-digit pass (per-tile digit
+// counts, a scan into per-tile offsets, then a scatter of every tile) on its top
 // varying 8-bit window into 256 sub-buckets, which are sorted the same way,
 // recursively; a segment whose keys are all equal is copied straight to the
 // output.
@@ -20,7 +20,7 @@ constexpr int kMaxDepth = 8;
 constexpr int kOsThreads = 256;
 constexpr int kOsWarps = kOsThreads / 32;
 constexpr int kOsItems = 16;
-constexpr int kOsTile = kOsThreads * kOsItems;  // 4096 keys per one-sweep tile
+constexpr int kOsTile = kOsThreads * kOsItems;  // 4096 keys per split tile
 
 // On-chip sort: three CTA shapes by segment size (threads x items per thread).
 constexpr int kC0Threads = 128, kC0Items = 12;  // up to 1536 keys
@@ -36,12 +36,12 @@ struct SegSortWs {
     uint64_t max_list;     // bound on the length of any segment list
     uint64_t max_tiles;
     uint32_t* tile_start;  // [max_list + 1]
+    uint32_t* tile_seg;    // [max_tiles] segment of every tile of this level's large segments
     uint32_t* large_id;    // [max_list]
     uint32_t* large_seg;   // [max_large]
-    uint32_t* hist;        // [max_large][2][256] digit counts: the speculative window, then a recount
+    uint16_t* tile_hist;   // [max_tiles][2][256] digit counts of every tile: the speculative window, then a recount
     unsigned long long* vor;   // [max_large] OR of the keys
     unsigned long long* vand;  // [max_large] AND of the keys
-    uint32_t* msd_off;     // [max_large][256] exclusive offsets of the MSD digit
     uint32_t* msd_shift[2];  // [max_large] split window (bits) of each large segment, by level parity
     uint32_t* spec;        // [max_large] byte counted speculatively by the statistics pass
     uint64_t* msd_base;    // [max_large] digit = ((key >> shift) - base) & 255, or
@@ -49,7 +49,7 @@ struct SegSortWs {
     uint32_t* direct;      // [max_large] all keys equal: copy to the output
     uint64_t* sub_lo[2];   // [max_large * 256] sub-bucket bounds, double-buffered by depth
     uint64_t* sub_hi[2];
-    uint32_t* status;      // [2][max_tiles][256] look-back words
+    uint32_t* tile_off;    // [max_tiles][256] destination of each tile's digit-d keys, relative to its segment
     uint32_t* counters;    // [64]
     uint32_t* list[3];     // [max_list] segments of each on-chip size class
     uint32_t* fb_list;     // [max_list] segments left to the stable LSD kernel (count in counters[24])

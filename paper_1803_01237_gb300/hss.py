@@ -29,6 +29,7 @@ FLAG_SYNC = 1
 FLAG_TIMING = 2
 FLAG_HIST_PROBE = 4   # force the probe-side histogram
 FLAG_HIST_STAGED = 8  # force the staged histogram in rounds whose probes share one interval
+FLAG_HOST_ROUNDS = 16  # drive the splitter rounds from the host instead of the device-driven graph loop
 MAX_ROUNDS = 64
 NUM_PHASES = 4
 PHASES = ("local_sort", "rounds", "exchange", "merge")
@@ -279,6 +280,42 @@ def partition(keys, p: int, eps: float, seed: int, oversample: float = 5.0, max_
                            ws.numel(), ctypes.byref(st), _stream(stream))
     _check(rc, "hss_partition", allow=(-3,) if allow_round_limit else ())
     return _result(None, None, spl[:p - 1], off, st), ws
+
+
+def partition_async(keys, p: int, eps: float, seed: int, oversample: float = 5.0, max_rounds: int = 0,
+                    key_type: str = "u64", flags: int = 0, stream=None):
+    """hss_partition without statistics: returns (splitters, offsets, ws)
+    without waiting for the GPU (the rounds run as a device-driven graph);
+    call_stats(...) with the same arguments reads the statistics later."""
+    lib = load()
+    keys = _as_key_tensor(keys)
+    N = keys.numel()
+    prm = _params(p, eps, seed, oversample, max_rounds, flags)
+    nb = int(lib.hss_workspace_bytes(OP["partition"], N, ctypes.byref(prm), p, KEY_TYPES[key_type], 0))
+    ws = workspace(nb, keys.device)
+    spl = torch.empty((max(p - 1, 1), 2), dtype=torch.int64, device=keys.device)
+    off = torch.empty(p + 1, dtype=torch.int64, device=keys.device)
+    rc = lib.hss_partition(_ptr(keys), KEY_TYPES[key_type], N, ctypes.byref(prm), _ptr(spl), _ptr(off), _ptr(ws),
+                           ws.numel(), None, _stream(stream))
+    _check(rc, "hss_partition")
+    return spl[:p - 1], off, ws
+
+
+def call_stats(op: str, N: int, p: int, eps: float, seed: int, ws: torch.Tensor, oversample: float = 5.0,
+               max_rounds: int = 0, key_type: str = "u64", payload: bool = False, flags: int = 0, stream=None):
+    """hss_call_stats: (status, Stats) of the last call on workspace ws."""
+    lib = load()
+    if not hasattr(lib, "_call_stats_bound"):
+        P = ctypes.c_void_p
+        lib.hss_call_stats.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(Params), ctypes.c_int,
+                                       ctypes.c_int, P, ctypes.c_size_t, ctypes.POINTER(Stats), P]
+        lib.hss_call_stats.restype = ctypes.c_int
+        lib._call_stats_bound = True
+    prm = _params(p, eps, seed, oversample, max_rounds, flags)
+    st = Stats()
+    rc = lib.hss_call_stats(OP[op], N, ctypes.byref(prm), KEY_TYPES[key_type], int(payload), _ptr(ws), ws.numel(),
+                            ctypes.byref(st), _stream(stream))
+    return rc, st
 
 
 def _proposal_tensor(proposal, keys: torch.Tensor):

@@ -407,3 +407,46 @@ def test_histogram_staged_with_proposal(hss):
         res, _ = hss.partition_with_proposal(dev(keys), p, eps, seed, dev(prop), flags=flags)
         ref = oracle.hss(keys, p, eps, seed, sort=False, proposal=prop)
         _cmp_partition(res, ref)
+
+
+# ---------------------------------------------------------------------------
+# a6: the rounds driven on the device (graph loop) and from the host
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("N,p,eps,seed,max_rounds", [(1 << 20, 64, 0.05, 1, 0), (1 << 18, 1024, 0.02, 4, 0),
+                                                     (1 << 16, 16, 0.001, 3, 2), (5000, 4999, 0.05, 2, 0),
+                                                     (1 << 17, 8, 10.0, 1, 0)])
+def test_device_and_host_rounds_agree_with_oracle(hss, N, p, eps, seed, max_rounds):
+    """The default device-driven loop (one CUDA graph, a device kernel deciding
+    each next round) and the host-driven loop give the oracle's rounds, sample
+    sizes, |gamma|, unresolved counts, splitters and offsets -- also when the
+    round limit stops them (status HSS_ERR_ROUND_LIMIT) and when no round is
+    needed (eps >= 1)."""
+    keys = inputs.uniform(N, seed)
+    ref = oracle.hss(keys, p, eps, seed, sort=False, max_rounds=max_rounds or 64)
+    for flags in (0, hss.FLAG_HOST_ROUNDS):
+        res, _ = hss.partition(dev(keys), p, eps, seed, max_rounds=max_rounds, flags=flags, allow_round_limit=True)
+        assert res.status == ref.status
+        _cmp_partition(res, ref)
+
+
+def test_partition_returns_before_the_gpu_and_stats_come_later(hss):
+    """Without statistics hss_partition enqueues everything and returns;
+    hss_call_stats then reads the rounds, sample sizes and status from the
+    workspace, equal to the oracle's."""
+    N, p, eps, seed = 1 << 20, 256, 0.02, 9
+    keys = inputs.gauss_mix(N, seed)
+    dk = dev(keys)
+    spl, off, ws = hss.partition_async(dk, p, eps, seed)
+    rc, st = hss.call_stats("partition", N, p, eps, seed, ws)
+    ref = oracle.hss(keys, p, eps, seed, sort=False)
+    assert rc == 0 and st.status == 0
+    assert st.rounds == ref.rounds
+    assert [int(x) for x in st.sample_size[:st.rounds]] == [int(x) for x in ref.sample_size]
+    assert [int(x) for x in st.gamma[:st.rounds]] == [int(x) for x in ref.gamma]
+    assert [int(x) for x in st.unresolved[:st.rounds + 1]] == [int(x) for x in ref.unresolved]
+    assert np.array_equal(off.cpu().numpy().astype(np.uint64), ref.offsets)
+    # a host-driven call leaves the same record
+    _, off2, ws2 = hss.partition_async(dk, p, eps, seed, flags=hss.FLAG_HOST_ROUNDS)
+    rc2, st2 = hss.call_stats("partition", N, p, eps, seed, ws2, flags=hss.FLAG_HOST_ROUNDS)
+    assert rc2 == 0 and st2.rounds == ref.rounds
+    assert [int(x) for x in st2.sample_size[:st2.rounds]] == [int(x) for x in ref.sample_size]
