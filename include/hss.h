@@ -228,8 +228,11 @@ int hss_sort_with_proposal(const void* d_keys, const uint32_t* d_payload, int ke
 
 /* hss_sort from host buffers: copies the keys (and payload) to the
  * workspace, sorts, and copies the sorted keys, payload, splitters and
- * offsets back to host memory.  Pinned host memory gives full copy speed.
- * Synchronous.  Workspace: hss_workspace_bytes(HSS_OP_SORT_HOST, ...). */
+ * offsets back to host memory.  The copies run on a library stream in chunks
+ * of whole processors (in) and whole buckets (out) so that they overlap the
+ * local sort and the merge; pinned host memory gives full copy speed.
+ * Synchronous; calls on one device are serialised (they share that stream).
+ * Workspace: hss_workspace_bytes(HSS_OP_SORT_HOST, ...). */
 int hss_sort_host(const void* h_keys, const uint32_t* h_payload, int key_type, uint64_t N, const hss_params* prm,
                   void* h_keys_out, uint32_t* h_payload_out, hss_cut* h_splitters, uint64_t* h_offsets,
                   void* d_work, size_t work_bytes, hss_stats* h_stats, void* stream);
@@ -401,6 +404,30 @@ int hss_cdf_eval(const hss_cdf_model* d_model, const void* d_keys, uint32_t n, f
  * in the model's key type, ready for hss_partition_with_proposal. */
 int hss_cdf_propose(const hss_cdf_model* d_model, uint32_t p, uint32_t per_splitter, double delta, void* d_out_keys,
                     void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Tuning of the segmented sort (the local sort and the merge), process-wide.
+ * The project's autotuner (paper_1803_01237_gb300/autotune.py) measures the
+ * choices per workload shape and sets them here; the sorted output,
+ * splitters and offsets do not depend on them.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    /* Keys alone: the largest segment sorted on chip; a larger one is split
+     * again.  4096 (the default) or 14336 (the largest on-chip class). */
+    uint32_t chip_max_keys;
+    /* 1: a sub-bucket that is split again interpolates its own key range
+     * (gathered by the split that made it) with a digit width giving about
+     * child_bucket_keys keys per sub-bucket; 0 (default): its top varying
+     * byte. */
+    uint32_t child_interp;
+    uint32_t child_bucket_keys;  /* 128 .. 4096 (0 = 384) */
+    uint32_t reserved[5];        /* zero */
+} hss_tuning;
+
+/* Set the tuning (NULL restores the defaults); HSS_ERR_INVALID for a value
+ * out of range.  Calls already enqueued keep the tuning they started with. */
+int hss_set_tuning(const hss_tuning* t);
+int hss_get_tuning(hss_tuning* t);
 
 /* Kernels launched by this library in this process so far. */
 uint64_t hss_kernel_launch_count(void);

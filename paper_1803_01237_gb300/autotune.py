@@ -1,0 +1,192 @@
+"""Autotuner of the HSS sort on this GPU (project-written).
+
+For a workload shape it measures a small space of choices with CUDA events
+on a synthetic input of that shape and keeps the fastest:
+
+  oversample s       probes per processor per round (Sec. 6 draws s p per
+                     round; Sec. 7.2 uses 5): larger s means fewer rounds but
+                     a larger sample to sort and rank each round.  The output
+                     is then the HSS result of that s (bit-exact with the
+                     oracle run with the same s);
+  histogram form     probe-side searches or the staged form in the rounds
+                     whose probes share one interval (HSS_FLAG_HIST_*);
+  round driver       the device-driven graph loop or the host loop
+                     (HSS_FLAG_HOST_ROUNDS);
+  sort tiling        the largest segment sorted on chip before another split
+                     (4096 or 14336 keys: the CTA shape of the on-chip
+                     sort), and whether a sub-bucket split again interpolates
+                     its own key range with a digit width aimed at a given
+                     number of keys per sub-bucket (hss_set_tuning).
+
+Results are cached in a JSON file keyed by (GPU name, key type, log2 N,
+log2 p, input kind); the cache path is $HSS_TUNING_CACHE or
+~/.cache/hss_gb300/tuning.json.  The batched form is tuned the same way on a
+subset of the batch's jobs (tune_batch).
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import math
+import os
+import threading
+from dataclasses import asdict, dataclass
+
+import numpy as np
+
+from . import hss, inputs
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "hss_gb300", "tuning.json")
+
+
+@dataclass(frozen=True)
+class Choice:
+    oversample: float = 5.0
+    hist_flags: int = 0            # 0 auto, hss.FLAG_HIST_PROBE or hss.FLAG_HIST_STAGED
+    host_rounds: int = 0           # 1: hss.FLAG_HOST_ROUNDS
+    chip_max_keys: int = 4096
+    child_interp: int = 0
+    child_bucket_keys: int = 384
+
+    def flags(self) -> int:
+        return int(self.hist_flags) | (hss.FLAG_HOST_ROUNDS if self.host_rounds else 0)
+
+    def apply(self):
+        """Set the process-wide sort tiling; returns (oversample, flags) for the calls."""
+        hss.set_tuning(self.chip_max_keys, self.child_interp, self.child_bucket_keys)
+        return float(self.oversample), self.flags()
+
+
+def default_space(p: int):
+    """Candidates: oversampling and tiling first (the largest effects), then
+    the histogram form and the round driver around the best of those."""
+    over = [3.0, 5.0, 8.0, 12.0]
+    tiles = [(4096, 0, 384), (14336, 0, 384), (4096, 1, 384), (4096, 1, 768)]
+    return over, tiles
+
+
+def gpu_name() -> str:
+    import torch
+    return torch.cuda.get_device_name(torch.cuda.current_device())
+
+
+def cache_key(N: int, p: int, key_type: str, kind: str) -> str:
+    return f"{gpu_name()}|{key_type}|n{int(math.log2(max(N, 1)))}|p{int(math.log2(max(p, 1)))}|{kind}"
+
+
+class Tuner:
+    def __init__(self, cache_path: str | None = None):
+        self.path = cache_path or os.environ.get("HSS_TUNING_CACHE", DEFAULT_CACHE)
+        self._lock = threading.Lock()
+        self.cache = {}
+        if os.path.exists(self.path):
+            try:
+                with open(self.path) as f:
+                    self.cache = json.load(f)
+            except (OSError, ValueError):
+                self.cache = {}
+
+    def save(self):
+        os.makedirs(os.path.dirname(self.path) or ".", exist_ok=True)
+        tmp = f"{self.path}.tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(self.cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, self.path)
+
+    # --- measurement -------------------------------------------------------
+    @staticmethod
+    def _time_sort(keys, p, eps, seed, choice: Choice, trials: int, key_type: str):
+        import torch
+        s, flags = choice.apply()
+        out = torch.empty_like(keys)
+        hss.sort(keys, p, eps, seed, oversample=s, flags=flags, key_type=key_type, out=out)  # warm-up, graph build
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(trials):
+            r = hss.sort(keys, p, eps, seed, oversample=s, flags=flags, key_type=key_type, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / trials, r.rounds
+
+    def tune(self, N: int, p: int, eps: float = 0.02, key_type: str = "u64", kind: str = "uniform", sample=None,
+             seed: int = 1, trials: int = 3, space=None, force: bool = False) -> Choice:
+        """The fastest Choice for sorting N keys on p processors (measured on
+        `sample` -- a device tensor of N keys -- or on a synthetic input of
+        `kind`), from the cache when present."""
+        import torch
+        key = cache_key(N, p, key_type, kind)
+        with self._lock:
+            if not force and key in self.cache:
+                return Choice(**self.cache[key]["choice"])
+        if sample is None:
+            gen = inputs.SCALE_DISTRIBUTIONS.get(kind, inputs.uniform)
+            raw = gen(N, seed)
+            sample = torch.from_numpy(raw.view(np.int64)).cuda()
+        over, tiles = space or default_space(p)
+        results = []
+        try:
+            # stage 1: oversampling x tiling with the default histogram form and driver
+            for s, (cm, ci, ck) in itertools.product(over, tiles):
+                c = Choice(oversample=s, chip_max_keys=cm, child_interp=ci, child_bucket_keys=ck)
+                ms, rounds = self._time_sort(sample, p, eps, seed, c, trials, key_type)
+                results.append((ms, rounds, c))
+            best = min(results, key=lambda r: r[0])[2]
+            # stage 2: histogram form and round driver around the best
+            for hf, hr in ((hss.FLAG_HIST_PROBE, 0), (hss.FLAG_HIST_STAGED, 0), (0, 1)):
+                c = Choice(**{**asdict(best), "hist_flags": hf, "host_rounds": hr})
+                ms, rounds = self._time_sort(sample, p, eps, seed, c, trials, key_type)
+                results.append((ms, rounds, c))
+        finally:
+            hss.reset_tuning()
+        ms, rounds, best = min(results, key=lambda r: r[0])
+        default = [r for r in results if r[2] == Choice()]
+        rec = {"choice": asdict(best), "ms": ms, "rounds": rounds,
+               "default_ms": default[0][0] if default else None,
+               "measured": [{"choice": asdict(c), "ms": m, "rounds": r} for m, r, c in results]}
+        with self._lock:
+            self.cache[key] = rec
+            self.save()
+        return best
+
+    def tune_batch(self, keys, sizes, ps, eps: float = 0.05, seed: int = 1, key_type: str = "i64",
+                   kind: str = "batch", trials: int = 2, max_jobs: int = 512, force: bool = False) -> Choice:
+        """The fastest Choice (oversampling and tiling) for a batch, measured
+        on up to max_jobs of its jobs (every k-th job)."""
+        import torch
+        n_tot = int(np.sum(sizes))
+        key = f"{gpu_name()}|{key_type}|batch{len(sizes)}|n{int(math.log2(max(n_tot, 1)))}|{kind}"
+        with self._lock:
+            if not force and key in self.cache:
+                return Choice(**self.cache[key]["choice"])
+        step = max(1, len(sizes) // max_jobs)
+        offs = np.concatenate([[0], np.cumsum(sizes)])
+        pick = list(range(0, len(sizes), step))
+        sub = torch.cat([keys[int(offs[j]):int(offs[j + 1])] for j in pick])
+        ssz = [int(sizes[j]) for j in pick]
+        sps = [int(ps[j]) for j in pick]
+        over, tiles = default_space(max(sps))
+        results = []
+        try:
+            for s, (cm, ci, ck) in itertools.product(over, tiles[:2]):
+                c = Choice(oversample=s, chip_max_keys=cm, child_interp=ci, child_bucket_keys=ck)
+                so, _ = c.apply()
+                out = torch.empty_like(sub)
+                hss.sort_batch(sub, ssz, sps, eps, seed, oversample=so, key_type=key_type, out=out)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(trials):
+                    r = hss.sort_batch(sub, ssz, sps, eps, seed, oversample=so, key_type=key_type, out=out)
+                e1.record()
+                torch.cuda.synchronize()
+                results.append((e0.elapsed_time(e1) / trials, float(np.mean(r.job_rounds)), c))
+        finally:
+            hss.reset_tuning()
+        ms, rounds, best = min(results, key=lambda r: r[0])
+        rec = {"choice": asdict(best), "ms": ms, "mean_rounds": rounds, "jobs_measured": len(pick),
+               "measured": [{"choice": asdict(c), "ms": m, "mean_rounds": r} for m, r, c in results]}
+        with self._lock:
+            self.cache[key] = rec
+            self.save()
+        return best

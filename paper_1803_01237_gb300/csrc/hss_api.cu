@@ -204,11 +204,46 @@ static int read_dev_err(uint32_t* d_err, cudaStream_t st) {
     return HSS_OK;
 }
 
+// Host buffers of hss_sort_host: the copies run on a second stream in
+// chunks, overlapping the local sort (input, a group of processors at a time)
+// and the merge (output, a group of buckets at a time).
+struct HostIO {
+    const void* h_keys;
+    const uint32_t* h_payload;
+    void* h_keys_out;
+    uint32_t* h_payload_out;
+    uint64_t* h_offsets;  // filled before the merge (the output copies need them)
+    cudaStream_t cs;      // copy stream
+    cudaEvent_t ev[2 * 64];
+    uint32_t groups;      // chunks each way
+};
+
+static std::mutex g_io_mu;
+static std::mutex g_io_call_mu[256];  // one hss_sort_host at a time per device (they share the copy stream)
+static cudaStream_t g_io_stream[256] = {};
+static cudaEvent_t g_io_events[256][2 * 64] = {};
+
+// Copy stream and events of the current device (created once).
+static int io_resources(cudaStream_t* cs, cudaEvent_t** ev, int* dev_out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return HSS_ERR_CUDA;
+    *dev_out = dev;
+    std::lock_guard<std::mutex> lock(g_io_mu);
+    if (!g_io_stream[dev]) {
+        if (cudaStreamCreateWithFlags(&g_io_stream[dev], cudaStreamNonBlocking) != cudaSuccess) return HSS_ERR_CUDA;
+        for (auto& e : g_io_events[dev])
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return HSS_ERR_CUDA;
+    }
+    *cs = g_io_stream[dev];
+    *ev = g_io_events[dev];
+    return HSS_OK;
+}
+
 // Core of hss_partition / hss_sort.
 static int run_path(const void* d_keys, const uint32_t* d_payload, int key_type, uint64_t N, const hss_params* prm,
                     void* d_keys_out, uint32_t* d_payload_out, hss_cut* d_splitters, uint64_t* d_offsets,
                     void* d_work, size_t work_bytes, hss_stats* h_stats, cudaStream_t st, bool sort,
-                    const void* d_prop = nullptr, uint32_t nprop = 0) {
+                    const void* d_prop = nullptr, uint32_t nprop = 0, HostIO* hio = nullptr) {
     const uint64_t mark = g_launches.load();
     if (h_stats) std::memset(h_stats, 0, sizeof(*h_stats));
     if (!params_ok(prm) || (key_type != HSS_KEY_U64 && key_type != HSS_KEY_I64) || N >= kMaxN) return HSS_ERR_INVALID;
@@ -246,9 +281,31 @@ static int run_path(const void* d_keys, const uint32_t* d_payload, int key_type,
     // Local sort (Sec. 5): order-preserving bits into keysA.  With a single
     // processor the locally sorted segment is already the output.
     const bool single = sort && p == 1;
-    if (segsort((const uint64_t*)d_keys, single ? (uint64_t*)d_keys_out : keysA, keysB, d_payload,
-                single ? d_payload_out : payA, payB, N, p, seg_off, i64, single && i64, sws, st, &stime) != cudaSuccess)
+    if (hio) {
+        // Input in chunks of whole processors: chunk g is copied on the copy
+        // stream, and its processors are sorted as soon as it has landed.
+        const uint32_t G = hio->groups;
+        for (uint32_t g = 0; g < G; ++g) {
+            const uint64_t s0 = (uint64_t)g * p / G, s1 = (uint64_t)(g + 1) * p / G;
+            const uint64_t a = (uint64_t)(((unsigned __int128)s0 * N) / p), b = (uint64_t)(((unsigned __int128)s1 * N) / p);
+            if (b > a && cudaMemcpyAsync((uint64_t*)d_keys + a, (const uint64_t*)hio->h_keys + a, (b - a) * 8,
+                                         cudaMemcpyHostToDevice, hio->cs) != cudaSuccess)
+                return HSS_ERR_CUDA;
+            if (pay && b > a && cudaMemcpyAsync((uint32_t*)d_payload + a, hio->h_payload + a, (b - a) * 4,
+                                                cudaMemcpyHostToDevice, hio->cs) != cudaSuccess)
+                return HSS_ERR_CUDA;
+            if (cudaEventRecord(hio->ev[g], hio->cs) != cudaSuccess) return HSS_ERR_CUDA;
+            if (cudaStreamWaitEvent(st, hio->ev[g], 0) != cudaSuccess) return HSS_ERR_CUDA;
+            if (s1 > s0 && segsort((const uint64_t*)d_keys, single ? (uint64_t*)d_keys_out : keysA, keysB, d_payload,
+                                   single ? d_payload_out : payA, payB, b - a, s1 - s0, seg_off + s0, i64, single && i64,
+                                   sws, st, &stime) != cudaSuccess)
+                return HSS_ERR_CUDA;
+        }
+    } else if (segsort((const uint64_t*)d_keys, single ? (uint64_t*)d_keys_out : keysA, keysB, d_payload,
+                       single ? d_payload_out : payA, payB, N, p, seg_off, i64, single && i64, sws, st, &stime) !=
+               cudaSuccess) {
         return HSS_ERR_CUDA;
+    }
     tm.mark(HSS_PHASE_LOCAL_SORT);
 
     // Splitter rounds (Sec. 4.2.2).
@@ -274,9 +331,36 @@ static int run_path(const void* d_keys, const uint32_t* d_payload, int key_type,
             // The keys of bucket b lie between splitters b and b+1, so the first
             // split of each bucket spreads that key range over 256 sub-buckets.
             if (bucket_hints(rws, keysA, seg_off, p, st) != cudaSuccess) return HSS_ERR_CUDA;
-            if (segsort(keysB, (uint64_t*)d_keys_out, keysA, payB, d_payload_out, payA, N, p, d_offsets, false, i64, sws,
-                        st, &stime, rws.bucket_lo, rws.bucket_mult) != cudaSuccess)
+            if (hio) {
+                // Output in chunks of whole buckets: chunk g goes back on the
+                // copy stream while the next chunk merges.  The bucket bounds
+                // come first (the host needs them to cut the chunks).
+                if (cudaMemcpyAsync(hio->h_offsets, d_offsets, (uint64_t)(p + 1) * 8, cudaMemcpyDeviceToHost, st) !=
+                        cudaSuccess ||
+                    cudaStreamSynchronize(st) != cudaSuccess)
+                    return HSS_ERR_CUDA;
+                const uint32_t G = hio->groups;
+                for (uint32_t g = 0; g < G; ++g) {
+                    const uint64_t b0 = (uint64_t)g * p / G, b1 = (uint64_t)(g + 1) * p / G;
+                    const uint64_t a = hio->h_offsets[b0], b = hio->h_offsets[b1];
+                    if (b1 > b0 && b > a &&
+                        segsort(keysB, (uint64_t*)d_keys_out, keysA, payB, d_payload_out, payA, b - a, b1 - b0,
+                                d_offsets + b0, false, i64, sws, st, &stime, rws.bucket_lo + b0,
+                                rws.bucket_mult + b0) != cudaSuccess)
+                        return HSS_ERR_CUDA;
+                    if (cudaEventRecord(hio->ev[64 + g], st) != cudaSuccess) return HSS_ERR_CUDA;
+                    if (cudaStreamWaitEvent(hio->cs, hio->ev[64 + g], 0) != cudaSuccess) return HSS_ERR_CUDA;
+                    if (b > a && cudaMemcpyAsync((uint64_t*)hio->h_keys_out + a, (uint64_t*)d_keys_out + a, (b - a) * 8,
+                                                 cudaMemcpyDeviceToHost, hio->cs) != cudaSuccess)
+                        return HSS_ERR_CUDA;
+                    if (pay && b > a && cudaMemcpyAsync(hio->h_payload_out + a, d_payload_out + a, (b - a) * 4,
+                                                        cudaMemcpyDeviceToHost, hio->cs) != cudaSuccess)
+                        return HSS_ERR_CUDA;
+                }
+            } else if (segsort(keysB, (uint64_t*)d_keys_out, keysA, payB, d_payload_out, payA, N, p, d_offsets, false, i64,
+                               sws, st, &stime, rws.bucket_lo, rws.bucket_mult) != cudaSuccess) {
                 return HSS_ERR_CUDA;
+            }
             tm.mark(HSS_PHASE_MERGE);
         }
     }
@@ -451,18 +535,40 @@ int hss_sort_host(const void* h_keys, const uint32_t* h_payload, int key_type, u
     uint32_t* iop = pay ? at<uint32_t>(d_work, L.io_pay) : nullptr;
     hss_cut* spl = at<hss_cut>(d_work, L.io_spl);
     uint64_t* off = at<uint64_t>(d_work, L.io_off);
-    if (N > 0 && cudaMemcpyAsync(io, h_keys, N * 8, cudaMemcpyHostToDevice, st) != cudaSuccess) return HSS_ERR_CUDA;
-    if (pay && N > 0 && cudaMemcpyAsync(iop, h_payload, N * 4, cudaMemcpyHostToDevice, st) != cudaSuccess) return HSS_ERR_CUDA;
+    HostIO hio{};
+    cudaEvent_t* ev = nullptr;
+    int dev = 0;
+    if (io_resources(&hio.cs, &ev, &dev) != HSS_OK) return HSS_ERR_CUDA;
+    std::lock_guard<std::mutex> call_lock(g_io_call_mu[dev]);
+    for (int i = 0; i < 2 * 64; ++i) hio.ev[i] = ev[i];
+    hio.h_keys = h_keys;
+    hio.h_payload = h_payload;
+    hio.h_keys_out = h_keys_out;
+    hio.h_payload_out = h_payload_out;
+    hio.h_offsets = h_offsets;
+    // chunks of at least 16 Mi keys, at most 32 and one per processor
+    hio.groups = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>({32, (uint64_t)p, N >> 24}));
+    // the copy stream starts after the work already on the caller's stream
+    if (cudaEventRecord(hio.ev[127], st) != cudaSuccess || cudaStreamWaitEvent(hio.cs, hio.ev[127], 0) != cudaSuccess)
+        return HSS_ERR_CUDA;
     // run with the SORT layout inside the same workspace (it is a prefix of SORT_HOST's)
-    int rc = run_path(io, iop, key_type, N, prm, io, iop, spl, off, d_work, work_bytes, h_stats, st, true);
-    if (rc == HSS_ERR_CUDA || rc == HSS_ERR_INVALID || rc == HSS_ERR_WORKSPACE) return rc;
-    if (N > 0 && cudaMemcpyAsync(h_keys_out, io, N * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return HSS_ERR_CUDA;
-    if (pay && N > 0 && cudaMemcpyAsync(h_payload_out, iop, N * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return HSS_ERR_CUDA;
+    int rc = run_path(io, iop, key_type, N, prm, io, iop, spl, off, d_work, work_bytes, h_stats, st, true, nullptr, 0,
+                      &hio);
+    if (rc == HSS_ERR_CUDA || rc == HSS_ERR_INVALID || rc == HSS_ERR_WORKSPACE) {
+        cudaStreamSynchronize(hio.cs);
+        return rc;
+    }
+    if (p == 1) {  // no merge: the locally sorted keys are the output
+        if (N > 0 && cudaMemcpyAsync(h_keys_out, io, N * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return HSS_ERR_CUDA;
+        if (pay && N > 0 && cudaMemcpyAsync(h_payload_out, iop, N * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return HSS_ERR_CUDA;
+        if (cudaMemcpyAsync(h_offsets, off, (uint64_t)(p + 1) * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return HSS_ERR_CUDA;
+    }
     if (p > 1 && h_splitters &&
         cudaMemcpyAsync(h_splitters, spl, (uint64_t)(p - 1) * sizeof(hss_cut), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return HSS_ERR_CUDA;
-    if (cudaMemcpyAsync(h_offsets, off, (uint64_t)(p + 1) * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return HSS_ERR_CUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return HSS_ERR_CUDA;
+    if (cudaStreamSynchronize(hio.cs) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return HSS_ERR_CUDA;
     return rc;
 }
 
@@ -498,6 +604,14 @@ int hss_sample_words(uint64_t seed, uint32_t seg, uint32_t round, uint32_t spos0
     if (count > 0 && !d_out) return HSS_ERR_INVALID;
     if ((uint64_t)spos0 + count > (1ull << 32)) return HSS_ERR_INVALID;
     if (sample_words_launch(seed, seg, round, spos0, count, d_out, (cudaStream_t)stream) != cudaSuccess) return HSS_ERR_CUDA;
+    return HSS_OK;
+}
+
+int hss_set_tuning(const hss_tuning* t) { return set_tuning(t); }
+
+int hss_get_tuning(hss_tuning* t) {
+    if (!t) return HSS_ERR_INVALID;
+    get_tuning(t);
     return HSS_OK;
 }
 

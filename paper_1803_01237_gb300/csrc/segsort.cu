@@ -25,13 +25,46 @@
 #include "segsort.cuh"
 
 #include <algorithm>
+#include <atomic>
 
 namespace hss {
 
 __host__ __device__ static inline uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 static inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-static uint64_t max_large_of(uint64_t N) { return std::max<uint64_t>(1, N / (kSmallCap + 1)); }
+// Process-wide tuning (hss_set_tuning).
+static std::atomic<uint32_t> g_chip_max{(uint32_t)kC1Cap};
+static std::atomic<uint32_t> g_child_interp{0u};
+static std::atomic<uint32_t> g_child_keys{384u};
+
+int set_tuning(const hss_tuning* t) {
+    if (!t) {
+        g_chip_max = (uint32_t)kC1Cap;
+        g_child_interp = 0u;
+        g_child_keys = 384u;
+        return HSS_OK;
+    }
+    const uint32_t cm = t->chip_max_keys ? t->chip_max_keys : (uint32_t)kC1Cap;
+    const uint32_t ck = t->child_bucket_keys ? t->child_bucket_keys : 384u;
+    if ((cm != (uint32_t)kC1Cap && cm != (uint32_t)kSmallCap) || t->child_interp > 1u || ck < 128u || ck > 4096u)
+        return HSS_ERR_INVALID;
+    for (uint32_t r : t->reserved)
+        if (r) return HSS_ERR_INVALID;
+    g_chip_max = cm;
+    g_child_interp = t->child_interp;
+    g_child_keys = ck;
+    return HSS_OK;
+}
+void get_tuning(hss_tuning* t) {
+    *t = hss_tuning{};
+    t->chip_max_keys = g_chip_max;
+    t->child_interp = g_child_interp;
+    t->child_bucket_keys = g_child_keys;
+}
+
+// Large segments of a level hold more than kC1Cap keys (keys alone split above
+// the middle on-chip class), so a level has at most N / (kC1Cap + 1) of them.
+static uint64_t max_large_of(uint64_t N) { return std::max<uint64_t>(1, N / (kC1Cap + 1)); }
 
 struct WsDims {
     uint64_t ml, list, tiles;
@@ -55,6 +88,8 @@ size_t segsort_ws_bytes(uint64_t N, uint64_t nseg) {
     b += 4 * align_up(d.ml * 4, 256);                                 // msd_shift x2, spec, direct
     b += 2 * align_up(d.ml * 8, 256);                                 // msd_base, msd_mult
     b += 4 * align_up(d.ml * kRadix * 8, 256);                        // sub_lo/hi x2
+    b += 6 * align_up(d.ml * kRadix * 8, 256);                        // cmin/cmax/cmult x2
+    b += align_up(d.ml * 8 * 4, 256) + align_up(d.ml * 4, 256);       // large_mask, any_large
     b += align_up(d.tiles * kRadix * 4, 256);                         // tile_off
     b += align_up(64 * 4, 256);                                       // counters
     b += 8 * align_up(d.list * 4, 256);                               // class lists, fallback, slow lists
@@ -86,7 +121,12 @@ SegSortWs segsort_ws_carve(void* base, uint64_t N, uint64_t nseg, uint32_t* err)
     for (int i = 0; i < 2; ++i) {
         w.sub_lo[i] = (uint64_t*)take(d.ml * kRadix * 8);
         w.sub_hi[i] = (uint64_t*)take(d.ml * kRadix * 8);
+        w.cmin[i] = (uint64_t*)take(d.ml * kRadix * 8);
+        w.cmax[i] = (uint64_t*)take(d.ml * kRadix * 8);
+        w.cmult[i] = (uint64_t*)take(d.ml * kRadix * 8);
     }
+    w.large_mask = (uint32_t*)take(d.ml * 8 * 4);
+    w.any_large = (uint32_t*)take(d.ml * 4);
     w.tile_off = (uint32_t*)take(d.tiles * kRadix * 4);
     w.counters = (uint32_t*)take(64 * 4);
     for (int i = 0; i < 3; ++i) w.list[i] = (uint32_t*)take(d.list * 4);
@@ -1108,7 +1148,10 @@ struct PlanV {
     unsigned long long keys;
 };
 
-__device__ __forceinline__ PlanV plan_item(const uint64_t* seg_lo, const uint64_t* seg_hi, uint64_t nseg, uint64_t s) {
+// chip_max: the largest segment sorted on chip at this level (kSmallCap, or
+// kC1Cap to split larger ones again instead of the largest on-chip class).
+__device__ __forceinline__ PlanV plan_item(const uint64_t* seg_lo, const uint64_t* seg_hi, uint64_t nseg, uint64_t s,
+                                           uint32_t chip_max) {
     PlanV v = {{0, 0, 0, 0, 0}, 0ull};
     if (s < nseg) {
         const uint64_t n = seg_hi[s] - seg_lo[s];
@@ -1117,7 +1160,7 @@ __device__ __forceinline__ PlanV plan_item(const uint64_t* seg_lo, const uint64_
             v.c[0] = 1;
         } else if (n <= (uint64_t)kC1Cap) {
             v.c[1] = 1;
-        } else if (n <= (uint64_t)kSmallCap) {
+        } else if (n <= (uint64_t)chip_max) {
             v.c[2] = 1;
         } else if (n >= kMaxSegKeys) {
             // too large for the split's 30-bit counts: left unsorted, reported by k_plan_write
@@ -1180,8 +1223,8 @@ __device__ __forceinline__ PlanV blk_load(const uint32_t* blk, uint32_t i) {
 }
 
 __global__ __launch_bounds__(1024) void k_plan_count(const uint64_t* __restrict__ seg_lo, const uint64_t* __restrict__ seg_hi,
-                                                     uint64_t nseg, uint32_t* __restrict__ blk) {
-    PlanV v = plan_item(seg_lo, seg_hi, nseg, (uint64_t)blockIdx.x * 1024 + threadIdx.x), tot;
+                                                     uint64_t nseg, uint32_t* __restrict__ blk, uint32_t chip_max) {
+    PlanV v = plan_item(seg_lo, seg_hi, nseg, (uint64_t)blockIdx.x * 1024 + threadIdx.x, chip_max), tot;
     plan_scan(v, tot);
     if (threadIdx.x == 0) blk_store(blk, blockIdx.x, tot);
 }
@@ -1223,9 +1266,9 @@ __global__ __launch_bounds__(1024) void k_plan_write(const uint64_t* __restrict_
                                                      uint32_t* __restrict__ large_id, uint32_t* __restrict__ large_seg,
                                                      uint32_t* __restrict__ list0, uint32_t* __restrict__ list1,
                                                      uint32_t* __restrict__ list2, uint32_t* __restrict__ err,
-                                                     uint32_t* __restrict__ tile_seg) {
+                                                     uint32_t* __restrict__ tile_seg, uint32_t chip_max) {
     const uint64_t s = (uint64_t)blockIdx.x * 1024 + threadIdx.x;
-    const PlanV item = plan_item(seg_lo, seg_hi, nseg, s);
+    const PlanV item = plan_item(seg_lo, seg_hi, nseg, s, chip_max);
     if (s < nseg && seg_hi[s] - seg_lo[s] >= kMaxSegKeys) atomicOr(err, kDevErrSize);
     PlanV v = item, tot;
     plan_scan(v, tot);
@@ -1273,6 +1316,7 @@ __global__ __launch_bounds__(256) void k_tile_stats(const uint64_t* __restrict__
                                                     const uint32_t* __restrict__ large_id, uint16_t* __restrict__ tile_hist,
                                                     unsigned long long* __restrict__ vor, unsigned long long* __restrict__ vand,
                                                     const uint64_t* __restrict__ hint_lo, const uint64_t* __restrict__ hint_mult,
+                                                    const uint64_t* __restrict__ hint_hi,
                                                     const uint32_t* __restrict__ prev_shift, uint32_t* __restrict__ spec_out,
                                                     uint64_t flip_in) {
     __shared__ uint32_t s_h[kRadix];
@@ -1288,6 +1332,15 @@ __global__ __launch_bounds__(256) void k_tile_stats(const uint64_t* __restrict__
     const bool win = hint_lo != nullptr;
     const int spec = spec_window(prev_shift, s);
     if (ti == 0 && threadIdx.x == 0) spec_out[id] = (uint32_t)spec;
+    if (win && hint_hi && hint_hi[s] == hint_lo[s]) {
+        // every key of the segment equals the one the parent's split saw: no read
+        if (threadIdx.x == 0) {
+            atomicOr(&vor[id], (unsigned long long)hint_lo[s]);
+            atomicAnd(&vand[id], (unsigned long long)hint_lo[s]);
+        }
+        tile_hist[(uint64_t)t * (2 * kRadix) + threadIdx.x] = (uint16_t)(threadIdx.x == 0 ? b - a : 0);
+        return;
+    }
     const uint64_t hb = win ? hint_lo[s] : 0ull;
     const uint64_t hm = win ? hint_mult[s] : 0ull;
     const int sh = 8 * spec;
@@ -1362,7 +1415,9 @@ __global__ __launch_bounds__(256) void k_msd_prep(const uint64_t* __restrict__ s
                                                   uint64_t* __restrict__ msd_mult, uint32_t* __restrict__ msd_shift,
                                                   const uint32_t* __restrict__ spec, uint32_t* __restrict__ direct,
                                                   uint64_t* __restrict__ sub_lo, uint64_t* __restrict__ sub_hi,
-                                                  uint32_t* __restrict__ tile_off) {
+                                                  uint32_t* __restrict__ tile_off, uint32_t chip_max,
+                                                  uint32_t* __restrict__ large_mask, uint32_t* __restrict__ any_large,
+                                                  uint64_t* __restrict__ cmin, uint64_t* __restrict__ cmax) {
     __shared__ uint32_t s_c[kRadix], s_x[kRadix], s_warp[32];
     const uint32_t id = blockIdx.x;
     if (id >= counters[19]) return;
@@ -1392,6 +1447,16 @@ __global__ __launch_bounds__(256) void k_msd_prep(const uint64_t* __restrict__ s
     const uint32_t x = s_x[d];
     sub_lo[(uint64_t)id * kRadix + d] = dir ? lo : lo + x;
     sub_hi[(uint64_t)id * kRadix + d] = dir ? lo : lo + x + total;
+    // sub-buckets that the next level splits again: the split pass gathers
+    // their smallest and largest key
+    const bool large = !dir && total > chip_max;  // chip_max = ~0: nothing gathered
+    const uint32_t bal = __ballot_sync(0xffffffffu, large);
+    if ((d & 31) == 0) large_mask[(uint64_t)id * 8 + (d >> 5)] = bal;
+    if (d == 0) any_large[id] = 0u;
+    cmin[(uint64_t)id * kRadix + d] = ~0ull;
+    cmax[(uint64_t)id * kRadix + d] = 0ull;
+    __syncthreads();
+    if (bal && (d & 31) == 0) atomicOr(&any_large[id], 1u);
     uint32_t run = x;
     for (uint32_t t = t0; t < t1; ++t) {
         tile_off[(uint64_t)t * kRadix + d] = run;
@@ -1428,6 +1493,10 @@ struct SplitArgs {
     const uint64_t* msd_base;
     const uint64_t* msd_mult;
     const uint32_t* direct;
+    const uint32_t* large_mask;  // [large id][8] sub-buckets that the next level splits again
+    const uint32_t* any_large;
+    uint64_t* cmin;              // their smallest and largest key (atomics)
+    uint64_t* cmax;
     uint32_t* err;
     uint64_t flip_in;
     uint64_t flip_out;
@@ -1443,6 +1512,8 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
     __shared__ uint32_t s_total[kRadix], s_start[kRadix];
     __shared__ uint64_t s_gbase[kRadix];
     __shared__ uint32_t s_warp[32];
+    __shared__ uint64_t s_mn[kRadix], s_mx[kRadix];
+    __shared__ uint32_t s_mask[8];
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const uint32_t total_tiles = A.tile_start[A.nseg];
@@ -1462,6 +1533,14 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
     uint64_t* kout = dir ? A.kfinal : A.kout;
     uint32_t* pout = dir ? A.pfinal : A.pout;
     const uint64_t flip_out = dir ? A.flip_out : 0ull;
+    // A segment of one key value already in place in the output (every
+    // second level reads the output buffer) needs no copy at all.
+    if (dir && A.kin == A.kfinal && flip_out == 0ull && (!PAY || A.pin == A.pfinal)) return;
+    const bool gather = A.any_large[id] != 0u;  // some sub-bucket is split again: note its key range
+    if (gather) {
+        if (tid < kRadix) { s_mn[tid] = ~0ull; s_mx[tid] = 0ull; }
+        if (tid < 8) s_mask[tid] = A.large_mask[(uint64_t)id * 8 + tid];
+    }
 
     uint64_t key[kOsItems];
     uint32_t pay[kOsItems];
@@ -1542,6 +1621,69 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
         kout[dst] = k ^ flip_out;
         if (PAY) pout[dst] = s_pay[j];
     }
+    if (gather) {  // uniform per CTA
+        // Smallest and largest key of every sub-bucket the next level splits
+        // again (its digit range there).  The staged keys come in digit runs,
+        // so a warp usually reduces one run and issues one atomic pair.
+        for (uint32_t j0 = (uint32_t)w * 32; j0 < count; j0 += kOsThreads) {
+            const uint32_t j = j0 + lane;
+            const bool v = j < count;
+            const uint64_t k = v ? s_keys[j] : 0ull;
+            const uint32_t d = v ? (uint32_t)s_dg[j] : 0x1ffu;
+            const bool flagged = v && ((s_mask[d >> 5] >> (d & 31)) & 1u);
+            const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+            if (__all_sync(0xffffffffu, d == d0)) {
+                if (flagged) {  // the whole warp: one digit
+                    uint64_t mn = k, mx = k;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        mn = min(mn, (uint64_t)__shfl_xor_sync(0xffffffffu, mn, o));
+                        mx = max(mx, (uint64_t)__shfl_xor_sync(0xffffffffu, mx, o));
+                    }
+                    if (lane == 0) {
+                        if (mn < s_mn[d]) atomicMin((unsigned long long*)&s_mn[d], (unsigned long long)mn);
+                        if (mx > s_mx[d]) atomicMax((unsigned long long*)&s_mx[d], (unsigned long long)mx);
+                    }
+                }
+            } else if (flagged) {
+                if (k < s_mn[d]) atomicMin((unsigned long long*)&s_mn[d], (unsigned long long)k);
+                if (k > s_mx[d]) atomicMax((unsigned long long*)&s_mx[d], (unsigned long long)k);
+            }
+        }
+        __syncthreads();
+        if (tid < kRadix && ((s_mask[tid >> 5] >> (tid & 31)) & 1u) && s_mx[tid] >= s_mn[tid]) {
+            atomicMin((unsigned long long*)&A.cmin[(uint64_t)id * kRadix + tid], (unsigned long long)s_mn[tid]);
+            atomicMax((unsigned long long*)&A.cmax[(uint64_t)id * kRadix + tid], (unsigned long long)s_mx[tid]);
+        }
+    }
+}
+
+// The digit of the next split of every sub-bucket that will be split again:
+// its own key range [min, max] interpolated onto 2^b sub-buckets, b chosen so
+// that they hold about `target` keys on average; a sub-bucket of one key
+// value keeps multiplier 0.  An interpolated split into 2^b sub-buckets
+// narrows the key range by a factor 2^b - 1 >= 2^(b-1) whatever the keys, so
+// b is at least ceil(B / levels) + 1 for a range of B bits and `levels`
+// levels left before the depth limit (one kept for the copy of single-valued
+// sub-buckets): clustered keys with a few outliers then still end within the
+// limit (each level keeps B / levels from growing).
+__global__ void k_child_hints(uint32_t n_children, const uint64_t* __restrict__ sub_lo, const uint64_t* __restrict__ sub_hi,
+                              const uint64_t* __restrict__ cmin, const uint64_t* __restrict__ cmax,
+                              uint64_t* __restrict__ cmult, uint32_t chip_max, uint32_t target, uint32_t child_depth) {
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_children) return;
+    const uint64_t n = sub_hi[c] - sub_lo[c];
+    if (n <= chip_max) return;
+    const uint64_t lo = cmin[c], hi = cmax[c];
+    if (hi < lo) return;  // no key seen (cannot happen for a non-empty sub-bucket)
+    const uint32_t want = (uint32_t)min((n + target - 1) / target, (uint64_t)kRadix);  // sub-buckets wanted
+    uint32_t b = 1;
+    while (b < 8 && (1u << b) < want) ++b;
+    const int levels = kMaxDepth - (int)child_depth - 1;
+    const uint32_t B = hi > lo ? 64u - (uint32_t)__clzll((long long)(hi - lo)) : 0u;
+    const uint32_t b_min = levels >= 1 ? min(8u, (B + (uint32_t)levels - 1u) / (uint32_t)levels + 1u) : 8u;
+    b = max(b, b_min);
+    cmult[c] = interp_mult(hi - lo, 1u << b);
 }
 
 __global__ void k_even_offsets(uint64_t* __restrict__ seg_off, uint64_t N, uint64_t p) {
@@ -1645,6 +1787,7 @@ struct Level {
     const uint64_t* hint_lo;
     const uint64_t* hint_mult;
     int depth;
+    const uint64_t* hint_hi = nullptr;  // largest key of each segment, when known
 };
 
 template <bool PAY>
@@ -1654,6 +1797,9 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
                              const uint64_t* hint_lo, const uint64_t* hint_mult) {
     if (N == 0 || nseg == 0) return cudaSuccess;
     const uint64_t fout = flip_out ? kSignBit : 0ull;
+    const uint32_t tune_chip_max = g_chip_max.load();
+    const bool child_interp = g_child_interp.load() != 0u;
+    const uint32_t child_keys = g_child_keys.load();
     cudaError_t e;
     Level L{src, psrc, d_seg_off, d_seg_off + 1, nseg, flip_in ? kSignBit : 0ull, hint_lo, hint_mult, 0};
     if (N <= (uint64_t)kSmallCap) {
@@ -1683,10 +1829,15 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
     for (;;) {
         if (L.nseg > ws.max_list) return cudaErrorInvalidValue;
         const uint32_t nblk = (uint32_t)ceil_div(L.nseg + 1, 1024);
-        HSS_LAUNCH(k_plan_count, nblk, 1024, 0, st, L.seg_lo, L.seg_hi, L.nseg, ws.blk);
+        // Keys alone: by default a segment above the middle on-chip class is
+        // split again (into buckets of about a thousand keys that the
+        // prefetching small classes sort) rather than sorted by the largest
+        // class (tuning.chip_max_keys).
+        const uint32_t chip_max = PAY ? (uint32_t)kSmallCap : tune_chip_max;
+        HSS_LAUNCH(k_plan_count, nblk, 1024, 0, st, L.seg_lo, L.seg_hi, L.nseg, ws.blk, chip_max);
         HSS_LAUNCH(k_plan_scan, 1, 1024, 0, st, nblk, ws.blk, ws.counters);
         HSS_LAUNCH(k_plan_write, nblk, 1024, 0, st, L.seg_lo, L.seg_hi, L.nseg, ws.blk, ws.counters, ws.tile_start,
-                   ws.large_id, ws.large_seg, ws.list[0], ws.list[1], ws.list[2], ws.err, ws.tile_seg);
+                   ws.large_id, ws.large_seg, ws.list[0], ws.list[1], ws.list[2], ws.err, ws.tile_seg, chip_max);
         uint32_t hc[8];
         if ((e = cudaMemcpyAsync(hc, ws.counters + 16, sizeof(hc), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
@@ -1758,13 +1909,14 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
         const int buf = L.depth & 1;
         const uint32_t* prev_shift = L.depth > 0 ? ws.msd_shift[buf ^ 1] : nullptr;
         HSS_LAUNCH(k_tile_stats, tiles, 256, 0, st, L.in, L.seg_lo, L.seg_hi, L.nseg, ws.tile_start, ws.tile_seg, ws.large_id,
-                   ws.tile_hist, ws.vor, ws.vand, L.hint_lo, L.hint_mult, prev_shift, ws.spec, L.flip_in);
+                   ws.tile_hist, ws.vor, ws.vand, L.hint_lo, L.hint_mult, L.hint_hi, prev_shift, ws.spec, L.flip_in);
         if (!L.hint_lo)
             HSS_LAUNCH(k_tile_recount, tiles, 256, 0, st, L.in, L.seg_lo, L.seg_hi, L.nseg, ws.tile_start, ws.tile_seg, ws.large_id,
                        ws.tile_hist, ws.vor, ws.vand, ws.spec, L.flip_in);
         HSS_LAUNCH(k_msd_prep, n_large, 256, 0, st, L.seg_lo, ws.large_seg, ws.counters, ws.tile_start, ws.tile_hist,
                    ws.vor, ws.vand, L.hint_lo, L.hint_mult, ws.msd_base, ws.msd_mult, ws.msd_shift[buf], ws.spec,
-                   ws.direct, ws.sub_lo[buf], ws.sub_hi[buf], ws.tile_off);
+                   ws.direct, ws.sub_lo[buf], ws.sub_hi[buf], ws.tile_off, child_interp ? chip_max : 0xffffffffu,
+                   ws.large_mask, ws.any_large, ws.cmin[buf], ws.cmax[buf]);
         // The split pass: level buffers alternate tmp, dst, tmp, ... after src.
         uint64_t* next = (L.depth & 1) ? dst : tmp;
         uint32_t* pnext = PAY ? ((L.depth & 1) ? pdst : ptmp) : nullptr;
@@ -1775,6 +1927,7 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
         A.tile_start = ws.tile_start; A.tile_seg = ws.tile_seg; A.large_id = ws.large_id;
         A.tile_off = ws.tile_off; A.msd_shift = ws.msd_shift[buf]; A.msd_base = ws.msd_base; A.msd_mult = ws.msd_mult;
         A.direct = ws.direct;
+        A.large_mask = ws.large_mask; A.any_large = ws.any_large; A.cmin = ws.cmin[buf]; A.cmax = ws.cmax[buf];
         A.err = ws.err;
         A.flip_in = L.flip_in; A.flip_out = fout;
         const size_t smem = (size_t)kOsTile * 9 + (PAY ? (size_t)kOsTile * 4 : 0);
@@ -1793,9 +1946,18 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
             timing->n += 1;
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        // Next level: the 256 sub-buckets of every large segment.
-        L = Level{next, pnext, ws.sub_lo[buf], ws.sub_hi[buf], (uint64_t)n_large * kRadix, 0ull, nullptr, nullptr,
-                  L.depth + 1};
+        // Next level: the 256 sub-buckets of every large segment; those split
+        // again interpolate their own key range (gathered by the split).
+        const uint32_t nch = n_large * kRadix;
+        if (child_interp) {
+            HSS_LAUNCH(k_child_hints, (nch + 255) / 256, 256, 0, st, nch, ws.sub_lo[buf], ws.sub_hi[buf], ws.cmin[buf],
+                       ws.cmax[buf], ws.cmult[buf], chip_max, child_keys, (uint32_t)L.depth + 1u);
+            L = Level{next, pnext, ws.sub_lo[buf], ws.sub_hi[buf], (uint64_t)n_large * kRadix, 0ull, ws.cmin[buf],
+                      ws.cmult[buf], L.depth + 1, ws.cmax[buf]};
+        } else {
+            L = Level{next, pnext, ws.sub_lo[buf], ws.sub_hi[buf], (uint64_t)n_large * kRadix, 0ull, nullptr, nullptr,
+                      L.depth + 1};
+        }
     }
 }
 

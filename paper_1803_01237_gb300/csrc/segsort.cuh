@@ -15,7 +15,10 @@ namespace hss {
 
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 256;
-constexpr int kMaxDepth = 8;
+// Levels of the split recursion: byte splits need at most 8 (one per byte of
+// the key) and one more to copy single-valued sub-buckets; interpolated splits
+// of sub-buckets choose their width to finish within the limit.
+constexpr int kMaxDepth = 16;
 
 constexpr int kOsThreads = 256;
 constexpr int kOsWarps = kOsThreads / 32;
@@ -49,6 +52,14 @@ struct SegSortWs {
     uint32_t* direct;      // [max_large] all keys equal: copy to the output
     uint64_t* sub_lo[2];   // [max_large * 256] sub-bucket bounds, double-buffered by depth
     uint64_t* sub_hi[2];
+    // Sub-buckets that will be split again: their smallest and largest key
+    // (gathered by the split pass) and the interpolating digit of their own
+    // split, double-buffered by depth like the bounds.
+    uint64_t* cmin[2];     // [max_large * 256]
+    uint64_t* cmax[2];
+    uint64_t* cmult[2];
+    uint32_t* large_mask;  // [max_large * 8] sub-buckets above the on-chip limit, one bit per digit
+    uint32_t* any_large;   // [max_large]
     uint32_t* tile_off;    // [max_tiles][256] destination of each tile's digit-d keys, relative to its segment
     uint32_t* counters;    // [64]
     uint32_t* list[3];     // [max_list] segments of each on-chip size class
@@ -104,6 +115,10 @@ cudaError_t segsort(const uint64_t* src, uint64_t* dst, uint64_t* tmp,
                     bool flip_in, bool flip_out, const SegSortWs& ws, cudaStream_t st,
                     SegSortTiming* timing, const uint64_t* hint_lo = nullptr,
                     const uint64_t* hint_mult = nullptr);
+
+// Process-wide tuning of the sort (hss_set_tuning / hss_get_tuning).
+int set_tuning(const hss_tuning* t);
+void get_tuning(hss_tuning* t);
 
 // seg_off[s] = floor(s * N / p) for s = 0..p.
 cudaError_t fill_even_offsets(uint64_t* d_seg_off, uint64_t N, uint64_t p, cudaStream_t st);

@@ -458,6 +458,30 @@ def sample_words(seed: int, seg: int, rnd: int, spos0: int, count: int, device="
     return out
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("chip_max_keys", ctypes.c_uint32), ("child_interp", ctypes.c_uint32),
+                ("child_bucket_keys", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
+
+
+def set_tuning(chip_max_keys: int = 0, child_interp: int = 0, child_bucket_keys: int = 0):
+    """hss_set_tuning: process-wide choices of the segmented sort (results unchanged)."""
+    lib = load()
+    t = Tuning(chip_max_keys=int(chip_max_keys), child_interp=int(child_interp),
+               child_bucket_keys=int(child_bucket_keys))
+    _check(lib.hss_set_tuning(ctypes.byref(t)), "hss_set_tuning")
+
+
+def reset_tuning():
+    _check(load().hss_set_tuning(None), "hss_set_tuning")
+
+
+def get_tuning() -> dict:
+    t = Tuning()
+    _check(load().hss_get_tuning(ctypes.byref(t)), "hss_get_tuning")
+    return {"chip_max_keys": t.chip_max_keys, "child_interp": t.child_interp,
+            "child_bucket_keys": t.child_bucket_keys}
+
+
 def launch_count() -> int:
     return int(load().hss_kernel_launch_count())
 

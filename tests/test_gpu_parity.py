@@ -115,6 +115,34 @@ def test_local_sort_deep_recursion_payload(hss, N, p):
     assert np.array_equal(outp.cpu().numpy().view(np.uint32), wantp)
 
 
+def _byte_ladder(seed: int, heavy: int, pair: bool):
+    """A heavy key value (or two adjacent ones) with a few outliers that
+    differ from it in the top bit of each byte: the byte split peels off one
+    outlier per level and reaches the heavy values only after eight levels,
+    then copies them in a ninth."""
+    g = np.random.default_rng(seed)
+    v = np.uint64(g.integers(0, 1 << 63, dtype=np.uint64)) | np.uint64(1)
+    parts = [np.full(heavy, v, dtype=np.uint64)]
+    if pair:
+        parts.append(np.full(heavy, v - np.uint64(1), dtype=np.uint64))
+    for k in range(8):
+        parts.append(np.full(3, v ^ np.uint64(1 << (8 * k + 7)), dtype=np.uint64))
+    keys = np.concatenate(parts)
+    return keys[g.permutation(keys.size)]
+
+
+@pytest.mark.parametrize("heavy,pair,p", [(6000, False, 1), (20000, False, 1), (20000, True, 1), (9000, True, 2)])
+def test_local_sort_byte_ladder_depth(hss, heavy, pair, p):
+    keys = np.concatenate([_byte_ladder(5 + s, heavy, pair) for s in range(p)])
+    out = hss.local_sort(dev(keys), p)
+    assert np.array_equal(host_u64(out), oracle.segment_sort(keys, p))
+    pay = (np.arange(keys.size, dtype=np.uint32) * np.uint32(2654435761)).astype(np.uint32)
+    out, outp = hss.local_sort(dev(keys), p, payload=dev(pay))
+    want, wantp = oracle.segment_sort(keys, p, payload=pay)
+    assert np.array_equal(host_u64(out), want)
+    assert np.array_equal(outp.cpu().numpy().view(np.uint32), wantp)
+
+
 @pytest.mark.parametrize("N,p", [(1 << 18, 1), (1 << 18, 4), (1 << 20, 16), (300007, 5)])
 def test_local_sort_crowded_groups(hss, N, p):
     """Morton keys of a Plummer sphere: the dense core crowds the on-chip
