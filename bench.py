@@ -425,6 +425,31 @@ def run_batch_workload(args):
     rounds_b = float(np.mean(r.job_rounds))
     # plain form: one hss_sort per job (the single-call path), same jobs
     offs = np.concatenate([[0], np.cumsum(sizes)])
+    tuned = None
+    if not args.no_tune:
+        # the project's autotuner picks oversampling and sort tiling on a
+        # subset of the jobs (cached per GPU and batch shape), then the whole
+        # batch is timed with its choice
+        from paper_1803_01237_gb300 import autotune
+        t_tune = time.perf_counter()
+        choice = autotune.Tuner().tune_batch(keys, sizes, ps, eps, seed, key_type="i64")
+        t_tune = time.perf_counter() - t_tune
+        s_t, flags_t = choice.apply()
+        try:
+            hss.sort_batch(keys, sizes, ps, eps, seed, oversample=s_t, flags=flags_t, key_type="i64", out=out)
+            torch.cuda.synchronize(dev)
+            ev0.record()
+            for _ in range(args.steps):
+                rt = hss.sort_batch(keys, sizes, ps, eps, seed, oversample=s_t, flags=flags_t, key_type="i64", out=out)
+            ev1.record()
+            torch.cuda.synchronize(dev)
+        finally:
+            hss.reset_tuning()
+        ms_t = ev0.elapsed_time(ev1) / args.steps
+        tuned = {"choice": choice.__dict__, "jobs_per_s": njobs / (ms_t / 1000.0), "ms_per_step": ms_t,
+                 "mean_rounds_per_job": float(np.mean(rt.job_rounds)), "all_jobs_ok": all(x == 0 for x in rt.job_status),
+                 "tuning_seconds": t_tune,
+                 "note": "oversampling s changes the sample, so the result is the oracle's for that s"}
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     rounds_p = []
@@ -435,8 +460,12 @@ def run_batch_workload(args):
     torch.cuda.synchronize(dev)
     plain_s = time.perf_counter() - t0
     line = {
-        "metric": "batched jobs/s (HSS sort of independent int64 jobs)", "value": njobs / (ms / 1000.0),
-        "unit": "jobs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "metric": "batched jobs/s (HSS sort of independent int64 jobs)",
+        "value": tuned["jobs_per_s"] if tuned else njobs / (ms / 1000.0),
+        "unit": "jobs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tuned["ms_per_step"] if tuned else ms,
+        "untuned": {"jobs_per_s": njobs / (ms / 1000.0), "ms_per_step": ms, "oversample": 5.0,
+                    "tiling": "library defaults"},
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": f"batched HSS sort: {njobs} int64 jobs, sizes log-uniform [2^10, 2^22], "
                                "p = max(4, n/2^14), eps = 0.05, uniform or Zipf(1.1) over 2^16 values by a seeded coin",
@@ -448,6 +477,7 @@ def run_batch_workload(args):
         "plain_form": {"jobs_per_s": njobs / plain_s, "keys_per_s": offs[-1] / plain_s, "seconds": plain_s,
                        "mean_rounds_per_job": float(np.mean(rounds_p)),
                        "api": "hss_sort per job, host loop, same stream"},
+        "autotuned": tuned,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
@@ -655,6 +685,7 @@ def main():
     ap.add_argument("--workload", default="sort", choices=["sort", "batch", "serve", "rounds", "schedules", "morton"],
                     help="sort: the N=2^28 bench line (default); batch: 4096 independent jobs; serve: Poisson requests")
     ap.add_argument("--batch-jobs", type=int, default=4096)
+    ap.add_argument("--no-tune", action="store_true", help="batch workload: skip the autotuned timing")
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-slots", type=int, default=8)

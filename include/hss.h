@@ -25,8 +25,9 @@
  *     the (key, processor, index) implicit tagging of the paper's Sec. 6.1;
  *     every sort here is therefore stable with respect to input order.
  *   - Return value: HSS_OK (0) or a negative HSS_ERR_* code.  Device-side
- *     failures (a bounded wait that ran out) travel through a status word and
- *     are reported as HSS_ERR_TIMEOUT; nothing traps the GPU.
+ *     failures (an index check that failed, a segment too large) travel
+ *     through a status word and are reported as an error code; nothing traps
+ *     the GPU.  No kernel waits on another, so HSS_ERR_TIMEOUT is reserved.
  *   - Limits: N < 2^40; 1 <= p <= 2^22 and p*(samples per round) positions
  *     must fit the workspace; a segment or bucket holds fewer than 2^30 keys.
  *     Calls whose even segments (ceil(N/p)), or for the sorting calls whose
@@ -49,8 +50,8 @@ extern "C" {
 #define HSS_ERR_INVALID (-1)      /* bad argument: null pointer, p = 0, eps <= 0, sizes out of range */
 #define HSS_ERR_WORKSPACE (-2)    /* work_bytes smaller than hss_workspace_bytes() */
 #define HSS_ERR_ROUND_LIMIT (-3)  /* max_rounds reached with splitters unresolved */
-#define HSS_ERR_TIMEOUT (-4)      /* a bounded device-side wait gave up */
-#define HSS_ERR_CUDA (-5)         /* a CUDA runtime call failed */
+#define HSS_ERR_TIMEOUT (-4)      /* reserved: a bounded device-side wait gave up (no kernel waits today) */
+#define HSS_ERR_CUDA (-5)         /* a CUDA runtime call failed, or a device index check did */
 #define HSS_ERR_CAPACITY (-6)     /* a round drew more probes than the sample buffer holds */
 #define HSS_ERR_NOALLOC_LIMIT (-7) /* input larger than the fixed scratch of hss_local_sort_noalloc */
 

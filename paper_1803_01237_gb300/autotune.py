@@ -168,7 +168,7 @@ class Tuner:
         over, tiles = default_space(max(sps))
         results = []
         try:
-            for s, (cm, ci, ck) in itertools.product(over, tiles[:2]):
+            for s, (cm, ci, ck) in itertools.product(over, tiles[:3]):
                 c = Choice(oversample=s, chip_max_keys=cm, child_interp=ci, child_bucket_keys=ck)
                 so, _ = c.apply()
                 out = torch.empty_like(sub)

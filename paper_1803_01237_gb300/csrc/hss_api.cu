@@ -13,6 +13,7 @@
 #include <cstring>
 #include <algorithm>
 #include <mutex>
+#include <map>
 #include <set>
 #include <utility>
 
@@ -51,6 +52,20 @@ cudaError_t ensure_func_attrs(const void* func, int max_dyn_smem, int carveout) 
         return e;
     g_attr_done.insert({dev, func});
     return cudaSuccess;
+}
+
+int resident_ctas(const void* func, int threads, size_t dyn_smem) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto it = cache.find({dev, func});
+    if (it != cache.end()) return it->second;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, func, threads, dyn_smem) != cudaSuccess || n < 1) n = 1;
+    cache[{dev, func}] = n;
+    return n;
 }
 
 int device_sm_count() {

@@ -20,9 +20,9 @@ constexpr uint32_t kDevErrBounds = 2u;
 constexpr uint32_t kDevErrSize = 4u;  // a segment of 2^30 keys or more (reported as HSS_ERR_INVALID)
 constexpr uint64_t kMaxSegKeys = 1ull << 30;
 
-// Bound on every spin-wait: iterations of a poll with a short sleep.  About a
-// second of waiting before the kernel records kDevErrTimeout and moves on.
-constexpr uint32_t kSpinLimit = 1u << 23;
+// No kernel of the library waits on another CTA or kernel (the split pass
+// takes its tile offsets from a scan, not a look-back), so kDevErrTimeout is
+// set by none today; the status it maps to stays part of the ABI.
 
 // Cut kinds, ordered so that comparison by (kind class, key, seg, spos) is the
 // tag order of Sec. 6.1.
@@ -126,6 +126,10 @@ struct LaunchCountPause {
 cudaError_t ensure_func_attrs(const void* func, int max_dyn_smem, int carveout = -1);
 // Streaming multiprocessors of the current device (cached per device).
 int device_sm_count();
+// CTAs of `func` resident per SM at this block size and dynamic shared
+// memory (the occupancy calculator, cached per device; at least 1).  Call
+// after ensure_func_attrs so that the shared-memory settings count.
+int resident_ctas(const void* func, int threads, size_t dyn_smem);
 
 }  // namespace hss
 

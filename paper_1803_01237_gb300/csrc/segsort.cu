@@ -837,7 +837,42 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 template <int CAP, int R, bool PREFETCH>
 constexpr size_t keys_sort_smem() {
-    return (size_t)CAP * 8 * (PREFETCH ? 2 : 1) + (size_t)(R + 1) * 4 + 32 * 4 + 2 * 32 * 8 + 64;
+    return (size_t)CAP * 8 * (PREFETCH ? 2 : 1) + (size_t)(R + 1) * 4 + 32 * 4 + 2 * 32 * 8 + 64 + (size_t)R;
+}
+
+// Mixed large groups sorted in place by the CTA per segment (more go to the
+// shared-memory kernel).
+constexpr int kKeysMixedMax = 8;
+
+// In-place ascending sort of s[0, m) by the whole CTA: a bitonic network over
+// the next power of two P >= m in the form whose comparators all put the
+// smaller key at the lower index (the first step of every merge compares
+// mirrored positions), so that positions past m act as +infinity and are
+// never touched.  Ends with a barrier.
+template <int THREADS>
+__device__ __forceinline__ void cta_bitonic_sort(uint64_t* s, uint32_t m) {
+    uint32_t P = 1;
+    while (P < m) P <<= 1;
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t t = threadIdx.x; t < (P >> 1); t += THREADS) {
+                uint32_t i, l;
+                if (j == (k >> 1)) {  // mirrored pairs of each k-block
+                    const uint32_t blk = t / j, r = t - blk * j;
+                    i = blk * k + r;
+                    l = blk * k + k - 1 - r;
+                } else {
+                    i = (t / j) * 2 * j + (t % j);
+                    l = i + j;
+                }
+                if (l < m) {
+                    const uint64_t x = s[i], y = s[l];
+                    if (y < x) { s[i] = y; s[l] = x; }
+                }
+            }
+            __syncthreads();
+        }
+    }
 }
 
 // CTAs per SM the register budget must allow: the small classes live on
@@ -864,10 +899,12 @@ __global__ __launch_bounds__(THREADS, keys_min_blocks<THREADS>()) void k_small_k
     uint32_t* s_start = (uint32_t*)(s_stage + (PREFETCH ? CAP : 0));                // R + 1
     uint32_t* s_warp = s_start + (R + 1);                                           // 32
     uint64_t* s_red = (uint64_t*)(((uintptr_t)(s_warp + 32) + 7) & ~(uintptr_t)7);  // 2 * 32
-    uint32_t* s_flag = (uint32_t*)(s_red + 64);                                     // [0] mixed large group
+    uint32_t* s_flag = (uint32_t*)(s_red + 64);  // [0] mixed large groups, [1..kKeysMixedMax] their digits
+    uint8_t* s_mark = (uint8_t*)(s_flag + 16);   // R: the group is large and holds distinct keys
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const uint64_t count = list ? (uint64_t)*nlist : nseg;
+    for (int d = tid; d < R; d += THREADS) s_mark[d] = 0;  // ordered by the first barrier below
     // Segment descriptors travel one iteration ahead in registers: the loads
     // of the next segment's list entry and bounds are issued at the top of an
     // iteration and first used after its first barrier, so their latency
@@ -1008,40 +1045,74 @@ __global__ __launch_bounds__(THREADS, keys_min_blocks<THREADS>()) void k_small_k
         }
         __syncthreads();
         if (mx > (uint32_t)kTinyGroup) {
-            // a large group is fine as it is if it holds a single value
+            // A large group is fine as it is if it holds a single value;
+            // the few that hold distinct keys are sorted in place by the CTA
+            // (a segment with more goes to the shared-memory kernel).
 #pragma unroll
             for (int i = 0; i < ITEMS; ++i) {
                 if ((uint32_t)(i * THREADS) >= n) break;
                 if (tid + i * THREADS >= n) continue;
                 const uint32_t d = dp[i] & kDigitMask;
                 const uint32_t a = s_start[d];
-                if (s_start[d + 1] - a > (uint32_t)kTinyGroup && s_key[a] != s_key[a + (dp[i] >> 13)]) s_flag[0] = 1u;
+                if (s_start[d + 1] - a > (uint32_t)kTinyGroup && s_key[a] != s_key[a + (dp[i] >> 13)]) s_mark[d] = 1u;
             }
             __syncthreads();
-            if (s_flag[0]) {  // uniform: a large group of distinct keys
+            for (int d = tid; d < R; d += THREADS) {
+                if (s_mark[d]) {
+                    s_mark[d] = 0;
+                    const uint32_t q = atomicAdd(&s_flag[0], 1u);
+                    if (q < (uint32_t)kKeysMixedMax) s_flag[1 + q] = (uint32_t)d;
+                }
+            }
+            __syncthreads();
+            const uint32_t nmixed = s_flag[0];
+            if (nmixed > (uint32_t)kKeysMixedMax) {  // uniform
                 if (tid == 0) slow_list[atomicAdd(slow_count, 1u)] = (uint32_t)s;
                 __syncthreads();
                 continue;
+            }
+            for (uint32_t q = 0; q < nmixed; ++q) {
+                const uint32_t d = s_flag[1 + q];
+                const uint32_t a = s_start[d];
+                cta_bitonic_sort<THREADS>(s_key + a, s_start[d + 1] - a);
             }
         }
         if (mx > 1u) {
             // Every group of 2..kTinyGroup keys is sorted in place by the
             // thread owning it (each thread owns G consecutive groups; the
             // groups hold a few keys, nearly in order); a large group holding
-            // one value needs nothing.
-            for (int g = tid * G; g < tid * G + G; ++g) {
-                const uint32_t a = s_start[g], b = s_start[g + 1];
-                if (b - a < 2u || b - a > (uint32_t)kTinyGroup) continue;
-                for (uint32_t j = a + 1; j < b; ++j) {
+            // one value needs nothing.  The groups come in key order, so when
+            // a thread's groups hold few keys in all, one insertion sort over
+            // their whole range does it (one loop instead of one per group:
+            // the lanes of a warp then run loops of similar length).
+            const uint32_t ga = s_start[tid * G], gb = s_start[tid * G + G];
+            if (gb - ga <= (uint32_t)kTinyGroup) {
+                for (uint32_t j = ga + 1; j < gb; ++j) {
                     const uint64_t x = s_key[j];
                     uint32_t i = j;
-                    while (i > a) {
+                    while (i > ga) {
                         const uint64_t y = s_key[i - 1];
                         if (y <= x) break;
                         s_key[i] = y;
                         --i;
                     }
                     s_key[i] = x;
+                }
+            } else {
+                for (int g = tid * G; g < tid * G + G; ++g) {
+                    const uint32_t a = s_start[g], b = s_start[g + 1];
+                    if (b - a < 2u || b - a > (uint32_t)kTinyGroup) continue;
+                    for (uint32_t j = a + 1; j < b; ++j) {
+                        const uint64_t x = s_key[j];
+                        uint32_t i = j;
+                        while (i > a) {
+                            const uint64_t y = s_key[i - 1];
+                            if (y <= x) break;
+                            s_key[i] = y;
+                            --i;
+                        }
+                        s_key[i] = x;
+                    }
                 }
             }
             __syncthreads();
@@ -1582,7 +1653,9 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
         // digit's keys inside the tile is free and one shared counter per
         // digit hands out the slots (one atomic per key instead of the
         // ballot ranking the payload path needs for stability).  rank[i]
-        // holds the digit and, from bit 8, the key's slot.
+        // holds the digit and, from bit 8, the key's slot.  (Aggregating the
+        // lanes of a warp that share a digit with a match instruction costs
+        // more than it saves, even on heavily duplicated keys.)
         for (int d = tid; d < kRadix; d += kOsThreads) s_total[d] = 0;
         __syncthreads();
 #pragma unroll
@@ -1709,10 +1782,10 @@ static cudaError_t launch_small(const uint64_t* in, uint64_t* out, const uint32_
                                 uint64_t fin, uint64_t fout, const SegSortWs& ws, cudaStream_t st) {
     constexpr size_t smem = msd_sort_smem<THREADS, CAP>();
     {
-        const cudaError_t e = ensure_func_attrs((const void*)k_small_msd<PAY, THREADS, CAP>, (int)smem);
+        const cudaError_t e = ensure_func_attrs((const void*)k_small_msd<PAY, THREADS, CAP>, (int)smem, 100);
         if (e != cudaSuccess) return e;
     }
-    const int per_sm = std::max<int>(1, std::min<int>(2048 / THREADS, (int)(227 * 1024 / smem)));
+    const int per_sm = resident_ctas((const void*)k_small_msd<PAY, THREADS, CAP>, THREADS, smem);
     const uint64_t grid = std::min<uint64_t>(count, (uint64_t)num_sms() * per_sm * 4);
     if (grid == 0) return cudaSuccess;
     HSS_LAUNCH((k_small_msd<PAY, THREADS, CAP>), (unsigned)grid, THREADS, smem, st, in, out, pin, pout, seg_lo, seg_hi,
@@ -1727,10 +1800,10 @@ static cudaError_t launch_small_reg(const uint64_t* in, uint64_t* out, const uin
                                     uint64_t fin, uint64_t fout, const SegSortWs& ws, cudaStream_t st) {
     constexpr size_t smem = reg_sort_smem<CAP>();
     {
-        const cudaError_t e = ensure_func_attrs((const void*)k_small_reg<PAY, THREADS, CAP>, (int)smem);
+        const cudaError_t e = ensure_func_attrs((const void*)k_small_reg<PAY, THREADS, CAP>, (int)smem, 100);
         if (e != cudaSuccess) return e;
     }
-    const int per_sm = std::max<int>(1, std::min<int>(2048 / THREADS, (int)(227 * 1024 / smem)));
+    const int per_sm = resident_ctas((const void*)k_small_reg<PAY, THREADS, CAP>, THREADS, smem);
     const uint64_t grid = std::min<uint64_t>(count, (uint64_t)num_sms() * per_sm * 4);
     if (grid == 0) return cudaSuccess;
     HSS_LAUNCH((k_small_reg<PAY, THREADS, CAP>), (unsigned)grid, THREADS, smem, st, in, out, pin, pout, seg_lo, seg_hi,
@@ -1744,11 +1817,13 @@ static cudaError_t launch_keys(const uint64_t* in, uint64_t* out, const uint64_t
                                uint32_t min_n, uint32_t max_n, uint64_t fin, uint64_t fout, uint32_t* slow,
                                uint32_t* slow_count, cudaStream_t st) {
     constexpr size_t smem = keys_sort_smem<CAP, R, PREFETCH>();
+    const void* fn = (const void*)k_small_keys<THREADS, CAP, R, PREFETCH>;
     {
-        const cudaError_t e = ensure_func_attrs((const void*)k_small_keys<THREADS, CAP, R, PREFETCH>, (int)smem);
+        // all of L1 as shared memory: the CTAs per SM are limited by their buffers
+        const cudaError_t e = ensure_func_attrs(fn, (int)smem, 100);
         if (e != cudaSuccess) return e;
     }
-    const int per_sm = std::max<int>(1, std::min<int>(2048 / THREADS, (int)(227 * 1024 / smem)));
+    const int per_sm = resident_ctas(fn, THREADS, smem);
     // With prefetching every CTA walks several segments of the list.
     const uint64_t grid = std::min<uint64_t>(count, (uint64_t)num_sms() * per_sm * (PREFETCH ? 1 : 4));
     if (grid == 0) return cudaSuccess;
