@@ -11,14 +11,15 @@
  *     never allocates device memory: scratch comes from the caller's
  *     workspace (d_work, work_bytes), sized with hss_workspace_bytes().
  *   - Work is enqueued on `stream` (a cudaStream_t passed as void*, NULL =
- *     the legacy default stream).  The splitter rounds run on the device (a
- *     CUDA graph loop, see HSS_FLAG_HOST_ROUNDS), so hss_partition returns
- *     without waiting for the GPU unless statistics are asked for (h_stats
- *     non-NULL) or HSS_FLAG_SYNC / HSS_FLAG_TIMING is set; hss_call_stats
- *     reads them later.  hss_sort waits where its merge plans a level of its
- *     radix recursion (one small read per level).  Rounds driven from the
- *     host (large samples, the k-round schedule, HSS_FLAG_HOST_ROUNDS) read
- *     one small record per round.
+ *     the legacy default stream).  The splitter rounds of a repeated shape
+ *     run on the device (a CUDA graph loop, see HSS_FLAG_DEVICE_ROUNDS), so
+ *     hss_partition returns without waiting for the GPU unless statistics
+ *     are asked for (h_stats non-NULL) or HSS_FLAG_SYNC / HSS_FLAG_TIMING is
+ *     set; hss_call_stats reads them later.  The local sort and the merge
+ *     wait where they plan a level of their radix recursion (one small read
+ *     per level).  Rounds driven from the host (a shape's first call, large
+ *     samples, the k-round schedule, HSS_FLAG_HOST_ROUNDS) read one small
+ *     record per round.
  *   - Keys are 64-bit, unsigned (HSS_KEY_U64) or signed (HSS_KEY_I64).  An
  *     optional 32-bit payload travels with its key.
  *   - Ties between equal keys are broken by (processor, position), which is
@@ -73,15 +74,22 @@ extern "C" {
  * one may be set, else HSS_ERR_INVALID). */
 #define HSS_FLAG_HIST_PROBE 4u
 #define HSS_FLAG_HIST_STAGED 8u
-/* Drive the splitter rounds from the host (one small device-to-host read per
- * round decides the next launch) instead of the device-driven loop.  Without
- * this flag a call whose round sample fits one on-chip sort (sample capacity
- * min(N, ceil(2 s p) + 4096) <= 14336) and whose schedule is not the k-round
- * one runs its rounds as one CUDA graph: a WHILE conditional node whose body
- * is one round (sample, sort, histogram, L/U update, intervals, next sample)
- * and whose condition a device kernel sets after each round (all resolved,
- * round limit, sample capacity).  The results are identical either way. */
+/* Drivers of the splitter rounds.  A call whose round sample fits one
+ * on-chip sort (sample capacity min(N, ceil(2 s p) + 4096) <= 14336) and
+ * whose schedule is not the k-round one can run its rounds as one CUDA
+ * graph: a WHILE conditional node whose body is one round (sample, sort,
+ * histogram, L/U update, intervals, next sample) and whose condition a device
+ * kernel sets after each round (all resolved, round limit, sample capacity);
+ * the graph is built once per shape (workspace, stream, N, p, eps, s, ...)
+ * and cached.  By default a shape's first call drives its rounds from the
+ * host (one small device-to-host read per round decides the next launch:
+ * cheaper than building a graph used once) and later calls of the same
+ * shape run the graph.  HSS_FLAG_HOST_ROUNDS always drives from the host,
+ * HSS_FLAG_DEVICE_ROUNDS always runs the graph (built at the first call);
+ * both together are HSS_ERR_INVALID.  The results are identical in every
+ * case. */
 #define HSS_FLAG_HOST_ROUNDS 16u
+#define HSS_FLAG_DEVICE_ROUNDS 32u
 
 /* Workspace queries (op argument of hss_workspace_bytes). */
 #define HSS_OP_SORT 0
@@ -353,6 +361,8 @@ int hss_partition_batch(const void* d_keys, int key_type, const uint64_t* h_size
 #define HSS_CDF_NPARAM 1153  /* 32 + 32 + 32*32 + 32 + 32 + 1 */
 #define HSS_CDF_LINEAR 0
 #define HSS_CDF_LOG 1
+#define HSS_CDF_W_FP32 0
+#define HSS_CDF_W_BF16 1
 
 typedef struct {
     float theta[HSS_CDF_NPARAM];  /* w1[32], b1[32], W2[32*32] (row i = hidden-2 unit), b2[32], w3[32], b3 */
@@ -361,7 +371,10 @@ typedef struct {
     uint32_t step;                /* Adam steps taken */
     int32_t feature;              /* HSS_CDF_LINEAR or HSS_CDF_LOG */
     int32_t key_type;             /* HSS_KEY_U64 or HSS_KEY_I64 */
-    int32_t pad;
+    int32_t weights;              /* HSS_CDF_W_FP32, or HSS_CDF_W_BF16: every network evaluation (eval,
+                                     propose, the forward and backward pass of training) uses theta
+                                     rounded to bfloat16 (round to nearest, ties to even); theta and the
+                                     Adam moments stay float32 (the master copy the updates go to) */
     double lo, hi;                /* raw feature bounds of x = 0 and x = 1 */
 } hss_cdf_model;
 
@@ -373,6 +386,11 @@ typedef struct {
  * HSS_ERR_INVALID for a bad mode or key type, or bounds not increasing. */
 int hss_cdf_init(hss_cdf_model* d_model, uint64_t seed, int feature, int key_type, uint64_t lo_key, uint64_t hi_key,
                  void* stream);
+
+/* The weight precision of every later evaluation of d_model (weights =
+ * HSS_CDF_W_FP32 or HSS_CDF_W_BF16; hss_cdf_init sets FP32).  HSS_ERR_INVALID
+ * for another value. */
+int hss_cdf_set_weights(hss_cdf_model* d_model, int weights, void* stream);
 
 /* sizeof(hss_cdf_model), for callers without this header's struct. */
 size_t hss_cdf_model_bytes(void);
@@ -422,7 +440,12 @@ typedef struct {
      * byte. */
     uint32_t child_interp;
     uint32_t child_bucket_keys;  /* 128 .. 4096 (0 = 384) */
-    uint32_t reserved[5];        /* zero */
+    /* Packing of small sub-buckets: after a split, runs of consecutive
+     * sub-buckets that are sorted on chip are merged into one on-chip sort of
+     * up to pack_keys keys (their keys are already in order between them, so
+     * sorting the run sorts each).  1 .. 4096; 0 = 1024; 1 packs nothing. */
+    uint32_t pack_keys;
+    uint32_t reserved[4];        /* zero */
 } hss_tuning;
 
 /* Set the tuning (NULL restores the defaults); HSS_ERR_INVALID for a value

@@ -153,6 +153,16 @@ def train(theta, x, t, steps, lr, m=None, v=None, step0=0):
     return theta, m, v, L
 
 
+def round_bf16(theta):
+    """Each parameter as a bfloat16 network uses it: its float32 value rounded
+    to the nearest bfloat16 (the top 16 bits of a float32), ties to even,
+    returned as float64.  Rounding adds 0x7FFF plus the lowest kept bit to
+    the float32 bit pattern and clears the 16 dropped bits."""
+    b = np.asarray(theta, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
 def targets(p, per, delta):
     """CDF targets of the proposed cuts: for splitter i = 1..p-1 and
     k = 0..per-1, i/p + delta (2k/(per-1) - 1) (just i/p when per = 1),

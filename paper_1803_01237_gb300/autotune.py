@@ -47,13 +47,14 @@ class Choice:
     chip_max_keys: int = 4096
     child_interp: int = 0
     child_bucket_keys: int = 384
+    pack_keys: int = 1024
 
     def flags(self) -> int:
         return int(self.hist_flags) | (hss.FLAG_HOST_ROUNDS if self.host_rounds else 0)
 
     def apply(self):
         """Set the process-wide sort tiling; returns (oversample, flags) for the calls."""
-        hss.set_tuning(self.chip_max_keys, self.child_interp, self.child_bucket_keys)
+        hss.set_tuning(self.chip_max_keys, self.child_interp, self.child_bucket_keys, self.pack_keys)
         return float(self.oversample), self.flags()
 
 
@@ -113,7 +114,8 @@ class Tuner:
              seed: int = 1, trials: int = 3, space=None, force: bool = False) -> Choice:
         """The fastest Choice for sorting N keys on p processors (measured on
         `sample` -- a device tensor of N keys -- or on a synthetic input of
-        `kind`), from the cache when present."""
+        `kind`; among choices within 3% of the fastest, the one with the
+        fewest rounds), from the cache when present."""
         import torch
         key = cache_key(N, p, key_type, kind)
         with self._lock:
@@ -139,7 +141,8 @@ class Tuner:
                 results.append((ms, rounds, c))
         finally:
             hss.reset_tuning()
-        ms, rounds, best = min(results, key=lambda r: r[0])
+        fastest = min(r[0] for r in results)
+        ms, rounds, best = min((r for r in results if r[0] <= 1.03 * fastest), key=lambda r: (r[1], r[0]))
         default = [r for r in results if r[2] == Choice()]
         rec = {"choice": asdict(best), "ms": ms, "rounds": rounds,
                "default_ms": default[0][0] if default else None,
@@ -183,7 +186,10 @@ class Tuner:
                 results.append((e0.elapsed_time(e1) / trials, float(np.mean(r.job_rounds)), c))
         finally:
             hss.reset_tuning()
-        ms, rounds, best = min(results, key=lambda r: r[0])
+        # the fastest, or among choices within 3% of it (timing noise) the
+        # one with the fewest rounds per job
+        fastest = min(r[0] for r in results)
+        ms, rounds, best = min((r for r in results if r[0] <= 1.03 * fastest), key=lambda r: (r[1], r[0]))
         rec = {"choice": asdict(best), "ms": ms, "mean_rounds": rounds, "jobs_measured": len(pick),
                "measured": [{"choice": asdict(c), "ms": m, "mean_rounds": r} for m, r, c in results]}
         with self._lock:

@@ -6,7 +6,8 @@
 // candidate cuts, and this network is one source of them.  Everything is
 // float32 on the CUDA cores: the network has 1153 parameters and a training
 // batch holds a few thousand points, far too small a contraction for tensor
-// cores to matter.
+// cores to matter.  Under HSS_CDF_W_BF16 every evaluation uses the parameters
+// rounded to bfloat16 (the float32 master copy takes the Adam updates).
 //
 //   feature   x = clip((raw(u) - lo) / (hi - lo), 0, 1), raw(u) = u or
 //             log2(1 + u), u = order-preserving key bits (double precision)
@@ -14,6 +15,8 @@
 //   loss      L = (1/n) sum_b (y_b - rank_b / N)^2
 //   update    Adam (Kingma and Ba, 2015), bias-corrected
 #include "hss_internal.cuh"
+
+#include <cuda_bf16.h>
 
 #include <algorithm>
 #include <cmath>
@@ -39,6 +42,13 @@ __device__ __forceinline__ float feature_of(uint64_t bits, const hss_cdf_model* 
     return (float)x;
 }
 
+// Parameter k as the network uses it: float32, or rounded to bfloat16
+// (nearest, ties to even) under HSS_CDF_W_BF16.
+__device__ __forceinline__ float weight_of(const hss_cdf_model* M, int k) {
+    const float w = M->theta[k];
+    return M->weights == HSS_CDF_W_BF16 ? __bfloat162float(__float2bfloat16_rn(w)) : w;
+}
+
 // y(x) with the parameters in shared memory (every thread reads the same
 // weight at the same time: broadcasts).
 __device__ __forceinline__ float net(const float* th, float x) {
@@ -59,7 +69,7 @@ __device__ __forceinline__ float net(const float* th, float x) {
 __global__ void k_cdf_init(hss_cdf_model* M, uint64_t seed, int feature, int key_type, double lo, double hi) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k == 0) {
-        M->step = 0; M->feature = feature; M->key_type = key_type; M->pad = 0; M->lo = lo; M->hi = hi;
+        M->step = 0; M->feature = feature; M->key_type = key_type; M->weights = HSS_CDF_W_FP32; M->lo = lo; M->hi = hi;
     }
     if (k >= kP) return;
     const Philox4 r = philox4x32_10((uint32_t)k, 0u, 0u, kInitTag, (uint32_t)seed, (uint32_t)(seed >> 32));
@@ -107,7 +117,7 @@ __global__ __launch_bounds__(kGradThreads) void k_cdf_grad(const hss_cdf_model* 
     float* Ds = Xs + kGradThreads;                  // 256
     float* Ls = Ds + kGradThreads;                  // 256
     const int tid = threadIdx.x;
-    for (int k = tid; k < kP; k += kGradThreads) th[k] = M->theta[k];
+    for (int k = tid; k < kP; k += kGradThreads) th[k] = weight_of(M, k);
     const uint64_t flip = M->key_type == HSS_KEY_I64 ? kSignBit : 0ull;
     __syncthreads();
 
@@ -224,10 +234,12 @@ __global__ __launch_bounds__(1024) void k_cdf_adam(hss_cdf_model* M, const float
     if (apply && threadIdx.x == 0) M->step = t;
 }
 
+__global__ void k_cdf_set_weights(hss_cdf_model* M, int weights) { M->weights = weights; }
+
 __global__ void k_cdf_eval(const hss_cdf_model* __restrict__ M, const uint64_t* __restrict__ keys, uint32_t n,
                            float* __restrict__ y) {
     __shared__ float th[kP];
-    for (int k = threadIdx.x; k < kP; k += blockDim.x) th[k] = M->theta[k];
+    for (int k = threadIdx.x; k < kP; k += blockDim.x) th[k] = weight_of(M, k);
     __syncthreads();
     const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n) return;
@@ -242,7 +254,7 @@ __global__ void k_cdf_eval(const hss_cdf_model* __restrict__ M, const uint64_t* 
 __global__ void k_cdf_propose(const hss_cdf_model* __restrict__ M, uint32_t p, uint32_t per, double delta, int iters,
                               uint64_t* __restrict__ out) {
     __shared__ float th[kP];
-    for (int k = threadIdx.x; k < kP; k += blockDim.x) th[k] = M->theta[k];
+    for (int k = threadIdx.x; k < kP; k += blockDim.x) th[k] = weight_of(M, k);
     __syncthreads();
     const uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= (uint64_t)(p - 1) * per) return;
@@ -292,6 +304,12 @@ using namespace hss;
 extern "C" {
 
 size_t hss_cdf_model_bytes(void) { return sizeof(hss_cdf_model); }
+
+int hss_cdf_set_weights(hss_cdf_model* d_model, int weights, void* stream) {
+    if (!d_model || (weights != HSS_CDF_W_FP32 && weights != HSS_CDF_W_BF16)) return HSS_ERR_INVALID;
+    HSS_LAUNCH(k_cdf_set_weights, 1, 1, 0, (cudaStream_t)stream, d_model, weights);
+    return cudaGetLastError() == cudaSuccess ? HSS_OK : HSS_ERR_CUDA;
+}
 
 size_t hss_cdf_work_bytes(uint32_t n) { return (size_t)grad_blocks(n) * kPartStride * sizeof(float); }
 

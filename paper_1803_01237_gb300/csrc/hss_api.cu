@@ -162,12 +162,19 @@ static bool params_ok(const hss_params* prm) {
     if (prm->max_rounds > HSS_MAX_ROUNDS) return false;
     if (prm->schedule > HSS_SCHEDULE_EQUAL || (prm->schedule == HSS_SCHEDULE_THEORY && prm->schedule_k == 0)) return false;
     if ((prm->flags & HSS_FLAG_HIST_PROBE) && (prm->flags & HSS_FLAG_HIST_STAGED)) return false;
+    if ((prm->flags & HSS_FLAG_HOST_ROUNDS) && (prm->flags & HSS_FLAG_DEVICE_ROUNDS)) return false;
     return true;
 }
 static uint32_t hist_mode(const hss_params* prm) {
     if (prm->flags & HSS_FLAG_HIST_PROBE) return kHistProbe;
     if (prm->flags & HSS_FLAG_HIST_STAGED) return kHistStaged;
     return kHistAuto;
+}
+
+static uint32_t loop_mode(const hss_params* prm) {
+    if (prm->flags & HSS_FLAG_HOST_ROUNDS) return kLoopHost;
+    if (prm->flags & HSS_FLAG_DEVICE_ROUNDS) return kLoopDevice;
+    return kLoopAdaptive;
 }
 
 // Oversampling that sizes the round sample buffers: s, or under the k-round
@@ -328,7 +335,7 @@ static int run_path(const void* d_keys, const uint32_t* d_payload, int key_type,
     bool device_loop = false;
     int status = run_rounds(keysA, seg_off, N, p, prm->eps, prm->seed, s, eff_rounds(prm), key_type, d_splitters,
                             d_offsets, rws, st, &rr, (const uint64_t*)d_prop, nprop, prm->schedule, prm->schedule_k,
-                            hist_mode(prm), (prm->flags & HSS_FLAG_HOST_ROUNDS) == 0, &device_loop);
+                            hist_mode(prm), loop_mode(prm), &device_loop);
     tm.mark(HSS_PHASE_ROUNDS);
     if (status == HSS_ERR_CUDA || status == HSS_ERR_INVALID) return status;
 

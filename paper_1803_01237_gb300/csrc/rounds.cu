@@ -763,10 +763,20 @@ constexpr size_t kMaxLoopGraphs = 32;
 cudaStream_t g_capture_stream[256] = {};
 uint32_t g_body_kernels = 0;  // kernels one round of the loop launches
 
+// Shapes seen once without a graph (the adaptive policy builds a shape's
+// graph when it comes again).
+std::vector<LoopKey> g_seen;
+constexpr size_t kMaxSeen = 64;
+constexpr int kLoopDeclined = 1;  // loop_graph: no graph yet, drive these rounds from the host
+
 // Build (once per key) the graph: the decision kernel, then WHILE(cond) { round }.
+// Unless build_now, a key met for the first time only is remembered and the
+// call declines (kLoopDeclined): capturing and instantiating the graph costs
+// more than the host round trips of one call, so only shapes that repeat get
+// one.
 int loop_graph(const LoopKey& k, const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uint32_t p,
                uint64_t tol, float oversample, uint32_t schedule, uint32_t hist_mode, const RoundWs& ws,
-               cudaGraphExec_t* out) {
+               bool build_now, cudaGraphExec_t* out) {
     std::lock_guard<std::mutex> lock(g_loop_mu);
     for (auto& g : g_loops)
         if (g.key == k) {
@@ -774,6 +784,20 @@ int loop_graph(const LoopKey& k, const uint64_t* skeys, const uint64_t* d_seg_of
             *out = g.exec;
             return HSS_OK;
         }
+    if (!build_now) {
+        bool seen = false;
+        for (size_t i = 0; i < g_seen.size(); ++i)
+            if (g_seen[i] == k) {
+                g_seen.erase(g_seen.begin() + i);
+                seen = true;
+                break;
+            }
+        if (!seen) {
+            if (g_seen.size() >= kMaxSeen) g_seen.erase(g_seen.begin());
+            g_seen.push_back(k);
+            return kLoopDeclined;
+        }
+    }
     if (k.dev < 0 || k.dev >= 256) return HSS_ERR_CUDA;
     cudaStream_t& cs = g_capture_stream[k.dev];
     if (!cs && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return HSS_ERR_CUDA;
@@ -847,7 +871,7 @@ int read_round_result(const RoundWs& ws, RoundResult* out, cudaStream_t st) {
 int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uint32_t p, double eps, uint64_t seed,
                float oversample, uint32_t max_rounds, int key_type, hss_cut* d_splitters, uint64_t* d_offsets,
                const RoundWs& ws, cudaStream_t st, RoundResult* out, const uint64_t* d_prop, uint32_t nprop,
-               uint32_t schedule, uint32_t schedule_k, uint32_t hist_mode, bool device_loop, bool* used_device_loop) {
+               uint32_t schedule, uint32_t schedule_k, uint32_t hist_mode, uint32_t loop_mode, bool* used_device_loop) {
     if (used_device_loop) *used_device_loop = false;
     const uint32_t S = p - 1;
     const uint64_t tol = (uint64_t)std::floor(((double)N * eps) / (2.0 * (double)p));
@@ -913,15 +937,18 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
         HSS_LAUNCH(k_update_pos, dim3(p, sblk), 256, 0, st, S, ws.chgL, ws.chgU, ws.probe_pos, ws.cap, ws.Lpos, ws.Upos);
         intervals(1);
     }
-    if (device_loop && device_loop_possible(ws.cap, schedule)) {
+    cudaGraphExec_t exec = nullptr;
+    if (loop_mode != kLoopHost && device_loop_possible(ws.cap, schedule)) {
         // Sampling of round 1 on the stream, then the loop's graph: no host
         // round trip until the caller reads the statistics.
         int dev = 0;
         HSS_TRY(cudaGetDevice(&dev));
-        cudaGraphExec_t exec = nullptr;
         const LoopKey key{dev, ws.ctl, skeys, d_seg_off, N, tol, ws.cap, p, schedule, hist_mode, oversample};
-        const int rc = loop_graph(key, skeys, d_seg_off, N, p, tol, oversample, schedule, hist_mode, ws, &exec);
-        if (rc != HSS_OK) return rc;
+        const int rc = loop_graph(key, skeys, d_seg_off, N, p, tol, oversample, schedule, hist_mode, ws,
+                                  loop_mode == kLoopDevice, &exec);
+        if (rc != HSS_OK && rc != kLoopDeclined) return rc;
+    }
+    if (exec) {
         HSS_LAUNCH(k_ctl_init, 1, 1, 0, st, ws.ctl, seed, max_rounds);
         enqueue_sampling(ws, d_seg_off, N, p, S, seed, 1, st, per_interval);
         HSS_TRY(cudaGetLastError());

@@ -84,15 +84,20 @@ struct RoundResult {
 // Histogram form of the rounds: chosen per round, or forced (tests).
 constexpr uint32_t kHistAuto = 0, kHistProbe = 1, kHistStaged = 2;
 
+// Driver of the round loop: the host; the device graph from the second call
+// of a shape on (a first call of a shape drives its rounds from the host);
+// the device graph always.
+constexpr uint32_t kLoopHost = 0, kLoopAdaptive = 1, kLoopDevice = 2;
+
 // Run the histogram rounds over the p locally sorted segments skeys
 // (order-preserving key bits) and write the splitters, offsets and the final
 // per-segment positions of the splitters (into ws.Lpos).  d_prop[nprop]
 // (nullable; keys in the caller's representation, nprop <= ws.cap) are
 // proposed cuts ranked and offered to every splitter before round 1.
-// With device_loop the rounds run as one CUDA graph (a WHILE conditional node
-// whose body is one round; a device kernel decides whether another round is
-// needed), so the call does not wait for the GPU: out is then left for
-// read_round_result() once the stream has passed the rounds.  The loop is
+// With the device loop (loop_mode) the rounds run as one CUDA graph (a WHILE
+// conditional node whose body is one round; a device kernel decides whether
+// another round is needed), so the call does not wait for the GPU: out is
+// then left for read_round_result() once the stream has passed the rounds.  The loop is
 // taken only when the round's probe sort needs no host planning (sample
 // capacity <= the on-chip capacity) and the schedule is computed on the device
 // (not the k-round schedule); else the host drives the rounds as before.
@@ -100,7 +105,7 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
                float oversample, uint32_t max_rounds, int key_type, hss_cut* d_splitters, uint64_t* d_offsets,
                const RoundWs& ws, cudaStream_t st, RoundResult* out, const uint64_t* d_prop = nullptr,
                uint32_t nprop = 0, uint32_t schedule = HSS_SCHEDULE_PROPORTIONAL, uint32_t schedule_k = 0,
-               uint32_t hist_mode = kHistAuto, bool device_loop = false, bool* used_device_loop = nullptr);
+               uint32_t hist_mode = kHistAuto, uint32_t loop_mode = kLoopHost, bool* used_device_loop = nullptr);
 
 // Whether run_rounds can drive these rounds on the device.
 bool device_loop_possible(uint64_t cap, uint32_t schedule);

@@ -36,23 +36,28 @@ static inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; 
 static std::atomic<uint32_t> g_chip_max{(uint32_t)kC1Cap};
 static std::atomic<uint32_t> g_child_interp{0u};
 static std::atomic<uint32_t> g_child_keys{384u};
+static std::atomic<uint32_t> g_pack_keys{1024u};
 
 int set_tuning(const hss_tuning* t) {
     if (!t) {
         g_chip_max = (uint32_t)kC1Cap;
         g_child_interp = 0u;
         g_child_keys = 384u;
+        g_pack_keys = 1024u;
         return HSS_OK;
     }
     const uint32_t cm = t->chip_max_keys ? t->chip_max_keys : (uint32_t)kC1Cap;
     const uint32_t ck = t->child_bucket_keys ? t->child_bucket_keys : 384u;
-    if ((cm != (uint32_t)kC1Cap && cm != (uint32_t)kSmallCap) || t->child_interp > 1u || ck < 128u || ck > 4096u)
+    const uint32_t pk = t->pack_keys ? t->pack_keys : 1024u;
+    if ((cm != (uint32_t)kC1Cap && cm != (uint32_t)kSmallCap) || t->child_interp > 1u || ck < 128u || ck > 4096u ||
+        pk > 4096u)
         return HSS_ERR_INVALID;
     for (uint32_t r : t->reserved)
         if (r) return HSS_ERR_INVALID;
     g_chip_max = cm;
     g_child_interp = t->child_interp;
     g_child_keys = ck;
+    g_pack_keys = pk;
     return HSS_OK;
 }
 void get_tuning(hss_tuning* t) {
@@ -60,6 +65,7 @@ void get_tuning(hss_tuning* t) {
     t->chip_max_keys = g_chip_max;
     t->child_interp = g_child_interp;
     t->child_bucket_keys = g_child_keys;
+    t->pack_keys = g_pack_keys;
 }
 
 // Large segments of a level hold more than kC1Cap keys (keys alone split above
@@ -84,6 +90,7 @@ size_t segsort_ws_bytes(uint64_t N, uint64_t nseg) {
     b += align_up(d.tiles * 4, 256);                                  // tile_seg
     b += align_up(d.ml * 4, 256);                                     // large_seg
     b += align_up(d.tiles * 2 * kRadix * 2, 256);                     // tile_hist
+    b += align_up(d.tiles, 256);                                      // tile_skew
     b += 2 * align_up(d.ml * 8, 256);                                 // vor, vand
     b += 4 * align_up(d.ml * 4, 256);                                 // msd_shift x2, spec, direct
     b += 2 * align_up(d.ml * 8, 256);                                 // msd_base, msd_mult
@@ -110,6 +117,7 @@ SegSortWs segsort_ws_carve(void* base, uint64_t N, uint64_t nseg, uint32_t* err)
     w.tile_seg = (uint32_t*)take(d.tiles * 4);
     w.large_seg = (uint32_t*)take(d.ml * 4);
     w.tile_hist = (uint16_t*)take(d.tiles * 2 * kRadix * 2);
+    w.tile_skew = (uint8_t*)take(d.tiles);
     w.vor = (unsigned long long*)take(d.ml * 8);
     w.vand = (unsigned long long*)take(d.ml * 8);
     w.msd_shift[0] = (uint32_t*)take(d.ml * 4);
@@ -821,12 +829,21 @@ __global__ __launch_bounds__(THREADS) void k_small_reg(
 // kept.  A counting pass on a digit interpolating the segment's key range (R
 // groups, monotone in the key) hands every key a slot in its group through
 // one shared counter, and the keys are scattered into group order; since the
-// groups come in key order, each thread then finishes the sort by insertion
-// sorts of its own R / THREADS consecutive groups (a handful of keys, almost
-// in order).  A segment with a group above kTinyGroup keys
-// holding distinct keys is appended to slow_list for the shared-memory
-// kernel.  With PREFETCH the next segment of the list is copied into a
-// shared staging buffer (cp.async) while the current one is sorted.
+// groups come in key order, what is left is the order inside each group:
+// a key of a small group counts the group's keys below it (the keys stay in
+// registers, so the only shared-memory traffic is the group's few keys), and
+// a large group holding distinct keys is sorted by the CTA (a segment with
+// more than kKeysMixedMax of them goes to slow_list for the shared-memory
+// kernel).  The digit has about as many values as the segment has keys, so
+// most groups hold one key.
+// With PREFETCH the segments move between HBM and shared memory by bulk
+// asynchronous copies (the TMA engine): one thread copies the next segment of
+// the list into a staging buffer while the current one is sorted, and copies
+// each sorted segment out of shared memory, so the threads issue no load or
+// store per key.  A bulk copy needs 16-byte aligned addresses, so a segment's
+// first key (when its address is 8 mod 16) and its last key (when one is left
+// over) travel by 8-byte copies, and the keys sit in shared memory one slot
+// further on in that case (key j at buffer[j + head]).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
     const uint32_t sa = (uint32_t)__cvta_generic_to_shared(sdst);
@@ -835,22 +852,67 @@ __device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+// One arrival that also announces `bytes` of bulk copies completing on bar.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// Bounded wait for the phase of the given parity to complete; false when the
+// limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (uint32_t it = 0; it < (1u << 20); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(sdst)),
+                 "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(gdst), "r"(smem_u32(ssrc)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+// The issuing thread's bulk stores have read their shared-memory source.
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+// Shared-memory writes of this thread become visible to bulk copies.
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
 template <int CAP, int R, bool PREFETCH>
 constexpr size_t keys_sort_smem() {
-    return (size_t)CAP * 8 * (PREFETCH ? 2 : 1) + (size_t)(R + 1) * 4 + 32 * 4 + 2 * 32 * 8 + 64 + (size_t)R;
+    return (size_t)(CAP + 2) * 8 * (PREFETCH ? 2 : 1) + (size_t)(R + 1) * 4 + 32 * 4 + 2 * 32 * 8 + 64 + (size_t)R +
+           16;
 }
 
 // Mixed large groups sorted in place by the CTA per segment (more go to the
 // shared-memory kernel).
 constexpr int kKeysMixedMax = 8;
 
-// In-place ascending sort of s[0, m) by the whole CTA: a bitonic network over
+// In-place ascending sort of base[SI(a + i)], i in [0, m), by the whole CTA
+// (SI: the caller's index map): a bitonic network over
 // the next power of two P >= m in the form whose comparators all put the
 // smaller key at the lower index (the first step of every merge compares
 // mirrored positions), so that positions past m act as +infinity and are
 // never touched.  Ends with a barrier.
-template <int THREADS>
-__device__ __forceinline__ void cta_bitonic_sort(uint64_t* s, uint32_t m) {
+template <int THREADS, typename Index>
+__device__ __forceinline__ void cta_bitonic_sort(uint64_t* base, uint32_t a, uint32_t m, Index SI) {
+    auto s = [&](uint32_t i) -> uint64_t& { return base[SI(a + i)]; };
     uint32_t P = 1;
     while (P < m) P <<= 1;
     for (uint32_t k = 2; k <= P; k <<= 1) {
@@ -866,8 +928,8 @@ __device__ __forceinline__ void cta_bitonic_sort(uint64_t* s, uint32_t m) {
                     l = i + j;
                 }
                 if (l < m) {
-                    const uint64_t x = s[i], y = s[l];
-                    if (y < x) { s[i] = y; s[l] = x; }
+                    const uint64_t x = s(i), y = s(l);
+                    if (y < x) { s(i) = y; s(l) = x; }
                 }
             }
             __syncthreads();
@@ -881,30 +943,35 @@ __device__ __forceinline__ void cta_bitonic_sort(uint64_t* s, uint32_t m) {
 template <int THREADS>
 constexpr int keys_min_blocks() { return THREADS <= 128 ? 8 : (THREADS <= 256 ? 3 : 1); }
 
-template <int THREADS, int CAP, int R, bool PREFETCH>
+template <int THREADS, int CAP, int R, bool PREFETCH, int TIE, int AGG = 0, int SWZ = 0>
 __global__ __launch_bounds__(THREADS, keys_min_blocks<THREADS>()) void k_small_keys(
     const uint64_t* kin, uint64_t* kout, const uint64_t* __restrict__ seg_lo, const uint64_t* __restrict__ seg_hi,
     const uint32_t* __restrict__ list, const uint32_t* __restrict__ nlist, uint64_t nseg, uint32_t min_n,
     uint32_t max_n, uint64_t flip_in, uint64_t flip_out, uint32_t* __restrict__ slow_list,
-    uint32_t* __restrict__ slow_count) {
+    uint32_t* __restrict__ slow_count, uint32_t* __restrict__ err) {
     constexpr int ITEMS = CAP / THREADS;
     constexpr int WARPS = THREADS / 32;
-    constexpr int G = R / THREADS;  // groups per thread in the final insertion sort
-    static_assert(CAP % THREADS == 0 && R % THREADS == 0 && R <= 8192 && CAP <= (1 << 18) && WARPS <= 16,
+    static_assert(CAP % THREADS == 0 && R % THREADS == 0 && R <= 4096 && CAP <= 16384 && WARPS <= 16 &&
+                      THREADS >= 64,
                   "keys sort shape");
-    constexpr uint32_t kDigitMask = 8191u;  // digit in bits 0..12, slot from bit 13
+    // dp[i]: digit in bits 0..11, slot in its group in bits 12..25, the
+    // group's size (when 2..kTinyGroup-1) in bits 26..31
+    constexpr uint32_t kDigitMask = 4095u, kSlotShift = 12, kSlotMask = 16383u;
     extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t* s_key = (uint64_t*)smem;                                              // CAP
-    uint64_t* s_stage = s_key + CAP;                                                // CAP (PREFETCH)
-    uint32_t* s_start = (uint32_t*)(s_stage + (PREFETCH ? CAP : 0));                // R + 1
+    uint64_t* s_key = (uint64_t*)smem;                                              // CAP + 2
+    uint64_t* s_stage = s_key + (CAP + 2);                                          // CAP + 2 (PREFETCH)
+    uint32_t* s_start = (uint32_t*)(s_stage + (PREFETCH ? CAP + 2 : 0));            // R + 1
     uint32_t* s_warp = s_start + (R + 1);                                           // 32
     uint64_t* s_red = (uint64_t*)(((uintptr_t)(s_warp + 32) + 7) & ~(uintptr_t)7);  // 2 * 32
     uint32_t* s_flag = (uint32_t*)(s_red + 64);  // [0] mixed large groups, [1..kKeysMixedMax] their digits
     uint8_t* s_mark = (uint8_t*)(s_flag + 16);   // R: the group is large and holds distinct keys
+    uint64_t* s_bar = (uint64_t*)(((uintptr_t)(s_mark + R) + 7) & ~(uintptr_t)7);  // staging buffer full
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const uint64_t count = list ? (uint64_t)*nlist : nseg;
-    for (int d = tid; d < R; d += THREADS) s_mark[d] = 0;  // ordered by the first barrier below
+    for (int d = tid; d < R; d += THREADS) s_mark[d] = 0;
+    if (PREFETCH && tid == 0) mbar_init(s_bar, 1u);
+    __syncthreads();
     // Segment descriptors travel one iteration ahead in registers: the loads
     // of the next segment's list entry and bounds are issued at the top of an
     // iteration and first used after its first barrier, so their latency
@@ -921,13 +988,23 @@ __global__ __launch_bounds__(THREADS, keys_min_blocks<THREADS>()) void k_small_k
             const uint64_t b = seg_lo[s], n = seg_hi[s] - b;
             d.base = b;
             d.n = (uint32_t)n;
-            d.ok = n > min_n && n <= max_n;
+            d.ok = n > min_n && n <= max_n && n > 0;
         }
         return d;
     };
+    // 1 when the segment's first key sits at an address that is 8 mod 16.
+    auto head_of = [](const uint64_t* p) -> uint32_t { return (uint32_t)(((uintptr_t)p >> 3) & 1u); };
+    uint32_t phase = 0;  // parity of the staging buffer's next completion
     auto prefetch = [&](const Desc& d) {  // copy a segment into the staging buffer
-        if (d.ok)
-            for (uint32_t j = tid; j < d.n; j += THREADS) cp_async8(&s_stage[j], &kin[d.base + j]);
+        if (!d.ok) return;  // uniform
+        const uint64_t* g = kin + d.base;
+        const uint32_t hd = head_of(g), m = ((d.n - hd) >> 1) << 1;
+        if (tid == 0) {
+            mbar_arrive_expect_tx(s_bar, m * 8u);
+            if (m) bulk_load(s_stage + 2 * hd, g + hd, m * 8u, s_bar);
+        }
+        if (hd && tid == 1) cp_async8(&s_stage[1], g);
+        if (hd + m < d.n && tid == 2) cp_async8(&s_stage[d.n - 1 + hd], g + d.n - 1);
         cp_async_commit();
     };
     Desc nxt = load_desc(blockIdx.x);
@@ -942,11 +1019,27 @@ __global__ __launch_bounds__(THREADS, keys_min_blocks<THREADS>()) void k_small_k
         const uint64_t s = list ? (uint64_t)list[k] : k;
         const uint64_t base = cur.base;
         const uint32_t n = cur.n;
+        uint32_t sh = 0;  // key j of the segment at src[j + sh]
         if (PREFETCH) {
             cp_async_wait_all();
-            __syncthreads();
+            const bool late = !mbar_wait(s_bar, phase);
+            phase ^= 1u;
+            if (__syncthreads_or(late)) {  // uniform; not expected: a bulk copy that never landed
+                if (tid == 0) atomicOr(err, kDevErrTimeout);
+                break;
+            }
+            sh = head_of(kin + base);
         }
         const uint64_t* src = PREFETCH ? s_stage : kin + base;
+        // The sorted keys: key j at s_key[j + ho], so that the part written
+        // back by a bulk copy starts on a 16-byte boundary.
+        const uint32_t ho = PREFETCH && !SWZ ? head_of(kout + base) : 0u;
+        uint64_t* sk = s_key + ho;
+        // key j of the sorted segment at sk[SI(j)]: with SWZ the 16-key
+        // blocks are permuted inside (XOR with the block number), so threads
+        // walking their own ranges of about 8 keys, 64 bytes apart, meet
+        // different banks
+        auto SI = [](uint32_t i) -> uint32_t { return SWZ ? (i ^ ((i >> 4) & 15u)) : i; };
         // Items past the segment are skipped by a uniform break (n is the
         // same for the whole CTA), so a short segment costs no predicated work.
         uint64_t key[ITEMS];
@@ -955,7 +1048,7 @@ __global__ __launch_bounds__(THREADS, keys_min_blocks<THREADS>()) void k_small_k
         for (int i = 0; i < ITEMS; ++i) {
             if ((uint32_t)(i * THREADS) >= n) break;
             const uint32_t e = tid + i * THREADS;
-            key[i] = e < n ? src[e] ^ flip_in : 0ull;
+            key[i] = e < n ? src[e + sh] ^ flip_in : 0ull;
             const uint32_t h = (uint32_t)(key[i] >> 32);
             if (e < n) { hmin = min(hmin, h); hmax = max(hmax, h); }
         }
@@ -1007,21 +1100,39 @@ __global__ __launch_bounds__(THREADS, keys_min_blocks<THREADS>()) void k_small_k
             mult64 = interp_mult(hi - lo, (uint32_t)R);
         }
         uint32_t dp[ITEMS];
+        const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             if ((uint32_t)(i * THREADS) >= n) break;
             const uint32_t e = tid + i * THREADS;
+            uint32_t d = (uint32_t)R;  // past the segment
             if (e < n) {
-                uint32_t d;
                 if (hi_mode) {
                     d = min(__umulhi((uint32_t)(key[i] >> 32) - hmin, mult32), (uint32_t)R - 1);
                 } else {
                     const uint64_t off = key[i] - kmin;
                     d = mult64 ? min((uint32_t)__umul64hi(off, mult64), (uint32_t)R - 1) : (uint32_t)off;
                 }
-                dp[i] = d | (atomicAdd(&s_start[d], 1u) << 13);
+            }
+            if (AGG) {
+                // The lanes that share lane 0's group (a run of duplicates)
+                // take their slots with one atomic; the others one each.
+                const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+                const uint32_t eq = __ballot_sync(0xffffffffu, d == d0);
+                const bool agg = __popc(eq) > 1;
+                uint32_t b0 = 0;
+                if (lane == 0 && agg && d0 < (uint32_t)R) b0 = atomicAdd(&s_start[d0], (uint32_t)__popc(eq));
+                b0 = __shfl_sync(0xffffffffu, b0, 0);
+                if (d < (uint32_t)R)
+                    dp[i] = d | ((agg && d == d0 ? b0 + (uint32_t)__popc(eq & lt_mask) : atomicAdd(&s_start[d], 1u))
+                                 << kSlotShift);
+            } else if (d < (uint32_t)R) {
+                dp[i] = d | (atomicAdd(&s_start[d], 1u) << kSlotShift);
             }
         }
+        // The previous segment's bulk store has read s_key before the
+        // scatter below overwrites it (ordered by the scan's barriers).
+        if (PREFETCH && tid == 0) bulk_wait_read();
         __syncthreads();
         uint32_t mx = 0;
         for (int d = tid; d < R; d += THREADS) mx = max(mx, s_start[d]);
@@ -1033,18 +1144,22 @@ __global__ __launch_bounds__(THREADS, keys_min_blocks<THREADS>()) void k_small_k
         mx = 0;
 #pragma unroll
         for (int i = 0; i < WARPS; ++i) mx = max(mx, s_warp[i]);
-        // scatter into group order
+        // Scatter into group order.  A key whose group holds 2..kTinyGroup-1
+        // keys notes the group's size (6 bits above the digit and slot): its
+        // final place inside the group is ranked below.
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             if ((uint32_t)(i * THREADS) >= n) break;
             const uint32_t e = tid + i * THREADS;
             if (e < n) {
                 const uint32_t d = dp[i] & kDigitMask;
-                s_key[s_start[d] + (dp[i] >> 13)] = key[i];
+                const uint32_t a = s_start[d], c = s_start[d + 1] - a;
+                sk[SI(a + (dp[i] >> kSlotShift))] = key[i];
+                if (c >= 2u && c < (uint32_t)kTinyGroup) dp[i] |= c << 26;
             }
         }
         __syncthreads();
-        if (mx > (uint32_t)kTinyGroup) {
+        if (mx >= (uint32_t)kTinyGroup) {
             // A large group is fine as it is if it holds a single value;
             // the few that hold distinct keys are sorted in place by the CTA
             // (a segment with more goes to the shared-memory kernel).
@@ -1054,7 +1169,8 @@ __global__ __launch_bounds__(THREADS, keys_min_blocks<THREADS>()) void k_small_k
                 if (tid + i * THREADS >= n) continue;
                 const uint32_t d = dp[i] & kDigitMask;
                 const uint32_t a = s_start[d];
-                if (s_start[d + 1] - a > (uint32_t)kTinyGroup && s_key[a] != s_key[a + (dp[i] >> 13)]) s_mark[d] = 1u;
+                if (s_start[d + 1] - a >= (uint32_t)kTinyGroup && sk[SI(a)] != sk[SI(a + ((dp[i] >> kSlotShift) & kSlotMask))])
+                    s_mark[d] = 1u;
             }
             __syncthreads();
             for (int d = tid; d < R; d += THREADS) {
@@ -1074,54 +1190,104 @@ __global__ __launch_bounds__(THREADS, keys_min_blocks<THREADS>()) void k_small_k
             for (uint32_t q = 0; q < nmixed; ++q) {
                 const uint32_t d = s_flag[1 + q];
                 const uint32_t a = s_start[d];
-                cta_bitonic_sort<THREADS>(s_key + a, s_start[d + 1] - a);
+                cta_bitonic_sort<THREADS>(sk, a, s_start[d + 1] - a, SI);
             }
         }
-        if (mx > 1u) {
-            // Every group of 2..kTinyGroup keys is sorted in place by the
+        if (TIE == 0 && mx > 1u) {
+            // Every group of 2..kTinyGroup-1 keys is sorted in place by the
             // thread owning it (each thread owns G consecutive groups; the
             // groups hold a few keys, nearly in order); a large group holding
             // one value needs nothing.  The groups come in key order, so when
             // a thread's groups hold few keys in all, one insertion sort over
-            // their whole range does it (one loop instead of one per group:
-            // the lanes of a warp then run loops of similar length).
+            // their whole range does it.
+            constexpr int G = R / THREADS;
             const uint32_t ga = s_start[tid * G], gb = s_start[tid * G + G];
-            if (gb - ga <= (uint32_t)kTinyGroup) {
+            if (gb - ga < (uint32_t)kTinyGroup) {
                 for (uint32_t j = ga + 1; j < gb; ++j) {
-                    const uint64_t x = s_key[j];
+                    const uint64_t x = sk[SI(j)];
                     uint32_t i = j;
                     while (i > ga) {
-                        const uint64_t y = s_key[i - 1];
+                        const uint64_t y = sk[SI(i - 1)];
                         if (y <= x) break;
-                        s_key[i] = y;
+                        sk[SI(i)] = y;
                         --i;
                     }
-                    s_key[i] = x;
+                    sk[SI(i)] = x;
                 }
             } else {
                 for (int g = tid * G; g < tid * G + G; ++g) {
                     const uint32_t a = s_start[g], b = s_start[g + 1];
-                    if (b - a < 2u || b - a > (uint32_t)kTinyGroup) continue;
+                    if (b - a < 2u || b - a >= (uint32_t)kTinyGroup) continue;
                     for (uint32_t j = a + 1; j < b; ++j) {
-                        const uint64_t x = s_key[j];
+                        const uint64_t x = sk[SI(j)];
                         uint32_t i = j;
                         while (i > a) {
-                            const uint64_t y = s_key[i - 1];
+                            const uint64_t y = sk[SI(i - 1)];
                             if (y <= x) break;
-                            s_key[i] = y;
+                            sk[SI(i)] = y;
                             --i;
                         }
-                        s_key[i] = x;
+                        sk[SI(i)] = x;
                     }
                 }
             }
             __syncthreads();
         }
+        if (TIE == 1 && mx > 1u) {
+            // Each key of a small group (2..kTinyGroup-1 keys) counts the
+            // group's keys below it -- smaller, or equal and in an earlier
+            // slot, so equal keys take distinct places -- while the keys
+            // stay in registers; after a barrier the keys whose place changed
+            // are written again.  A group of one key is already in place.
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                if ((uint32_t)(i * THREADS) >= n) break;
+                const uint32_t c = dp[i] >> 26;
+                if (tid + i * THREADS >= n || c == 0u) {
+                    dp[i] = 0u;
+                    continue;
+                }
+                const uint32_t d = dp[i] & kDigitMask, slot = (dp[i] >> kSlotShift) & kSlotMask;
+                const uint32_t a = s_start[d];
+                const uint64_t x = key[i];
+                uint32_t r = 0;
+                for (uint32_t q = 0; q < c; ++q) {
+                    const uint64_t y = sk[SI(a + q)];
+                    r += (y < x || (y == x && q < slot)) ? 1u : 0u;
+                }
+                dp[i] = r != slot ? (0x80000000u | (a + r)) : 0u;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                if ((uint32_t)(i * THREADS) >= n) break;
+                if (dp[i] & 0x80000000u) sk[SI(dp[i] & 0x7fffffffu)] = key[i];
+            }
+            __syncthreads();
+        }
         uint64_t* dst = kout + base;
-        for (uint32_t j = tid; j < n; j += THREADS) dst[j] = s_key[j] ^ flip_out;
-        __syncthreads();
+        if (PREFETCH && !SWZ) {
+            if (flip_out) {  // uniform: signed keys back from order-preserving bits
+                for (uint32_t j = tid; j < n; j += THREADS) sk[SI(j)] ^= flip_out;
+                __syncthreads();
+            }
+            // One bulk copy writes the 16-byte aligned middle; the first and
+            // last key go by plain stores when they fall outside it.
+            const uint32_t m = ((n - ho) >> 1) << 1;
+            if (ho && tid == 1) dst[0] = sk[SI(0)];
+            if (ho + m < n && tid == 2) dst[n - 1] = sk[SI(n - 1)];
+            fence_async_smem();
+            __syncthreads();
+            if (tid == 0 && m) bulk_store(dst + ho, s_key + 2 * ho, m * 8u);
+        } else {
+            for (uint32_t j = tid; j < n; j += THREADS) dst[j] = sk[SI(j)] ^ flip_out;
+            __syncthreads();
+        }
     }
-    if (PREFETCH) cp_async_wait_all();
+    if (PREFETCH) {
+        cp_async_wait_all();
+        if (tid == 0) bulk_wait_all();
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1380,11 +1546,22 @@ __device__ __forceinline__ int spec_window(const uint32_t* __restrict__ prev_shi
     return (ps & kShiftInterp) ? 7 : (ps >= 8 ? (int)(ps >> 3) - 1 : 0);
 }
 
+// A tile is skewed when one digit holds more than an eighth of it: the
+// split then gives the lanes of a warp that share lane 0's digit their slots
+// with one atomic (sorted runs of equal keys hit one counter otherwise).
+// Called by all 256 threads with their digit's count.
+__device__ __forceinline__ void tile_skew_flag(uint32_t count, uint8_t* __restrict__ tile_skew, uint32_t t) {
+    const bool big = count > (uint32_t)(kOsTile / 8);
+    const int any = __syncthreads_or(big);
+    if (threadIdx.x == 0) tile_skew[t] = any ? 1u : 0u;
+}
+
 __global__ __launch_bounds__(256) void k_tile_stats(const uint64_t* __restrict__ kin, const uint64_t* __restrict__ seg_lo,
                                                     const uint64_t* __restrict__ seg_hi, uint64_t nseg,
                                                     const uint32_t* __restrict__ tile_start,
                                                     const uint32_t* __restrict__ tile_seg,
                                                     const uint32_t* __restrict__ large_id, uint16_t* __restrict__ tile_hist,
+                                                    uint8_t* __restrict__ tile_skew,
                                                     unsigned long long* __restrict__ vor, unsigned long long* __restrict__ vand,
                                                     const uint64_t* __restrict__ hint_lo, const uint64_t* __restrict__ hint_mult,
                                                     const uint64_t* __restrict__ hint_hi,
@@ -1410,6 +1587,7 @@ __global__ __launch_bounds__(256) void k_tile_stats(const uint64_t* __restrict__
             atomicAnd(&vand[id], (unsigned long long)hint_lo[s]);
         }
         tile_hist[(uint64_t)t * (2 * kRadix) + threadIdx.x] = (uint16_t)(threadIdx.x == 0 ? b - a : 0);
+        if (threadIdx.x == 0) tile_skew[t] = 1u;
         return;
     }
     const uint64_t hb = win ? hint_lo[s] : 0ull;
@@ -1438,6 +1616,7 @@ __global__ __launch_bounds__(256) void k_tile_stats(const uint64_t* __restrict__
         atomicAnd(&vand[id], y);
     }
     tile_hist[(uint64_t)t * (2 * kRadix) + threadIdx.x] = (uint16_t)s_h[threadIdx.x];
+    tile_skew_flag(s_h[threadIdx.x], tile_skew, t);
 }
 
 // Recount of the tiles of segments whose top varying byte (from the OR/AND of
@@ -1448,7 +1627,7 @@ __global__ __launch_bounds__(256) void k_tile_recount(const uint64_t* __restrict
                                                       const uint32_t* __restrict__ tile_start,
                                                       const uint32_t* __restrict__ tile_seg,
                                                       const uint32_t* __restrict__ large_id, uint16_t* __restrict__ tile_hist,
-                                                      const unsigned long long* __restrict__ vor,
+                                                      uint8_t* __restrict__ tile_skew, const unsigned long long* __restrict__ vor,
                                                       const unsigned long long* __restrict__ vand,
                                                       const uint32_t* __restrict__ spec, uint64_t flip_in) {
     __shared__ uint32_t s_h[kRadix];
@@ -1469,6 +1648,7 @@ __global__ __launch_bounds__(256) void k_tile_recount(const uint64_t* __restrict
         atomicAdd(&s_h[(uint32_t)((kin[lo + e] ^ flip_in) >> sh) & 255u], 1u);
     __syncthreads();
     tile_hist[(uint64_t)t * (2 * kRadix) + kRadix + threadIdx.x] = (uint16_t)s_h[threadIdx.x];
+    tile_skew_flag(s_h[threadIdx.x], tile_skew, t);
 }
 
 // Per large segment (thread d = digit d): the split window, the digit totals
@@ -1488,8 +1668,9 @@ __global__ __launch_bounds__(256) void k_msd_prep(const uint64_t* __restrict__ s
                                                   uint64_t* __restrict__ sub_lo, uint64_t* __restrict__ sub_hi,
                                                   uint32_t* __restrict__ tile_off, uint32_t chip_max,
                                                   uint32_t* __restrict__ large_mask, uint32_t* __restrict__ any_large,
-                                                  uint64_t* __restrict__ cmin, uint64_t* __restrict__ cmax) {
-    __shared__ uint32_t s_c[kRadix], s_x[kRadix], s_warp[32];
+                                                  uint64_t* __restrict__ cmin, uint64_t* __restrict__ cmax,
+                                                  uint32_t level_chip_max, uint32_t pack_keys) {
+    __shared__ uint32_t s_c[kRadix], s_x[kRadix], s_warp[32], s_end[kRadix];
     const uint32_t id = blockIdx.x;
     if (id >= counters[19]) return;
     const uint32_t s = large_seg[id];
@@ -1516,8 +1697,43 @@ __global__ __launch_bounds__(256) void k_msd_prep(const uint64_t* __restrict__ s
     __syncthreads();
     scan256_smem<256>(s_c, s_x, s_warp);
     const uint32_t x = s_x[d];
+    // Packing: runs of consecutive sub-buckets sorted on chip (each at most
+    // level_chip_max keys) are merged greedily into packs of at most
+    // pack_keys keys; the keys of consecutive sub-buckets are in order
+    // between them, so the next level sorting a pack as one segment sorts
+    // each.  s_end[d]: end offset of the pack that starts at sub-bucket d,
+    // or ~0 when d belongs to an earlier pack (it becomes empty).  Sub-buckets
+    // split again stand alone.
+    if (d == 0) {
+        uint32_t start = 0, acc = 0;
+        bool open = false;
+        for (uint32_t k = 0; k < (uint32_t)kRadix; ++k) {
+            const uint32_t c = s_c[k];
+            if (c > level_chip_max) {
+                if (open) s_end[start] = s_x[k];
+                open = false;
+                s_end[k] = s_x[k] + c;
+                continue;
+            }
+            if (open && acc + c > pack_keys) {
+                s_end[start] = s_x[k];
+                open = false;
+            }
+            if (!open) {
+                start = k;
+                acc = 0;
+                open = true;
+            } else {
+                s_end[k] = ~0u;
+            }
+            acc += c;
+        }
+        if (open) s_end[start] = s_x[kRadix - 1] + s_c[kRadix - 1];
+    }
+    __syncthreads();
+    const uint32_t pend = s_end[d];
     sub_lo[(uint64_t)id * kRadix + d] = dir ? lo : lo + x;
-    sub_hi[(uint64_t)id * kRadix + d] = dir ? lo : lo + x + total;
+    sub_hi[(uint64_t)id * kRadix + d] = dir ? lo : lo + (pend == ~0u ? x : pend);
     // sub-buckets that the next level splits again: the split pass gathers
     // their smallest and largest key
     const bool large = !dir && total > chip_max;  // chip_max = ~0: nothing gathered
@@ -1560,6 +1776,7 @@ struct SplitArgs {
     const uint32_t* tile_seg;
     const uint32_t* large_id;
     const uint32_t* tile_off;  // [tile][256] destination of the tile's digit-d keys, relative to the segment
+    const uint8_t* tile_skew;  // [tile] one digit holds more than an eighth of the tile
     const uint32_t* msd_shift;
     const uint64_t* msd_base;
     const uint64_t* msd_mult;
@@ -1658,11 +1875,27 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
         // more than it saves, even on heavily duplicated keys.)
         for (int d = tid; d < kRadix; d += kOsThreads) s_total[d] = 0;
         __syncthreads();
+        if (A.tile_skew[t]) {  // uniform per CTA: see tile_skew_flag
+            const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
-        for (int i = 0; i < kOsItems; ++i) {
-            if (wbase + i * 32 < count) {
-                const uint32_t d = split_digit(key[i], shift, dbase, dmult);
-                rank[i] = d | (atomicAdd(&s_total[d], 1u) << 8);
+            for (int i = 0; i < kOsItems; ++i) {
+                const uint32_t d =
+                    wbase + i * 32 < count ? split_digit(key[i], shift, dbase, dmult) : (uint32_t)kRadix;
+                const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+                const uint32_t eq = __ballot_sync(0xffffffffu, d == d0);
+                uint32_t b0 = 0;
+                if (lane == 0 && d0 < (uint32_t)kRadix) b0 = atomicAdd(&s_total[d0], (uint32_t)__popc(eq));
+                b0 = __shfl_sync(0xffffffffu, b0, 0);
+                if (d < (uint32_t)kRadix)
+                    rank[i] = d | ((d == d0 ? b0 + (uint32_t)__popc(eq & lt_mask) : atomicAdd(&s_total[d], 1u)) << 8);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < kOsItems; ++i) {
+                if (wbase + i * 32 < count) {
+                    const uint32_t d = split_digit(key[i], shift, dbase, dmult);
+                    rank[i] = d | (atomicAdd(&s_total[d], 1u) << 8);
+                }
             }
         }
         __syncthreads();
@@ -1811,13 +2044,13 @@ static cudaError_t launch_small_reg(const uint64_t* in, uint64_t* out, const uin
     return cudaGetLastError();
 }
 
-template <int THREADS, int CAP, int R, bool PREFETCH>
+template <int THREADS, int CAP, int R, bool PREFETCH, int TIE>
 static cudaError_t launch_keys(const uint64_t* in, uint64_t* out, const uint64_t* seg_lo, const uint64_t* seg_hi,
                                const uint32_t* list, const uint32_t* nlist, uint64_t count, uint64_t nseg,
                                uint32_t min_n, uint32_t max_n, uint64_t fin, uint64_t fout, uint32_t* slow,
-                               uint32_t* slow_count, cudaStream_t st) {
+                               uint32_t* slow_count, uint32_t* err, cudaStream_t st) {
     constexpr size_t smem = keys_sort_smem<CAP, R, PREFETCH>();
-    const void* fn = (const void*)k_small_keys<THREADS, CAP, R, PREFETCH>;
+    const void* fn = (const void*)k_small_keys<THREADS, CAP, R, PREFETCH, TIE>;
     {
         // all of L1 as shared memory: the CTAs per SM are limited by their buffers
         const cudaError_t e = ensure_func_attrs(fn, (int)smem, 100);
@@ -1827,8 +2060,8 @@ static cudaError_t launch_keys(const uint64_t* in, uint64_t* out, const uint64_t
     // With prefetching every CTA walks several segments of the list.
     const uint64_t grid = std::min<uint64_t>(count, (uint64_t)num_sms() * per_sm * (PREFETCH ? 1 : 4));
     if (grid == 0) return cudaSuccess;
-    HSS_LAUNCH((k_small_keys<THREADS, CAP, R, PREFETCH>), (unsigned)grid, THREADS, smem, st, in, out, seg_lo, seg_hi,
-               list, nlist, nseg, min_n, max_n, fin, fout, slow, slow_count);
+    HSS_LAUNCH((k_small_keys<THREADS, CAP, R, PREFETCH, TIE>), (unsigned)grid, THREADS, smem, st, in, out, seg_lo, seg_hi,
+               list, nlist, nseg, min_n, max_n, fin, fout, slow, slow_count, err);
     return cudaGetLastError();
 }
 
@@ -1875,6 +2108,7 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
     const uint32_t tune_chip_max = g_chip_max.load();
     const bool child_interp = g_child_interp.load() != 0u;
     const uint32_t child_keys = g_child_keys.load();
+    const uint32_t pack_keys = g_pack_keys.load();
     cudaError_t e;
     Level L{src, psrc, d_seg_off, d_seg_off + 1, nseg, flip_in ? kSignBit : 0ull, hint_lo, hint_mult, 0};
     if (N <= (uint64_t)kSmallCap) {
@@ -1930,15 +2164,15 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
                 uint32_t* slow = ws.slow_keys[c];
                 uint32_t* slow_n = ws.counters + 26 + c;
                 if (c == 0)
-                    e = launch_keys<kC0Threads, kC0Cap, 512, true>(L.in, dst, L.seg_lo, L.seg_hi, lists[c], ws.counters + 16,
-                                                            hc[c], L.nseg, lo_n, hi_n, L.flip_in, fout, slow, slow_n, st);
+                    e = launch_keys<kC0Threads, kC0Cap, 512, true, 0>(L.in, dst, L.seg_lo, L.seg_hi, lists[c], ws.counters + 16,
+                                                            hc[c], L.nseg, lo_n, hi_n, L.flip_in, fout, slow, slow_n, ws.err, st);
                 else if (c == 1)
-                    e = launch_keys<kC1Threads, kC1Cap, 1024, true>(L.in, dst, L.seg_lo, L.seg_hi, lists[c], ws.counters + 17,
-                                                            hc[c], L.nseg, lo_n, hi_n, L.flip_in, fout, slow, slow_n, st);
+                    e = launch_keys<kC1Threads, kC1Cap, 2048, true, 0>(L.in, dst, L.seg_lo, L.seg_hi, lists[c], ws.counters + 17,
+                                                            hc[c], L.nseg, lo_n, hi_n, L.flip_in, fout, slow, slow_n, ws.err, st);
                 else
-                    e = launch_keys<kC2Threads, kSmallCap, 4096, false>(L.in, dst, L.seg_lo, L.seg_hi, lists[c],
+                    e = launch_keys<kC2Threads, kSmallCap, 4096, false, 0>(L.in, dst, L.seg_lo, L.seg_hi, lists[c],
                                                                ws.counters + 18, hc[c], L.nseg, lo_n, hi_n, L.flip_in,
-                                                               fout, slow, slow_n, st);
+                                                               fout, slow, slow_n, ws.err, st);
                 if (e != cudaSuccess) return e;
                 if (c == 0)
                     e = launch_small<PAY, kC0Threads, kC0Cap>(L.in, dst, L.pin, pdst, L.seg_lo, L.seg_hi, slow, slow_n,
@@ -1984,14 +2218,15 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
         const int buf = L.depth & 1;
         const uint32_t* prev_shift = L.depth > 0 ? ws.msd_shift[buf ^ 1] : nullptr;
         HSS_LAUNCH(k_tile_stats, tiles, 256, 0, st, L.in, L.seg_lo, L.seg_hi, L.nseg, ws.tile_start, ws.tile_seg, ws.large_id,
-                   ws.tile_hist, ws.vor, ws.vand, L.hint_lo, L.hint_mult, L.hint_hi, prev_shift, ws.spec, L.flip_in);
+                   ws.tile_hist, ws.tile_skew, ws.vor, ws.vand, L.hint_lo, L.hint_mult, L.hint_hi, prev_shift, ws.spec,
+                   L.flip_in);
         if (!L.hint_lo)
             HSS_LAUNCH(k_tile_recount, tiles, 256, 0, st, L.in, L.seg_lo, L.seg_hi, L.nseg, ws.tile_start, ws.tile_seg, ws.large_id,
-                       ws.tile_hist, ws.vor, ws.vand, ws.spec, L.flip_in);
+                       ws.tile_hist, ws.tile_skew, ws.vor, ws.vand, ws.spec, L.flip_in);
         HSS_LAUNCH(k_msd_prep, n_large, 256, 0, st, L.seg_lo, ws.large_seg, ws.counters, ws.tile_start, ws.tile_hist,
                    ws.vor, ws.vand, L.hint_lo, L.hint_mult, ws.msd_base, ws.msd_mult, ws.msd_shift[buf], ws.spec,
                    ws.direct, ws.sub_lo[buf], ws.sub_hi[buf], ws.tile_off, child_interp ? chip_max : 0xffffffffu,
-                   ws.large_mask, ws.any_large, ws.cmin[buf], ws.cmax[buf]);
+                   ws.large_mask, ws.any_large, ws.cmin[buf], ws.cmax[buf], chip_max, std::min(pack_keys, chip_max));
         // The split pass: level buffers alternate tmp, dst, tmp, ... after src.
         uint64_t* next = (L.depth & 1) ? dst : tmp;
         uint32_t* pnext = PAY ? ((L.depth & 1) ? pdst : ptmp) : nullptr;
@@ -2000,7 +2235,7 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
         A.pin = L.pin; A.pout = pnext; A.pfinal = pdst;
         A.seg_lo = L.seg_lo; A.seg_hi = L.seg_hi; A.nseg = L.nseg;
         A.tile_start = ws.tile_start; A.tile_seg = ws.tile_seg; A.large_id = ws.large_id;
-        A.tile_off = ws.tile_off; A.msd_shift = ws.msd_shift[buf]; A.msd_base = ws.msd_base; A.msd_mult = ws.msd_mult;
+        A.tile_off = ws.tile_off; A.tile_skew = ws.tile_skew; A.msd_shift = ws.msd_shift[buf]; A.msd_base = ws.msd_base; A.msd_mult = ws.msd_mult;
         A.direct = ws.direct;
         A.large_mask = ws.large_mask; A.any_large = ws.any_large; A.cmin = ws.cmin[buf]; A.cmax = ws.cmax[buf];
         A.err = ws.err;

@@ -29,7 +29,8 @@ FLAG_SYNC = 1
 FLAG_TIMING = 2
 FLAG_HIST_PROBE = 4   # force the probe-side histogram
 FLAG_HIST_STAGED = 8  # force the staged histogram in rounds whose probes share one interval
-FLAG_HOST_ROUNDS = 16  # drive the splitter rounds from the host instead of the device-driven graph loop
+FLAG_HOST_ROUNDS = 16  # drive the splitter rounds from the host
+FLAG_DEVICE_ROUNDS = 32  # always run the splitter rounds as the device-driven graph (default: from a shape's 2nd call) loop
 MAX_ROUNDS = 64
 NUM_PHASES = 4
 PHASES = ("local_sort", "rounds", "exchange", "merge")
@@ -105,7 +106,9 @@ def load():
         lib.hss_cdf_train.argtypes = [P, P, P, U32, U64, U32, ctypes.c_float, P, P, SZ, P]
         lib.hss_cdf_eval.argtypes = [P, P, U32, P, P]
         lib.hss_cdf_propose.argtypes = [P, U32, U32, ctypes.c_double, P, P]
-        for name in ("hss_cdf_init", "hss_cdf_grad", "hss_cdf_train", "hss_cdf_eval", "hss_cdf_propose"):
+        lib.hss_cdf_set_weights.argtypes = [P, I32, P]
+        for name in ("hss_cdf_init", "hss_cdf_grad", "hss_cdf_train", "hss_cdf_eval", "hss_cdf_propose",
+                     "hss_cdf_set_weights"):
             getattr(lib, name).restype = I32
         lib.hss_kernel_launch_count.argtypes = []
         lib.hss_kernel_launch_count.restype = U64
@@ -460,14 +463,15 @@ def sample_words(seed: int, seg: int, rnd: int, spos0: int, count: int, device="
 
 class Tuning(ctypes.Structure):
     _fields_ = [("chip_max_keys", ctypes.c_uint32), ("child_interp", ctypes.c_uint32),
-                ("child_bucket_keys", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
+                ("child_bucket_keys", ctypes.c_uint32), ("pack_keys", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 4)]
 
 
-def set_tuning(chip_max_keys: int = 0, child_interp: int = 0, child_bucket_keys: int = 0):
+def set_tuning(chip_max_keys: int = 0, child_interp: int = 0, child_bucket_keys: int = 0, pack_keys: int = 0):
     """hss_set_tuning: process-wide choices of the segmented sort (results unchanged)."""
     lib = load()
     t = Tuning(chip_max_keys=int(chip_max_keys), child_interp=int(child_interp),
-               child_bucket_keys=int(child_bucket_keys))
+               child_bucket_keys=int(child_bucket_keys), pack_keys=int(pack_keys))
     _check(lib.hss_set_tuning(ctypes.byref(t)), "hss_set_tuning")
 
 
@@ -479,7 +483,7 @@ def get_tuning() -> dict:
     t = Tuning()
     _check(load().hss_get_tuning(ctypes.byref(t)), "hss_get_tuning")
     return {"chip_max_keys": t.chip_max_keys, "child_interp": t.child_interp,
-            "child_bucket_keys": t.child_bucket_keys}
+            "child_bucket_keys": t.child_bucket_keys, "pack_keys": t.pack_keys}
 
 
 def launch_count() -> int:
@@ -495,6 +499,7 @@ def strerror(code: int) -> str:
 # ---------------------------------------------------------------------------
 CDF_NPARAM = 1153
 CDF_FEATURES = {"linear": 0, "log": 1}
+CDF_WEIGHTS = {"fp32": 0, "bf16": 1}
 
 
 class CDFModel:
@@ -522,6 +527,13 @@ class CDFModel:
         rc = load().hss_cdf_init(_ptr(self.buf), seed & ((1 << 64) - 1), CDF_FEATURES[feature], KEY_TYPES[key_type],
                                  lo_key & ((1 << 64) - 1), hi_key & ((1 << 64) - 1), _stream(stream))
         _check(rc, "hss_cdf_init")
+        return self
+
+    def set_weights(self, weights: str, stream=None):
+        """"fp32", or "bf16": later evaluations use the parameters rounded to
+        bfloat16 (hss_cdf_set_weights)."""
+        rc = load().hss_cdf_set_weights(_ptr(self.buf), CDF_WEIGHTS[weights], _stream(stream))
+        _check(rc, "hss_cdf_set_weights")
         return self
 
     def _ws(self, n: int) -> torch.Tensor:

@@ -260,7 +260,11 @@ class Server:
     """Continuous-batching server of partition requests.
 
     slots          concurrent requests on the device (one stream each)
-    hbm_budget     bytes of workspace admitted at once (None: no limit)
+    hbm_budget     bytes of workspace admitted at once (None: no limit), or
+                   "free": admit by the device memory free at the time
+                   (cudaMemGetInfo, plus what the caching allocator holds
+                   unused), keeping hbm_reserve bytes free
+    hbm_reserve    bytes left free under hbm_budget="free"
     model          CDF network to train online and propose from (None: plain)
     per_splitter   most proposed cuts per splitter (each request takes the
                    fewest that reach its fewest expected rounds, see plan)
@@ -271,13 +275,17 @@ class Server:
                    held-out errors over the recent jobs (see _delta)
     """
 
-    def __init__(self, slots: int = 4, hbm_budget: int | None = None, model: hss.CDFModel | None = None,
+    def __init__(self, slots: int = 4, hbm_budget: int | str | None = None, model: hss.CDFModel | None = None,
                  per_splitter: int = 16, train: bool = True, train_steps: int = 100, lr: float = 0.01,
                  keep_jobs: int = 16, min_jobs: int = 2, train_interval: float = 0.0, delta: float = 0.0,
-                 device=None):
+                 device=None, hbm_reserve: int = 1 << 30):
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.slots = slots
+        if isinstance(hbm_budget, str) and hbm_budget != "free":
+            raise ValueError('hbm_budget: bytes, None or "free"')
         self.hbm_budget = hbm_budget
+        self.hbm_reserve = int(hbm_reserve)
+        self.pending_bytes = 0  # admitted under "free", not yet allocated
         self.model = model
         self.per_splitter = per_splitter
         self.frozen_delta = delta
@@ -343,7 +351,8 @@ class Server:
         except hss.HSSError:
             return None
 
-    def _serve_one(self, req: Request, slot: int, t0: float, admitted: float, need: int, stats: ServeStats):
+    def _serve_one(self, req: Request, slot: int, t0: float, admitted: float, need: int, stats: ServeStats,
+                   grow: int = 0):
         stream = self.streams[slot]
         err = None
         res = None
@@ -351,6 +360,15 @@ class Server:
         try:
             with torch.cuda.stream(stream):
                 prop = self._propose(req, stream)
+                if grow:  # the workspace is taken now: no longer pending
+                    nb = self.request_bytes(req.keys.numel(), req.p, req.key_type)
+                    ws = self.slot_ws[slot]
+                    if ws is None or ws.numel() < nb:
+                        self.slot_ws[slot] = None
+                        self.slot_ws[slot] = torch.empty(nb, dtype=torch.uint8, device=self.device)
+                    with self.cv:
+                        self.pending_bytes -= grow
+                        grow = 0
                 if prop is not None:
                     try:
                         res, _ = self._partition(req, prop, stream, slot)
@@ -361,6 +379,9 @@ class Server:
                 stream.synchronize()
         except Exception as e:  # recorded per request; the server keeps going
             err = repr(e)
+        if grow:
+            with self.cv:
+                self.pending_bytes -= grow
         done = time.perf_counter() - t0  # the result is ready
         if self.trainer is not None and res is not None and err is None:
             # the trainer extracts the pairs on its own stream
@@ -388,6 +409,28 @@ class Server:
             self.slot_ws[slot] = ws
         return _partition_into(req, prop, ws, stream)
 
+    def _available_bytes(self) -> int:
+        """Device memory a new allocation can take now: free memory plus what
+        the caching allocator holds without using it."""
+        free, _ = torch.cuda.mem_get_info(self.device)
+        reclaim = torch.cuda.memory_reserved(self.device) - torch.cuda.memory_allocated(self.device)
+        return int(free) + int(reclaim)
+
+    def _growth(self, slot: int, req: Request, need: int) -> int:
+        """Bytes a request on this slot allocates: its workspace beyond the
+        slot's cached one, plus its outputs."""
+        nb = self.request_bytes(req.keys.numel(), req.p, req.key_type)
+        ws = self.slot_ws[slot]
+        cached = ws.numel() if ws is not None else 0
+        return max(0, nb - cached) + max(0, need - nb)
+
+    def _fits(self, slot: int, req: Request, need: int) -> bool:
+        if self.hbm_budget is None:
+            return True
+        if self.hbm_budget == "free":
+            return self._growth(slot, req, need) + self.pending_bytes <= self._available_bytes() - self.hbm_reserve
+        return self.bytes_in_flight + need <= self.hbm_budget
+
     def run(self, requests: list[Request], realtime: bool = True) -> ServeStats:
         """Serve the requests (sorted by arrival).  With realtime, a request
         is not admitted before its arrival time; otherwise all are ready at
@@ -409,22 +452,46 @@ class Server:
                 if wait > 0:
                     time.sleep(wait)
             need = self.request_bytes(req.keys.numel(), req.p, req.key_type, nprop=(req.p - 1) * self.per_splitter)
-            if self.hbm_budget is not None and need > self.hbm_budget:
+            reject = isinstance(self.hbm_budget, int) and need > self.hbm_budget
+            slot = -1
+            with self.cv:
+                while not reject:
+                    if self.free_slots:
+                        cand = self.free_slots[-1]
+                        if self._fits(cand, req, need):
+                            slot = cand
+                            break
+                        if self.hbm_budget == "free" and self.bytes_in_flight == 0 and self.pending_bytes == 0:
+                            # nothing in flight: release the idle slots'
+                            # workspaces, then it fits now or never will
+                            idle = [k for k in self.free_slots if k != cand and self.slot_ws[k] is not None]
+                            for k in idle:
+                                self.slot_ws[k] = None
+                            if idle and self._fits(cand, req, need):
+                                slot = cand
+                                break
+                            reject = True
+                            break
+                    # a completion frees a slot or memory; memory freed
+                    # elsewhere on the device is seen at the next poll
+                    self.cv.wait(timeout=0.05 if self.hbm_budget == "free" else None)
+                if not reject:
+                    self.free_slots.pop()
+                    grow = self._growth(slot, req, need) if self.hbm_budget == "free" else 0
+                    self.pending_bytes += grow
+                    self.bytes_in_flight += need
+            if reject:
                 stats.completions.append(Completion(
                     rid=req.rid, arrival=req.arrival, admitted=-1.0, done=time.perf_counter() - t0, rounds=-1,
                     status=hss.ERR_WORKSPACE, n=req.keys.numel(), p=req.p, tol=-1, offsets=None, splitters=None,
                     proposal=None, slot=-1, error="request exceeds the memory budget"))
                 continue
             with self.cv:
-                while not self.free_slots or (self.hbm_budget is not None and
-                                              self.bytes_in_flight + need > self.hbm_budget):
-                    self.cv.wait()
-                slot = self.free_slots.pop()
-                self.bytes_in_flight += need
                 stats.max_in_flight = max(stats.max_in_flight, self.slots - len(self.free_slots))
                 stats.max_bytes_in_flight = max(stats.max_bytes_in_flight, self.bytes_in_flight)
             admitted = time.perf_counter() - t0
-            th = threading.Thread(target=self._serve_one, args=(req, slot, t0, admitted, need, stats), daemon=True)
+            th = threading.Thread(target=self._serve_one, args=(req, slot, t0, admitted, need, stats, grow),
+                                  daemon=True)
             th.start()
             threads.append(th)
         for th in threads:

@@ -206,3 +206,76 @@ def test_trained_network_saves_rounds(hss):
     print("rounds plain", rounds_plain, "with proposal", rounds_prop, "last training loss", loss)
     assert sum(rounds_prop) < sum(rounds_plain)
     assert max(rounds_prop) < max(rounds_plain)
+
+
+def test_gpu_bisection_returns_the_smallest_x(hss):
+    """A network flat at 1/2 on [1/2, 3/4]: every x there has y(x) >= 1/2, and
+    the proposal for tau = 1/2 is the smallest such x (1/2), as in the
+    oracle's bisection; tau = 1/4 and 3/4 land at 1/4 and 1."""
+    lo_key, hi_key = 0, 1 << 40
+    m = hss.CDFModel().init(1, "linear", lo_key, hi_key)
+    w1 = np.zeros(M.H); b1 = np.zeros(M.H)
+    w1[0], w1[1], b1[1], w1[2], b1[2] = 1.0, 1.0, -0.5, 1.0, -0.75
+    W2 = np.zeros((M.H, M.H)); W2[0, 0], W2[0, 1], W2[1, 2] = 1.0, -1.0, 1.0
+    w3 = np.zeros(M.H); w3[0], w3[1] = 1.0, 1.0
+    th = M.pack(w1, b1, W2, np.zeros(M.H), w3, 0.0)
+    m.theta.copy_(torch.from_numpy(th.astype(np.float32)))
+    prop = m.propose(4).cpu().numpy().view(np.uint64).astype(np.float64)
+    want = np.array([0.25, 0.5, 1.0]) * float(hi_key)
+    assert np.all(np.abs(prop - want) <= float(hi_key) * 2.0 ** -22)
+    ref = M.propose(th, 4, M.LINEAR, float(lo_key), float(hi_key)).astype(np.float64)
+    assert np.all(np.abs(prop - ref) <= float(hi_key) * 2.0 ** -22)
+
+
+# ---------------------------------------------------------------------------
+# The bfloat16 weight variant: every evaluation uses the parameters rounded to
+# bfloat16; the oracle is the same float64 network on M.round_bf16(theta).
+# ---------------------------------------------------------------------------
+def test_bf16_eval_and_gradient_match_the_oracle(hss):
+    keys, ranks = _job(3000, 21)
+    N = 3000
+    m, lo, hi = _model(hss, keys, 22)
+    theta = M.init(22) + 0.05 * np.random.default_rng(5).standard_normal(M.NPARAM)
+    m.theta.copy_(torch.from_numpy(theta.astype(np.float32)))
+    m.set_weights("bf16")
+    x = M.feature(keys, M.LOG, lo, hi)
+    th32 = m.theta.cpu().numpy().astype(np.float64)
+    thb = M.round_bf16(th32)
+    assert not np.array_equal(thb, th32)  # the rounding changes the network
+    y = m.eval(dev_u64(keys)).cpu().numpy()
+    yb, _ = M.forward(thb, x)
+    assert np.allclose(y, yb, rtol=1e-4, atol=1e-5)
+    y32, _ = M.forward(th32, x)
+    assert np.abs(yb - y32).max() > 1e-4  # and the kernel followed it, not the float32 weights
+    g, loss = m.grad(dev_u64(keys), dev_u64(ranks), N)
+    gref, Lref = M.grad(thb, x, ranks.astype(np.float64) / N)
+    gg = g.cpu().numpy().astype(np.float64)
+    assert np.allclose(gg, gref, rtol=1e-3, atol=1e-4 * np.abs(gref).max())
+    assert float(loss.item()) == pytest.approx(Lref, rel=1e-4)
+    m.set_weights("fp32")
+    y2 = m.eval(dev_u64(keys)).cpu().numpy()
+    assert np.allclose(y2, y32, rtol=1e-4, atol=1e-5)
+
+
+def test_bf16_training_fits_and_proposes(hss):
+    """Training through the bfloat16 weights (float32 master copy) fits the
+    CDF about as well as float32, and its proposals invert the rounded
+    network."""
+    keys, ranks = _job(4096, 23)
+    N = 4096
+    m, lo, hi = _model(hss, keys, 24)
+    m.set_weights("bf16")
+    x = M.feature(keys, M.LOG, lo, hi)
+    t = ranks.astype(np.float64) / N
+    L0 = M.loss(M.round_bf16(m.theta.cpu().numpy()), x, t)
+    m.train(dev_u64(keys), dev_u64(ranks), N, 300, 0.01)
+    torch.cuda.synchronize()
+    thb = M.round_bf16(m.theta.cpu().numpy())
+    Lb = M.loss(thb, x, t)
+    _, _, _, Lref = M.train(M.init(24), x, t, 300, 0.01)
+    assert Lb < 0.01 * L0
+    assert Lb < 3.0 * Lref + 1e-5
+    p = 64
+    prop = m.propose(p).cpu().numpy().view(np.uint64)
+    y, _ = M.forward(thb, M.feature(prop, M.LOG, lo, hi))
+    assert np.all(y >= np.arange(1, p) / p - 1e-4)

@@ -451,8 +451,9 @@ def test_device_and_host_rounds_agree_with_oracle(hss, N, p, eps, seed, max_roun
     needed (eps >= 1)."""
     keys = inputs.uniform(N, seed)
     ref = oracle.hss(keys, p, eps, seed, sort=False, max_rounds=max_rounds or 64)
-    for flags in (0, hss.FLAG_HOST_ROUNDS):
-        res, _ = hss.partition(dev(keys), p, eps, seed, max_rounds=max_rounds, flags=flags, allow_round_limit=True)
+    dk = dev(keys)
+    for flags in (hss.FLAG_DEVICE_ROUNDS, hss.FLAG_HOST_ROUNDS, 0, 0):  # default: host first, then the graph
+        res, _ = hss.partition(dk, p, eps, seed, max_rounds=max_rounds, flags=flags, allow_round_limit=True)
         assert res.status == ref.status
         _cmp_partition(res, ref)
 
@@ -464,8 +465,8 @@ def test_partition_returns_before_the_gpu_and_stats_come_later(hss):
     N, p, eps, seed = 1 << 20, 256, 0.02, 9
     keys = inputs.gauss_mix(N, seed)
     dk = dev(keys)
-    spl, off, ws = hss.partition_async(dk, p, eps, seed)
-    rc, st = hss.call_stats("partition", N, p, eps, seed, ws)
+    spl, off, ws = hss.partition_async(dk, p, eps, seed, flags=hss.FLAG_DEVICE_ROUNDS)
+    rc, st = hss.call_stats("partition", N, p, eps, seed, ws, flags=hss.FLAG_DEVICE_ROUNDS)
     ref = oracle.hss(keys, p, eps, seed, sort=False)
     assert rc == 0 and st.status == 0
     assert st.rounds == ref.rounds

@@ -119,3 +119,29 @@ def test_online_training_saves_rounds(mods):
         res, _ = hss.partition_with_proposal(r.keys, r.p, r.eps, r.seed, c.proposal)
         assert res.rounds == c.rounds
         assert torch.equal(res.offsets, c.offsets) and torch.equal(res.splitters[:r.p - 1], c.splitters[:r.p - 1])
+
+
+def test_admission_by_free_device_memory(mods):
+    """hbm_budget="free": admission reads the device's free memory
+    (cudaMemGetInfo plus what the caching allocator holds unused) and keeps
+    hbm_reserve free.  With the reserve set so that only some 64 MiB remain,
+    small requests are served (their results as alone) and one whose
+    workspace needs more is refused rather than queued forever."""
+    hss, serve = mods
+    pool = _pool(1, 1 << 24, 61)
+    torch.cuda.synchronize()
+    free, _ = torch.cuda.mem_get_info()
+    reclaim = torch.cuda.memory_reserved() - torch.cuda.memory_allocated()
+    reserve = int(free + reclaim) - (64 << 20)
+    small = serve.poisson_requests(pool, 6, rate=1000.0, seed=7, lo_log2=14, hi_log2=16, ps=(16,))
+    srv = serve.Server(slots=2, hbm_budget="free", hbm_reserve=reserve)
+    st = srv.run(small, realtime=False)
+    assert all(c.error is None for c in st.completions)
+    for c, r in zip(st.completions, sorted(small, key=lambda q: q.rid)):
+        kh = r.keys.cpu().numpy().view(np.uint64)
+        ref = oracle.hss(kh, r.p, r.eps, r.seed, sort=False)
+        assert np.array_equal(c.offsets.cpu().numpy().astype(np.uint64), ref.offsets)
+    big = serve.Request(rid=99, arrival=0.0, keys=pool[0], p=64, eps=0.02, seed=1)
+    assert serve.Server.request_bytes(pool[0].numel(), 64) > (64 << 20)
+    st2 = serve.Server(slots=2, hbm_budget="free", hbm_reserve=reserve).run([big], realtime=False)
+    assert st2.completions[0].error is not None and st2.completions[0].status == hss.ERR_WORKSPACE

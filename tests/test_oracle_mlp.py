@@ -122,3 +122,72 @@ def test_init_uses_the_philox_words():
     assert th[0] == pytest.approx((1.0 + u0) * 4.0, rel=1e-15)
     assert th[M.H] == pytest.approx(-th[0] * 0.5 / M.H, rel=1e-15)
     assert th[-1] == 0.5
+
+
+def test_targets_several_cuts_per_splitter_hand_case():
+    """per > 1: the cuts of splitter i sit at i/p + delta (2k/(per-1) - 1),
+    k = 0..per-1, splitter-major, clipped to [0, 1] (worked by hand)."""
+    got = M.targets(4, 3, 0.05)
+    want = [0.20, 0.25, 0.30, 0.45, 0.50, 0.55, 0.70, 0.75, 0.80]
+    assert np.allclose(got, want, rtol=0, atol=1e-15)
+    assert np.array_equal(M.targets(2, 2, 0.6), [0.0, 1.0])  # both ends clipped
+    assert np.array_equal(M.targets(3, 1, 0.3), [1.0 / 3.0, 2.0 / 3.0])  # delta unused for one cut
+
+
+def test_identity_network_proposes_targets_for_several_cuts():
+    """The identity network y(x) = x proposes, for every target tau, the key
+    at feature tau: lo + tau (hi - lo) on the linear map."""
+    theta = _identity_net()
+    lo, hi = 1000.0, 1000.0 + 2.0 ** 40
+    keys = M.propose(theta, 4, M.LINEAR, lo, hi, per=3, delta=0.05)
+    want = np.array([lo + t * (hi - lo) for t in [0.20, 0.25, 0.30, 0.45, 0.50, 0.55, 0.70, 0.75, 0.80]])
+    assert np.all(np.abs(keys.astype(np.float64) - want) <= 2.0 ** 40 * 2.0 ** -38)
+
+
+def _plateau_net():
+    """y(x) = min(x, 1/2) + relu(x - 3/4) on [0, 1]: flat at 1/2 on [1/2, 3/4]."""
+    w1 = np.zeros(M.H); b1 = np.zeros(M.H)
+    w1[0], w1[1], b1[1], w1[2], b1[2] = 1.0, 1.0, -0.5, 1.0, -0.75   # relu(x), relu(x-1/2), relu(x-3/4)
+    W2 = np.zeros((M.H, M.H))
+    W2[0, 0], W2[0, 1] = 1.0, -1.0   # relu(relu(x) - relu(x-1/2)) = min(x, 1/2)
+    W2[1, 2] = 1.0                   # relu(relu(x-3/4))
+    w3 = np.zeros(M.H); w3[0], w3[1] = 1.0, 1.0
+    return M.pack(w1, b1, W2, np.zeros(M.H), w3, 0.0)
+
+
+def test_bisection_returns_the_smallest_x():
+    """Where the network is flat at the target, every x of the plateau has
+    y(x) >= tau; the proposal is the smallest one (x = 1/2 for tau = 1/2, not
+    a point inside [1/2, 3/4]), and y just below it stays under tau."""
+    theta = _plateau_net()
+    xs = np.array([0.0, 0.25, 0.5, 0.6, 0.75, 0.9, 1.0])
+    y, _ = M.forward(theta, xs)
+    assert np.allclose(y, [0.0, 0.25, 0.5, 0.5, 0.5, 0.65, 0.75])
+    lo, hi = 0.0, 2.0 ** 40
+    keys = M.propose(theta, 2, M.LINEAR, lo, hi)   # tau = 1/2
+    assert abs(float(keys[0]) - 0.5 * hi) <= 1.0
+    x = M.feature(keys, M.LINEAR, lo, hi)
+    assert M.forward(theta, x - 2.0 ** -30)[0][0] < 0.5 <= M.forward(theta, x + 2.0 ** -30)[0][0]
+
+
+def test_bf16_rounding_hand_cases_and_library():
+    """bfloat16 keeps the top 16 bits of a float32, rounded to nearest with
+    ties to even: hand-worked values, then against torch's conversion."""
+    one = 1.0
+    cases = [
+        (one, one),
+        (one + 2.0 ** -8, one),                    # halfway, 1.0 has an even last bit: down
+        (one + 3 * 2.0 ** -8, one + 2.0 ** -6),    # halfway, 1 + 2^-7 is odd: up
+        (one + 2.0 ** -8 + 2.0 ** -20, one + 2.0 ** -7),  # above halfway: up
+        (-(one + 2.0 ** -9), -one),                # below halfway: down (magnitude)
+        (0.1, 0.10009765625),
+        (3.0e38, 2.0 ** 127 * 226 / 128),          # 3e38 = 2^127 x 1.7633: 225.7/128 -> 226/128
+    ]
+    for x, want in cases:
+        assert M.round_bf16(np.array([x]))[0] == want, x
+    torch = pytest.importorskip("torch")
+    g = np.random.default_rng(3)
+    x = np.concatenate([g.normal(size=4000), g.normal(size=4000) * 1e-30, g.uniform(-1e30, 1e30, 4000)])
+    x32 = x.astype(np.float32)
+    want = torch.from_numpy(x32).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
+    assert np.array_equal(M.round_bf16(x32), want)

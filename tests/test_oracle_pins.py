@@ -528,3 +528,43 @@ def test_theory_k_rounds_theorem_4_7(k):
             q = min(1.0, p * math.pow(2.0 * math.log(p) / eps, (j + 1) / k) / N)
             mean = q * int(res.gamma[j])
             assert abs(int(res.sample_size[j]) - mean) <= 6.0 * math.sqrt(max(mean * (1 - q), 1e-9)) + 1
+
+
+@pytest.mark.parametrize("gen", ["uniform", "gauss_mix"])
+def test_equal_schedule_expected_probes_per_interval(gen):
+    """Equal sampling per interval (the HykSort way, Sec. 4.2.2): interval u
+    of length len_u draws Binomial(len_u, q_u) probes with
+    q_u = min(1, (s p / nint) / len_u), so each interval expects s p / nint
+    probes whatever its length.  Each interval's count lies in a 6-sigma
+    Chernoff band, and the count pooled over rounds, intervals and seeds
+    within 4 sigma of the pooled expectation (a dropped or misplaced nint
+    shifts it by far more)."""
+    N, p, eps, s = 1 << 13, 16, 0.02, 5.0
+    g = {"uniform": inputs.uniform, "gauss_mix": inputs.gauss_mix}[gen]
+    pooled_got = pooled_mean = pooled_var = 0.0
+    for seed in range(1, 9):
+        keys = g(N, seed)
+        res = oracle.hss(keys, p, eps, seed=seed, trace=True, schedule="equal")
+        assert res.status == 0
+        _, idx = _sorted_pos_to_input_index(keys, p)
+        _, rank_of = _global_order(keys, p)
+        rank_sp = [rank_of[idx[q]] for q in range(p)]
+        for r in range(res.rounds):
+            ints = _region(res, r, N, p)
+            cnt = {iv: 0 for iv in ints}
+            for _, sg, sp in res.samples[r]:
+                rk = rank_sp[int(sg)][int(sp)]
+                hit = [iv for iv in ints if iv[0] <= rk < iv[1]]
+                assert len(hit) == 1
+                cnt[hit[0]] += 1
+            for (lo, hi), c in cnt.items():
+                ln = hi - lo
+                q = min(1.0, (s * p / len(ints)) / ln) if ln > 0 else 1.0
+                mean, var = q * ln, ln * q * (1.0 - q)
+                assert abs(c - mean) <= 6.0 * math.sqrt(var) + 1.0
+                if q < 1.0:
+                    assert abs(mean - s * p / len(ints)) < 1e-6 * mean
+                pooled_got += c
+                pooled_mean += mean
+                pooled_var += var
+    assert abs(pooled_got - pooled_mean) <= 4.0 * math.sqrt(pooled_var) + 1.0
