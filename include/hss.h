@@ -445,7 +445,14 @@ typedef struct {
      * up to pack_keys keys (their keys are already in order between them, so
      * sorting the run sorts each).  1 .. 4096; 0 = 1024; 1 packs nothing. */
     uint32_t pack_keys;
-    uint32_t reserved[4];        /* zero */
+    /* First split of each segment of a local sort: 0 (default) on its top
+     * varying byte; 1 samples the segment first and, when the sample's top
+     * varying byte crowds its keys into few values (Gaussian clusters, heavy
+     * duplicates), splits on 255 splitters taken from the sorted sample (a
+     * binary search per key: measured slower than the extra split level it
+     * saves, so off by default). */
+    uint32_t first_split;
+    uint32_t reserved[3];        /* zero */
 } hss_tuning;
 
 /* Set the tuning (NULL restores the defaults); HSS_ERR_INVALID for a value

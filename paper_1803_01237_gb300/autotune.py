@@ -48,13 +48,15 @@ class Choice:
     child_interp: int = 0
     child_bucket_keys: int = 384
     pack_keys: int = 1024
+    first_split: int = 0
 
     def flags(self) -> int:
         return int(self.hist_flags) | (hss.FLAG_HOST_ROUNDS if self.host_rounds else 0)
 
     def apply(self):
         """Set the process-wide sort tiling; returns (oversample, flags) for the calls."""
-        hss.set_tuning(self.chip_max_keys, self.child_interp, self.child_bucket_keys, self.pack_keys)
+        hss.set_tuning(self.chip_max_keys, self.child_interp, self.child_bucket_keys, self.pack_keys,
+                       self.first_split)
         return float(self.oversample), self.flags()
 
 

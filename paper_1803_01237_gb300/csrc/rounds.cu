@@ -159,7 +159,76 @@ __global__ __launch_bounds__(1024) void k_intervals(uint32_t S, uint64_t N, uint
 // ---------------------------------------------------------------------------
 // Sampling.
 // ---------------------------------------------------------------------------
-__global__ __launch_bounds__(kSampThreads) void k_sample_mark(
+// Round-j Bernoulli marks of segment blockIdx.x (Sec. 4.2.2 step 4, Sec. 6):
+// every key of an unresolved interval draws its Philox word and is kept when
+// the word is below the round's threshold.  gridDim.y CTAs share a segment,
+// each taking an equal share of its position pairs; each thread walks a
+// contiguous run of pairs two at a time (two independent Philox chains in
+// flight) and the CTA adds its count to seg_cnt[s] (zeroed before the round).
+// Philox4x32-10 of the counters (m, seg, round, 0) for one (seed, seg,
+// round): the round keys and the parts of the first two rounds that do not
+// depend on m are computed once, so a word pair costs 18 of the 20
+// multiplies and none of the key additions.  Same words as sample_words.
+struct PairDraw {
+    uint32_t k0[10], k1[10];  // round keys
+    uint32_t c0_1, c1_1;      // words 0 and 1 after round 1 (independent of m)
+    uint32_t lo0_2, hi0_2;    // M0 x (word 0 after round 1), used in round 2
+    __device__ __forceinline__ void init(uint64_t seed, uint32_t seg, uint32_t round) {
+        const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u, M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+        uint32_t a = (uint32_t)seed, b = (uint32_t)(seed >> 32);
+#pragma unroll
+        for (int r = 0; r < 10; ++r) { k0[r] = a; k1[r] = b; a += W0; b += W1; }
+        // round 1 on (m, seg, round, 0): the M1 product and the new word 0
+        // involve only seg and round
+        const uint32_t lo1 = M1 * round, hi1 = __umulhi(M1, round);
+        c0_1 = hi1 ^ seg ^ k0[0];
+        c1_1 = lo1;
+        lo0_2 = M0 * c0_1;
+        hi0_2 = __umulhi(M0, c0_1);
+    }
+    __device__ __forceinline__ void words(uint32_t m, uint64_t& even, uint64_t& odd) const {
+        const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+        // round 1: only the M0 x m product varies
+        const uint32_t lo0 = M0 * m, hi0 = __umulhi(M0, m);
+        uint32_t c2 = hi0 ^ k1[0];  // ^ word 3 (0)
+        uint32_t c3 = lo0;
+        uint32_t c0 = c0_1, c1 = c1_1;
+        // round 2: the M0 product is known
+        {
+            const uint32_t l1 = M1 * c2, h1 = __umulhi(M1, c2);
+            const uint32_t n0 = h1 ^ c1 ^ k0[1];
+            const uint32_t n2 = hi0_2 ^ c3 ^ k1[1];
+            c0 = n0; c1 = l1; c2 = n2; c3 = lo0_2;
+        }
+#pragma unroll
+        for (int r = 2; r < 10; ++r) {
+            const uint32_t l0 = M0 * c0, h0 = __umulhi(M0, c0);
+            const uint32_t l1 = M1 * c2, h1 = __umulhi(M1, c2);
+            const uint32_t n0 = h1 ^ c1 ^ k0[r];
+            const uint32_t n2 = h0 ^ c3 ^ k1[r];
+            c0 = n0; c1 = l1; c2 = n2; c3 = l0;
+        }
+        even = ((uint64_t)c1 << 32) | c0;
+        odd = ((uint64_t)c3 << 32) | c2;
+    }
+};
+
+__device__ __forceinline__ void mark_pair(uint32_t a, uint32_t b, uint32_t m, uint64_t w0, uint64_t w1, uint64_t Tu,
+                                          bool all_u, uint64_t base, uint32_t* __restrict__ bitmap, uint32_t& cnt) {
+    const uint32_t p0 = 2 * m, p1 = 2 * m + 1;
+    if (p0 >= a && p0 < b && (all_u || w0 < Tu)) {
+        const uint64_t g = base + p0;
+        atomicOr(&bitmap[g >> 5], 1u << (g & 31));
+        ++cnt;
+    }
+    if (p1 >= a && p1 < b && (all_u || w1 < Tu)) {
+        const uint64_t g = base + p1;
+        atomicOr(&bitmap[g >> 5], 1u << (g & 31));
+        ++cnt;
+    }
+}
+
+__global__ __launch_bounds__(kSampThreads, 4) void k_sample_mark(
     const uint64_t* __restrict__ seg_off, uint32_t S, const uint32_t* __restrict__ Lpos, const uint32_t* __restrict__ Upos,
     const DCut* __restrict__ Lcut, const uint32_t* __restrict__ int_rep, const RoundCtl* __restrict__ ctl,
     uint64_t seed, uint32_t round, uint32_t* __restrict__ bitmap, uint32_t* __restrict__ seg_cnt,
@@ -175,39 +244,69 @@ __global__ __launch_bounds__(kSampThreads) void k_sample_mark(
     const uint32_t nint = ctl->nint;
     const uint64_t T = ctl->T;
     const bool take_all = ctl->take_all != 0;
+    PairDraw pd;
+    pd.init(seed, s, round);
     uint32_t cnt = 0;
     for (uint32_t u0 = 0; u0 < nint; u0 += kIntChunk) {
         const uint32_t nu = min((uint32_t)kIntChunk, nint - u0);
         const uint32_t P = load_seg_intervals(s, (uint32_t)(seg_off[s + 1] - base), S, u0, nu, Lpos, Upos, Lcut, int_rep,
                                               s_a, s_b, s_pre, s_warp);
-        for_each_pair(s_pre, nu, P, [&](uint32_t u, uint32_t f) {
-            const uint32_t a = s_a[u], b = s_b[u];
-            const uint32_t m = (a >> 1) + (f - s_pre[u]);
-            uint64_t w0, w1;
-            sample_words(seed, s, round, m, w0, w1);
-            const uint32_t p0 = 2 * m, p1 = 2 * m + 1;
-            uint64_t Tu = T;
-            bool all_u = take_all;
-            if (int_T) {  // equal-per-interval schedule
-                Tu = int_T[u0 + u];
-                all_u = int_all[u0 + u] != 0u;
+        // this CTA's share of the pairs, then each thread's run of it
+        const uint32_t F0 = (uint32_t)(((uint64_t)P * blockIdx.y) / gridDim.y);
+        const uint32_t F1 = (uint32_t)(((uint64_t)P * (blockIdx.y + 1)) / gridDim.y);
+        const uint32_t per = (F1 - F0 + kSampThreads - 1) / kSampThreads;
+        const uint32_t f0 = min(F1, F0 + threadIdx.x * per), f1 = min(F1, f0 + per);
+        if (f0 < f1) {
+            uint32_t u = find_interval(s_pre, nu, f0);
+            auto thr = [&](uint32_t uu, uint64_t& Tu, bool& all_u) {
+                Tu = T;
+                all_u = take_all;
+                if (int_T) {  // equal-per-interval schedule
+                    Tu = int_T[u0 + uu];
+                    all_u = int_all[u0 + uu] != 0u;
+                }
+            };
+            uint32_t f = f0;
+            for (; f + 1 < f1; f += 2) {
+                while (u + 1 < nu && s_pre[u + 1] <= f) ++u;
+                uint32_t v = u;
+                while (v + 1 < nu && s_pre[v + 1] <= f + 1) ++v;
+                const uint32_t m0 = (s_a[u] >> 1) + (f - s_pre[u]);
+                const uint32_t m1 = (s_a[v] >> 1) + (f + 1 - s_pre[v]);
+                uint64_t x0, x1, y0, y1;
+                pd.words(m0, x0, x1);
+                pd.words(m1, y0, y1);
+                uint64_t Tu, Tv;
+                bool au, av;
+                thr(u, Tu, au);
+                thr(v, Tv, av);
+                mark_pair(s_a[u], s_b[u], m0, x0, x1, Tu, au, base, bitmap, cnt);
+                mark_pair(s_a[v], s_b[v], m1, y0, y1, Tv, av, base, bitmap, cnt);
+                u = v;
             }
-            if (p0 >= a && p0 < b && (all_u || w0 < Tu)) {
-                const uint64_t g = base + p0;
-                atomicOr(&bitmap[g >> 5], 1u << (g & 31));
-                ++cnt;
+            if (f < f1) {
+                while (u + 1 < nu && s_pre[u + 1] <= f) ++u;
+                const uint32_t m0 = (s_a[u] >> 1) + (f - s_pre[u]);
+                uint64_t x0, x1, Tu;
+                bool au;
+                pd.words(m0, x0, x1);
+                thr(u, Tu, au);
+                mark_pair(s_a[u], s_b[u], m0, x0, x1, Tu, au, base, bitmap, cnt);
             }
-            if (p1 >= a && p1 < b && (all_u || w1 < Tu)) {
-                const uint64_t g = base + p1;
-                atomicOr(&bitmap[g >> 5], 1u << (g & 31));
-                ++cnt;
-            }
-        });
+        }
         __syncthreads();
     }
     uint32_t tot;
     block_incl_scan<uint32_t>(cnt, 0u, AddU32(), s_warp, tot);
-    if (threadIdx.x == 0) seg_cnt[s] = tot;
+    if (threadIdx.x == 0 && tot) atomicAdd(&seg_cnt[s], tot);
+}
+
+// CTAs per segment of the marking pass: about 16K position pairs each in a
+// round that samples whole segments, at most 8 (each one reads the
+// segment's intervals).
+static unsigned mark_chunks(uint64_t N, uint32_t p) {
+    const uint64_t pairs = (N / std::max<uint32_t>(p, 1) + 1) / 2;
+    return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(8, pairs / 16384));
 }
 
 __global__ __launch_bounds__(1024) void k_count_scan(const uint32_t* __restrict__ seg_cnt, uint32_t p, uint32_t* __restrict__ seg_cnt_off,
@@ -682,8 +781,12 @@ __global__ void k_round_decide(RoundCtl* ctl, uint64_t cap, uint64_t N, uint32_t
 static void enqueue_sampling(const RoundWs& ws, const uint64_t* d_seg_off, uint64_t N, uint32_t p, uint32_t S,
                              uint64_t seed, uint32_t round, cudaStream_t st, bool per_interval) {
     cudaMemsetAsync(ws.bitmap, 0, (N / 32 + 2) * sizeof(uint32_t), st);
-    HSS_LAUNCH(k_sample_mark, p, kSampThreads, 0, st, d_seg_off, S, ws.Lpos, ws.Upos, ws.Lcut, ws.int_rep, ws.ctl, seed,
-               round, ws.bitmap, ws.seg_cnt, per_interval ? ws.int_T : nullptr, per_interval ? ws.int_all : nullptr);
+    cudaMemsetAsync(ws.seg_cnt, 0, (size_t)p * sizeof(uint32_t), st);
+    // round 1 samples whole segments: several CTAs share each; later rounds
+    // sample narrow intervals, one CTA per segment
+    HSS_LAUNCH(k_sample_mark, dim3(p, round == 1 ? mark_chunks(N, p) : 1u), kSampThreads, 0, st, d_seg_off, S, ws.Lpos,
+               ws.Upos, ws.Lcut, ws.int_rep, ws.ctl, seed, round, ws.bitmap, ws.seg_cnt,
+               per_interval ? ws.int_T : nullptr, per_interval ? ws.int_all : nullptr);
     HSS_LAUNCH(k_count_scan, 1, 1024, 0, st, ws.seg_cnt, p, ws.seg_cnt_off, ws.cap, ws.ctl);
 }
 
@@ -727,8 +830,10 @@ cudaError_t enqueue_device_round(const uint64_t* skeys, const uint64_t* d_seg_of
     HSS_LAUNCH(k_intervals, 1, 1024, 0, st, S, N, p, tol, oversample, ws.Lcut, ws.Ucut, ws.res, ws.int_rep, ws.ctl,
                schedule, 0ull, 0u, ws.int_T, ws.int_all);
     if ((e = cudaMemsetAsync(ws.bitmap, 0, (N / 32 + 2) * sizeof(uint32_t), st)) != cudaSuccess) return e;
-    HSS_LAUNCH(k_sample_mark, p, kSampThreads, 0, st, d_seg_off, S, ws.Lpos, ws.Upos, ws.Lcut, ws.int_rep, ws.ctl, 0ull,
-               0u, ws.bitmap, ws.seg_cnt, per_interval ? ws.int_T : nullptr, per_interval ? ws.int_all : nullptr);
+    if ((e = cudaMemsetAsync(ws.seg_cnt, 0, (size_t)p * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    HSS_LAUNCH(k_sample_mark, dim3(p, 1u), kSampThreads, 0, st, d_seg_off, S, ws.Lpos, ws.Upos, ws.Lcut, ws.int_rep,
+               ws.ctl, 0ull, 0u, ws.bitmap, ws.seg_cnt, per_interval ? ws.int_T : nullptr,
+               per_interval ? ws.int_all : nullptr);
     HSS_LAUNCH(k_count_scan, 1, 1024, 0, st, ws.seg_cnt, p, ws.seg_cnt_off, cap, ws.ctl);
     HSS_LAUNCH(k_round_decide, 1, 1, 0, st, ws.ctl, cap, N, p, hist_mode, loop);
     return cudaGetLastError();

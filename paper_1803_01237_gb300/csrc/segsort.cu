@@ -37,6 +37,7 @@ static std::atomic<uint32_t> g_chip_max{(uint32_t)kC1Cap};
 static std::atomic<uint32_t> g_child_interp{0u};
 static std::atomic<uint32_t> g_child_keys{384u};
 static std::atomic<uint32_t> g_pack_keys{1024u};
+static std::atomic<uint32_t> g_splitters{0u};
 
 int set_tuning(const hss_tuning* t) {
     if (!t) {
@@ -44,13 +45,14 @@ int set_tuning(const hss_tuning* t) {
         g_child_interp = 0u;
         g_child_keys = 384u;
         g_pack_keys = 1024u;
+        g_splitters = 0u;
         return HSS_OK;
     }
     const uint32_t cm = t->chip_max_keys ? t->chip_max_keys : (uint32_t)kC1Cap;
     const uint32_t ck = t->child_bucket_keys ? t->child_bucket_keys : 384u;
     const uint32_t pk = t->pack_keys ? t->pack_keys : 1024u;
     if ((cm != (uint32_t)kC1Cap && cm != (uint32_t)kSmallCap) || t->child_interp > 1u || ck < 128u || ck > 4096u ||
-        pk > 4096u)
+        pk > 4096u || t->first_split > 1u)
         return HSS_ERR_INVALID;
     for (uint32_t r : t->reserved)
         if (r) return HSS_ERR_INVALID;
@@ -58,6 +60,7 @@ int set_tuning(const hss_tuning* t) {
     g_child_interp = t->child_interp;
     g_child_keys = ck;
     g_pack_keys = pk;
+    g_splitters = t->first_split;
     return HSS_OK;
 }
 void get_tuning(hss_tuning* t) {
@@ -66,6 +69,7 @@ void get_tuning(hss_tuning* t) {
     t->child_interp = g_child_interp;
     t->child_bucket_keys = g_child_keys;
     t->pack_keys = g_pack_keys;
+    t->first_split = g_splitters;
 }
 
 // Large segments of a level hold more than kC1Cap keys (keys alone split above
@@ -91,6 +95,8 @@ size_t segsort_ws_bytes(uint64_t N, uint64_t nseg) {
     b += align_up(d.ml * 4, 256);                                     // large_seg
     b += align_up(d.tiles * 2 * kRadix * 2, 256);                     // tile_hist
     b += align_up(d.tiles, 256);                                      // tile_skew
+    b += align_up(std::min(nseg, d.ml) * kRadix * 8, 256);           // spl_tab
+    b += align_up(std::min(nseg, d.ml), 256);                        // spl_mode
     b += 2 * align_up(d.ml * 8, 256);                                 // vor, vand
     b += 4 * align_up(d.ml * 4, 256);                                 // msd_shift x2, spec, direct
     b += 2 * align_up(d.ml * 8, 256);                                 // msd_base, msd_mult
@@ -118,6 +124,9 @@ SegSortWs segsort_ws_carve(void* base, uint64_t N, uint64_t nseg, uint32_t* err)
     w.large_seg = (uint32_t*)take(d.ml * 4);
     w.tile_hist = (uint16_t*)take(d.tiles * 2 * kRadix * 2);
     w.tile_skew = (uint8_t*)take(d.tiles);
+    w.max_spl = std::min(nseg, d.ml);
+    w.spl_tab = (uint64_t*)take(w.max_spl * kRadix * 8);
+    w.spl_mode = (uint8_t*)take(w.max_spl);
     w.vor = (unsigned long long*)take(d.ml * 8);
     w.vand = (unsigned long long*)take(d.ml * 8);
     w.msd_shift[0] = (uint32_t*)take(d.ml * 4);
@@ -1537,13 +1546,89 @@ __global__ __launch_bounds__(1024) void k_plan_write(const uint64_t* __restrict_
 // msd_shift flag: the split interpolated the key range (no byte is fixed in
 // its sub-buckets).
 constexpr uint32_t kShiftInterp = 0x100u;
+// msd_shift flag: the split's digit is the bucket among 255 sampled splitters.
+constexpr uint32_t kShiftSplit = 0x200u;
+
+// Bucket of key k among the 255 sorted splitters spl[0..254]: the number of
+// splitters <= k (0..255), by eight halvings without branches.  Monotone in
+// the key, so it serves as a digit of the split.
+__device__ __forceinline__ uint32_t splitter_digit(const uint64_t* spl, uint64_t k) {
+    uint32_t i = 0;
+#pragma unroll
+    for (uint32_t step = 128; step > 0; step >>= 1)
+        if (spl[i + step - 1] <= k) i += step;
+    return i;
+}
+
+// Splitters of the first split of a segment with skewed keys (Gaussian
+// clusters, heavy duplicates), where the top varying byte would leave most of
+// the segment in a few buckets and cost another level: one CTA per segment
+// split at this level draws 2048 keys at evenly spaced positions; when the
+// busiest value of the sample's top varying byte holds more than 4x its
+// share (32 of 2048), it sorts the sample and keeps every 8th key as the 255
+// splitters (spl_mode 1), else the byte split stays (spl_mode 0).
+constexpr int kSplSample = 2048;
+__global__ __launch_bounds__(256) void k_seg_sample(const uint64_t* __restrict__ kin, const uint64_t* __restrict__ seg_lo,
+                                                    const uint64_t* __restrict__ seg_hi,
+                                                    const uint32_t* __restrict__ large_seg,
+                                                    const uint32_t* __restrict__ counters, uint64_t flip_in,
+                                                    uint64_t* __restrict__ spl_tab, uint8_t* __restrict__ spl_mode) {
+    __shared__ uint64_t s_k[kSplSample];
+    __shared__ uint32_t s_h[kRadix];
+    __shared__ unsigned long long s_or[8], s_and[8];
+    __shared__ uint32_t s_flag;
+    const uint32_t id = blockIdx.x;
+    if (id >= counters[19]) return;  // uniform
+    const uint32_t s = large_seg[id];
+    const uint64_t lo = seg_lo[s], n = seg_hi[s] - lo;
+    const int tid = threadIdx.x;
+    s_h[tid] = 0;
+    unsigned long long o = 0, an = ~0ull;
+    for (int i = tid; i < kSplSample; i += 256) {
+        const uint64_t pos = (uint64_t)(((unsigned __int128)(2 * i + 1) * n) / (2 * kSplSample));
+        const uint64_t k = kin[lo + pos] ^ flip_in;
+        s_k[i] = k;
+        o |= k;
+        an &= k;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        o |= __shfl_xor_sync(0xffffffffu, o, off);
+        an &= __shfl_xor_sync(0xffffffffu, an, off);
+    }
+    if ((tid & 31) == 0) { s_or[tid >> 5] = o; s_and[tid >> 5] = an; }
+    __syncthreads();
+    unsigned long long vo = 0, va = ~0ull;
+    for (int i = 0; i < 8; ++i) { vo |= s_or[i]; va &= s_and[i]; }
+    const unsigned long long vary = vo ^ va;
+    if (vary == 0ull) {  // uniform: a single value in the sample
+        if (tid == 0) spl_mode[id] = 0u;
+        return;
+    }
+    const int sh = 8 * (int)((uint32_t)(63 - __clzll((long long)vary)) >> 3);
+    for (int i = tid; i < kSplSample; i += 256) atomicAdd(&s_h[(uint32_t)(s_k[i] >> sh) & 255u], 1u);
+    __syncthreads();
+    const int crowded = __syncthreads_or(s_h[tid] > 4u * (kSplSample / kRadix));
+    if (!crowded) {
+        if (tid == 0) spl_mode[id] = 0u;
+        return;
+    }
+    cta_bitonic_sort<256>(s_k, 0u, (uint32_t)kSplSample, [](uint32_t i) { return i; });
+    uint64_t* spl = spl_tab + (uint64_t)id * kRadix;
+    for (int i = tid; i < kRadix - 1; i += 256) spl[i] = s_k[(i + 1) * (kSplSample / kRadix) - 1];
+    if (tid == 0) {
+        spl[kRadix - 1] = ~0ull;
+        spl_mode[id] = 1u;
+    }
+    (void)s_flag;
+}
 
 __device__ __forceinline__ int spec_window(const uint32_t* __restrict__ prev_shift, uint32_t s) {
     // the byte below the parent split's window (a sub-bucket's keys agree on
     // that window and above); the top byte at the first level
     if (!prev_shift) return 7;
     const uint32_t ps = prev_shift[s >> 8];
-    return (ps & kShiftInterp) ? 7 : (ps >= 8 ? (int)(ps >> 3) - 1 : 0);
+    return (ps & (kShiftInterp | kShiftSplit)) ? 7 : (ps >= 8 ? (int)(ps >> 3) - 1 : 0);
 }
 
 // A tile is skewed when one digit holds more than an eighth of it: the
@@ -1566,14 +1651,18 @@ __global__ __launch_bounds__(256) void k_tile_stats(const uint64_t* __restrict__
                                                     const uint64_t* __restrict__ hint_lo, const uint64_t* __restrict__ hint_mult,
                                                     const uint64_t* __restrict__ hint_hi,
                                                     const uint32_t* __restrict__ prev_shift, uint32_t* __restrict__ spec_out,
-                                                    uint64_t flip_in) {
+                                                    uint64_t flip_in, const uint64_t* __restrict__ spl_tab,
+                                                    const uint8_t* __restrict__ spl_mode) {
     __shared__ uint32_t s_h[kRadix];
     __shared__ unsigned long long s_or[8], s_and[8];
+    __shared__ uint64_t s_spl[kRadix];
     const uint32_t t = blockIdx.x;
     if (t >= tile_start[nseg]) return;  // uniform
     s_h[threadIdx.x] = 0;
-    __syncthreads();
     const uint32_t s = tile_seg[t], id = large_id[s];
+    const bool bysplit = spl_mode && spl_mode[id];  // uniform per CTA
+    if (bysplit) s_spl[threadIdx.x] = spl_tab[(uint64_t)id * kRadix + threadIdx.x];
+    __syncthreads();
     const uint64_t lo = seg_lo[s], n = seg_hi[s] - lo;
     const uint32_t ti = t - tile_start[s];
     const uint64_t a = (uint64_t)ti * kOsTile, b = min(n, a + kOsTile);
@@ -1599,7 +1688,8 @@ __global__ __launch_bounds__(256) void k_tile_stats(const uint64_t* __restrict__
         const uint64_t k = kin[lo + e] ^ flip_in;
         o |= k;
         an &= k;
-        const uint32_t d = win ? split_digit(k, 0, hb, hm) : (uint32_t)(k >> sh) & 255u;
+        const uint32_t d =
+            bysplit ? splitter_digit(s_spl, k) : (win ? split_digit(k, 0, hb, hm) : (uint32_t)(k >> sh) & 255u);
         atomicAdd(&s_h[d], 1u);
     }
 #pragma unroll
@@ -1627,7 +1717,8 @@ __global__ __launch_bounds__(256) void k_tile_recount(const uint64_t* __restrict
                                                       const uint32_t* __restrict__ tile_start,
                                                       const uint32_t* __restrict__ tile_seg,
                                                       const uint32_t* __restrict__ large_id, uint16_t* __restrict__ tile_hist,
-                                                      uint8_t* __restrict__ tile_skew, const unsigned long long* __restrict__ vor,
+                                                      uint8_t* __restrict__ tile_skew, const uint8_t* __restrict__ spl_mode,
+                                                      const unsigned long long* __restrict__ vor,
                                                       const unsigned long long* __restrict__ vand,
                                                       const uint32_t* __restrict__ spec, uint64_t flip_in) {
     __shared__ uint32_t s_h[kRadix];
@@ -1636,6 +1727,7 @@ __global__ __launch_bounds__(256) void k_tile_recount(const uint64_t* __restrict
     s_h[threadIdx.x] = 0;
     __syncthreads();
     const uint32_t s = tile_seg[t], id = large_id[s];
+    if (spl_mode && spl_mode[id]) return;  // uniform: the statistics pass counted the splitter buckets
     const unsigned long long vary = vor[id] ^ vand[id];
     if (vary == 0ull) return;
     const uint32_t w = (uint32_t)(63 - __clzll((long long)vary)) >> 3;
@@ -1669,7 +1761,8 @@ __global__ __launch_bounds__(256) void k_msd_prep(const uint64_t* __restrict__ s
                                                   uint32_t* __restrict__ tile_off, uint32_t chip_max,
                                                   uint32_t* __restrict__ large_mask, uint32_t* __restrict__ any_large,
                                                   uint64_t* __restrict__ cmin, uint64_t* __restrict__ cmax,
-                                                  uint32_t level_chip_max, uint32_t pack_keys) {
+                                                  uint32_t level_chip_max, uint32_t pack_keys,
+                                                  const uint8_t* __restrict__ spl_mode) {
     __shared__ uint32_t s_c[kRadix], s_x[kRadix], s_warp[32], s_end[kRadix];
     const uint32_t id = blockIdx.x;
     if (id >= counters[19]) return;
@@ -1687,6 +1780,8 @@ __global__ __launch_bounds__(256) void k_msd_prep(const uint64_t* __restrict__ s
         shift = 8 * w;
         row = w == spec[id] ? 0u : 1u;
     }
+    const bool bysplit = spl_mode && spl_mode[id];
+    if (bysplit) row = 0;
     const bool dir = vary == 0ull;
     const uint32_t d = threadIdx.x;
     const uint32_t t0 = tile_start[s], t1 = tile_start[s + 1];
@@ -1750,7 +1845,7 @@ __global__ __launch_bounds__(256) void k_msd_prep(const uint64_t* __restrict__ s
         run += h[(uint64_t)t * (2 * kRadix)];
     }
     if (d == 0) {
-        msd_shift[id] = shift | (hint_lo ? kShiftInterp : 0u);
+        msd_shift[id] = shift | (hint_lo ? kShiftInterp : 0u) | (bysplit ? kShiftSplit : 0u);
         msd_base[id] = base;
         msd_mult[id] = mult;
         direct[id] = dir ? 1u : 0u;
@@ -1777,6 +1872,7 @@ struct SplitArgs {
     const uint32_t* large_id;
     const uint32_t* tile_off;  // [tile][256] destination of the tile's digit-d keys, relative to the segment
     const uint8_t* tile_skew;  // [tile] one digit holds more than an eighth of the tile
+    const uint64_t* spl_tab;   // [large id][256] sampled splitters (segments split with kShiftSplit)
     const uint32_t* msd_shift;
     const uint64_t* msd_base;
     const uint64_t* msd_mult;
@@ -1801,6 +1897,7 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
     __shared__ uint64_t s_gbase[kRadix];
     __shared__ uint32_t s_warp[32];
     __shared__ uint64_t s_mn[kRadix], s_mx[kRadix];
+    __shared__ uint64_t s_spl[kRadix];
     __shared__ uint32_t s_mask[8];
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -1817,6 +1914,7 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
     const int shift = (int)(A.msd_shift[id] & 0xffu);
     const uint64_t dbase = A.msd_base[id];
     const uint64_t dmult = A.msd_mult[id];
+    const bool bysplit = (A.msd_shift[id] & kShiftSplit) != 0u;  // uniform per CTA
     const bool dir = A.direct[id] != 0u;
     uint64_t* kout = dir ? A.kfinal : A.kout;
     uint32_t* pout = dir ? A.pfinal : A.pout;
@@ -1829,6 +1927,13 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
         if (tid < kRadix) { s_mn[tid] = ~0ull; s_mx[tid] = 0ull; }
         if (tid < 8) s_mask[tid] = A.large_mask[(uint64_t)id * 8 + tid];
     }
+    if (bysplit) {
+        if (tid < kRadix) s_spl[tid] = A.spl_tab[(uint64_t)id * kRadix + tid];
+        __syncthreads();
+    }
+    auto dig = [&](uint64_t k) -> uint32_t {
+        return bysplit ? splitter_digit(s_spl, k) : split_digit(k, shift, dbase, dmult);
+    };
 
     uint64_t key[kOsItems];
     uint32_t pay[kOsItems];
@@ -1852,7 +1957,7 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
         for (int i = 0; i < kOsItems / 4; ++i) dpk[i] = 0;
 #pragma unroll
         for (int i = 0; i < kOsItems; ++i)
-            dpk[i >> 2] |= split_digit(key[i], shift, dbase, dmult) << (8 * (i & 3));
+            dpk[i >> 2] |= dig(key[i]) << (8 * (i & 3));
         auto digit_of = [&](int i) -> uint32_t {
             return (wbase + i * 32 < count) ? (dpk[i >> 2] >> (8 * (i & 3))) & 255u : (uint32_t)kRadix;
         };
@@ -1880,7 +1985,7 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
 #pragma unroll
             for (int i = 0; i < kOsItems; ++i) {
                 const uint32_t d =
-                    wbase + i * 32 < count ? split_digit(key[i], shift, dbase, dmult) : (uint32_t)kRadix;
+                    wbase + i * 32 < count ? dig(key[i]) : (uint32_t)kRadix;
                 const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
                 const uint32_t eq = __ballot_sync(0xffffffffu, d == d0);
                 uint32_t b0 = 0;
@@ -1893,7 +1998,7 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
 #pragma unroll
             for (int i = 0; i < kOsItems; ++i) {
                 if (wbase + i * 32 < count) {
-                    const uint32_t d = split_digit(key[i], shift, dbase, dmult);
+                    const uint32_t d = dig(key[i]);
                     rank[i] = d | (atomicAdd(&s_total[d], 1u) << 8);
                 }
             }
@@ -2109,6 +2214,7 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
     const bool child_interp = g_child_interp.load() != 0u;
     const uint32_t child_keys = g_child_keys.load();
     const uint32_t pack_keys = g_pack_keys.load();
+    const bool use_splitters = g_splitters.load() != 0u;
     cudaError_t e;
     Level L{src, psrc, d_seg_off, d_seg_off + 1, nseg, flip_in ? kSignBit : 0ull, hint_lo, hint_mult, 0};
     if (N <= (uint64_t)kSmallCap) {
@@ -2217,16 +2323,24 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
         if ((e = cudaMemsetAsync(ws.vand, 0xff, (size_t)n_large * 8, st)) != cudaSuccess) return e;
         const int buf = L.depth & 1;
         const uint32_t* prev_shift = L.depth > 0 ? ws.msd_shift[buf ^ 1] : nullptr;
+        // The first split of a level-0 segment may take sampled splitters
+        // (skewed keys); later levels and hinted splits keep their digits.
+        const bool bysplit_level = use_splitters && L.depth == 0 && !L.hint_lo && n_large <= ws.max_spl;
+        if (bysplit_level)
+            HSS_LAUNCH(k_seg_sample, n_large, 256, 0, st, L.in, L.seg_lo, L.seg_hi, ws.large_seg, ws.counters, L.flip_in,
+                       ws.spl_tab, ws.spl_mode);
         HSS_LAUNCH(k_tile_stats, tiles, 256, 0, st, L.in, L.seg_lo, L.seg_hi, L.nseg, ws.tile_start, ws.tile_seg, ws.large_id,
                    ws.tile_hist, ws.tile_skew, ws.vor, ws.vand, L.hint_lo, L.hint_mult, L.hint_hi, prev_shift, ws.spec,
-                   L.flip_in);
+                   L.flip_in, bysplit_level ? ws.spl_tab : nullptr, bysplit_level ? ws.spl_mode : nullptr);
         if (!L.hint_lo)
             HSS_LAUNCH(k_tile_recount, tiles, 256, 0, st, L.in, L.seg_lo, L.seg_hi, L.nseg, ws.tile_start, ws.tile_seg, ws.large_id,
-                       ws.tile_hist, ws.tile_skew, ws.vor, ws.vand, ws.spec, L.flip_in);
+                       ws.tile_hist, ws.tile_skew, bysplit_level ? ws.spl_mode : nullptr, ws.vor, ws.vand, ws.spec,
+                       L.flip_in);
         HSS_LAUNCH(k_msd_prep, n_large, 256, 0, st, L.seg_lo, ws.large_seg, ws.counters, ws.tile_start, ws.tile_hist,
                    ws.vor, ws.vand, L.hint_lo, L.hint_mult, ws.msd_base, ws.msd_mult, ws.msd_shift[buf], ws.spec,
                    ws.direct, ws.sub_lo[buf], ws.sub_hi[buf], ws.tile_off, child_interp ? chip_max : 0xffffffffu,
-                   ws.large_mask, ws.any_large, ws.cmin[buf], ws.cmax[buf], chip_max, std::min(pack_keys, chip_max));
+                   ws.large_mask, ws.any_large, ws.cmin[buf], ws.cmax[buf], chip_max, std::min(pack_keys, chip_max),
+                   bysplit_level ? ws.spl_mode : nullptr);
         // The split pass: level buffers alternate tmp, dst, tmp, ... after src.
         uint64_t* next = (L.depth & 1) ? dst : tmp;
         uint32_t* pnext = PAY ? ((L.depth & 1) ? pdst : ptmp) : nullptr;
@@ -2235,7 +2349,7 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
         A.pin = L.pin; A.pout = pnext; A.pfinal = pdst;
         A.seg_lo = L.seg_lo; A.seg_hi = L.seg_hi; A.nseg = L.nseg;
         A.tile_start = ws.tile_start; A.tile_seg = ws.tile_seg; A.large_id = ws.large_id;
-        A.tile_off = ws.tile_off; A.tile_skew = ws.tile_skew; A.msd_shift = ws.msd_shift[buf]; A.msd_base = ws.msd_base; A.msd_mult = ws.msd_mult;
+        A.tile_off = ws.tile_off; A.tile_skew = ws.tile_skew; A.spl_tab = ws.spl_tab; A.msd_shift = ws.msd_shift[buf]; A.msd_base = ws.msd_base; A.msd_mult = ws.msd_mult;
         A.direct = ws.direct;
         A.large_mask = ws.large_mask; A.any_large = ws.any_large; A.cmin = ws.cmin[buf]; A.cmax = ws.cmax[buf];
         A.err = ws.err;

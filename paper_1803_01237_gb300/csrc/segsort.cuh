@@ -44,6 +44,9 @@ struct SegSortWs {
     uint32_t* large_seg;   // [max_large]
     uint16_t* tile_hist;   // [max_tiles][2][256] digit counts of every tile: the speculative window, then a recount
     uint8_t* tile_skew;    // [max_tiles] one digit holds more than an eighth of the tile
+    uint64_t max_spl;      // segments of the first level that can take sampled splitters
+    uint64_t* spl_tab;     // [max_spl][256] sampled splitters of each first-level segment split
+    uint8_t* spl_mode;     // [max_spl] 1: that segment's first split uses them
     unsigned long long* vor;   // [max_large] OR of the keys
     unsigned long long* vand;  // [max_large] AND of the keys
     uint32_t* msd_shift[2];  // [max_large] split window (bits) of each large segment, by level parity

@@ -37,7 +37,8 @@ def _case(gen):
 
 @pytest.mark.parametrize("gen", list(_GENS))
 @pytest.mark.parametrize("tiling", [(4096, 0, 384), (14336, 0, 384), (4096, 1, 384), (4096, 1, 128), (14336, 1, 4096),
-                                    (4096, 0, 384, 1), (4096, 0, 384, 4096), (14336, 0, 384, 4096)])
+                                    (4096, 0, 384, 1), (4096, 0, 384, 4096), (14336, 0, 384, 4096),
+                                    (4096, 0, 384, 0, 1), (14336, 1, 384, 1, 1)])
 def test_tilings_give_the_oracle_result(hss, gen, tiling):
     p, eps, seed = 16, 0.02, 3
     keys, ref = _case(gen)
