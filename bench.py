@@ -69,6 +69,7 @@ def _measured_peaks():
 # device helpers.  The committed traffic record holds their hash.
 _SPLIT_REGIONS = (("__device__ __forceinline__ uint32_t split_digit(", "// Exclusive scan of 256 shared values"),
                   ("__device__ __forceinline__ uint32_t warp_peers8(", "// On-chip sort of segments"),
+                  ("__device__ __forceinline__ uint32_t splitter_digit(", "// Splitters of the first split"),
                   ("struct SplitArgs {", "__global__ void k_even_offsets("))
 
 

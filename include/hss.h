@@ -431,8 +431,8 @@ int hss_cdf_propose(const hss_cdf_model* d_model, uint32_t p, uint32_t per_split
  * splitters and offsets do not depend on them.
  * ------------------------------------------------------------------------- */
 typedef struct {
-    /* Keys alone: the largest segment sorted on chip; a larger one is split
-     * again.  4096 (the default) or 14336 (the largest on-chip class). */
+    /* The largest segment sorted on chip; a larger one is split again.  4096
+     * (the default) or 14336 (the largest on-chip class). */
     uint32_t chip_max_keys;
     /* 1: a sub-bucket that is split again interpolates its own key range
      * (gathered by the split that made it) with a digit width giving about

@@ -952,7 +952,7 @@ __device__ __forceinline__ void cta_bitonic_sort(uint64_t* base, uint32_t a, uin
 template <int THREADS>
 constexpr int keys_min_blocks() { return THREADS <= 128 ? 8 : (THREADS <= 256 ? 3 : 1); }
 
-template <int THREADS, int CAP, int R, bool PREFETCH, int TIE, int AGG = 0, int SWZ = 0>
+template <int THREADS, int CAP, int R, bool PREFETCH>
 __global__ __launch_bounds__(THREADS, keys_min_blocks<THREADS>()) void k_small_keys(
     const uint64_t* kin, uint64_t* kout, const uint64_t* __restrict__ seg_lo, const uint64_t* __restrict__ seg_hi,
     const uint32_t* __restrict__ list, const uint32_t* __restrict__ nlist, uint64_t nseg, uint32_t min_n,
@@ -963,8 +963,7 @@ __global__ __launch_bounds__(THREADS, keys_min_blocks<THREADS>()) void k_small_k
     static_assert(CAP % THREADS == 0 && R % THREADS == 0 && R <= 4096 && CAP <= 16384 && WARPS <= 16 &&
                       THREADS >= 64,
                   "keys sort shape");
-    // dp[i]: digit in bits 0..11, slot in its group in bits 12..25, the
-    // group's size (when 2..kTinyGroup-1) in bits 26..31
+    // dp[i]: digit in bits 0..11, slot in its group from bit 12
     constexpr uint32_t kDigitMask = 4095u, kSlotShift = 12, kSlotMask = 16383u;
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* s_key = (uint64_t*)smem;                                              // CAP + 2
@@ -1042,13 +1041,8 @@ __global__ __launch_bounds__(THREADS, keys_min_blocks<THREADS>()) void k_small_k
         const uint64_t* src = PREFETCH ? s_stage : kin + base;
         // The sorted keys: key j at s_key[j + ho], so that the part written
         // back by a bulk copy starts on a 16-byte boundary.
-        const uint32_t ho = PREFETCH && !SWZ ? head_of(kout + base) : 0u;
+        const uint32_t ho = PREFETCH ? head_of(kout + base) : 0u;
         uint64_t* sk = s_key + ho;
-        // key j of the sorted segment at sk[SI(j)]: with SWZ the 16-key
-        // blocks are permuted inside (XOR with the block number), so threads
-        // walking their own ranges of about 8 keys, 64 bytes apart, meet
-        // different banks
-        auto SI = [](uint32_t i) -> uint32_t { return SWZ ? (i ^ ((i >> 4) & 15u)) : i; };
         // Items past the segment are skipped by a uniform break (n is the
         // same for the whole CTA), so a short segment costs no predicated work.
         uint64_t key[ITEMS];
@@ -1109,7 +1103,6 @@ __global__ __launch_bounds__(THREADS, keys_min_blocks<THREADS>()) void k_small_k
             mult64 = interp_mult(hi - lo, (uint32_t)R);
         }
         uint32_t dp[ITEMS];
-        const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             if ((uint32_t)(i * THREADS) >= n) break;
@@ -1123,19 +1116,7 @@ __global__ __launch_bounds__(THREADS, keys_min_blocks<THREADS>()) void k_small_k
                     d = mult64 ? min((uint32_t)__umul64hi(off, mult64), (uint32_t)R - 1) : (uint32_t)off;
                 }
             }
-            if (AGG) {
-                // The lanes that share lane 0's group (a run of duplicates)
-                // take their slots with one atomic; the others one each.
-                const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
-                const uint32_t eq = __ballot_sync(0xffffffffu, d == d0);
-                const bool agg = __popc(eq) > 1;
-                uint32_t b0 = 0;
-                if (lane == 0 && agg && d0 < (uint32_t)R) b0 = atomicAdd(&s_start[d0], (uint32_t)__popc(eq));
-                b0 = __shfl_sync(0xffffffffu, b0, 0);
-                if (d < (uint32_t)R)
-                    dp[i] = d | ((agg && d == d0 ? b0 + (uint32_t)__popc(eq & lt_mask) : atomicAdd(&s_start[d], 1u))
-                                 << kSlotShift);
-            } else if (d < (uint32_t)R) {
+            if (d < (uint32_t)R) {
                 dp[i] = d | (atomicAdd(&s_start[d], 1u) << kSlotShift);
             }
         }
@@ -1153,19 +1134,12 @@ __global__ __launch_bounds__(THREADS, keys_min_blocks<THREADS>()) void k_small_k
         mx = 0;
 #pragma unroll
         for (int i = 0; i < WARPS; ++i) mx = max(mx, s_warp[i]);
-        // Scatter into group order.  A key whose group holds 2..kTinyGroup-1
-        // keys notes the group's size (6 bits above the digit and slot): its
-        // final place inside the group is ranked below.
+        // scatter into group order
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             if ((uint32_t)(i * THREADS) >= n) break;
             const uint32_t e = tid + i * THREADS;
-            if (e < n) {
-                const uint32_t d = dp[i] & kDigitMask;
-                const uint32_t a = s_start[d], c = s_start[d + 1] - a;
-                sk[SI(a + (dp[i] >> kSlotShift))] = key[i];
-                if (c >= 2u && c < (uint32_t)kTinyGroup) dp[i] |= c << 26;
-            }
+            if (e < n) sk[s_start[dp[i] & kDigitMask] + (dp[i] >> kSlotShift)] = key[i];
         }
         __syncthreads();
         if (mx >= (uint32_t)kTinyGroup) {
@@ -1178,7 +1152,7 @@ __global__ __launch_bounds__(THREADS, keys_min_blocks<THREADS>()) void k_small_k
                 if (tid + i * THREADS >= n) continue;
                 const uint32_t d = dp[i] & kDigitMask;
                 const uint32_t a = s_start[d];
-                if (s_start[d + 1] - a >= (uint32_t)kTinyGroup && sk[SI(a)] != sk[SI(a + ((dp[i] >> kSlotShift) & kSlotMask))])
+                if (s_start[d + 1] - a >= (uint32_t)kTinyGroup && sk[a] != sk[a + ((dp[i] >> kSlotShift) & kSlotMask)])
                     s_mark[d] = 1u;
             }
             __syncthreads();
@@ -1199,10 +1173,10 @@ __global__ __launch_bounds__(THREADS, keys_min_blocks<THREADS>()) void k_small_k
             for (uint32_t q = 0; q < nmixed; ++q) {
                 const uint32_t d = s_flag[1 + q];
                 const uint32_t a = s_start[d];
-                cta_bitonic_sort<THREADS>(sk, a, s_start[d + 1] - a, SI);
+                cta_bitonic_sort<THREADS>(sk, a, s_start[d + 1] - a, [](uint32_t i) { return i; });
             }
         }
-        if (TIE == 0 && mx > 1u) {
+        if (mx > 1u) {
             // Every group of 2..kTinyGroup-1 keys is sorted in place by the
             // thread owning it (each thread owns G consecutive groups; the
             // groups hold a few keys, nearly in order); a large group holding
@@ -1213,83 +1187,51 @@ __global__ __launch_bounds__(THREADS, keys_min_blocks<THREADS>()) void k_small_k
             const uint32_t ga = s_start[tid * G], gb = s_start[tid * G + G];
             if (gb - ga < (uint32_t)kTinyGroup) {
                 for (uint32_t j = ga + 1; j < gb; ++j) {
-                    const uint64_t x = sk[SI(j)];
+                    const uint64_t x = sk[j];
                     uint32_t i = j;
                     while (i > ga) {
-                        const uint64_t y = sk[SI(i - 1)];
+                        const uint64_t y = sk[i - 1];
                         if (y <= x) break;
-                        sk[SI(i)] = y;
+                        sk[i] = y;
                         --i;
                     }
-                    sk[SI(i)] = x;
+                    sk[i] = x;
                 }
             } else {
                 for (int g = tid * G; g < tid * G + G; ++g) {
                     const uint32_t a = s_start[g], b = s_start[g + 1];
                     if (b - a < 2u || b - a >= (uint32_t)kTinyGroup) continue;
                     for (uint32_t j = a + 1; j < b; ++j) {
-                        const uint64_t x = sk[SI(j)];
+                        const uint64_t x = sk[j];
                         uint32_t i = j;
                         while (i > a) {
-                            const uint64_t y = sk[SI(i - 1)];
+                            const uint64_t y = sk[i - 1];
                             if (y <= x) break;
-                            sk[SI(i)] = y;
+                            sk[i] = y;
                             --i;
                         }
-                        sk[SI(i)] = x;
+                        sk[i] = x;
                     }
                 }
             }
             __syncthreads();
         }
-        if (TIE == 1 && mx > 1u) {
-            // Each key of a small group (2..kTinyGroup-1 keys) counts the
-            // group's keys below it -- smaller, or equal and in an earlier
-            // slot, so equal keys take distinct places -- while the keys
-            // stay in registers; after a barrier the keys whose place changed
-            // are written again.  A group of one key is already in place.
-#pragma unroll
-            for (int i = 0; i < ITEMS; ++i) {
-                if ((uint32_t)(i * THREADS) >= n) break;
-                const uint32_t c = dp[i] >> 26;
-                if (tid + i * THREADS >= n || c == 0u) {
-                    dp[i] = 0u;
-                    continue;
-                }
-                const uint32_t d = dp[i] & kDigitMask, slot = (dp[i] >> kSlotShift) & kSlotMask;
-                const uint32_t a = s_start[d];
-                const uint64_t x = key[i];
-                uint32_t r = 0;
-                for (uint32_t q = 0; q < c; ++q) {
-                    const uint64_t y = sk[SI(a + q)];
-                    r += (y < x || (y == x && q < slot)) ? 1u : 0u;
-                }
-                dp[i] = r != slot ? (0x80000000u | (a + r)) : 0u;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int i = 0; i < ITEMS; ++i) {
-                if ((uint32_t)(i * THREADS) >= n) break;
-                if (dp[i] & 0x80000000u) sk[SI(dp[i] & 0x7fffffffu)] = key[i];
-            }
-            __syncthreads();
-        }
         uint64_t* dst = kout + base;
-        if (PREFETCH && !SWZ) {
+        if (PREFETCH) {
             if (flip_out) {  // uniform: signed keys back from order-preserving bits
-                for (uint32_t j = tid; j < n; j += THREADS) sk[SI(j)] ^= flip_out;
+                for (uint32_t j = tid; j < n; j += THREADS) sk[j] ^= flip_out;
                 __syncthreads();
             }
             // One bulk copy writes the 16-byte aligned middle; the first and
             // last key go by plain stores when they fall outside it.
             const uint32_t m = ((n - ho) >> 1) << 1;
-            if (ho && tid == 1) dst[0] = sk[SI(0)];
-            if (ho + m < n && tid == 2) dst[n - 1] = sk[SI(n - 1)];
+            if (ho && tid == 1) dst[0] = sk[0];
+            if (ho + m < n && tid == 2) dst[n - 1] = sk[n - 1];
             fence_async_smem();
             __syncthreads();
             if (tid == 0 && m) bulk_store(dst + ho, s_key + 2 * ho, m * 8u);
         } else {
-            for (uint32_t j = tid; j < n; j += THREADS) dst[j] = sk[SI(j)] ^ flip_out;
+            for (uint32_t j = tid; j < n; j += THREADS) dst[j] = sk[j] ^ flip_out;
             __syncthreads();
         }
     }
@@ -1576,7 +1518,6 @@ __global__ __launch_bounds__(256) void k_seg_sample(const uint64_t* __restrict__
     __shared__ uint64_t s_k[kSplSample];
     __shared__ uint32_t s_h[kRadix];
     __shared__ unsigned long long s_or[8], s_and[8];
-    __shared__ uint32_t s_flag;
     const uint32_t id = blockIdx.x;
     if (id >= counters[19]) return;  // uniform
     const uint32_t s = large_seg[id];
@@ -1620,7 +1561,6 @@ __global__ __launch_bounds__(256) void k_seg_sample(const uint64_t* __restrict__
         spl[kRadix - 1] = ~0ull;
         spl_mode[id] = 1u;
     }
-    (void)s_flag;
 }
 
 __device__ __forceinline__ int spec_window(const uint32_t* __restrict__ prev_shift, uint32_t s) {
@@ -1641,6 +1581,7 @@ __device__ __forceinline__ void tile_skew_flag(uint32_t count, uint8_t* __restri
     if (threadIdx.x == 0) tile_skew[t] = any ? 1u : 0u;
 }
 
+template <bool SPL>
 __global__ __launch_bounds__(256) void k_tile_stats(const uint64_t* __restrict__ kin, const uint64_t* __restrict__ seg_lo,
                                                     const uint64_t* __restrict__ seg_hi, uint64_t nseg,
                                                     const uint32_t* __restrict__ tile_start,
@@ -1660,7 +1601,7 @@ __global__ __launch_bounds__(256) void k_tile_stats(const uint64_t* __restrict__
     if (t >= tile_start[nseg]) return;  // uniform
     s_h[threadIdx.x] = 0;
     const uint32_t s = tile_seg[t], id = large_id[s];
-    const bool bysplit = spl_mode && spl_mode[id];  // uniform per CTA
+    const bool bysplit = SPL && spl_mode[id];  // uniform per CTA
     if (bysplit) s_spl[threadIdx.x] = spl_tab[(uint64_t)id * kRadix + threadIdx.x];
     __syncthreads();
     const uint64_t lo = seg_lo[s], n = seg_hi[s] - lo;
@@ -1886,7 +1827,7 @@ struct SplitArgs {
     uint64_t flip_out;
 };
 
-template <bool PAY>
+template <bool PAY, bool SPL>
 __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitArgs A) {
     extern __shared__ __align__(16) unsigned char os_smem[];
     uint64_t* s_keys = (uint64_t*)os_smem;             // kOsTile keys
@@ -1914,7 +1855,8 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
     const int shift = (int)(A.msd_shift[id] & 0xffu);
     const uint64_t dbase = A.msd_base[id];
     const uint64_t dmult = A.msd_mult[id];
-    const bool bysplit = (A.msd_shift[id] & kShiftSplit) != 0u;  // uniform per CTA
+    // SPL: this level's segments may split on sampled splitters (uniform per CTA)
+    const bool bysplit = SPL && (A.msd_shift[id] & kShiftSplit) != 0u;
     const bool dir = A.direct[id] != 0u;
     uint64_t* kout = dir ? A.kfinal : A.kout;
     uint32_t* pout = dir ? A.pfinal : A.pout;
@@ -2149,13 +2091,13 @@ static cudaError_t launch_small_reg(const uint64_t* in, uint64_t* out, const uin
     return cudaGetLastError();
 }
 
-template <int THREADS, int CAP, int R, bool PREFETCH, int TIE>
+template <int THREADS, int CAP, int R, bool PREFETCH>
 static cudaError_t launch_keys(const uint64_t* in, uint64_t* out, const uint64_t* seg_lo, const uint64_t* seg_hi,
                                const uint32_t* list, const uint32_t* nlist, uint64_t count, uint64_t nseg,
                                uint32_t min_n, uint32_t max_n, uint64_t fin, uint64_t fout, uint32_t* slow,
                                uint32_t* slow_count, uint32_t* err, cudaStream_t st) {
     constexpr size_t smem = keys_sort_smem<CAP, R, PREFETCH>();
-    const void* fn = (const void*)k_small_keys<THREADS, CAP, R, PREFETCH, TIE>;
+    const void* fn = (const void*)k_small_keys<THREADS, CAP, R, PREFETCH>;
     {
         // all of L1 as shared memory: the CTAs per SM are limited by their buffers
         const cudaError_t e = ensure_func_attrs(fn, (int)smem, 100);
@@ -2165,7 +2107,7 @@ static cudaError_t launch_keys(const uint64_t* in, uint64_t* out, const uint64_t
     // With prefetching every CTA walks several segments of the list.
     const uint64_t grid = std::min<uint64_t>(count, (uint64_t)num_sms() * per_sm * (PREFETCH ? 1 : 4));
     if (grid == 0) return cudaSuccess;
-    HSS_LAUNCH((k_small_keys<THREADS, CAP, R, PREFETCH, TIE>), (unsigned)grid, THREADS, smem, st, in, out, seg_lo, seg_hi,
+    HSS_LAUNCH((k_small_keys<THREADS, CAP, R, PREFETCH>), (unsigned)grid, THREADS, smem, st, in, out, seg_lo, seg_hi,
                list, nlist, nseg, min_n, max_n, fin, fout, slow, slow_count, err);
     return cudaGetLastError();
 }
@@ -2244,11 +2186,10 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
     for (;;) {
         if (L.nseg > ws.max_list) return cudaErrorInvalidValue;
         const uint32_t nblk = (uint32_t)ceil_div(L.nseg + 1, 1024);
-        // Keys alone: by default a segment above the middle on-chip class is
-        // split again (into buckets of about a thousand keys that the
-        // prefetching small classes sort) rather than sorted by the largest
-        // class (tuning.chip_max_keys).
-        const uint32_t chip_max = PAY ? (uint32_t)kSmallCap : tune_chip_max;
+        // By default a segment above the middle on-chip class is split again
+        // (into buckets of about a thousand keys that the small classes sort)
+        // rather than sorted by the largest class (tuning.chip_max_keys).
+        const uint32_t chip_max = tune_chip_max;
         HSS_LAUNCH(k_plan_count, nblk, 1024, 0, st, L.seg_lo, L.seg_hi, L.nseg, ws.blk, chip_max);
         HSS_LAUNCH(k_plan_scan, 1, 1024, 0, st, nblk, ws.blk, ws.counters);
         HSS_LAUNCH(k_plan_write, nblk, 1024, 0, st, L.seg_lo, L.seg_hi, L.nseg, ws.blk, ws.counters, ws.tile_start,
@@ -2270,13 +2211,13 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
                 uint32_t* slow = ws.slow_keys[c];
                 uint32_t* slow_n = ws.counters + 26 + c;
                 if (c == 0)
-                    e = launch_keys<kC0Threads, kC0Cap, 512, true, 0>(L.in, dst, L.seg_lo, L.seg_hi, lists[c], ws.counters + 16,
+                    e = launch_keys<kC0Threads, kC0Cap, 512, true>(L.in, dst, L.seg_lo, L.seg_hi, lists[c], ws.counters + 16,
                                                             hc[c], L.nseg, lo_n, hi_n, L.flip_in, fout, slow, slow_n, ws.err, st);
                 else if (c == 1)
-                    e = launch_keys<kC1Threads, kC1Cap, 2048, true, 0>(L.in, dst, L.seg_lo, L.seg_hi, lists[c], ws.counters + 17,
+                    e = launch_keys<kC1Threads, kC1Cap, 2048, true>(L.in, dst, L.seg_lo, L.seg_hi, lists[c], ws.counters + 17,
                                                             hc[c], L.nseg, lo_n, hi_n, L.flip_in, fout, slow, slow_n, ws.err, st);
                 else
-                    e = launch_keys<kC2Threads, kSmallCap, 4096, false, 0>(L.in, dst, L.seg_lo, L.seg_hi, lists[c],
+                    e = launch_keys<kC2Threads, kSmallCap, 4096, false>(L.in, dst, L.seg_lo, L.seg_hi, lists[c],
                                                                ws.counters + 18, hc[c], L.nseg, lo_n, hi_n, L.flip_in,
                                                                fout, slow, slow_n, ws.err, st);
                 if (e != cudaSuccess) return e;
@@ -2329,9 +2270,14 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
         if (bysplit_level)
             HSS_LAUNCH(k_seg_sample, n_large, 256, 0, st, L.in, L.seg_lo, L.seg_hi, ws.large_seg, ws.counters, L.flip_in,
                        ws.spl_tab, ws.spl_mode);
-        HSS_LAUNCH(k_tile_stats, tiles, 256, 0, st, L.in, L.seg_lo, L.seg_hi, L.nseg, ws.tile_start, ws.tile_seg, ws.large_id,
-                   ws.tile_hist, ws.tile_skew, ws.vor, ws.vand, L.hint_lo, L.hint_mult, L.hint_hi, prev_shift, ws.spec,
-                   L.flip_in, bysplit_level ? ws.spl_tab : nullptr, bysplit_level ? ws.spl_mode : nullptr);
+        if (bysplit_level)
+            HSS_LAUNCH(k_tile_stats<true>, tiles, 256, 0, st, L.in, L.seg_lo, L.seg_hi, L.nseg, ws.tile_start, ws.tile_seg,
+                       ws.large_id, ws.tile_hist, ws.tile_skew, ws.vor, ws.vand, L.hint_lo, L.hint_mult, L.hint_hi,
+                       prev_shift, ws.spec, L.flip_in, ws.spl_tab, ws.spl_mode);
+        else
+            HSS_LAUNCH(k_tile_stats<false>, tiles, 256, 0, st, L.in, L.seg_lo, L.seg_hi, L.nseg, ws.tile_start, ws.tile_seg,
+                       ws.large_id, ws.tile_hist, ws.tile_skew, ws.vor, ws.vand, L.hint_lo, L.hint_mult, L.hint_hi,
+                       prev_shift, ws.spec, L.flip_in, nullptr, nullptr);
         if (!L.hint_lo)
             HSS_LAUNCH(k_tile_recount, tiles, 256, 0, st, L.in, L.seg_lo, L.seg_hi, L.nseg, ws.tile_start, ws.tile_seg, ws.large_id,
                        ws.tile_hist, ws.tile_skew, bysplit_level ? ws.spl_mode : nullptr, ws.vor, ws.vand, ws.spec,
@@ -2356,14 +2302,18 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
         A.flip_in = L.flip_in; A.flip_out = fout;
         const size_t smem = (size_t)kOsTile * 9 + (PAY ? (size_t)kOsTile * 4 : 0);
         // all of L1 as shared memory: the CTAs per SM are limited by their tiles
-        if ((e = ensure_func_attrs((const void*)k_split<PAY>, (int)smem, 100)) != cudaSuccess) return e;
+        const void* split_fn = bysplit_level ? (const void*)k_split<PAY, true> : (const void*)k_split<PAY, false>;
+        if ((e = ensure_func_attrs(split_fn, (int)smem, 100)) != cudaSuccess) return e;
         const bool timed = timing && timing->enabled && timing->n < 16;
         if (timed) {
             cudaEventCreate(&timing->ev[timing->n][0]);
             cudaEventCreate(&timing->ev[timing->n][1]);
             cudaEventRecord(timing->ev[timing->n][0], st);
         }
-        HSS_LAUNCH(k_split<PAY>, tiles, kOsThreads, smem, st, A);
+        if (bysplit_level)
+            HSS_LAUNCH((k_split<PAY, true>), tiles, kOsThreads, smem, st, A);
+        else
+            HSS_LAUNCH((k_split<PAY, false>), tiles, kOsThreads, smem, st, A);
         if (timed) {
             cudaEventRecord(timing->ev[timing->n][1], st);
             timing->keys[timing->n] = keys_large;
