@@ -1662,26 +1662,30 @@ __global__ __launch_bounds__(256) void k_tile_recount(const uint64_t* __restrict
                                                       const unsigned long long* __restrict__ vor,
                                                       const unsigned long long* __restrict__ vand,
                                                       const uint32_t* __restrict__ spec, uint64_t flip_in) {
+    // A grid of a few CTAs per SM walks the tiles: most levels recount few
+    // or none, and a CTA per tile would cost a launch of tens of thousands of
+    // CTAs that all return at once.
     __shared__ uint32_t s_h[kRadix];
-    const uint32_t t = blockIdx.x;
-    if (t >= tile_start[nseg]) return;  // uniform
-    s_h[threadIdx.x] = 0;
-    __syncthreads();
-    const uint32_t s = tile_seg[t], id = large_id[s];
-    if (spl_mode && spl_mode[id]) return;  // uniform: the statistics pass counted the splitter buckets
-    const unsigned long long vary = vor[id] ^ vand[id];
-    if (vary == 0ull) return;
-    const uint32_t w = (uint32_t)(63 - __clzll((long long)vary)) >> 3;
-    if (w == spec[id]) return;  // uniform per CTA
-    const uint64_t lo = seg_lo[s], n = seg_hi[s] - lo;
-    const uint64_t a = (uint64_t)(t - tile_start[s]) * kOsTile, b = min(n, a + kOsTile);
-    const int sh = 8 * (int)w;
+    const uint32_t total = tile_start[nseg];
+    for (uint32_t t = blockIdx.x; t < total; t += gridDim.x) {  // uniform per CTA
+        const uint32_t s = tile_seg[t], id = large_id[s];
+        if (spl_mode && spl_mode[id]) continue;  // the statistics pass counted the splitter buckets
+        const unsigned long long vary = vor[id] ^ vand[id];
+        if (vary == 0ull) continue;
+        const uint32_t w = (uint32_t)(63 - __clzll((long long)vary)) >> 3;
+        if (w == spec[id]) continue;
+        s_h[threadIdx.x] = 0;
+        __syncthreads();
+        const uint64_t lo = seg_lo[s], n = seg_hi[s] - lo;
+        const uint64_t a = (uint64_t)(t - tile_start[s]) * kOsTile, b = min(n, a + kOsTile);
+        const int sh = 8 * (int)w;
 #pragma unroll 4
-    for (uint64_t e = a + threadIdx.x; e < b; e += 256)
-        atomicAdd(&s_h[(uint32_t)((kin[lo + e] ^ flip_in) >> sh) & 255u], 1u);
-    __syncthreads();
-    tile_hist[(uint64_t)t * (2 * kRadix) + kRadix + threadIdx.x] = (uint16_t)s_h[threadIdx.x];
-    tile_skew_flag(s_h[threadIdx.x], tile_skew, t);
+        for (uint64_t e = a + threadIdx.x; e < b; e += 256)
+            atomicAdd(&s_h[(uint32_t)((kin[lo + e] ^ flip_in) >> sh) & 255u], 1u);
+        __syncthreads();
+        tile_hist[(uint64_t)t * (2 * kRadix) + kRadix + threadIdx.x] = (uint16_t)s_h[threadIdx.x];
+        tile_skew_flag(s_h[threadIdx.x], tile_skew, t);  // ends with a barrier
+    }
 }
 
 // Per large segment (thread d = digit d): the split window, the digit totals
@@ -1740,7 +1744,11 @@ __global__ __launch_bounds__(256) void k_msd_prep(const uint64_t* __restrict__ s
     // each.  s_end[d]: end offset of the pack that starts at sub-bucket d,
     // or ~0 when d belongs to an earlier pack (it becomes empty).  Sub-buckets
     // split again stand alone.
-    if (d == 0) {
+    // Nothing to pack unless two neighbouring sub-buckets fit one pack
+    // (uniform keys: none do, and the serial walk below is skipped).
+    const bool pair_fits = d + 1 < (uint32_t)kRadix && total + s_c[d + 1] <= pack_keys && total + s_c[d + 1] > 0u;
+    const bool packable = __syncthreads_or(pair_fits) != 0;
+    if (packable && d == 0) {
         uint32_t start = 0, acc = 0;
         bool open = false;
         for (uint32_t k = 0; k < (uint32_t)kRadix; ++k) {
@@ -1766,6 +1774,7 @@ __global__ __launch_bounds__(256) void k_msd_prep(const uint64_t* __restrict__ s
         }
         if (open) s_end[start] = s_x[kRadix - 1] + s_c[kRadix - 1];
     }
+    if (!packable) s_end[d] = x + total;
     __syncthreads();
     const uint32_t pend = s_end[d];
     sub_lo[(uint64_t)id * kRadix + d] = dir ? lo : lo + x;
@@ -2279,7 +2288,8 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
                        ws.large_id, ws.tile_hist, ws.tile_skew, ws.vor, ws.vand, L.hint_lo, L.hint_mult, L.hint_hi,
                        prev_shift, ws.spec, L.flip_in, nullptr, nullptr);
         if (!L.hint_lo)
-            HSS_LAUNCH(k_tile_recount, tiles, 256, 0, st, L.in, L.seg_lo, L.seg_hi, L.nseg, ws.tile_start, ws.tile_seg, ws.large_id,
+            HSS_LAUNCH(k_tile_recount, (unsigned)std::min<uint64_t>(tiles, (uint64_t)num_sms() * 8), 256, 0, st, L.in,
+                       L.seg_lo, L.seg_hi, L.nseg, ws.tile_start, ws.tile_seg, ws.large_id,
                        ws.tile_hist, ws.tile_skew, bysplit_level ? ws.spl_mode : nullptr, ws.vor, ws.vand, ws.spec,
                        L.flip_in);
         HSS_LAUNCH(k_msd_prep, n_large, 256, 0, st, L.seg_lo, ws.large_seg, ws.counters, ws.tile_start, ws.tile_hist,
