@@ -597,9 +597,11 @@ def run_serve_workload(args):
 def run_rounds_workload(args):
     """Round-count study (the rounds of Sec. 7.1, Fig. 1): histogram rounds
     of hss_partition against p for oversampling s = 1 and s = 5 at eps = 2%,
-    N = 2^26 uniform keys, p = 2^4 .. 2^14 (the p x (p-1) per-segment cut
-    positions bound p on one device), with the round bound of Theorem 4.8,
-    O(log(log p / eps)), printed beside as log2(log2(p) / eps)."""
+    N = 2^26 uniform keys, p = 2^4 .. 2^16 (at p = 2^16 the p x (p-1)
+    per-segment cut positions and the p x (sample capacity) probe positions
+    take about 195 GiB of the device), with the growth of Theorem 4.8,
+    O(log(log p / eps)), printed beside as log2(log2(p) / eps), and for s = 5
+    the bound ceil(ln(2 ln p / eps) / ln(s / 4)) + 2."""
     import math
     import numpy as np
     import torch
@@ -612,9 +614,10 @@ def run_rounds_workload(args):
     N, eps = 1 << 26, 0.02
     keys = torch.from_numpy(inputs.uniform(N, 1).view(np.int64)).to(dev)
     table = []
-    for lp in range(4, 15):
+    for lp in range(4, 17):
         p = 1 << lp
-        row = {"p": p, "log2_log2p_over_eps": math.log2(math.log2(p) / eps)}
+        row = {"p": p, "log2_log2p_over_eps": math.log2(math.log2(p) / eps),
+               "bound_s5": math.ceil(math.log(2.0 * math.log(p) / eps) / math.log(5.0 / 4.0)) + 2}
         for s_ in (1.0, 5.0):
             rounds = []
             for seed in (1, 2, 3):
@@ -627,7 +630,7 @@ def run_rounds_workload(args):
     line = {"metric": "HSS rounds vs p (s = 1 and s = 5, eps = 0.02)", "value": table[-1]["mean_rounds_s5"],
             "unit": "rounds", "n_gpus": 1, "steps": len(table), "warmup": 0, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "round-count study: N = 2^26 uniform u64, eps = 0.02, p = 2^4 .. 2^14, "
+            "config": {"workload": "round-count study: N = 2^26 uniform u64, eps = 0.02, p = 2^4 .. 2^16, "
                                    "s in {1, 5}, seeds 1-3"},
             "table": table}
     print(json.dumps(line), flush=True)

@@ -153,6 +153,11 @@ def _load():
                                        ctypes.c_int, ctypes.c_uint32,
                                        P, P, P, P, P, P, ctypes.POINTER(_Stats), P, P, P, P, ctypes.c_uint64]
             lib.oracle_hss.restype = ctypes.c_int
+            lib.oracle_hss_groups.argtypes = [P, P, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32,
+                                              ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_float,
+                                              ctypes.c_uint32, P, ctypes.c_uint32, ctypes.c_int, ctypes.c_uint32,
+                                              P, P, P, P, P, P, ctypes.POINTER(_Stats), P, P, P, P, ctypes.c_uint64]
+            lib.oracle_hss_groups.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -319,3 +324,82 @@ def hss(keys, p: int, eps: float, seed: int, oversample: float = 5.0, max_rounds
             res.samples.append(blk.copy())
             used += take
     return res
+
+
+def hss_groups(keys, p: int, nb: int, eps: float, seed: int, oversample: float = 5.0, max_rounds: int = 64,
+               payload=None, exchange_only: bool = True):
+    """The partition step of one stage of multi-stage HSS (Sec. 5.3): the p
+    processors' keys split into nb buckets (nb - 1 splitters at ranks i N / nb,
+    tolerance floor(N eps / (2 nb)), s nb probes per round), then the data
+    exchange: bucket b is the concatenation of its runs in processor order
+    (exchange_only; else each bucket is also merged)."""
+    lib = _load()
+    k, kt = _keys_u64(keys)
+    N = int(k.shape[0])
+    S = max(nb - 1, 0)
+    spl_key = np.zeros(max(S, 1), dtype=np.uint64)
+    spl_seg = np.zeros(max(S, 1), dtype=np.int32)
+    spl_spos = np.zeros(max(S, 1), dtype=np.uint32)
+    offsets = np.zeros(nb + 1, dtype=np.uint64)
+    pay = None if payload is None else np.ascontiguousarray(payload, dtype=np.uint32)
+    out_keys = np.empty(max(N, 1), dtype=np.uint64)
+    out_pay = np.empty(max(N, 1), dtype=np.uint32) if payload is not None else None
+    st = _Stats()
+    rc = lib.oracle_hss_groups(_ptr(k), _ptr(pay), N, kt, p, nb, int(exchange_only), float(eps),
+                               int(seed) & ((1 << 64) - 1), float(oversample), max_rounds, None, 0, 0, 0,
+                               _ptr(spl_key), _ptr(spl_seg), _ptr(spl_spos), _ptr(offsets), _ptr(out_keys),
+                               _ptr(out_pay), ctypes.byref(st), None, None, None, None, 0)
+    if rc == -1:
+        raise ValueError("oracle_hss_groups: invalid arguments")
+    R = st.rounds
+    res = HSSResult(
+        splitter_key=(spl_key[:S].view(np.int64) if kt == KEY_I64 else spl_key[:S]),
+        splitter_seg=spl_seg[:S], splitter_spos=spl_spos[:S], offsets=offsets, rounds=R, status=st.status,
+        tol=st.tol, sample_size=np.array(st.sample_size[:R], dtype=np.uint64),
+        gamma=np.array(st.gamma[:R], dtype=np.uint64), unresolved=np.array(st.unresolved[:R + 1], dtype=np.uint64))
+    ok = out_keys[:N]
+    res.out_keys = ok.view(np.int64) if kt == KEY_I64 else ok
+    res.out_payload = None if out_pay is None else out_pay[:N]
+    return res
+
+
+@dataclass
+class TwoStageResult:
+    offsets: np.ndarray          # p + 1 bucket offsets of the final buckets
+    out_keys: np.ndarray
+    out_payload: np.ndarray | None
+    stage1: HSSResult            # the r-group partition
+    stage2: list                 # HSSResult of every group
+
+
+def hss_two_stage(keys, p: int, r: int, eps: float, seed: int, oversample: float = 5.0, max_rounds: int = 64,
+                  payload=None) -> TwoStageResult:
+    """Two-stage HSS (Sec. 5.3; Sec. 7.3 runs 2 stages with r = sqrt(p)
+    groups and eps per stage): stage 1 splits the p processors' keys into r
+    groups with HSS (r - 1 splitters) and exchanges them; each group's
+    exchanged keys (its runs in processor order) are then dealt evenly to its
+    p / r processors by position, and stage 2 sorts group g with single-stage
+    HSS on them, seed + 1 + g.  The final buckets are the groups' buckets in
+    group order; the output is the stable sort of the input."""
+    if r < 1 or p % r != 0:
+        raise ValueError("r must divide p")
+    pg = p // r
+    st1 = hss_groups(keys, p, r, eps, seed, oversample, max_rounds, payload, exchange_only=True)
+    k, kt = _keys_u64(keys)
+    gk = st1.out_keys
+    gp = st1.out_payload
+    offsets = [0]
+    outs, outp, st2 = [], [], []
+    for g in range(r):
+        a, b = int(st1.offsets[g]), int(st1.offsets[g + 1])
+        res = hss(gk[a:b], pg, eps, seed + 1 + g, oversample=oversample, max_rounds=max_rounds,
+                  payload=None if gp is None else gp[a:b])
+        st2.append(res)
+        outs.append(res.out_keys)
+        if gp is not None:
+            outp.append(res.out_payload)
+        offsets.extend(int(a + x) for x in res.offsets[1:])
+    out_keys = np.concatenate(outs) if outs else gk[:0]
+    out_pay = np.concatenate(outp) if gp is not None and outp else None
+    return TwoStageResult(offsets=np.array(offsets, dtype=np.uint64), out_keys=out_keys, out_payload=out_pay,
+                          stage1=st1, stage2=st2)

@@ -324,26 +324,32 @@ static void offer(ocut* L, ocut* U, uint64_t t, const ocut* c)
  *   trace_samples (nullable, cap trace_cap): sorted probes of every round,
  *       as (key, seg, spos) triples, rounds concatenated.
  */
-int oracle_hss(const uint64_t* keys, const uint32_t* payload, uint64_t N, int key_type,
-               uint32_t p, double eps, uint64_t seed, float oversample, uint32_t max_rounds,
-               const uint64_t* proposal_keys, uint32_t nprop, int schedule, uint32_t schedule_k,
-               uint64_t* spl_key, int32_t* spl_seg, uint32_t* spl_spos, uint64_t* offsets,
-               uint64_t* out_keys, uint32_t* out_payload, oracle_stats* stats,
-               uint64_t* trace_lrank, uint64_t* trace_urank, uint8_t* trace_resolved,
-               uint64_t* trace_samples, uint64_t trace_cap)
+/* HSS over p processors into nb buckets (nb = p: the single-stage method;
+ * nb < p: the partition step of a stage of multi-stage HSS, Sec. 5.3, whose
+ * nb - 1 splitters target ranks i N / nb with tolerance N eps / (2 nb) and
+ * draw s nb probes per round).  exchange_only: out_keys receives each
+ * bucket as the concatenation of its runs in processor order (the data
+ * exchange without the merge). */
+int oracle_hss_groups(const uint64_t* keys, const uint32_t* payload, uint64_t N, int key_type,
+                      uint32_t p, uint32_t nb, int exchange_only, double eps, uint64_t seed, float oversample,
+                      uint32_t max_rounds, const uint64_t* proposal_keys, uint32_t nprop, int schedule,
+                      uint32_t schedule_k, uint64_t* spl_key, int32_t* spl_seg, uint32_t* spl_spos, uint64_t* offsets,
+                      uint64_t* out_keys, uint32_t* out_payload, oracle_stats* stats,
+                      uint64_t* trace_lrank, uint64_t* trace_urank, uint8_t* trace_resolved,
+                      uint64_t* trace_samples, uint64_t trace_cap)
 {
-    if (p == 0 || !(eps > 0.0) || max_rounds > ORACLE_MAX_ROUNDS) return -1;
+    if (p == 0 || nb == 0 || nb > p || !(eps > 0.0) || max_rounds > ORACLE_MAX_ROUNDS) return -1;
     if (schedule < 0 || schedule > 2 || (schedule == 1 && schedule_k == 0)) return -1;
     memset(stats, 0, sizeof(*stats));
 
     /* Step 1: processors and targets. */
     uint64_t* seg_start = (uint64_t*)malloc(sizeof(uint64_t) * (p + 1));
     segment_bounds(N, p, seg_start);
-    uint64_t tol = oracle_tolerance(N, p, eps);
+    uint64_t tol = oracle_tolerance(N, nb, eps);
     stats->tol = tol;
-    uint32_t S = p - 1;  /* number of splitters */
+    uint32_t S = nb - 1;  /* number of splitters */
     uint64_t* t = (uint64_t*)malloc(sizeof(uint64_t) * (S + 1));
-    for (uint32_t i = 1; i <= S; ++i) t[i - 1] = (uint64_t)(((unsigned __int128)i * N) / p);
+    for (uint32_t i = 1; i <= S; ++i) t[i - 1] = (uint64_t)(((unsigned __int128)i * N) / nb);
 
     /* Step 2: local sort with implicit tagging. */
     uint64_t* okeys = (uint64_t*)malloc(sizeof(uint64_t) * (N ? N : 1));
@@ -397,9 +403,9 @@ int oracle_hss(const uint64_t* keys, const uint32_t* payload, uint64_t N, int ke
          * per interval (HykSort, Sec. 4.2.2 remark): s p / nint expected
          * samples for each distinct unresolved interval. */
         uint64_t T; int take_all;
-        if (schedule == 1) oracle_threshold_q(oracle_theory_q(p, eps, N, j, schedule_k), &T, &take_all);
-        else oracle_threshold((double)oversample, p, gamma, &T, &take_all);
-        const double per_int = nint ? ((double)oversample * (double)p) / (double)nint : 0.0;
+        if (schedule == 1) oracle_threshold_q(oracle_theory_q(nb, eps, N, j, schedule_k), &T, &take_all);
+        else oracle_threshold((double)oversample, nb, gamma, &T, &take_all);
+        const double per_int = nint ? ((double)oversample * (double)nb) / (double)nint : 0.0;
 
         /* Sampling phase: every key strictly inside an unresolved interval is
          * drawn independently. */
@@ -479,7 +485,7 @@ int oracle_hss(const uint64_t* keys, const uint32_t* payload, uint64_t N, int ke
         spl[i + 1] = (dl <= du) ? L[i] : U[i];
     }
     memset(&spl[S + 1], 0, sizeof(ocut)); spl[S + 1].kind = CUT_POS_INF; spl[S + 1].rank = N;
-    for (uint32_t b = 0; b <= p; ++b) offsets[b] = spl[b].rank;
+    for (uint32_t b = 0; b <= nb; ++b) offsets[b] = spl[b].rank;
     for (uint32_t i = 0; i < S; ++i) {
         const ocut* c = &spl[i + 1];
         if (c->kind == CUT_MEMBER)          { spl_key[i] = from_okey(c->okey, key_type); spl_seg[i] = c->seg; spl_spos[i] = c->spos; }
@@ -494,9 +500,9 @@ int oracle_hss(const uint64_t* keys, const uint32_t* payload, uint64_t N, int ke
     if (out_keys) {
         /* one bucket at a time: the buffer holds the largest bucket */
         uint64_t maxb = 1;
-        for (uint32_t b = 0; b < p; ++b) if (offsets[b + 1] - offsets[b] > maxb) maxb = offsets[b + 1] - offsets[b];
+        for (uint32_t b = 0; b < nb; ++b) if (offsets[b + 1] - offsets[b] > maxb) maxb = offsets[b + 1] - offsets[b];
         kv* buf = (kv*)malloc(sizeof(kv) * maxb);
-        for (uint32_t b = 0; b < p; ++b) {
+        for (uint32_t b = 0; b < nb; ++b) {
             uint64_t n = 0, base = offsets[b];
             for (uint32_t s = 0; s < p; ++s) {
                 uint64_t a = seg_lower_bound(&st, s, &spl[b]);
@@ -507,7 +513,7 @@ int oracle_hss(const uint64_t* keys, const uint32_t* payload, uint64_t N, int ke
                     ++n;
                 }
             }
-            qsort(buf, n, sizeof(kv), kv_cmp);
+            if (!exchange_only) qsort(buf, n, sizeof(kv), kv_cmp);
             for (uint64_t k = 0; k < n; ++k) {
                 out_keys[base + k] = from_okey(buf[k].okey, key_type);
                 if (out_payload) out_payload[base + k] = opay[buf[k].idx];
@@ -518,6 +524,20 @@ int oracle_hss(const uint64_t* keys, const uint32_t* payload, uint64_t N, int ke
 
     free(spl); free(res); free(U); free(L); free(opay); free(okeys); free(t); free(seg_start);
     return stats->status;
+}
+
+/* The single-stage method: p processors, p buckets, exchange and merge. */
+int oracle_hss(const uint64_t* keys, const uint32_t* payload, uint64_t N, int key_type,
+               uint32_t p, double eps, uint64_t seed, float oversample, uint32_t max_rounds,
+               const uint64_t* proposal_keys, uint32_t nprop, int schedule, uint32_t schedule_k,
+               uint64_t* spl_key, int32_t* spl_seg, uint32_t* spl_spos, uint64_t* offsets,
+               uint64_t* out_keys, uint32_t* out_payload, oracle_stats* stats,
+               uint64_t* trace_lrank, uint64_t* trace_urank, uint8_t* trace_resolved,
+               uint64_t* trace_samples, uint64_t trace_cap)
+{
+    return oracle_hss_groups(keys, payload, N, key_type, p, p, 0, eps, seed, oversample, max_rounds, proposal_keys,
+                             nprop, schedule, schedule_k, spl_key, spl_seg, spl_spos, offsets, out_keys, out_payload,
+                             stats, trace_lrank, trace_urank, trace_resolved, trace_samples, trace_cap);
 }
 
 /* Global rank of an arbitrary cut over the locally sorted segments of an input

@@ -804,10 +804,10 @@ namespace {
 // probes, update L/U and their positions, recompute the intervals, sample the
 // next round and decide whether it runs.  Every kernel reads the round's
 // sample size, seed and histogram form from the control record.
-cudaError_t enqueue_device_round(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uint32_t p, uint64_t tol,
-                                 float oversample, uint32_t schedule, uint32_t hist_mode, const RoundWs& ws,
+cudaError_t enqueue_device_round(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uint32_t p, uint32_t NB,
+                                 uint64_t tol, float oversample, uint32_t schedule, uint32_t hist_mode, const RoundWs& ws,
                                  cudaGraphConditionalHandle loop, cudaStream_t st) {
-    const uint32_t S = p - 1;
+    const uint32_t S = NB - 1;
     const unsigned sblk = (unsigned)cdiv(S, 256);
     const uint64_t cap = ws.cap;
     const bool per_interval = schedule == HSS_SCHEDULE_EQUAL;
@@ -824,10 +824,10 @@ cudaError_t enqueue_device_round(const uint64_t* skeys, const uint64_t* d_seg_of
     HSS_LAUNCH(k_histogram, dim3((unsigned)cdiv(cap, 32), (unsigned)cdiv(p, kHistSegPerBlock)), 256, 0, st, skeys,
                d_seg_off, p, S, ws.Lpos, ws.Upos, ws.int_rep, ws.pkey, ws.pseg, ws.pspos, ws.pint, kZFromCtl, ws.prank,
                ws.probe_pos, cap, ws.sws.err, ws.ctl);
-    HSS_LAUNCH(k_update, sblk, 256, 0, st, S, N, p, ws.pkey, ws.pseg, ws.pspos, ws.prank, kZFromCtl, (int32_t)kMember,
+    HSS_LAUNCH(k_update, sblk, 256, 0, st, S, N, NB, ws.pkey, ws.pseg, ws.pspos, ws.prank, kZFromCtl, (int32_t)kMember,
                ws.Lcut, ws.Ucut, ws.chgL, ws.chgU, ws.ctl);
     HSS_LAUNCH(k_update_pos, dim3(p, sblk), 256, 0, st, S, ws.chgL, ws.chgU, ws.probe_pos, cap, ws.Lpos, ws.Upos);
-    HSS_LAUNCH(k_intervals, 1, 1024, 0, st, S, N, p, tol, oversample, ws.Lcut, ws.Ucut, ws.res, ws.int_rep, ws.ctl,
+    HSS_LAUNCH(k_intervals, 1, 1024, 0, st, S, N, NB, tol, oversample, ws.Lcut, ws.Ucut, ws.res, ws.int_rep, ws.ctl,
                schedule, 0ull, 0u, ws.int_T, ws.int_all);
     if ((e = cudaMemsetAsync(ws.bitmap, 0, (N / 32 + 2) * sizeof(uint32_t), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(ws.seg_cnt, 0, (size_t)p * sizeof(uint32_t), st)) != cudaSuccess) return e;
@@ -850,10 +850,11 @@ struct LoopKey {
     uint64_t N, tol, cap;
     uint32_t p, schedule, hist_mode;
     float oversample;
+    uint32_t nb;
     bool operator==(const LoopKey& o) const {
         return dev == o.dev && ctl == o.ctl && skeys == o.skeys && seg_off == o.seg_off && N == o.N && tol == o.tol &&
                cap == o.cap && p == o.p && schedule == o.schedule && hist_mode == o.hist_mode &&
-               oversample == o.oversample;
+               oversample == o.oversample && nb == o.nb;
     }
 };
 struct LoopGraph {
@@ -879,7 +880,7 @@ constexpr int kLoopDeclined = 1;  // loop_graph: no graph yet, drive these round
 // call declines (kLoopDeclined): capturing and instantiating the graph costs
 // more than the host round trips of one call, so only shapes that repeat get
 // one.
-int loop_graph(const LoopKey& k, const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uint32_t p,
+int loop_graph(const LoopKey& k, const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uint32_t p, uint32_t NB,
                uint64_t tol, float oversample, uint32_t schedule, uint32_t hist_mode, const RoundWs& ws,
                bool build_now, cudaGraphExec_t* out) {
     std::lock_guard<std::mutex> lock(g_loop_mu);
@@ -932,7 +933,8 @@ int loop_graph(const LoopKey& k, const uint64_t* skeys, const uint64_t* d_seg_of
     if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
         return fail();
     const uint64_t before = pause.captured();
-    const cudaError_t ce = enqueue_device_round(skeys, d_seg_off, N, p, tol, oversample, schedule, hist_mode, ws, loop, cs);
+    const cudaError_t ce = enqueue_device_round(skeys, d_seg_off, N, p, NB, tol, oversample, schedule, hist_mode, ws, loop,
+                                                cs);
     g_body_kernels = (uint32_t)(pause.captured() - before);
     tmp = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(cs, &tmp);
@@ -976,10 +978,13 @@ int read_round_result(const RoundWs& ws, RoundResult* out, cudaStream_t st) {
 int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uint32_t p, double eps, uint64_t seed,
                float oversample, uint32_t max_rounds, int key_type, hss_cut* d_splitters, uint64_t* d_offsets,
                const RoundWs& ws, cudaStream_t st, RoundResult* out, const uint64_t* d_prop, uint32_t nprop,
-               uint32_t schedule, uint32_t schedule_k, uint32_t hist_mode, uint32_t loop_mode, bool* used_device_loop) {
+               uint32_t schedule, uint32_t schedule_k, uint32_t hist_mode, uint32_t loop_mode, bool* used_device_loop,
+               uint32_t nb) {
     if (used_device_loop) *used_device_loop = false;
-    const uint32_t S = p - 1;
-    const uint64_t tol = (uint64_t)std::floor(((double)N * eps) / (2.0 * (double)p));
+    const uint32_t NB = nb ? nb : p;  // buckets: the splitters target ranks i N / NB
+    if (NB > p) return HSS_ERR_INVALID;
+    const uint32_t S = NB - 1;
+    const uint64_t tol = (uint64_t)std::floor(((double)N * eps) / (2.0 * (double)NB));
     const bool per_interval = schedule == HSS_SCHEDULE_EQUAL;
     // The interval pass before sampling round r; under the k-round schedule
     // the host supplies round r's threshold: probability p s_r / N,
@@ -989,12 +994,12 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
         uint32_t allq = 0;
         if (schedule == HSS_SCHEDULE_THEORY) {
             const uint32_t rr = r < schedule_k ? r : schedule_k;
-            const double sj = std::pow(2.0 * std::log((double)p) / eps, (double)rr / (double)schedule_k);
-            const double q = ((double)p * sj) / (double)N;
+            const double sj = std::pow(2.0 * std::log((double)NB) / eps, (double)rr / (double)schedule_k);
+            const double q = ((double)NB * sj) / (double)N;
             if (q >= 1.0) allq = 1u;
             else Tq = (uint64_t)std::floor(std::ldexp(q, 64));
         }
-        HSS_LAUNCH(k_intervals, 1, 1024, 0, st, S, N, p, tol, oversample, ws.Lcut, ws.Ucut, ws.res, ws.int_rep, ws.ctl,
+        HSS_LAUNCH(k_intervals, 1, 1024, 0, st, S, N, NB, tol, oversample, ws.Lcut, ws.Ucut, ws.res, ws.int_rep, ws.ctl,
                    schedule, Tq, allq, ws.int_T, ws.int_all);
     };
     // The histogram of Z probes: staged when they share one interval and
@@ -1017,7 +1022,7 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
     };
     HSS_TRY(cudaMemsetAsync(ws.ctl, 0, sizeof(RoundCtl), st));
     if (S == 0) {
-        HSS_LAUNCH(k_finalize, 1, 32, 0, st, 0u, N, p, key_type, ws.Lcut, ws.Ucut, d_splitters, d_offsets, ws.choose_u,
+        HSS_LAUNCH(k_finalize, 1, 32, 0, st, 0u, N, NB, key_type, ws.Lcut, ws.Ucut, d_splitters, d_offsets, ws.choose_u,
                    ws.fin_okey, ws.fin_kind);
         HSS_TRY(cudaGetLastError());
         out->rounds = 0;
@@ -1037,7 +1042,7 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
         HSS_LAUNCH(k_prop_probes, (unsigned)cdiv(nprop, 256), 256, 0, st, nprop, ws.skey_sorted, ws.pkey, ws.pseg,
                    ws.pspos, ws.pint, ws.prank);
         HSS_TRY(histogram((uint64_t)nprop, 1u));
-        HSS_LAUNCH(k_update, sblk, 256, 0, st, S, N, p, ws.pkey, ws.pseg, ws.pspos, ws.prank, (uint64_t)nprop,
+        HSS_LAUNCH(k_update, sblk, 256, 0, st, S, N, NB, ws.pkey, ws.pseg, ws.pspos, ws.prank, (uint64_t)nprop,
                    (int32_t)kNonMember, ws.Lcut, ws.Ucut, ws.chgL, ws.chgU, ws.ctl);
         HSS_LAUNCH(k_update_pos, dim3(p, sblk), 256, 0, st, S, ws.chgL, ws.chgU, ws.probe_pos, ws.cap, ws.Lpos, ws.Upos);
         intervals(1);
@@ -1048,8 +1053,8 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
         // round trip until the caller reads the statistics.
         int dev = 0;
         HSS_TRY(cudaGetDevice(&dev));
-        const LoopKey key{dev, ws.ctl, skeys, d_seg_off, N, tol, ws.cap, p, schedule, hist_mode, oversample};
-        const int rc = loop_graph(key, skeys, d_seg_off, N, p, tol, oversample, schedule, hist_mode, ws,
+        const LoopKey key{dev, ws.ctl, skeys, d_seg_off, N, tol, ws.cap, p, schedule, hist_mode, oversample, NB};
+        const int rc = loop_graph(key, skeys, d_seg_off, N, p, NB, tol, oversample, schedule, hist_mode, ws,
                                   loop_mode == kLoopDevice, &exec);
         if (rc != HSS_OK && rc != kLoopDeclined) return rc;
     }
@@ -1058,7 +1063,7 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
         enqueue_sampling(ws, d_seg_off, N, p, S, seed, 1, st, per_interval);
         HSS_TRY(cudaGetLastError());
         HSS_TRY(cudaGraphLaunch(exec, st));
-        HSS_LAUNCH(k_finalize, (unsigned)cdiv(S, 256), 256, 0, st, S, N, p, key_type, ws.Lcut, ws.Ucut, d_splitters,
+        HSS_LAUNCH(k_finalize, (unsigned)cdiv(S, 256), 256, 0, st, S, N, NB, key_type, ws.Lcut, ws.Ucut, d_splitters,
                    d_offsets, ws.choose_u, ws.fin_okey, ws.fin_kind);
         HSS_LAUNCH(k_final_pos, dim3(p, sblk), 256, 0, st, S, ws.choose_u, ws.Lpos, ws.Upos);
         HSS_TRY(cudaGetLastError());
@@ -1089,7 +1094,7 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
             HSS_LAUNCH(k_probe_build, (unsigned)cdiv(Z, 256), 256, 0, st, Z, ws.skey_sorted, ws.sperm, ws.sseg, ws.sspos,
                        ws.Ucut, ws.int_rep, ws.ctl, ws.pkey, ws.pseg, ws.pspos, ws.pint, ws.prank);
             HSS_TRY(histogram(Z, h.nint));
-            HSS_LAUNCH(k_update, sblk, 256, 0, st, S, N, p, ws.pkey, ws.pseg, ws.pspos, ws.prank, Z, (int32_t)kMember,
+            HSS_LAUNCH(k_update, sblk, 256, 0, st, S, N, NB, ws.pkey, ws.pseg, ws.pspos, ws.prank, Z, (int32_t)kMember,
                        ws.Lcut, ws.Ucut, ws.chgL, ws.chgU, ws.ctl);
             HSS_LAUNCH(k_update_pos, dim3(p, sblk), 256, 0, st, S, ws.chgL, ws.chgU, ws.probe_pos, ws.cap, ws.Lpos, ws.Upos);
         }
@@ -1108,7 +1113,7 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
         HSS_TRY(cudaMemcpyAsync(ws.ctl->hist_gamma, out->gamma, sizeof(out->gamma), cudaMemcpyHostToDevice, st));
         HSS_TRY(cudaMemcpyAsync(ws.ctl->hist_unres, out->unresolved, sizeof(out->unresolved), cudaMemcpyHostToDevice, st));
     }
-    HSS_LAUNCH(k_finalize, (unsigned)cdiv(S, 256), 256, 0, st, S, N, p, key_type, ws.Lcut, ws.Ucut, d_splitters, d_offsets,
+    HSS_LAUNCH(k_finalize, (unsigned)cdiv(S, 256), 256, 0, st, S, N, NB, key_type, ws.Lcut, ws.Ucut, d_splitters, d_offsets,
                ws.choose_u, ws.fin_okey, ws.fin_kind);
     HSS_LAUNCH(k_final_pos, dim3(p, sblk), 256, 0, st, S, ws.choose_u, ws.Lpos, ws.Upos);
     HSS_TRY(cudaGetLastError());
@@ -1127,31 +1132,31 @@ __device__ __forceinline__ uint32_t bucket_pos(const uint32_t* __restrict__ pos,
 // Column scans of the run lengths: CTA x handles 32 buckets; its 32 warps
 // split the segments into 32 groups, sum their group, scan the group sums and
 // write the destinations.
-__global__ __launch_bounds__(1024) void k_exchange_dst(const uint64_t* __restrict__ seg_off, uint32_t p,
+__global__ __launch_bounds__(1024) void k_exchange_dst(const uint64_t* __restrict__ seg_off, uint32_t p, uint32_t NB,
                                                        const uint32_t* __restrict__ pos, const uint64_t* __restrict__ offsets,
                                                        uint64_t* __restrict__ dst, uint32_t* err) {
     __shared__ uint64_t s_part[32][33];
     const uint32_t col = threadIdx.x & 31, grp = threadIdx.x >> 5;
     const uint32_t b = blockIdx.x * 32 + col;
-    const uint32_t S = p - 1;
+    const uint32_t S = NB - 1;
     const uint32_t R = (p + 31) / 32;
     const uint32_t s0 = min(p, grp * R), s1 = min(p, s0 + R);
     uint64_t part = 0;
-    if (b < p) {
+    if (b < NB) {
         for (uint32_t s = s0; s < s1; ++s) {
             const uint32_t n = (uint32_t)(seg_off[s + 1] - seg_off[s]);
-            part += bucket_pos(pos, S, p, s, b + 1, n) - bucket_pos(pos, S, p, s, b, n);
+            part += bucket_pos(pos, S, NB, s, b + 1, n) - bucket_pos(pos, S, NB, s, b, n);
         }
     }
     s_part[grp][col] = part;
     __syncthreads();
-    if (b >= p) return;
+    if (b >= NB) return;
     uint64_t run = offsets[b];
     for (uint32_t g = 0; g < grp; ++g) run += s_part[g][col];
     for (uint32_t s = s0; s < s1; ++s) {
         const uint32_t n = (uint32_t)(seg_off[s + 1] - seg_off[s]);
-        dst[(uint64_t)s * p + b] = run;
-        run += bucket_pos(pos, S, p, s, b + 1, n) - bucket_pos(pos, S, p, s, b, n);
+        dst[(uint64_t)s * NB + b] = run;
+        run += bucket_pos(pos, S, NB, s, b + 1, n) - bucket_pos(pos, S, NB, s, b, n);
     }
     if (s1 == p && s0 < s1 && run != offsets[b + 1]) atomicOr(err, kDevErrBounds);
 }
@@ -1179,14 +1184,14 @@ constexpr uint32_t kXchChunk = 8192;
 constexpr uint32_t kXchMaxB = 4096;
 
 __global__ __launch_bounds__(256) void k_exchange_copy(const uint64_t* __restrict__ skeys, const uint32_t* __restrict__ spay,
-                                                       const uint64_t* __restrict__ seg_off, uint32_t p,
+                                                       const uint64_t* __restrict__ seg_off, uint32_t NB,
                                                        const uint32_t* __restrict__ pos, const uint64_t* __restrict__ dst,
                                                        uint64_t* __restrict__ bkeys, uint32_t* __restrict__ bpay, uint64_t N,
                                                        uint32_t* __restrict__ err) {
     __shared__ uint32_t s_bnd[kXchMaxB + 1];
     __shared__ uint32_t s_b0, s_nb;
     const uint64_t s = blockIdx.x;
-    const uint32_t S = p - 1;
+    const uint32_t S = NB - 1;
     const uint64_t base = seg_off[s];
     const uint32_t n = (uint32_t)(seg_off[s + 1] - base);
     const uint32_t c0 = blockIdx.y * kXchChunk;
@@ -1194,8 +1199,8 @@ __global__ __launch_bounds__(256) void k_exchange_copy(const uint64_t* __restric
     const uint32_t c1 = min(n, c0 + kXchChunk);
     if (threadIdx.x < 32) {
         // buckets b0..b1 whose runs meet [c0, c1): last b with pos(b) <= c0, last b with pos(b) <= c1-1
-        const uint32_t b0 = warp_last_le(pos, S, p, s, n, c0, 0, p);
-        const uint32_t b1 = warp_last_le(pos, S, p, s, n, c1 - 1, b0, p);
+        const uint32_t b0 = warp_last_le(pos, S, NB, s, n, c0, 0, NB);
+        const uint32_t b1 = warp_last_le(pos, S, NB, s, n, c1 - 1, b0, NB);
         if (threadIdx.x == 0) {
             s_b0 = b0;
             s_nb = b1 - b0 + 1;
@@ -1204,7 +1209,7 @@ __global__ __launch_bounds__(256) void k_exchange_copy(const uint64_t* __restric
     __syncthreads();
     const uint32_t b0 = s_b0, nb = s_nb;
     if (nb <= kXchMaxB) {
-        for (uint32_t i = threadIdx.x; i <= nb; i += blockDim.x) s_bnd[i] = bucket_pos(pos, S, p, s, b0 + i, n);
+        for (uint32_t i = threadIdx.x; i <= nb; i += blockDim.x) s_bnd[i] = bucket_pos(pos, S, NB, s, b0 + i, n);
         __syncthreads();
         // Four keys per thread per step, their loads issued together (memory
         // parallelism); j grows by the CTA width, so the run of j follows
@@ -1231,7 +1236,7 @@ __global__ __launch_bounds__(256) void k_exchange_copy(const uint64_t* __restric
                     while (hi - at > 1) { const uint32_t m = (at + hi) >> 1; if (s_bnd[m] <= j) at = m; else hi = m; }
                     lo = at;
                 }
-                const uint64_t d = dst[s * p + b0 + lo] + (j - s_bnd[lo]);
+                const uint64_t d = dst[s * NB + b0 + lo] + (j - s_bnd[lo]);
                 if (d >= N) { atomicOr(err, kDevErrBounds); continue; }
                 bkeys[d] = kv[u];
                 if (bpay) bpay[d] = pv[u];
@@ -1240,8 +1245,8 @@ __global__ __launch_bounds__(256) void k_exchange_copy(const uint64_t* __restric
     } else {
         for (uint32_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
             uint32_t lo = b0, hi = b0 + nb;
-            while (hi - lo > 1) { const uint32_t m = (lo + hi) >> 1; if (bucket_pos(pos, S, p, s, m, n) <= j) lo = m; else hi = m; }
-            const uint64_t d = dst[s * p + lo] + (j - bucket_pos(pos, S, p, s, lo, n));
+            while (hi - lo > 1) { const uint32_t m = (lo + hi) >> 1; if (bucket_pos(pos, S, NB, s, m, n) <= j) lo = m; else hi = m; }
+            const uint64_t d = dst[s * NB + lo] + (j - bucket_pos(pos, S, NB, s, lo, n));
             if (d >= N) { atomicOr(err, kDevErrBounds); continue; }
             bkeys[d] = skeys[base + j];
             if (bpay) bpay[d] = spay[base + j];
@@ -1251,11 +1256,12 @@ __global__ __launch_bounds__(256) void k_exchange_copy(const uint64_t* __restric
 
 cudaError_t exchange(const uint64_t* skeys, const uint32_t* spay, uint64_t N, uint32_t p, const uint64_t* d_seg_off,
                      const uint32_t* pos, const uint64_t* d_offsets, uint64_t* bkeys, uint32_t* bpay,
-                     uint64_t* dst_scratch, uint32_t* err, cudaStream_t st) {
+                     uint64_t* dst_scratch, uint32_t* err, cudaStream_t st, uint32_t nb) {
     if (N == 0) return cudaSuccess;
-    HSS_LAUNCH(k_exchange_dst, (unsigned)cdiv(p, 32), 1024, 0, st, d_seg_off, p, pos, d_offsets, dst_scratch, err);
+    const uint32_t NB = nb ? nb : p;
+    HSS_LAUNCH(k_exchange_dst, (unsigned)cdiv(NB, 32), 1024, 0, st, d_seg_off, p, NB, pos, d_offsets, dst_scratch, err);
     const uint64_t maxn = cdiv(N, p) + 1;
-    HSS_LAUNCH(k_exchange_copy, dim3(p, (unsigned)cdiv(maxn, kXchChunk)), 256, 0, st, skeys, spay, d_seg_off, p, pos,
+    HSS_LAUNCH(k_exchange_copy, dim3(p, (unsigned)cdiv(maxn, kXchChunk)), 256, 0, st, skeys, spay, d_seg_off, NB, pos,
                dst_scratch, bkeys, bpay, N, err);
     return cudaGetLastError();
 }

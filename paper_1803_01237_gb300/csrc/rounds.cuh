@@ -91,7 +91,9 @@ constexpr uint32_t kLoopHost = 0, kLoopAdaptive = 1, kLoopDevice = 2;
 
 // Run the histogram rounds over the p locally sorted segments skeys
 // (order-preserving key bits) and write the splitters, offsets and the final
-// per-segment positions of the splitters (into ws.Lpos).  d_prop[nprop]
+// per-segment positions of the splitters (into ws.Lpos).  nb (0: p) is the
+// number of buckets: nb - 1 splitters at ranks i N / nb (a stage of
+// multi-stage HSS partitions p processors' keys into nb < p groups).  d_prop[nprop]
 // (nullable; keys in the caller's representation, nprop <= ws.cap) are
 // proposed cuts ranked and offered to every splitter before round 1.
 // With the device loop (loop_mode) the rounds run as one CUDA graph (a WHILE
@@ -105,7 +107,8 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
                float oversample, uint32_t max_rounds, int key_type, hss_cut* d_splitters, uint64_t* d_offsets,
                const RoundWs& ws, cudaStream_t st, RoundResult* out, const uint64_t* d_prop = nullptr,
                uint32_t nprop = 0, uint32_t schedule = HSS_SCHEDULE_PROPORTIONAL, uint32_t schedule_k = 0,
-               uint32_t hist_mode = kHistAuto, uint32_t loop_mode = kLoopHost, bool* used_device_loop = nullptr);
+               uint32_t hist_mode = kHistAuto, uint32_t loop_mode = kLoopHost, bool* used_device_loop = nullptr,
+               uint32_t nb = 0);
 
 // Whether run_rounds can drive these rounds on the device.
 bool device_loop_possible(uint64_t cap, uint32_t schedule);
@@ -122,8 +125,8 @@ cudaError_t bucket_hints(const RoundWs& ws, const uint64_t* skeys, const uint64_
 
 // Exchange: per-(segment, bucket) destinations, then the run copy.
 cudaError_t exchange(const uint64_t* skeys, const uint32_t* spay, uint64_t N, uint32_t p, const uint64_t* d_seg_off,
-                     const uint32_t* pos /*[p][p-1]*/, const uint64_t* d_offsets, uint64_t* bkeys, uint32_t* bpay,
-                     uint64_t* dst_scratch /*[p][p]*/, uint32_t* err, cudaStream_t st);
+                     const uint32_t* pos /*[p][nb-1]*/, const uint64_t* d_offsets, uint64_t* bkeys, uint32_t* bpay,
+                     uint64_t* dst_scratch /*[p][nb]*/, uint32_t* err, cudaStream_t st, uint32_t nb = 0);
 
 // Ranks of arbitrary cuts (keys in caller representation).
 cudaError_t rank_cuts(const uint64_t* skeys, int key_type, uint64_t N, uint32_t p,
