@@ -341,6 +341,53 @@ int hss_partition_batch(const void* d_keys, int key_type, const uint64_t* h_size
                         size_t work_bytes, hss_batch_stats* h_stats, hss_job_stats* h_job_stats, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Two-stage HSS (Sec. 5.3, multi-stage with two stages; Sec. 7.3 uses
+ * r = sqrt(p) groups and the same eps in both stages).
+ *
+ * Stage 1 splits the N keys of p = prm->p processors (segments as for
+ * hss_sort) into `groups` = r groups: the same local sort, then histogram
+ * rounds for r - 1 group splitters whose target ranks are i N / r with
+ * tolerance floor(N eps / (2r)) and s r expected probes per round, then the
+ * exchange (group g holds its runs in processor order).  Stage 2 deals group
+ * g's keys by position to its p / r processors and sorts them with
+ * single-stage HSS, seed prm->seed + 1 + g (as hss_sort_batch does with
+ * seed prm->seed + 1).  The final p buckets are the groups' buckets in group
+ * order; the output is the stable sort of the input (payload in tow).
+ *
+ * Requirements (else HSS_ERR_INVALID before any device work): 2 <= r <= p,
+ * r divides p, p / r <= 65536, N >= 2p, the proportional schedule, u64 or
+ * i64 keys.  If stage 1 leaves a group with fewer than p / r keys (only when
+ * it did not balance) the call returns HSS_ERR_INVALID after stage 1.
+ *
+ * Outputs (device): d_keys_out[N] (d_payload_out[N] when d_payload is set),
+ * d_group_splitters[r - 1] (stage-1 cuts: seg / spos name an input processor
+ * and a position in its locally sorted keys), d_splitters[r (p/r - 1)]
+ * (stage-2 cuts, group-major; seg / spos name a processor of the group and
+ * a position in its sorted share; may be NULL when p = r), d_offsets[p + 1]
+ * (absolute: bucket g (p/r) + i of group g).  h_stats and h_group_stats[r]
+ * (host, nullable) receive each stage's round statistics.  The return value
+ * is stage 1's status if it failed, else the first failing group's.
+ * Synchronous (stage 2's tables depend on the group sizes).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    uint32_t groups;
+    int32_t status;
+    uint32_t kernel_launches;    /* kernels both stages launched */
+    uint32_t pad;
+    hss_stats stage1;            /* the group split: rounds, sample sizes, |gamma|; ms_phase 0..2 with HSS_FLAG_TIMING */
+    hss_batch_stats stage2;      /* the r group sorts */
+} hss_two_stage_stats;
+
+/* Workspace bytes of hss_sort_two_stage; 0 when the arguments are refused. */
+size_t hss_two_stage_workspace_bytes(uint64_t N, const hss_params* prm, uint32_t groups, int key_type,
+                                     int has_payload);
+
+int hss_sort_two_stage(const void* d_keys, const uint32_t* d_payload, int key_type, uint64_t N, const hss_params* prm,
+                       uint32_t groups, void* d_keys_out, uint32_t* d_payload_out, hss_cut* d_group_splitters,
+                       hss_cut* d_splitters, uint64_t* d_offsets, void* d_work, size_t work_bytes,
+                       hss_two_stage_stats* h_stats, hss_job_stats* h_group_stats, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Learned splitter proposal: a 1-32-32-1 CDF network of the keys.
  *
  * The paper proposes no model; its rounds (Sec. 4.2.2) take any candidate

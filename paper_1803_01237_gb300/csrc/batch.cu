@@ -20,6 +20,7 @@
 #include "rounds.cuh"
 #include "rounds_dev.cuh"
 #include "segsort.cuh"
+#include "batch.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -654,10 +655,12 @@ T* at(void* base, size_t off) { return (T*)((char*)base + off); }
 
 #define HSS_BTRY(x) do { if ((x) != cudaSuccess) return HSS_ERR_CUDA; } while (0)
 
+}  // namespace
+
 int run_batch(const void* d_keys, const uint32_t* d_payload, int key_type, const uint64_t* h_sizes, const uint32_t* h_p,
               uint32_t njobs, const hss_params* prm, void* d_keys_out, uint32_t* d_payload_out, hss_cut* d_splitters,
               uint64_t* d_offsets, void* d_work, size_t work_bytes, hss_batch_stats* h_stats,
-              hss_job_stats* h_job_stats, cudaStream_t st, bool sort) {
+              hss_job_stats* h_job_stats, cudaStream_t st, bool sort, const BatchExtra& ex) {
     const uint64_t mark = hss_kernel_launch_count();
     if (h_stats) std::memset(h_stats, 0, sizeof(*h_stats));
     if (!prm || !(prm->eps > 0.0) || !(prm->oversample > 0.0f) || njobs == 0 || !h_sizes || !h_p) return HSS_ERR_INVALID;
@@ -735,7 +738,7 @@ int run_batch(const void* d_keys, const uint32_t* d_payload, int key_type, const
 
     // Local sort of every segment of every job.
     HSS_BTRY(segsort((const uint64_t*)d_keys, keysA, keysB, d_payload, pay ? payA : nullptr, pay ? payB : nullptr, T.N_tot,
-                     T.P_tot, seg_off, i64, false, sws, st, nullptr));
+                     T.P_tot, seg_off, i64 && !ex.keys_ordered, false, sws, st, nullptr, ex.hint_lo, ex.hint_mult));
     if (timing) cudaEventRecord(ev[1], st);
 
     // Rounds, all jobs in lock step.
@@ -842,7 +845,23 @@ int run_batch(const void* d_keys, const uint32_t* d_payload, int key_type, const
     return status;
 }
 
-}  // namespace
+size_t batch_bytes_bound(uint64_t N, uint32_t njobs, uint32_t pj, const hss_params* prm, bool pay) {
+    if (!prm || njobs == 0 || pj == 0) return 0;
+    // The layout depends on the sizes only through the sample capacities,
+    // each at most ceil(2 s p_j) + 4096 whatever the job's size: lay out
+    // jobs of equal size and the largest capacity.
+    std::vector<uint64_t> sizes(njobs);
+    for (uint32_t j = 0; j < njobs; ++j)
+        sizes[j] = (uint64_t)(((unsigned __int128)(j + 1) * N) / njobs) - (uint64_t)(((unsigned __int128)j * N) / njobs);
+    std::vector<uint32_t> ps(njobs, pj);
+    Tables T;
+    if (build_tables(sizes.data(), ps.data(), njobs, prm, T) != HSS_OK) return 0;
+    const uint64_t cap = (uint64_t)std::ceil(2.0 * (double)prm->oversample * (double)pj) + 4096;
+    T.C_tot = cap * njobs;
+    T.PP_tot = (uint64_t)pj * cap * njobs;
+    return plan_batch(T, njobs, pay, true).total;
+}
+
 }  // namespace hss
 
 using namespace hss;
@@ -863,14 +882,14 @@ int hss_sort_batch(const void* d_keys, const uint32_t* d_payload, int key_type, 
                    hss_cut* d_splitters, uint64_t* d_offsets, void* d_work, size_t work_bytes, hss_batch_stats* h_stats,
                    hss_job_stats* h_job_stats, void* stream) {
     return run_batch(d_keys, d_payload, key_type, h_sizes, h_p, njobs, prm, d_keys_out, d_payload_out, d_splitters,
-                     d_offsets, d_work, work_bytes, h_stats, h_job_stats, (cudaStream_t)stream, true);
+                     d_offsets, d_work, work_bytes, h_stats, h_job_stats, (cudaStream_t)stream, true, BatchExtra{});
 }
 
 int hss_partition_batch(const void* d_keys, int key_type, const uint64_t* h_sizes, const uint32_t* h_p, uint32_t njobs,
                         const hss_params* prm, hss_cut* d_splitters, uint64_t* d_offsets, void* d_work,
                         size_t work_bytes, hss_batch_stats* h_stats, hss_job_stats* h_job_stats, void* stream) {
     return run_batch(d_keys, nullptr, key_type, h_sizes, h_p, njobs, prm, nullptr, nullptr, d_splitters, d_offsets,
-                     d_work, work_bytes, h_stats, h_job_stats, (cudaStream_t)stream, false);
+                     d_work, work_bytes, h_stats, h_job_stats, (cudaStream_t)stream, false, BatchExtra{});
 }
 
 }  // extern "C"

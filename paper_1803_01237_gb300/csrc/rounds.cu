@@ -43,8 +43,9 @@ uint64_t sample_capacity(uint64_t N, uint64_t p, float oversample) {
     return std::max<uint64_t>(cap, 1);
 }
 
-size_t rounds_ws_bytes(uint64_t N, uint64_t p, uint64_t cap) {
-    const uint64_t S = p > 0 ? p - 1 : 0;
+size_t rounds_ws_bytes(uint64_t N, uint64_t p, uint64_t cap, uint64_t nb) {
+    const uint64_t NB = nb ? nb : p;
+    const uint64_t S = NB > 0 ? NB - 1 : 0;
     const uint64_t S1 = std::max<uint64_t>(S, 1);
     size_t b = 0;
     b += aup(sizeof(RoundCtl));
@@ -66,8 +67,9 @@ size_t rounds_ws_bytes(uint64_t N, uint64_t p, uint64_t cap) {
     return b;
 }
 
-RoundWs rounds_ws_carve(void* base, uint64_t N, uint64_t p, uint64_t cap, uint32_t* err) {
-    const uint64_t S = p > 0 ? p - 1 : 0;
+RoundWs rounds_ws_carve(void* base, uint64_t N, uint64_t p, uint64_t cap, uint32_t* err, uint64_t nb) {
+    const uint64_t NB = nb ? nb : p;
+    const uint64_t S = NB > 0 ? NB - 1 : 0;
     const uint64_t S1 = std::max<uint64_t>(S, 1);
     RoundWs w;
     char* q = (char*)base;
@@ -710,9 +712,10 @@ __global__ void k_bucket_hint(uint32_t p, const uint64_t* __restrict__ fin_okey,
 }
 
 cudaError_t bucket_hints(const RoundWs& ws, const uint64_t* skeys, const uint64_t* d_seg_off, uint32_t p,
-                         cudaStream_t st) {
+                         cudaStream_t st, uint32_t nb) {
+    const uint32_t NB = nb ? nb : p;
     HSS_LAUNCH(k_key_range, 1, 1024, 0, st, skeys, d_seg_off, p, ws.key_range);
-    HSS_LAUNCH(k_bucket_hint, (unsigned)cdiv(p, 256), 256, 0, st, p, ws.fin_okey, ws.fin_kind, ws.key_range,
+    HSS_LAUNCH(k_bucket_hint, (unsigned)cdiv(NB, 256), 256, 0, st, NB, ws.fin_okey, ws.fin_kind, ws.key_range,
                ws.bucket_lo, ws.bucket_mult);
     return cudaGetLastError();
 }

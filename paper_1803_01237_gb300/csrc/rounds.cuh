@@ -69,8 +69,10 @@ struct RoundWs {
     uint64_t cap;        // sample capacity
 };
 
-size_t rounds_ws_bytes(uint64_t N, uint64_t p, uint64_t cap);
-RoundWs rounds_ws_carve(void* base, uint64_t N, uint64_t p, uint64_t cap, uint32_t* err);
+// nb (0: p) buckets: the per-splitter arrays hold nb - 1 entries, the
+// per-(segment, splitter) arrays p x (nb - 1).
+size_t rounds_ws_bytes(uint64_t N, uint64_t p, uint64_t cap, uint64_t nb = 0);
+RoundWs rounds_ws_carve(void* base, uint64_t N, uint64_t p, uint64_t cap, uint32_t* err, uint64_t nb = 0);
 uint64_t sample_capacity(uint64_t N, uint64_t p, float oversample);
 
 struct RoundResult {
@@ -119,9 +121,10 @@ int read_round_result(const RoundWs& ws, RoundResult* out, cudaStream_t st);
 // Kernels one round of the device-driven loop launches.
 uint32_t device_round_kernels();
 
-// Per-bucket split windows for the merge, from the final splitters.
+// Per-bucket split windows for the merge, from the final splitters: the key
+// range of the p locally sorted segments, cut into nb (0: p) buckets.
 cudaError_t bucket_hints(const RoundWs& ws, const uint64_t* skeys, const uint64_t* d_seg_off, uint32_t p,
-                         cudaStream_t st);
+                         cudaStream_t st, uint32_t nb = 0);
 
 // Exchange: per-(segment, bucket) destinations, then the run copy.
 cudaError_t exchange(const uint64_t* skeys, const uint32_t* spay, uint64_t N, uint32_t p, const uint64_t* d_seg_off,

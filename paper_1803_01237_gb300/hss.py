@@ -707,3 +707,89 @@ def partition_batch(keys, sizes, ps, eps: float, seed: int, oversample: float = 
                     key_type: str = "u64", flags: int = 0, stream=None) -> BatchResult:
     """hss_partition of every job of a batch, all jobs together."""
     return _batch(keys, sizes, ps, eps, seed, None, oversample, max_rounds, key_type, flags, False, None, None, stream)
+
+
+# ---------------------------------------------------------------------------
+# Two-stage HSS (hss_sort_two_stage)
+# ---------------------------------------------------------------------------
+class TwoStageStats(ctypes.Structure):
+    _fields_ = [("groups", ctypes.c_uint32), ("status", ctypes.c_int32), ("kernel_launches", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32), ("stage1", Stats), ("stage2", BatchStats)]
+
+
+@dataclass
+class TwoStageResult:
+    keys: torch.Tensor
+    payload: torch.Tensor | None
+    offsets: torch.Tensor          # (p + 1,) absolute bucket offsets
+    group_splitters: torch.Tensor  # (r - 1, 2) packed hss_cut records (stage 1)
+    splitters: torch.Tensor        # (r (p/r - 1), 2) packed hss_cut records (stage 2, group-major)
+    groups: int
+    status: int
+    stage1: Result                 # the group split (keys None; offsets = group offsets)
+    group_rounds: list
+    group_sample_size: list
+    group_gamma: list
+    group_unresolved: list
+    group_status: list
+    group_tol: list
+    lockstep_rounds: int
+    kernel_launches: int
+    ms_phase: dict                 # stage-1 and stage-2 phases
+
+    def group_splitters_of(self, g: int) -> torch.Tensor:
+        pg = (self.offsets.numel() - 1) // self.groups
+        return self.splitters[g * (pg - 1):(g + 1) * (pg - 1)]
+
+
+def sort_two_stage(keys, p: int, groups: int, eps: float, seed: int, payload=None, oversample: float = 5.0,
+                   max_rounds: int = 0, key_type: str = "u64", flags: int = 0, out=None, out_payload=None,
+                   stream=None) -> TwoStageResult:
+    """Two-stage HSS (hss_sort_two_stage): the p processors' keys split into
+    `groups` groups, then each group sorted over its p / groups processors
+    with seed + 1 + g."""
+    lib = load()
+    if not hasattr(lib, "_two_stage_bound"):
+        P, U64, U32, I32, SZ = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_size_t
+        lib.hss_two_stage_workspace_bytes.argtypes = [U64, ctypes.POINTER(Params), U32, I32, I32]
+        lib.hss_two_stage_workspace_bytes.restype = SZ
+        lib.hss_sort_two_stage.argtypes = [P, P, I32, U64, ctypes.POINTER(Params), U32, P, P, P, P, P, P, SZ,
+                                           ctypes.POINTER(TwoStageStats), P, P]
+        lib.hss_sort_two_stage.restype = I32
+        lib._two_stage_bound = True
+    keys = _as_key_tensor(keys)
+    N = keys.numel()
+    r = int(groups)
+    prm = _params(p, eps, seed, oversample, max_rounds, flags)
+    nb = int(lib.hss_two_stage_workspace_bytes(N, ctypes.byref(prm), r, KEY_TYPES[key_type], int(payload is not None)))
+    if nb == 0:
+        raise HSSError(ERR_INVALID, "hss_two_stage_workspace_bytes")
+    ws = workspace(nb, keys.device)
+    if out is None:
+        out = torch.empty_like(keys)
+    if payload is not None and out_payload is None:
+        out_payload = torch.empty_like(payload)
+    pg = p // r
+    gspl = torch.empty((max(r - 1, 1), 2), dtype=torch.int64, device=keys.device)
+    spl = torch.empty((max(r * (pg - 1), 1), 2), dtype=torch.int64, device=keys.device)
+    off = torch.empty(p + 1, dtype=torch.int64, device=keys.device)
+    st = TwoStageStats()
+    js = (JobStats * r)()
+    rc = lib.hss_sort_two_stage(_ptr(keys), _ptr(payload), KEY_TYPES[key_type], N, ctypes.byref(prm), r, _ptr(out),
+                                _ptr(out_payload), _ptr(gspl), _ptr(spl), _ptr(off), _ptr(ws), ws.numel(),
+                                ctypes.byref(st), js, _stream(stream))
+    if rc in (ERR_INVALID, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT):
+        raise HSSError(rc, "hss_sort_two_stage")
+    goff = off[::pg].clone()
+    s1 = _result(None, None, gspl[:r - 1], goff, st.stage1)
+    ms = {f"stage1_{PHASES[i]}": float(st.stage1.ms_phase[i]) for i in range(3)}
+    ms.update({f"stage2_{PHASES[i]}": float(st.stage2.ms_phase[i]) for i in range(NUM_PHASES)})
+    return TwoStageResult(
+        keys=out, payload=out_payload, offsets=off, group_splitters=gspl[:r - 1], splitters=spl[:r * (pg - 1)],
+        groups=r, status=rc, stage1=s1,
+        group_rounds=[int(x.rounds) for x in js], group_status=[int(x.status) for x in js],
+        group_tol=[int(x.tol) for x in js],
+        group_sample_size=[[int(v) for v in x.sample_size[:x.rounds]] for x in js],
+        group_gamma=[[int(v) for v in x.gamma[:x.rounds]] for x in js],
+        group_unresolved=[[int(v) for v in x.unresolved[:x.rounds + 1]] for x in js],
+        lockstep_rounds=int(st.stage2.lockstep_rounds), kernel_launches=int(st.kernel_launches), ms_phase=ms)

@@ -151,3 +151,37 @@ def test_segment_size_limit_rejected_without_device(lib):
     prm2 = hss.Params(eps=1.0, seed=1, p=2, oversample=5.0, max_rounds=0, flags=0)
     assert L.hss_sort(dummy, None, 0, 1 << 30, ctypes.byref(prm2), dummy, None, dummy, dummy, dummy, 1 << 62,
                       ctypes.byref(st), None) == -1
+
+
+def test_two_stage_arguments_rejected_without_device(lib):
+    """hss_sort_two_stage sizes its workspace on the host and refuses group
+    counts that do not divide p, a single group, fewer than 2p keys and
+    schedules other than the proportional one before any device work."""
+    from paper_1803_01237_gb300 import hss
+    L = hss.load()
+    L.hss_two_stage_workspace_bytes.restype = ctypes.c_size_t
+    L.hss_two_stage_workspace_bytes.argtypes = [ctypes.c_uint64, ctypes.POINTER(hss.Params), ctypes.c_uint32,
+                                                ctypes.c_int, ctypes.c_int]
+
+    def prm(p, **kw):
+        return hss.Params(eps=kw.get("eps", 0.02), seed=1, p=p, oversample=5.0, max_rounds=0, flags=0,
+                          schedule=kw.get("schedule", 0))
+
+    N = 1 << 20
+    ok = L.hss_two_stage_workspace_bytes(N, ctypes.byref(prm(256)), 16, 0, 0)
+    assert ok >= 2 * 8 * N
+    assert L.hss_two_stage_workspace_bytes(N, ctypes.byref(prm(256)), 16, 0, 1) > ok
+    assert L.hss_two_stage_workspace_bytes(N << 1, ctypes.byref(prm(256)), 16, 0, 0) > ok
+    for n, p, r, kw in [(N, 256, 1, {}), (N, 256, 24, {}), (N, 256, 512, {}), (300, 256, 16, {}),
+                        (N, 256, 16, {"schedule": 1}), (N, 256, 16, {"eps": 0.0}), (N, 1 << 18, 2, {})]:
+        assert L.hss_two_stage_workspace_bytes(n, ctypes.byref(prm(p, **kw)), r, 0, 0) == 0
+    P = ctypes.c_void_p
+    L.hss_sort_two_stage.restype = ctypes.c_int
+    L.hss_sort_two_stage.argtypes = [P, P, ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(hss.Params), ctypes.c_uint32,
+                                     P, P, P, P, P, P, ctypes.c_size_t, ctypes.POINTER(hss.TwoStageStats), P, P]
+    st = hss.TwoStageStats()
+    dummy = ctypes.c_void_p(16)
+    args = lambda p, r, work: (dummy, None, 0, N, ctypes.byref(prm(p)), r, dummy, None, dummy, dummy, dummy, dummy,
+                               work, ctypes.byref(st), None, None)
+    assert L.hss_sort_two_stage(*args(256, 24, 1 << 40)) == -1
+    assert L.hss_sort_two_stage(*args(256, 16, 16)) == -2

@@ -1,0 +1,161 @@
+"""Pins of the oracle's two-stage HSS (Sec. 5.3; Sec. 7.3 runs two stages with
+r = sqrt(p) groups and eps per stage) against brute force and the
+single-stage special case.  CPU only."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1803_01237_gb300 import inputs
+
+GENS = {"uniform": inputs.uniform, "gauss_mix": inputs.gauss_mix, "zipf": inputs.zipf, "skew3": inputs.skew3,
+        "allzeros": inputs.allzeros}
+
+
+def _local_order(keys, p):
+    """Input index of every (processor, position) after the stable local sort."""
+    b = oracle.segment_bounds(keys.shape[0], p)
+    return b, [int(b[s]) + np.argsort(keys[int(b[s]):int(b[s + 1])], kind="stable") for s in range(p)]
+
+
+def _global_rank(keys):
+    order = np.argsort(keys, kind="stable")
+    rank = np.empty(keys.shape[0], dtype=np.int64)
+    rank[order] = np.arange(keys.shape[0])
+    return rank
+
+
+@pytest.mark.parametrize("gen", ["uniform", "zipf"])
+def test_groups_with_nb_equal_p_is_single_stage(gen):
+    N, p, eps, seed = 5000, 16, 0.05, 4
+    keys = GENS[gen](N, 2)
+    one = oracle.hss(keys, p, eps, seed)
+    grp = oracle.hss_groups(keys, p, p, eps, seed, exchange_only=False)
+    assert grp.rounds == one.rounds
+    assert np.array_equal(grp.offsets, one.offsets)
+    assert np.array_equal(grp.splitter_key, one.splitter_key)
+    assert np.array_equal(grp.splitter_seg, one.splitter_seg)
+    assert np.array_equal(grp.splitter_spos, one.splitter_spos)
+    assert np.array_equal(grp.sample_size, one.sample_size)
+    assert np.array_equal(grp.out_keys, one.out_keys)
+
+
+@pytest.mark.parametrize("gen", list(GENS))
+def test_group_split_contract(gen):
+    """Stage 1: r - 1 cuts at ranks within floor(N eps / 2r) of i N / r; each
+    cut is the input element of that rank."""
+    N, p, r, eps, seed = 1 << 14, 64, 8, 0.04, 7
+    keys = GENS[gen](N, 3)
+    st1 = oracle.hss_groups(keys, p, r, eps, seed)
+    assert st1.status == 0
+    tol = int(np.floor(N * eps / (2 * r)))
+    assert st1.tol == tol
+    off = st1.offsets.astype(np.int64)
+    assert off[0] == 0 and off[-1] == N and np.all(np.diff(off) >= 0)
+    t = np.array([(i * N) // r for i in range(1, r)], dtype=np.int64)
+    assert np.all(np.abs(off[1:-1] - t) <= tol)
+    rank = _global_rank(keys)
+    _, idx = _local_order(keys, p)
+    for i in range(r - 1):
+        seg = int(st1.splitter_seg[i])
+        if seg >= 0:
+            e = idx[seg][int(st1.splitter_spos[i])]
+            assert rank[e] == off[i + 1]
+            assert keys[e] == st1.splitter_key[i]
+
+
+@pytest.mark.parametrize("gen", ["uniform", "zipf", "allzeros"])
+def test_group_exchange_order_brute_force(gen):
+    """Group g holds, processor by processor, each processor's locally sorted
+    keys whose global rank lies in [off_g, off_{g+1})."""
+    N, p, r, eps, seed = 6000, 24, 6, 0.05, 11
+    keys = GENS[gen](N, 5)
+    payload = np.arange(N, dtype=np.uint32)
+    st1 = oracle.hss_groups(keys, p, r, eps, seed, payload=payload)
+    rank = _global_rank(keys)
+    _, idx = _local_order(keys, p)
+    off = st1.offsets.astype(np.int64)
+    want = []
+    for g in range(r):
+        for q in range(p):
+            e = idx[q]
+            sel = e[(rank[e] >= off[g]) & (rank[e] < off[g + 1])]
+            want.append(sel)
+    want = np.concatenate(want)
+    assert np.array_equal(st1.out_payload, want.astype(np.uint32))
+    assert np.array_equal(st1.out_keys, keys[want])
+
+
+@pytest.mark.parametrize("gen", list(GENS))
+def test_two_stage_contract(gen):
+    """The output is the stable sort; the group boundaries are stage 1's
+    offsets; inside group g every bucket start is within
+    floor(n_g eps / (2 p/r)) of i n_g / (p/r)."""
+    N, p, r, eps, seed = 1 << 14, 64, 8, 0.04, 9
+    keys = GENS[gen](N, 6)
+    payload = np.arange(N, dtype=np.uint32)
+    res = oracle.hss_two_stage(keys, p, r, eps, seed, payload=payload)
+    order = np.argsort(keys, kind="stable")
+    assert np.array_equal(res.out_keys, keys[order])
+    assert np.array_equal(res.out_payload, payload[order])
+    pg = p // r
+    off = res.offsets.astype(np.int64)
+    assert off.shape[0] == p + 1 and off[0] == 0 and off[-1] == N and np.all(np.diff(off) >= 0)
+    assert np.array_equal(off[::pg], res.stage1.offsets.astype(np.int64))
+    for g in range(r):
+        a, b = int(off[g * pg]), int(off[(g + 1) * pg])
+        n = b - a
+        tol = int(np.floor(n * eps / (2 * pg)))
+        st = res.stage2[g]
+        assert st.status == 0 and st.tol == tol
+        rel = off[g * pg:(g + 1) * pg + 1] - a
+        t = np.array([(i * n) // pg for i in range(1, pg)], dtype=np.int64)
+        assert np.all(np.abs(rel[1:-1] - t) <= tol)
+
+
+@pytest.mark.parametrize("gen", ["uniform", "gauss_mix", "zipf"])
+def test_stage_two_deals_groups_by_position(gen):
+    """Every stage-2 cut (seg j, spos) names position spos of the stable sort
+    of the j-th of p/r equal slices of the group's exchanged keys, and that
+    element has the cut's rank in the group."""
+    N, p, r, eps, seed = 1 << 13, 32, 4, 0.05, 2
+    keys = GENS[gen](N, 8)
+    res = oracle.hss_two_stage(keys, p, r, eps, seed)
+    pg = p // r
+    st1 = res.stage1
+    for g in range(r):
+        a, b = int(st1.offsets[g]), int(st1.offsets[g + 1])
+        gk = st1.out_keys[a:b]
+        n = b - a
+        rank = _global_rank(gk)
+        st = res.stage2[g]
+        for i in range(pg - 1):
+            j = int(st.splitter_seg[i])
+            if j < 0:
+                continue
+            lo, hi = (j * n) // pg, ((j + 1) * n) // pg
+            e = lo + np.argsort(gk[lo:hi], kind="stable")[int(st.splitter_spos[i])]
+            assert gk[e] == st.splitter_key[i]
+            assert rank[e] == int(st.offsets[i + 1])
+
+
+def test_stage_one_draws_s_r_probes():
+    """Round 1 of stage 1 samples every key with probability s r / N, so it
+    draws s r probes in expectation (not s p)."""
+    N, p, r, eps, s = 1 << 15, 256, 16, 0.02, 5.0
+    keys = inputs.uniform(N, 1)
+    z = [int(oracle.hss_groups(keys, p, r, eps, seed, oversample=s).sample_size[0]) for seed in range(12)]
+    mean = float(np.mean(z))
+    # Binomial(N, s r / N): mean s r = 80, sd about 9; the mean of 12 draws
+    # has sd about 2.6, while s p would be 1280
+    assert abs(mean - s * r) < 12.0
+    assert max(z) < 3 * s * r
+
+
+def test_two_stage_with_r_equal_p():
+    """p / r = 1: every group is one final bucket, sorted by its own
+    single-processor HSS."""
+    N, p, eps = 3000, 8, 0.05
+    keys = inputs.zipf(N, 4)
+    res = oracle.hss_two_stage(keys, p, p, eps, 3)
+    assert np.array_equal(res.out_keys, np.sort(keys, kind="stable"))
+    assert np.array_equal(res.offsets, res.stage1.offsets)
