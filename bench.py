@@ -525,6 +525,32 @@ def run_morton_workload(args):
     launches = hss.launch_count() - l0
     ms = ev0.elapsed_time(ev1) / args.steps
     o = out[:: max(1, N // (1 << 20))].cpu().numpy().view(np.uint64)
+    two = None
+    if args.groups > 1:
+        # The same step as two-stage HSS: the p processors split into
+        # `groups` groups first, then every group sorted over p / groups
+        # processors (Sec. 5.3; Sec. 7.3 takes r = sqrt(p) = 128 at p = 16384).
+        R = args.groups
+        for _ in range(max(1, args.warmup)):
+            hss.sort_two_stage(keys, P, R, E, SEED, payload=pay, out=out, out_payload=out_p)
+        torch.cuda.synchronize(dev)
+        phase2 = {}
+        l2 = hss.launch_count()
+        ev0.record()
+        for _ in range(args.steps):
+            t = hss.sort_two_stage(keys, P, R, E, SEED, payload=pay, out=out, out_payload=out_p, flags=hss.FLAG_TIMING)
+            for k, v in t.ms_phase.items():
+                phase2[k] = phase2.get(k, 0.0) + v / args.steps
+        ev1.record()
+        torch.cuda.synchronize(dev)
+        ms2 = ev0.elapsed_time(ev1) / args.steps
+        o2 = out[:: max(1, N // (1 << 20))].cpu().numpy().view(np.uint64)
+        two = {"groups": R, "ms_per_step": ms2, "keys_per_s": N / (ms2 / 1000.0),
+               "stage1_rounds": t.stage1.rounds, "stage1_sample_size": t.stage1.sample_size,
+               "stage2_lockstep_rounds": t.lockstep_rounds,
+               "stage2_mean_rounds": float(np.mean(t.group_rounds)), "phase_ms": phase2,
+               "gpu_launches": hss.launch_count() - l2, "output_sorted": bool(np.all(o2[:-1] <= o2[1:])),
+               "same_output_as_single_stage": bool(np.array_equal(o, o2))}
     line = {
         "metric": "keys/s (HSS sort with u32 payload)", "value": N / (ms / 1000.0), "unit": "keys/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -536,6 +562,8 @@ def run_morton_workload(args):
                 "output_sorted": bool(np.all(o[:-1] <= o[1:]))},
         "gpu_launches": launches, "clocks": clk,
     }
+    if two is not None:
+        line["two_stage"] = two
     print(json.dumps(line), flush=True)
     return 0
 
@@ -699,6 +727,8 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-low-rate", type=float, default=300.0)
     ap.add_argument("--morton-log2n", type=int, default=30, help="config 3 size (morton workload)")
+    ap.add_argument("--groups", type=int, default=128,
+                    help="morton workload: also time two-stage HSS with this many groups (0: skip)")
     args = ap.parse_args()
     if args.workload == "batch" and args.impl == "gb300":
         args.warmup = max(args.warmup, 1)

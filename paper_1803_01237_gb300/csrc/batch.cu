@@ -500,14 +500,20 @@ __global__ __launch_bounds__(1024) void kb_exchange_dst(const BJob* __restrict__
     if (s1 == p && s0 < s1 && run != J.koff + off[b + 1]) atomicOr(err, kDevErrBounds);
 }
 
-constexpr uint32_t kBXchChunk = 4096;
+constexpr uint32_t kBXchChunk = 8192;
+constexpr uint32_t kBXchMaxB = 2048;
 
+// CTA (g, y): keys [y kBXchChunk, (y + 1) kBXchChunk) of segment g.  The run
+// boundaries of the buckets that chunk meets are staged in shared memory;
+// each thread moves four keys per step (their loads issued together) and
+// finds each key's run by galloping forward from the previous one.
 __global__ __launch_bounds__(256) void kb_exchange_copy(const uint64_t* __restrict__ skeys, const uint32_t* __restrict__ spay,
                                                         const BJob* __restrict__ jobs,
                                                         const uint32_t* __restrict__ job_of_seg,
                                                         const uint32_t* __restrict__ pos, const uint64_t* __restrict__ dst,
                                                         uint64_t* __restrict__ bkeys, uint32_t* __restrict__ bpay,
                                                         uint32_t* __restrict__ err) {
+    __shared__ uint32_t s_bnd[kBXchMaxB + 1];
     __shared__ uint32_t s_b0, s_nb;
     const uint32_t g = blockIdx.x;
     const BJob J = jobs[job_of_seg[g]];
@@ -541,13 +547,46 @@ __global__ __launch_bounds__(256) void kb_exchange_copy(const uint64_t* __restri
     __syncthreads();
     const uint32_t b0 = s_b0, nb = s_nb;
     const uint64_t lim = J.koff + J.n;
-    for (uint32_t q = c0 + threadIdx.x; q < c1; q += blockDim.x) {
-        uint32_t lo = b0, hi = b0 + nb;  // last bucket whose run starts at or before q
-        while (hi - lo > 1) { const uint32_t m = (lo + hi) >> 1; if (bpos(P, S, p, s, m, n) <= q) lo = m; else hi = m; }
-        const uint64_t d = dst[J.dbase + (uint64_t)s * p + lo] + (q - bpos(P, S, p, s, lo, n));
-        if (d < J.koff || d >= lim) { atomicOr(err, kDevErrBounds); continue; }
-        bkeys[d] = skeys[base + q];
-        if (bpay) bpay[d] = spay[base + q];
+    const uint64_t* D = dst + J.dbase + (uint64_t)s * p;
+    if (nb <= kBXchMaxB) {
+        for (uint32_t i = threadIdx.x; i <= nb; i += blockDim.x) s_bnd[i] = bpos(P, S, p, s, b0 + i, n);
+        __syncthreads();
+        uint32_t lo = 0;
+        for (uint32_t j0 = c0 + threadIdx.x; j0 < c1; j0 += 4 * blockDim.x) {
+            uint64_t kv[4];
+            uint32_t pv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t j = j0 + u * blockDim.x;
+                kv[u] = j < c1 ? skeys[base + j] : 0ull;
+                pv[u] = (bpay && j < c1) ? spay[base + j] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t j = j0 + u * blockDim.x;
+                if (j >= c1) break;
+                if (lo + 1 < nb && s_bnd[lo + 1] <= j) {  // gallop forward, then bisect
+                    uint32_t at = lo + 1, step = 1;
+                    while (at + step < nb && s_bnd[at + step] <= j) { at += step; step <<= 1; }
+                    uint32_t hi = min(at + step, nb);
+                    while (hi - at > 1) { const uint32_t m = (at + hi) >> 1; if (s_bnd[m] <= j) at = m; else hi = m; }
+                    lo = at;
+                }
+                const uint64_t d = D[b0 + lo] + (j - s_bnd[lo]);
+                if (d < J.koff || d >= lim) { atomicOr(err, kDevErrBounds); continue; }
+                bkeys[d] = kv[u];
+                if (bpay) bpay[d] = pv[u];
+            }
+        }
+    } else {
+        for (uint32_t q = c0 + threadIdx.x; q < c1; q += blockDim.x) {
+            uint32_t lo = b0, hi = b0 + nb;  // last bucket whose run starts at or before q
+            while (hi - lo > 1) { const uint32_t m = (lo + hi) >> 1; if (bpos(P, S, p, s, m, n) <= q) lo = m; else hi = m; }
+            const uint64_t d = D[lo] + (q - bpos(P, S, p, s, lo, n));
+            if (d < J.koff || d >= lim) { atomicOr(err, kDevErrBounds); continue; }
+            bkeys[d] = skeys[base + q];
+            if (bpay) bpay[d] = spay[base + q];
+        }
     }
 }
 
@@ -560,6 +599,61 @@ __global__ void kb_bucket_off(uint32_t P_tot, uint64_t N_tot, const BJob* __rest
     if (g == P_tot) { boff[g] = N_tot; return; }
     const BJob J = jobs[job_of_seg[g]];
     boff[g] = J.koff + offsets[J.obase + (g - J.sbase)];
+}
+
+// Key range of every job: the smallest first key and the largest last key
+// of its locally sorted segments.
+__global__ __launch_bounds__(256) void kb_key_range(const uint64_t* __restrict__ skeys, const BJob* __restrict__ jobs,
+                                                    const uint64_t* __restrict__ seg_off, uint64_t* __restrict__ range) {
+    __shared__ uint64_t s_lo[8], s_hi[8];
+    const BJob J = jobs[blockIdx.x];
+    uint64_t lo = ~0ull, hi = 0ull;
+    for (uint32_t s = threadIdx.x; s < J.p; s += blockDim.x) {
+        const uint64_t a = seg_off[J.sbase + s], b = seg_off[J.sbase + s + 1];
+        if (a < b) {
+            lo = min(lo, skeys[a]);
+            hi = max(hi, skeys[b - 1]);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) { s_lo[threadIdx.x >> 5] = lo; s_hi[threadIdx.x >> 5] = hi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) { lo = min(lo, s_lo[w]); hi = max(hi, s_hi[w]); }
+        range[2 * (uint64_t)blockIdx.x] = lo;
+        range[2 * (uint64_t)blockIdx.x + 1] = hi;
+    }
+}
+
+// Window of every bucket for the first split of the merge: its keys lie
+// between the job's final cuts b and b + 1 (tag order), clipped to the job's
+// key range; mulhi(key - lo, mult) maps that interval onto 0..255.
+__global__ void kb_bucket_hint(uint32_t P_tot, const BJob* __restrict__ jobs, const uint32_t* __restrict__ job_of_seg,
+                               const DCut* __restrict__ Lcut, const DCut* __restrict__ Ucut,
+                               const uint32_t* __restrict__ choose_u, const uint64_t* __restrict__ range,
+                               uint64_t* __restrict__ lo_out, uint64_t* __restrict__ mult_out) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= P_tot) return;
+    const uint32_t j = job_of_seg[g];
+    const BJob J = jobs[j];
+    const uint32_t b = g - J.sbase;
+    auto bound = [&](uint32_t i, uint64_t if_none) -> uint64_t {  // cut i (1..p-1) of the job
+        if (i == 0 || i == J.p) return if_none;
+        const uint32_t gi = J.ibase + i - 1;
+        const DCut c = choose_u[gi] ? Ucut[gi] : Lcut[gi];
+        if (c.kind == kNegInf) return 0ull;
+        if (c.kind == kPosInf) return ~0ull;
+        return c.okey;
+    };
+    const uint64_t lo = max(bound(b, 0ull), range[2 * (uint64_t)j]);
+    uint64_t hi = min(bound(b + 1, ~0ull), range[2 * (uint64_t)j + 1]);
+    if (hi < lo) hi = lo;  // empty bucket
+    const uint64_t r = hi - lo;
+    lo_out[g] = lo;
+    mult_out[g] = r < 256 ? 0ull : (uint64_t)(((unsigned __int128)255 << 64) / r);
 }
 
 // ---------------------------------------------------------------------------
@@ -611,7 +705,8 @@ int build_tables(const uint64_t* sizes, const uint32_t* ps, uint32_t njobs, cons
 struct BLayout {
     size_t keysA, keysB, payA, payB, seg_off, err, sws, jobs, jseg, jspl, ctl, jst, tot, Lcut, Ucut, res, chgL, chgU,
         choose_u, int_rep, Lpos, Upos, bitmap, seg_cnt, G, zoff, skey, skey_sorted, stmp, sseg, sspos, siota, sperm,
-        ptmp, pkey, prank, pseg, pspos, pint, pjob, probe_pos, dst, boff, sws_s, spl_in, off_in, total;
+        ptmp, pkey, prank, pseg, pspos, pint, pjob, probe_pos, dst, boff, hlo, hmult, jrange, sws_s, spl_in, off_in,
+        total;
 };
 
 BLayout plan_batch(const Tables& T, uint32_t njobs, bool pay, bool sort) {
@@ -645,6 +740,9 @@ BLayout plan_batch(const Tables& T, uint32_t njobs, bool pay, bool sort) {
     L.probe_pos = take(std::max<uint64_t>(T.PP_tot, 1) * 4);
     L.dst = sort ? take(std::max<uint64_t>(T.D_tot, 1) * 8) : 0;
     L.boff = sort ? take(((uint64_t)T.P_tot + 1) * 8) : 0;
+    L.hlo = sort ? take((uint64_t)T.P_tot * 8) : 0;
+    L.hmult = sort ? take((uint64_t)T.P_tot * 8) : 0;
+    L.jrange = sort ? take((uint64_t)njobs * 16) : 0;
     L.sws_s = take(segsort_ws_bytes(C1, njobs));
     L.total = o;
     return L;
@@ -789,6 +887,14 @@ int run_batch(const void* d_keys, const uint32_t* d_payload, int key_type, const
     if (sort) {
         uint64_t* dst = at<uint64_t>(d_work, L.dst);
         uint64_t* boff = at<uint64_t>(d_work, L.boff);
+        uint64_t* hlo = at<uint64_t>(d_work, L.hlo);
+        uint64_t* hmult = at<uint64_t>(d_work, L.hmult);
+        uint64_t* jrange = at<uint64_t>(d_work, L.jrange);
+        // The merge's first split interpolates each bucket's key window
+        // (computed while the locally sorted keys are still in keysA).
+        HSS_LAUNCH(kb_key_range, njobs, 256, 0, st, keysA, jobs, seg_off, jrange);
+        HSS_LAUNCH(kb_bucket_hint, (unsigned)cdivh(T.P_tot, 256), 256, 0, st, T.P_tot, jobs, jseg, Lcut, Ucut, choose_u,
+                   jrange, hlo, hmult);
         if (T.N_tot > 0) {
             HSS_LAUNCH(kb_exchange_dst, dim3((unsigned)cdivh(T.max_p, 32), njobs), 1024, 0, st, jobs, Lpos, offsets, dst,
                        err);
@@ -799,7 +905,7 @@ int run_batch(const void* d_keys, const uint32_t* d_payload, int key_type, const
         HSS_LAUNCH(kb_bucket_off, (unsigned)cdivh((uint64_t)T.P_tot + 1, 256), 256, 0, st, T.P_tot, T.N_tot, jobs, jseg,
                    offsets, boff);
         HSS_BTRY(segsort(keysB, (uint64_t*)d_keys_out, keysA, payB, d_payload_out, payA, T.N_tot, T.P_tot, boff, false, i64,
-                         sws, st, nullptr));
+                         sws, st, nullptr, hlo, hmult));
         if (timing) cudaEventRecord(ev[4], st);
     }
     HSS_BTRY(cudaGetLastError());
