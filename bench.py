@@ -491,7 +491,10 @@ def run_morton_workload(args):
     """Config 3: N = 2^30 64-bit Morton keys of a seeded Plummer sphere (21
     bits per axis) with the particle index as a u32 payload, p = 16384,
     eps = 0.01.  A step is one hss_sort of keys and payload, both resident
-    in HBM (12 GiB in, 12 GiB out: larger than L2, no flush)."""
+    in HBM (12 GiB in, 12 GiB out: larger than L2, no flush).  The same
+    line times the step as two-stage HSS with --groups groups
+    (hss_sort_two_stage, key `two_stage`); --morton-form two times that form
+    alone and makes it the line's value."""
     import numpy as np
     import torch
     from paper_1803_01237_gb300 import hss, inputs
@@ -506,27 +509,28 @@ def run_morton_workload(args):
     pay = torch.from_numpy(ph.view(np.int32)).to(dev)
     del kh, ph
     out, out_p = torch.empty_like(keys), torch.empty_like(pay)
-    for _ in range(args.warmup):
-        hss.sort(keys, P, E, SEED, payload=pay, out=out, out_payload=out_p)
-    torch.cuda.synchronize(dev)
+    single = args.morton_form in ("both", "single")
     clocks = ClockSampler(local)
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    l0 = hss.launch_count()
-    phase = {}
-    ev0.record()
-    for _ in range(args.steps):
-        r = hss.sort(keys, P, E, SEED, payload=pay, out=out, out_payload=out_p, flags=hss.FLAG_TIMING)
-        for k, v in r.ms_phase.items():
-            phase[k] = phase.get(k, 0.0) + v / args.steps
-    ev1.record()
-    torch.cuda.synchronize(dev)
-    clk = clocks.stop()
-    launches = hss.launch_count() - l0
-    ms = ev0.elapsed_time(ev1) / args.steps
-    o = out[:: max(1, N // (1 << 20))].cpu().numpy().view(np.uint64)
+    r, phase, ms, launches, o = None, {}, None, 0, None
+    if single:
+        for _ in range(args.warmup):
+            hss.sort(keys, P, E, SEED, payload=pay, out=out, out_payload=out_p)
+        torch.cuda.synchronize(dev)
+        l0 = hss.launch_count()
+        ev0.record()
+        for _ in range(args.steps):
+            r = hss.sort(keys, P, E, SEED, payload=pay, out=out, out_payload=out_p, flags=hss.FLAG_TIMING)
+            for k, v in r.ms_phase.items():
+                phase[k] = phase.get(k, 0.0) + v / args.steps
+        ev1.record()
+        torch.cuda.synchronize(dev)
+        launches = hss.launch_count() - l0
+        ms = ev0.elapsed_time(ev1) / args.steps
+        o = out[:: max(1, N // (1 << 20))].cpu().numpy().view(np.uint64)
     two = None
-    if args.groups > 1:
+    if args.groups > 1 and args.morton_form in ("both", "two"):
         # The same step as two-stage HSS: the p processors split into
         # `groups` groups first, then every group sorted over p / groups
         # processors (Sec. 5.3; Sec. 7.3 takes r = sqrt(p) = 128 at p = 16384).
@@ -550,16 +554,23 @@ def run_morton_workload(args):
                "stage2_lockstep_rounds": t.lockstep_rounds,
                "stage2_mean_rounds": float(np.mean(t.group_rounds)), "phase_ms": phase2,
                "gpu_launches": hss.launch_count() - l2, "output_sorted": bool(np.all(o2[:-1] <= o2[1:])),
-               "same_output_as_single_stage": bool(np.array_equal(o, o2))}
+               "same_output_as_single_stage": None if o is None else bool(np.array_equal(o, o2))}
+    clk = clocks.stop()
+    if not single:
+        if two is None:
+            raise SystemExit("--morton-form two needs --groups > 1")
+        # the two-stage form alone: it is the line's value
+        ms, launches = two["ms_per_step"], two["gpu_launches"]
     line = {
         "metric": "keys/s (HSS sort with u32 payload)", "value": N / (ms / 1000.0), "unit": "keys/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": f"HSS sort of 2^{args.morton_log2n} Morton keys (Plummer sphere, 21 bits per axis) "
-                               "+ u32 payload, p = 16384, eps = 0.01",
+                               "+ u32 payload, p = 16384, eps = 0.01"
+                               + ("" if single else f", two-stage with {args.groups} groups"),
                    "N": N, "p": P, "eps": E, "l2": "inputs larger than L2; no flush"},
-        "hss": {"rounds": r.rounds, "sample_size": r.sample_size, "phase_ms": phase,
-                "output_sorted": bool(np.all(o[:-1] <= o[1:]))},
+        "hss": None if r is None else {"rounds": r.rounds, "sample_size": r.sample_size, "phase_ms": phase,
+                                       "output_sorted": bool(np.all(o[:-1] <= o[1:]))},
         "gpu_launches": launches, "clocks": clk,
     }
     if two is not None:
@@ -727,6 +738,9 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-low-rate", type=float, default=300.0)
     ap.add_argument("--morton-log2n", type=int, default=30, help="config 3 size (morton workload)")
+    ap.add_argument("--morton-form", default="both", choices=["both", "single", "two"],
+                    help="morton workload: time single-stage HSS, two-stage HSS or both (the value is the single stage "
+                         "unless only the two-stage form runs)")
     ap.add_argument("--groups", type=int, default=128,
                     help="morton workload: also time two-stage HSS with this many groups (0: skip)")
     args = ap.parse_args()

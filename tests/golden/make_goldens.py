@@ -14,13 +14,16 @@ splitter list is kept for element-by-element comparison):
             as payload, p = 16384, eps = 0.01, seed 7.
   batch     4096 int64 jobs, sizes log-uniform in [2^10, 2^22] (plan seed 4),
             p = max(4, n / 2^14), eps = 0.05, job j with seed 1 + j.
+  two_stage the morton workload sorted by two-stage HSS with r = 128 groups
+            (Sec. 5.3; Sec. 7.3's r = sqrt(p)): stage 1's record and group
+            offsets, every group's stage-2 record, the final offsets.
 
 For every case: the round count, per-round sample sizes Z_j, |gamma_j| and
 unresolved splitters (Sec. 4.2.2), tol, status, the offsets chi(0..p), the
 splitter tags (key, seg, spos), and SHA-256 digests of the input and of the
 globally sorted keys and payload (little-endian bytes).
 
-Usage:  python tests/golden/make_goldens.py {scale|morton|batch} [--workers K]
+Usage:  python tests/golden/make_goldens.py {scale|morton|batch|two_stage} [--workers K]
 """
 from __future__ import annotations
 
@@ -42,6 +45,7 @@ if ROOT not in sys.path:
 SCALE = {"N": 1 << 28, "p": 1024, "eps": 0.02, "oversample": 5.0,
          "inputs": {"uniform": 1, "gauss_mix": 2, "zipf": 3}}
 MORTON = {"log2n": 30, "p": 16384, "eps": 0.01, "seed": 7, "oversample": 5.0}
+TWO_STAGE = dict(MORTON, groups=128)
 BATCH = {"njobs": 4096, "plan_seed": 4, "lo_log2": 10, "hi_log2": 22, "zipf_s": 1.1, "zipf_distinct": 1 << 16,
          "eps": 0.05, "seed": 1, "oversample": 5.0}
 
@@ -112,6 +116,43 @@ def make_morton(workers: int):
     _write("morton", {"config": dict(MORTON), "cases": {"plummer": rec}}, arrays)
 
 
+def make_two_stage(workers: int):
+    import oracle
+    from paper_1803_01237_gb300 import inputs
+    cfg = TWO_STAGE
+    N = 1 << cfg["log2n"]
+    keys, pay = inputs.plummer_morton(N, cfg["seed"])
+    t = time.time()
+    res = oracle.hss_two_stage(keys, cfg["p"], cfg["groups"], cfg["eps"], cfg["seed"], oversample=cfg["oversample"],
+                               payload=pay)
+    st1 = res.stage1
+    rec1 = {
+        "rounds": int(st1.rounds), "status": int(st1.status), "tol": int(st1.tol),
+        "sample_size": [int(x) for x in st1.sample_size], "gamma": [int(x) for x in st1.gamma],
+        "unresolved": [int(x) for x in st1.unresolved],
+        "input_sha256": sha(np.ascontiguousarray(keys).view(np.uint64)),
+    }
+    groups = []
+    for g, st in enumerate(res.stage2):
+        spl_key = np.ascontiguousarray(st.splitter_key).view(np.uint64)
+        groups.append({
+            "rounds": int(st.rounds), "status": int(st.status), "tol": int(st.tol),
+            "sample_size": [int(x) for x in st.sample_size], "gamma": [int(x) for x in st.gamma],
+            "unresolved": [int(x) for x in st.unresolved],
+            "splitters_sha256": sha(np.concatenate([spl_key, st.splitter_seg.astype(np.int64).view(np.uint64),
+                                                    st.splitter_spos.astype(np.uint64)]), 16),
+        })
+    recs = {"config": dict(cfg), "stage1": rec1, "groups": groups,
+            "offsets_sha256": sha(res.offsets.astype(np.uint64)),
+            "out_keys_sha256": sha(np.ascontiguousarray(res.out_keys).view(np.uint64)),
+            "out_payload_sha256": sha(res.out_payload.astype(np.uint32)),
+            "oracle_seconds": round(time.time() - t, 1)}
+    arrays = {"offsets": res.offsets.astype(np.uint64),
+              "group_spl_key": np.ascontiguousarray(st1.splitter_key).view(np.uint64),
+              "group_spl_seg": st1.splitter_seg.astype(np.int32), "group_spl_spos": st1.splitter_spos.astype(np.uint32)}
+    _write("two_stage", recs, arrays)
+
+
 def _batch_one(j: int):
     import oracle
     from paper_1803_01237_gb300 import inputs
@@ -152,11 +193,11 @@ def _write(name: str, recs: dict, arrays):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["scale", "morton", "batch"])
+    ap.add_argument("which", choices=["scale", "morton", "batch", "two_stage"])
     ap.add_argument("--workers", type=int, default=max(1, (os.cpu_count() or 2) - 1))
     a = ap.parse_args()
     t = time.time()
-    {"scale": make_scale, "morton": make_morton, "batch": make_batch}[a.which](a.workers)
+    {"scale": make_scale, "morton": make_morton, "batch": make_batch, "two_stage": make_two_stage}[a.which](a.workers)
     print(f"{a.which}: {time.time() - t:.0f} s", flush=True)
 
 

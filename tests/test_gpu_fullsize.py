@@ -18,7 +18,8 @@ Workloads: the bench input set (N = 2^28, p = 1024, eps = 0.02; uniform,
 32-Gaussian mixture, Zipf) with the payload = input index and keys alone (the
 bench's own call); the Plummer/Morton workload (N = 2^30 with payload,
 p = 16384, eps = 0.01); the batched workload (4096 int64 jobs of 2^10..2^22
-keys, one hss_sort_batch call), every job against its record.
+keys, one hss_sort_batch call), every job against its record; the
+Plummer/Morton workload by two-stage HSS with 128 groups.
 """
 import hashlib
 import json
@@ -131,6 +132,49 @@ def test_plummer_morton_vs_oracle_record(hss):
     res = hss.sort(dk, cfg["p"], cfg["eps"], cfg["seed"], payload=dp, oversample=cfg["oversample"])
     torch.cuda.synchronize()
     _compare(res, rec, arr, "", N)
+
+
+@pytest.mark.timeout(1500)
+def test_two_stage_morton_vs_oracle_record(hss):
+    """The Plummer/Morton workload sorted by two-stage HSS with 128 groups
+    (bench.py --workload morton times this call beside the single stage):
+    stage 1's rounds and group cuts, every group's rounds, sample sizes and
+    cut digest, the final offsets and the sorted keys and payload."""
+    rec, arr = _load("two_stage")
+    cfg = rec["config"]
+    N = 1 << cfg["log2n"]
+    keys, payload = inputs.plummer_morton(N, cfg["seed"])
+    assert _sha(keys) == rec["stage1"]["input_sha256"], "the input generator drew different keys on this machine"
+    dk = torch.from_numpy(keys.view(np.int64)).cuda()
+    dp = torch.from_numpy(payload.view(np.int32)).cuda()
+    del keys, payload
+    res = hss.sort_two_stage(dk, cfg["p"], cfg["groups"], cfg["eps"], cfg["seed"], payload=dp,
+                             oversample=cfg["oversample"])
+    torch.cuda.synchronize()
+    s1, r1 = res.stage1, rec["stage1"]
+    assert (s1.status, s1.tol, s1.rounds) == (r1["status"], r1["tol"], r1["rounds"])
+    assert (s1.sample_size, s1.gamma, s1.unresolved) == (r1["sample_size"], r1["gamma"], r1["unresolved"])
+    k, s, sp = hss.cuts_to_numpy(res.group_splitters)
+    assert np.array_equal(k.view(np.uint64), arr["group_spl_key"])
+    assert np.array_equal(s.astype(np.int32), arr["group_spl_seg"])
+    assert np.array_equal(sp.astype(np.uint32), arr["group_spl_spos"])
+    off = res.offsets.cpu().numpy().astype(np.uint64)
+    bad = np.nonzero(off != arr["offsets"])[0]
+    assert bad.size == 0, f"offsets differ at {bad[:8]}"
+    bad = []
+    for g, rg in enumerate(rec["groups"]):
+        k, s, sp = hss.cuts_to_numpy(res.group_splitters_of(g))
+        digest = _sha(np.concatenate([k.view(np.uint64), s.astype(np.int64).view(np.uint64),
+                                      sp.astype(np.uint64)]), 16)
+        got = (res.group_status[g], res.group_tol[g], res.group_rounds[g], res.group_sample_size[g],
+               res.group_gamma[g], res.group_unresolved[g], digest)
+        want = (rg["status"], rg["tol"], rg["rounds"], rg["sample_size"], rg["gamma"], rg["unresolved"],
+                rg["splitters_sha256"])
+        if got != want:
+            bad.append(g)
+    assert not bad, f"groups differing from the oracle: {bad[:8]}"
+    assert _sha(res.keys.cpu().numpy().view(np.uint64)) == rec["out_keys_sha256"], "sorted keys differ"
+    assert _sha(res.payload.cpu().numpy().view(np.uint32)) == rec["out_payload_sha256"], "payload differs"
 
 
 @pytest.mark.timeout(1800)
