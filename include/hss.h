@@ -499,7 +499,14 @@ typedef struct {
      * binary search per key: measured slower than the extra split level it
      * saves, so off by default). */
     uint32_t first_split;
-    uint32_t reserved[3];        /* zero */
+    /* How the split pass writes a tile: 0 stages the tile in shared memory in
+     * digit order and writes each digit's run with consecutive stores; 1
+     * writes every key straight to its slot in its digit's run (no staging,
+     * no second pass over shared memory; the L2 cache assembles the runs),
+     * except in tiles whose sub-buckets' key ranges are gathered for the next
+     * level, which stay staged. */
+    uint32_t split_scatter;
+    uint32_t reserved[2];        /* zero */
 } hss_tuning;
 
 /* Set the tuning (NULL restores the defaults); HSS_ERR_INVALID for a value

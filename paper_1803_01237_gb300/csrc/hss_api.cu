@@ -304,8 +304,10 @@ static int run_path(const void* d_keys, const uint32_t* d_payload, int key_type,
     // processor the locally sorted segment is already the output.
     const bool single = sort && p == 1;
     if (hio) {
-        // Input in chunks of whole processors: chunk g is copied on the copy
-        // stream, and its processors are sorted as soon as it has landed.
+        // Input in chunks of whole processors: every chunk's copy is queued
+        // on the copy stream first (the copy engine then runs without a gap
+        // while the host plans the sorts), and the processors of chunk g are
+        // sorted as soon as it has landed.
         const uint32_t G = hio->groups;
         for (uint32_t g = 0; g < G; ++g) {
             const uint64_t s0 = (uint64_t)g * p / G, s1 = (uint64_t)(g + 1) * p / G;
@@ -317,6 +319,10 @@ static int run_path(const void* d_keys, const uint32_t* d_payload, int key_type,
                                                 cudaMemcpyHostToDevice, hio->cs) != cudaSuccess)
                 return HSS_ERR_CUDA;
             if (cudaEventRecord(hio->ev[g], hio->cs) != cudaSuccess) return HSS_ERR_CUDA;
+        }
+        for (uint32_t g = 0; g < G; ++g) {
+            const uint64_t s0 = (uint64_t)g * p / G, s1 = (uint64_t)(g + 1) * p / G;
+            const uint64_t a = (uint64_t)(((unsigned __int128)s0 * N) / p), b = (uint64_t)(((unsigned __int128)s1 * N) / p);
             if (cudaStreamWaitEvent(st, hio->ev[g], 0) != cudaSuccess) return HSS_ERR_CUDA;
             if (s1 > s0 && segsort((const uint64_t*)d_keys, single ? (uint64_t*)d_keys_out : keysA, keysB, d_payload,
                                    single ? d_payload_out : payA, payB, b - a, s1 - s0, seg_off + s0, i64, single && i64,

@@ -74,6 +74,7 @@ extern "C" int hss_local_sort_noalloc(const void* d_keys, const uint32_t* d_payl
     if (cudaMemsetAsync(err, 0, 256, st) != cudaSuccess) return HSS_ERR_CUDA;
     if (fill_even_offsets(seg_off, N, p, st) != cudaSuccess) return HSS_ERR_CUDA;
     SegSortWs ws = segsort_ws_carve(b + o_ws, N1, p, err);
+    ws.mapped_counts = false;  // allocate nothing, not even the pinned count buffer
     const bool i64 = key_type == HSS_KEY_I64;
     if (segsort((const uint64_t*)d_keys, (uint64_t*)d_keys_out, (uint64_t*)(b + o_keys), d_payload, d_payload_out,
                 pay ? (uint32_t*)(b + o_pay) : nullptr, N, p, seg_off, i64, i64, ws, st, nullptr) != cudaSuccess)

@@ -38,6 +38,7 @@ static std::atomic<uint32_t> g_child_interp{0u};
 static std::atomic<uint32_t> g_child_keys{384u};
 static std::atomic<uint32_t> g_pack_keys{1024u};
 static std::atomic<uint32_t> g_splitters{0u};
+static std::atomic<uint32_t> g_scatter{0u};
 
 int set_tuning(const hss_tuning* t) {
     if (!t) {
@@ -46,13 +47,14 @@ int set_tuning(const hss_tuning* t) {
         g_child_keys = 384u;
         g_pack_keys = 1024u;
         g_splitters = 0u;
+        g_scatter = 0u;
         return HSS_OK;
     }
     const uint32_t cm = t->chip_max_keys ? t->chip_max_keys : (uint32_t)kC1Cap;
     const uint32_t ck = t->child_bucket_keys ? t->child_bucket_keys : 384u;
     const uint32_t pk = t->pack_keys ? t->pack_keys : 1024u;
     if ((cm != (uint32_t)kC1Cap && cm != (uint32_t)kSmallCap) || t->child_interp > 1u || ck < 128u || ck > 4096u ||
-        pk > 4096u || t->first_split > 1u)
+        pk > 4096u || t->first_split > 1u || t->split_scatter > 1u)
         return HSS_ERR_INVALID;
     for (uint32_t r : t->reserved)
         if (r) return HSS_ERR_INVALID;
@@ -61,6 +63,7 @@ int set_tuning(const hss_tuning* t) {
     g_child_keys = ck;
     g_pack_keys = pk;
     g_splitters = t->first_split;
+    g_scatter = t->split_scatter;
     return HSS_OK;
 }
 void get_tuning(hss_tuning* t) {
@@ -70,6 +73,7 @@ void get_tuning(hss_tuning* t) {
     t->child_bucket_keys = g_child_keys;
     t->pack_keys = g_pack_keys;
     t->first_split = g_splitters;
+    t->split_scatter = g_scatter;
 }
 
 // Large segments of a level hold more than kC1Cap keys (keys alone split above
@@ -1418,7 +1422,8 @@ __global__ __launch_bounds__(1024) void k_plan_count(const uint64_t* __restrict_
 }
 
 // Exclusive scan of the chunk totals (one CTA), totals into counters.
-__global__ __launch_bounds__(1024) void k_plan_scan(uint32_t nblk, uint32_t* __restrict__ blk, uint32_t* __restrict__ counters) {
+__global__ __launch_bounds__(1024) void k_plan_scan(uint32_t nblk, uint32_t* __restrict__ blk, uint32_t* __restrict__ counters,
+                                                    volatile uint32_t* host_counts) {
     PlanV carry = {{0, 0, 0, 0, 0}, 0ull};
     for (uint32_t base = 0; base < nblk; base += blockDim.x) {
         const uint32_t i = base + threadIdx.x;
@@ -1440,6 +1445,12 @@ __global__ __launch_bounds__(1024) void k_plan_scan(uint32_t nblk, uint32_t* __r
     if (threadIdx.x == 0) {
         for (int k = 0; k < 5; ++k) counters[16 + k] = carry.c[k];
         *(unsigned long long*)(counters + 22) = carry.keys;
+        if (host_counts) {  // the same eight words for the host, in mapped pinned memory
+            for (int k = 0; k < 5; ++k) host_counts[k] = carry.c[k];
+            host_counts[5] = 0;
+            host_counts[6] = (uint32_t)carry.keys;
+            host_counts[7] = (uint32_t)(carry.keys >> 32);
+        }
         counters[24] = 0;  // fallback list of this level's on-chip sorts
         counters[25] = 0;  // segments the register kernels leave to the shared-memory kernel
         counters[26] = 0;  // ... and the keys-only kernels, per size class
@@ -1834,6 +1845,7 @@ struct SplitArgs {
     uint32_t* err;
     uint64_t flip_in;
     uint64_t flip_out;
+    uint32_t scatter;  // 1: tiles that gather no key ranges write each key straight to its run
 };
 
 template <bool PAY, bool SPL>
@@ -1913,6 +1925,26 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
             return (wbase + i * 32 < count) ? (dpk[i >> 2] >> (8 * (i & 3))) & 255u : (uint32_t)kRadix;
         };
         block_rank<kOsWarps, kOsItems>(digit_of, count, rank, s_hist, s_total, s_start, s_warp, NoOp());
+        if (A.scatter && !gather) {  // uniform per CTA
+            // The stable tile rank less the digit's tile start is the key's
+            // place in its digit's run: write it there.
+            if (tid < kRadix)
+                s_gbase[tid] = seg_base + (uint64_t)A.tile_off[(uint64_t)t * kRadix + tid] - (uint64_t)s_start[tid];
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < kOsItems; ++i) {
+                if (wbase + i * 32 < count) {
+                    const uint64_t dst = s_gbase[(dpk[i >> 2] >> (8 * (i & 3))) & 255u] + rank[i];
+                    if (dst - seg_base >= seg_n) {  // never taken when the digit offsets are consistent
+                        atomicOr(A.err, kDevErrBounds);
+                        continue;
+                    }
+                    kout[dst] = key[i] ^ flip_out;
+                    pout[dst] = pay[i];
+                }
+            }
+            return;
+        }
 #pragma unroll
         for (int i = 0; i < kOsItems; ++i) {
             if (wbase + i * 32 < count) {
@@ -1929,8 +1961,43 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
         // holds the digit and, from bit 8, the key's slot.  (Aggregating the
         // lanes of a warp that share a digit with a match instruction costs
         // more than it saves, even on heavily duplicated keys.)
-        for (int d = tid; d < kRadix; d += kOsThreads) s_total[d] = 0;
+        const bool direct = A.scatter && !gather;  // uniform per CTA
+        for (int d = tid; d < kRadix; d += kOsThreads) {
+            s_total[d] = 0;
+            // direct: digit d's keys of this tile start here in the output
+            if (direct) s_gbase[d] = seg_base + (uint64_t)A.tile_off[(uint64_t)t * kRadix + d];
+        }
         __syncthreads();
+        if (direct) {
+            // Each key goes straight to the slot its digit's counter hands
+            // out; nothing is staged, so no further barrier.
+            const bool skew = A.tile_skew[t] != 0;
+            const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+            for (int i = 0; i < kOsItems; ++i) {
+                const uint32_t d = wbase + i * 32 < count ? dig(key[i]) : (uint32_t)kRadix;
+                uint32_t slot = 0;
+                if (skew) {
+                    const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+                    const uint32_t eq = __ballot_sync(0xffffffffu, d == d0);
+                    uint32_t b0 = 0;
+                    if (lane == 0 && d0 < (uint32_t)kRadix) b0 = atomicAdd(&s_total[d0], (uint32_t)__popc(eq));
+                    b0 = __shfl_sync(0xffffffffu, b0, 0);
+                    if (d < (uint32_t)kRadix) slot = d == d0 ? b0 + (uint32_t)__popc(eq & lt_mask) : atomicAdd(&s_total[d], 1u);
+                } else if (d < (uint32_t)kRadix) {
+                    slot = atomicAdd(&s_total[d], 1u);
+                }
+                if (d < (uint32_t)kRadix) {
+                    const uint64_t dst = s_gbase[d] + slot;
+                    if (dst - seg_base >= seg_n) {  // never taken when the digit offsets are consistent
+                        atomicOr(A.err, kDevErrBounds);
+                        continue;
+                    }
+                    kout[dst] = key[i] ^ flip_out;
+                }
+            }
+            return;
+        }
         if (A.tile_skew[t]) {  // uniform per CTA: see tile_skew_flag
             const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
@@ -2154,6 +2221,36 @@ struct Level {
     const uint64_t* hint_hi = nullptr;  // largest key of each segment, when known
 };
 
+// This thread's mapped pinned buffer for the planning counts (allocated once
+// per thread; null if the allocation fails, and then the counts are copied).
+struct MappedCounts {
+    volatile uint32_t* host = nullptr;
+    uint32_t* dev = nullptr;
+    bool tried = false;
+};
+static thread_local MappedCounts t_counts;
+
+static void mapped_counts(volatile uint32_t** host, uint32_t** dev) {
+    if (!t_counts.tried) {
+        t_counts.tried = true;
+        void* p = nullptr;
+        if (cudaHostAlloc(&p, 64, cudaHostAllocMapped | cudaHostAllocPortable) == cudaSuccess) {
+            void* dp = nullptr;
+            if (cudaHostGetDevicePointer(&dp, p, 0) == cudaSuccess) {
+                t_counts.host = (volatile uint32_t*)p;
+                t_counts.dev = (uint32_t*)dp;
+            } else {
+                (void)cudaGetLastError();
+                cudaFreeHost(p);
+            }
+        } else {
+            (void)cudaGetLastError();
+        }
+    }
+    *host = t_counts.host;
+    *dev = t_counts.dev;
+}
+
 template <bool PAY>
 static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, const uint32_t* psrc, uint32_t* pdst,
                              uint32_t* ptmp, uint64_t N, uint64_t nseg, const uint64_t* d_seg_off, bool flip_in,
@@ -2166,6 +2263,10 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
     const uint32_t child_keys = g_child_keys.load();
     const uint32_t pack_keys = g_pack_keys.load();
     const bool use_splitters = g_splitters.load() != 0u;
+    const uint32_t scatter = g_scatter.load();
+    volatile uint32_t* mapped = nullptr;  // host view of the planning counts
+    uint32_t* mapped_dev = nullptr;        // the kernel's view
+    if (ws.mapped_counts) mapped_counts(&mapped, &mapped_dev);
     cudaError_t e;
     Level L{src, psrc, d_seg_off, d_seg_off + 1, nseg, flip_in ? kSignBit : 0ull, hint_lo, hint_mult, 0};
     if (N <= (uint64_t)kSmallCap) {
@@ -2200,12 +2301,15 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
         // rather than sorted by the largest class (tuning.chip_max_keys).
         const uint32_t chip_max = tune_chip_max;
         HSS_LAUNCH(k_plan_count, nblk, 1024, 0, st, L.seg_lo, L.seg_hi, L.nseg, ws.blk, chip_max);
-        HSS_LAUNCH(k_plan_scan, 1, 1024, 0, st, nblk, ws.blk, ws.counters);
+        HSS_LAUNCH(k_plan_scan, 1, 1024, 0, st, nblk, ws.blk, ws.counters, mapped_dev);
         HSS_LAUNCH(k_plan_write, nblk, 1024, 0, st, L.seg_lo, L.seg_hi, L.nseg, ws.blk, ws.counters, ws.tile_start,
                    ws.large_id, ws.large_seg, ws.list[0], ws.list[1], ws.list[2], ws.err, ws.tile_seg, chip_max);
         uint32_t hc[8];
-        if ((e = cudaMemcpyAsync(hc, ws.counters + 16, sizeof(hc), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+        if (!mapped && (e = cudaMemcpyAsync(hc, ws.counters + 16, sizeof(hc), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return e;
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+        if (mapped)
+            for (int k = 0; k < 8; ++k) hc[k] = mapped[k];
         const uint32_t n_large = hc[3], tiles = hc[4];
         const uint64_t keys_large = (uint64_t)hc[6] | ((uint64_t)hc[7] << 32);
         // Segments of this level that fit on chip: straight to the output.
@@ -2309,6 +2413,7 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
         A.direct = ws.direct;
         A.large_mask = ws.large_mask; A.any_large = ws.any_large; A.cmin = ws.cmin[buf]; A.cmax = ws.cmax[buf];
         A.err = ws.err;
+        A.scatter = scatter;
         A.flip_in = L.flip_in; A.flip_out = fout;
         const size_t smem = (size_t)kOsTile * 9 + (PAY ? (size_t)kOsTile * 4 : 0);
         // all of L1 as shared memory: the CTAs per SM are limited by their tiles

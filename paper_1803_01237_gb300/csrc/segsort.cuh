@@ -72,6 +72,11 @@ struct SegSortWs {
     uint32_t* slow_keys[3];  // [max_list] per size class: segments the keys-only kernel leaves (counters[26..28])
     uint32_t* blk;         // [8 * (max_list / 1024 + 2)] per-chunk counts of the planning scan
     uint32_t* err;         // device error word (kDevErr*)
+    // false: the planning counts come back by a copy into pageable host
+    // memory (nothing allocated: hss_local_sort_noalloc); true: a kernel
+    // writes them into this thread's mapped pinned buffer, which needs no copy
+    // engine (a count read then never waits behind the caller's bulk copies).
+    bool mapped_counts = true;
 };
 
 // Bytes of scratch a segmented sort of N keys in nseg segments needs.

@@ -464,15 +464,17 @@ def sample_words(seed: int, seg: int, rnd: int, spos0: int, count: int, device="
 class Tuning(ctypes.Structure):
     _fields_ = [("chip_max_keys", ctypes.c_uint32), ("child_interp", ctypes.c_uint32),
                 ("child_bucket_keys", ctypes.c_uint32), ("pack_keys", ctypes.c_uint32),
-                ("first_split", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
+                ("first_split", ctypes.c_uint32), ("split_scatter", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 2)]
 
 
 def set_tuning(chip_max_keys: int = 0, child_interp: int = 0, child_bucket_keys: int = 0, pack_keys: int = 0,
-               first_split: int = 0):
+               first_split: int = 0, split_scatter: int = 0):
     """hss_set_tuning: process-wide choices of the segmented sort (results unchanged)."""
     lib = load()
     t = Tuning(chip_max_keys=int(chip_max_keys), child_interp=int(child_interp),
-               child_bucket_keys=int(child_bucket_keys), pack_keys=int(pack_keys), first_split=int(first_split))
+               child_bucket_keys=int(child_bucket_keys), pack_keys=int(pack_keys), first_split=int(first_split),
+               split_scatter=int(split_scatter))
     _check(lib.hss_set_tuning(ctypes.byref(t)), "hss_set_tuning")
 
 
@@ -484,7 +486,8 @@ def get_tuning() -> dict:
     t = Tuning()
     _check(load().hss_get_tuning(ctypes.byref(t)), "hss_get_tuning")
     return {"chip_max_keys": t.chip_max_keys, "child_interp": t.child_interp,
-            "child_bucket_keys": t.child_bucket_keys, "pack_keys": t.pack_keys, "first_split": t.first_split}
+            "child_bucket_keys": t.child_bucket_keys, "pack_keys": t.pack_keys, "first_split": t.first_split,
+            "split_scatter": t.split_scatter}
 
 
 def launch_count() -> int:

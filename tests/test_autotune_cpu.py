@@ -11,11 +11,12 @@ from paper_1803_01237_gb300 import hss
 def test_set_tuning_validates_and_round_trips():
     hss.reset_tuning()
     assert hss.get_tuning() == {"chip_max_keys": 4096, "child_interp": 0, "child_bucket_keys": 384, "pack_keys": 1024,
-                                "first_split": 0}
-    hss.set_tuning(14336, 1, 768, 2048, 1)
+                                "first_split": 0, "split_scatter": 0}
+    hss.set_tuning(14336, 1, 768, 2048, 1, 1)
     assert hss.get_tuning() == {"chip_max_keys": 14336, "child_interp": 1, "child_bucket_keys": 768, "pack_keys": 2048,
-                                "first_split": 1}
-    for bad in ((5000, 0, 0), (4096, 2, 0), (4096, 1, 64), (4096, 1, 5000), (4096, 0, 0, 5000), (4096, 0, 0, 0, 2)):
+                                "first_split": 1, "split_scatter": 1}
+    for bad in ((5000, 0, 0), (4096, 2, 0), (4096, 1, 64), (4096, 1, 5000), (4096, 0, 0, 5000), (4096, 0, 0, 0, 2),
+                (4096, 0, 0, 0, 0, 2)):
         with pytest.raises(hss.HSSError):
             hss.set_tuning(*bad)
     assert hss.get_tuning()["chip_max_keys"] == 14336  # a refused call changes nothing

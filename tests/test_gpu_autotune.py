@@ -38,7 +38,8 @@ def _case(gen):
 @pytest.mark.parametrize("gen", list(_GENS))
 @pytest.mark.parametrize("tiling", [(4096, 0, 384), (14336, 0, 384), (4096, 1, 384), (4096, 1, 128), (14336, 1, 4096),
                                     (4096, 0, 384, 1), (4096, 0, 384, 4096), (14336, 0, 384, 4096),
-                                    (4096, 0, 384, 0, 1), (14336, 1, 384, 1, 1)])
+                                    (4096, 0, 384, 0, 1), (14336, 1, 384, 1, 1), (4096, 0, 384, 0, 0, 1),
+                                    (14336, 1, 384, 0, 0, 1), (4096, 0, 384, 0, 1, 1)])
 def test_tilings_give_the_oracle_result(hss, gen, tiling):
     p, eps, seed = 16, 0.02, 3
     keys, ref = _case(gen)
@@ -50,6 +51,26 @@ def test_tilings_give_the_oracle_result(hss, gen, tiling):
         hss.reset_tuning()
     assert np.array_equal(res.offsets.cpu().numpy().astype(np.uint64), ref.offsets)
     assert np.array_equal(res.keys.cpu().numpy().view(np.uint64), ref.out_keys)
+
+
+@pytest.mark.parametrize("gen", ["uniform", "zipf", "nested"])
+@pytest.mark.parametrize("split_scatter", [0, 1])
+def test_split_scatter_keeps_the_payload_stable(hss, gen, split_scatter):
+    """Both ways of writing a split tile give the oracle's stable sort with
+    the payload in tow (equal keys keep input order)."""
+    N, p, eps, seed = 1 << 20, 16, 0.02, 5
+    keys = _GENS[gen](N, 9)
+    pay = np.arange(N, dtype=np.uint32)
+    ref = oracle.hss(keys, p, eps, seed, payload=pay)
+    hss.set_tuning(split_scatter=split_scatter)
+    try:
+        res = hss.sort(torch.from_numpy(keys.view(np.int64)).cuda(), p, eps, seed,
+                       payload=torch.from_numpy(pay.view(np.int32)).cuda())
+        torch.cuda.synchronize()
+    finally:
+        hss.reset_tuning()
+    assert np.array_equal(res.keys.cpu().numpy().view(np.uint64), ref.out_keys)
+    assert np.array_equal(res.payload.cpu().numpy().view(np.uint32), ref.out_payload)
 
 
 def test_tuner_picks_and_caches_a_choice(hss, tmp_path):
