@@ -855,8 +855,7 @@ int run_batch(const void* d_keys, const uint32_t* d_payload, int key_type, const
     uint32_t round = 0;
     for (;;) {
         HSS_BTRY(cudaGetLastError());
-        HSS_BTRY(cudaMemcpyAsync(&h, tot, sizeof(h), cudaMemcpyDeviceToHost, st));
-        HSS_BTRY(cudaStreamSynchronize(st));
+        HSS_BTRY(read_small(&h, tot, sizeof(h), st));
         if (h.active == 0) break;
         ++round;
         const uint64_t Zc = h.Zc;

@@ -68,6 +68,49 @@ int resident_ctas(const void* func, int threads, size_t dyn_smem) {
     return n;
 }
 
+__global__ void k_copy_words(const uint32_t* __restrict__ src, volatile uint32_t* dst, uint32_t n) {
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+static constexpr size_t kSmallRead = 8192;
+struct SmallReadBuf {
+    volatile uint32_t* host = nullptr;
+    uint32_t* dev = nullptr;
+    bool tried = false;
+};
+static thread_local SmallReadBuf t_small;
+
+cudaError_t read_small(void* h_dst, const void* d_src, size_t bytes, cudaStream_t st) {
+    if (!t_small.tried) {
+        t_small.tried = true;
+        void* p = nullptr;
+        if (cudaHostAlloc(&p, kSmallRead, cudaHostAllocMapped | cudaHostAllocPortable) == cudaSuccess) {
+            void* dp = nullptr;
+            if (cudaHostGetDevicePointer(&dp, p, 0) == cudaSuccess) {
+                t_small.host = (volatile uint32_t*)p;
+                t_small.dev = (uint32_t*)dp;
+            } else {
+                (void)cudaGetLastError();
+                cudaFreeHost(p);
+            }
+        } else {
+            (void)cudaGetLastError();
+        }
+    }
+    cudaError_t e;
+    if (!t_small.host || bytes > kSmallRead || bytes % 4 != 0 || ((uintptr_t)d_src & 3u) != 0) {
+        if ((e = cudaMemcpyAsync(h_dst, d_src, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+        return cudaStreamSynchronize(st);
+    }
+    const uint32_t n = (uint32_t)(bytes / 4);
+    HSS_LAUNCH(k_copy_words, 1, 256, 0, st, (const uint32_t*)d_src, t_small.dev, n);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    uint32_t* out = (uint32_t*)h_dst;
+    for (uint32_t i = 0; i < n; ++i) out[i] = t_small.host[i];
+    return cudaSuccess;
+}
+
 int device_sm_count() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 148;
@@ -218,8 +261,7 @@ struct PhaseTimer {
 
 static int read_dev_err(uint32_t* d_err, cudaStream_t st) {
     uint32_t h = 0;
-    if (cudaMemcpyAsync(&h, d_err, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return HSS_ERR_CUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return HSS_ERR_CUDA;
+    if (read_small(&h, d_err, sizeof(h), st) != cudaSuccess) return HSS_ERR_CUDA;
     if (h & kDevErrTimeout) return HSS_ERR_TIMEOUT;
     if (h & kDevErrSize) return HSS_ERR_INVALID;
     if (h & kDevErrBounds) return HSS_ERR_CUDA;

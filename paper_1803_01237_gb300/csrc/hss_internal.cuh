@@ -130,6 +130,13 @@ int device_sm_count();
 // memory (the occupancy calculator, cached per device; at least 1).  Call
 // after ensure_func_attrs so that the shared-memory settings count.
 int resident_ctas(const void* func, int threads, size_t dyn_smem);
+// Read `bytes` (a multiple of 4, d_src 4-byte aligned) of device memory that
+// the host needs for a decision (round state, status words), after the work
+// queued on `st`; synchronises `st`.  Up to 8 KiB go through this thread's
+// mapped pinned buffer, written by a copy kernel: no copy engine is involved,
+// so the read never waits behind bulk copies queued on other streams.  Larger
+// reads (or no pinned buffer) take cudaMemcpyAsync.
+cudaError_t read_small(void* h_dst, const void* d_src, size_t bytes, cudaStream_t st);
 
 }  // namespace hss
 

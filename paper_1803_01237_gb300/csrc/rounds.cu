@@ -963,8 +963,7 @@ uint32_t device_round_kernels() { return g_body_kernels; }
 
 int read_round_result(const RoundWs& ws, RoundResult* out, cudaStream_t st) {
     RoundCtl h;
-    if (cudaMemcpyAsync(&h, ws.ctl, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return HSS_ERR_CUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return HSS_ERR_CUDA;
+    if (read_small(&h, ws.ctl, sizeof(h), st) != cudaSuccess) return HSS_ERR_CUDA;
     out->rounds = h.round;
     out->status = h.status;
     for (uint32_t j = 0; j < h.round && j < HSS_MAX_ROUNDS; ++j) {
@@ -1076,8 +1075,7 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
     enqueue_sampling(ws, d_seg_off, N, p, S, seed, 1, st, per_interval);
     HSS_TRY(cudaGetLastError());
     RoundCtl h;
-    HSS_TRY(cudaMemcpyAsync(&h, ws.ctl, sizeof(h), cudaMemcpyDeviceToHost, st));
-    HSS_TRY(cudaStreamSynchronize(st));
+    HSS_TRY(read_small(&h, ws.ctl, sizeof(h), st));
     out->unresolved[0] = h.unresolved;
     uint32_t j = 0;
     int status = HSS_OK;
@@ -1104,8 +1102,7 @@ int run_rounds(const uint64_t* skeys, const uint64_t* d_seg_off, uint64_t N, uin
         intervals(j + 1);
         enqueue_sampling(ws, d_seg_off, N, p, S, seed, j + 1, st, per_interval);
         HSS_TRY(cudaGetLastError());
-        HSS_TRY(cudaMemcpyAsync(&h, ws.ctl, sizeof(h), cudaMemcpyDeviceToHost, st));
-        HSS_TRY(cudaStreamSynchronize(st));
+        HSS_TRY(read_small(&h, ws.ctl, sizeof(h), st));
         out->unresolved[j] = h.unresolved;
     }
     out->rounds = j;
