@@ -340,6 +340,21 @@ int hss_partition_batch(const void* d_keys, int key_type, const uint64_t* h_size
                         const hss_params* prm, hss_cut* d_splitters, uint64_t* d_offsets, void* d_work,
                         size_t work_bytes, hss_batch_stats* h_stats, hss_job_stats* h_job_stats, void* stream);
 
+/* The same calls with a seed per job: job j uses h_seeds[j] (host array of
+ * njobs entries) instead of prm->seed + j, so each job equals hss_sort
+ * (hss_partition) alone with its own seed -- a server batching independent
+ * requests keeps every request's result.  h_seeds = NULL is the plain form.
+ * Workspace: hss_batch_workspace_bytes (seeds do not change it). */
+int hss_sort_batch_seeded(const void* d_keys, const uint32_t* d_payload, int key_type, const uint64_t* h_sizes,
+                          const uint32_t* h_p, const uint64_t* h_seeds, uint32_t njobs, const hss_params* prm,
+                          void* d_keys_out, uint32_t* d_payload_out, hss_cut* d_splitters, uint64_t* d_offsets,
+                          void* d_work, size_t work_bytes, hss_batch_stats* h_stats, hss_job_stats* h_job_stats,
+                          void* stream);
+int hss_partition_batch_seeded(const void* d_keys, int key_type, const uint64_t* h_sizes, const uint32_t* h_p,
+                               const uint64_t* h_seeds, uint32_t njobs, const hss_params* prm, hss_cut* d_splitters,
+                               uint64_t* d_offsets, void* d_work, size_t work_bytes, hss_batch_stats* h_stats,
+                               hss_job_stats* h_job_stats, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Two-stage HSS (Sec. 5.3, multi-stage with two stages; Sec. 7.3 uses
  * r = sqrt(p) groups and the same eps in both stages).

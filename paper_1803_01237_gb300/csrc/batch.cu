@@ -667,7 +667,8 @@ struct Tables {
     uint32_t P_tot = 0, S_tot = 0, max_p = 0, max_seg = 0;
 };
 
-int build_tables(const uint64_t* sizes, const uint32_t* ps, uint32_t njobs, const hss_params* prm, Tables& T) {
+int build_tables(const uint64_t* sizes, const uint32_t* ps, uint32_t njobs, const hss_params* prm, Tables& T,
+                 const uint64_t* seeds = nullptr) {
     T.jobs.resize(njobs);
     uint64_t koff = 0, lb = 0, db = 0, cb = 0, pp = 0, ob = 0;
     uint32_t sb = 0, ib = 0;
@@ -684,7 +685,7 @@ int build_tables(const uint64_t* sizes, const uint32_t* ps, uint32_t njobs, cons
         J.cap = sample_capacity(n, p, prm->oversample);
         J.ppbase = pp;
         J.tol = (uint64_t)std::floor(((double)n * prm->eps) / (2.0 * (double)p));
-        J.seed = prm->seed + j;
+        J.seed = seeds ? seeds[j] : prm->seed + j;
         J.obase = ob;
         for (uint32_t s = 0; s < p; ++s) {
             T.seg_off.push_back(koff + (uint64_t)(((unsigned __int128)s * n) / p));
@@ -765,7 +766,7 @@ int run_batch(const void* d_keys, const uint32_t* d_payload, int key_type, const
     if (prm->schedule != HSS_SCHEDULE_PROPORTIONAL) return HSS_ERR_INVALID;
     if (key_type != HSS_KEY_U64 && key_type != HSS_KEY_I64) return HSS_ERR_INVALID;
     Tables T;
-    if (build_tables(h_sizes, h_p, njobs, prm, T) != HSS_OK) return HSS_ERR_INVALID;
+    if (build_tables(h_sizes, h_p, njobs, prm, T, ex.seeds) != HSS_OK) return HSS_ERR_INVALID;
     if ((T.N_tot > 0 && !d_keys) || !d_offsets || (T.S_tot > 0 && !d_splitters) || !d_work) return HSS_ERR_INVALID;
     const bool pay = sort && d_payload != nullptr;
     if (sort && ((d_payload == nullptr) != (d_payload_out == nullptr))) return HSS_ERR_INVALID;
@@ -988,6 +989,27 @@ int hss_sort_batch(const void* d_keys, const uint32_t* d_payload, int key_type, 
                    hss_job_stats* h_job_stats, void* stream) {
     return run_batch(d_keys, d_payload, key_type, h_sizes, h_p, njobs, prm, d_keys_out, d_payload_out, d_splitters,
                      d_offsets, d_work, work_bytes, h_stats, h_job_stats, (cudaStream_t)stream, true, BatchExtra{});
+}
+
+int hss_sort_batch_seeded(const void* d_keys, const uint32_t* d_payload, int key_type, const uint64_t* h_sizes,
+                          const uint32_t* h_p, const uint64_t* h_seeds, uint32_t njobs, const hss_params* prm,
+                          void* d_keys_out, uint32_t* d_payload_out, hss_cut* d_splitters, uint64_t* d_offsets,
+                          void* d_work, size_t work_bytes, hss_batch_stats* h_stats, hss_job_stats* h_job_stats,
+                          void* stream) {
+    BatchExtra ex;
+    ex.seeds = h_seeds;
+    return run_batch(d_keys, d_payload, key_type, h_sizes, h_p, njobs, prm, d_keys_out, d_payload_out, d_splitters,
+                     d_offsets, d_work, work_bytes, h_stats, h_job_stats, (cudaStream_t)stream, true, ex);
+}
+
+int hss_partition_batch_seeded(const void* d_keys, int key_type, const uint64_t* h_sizes, const uint32_t* h_p,
+                               const uint64_t* h_seeds, uint32_t njobs, const hss_params* prm, hss_cut* d_splitters,
+                               uint64_t* d_offsets, void* d_work, size_t work_bytes, hss_batch_stats* h_stats,
+                               hss_job_stats* h_job_stats, void* stream) {
+    BatchExtra ex;
+    ex.seeds = h_seeds;
+    return run_batch(d_keys, nullptr, key_type, h_sizes, h_p, njobs, prm, nullptr, nullptr, d_splitters, d_offsets,
+                     d_work, work_bytes, h_stats, h_job_stats, (cudaStream_t)stream, false, ex);
 }
 
 int hss_partition_batch(const void* d_keys, int key_type, const uint64_t* h_sizes, const uint32_t* h_p, uint32_t njobs,

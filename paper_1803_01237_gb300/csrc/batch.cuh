@@ -15,6 +15,8 @@ struct BatchExtra {
     // as for segsort().
     const uint64_t* hint_lo = nullptr;
     const uint64_t* hint_mult = nullptr;
+    // Host array of each job's Philox key (null: prm->seed + j).
+    const uint64_t* seeds = nullptr;
 };
 
 // hss_sort_batch (sort) / hss_partition_batch (!sort) with options.

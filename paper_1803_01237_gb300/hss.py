@@ -640,7 +640,7 @@ class BatchResult:
 
 
 def _batch(keys, sizes, ps, eps, seed, payload, oversample, max_rounds, key_type, flags, sort, out, out_payload,
-           stream):
+           stream, seeds=None, ws=None):
     lib = load()
     if not hasattr(lib, "_batch_bound"):
         P, U64, U32, I32, SZ = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_size_t
@@ -652,6 +652,12 @@ def _batch(keys, sizes, ps, eps, seed, payload, oversample, max_rounds, key_type
         lib.hss_partition_batch.argtypes = [P, I32, P, P, U32, ctypes.POINTER(Params), P, P, P, SZ,
                                             ctypes.POINTER(BatchStats), P, P]
         lib.hss_partition_batch.restype = I32
+        lib.hss_sort_batch_seeded.argtypes = [P, P, I32, P, P, P, U32, ctypes.POINTER(Params), P, P, P, P, P, SZ,
+                                              ctypes.POINTER(BatchStats), P, P]
+        lib.hss_sort_batch_seeded.restype = I32
+        lib.hss_partition_batch_seeded.argtypes = [P, I32, P, P, P, U32, ctypes.POINTER(Params), P, P, P, SZ,
+                                                   ctypes.POINTER(BatchStats), P, P]
+        lib.hss_partition_batch_seeded.restype = I32
         lib._batch_bound = True
     keys = _as_key_tensor(keys)
     sizes = np.ascontiguousarray(np.asarray(sizes, dtype=np.uint64))
@@ -664,7 +670,13 @@ def _batch(keys, sizes, ps, eps, seed, payload, oversample, max_rounds, key_type
                                            int(payload is not None), int(sort)))
     if nb == 0:
         raise HSSError(ERR_INVALID, "hss_batch_workspace_bytes")
-    ws = workspace(nb, keys.device)
+    if ws is None or ws.numel() < nb:
+        ws = workspace(nb, keys.device)
+    sd = None
+    if seeds is not None:
+        sd = np.ascontiguousarray(np.asarray([int(x) & ((1 << 64) - 1) for x in seeds], dtype=np.uint64))
+        if sd.shape[0] != nj:
+            raise ValueError("one seed per job")
     S_tot = int((ps.astype(np.int64) - 1).sum())
     O_tot = int((ps.astype(np.int64) + 1).sum())
     spl = torch.empty((max(S_tot, 1), 2), dtype=torch.int64, device=keys.device)
@@ -676,13 +688,13 @@ def _batch(keys, sizes, ps, eps, seed, payload, oversample, max_rounds, key_type
             out = torch.empty_like(keys)
         if payload is not None and out_payload is None:
             out_payload = torch.empty_like(payload)
-        rc = lib.hss_sort_batch(_ptr(keys), _ptr(payload), KEY_TYPES[key_type], _ptr(sizes), _ptr(ps), nj,
-                                ctypes.byref(prm), _ptr(out), _ptr(out_payload), _ptr(spl), _ptr(off), _ptr(ws),
-                                ws.numel(), ctypes.byref(st), js, _stream(stream))
+        rc = lib.hss_sort_batch_seeded(_ptr(keys), _ptr(payload), KEY_TYPES[key_type], _ptr(sizes), _ptr(ps),
+                                       _ptr(sd), nj, ctypes.byref(prm), _ptr(out), _ptr(out_payload), _ptr(spl),
+                                       _ptr(off), _ptr(ws), ws.numel(), ctypes.byref(st), js, _stream(stream))
     else:
-        rc = lib.hss_partition_batch(_ptr(keys), KEY_TYPES[key_type], _ptr(sizes), _ptr(ps), nj, ctypes.byref(prm),
-                                     _ptr(spl), _ptr(off), _ptr(ws), ws.numel(), ctypes.byref(st), js,
-                                     _stream(stream))
+        rc = lib.hss_partition_batch_seeded(_ptr(keys), KEY_TYPES[key_type], _ptr(sizes), _ptr(ps), _ptr(sd), nj,
+                                            ctypes.byref(prm), _ptr(spl), _ptr(off), _ptr(ws), ws.numel(),
+                                            ctypes.byref(st), js, _stream(stream))
     if rc in (ERR_INVALID, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT):
         raise HSSError(rc, "hss_sort_batch" if sort else "hss_partition_batch")
     return BatchResult(
@@ -698,18 +710,36 @@ def _batch(keys, sizes, ps, eps, seed, payload, oversample, max_rounds, key_type
         ms_phase={PHASES[i]: float(st.ms_phase[i]) for i in range(NUM_PHASES)})
 
 
+def batch_workspace_bytes(sizes, ps, eps: float, sort: bool = True, payload: bool = False, key_type: str = "u64",
+                          oversample: float = 5.0) -> int:
+    """hss_batch_workspace_bytes of a job list (0 when the list is refused)."""
+    lib = load()
+    P, U32, I32, SZ = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int, ctypes.c_size_t
+    lib.hss_batch_workspace_bytes.argtypes = [P, P, U32, ctypes.POINTER(Params), I32, I32, I32]
+    lib.hss_batch_workspace_bytes.restype = SZ
+    sz = np.ascontiguousarray(np.asarray(sizes, dtype=np.uint64))
+    pp = np.ascontiguousarray(np.asarray(ps, dtype=np.uint32))
+    prm = _params(1, eps, 0, oversample, 0, 0)
+    return int(lib.hss_batch_workspace_bytes(_ptr(sz), _ptr(pp), int(sz.shape[0]), ctypes.byref(prm),
+                                             KEY_TYPES[key_type], int(payload), int(sort)))
+
+
 def sort_batch(keys, sizes, ps, eps: float, seed: int, payload=None, oversample: float = 5.0, max_rounds: int = 0,
-               key_type: str = "u64", flags: int = 0, out=None, out_payload=None, stream=None) -> BatchResult:
+               key_type: str = "u64", flags: int = 0, out=None, out_payload=None, stream=None,
+               seeds=None) -> BatchResult:
     """hss_sort of every job of a batch (job j: the next sizes[j] keys, ps[j]
-    processors, seed + j), all jobs together."""
+    processors, seed + j, or seeds[j] when seeds is given), all jobs
+    together."""
     return _batch(keys, sizes, ps, eps, seed, payload, oversample, max_rounds, key_type, flags, True, out,
-                  out_payload, stream)
+                  out_payload, stream, seeds)
 
 
 def partition_batch(keys, sizes, ps, eps: float, seed: int, oversample: float = 5.0, max_rounds: int = 0,
-                    key_type: str = "u64", flags: int = 0, stream=None) -> BatchResult:
-    """hss_partition of every job of a batch, all jobs together."""
-    return _batch(keys, sizes, ps, eps, seed, None, oversample, max_rounds, key_type, flags, False, None, None, stream)
+                    key_type: str = "u64", flags: int = 0, stream=None, seeds=None, ws=None) -> BatchResult:
+    """hss_partition of every job of a batch, all jobs together (seeds as
+    for sort_batch; ws: a workspace to use when large enough)."""
+    return _batch(keys, sizes, ps, eps, seed, None, oversample, max_rounds, key_type, flags, False, None, None, stream,
+                  seeds, ws)
 
 
 # ---------------------------------------------------------------------------

@@ -146,3 +146,22 @@ def test_many_small_jobs(hss):
         o += n
     for j in (0, 17, 123, 299):  # full parity on a sample of the jobs
         _check_job(res, j, jobs_l[j], ps[j], eps, seed + j, key_type="i64")
+
+
+def test_batch_seeds_give_each_job_its_own_call(hss):
+    """hss_partition_batch_seeded: job j with seed s_j equals hss_partition
+    alone with s_j."""
+    sizes = [5000, 70000, 1, 33333]
+    ps = [4, 64, 1, 16]
+    seeds = [91, 7, 123456789012345, 3]
+    keys = np.concatenate([inputs.lognormal_job(n, 9 + j) for j, n in enumerate(sizes)])
+    dk = torch.from_numpy(keys.view(np.int64)).cuda()
+    res = hss.partition_batch(dk, sizes, ps, 0.03, 0, seeds=seeds)
+    o = 0
+    for j, (n, p, sd) in enumerate(zip(sizes, ps, seeds)):
+        one, _ = hss.partition(dk[o:o + n], p, 0.03, sd)
+        assert res.job_rounds[j] == one.rounds
+        assert torch.equal(res.job_offsets(j), one.offsets)
+        if p > 1:
+            assert torch.equal(res.job_splitters(j), one.splitters)
+        o += n
