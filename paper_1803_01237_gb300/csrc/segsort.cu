@@ -956,6 +956,22 @@ __device__ __forceinline__ void cta_bitonic_sort(uint64_t* base, uint32_t a, uin
 template <int THREADS>
 constexpr int keys_min_blocks() { return THREADS <= 128 ? 8 : (THREADS <= 256 ? 3 : 1); }
 
+// A digit monotone in off that spreads keys over many binary orders of
+// magnitude: the position e of off's leading one, counted from e_lo (32
+// positions e_lo .. e_lo + 31), followed by the M = log2(R) - 5 bits below
+// the leading one; offsets below 2^e_lo (zero included) take digit 0.
+template <int R>
+__device__ __forceinline__ uint32_t log_digit(uint64_t off, int e_lo) {
+    constexpr int M = (R >= 4096) ? 7 : (R >= 2048 ? 6 : (R >= 1024 ? 5 : 4));
+    static_assert(32 * (1 << M) <= R, "log digit width");
+    if (off == 0ull) return 0u;
+    const int e = 63 - __clzll((long long)off);
+    if (e < e_lo) return 0u;
+    const uint32_t mant = e >= M ? (uint32_t)(off >> (e - M)) & ((1u << M) - 1u)
+                                 : (uint32_t)(off << (M - e)) & ((1u << M) - 1u);
+    return ((uint32_t)(e - e_lo) << M) | mant;
+}
+
 template <int THREADS, int CAP, int R, bool PREFETCH>
 __global__ __launch_bounds__(THREADS, keys_min_blocks<THREADS>()) void k_small_keys(
     const uint64_t* kin, uint64_t* kout, const uint64_t* __restrict__ seg_lo, const uint64_t* __restrict__ seg_hi,
@@ -1168,11 +1184,87 @@ __global__ __launch_bounds__(THREADS, keys_min_blocks<THREADS>()) void k_small_k
                 }
             }
             __syncthreads();
-            const uint32_t nmixed = s_flag[0];
+            uint32_t nmixed = s_flag[0];
             if (nmixed > (uint32_t)kKeysMixedMax) {  // uniform
-                if (tid == 0) slow_list[atomicAdd(slow_count, 1u)] = (uint32_t)s;
+                // Keys spread over many binary orders of magnitude (lognormal
+                // ones, say) crowd the lowest groups of the linear digit: count
+                // and scatter once more on the logarithmic digit (log_digit of
+                // key - min, also monotone in the key), the keys re-read from
+                // the input, which is untouched until this segment is written.
+                const uint64_t* g = kin + base;
+                uint64_t lo = ~0ull, hi = 0ull;
+                for (uint32_t j = tid; j < n; j += THREADS) {
+                    const uint64_t k = g[j] ^ flip_in;
+                    lo = min(lo, k);
+                    hi = max(hi, k);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    lo = min(lo, (uint64_t)__shfl_xor_sync(0xffffffffu, lo, o));
+                    hi = max(hi, (uint64_t)__shfl_xor_sync(0xffffffffu, hi, o));
+                }
+                if (lane == 0) { s_red[w] = lo; s_red[32 + w] = hi; }
+                for (int d = tid; d < R; d += THREADS) s_start[d] = 0;
                 __syncthreads();
-                continue;
+                lo = ~0ull;
+                hi = 0ull;
+                for (int i = 0; i < WARPS; ++i) { lo = min(lo, s_red[i]); hi = max(hi, s_red[32 + i]); }
+                // the 32 binary orders of magnitude below the range's top
+                const int e_lo = max(0, (63 - __clzll((long long)(hi - lo))) - 31);
+#pragma unroll
+                for (int i = 0; i < ITEMS; ++i) {
+                    if ((uint32_t)(i * THREADS) >= n) break;
+                    const uint32_t e = tid + i * THREADS;
+                    if (e < n) {
+                        const uint32_t d = log_digit<R>((g[e] ^ flip_in) - lo, e_lo);
+                        dp[i] = d | (atomicAdd(&s_start[d], 1u) << kSlotShift);
+                    }
+                }
+                __syncthreads();
+                uint32_t m2 = 0;
+                for (int d = tid; d < R; d += THREADS) m2 = max(m2, s_start[d]);
+                m2 = __reduce_max_sync(0xffffffffu, m2);
+                scan_smem_inplace<THREADS, R>(s_start, s_warp);
+                if (lane == 0) s_warp[w] = m2;
+                if (tid == 0) { s_start[R] = n; s_flag[0] = 0; }
+                __syncthreads();
+                mx = 0;
+#pragma unroll
+                for (int i = 0; i < WARPS; ++i) mx = max(mx, s_warp[i]);
+#pragma unroll
+                for (int i = 0; i < ITEMS; ++i) {
+                    if ((uint32_t)(i * THREADS) >= n) break;
+                    const uint32_t e = tid + i * THREADS;
+                    if (e < n) sk[s_start[dp[i] & kDigitMask] + (dp[i] >> kSlotShift)] = g[e] ^ flip_in;
+                }
+                __syncthreads();
+                if (mx >= (uint32_t)kTinyGroup) {
+#pragma unroll
+                    for (int i = 0; i < ITEMS; ++i) {
+                        if ((uint32_t)(i * THREADS) >= n) break;
+                        if (tid + i * THREADS >= n) continue;
+                        const uint32_t d = dp[i] & kDigitMask;
+                        const uint32_t a = s_start[d];
+                        if (s_start[d + 1] - a >= (uint32_t)kTinyGroup &&
+                            sk[a] != sk[a + ((dp[i] >> kSlotShift) & kSlotMask)])
+                            s_mark[d] = 1u;
+                    }
+                    __syncthreads();
+                    for (int d = tid; d < R; d += THREADS) {
+                        if (s_mark[d]) {
+                            s_mark[d] = 0;
+                            const uint32_t q = atomicAdd(&s_flag[0], 1u);
+                            if (q < (uint32_t)kKeysMixedMax) s_flag[1 + q] = (uint32_t)d;
+                        }
+                    }
+                    __syncthreads();
+                }
+                nmixed = s_flag[0];
+                if (nmixed > (uint32_t)kKeysMixedMax) {  // the log digit crowds too
+                    if (tid == 0) slow_list[atomicAdd(slow_count, 1u)] = (uint32_t)s;
+                    __syncthreads();
+                    continue;
+                }
             }
             for (uint32_t q = 0; q < nmixed; ++q) {
                 const uint32_t d = s_flag[1 + q];

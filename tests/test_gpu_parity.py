@@ -94,6 +94,17 @@ def test_local_sort_keys_only_matches_oracle(hss, N, p, gen):
     assert np.array_equal(host_u64(out), oracle.segment_sort(keys, p))
 
 
+@pytest.mark.parametrize("N,p", [(1 << 20, 256), (1 << 22, 4096), (1 << 20, 1024), (3 << 18, 500), (1 << 21, 1)])
+@pytest.mark.parametrize("sigma", [2.0, 4.0])
+def test_local_sort_keys_only_lognormal(hss, N, p, sigma):
+    """Lognormal keys (many binary orders of magnitude) in segments that go
+    on chip directly crowd the low groups of a linear digit; the on-chip sort
+    then counts again on a logarithmic digit.  Same result as the oracle."""
+    keys = inputs.lognormal_job(N, 31, sigma=sigma)
+    out = hss.local_sort(dev(keys), p)
+    assert np.array_equal(host_u64(out), oracle.segment_sort(keys, p))
+
+
 @pytest.mark.parametrize("N,p,nvals,share,adjacent", [
     (1 << 20, 2, 3, 0.85, False), (1 << 20, 1, 100, 0.99, False), (600000, 3, 4, 0.5, True),
     (1 << 19, 1, 40, 0.95, False)])
