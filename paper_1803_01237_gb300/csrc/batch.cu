@@ -828,10 +828,11 @@ int run_batch(const void* d_keys, const uint32_t* d_payload, int key_type, const
     HSS_BTRY(cudaMemcpyAsync(seg_off, T.seg_off.data(), ((size_t)T.P_tot + 1) * 8, cudaMemcpyHostToDevice, st));
 
     float ms[4] = {0, 0, 0, 0};
-    cudaEvent_t ev[5] = {};
+    TimingEvents<5> tev;
+    cudaEvent_t* ev = tev.ev;
     const bool timing = (prm->flags & HSS_FLAG_TIMING) != 0;
     if (timing) {
-        for (auto& e : ev) cudaEventCreate(&e);
+        tev.create();
         cudaEventRecord(ev[0], st);
     }
 
@@ -946,8 +947,6 @@ int run_batch(const void* d_keys, const uint32_t* d_payload, int key_type, const
         }
         h_stats->kernel_launches = (uint32_t)(hss_kernel_launch_count() - mark);
     }
-    if (timing)
-        for (auto& e : ev) cudaEventDestroy(e);
     return status;
 }
 

@@ -257,6 +257,11 @@ struct PhaseTimer {
         for (auto& e : ev) cudaEventDestroy(e);
         on = false;
     }
+    ~PhaseTimer() {  // a call that returned early
+        if (on)
+            for (auto& e : ev)
+                if (e) cudaEventDestroy(e);
+    }
 };
 
 static int read_dev_err(uint32_t* d_err, cudaStream_t st) {

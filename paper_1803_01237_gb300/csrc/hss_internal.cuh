@@ -130,6 +130,22 @@ int device_sm_count();
 // memory (the occupancy calculator, cached per device; at least 1).  Call
 // after ensure_func_attrs so that the shared-memory settings count.
 int resident_ctas(const void* func, int threads, size_t dyn_smem);
+// Timing events of a call (HSS_FLAG_TIMING), destroyed on every way out of it.
+template <int K>
+struct TimingEvents {
+    cudaEvent_t ev[K] = {};
+    bool on = false;
+    void create() {
+        on = true;
+        for (auto& e : ev) cudaEventCreate(&e);
+    }
+    ~TimingEvents() {
+        if (on)
+            for (auto& e : ev)
+                if (e) cudaEventDestroy(e);
+    }
+};
+
 // Read `bytes` (a multiple of 4, d_src 4-byte aligned) of device memory that
 // the host needs for a decision (round state, status words), after the work
 // queued on `st`; synchronises `st`.  Up to 8 KiB go through this thread's

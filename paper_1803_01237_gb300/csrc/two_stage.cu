@@ -146,9 +146,10 @@ int run_two_stage(const void* d_keys, const uint32_t* d_payload, int key_type, u
     RoundWs rws = rounds_ws_carve(at<void>(d_work, L.rws), std::max<uint64_t>(N, 1), p, cap, err, r);
     uint64_t* dst = at<uint64_t>(d_work, L.dst);
 
-    cudaEvent_t ev[4] = {};
+    TimingEvents<4> tev;
+    cudaEvent_t* ev = tev.ev;
     if (timing) {
-        for (auto& e : ev) cudaEventCreate(&e);
+        tev.create();
         cudaEventRecord(ev[0], st);
     }
     HSS_TTRY(cudaMemsetAsync(err, 0, 256, st));
@@ -180,9 +181,8 @@ int run_two_stage(const void* d_keys, const uint32_t* d_payload, int key_type, u
     // The group sizes decide the batch's tables.
     std::vector<uint64_t> h_goff(r + 1);
     uint32_t h_err = 0;
-    HSS_TTRY(cudaMemcpyAsync(h_goff.data(), goff, ((size_t)r + 1) * 8, cudaMemcpyDeviceToHost, st));
-    HSS_TTRY(cudaMemcpyAsync(&h_err, err, 4, cudaMemcpyDeviceToHost, st));
-    HSS_TTRY(cudaStreamSynchronize(st));
+    HSS_TTRY(read_small(h_goff.data(), goff, ((size_t)r + 1) * 8, st));
+    HSS_TTRY(read_small(&h_err, err, 4, st));
     if (device_loop) {
         status1 = read_round_result(rws, &rr, st);
         add_launches(1 + (uint64_t)rr.rounds * device_round_kernels());
@@ -236,8 +236,6 @@ int run_two_stage(const void* d_keys, const uint32_t* d_payload, int key_type, u
         }
         h_stats->kernel_launches = (uint32_t)(hss_kernel_launch_count() - mark);
     }
-    if (timing)
-        for (auto& e : ev) cudaEventDestroy(e);
     return status;
 }
 
