@@ -1940,13 +1940,22 @@ struct SplitArgs {
     uint32_t scatter;  // 1: tiles that gather no key ranges write each key straight to its run
 };
 
+// The tile's shape: keys alone 256 threads x 16 keys (four CTAs per SM);
+// with a payload 512 threads x 8 (two per SM), whose stable ranking then
+// fits 64 registers without spilling.
+template <bool PAY>
+constexpr int split_threads() { return PAY ? 512 : 256; }
+
 template <bool PAY, bool SPL>
-__global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitArgs A) {
+__global__ __launch_bounds__(split_threads<PAY>(), PAY ? 2 : 4) void k_split(const SplitArgs A) {
+    constexpr int kThreads = split_threads<PAY>();
+    constexpr int kWarps = kThreads / 32;
+    constexpr int kItems = kOsTile / kThreads;
     extern __shared__ __align__(16) unsigned char os_smem[];
     uint64_t* s_keys = (uint64_t*)os_smem;             // kOsTile keys
     uint32_t* s_pay = (uint32_t*)(s_keys + kOsTile);   // kOsTile payloads (PAY)
     uint8_t* s_dg = (uint8_t*)(s_pay + (PAY ? kOsTile : 0));  // kOsTile digits of the staged keys
-    __shared__ uint32_t s_hist[PAY ? kOsWarps * kRadix : 1];
+    __shared__ uint32_t s_hist[PAY ? kWarps * kRadix : 1];
     __shared__ uint32_t s_total[kRadix], s_start[kRadix];
     __shared__ uint64_t s_gbase[kRadix];
     __shared__ uint32_t s_warp[32];
@@ -1990,12 +1999,12 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
         return bysplit ? splitter_digit(s_spl, k) : split_digit(k, shift, dbase, dmult);
     };
 
-    uint64_t key[kOsItems];
-    uint32_t pay[kOsItems];
-    uint32_t rank[kOsItems];
-    const uint32_t wbase = w * 32 * kOsItems + lane;
+    uint64_t key[kItems];
+    uint32_t pay[kItems];
+    uint32_t rank[kItems];
+    const uint32_t wbase = w * 32 * kItems + lane;
 #pragma unroll
-    for (int i = 0; i < kOsItems; ++i) {
+    for (int i = 0; i < kItems; ++i) {
         const uint32_t e = wbase + i * 32;
         if (e < count) {
             key[i] = A.kin[seg_base + tile_lo + e] ^ A.flip_in;
@@ -2007,16 +2016,16 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
     }
     if constexpr (PAY) {
         // Each key's digit once, byte-packed in four registers.
-        uint32_t dpk[kOsItems / 4];
+        uint32_t dpk[kItems / 4];
 #pragma unroll
-        for (int i = 0; i < kOsItems / 4; ++i) dpk[i] = 0;
+        for (int i = 0; i < kItems / 4; ++i) dpk[i] = 0;
 #pragma unroll
-        for (int i = 0; i < kOsItems; ++i)
+        for (int i = 0; i < kItems; ++i)
             dpk[i >> 2] |= dig(key[i]) << (8 * (i & 3));
         auto digit_of = [&](int i) -> uint32_t {
             return (wbase + i * 32 < count) ? (dpk[i >> 2] >> (8 * (i & 3))) & 255u : (uint32_t)kRadix;
         };
-        block_rank<kOsWarps, kOsItems>(digit_of, count, rank, s_hist, s_total, s_start, s_warp, NoOp());
+        block_rank<kWarps, kItems>(digit_of, count, rank, s_hist, s_total, s_start, s_warp, NoOp());
         if (A.scatter && !gather) {  // uniform per CTA
             // The stable tile rank less the digit's tile start is the key's
             // place in its digit's run: write it there.
@@ -2024,7 +2033,7 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
                 s_gbase[tid] = seg_base + (uint64_t)A.tile_off[(uint64_t)t * kRadix + tid] - (uint64_t)s_start[tid];
             __syncthreads();
 #pragma unroll
-            for (int i = 0; i < kOsItems; ++i) {
+            for (int i = 0; i < kItems; ++i) {
                 if (wbase + i * 32 < count) {
                     const uint64_t dst = s_gbase[(dpk[i >> 2] >> (8 * (i & 3))) & 255u] + rank[i];
                     if (dst - seg_base >= seg_n) {  // never taken when the digit offsets are consistent
@@ -2038,7 +2047,7 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
             return;
         }
 #pragma unroll
-        for (int i = 0; i < kOsItems; ++i) {
+        for (int i = 0; i < kItems; ++i) {
             if (wbase + i * 32 < count) {
                 s_keys[rank[i]] = key[i];
                 s_dg[rank[i]] = (uint8_t)((dpk[i >> 2] >> (8 * (i & 3))) & 255u);
@@ -2054,7 +2063,7 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
         // lanes of a warp that share a digit with a match instruction costs
         // more than it saves, even on heavily duplicated keys.)
         const bool direct = A.scatter && !gather;  // uniform per CTA
-        for (int d = tid; d < kRadix; d += kOsThreads) {
+        for (int d = tid; d < kRadix; d += kThreads) {
             s_total[d] = 0;
             // direct: digit d's keys of this tile start here in the output
             if (direct) s_gbase[d] = seg_base + (uint64_t)A.tile_off[(uint64_t)t * kRadix + d];
@@ -2066,7 +2075,7 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
             const bool skew = A.tile_skew[t] != 0;
             const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
-            for (int i = 0; i < kOsItems; ++i) {
+            for (int i = 0; i < kItems; ++i) {
                 const uint32_t d = wbase + i * 32 < count ? dig(key[i]) : (uint32_t)kRadix;
                 uint32_t slot = 0;
                 if (skew) {
@@ -2093,7 +2102,7 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
         if (A.tile_skew[t]) {  // uniform per CTA: see tile_skew_flag
             const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
-            for (int i = 0; i < kOsItems; ++i) {
+            for (int i = 0; i < kItems; ++i) {
                 const uint32_t d =
                     wbase + i * 32 < count ? dig(key[i]) : (uint32_t)kRadix;
                 const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
@@ -2106,7 +2115,7 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
             }
         } else {
 #pragma unroll
-            for (int i = 0; i < kOsItems; ++i) {
+            for (int i = 0; i < kItems; ++i) {
                 if (wbase + i * 32 < count) {
                     const uint32_t d = dig(key[i]);
                     rank[i] = d | (atomicAdd(&s_total[d], 1u) << 8);
@@ -2114,9 +2123,9 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
             }
         }
         __syncthreads();
-        scan256_smem<kOsThreads>(s_total, s_start, s_warp);
+        scan256_smem<kThreads>(s_total, s_start, s_warp);
 #pragma unroll
-        for (int i = 0; i < kOsItems; ++i) {
+        for (int i = 0; i < kItems; ++i) {
             if (wbase + i * 32 < count) {
                 const uint32_t d = rank[i] & 255u;
                 const uint32_t pos = s_start[d] + (rank[i] >> 8);
@@ -2131,7 +2140,7 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
     if (tid < kRadix)
         s_gbase[tid] = seg_base + (uint64_t)A.tile_off[(uint64_t)t * kRadix + tid] - (uint64_t)s_start[tid];
     __syncthreads();
-    for (uint32_t j = tid; j < count; j += kOsThreads) {
+    for (uint32_t j = tid; j < count; j += kThreads) {
         const uint64_t k = s_keys[j];
         const uint32_t d = s_dg[j];
         const uint64_t dst = s_gbase[d] + j;
@@ -2146,7 +2155,7 @@ __global__ __launch_bounds__(kOsThreads, PAY ? 3 : 4) void k_split(const SplitAr
         // Smallest and largest key of every sub-bucket the next level splits
         // again (its digit range there).  The staged keys come in digit runs,
         // so a warp usually reduces one run and issues one atomic pair.
-        for (uint32_t j0 = (uint32_t)w * 32; j0 < count; j0 += kOsThreads) {
+        for (uint32_t j0 = (uint32_t)w * 32; j0 < count; j0 += kThreads) {
             const uint32_t j = j0 + lane;
             const bool v = j < count;
             const uint64_t k = v ? s_keys[j] : 0ull;
@@ -2518,9 +2527,9 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
             cudaEventRecord(timing->ev[timing->n][0], st);
         }
         if (bysplit_level)
-            HSS_LAUNCH((k_split<PAY, true>), tiles, kOsThreads, smem, st, A);
+            HSS_LAUNCH((k_split<PAY, true>), tiles, split_threads<PAY>(), smem, st, A);
         else
-            HSS_LAUNCH((k_split<PAY, false>), tiles, kOsThreads, smem, st, A);
+            HSS_LAUNCH((k_split<PAY, false>), tiles, split_threads<PAY>(), smem, st, A);
         if (timed) {
             cudaEventRecord(timing->ev[timing->n][1], st);
             timing->keys[timing->n] = keys_large;
