@@ -112,3 +112,16 @@ def test_two_stage_refuses_bad_group_counts(hss):
             hss.sort_two_stage(keys, p, r, 0.05, 1)
     with pytest.raises(hss.HSSError):
         hss.sort_two_stage(keys[:40], 32, 4, 0.05, 1)  # fewer than 2p keys
+
+
+def test_two_stage_round_limit_matches_oracle(hss):
+    """With one round per stage the splitters stay unresolved: both stages
+    report the round limit, keep the closest cuts seen (Sec. 4.2.2 step 5),
+    and the result is still the oracle's, stage by stage."""
+    N, p, r, eps, seed = 1 << 18, 64, 8, 0.002, 4
+    keys = inputs.gauss_mix(N, 6)
+    res = hss.sort_two_stage(torch.from_numpy(keys.view(np.int64)).cuda(), p, r, eps, seed, max_rounds=1)
+    ref = oracle.hss_two_stage(keys, p, r, eps, seed, max_rounds=1)
+    assert ref.stage1.status == res.stage1.status == hss.ERR_ROUND_LIMIT
+    assert res.status == hss.ERR_ROUND_LIMIT
+    _check(hss, res, ref, r, p, None)
