@@ -9,7 +9,11 @@
  *   - Every buffer belongs to the caller.  Pointers named d_* are device
  *     pointers on the current device, h_* are host pointers.  The library
  *     never allocates device memory: scratch comes from the caller's
- *     workspace (d_work, work_bytes), sized with hss_workspace_bytes().
+ *     workspace (d_work, work_bytes), sized with hss_workspace_bytes().  The
+ *     small reads the host needs (a level's counts, a round's state, status
+ *     words) go through two mapped pinned host buffers per calling thread,
+ *     allocated at its first call (so they never wait behind bulk copies on
+ *     the copy engine); hss_local_sort_noalloc uses neither.
  *   - Work is enqueued on `stream` (a cudaStream_t passed as void*, NULL =
  *     the legacy default stream).  The splitter rounds of a repeated shape
  *     run on the device (a CUDA graph loop, see HSS_FLAG_DEVICE_ROUNDS), so
