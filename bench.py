@@ -494,7 +494,9 @@ def run_morton_workload(args):
     in HBM (12 GiB in, 12 GiB out: larger than L2, no flush).  The same
     line times the step as two-stage HSS with --groups groups
     (hss_sort_two_stage, key `two_stage`); --morton-form two times that form
-    alone and makes it the line's value."""
+    alone and makes it the line's value.  Unless --no-tune, the autotuner then
+    picks the sort tiling, histogram form and round driver on this input at
+    s = 5 (key `autotuned`: the same result, timed for both forms)."""
     import numpy as np
     import torch
     from paper_1803_01237_gb300 import hss, inputs
@@ -555,6 +557,42 @@ def run_morton_workload(args):
                "stage2_mean_rounds": float(np.mean(t.group_rounds)), "phase_ms": phase2,
                "gpu_launches": hss.launch_count() - l2, "output_sorted": bool(np.all(o2[:-1] <= o2[1:])),
                "same_output_as_single_stage": None if o is None else bool(np.array_equal(o, o2))}
+    tuned = None
+    if not args.no_tune:
+        # The autotuner on this input at s = 5 (its tiling, histogram form and
+        # round driver leave the result unchanged, so the tuned step is still
+        # the oracle's), then both forms timed with its choice.
+        import tempfile
+        from dataclasses import asdict
+        from paper_1803_01237_gb300 import autotune
+        with tempfile.TemporaryDirectory() as td:
+            tuner = autotune.Tuner(os.path.join(td, "tuning.json"))
+            t0 = time.perf_counter()
+            choice = tuner.tune(N, P, E, kind="morton", sample=keys, payload=pay, seed=SEED, trials=1,
+                                space=([5.0], autotune.default_space(P)[1]), force=True)
+            tuning_s = time.perf_counter() - t0
+        s_, fl_ = choice.apply()
+        try:
+            forms = {}
+            for form in (("single",) if not (args.groups > 1 and args.morton_form in ("both", "two")) else
+                         ("single", "two")):
+                call = (lambda: hss.sort(keys, P, E, SEED, payload=pay, out=out, out_payload=out_p, oversample=s_,
+                                         flags=fl_)) if form == "single" else \
+                       (lambda: hss.sort_two_stage(keys, P, args.groups, E, SEED, payload=pay, out=out,
+                                                   out_payload=out_p, oversample=s_, flags=fl_))
+                call()
+                torch.cuda.synchronize(dev)
+                ev0.record()
+                for _ in range(args.steps):
+                    call()
+                ev1.record()
+                torch.cuda.synchronize(dev)
+                forms[form] = ev0.elapsed_time(ev1) / args.steps
+        finally:
+            hss.reset_tuning()
+        tuned = {"choice": asdict(choice), "tuning_seconds": tuning_s,
+                 "single_ms_per_step": forms.get("single"), "two_stage_ms_per_step": forms.get("two"),
+                 "note": "autotuned at s = 5: same splitters, offsets and output as the library defaults"}
     clk = clocks.stop()
     if not single:
         if two is None:
@@ -575,6 +613,8 @@ def run_morton_workload(args):
     }
     if two is not None:
         line["two_stage"] = two
+    if tuned is not None:
+        line["autotuned"] = tuned
     print(json.dumps(line), flush=True)
     return 0
 
@@ -732,7 +772,7 @@ def main():
     ap.add_argument("--workload", default="sort", choices=["sort", "batch", "serve", "rounds", "schedules", "morton"],
                     help="sort: the N=2^28 bench line (default); batch: 4096 independent jobs; serve: Poisson requests")
     ap.add_argument("--batch-jobs", type=int, default=4096)
-    ap.add_argument("--no-tune", action="store_true", help="batch workload: skip the autotuned timing")
+    ap.add_argument("--no-tune", action="store_true", help="batch and morton workloads: skip the autotuned timing")
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-slots", type=int, default=8)

@@ -62,10 +62,19 @@ class Choice:
 
 def default_space(p: int):
     """Candidates: oversampling and tiling first (the largest effects), then
-    the histogram form and the round driver around the best of those."""
+    the histogram form and the round driver around the best of those.  A
+    tiling is (chip_max_keys, child_interp, child_bucket_keys[, pack_keys,
+    first_split]); the last one splits each segment first on sampled
+    splitters with small packs (spatially clustered keys, e.g. Morton codes of
+    a Plummer sphere, need one split level instead of three)."""
     over = [3.0, 5.0, 8.0, 12.0]
-    tiles = [(4096, 0, 384), (14336, 0, 384), (4096, 1, 384), (4096, 1, 768)]
+    tiles = [(4096, 0, 384), (14336, 0, 384), (4096, 1, 384), (4096, 1, 768), (4096, 0, 384, 256, 1)]
     return over, tiles
+
+
+def _tiling_fields(tiling) -> dict:
+    names = ("chip_max_keys", "child_interp", "child_bucket_keys", "pack_keys", "first_split")
+    return {k: int(v) for k, v in zip(names, tiling)}
 
 
 def gpu_name() -> str:
@@ -98,26 +107,31 @@ class Tuner:
 
     # --- measurement -------------------------------------------------------
     @staticmethod
-    def _time_sort(keys, p, eps, seed, choice: Choice, trials: int, key_type: str):
+    def _time_sort(keys, p, eps, seed, choice: Choice, trials: int, key_type: str, payload=None):
         import torch
         s, flags = choice.apply()
         out = torch.empty_like(keys)
-        hss.sort(keys, p, eps, seed, oversample=s, flags=flags, key_type=key_type, out=out)  # warm-up, graph build
+        outp = torch.empty_like(payload) if payload is not None else None
+        # warm-up, graph build
+        hss.sort(keys, p, eps, seed, payload=payload, oversample=s, flags=flags, key_type=key_type, out=out,
+                 out_payload=outp)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(trials):
-            r = hss.sort(keys, p, eps, seed, oversample=s, flags=flags, key_type=key_type, out=out)
+            r = hss.sort(keys, p, eps, seed, payload=payload, oversample=s, flags=flags, key_type=key_type, out=out,
+                         out_payload=outp)
         e1.record()
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / trials, r.rounds
 
     def tune(self, N: int, p: int, eps: float = 0.02, key_type: str = "u64", kind: str = "uniform", sample=None,
-             seed: int = 1, trials: int = 3, space=None, force: bool = False) -> Choice:
+             seed: int = 1, trials: int = 3, space=None, force: bool = False, payload=None) -> Choice:
         """The fastest Choice for sorting N keys on p processors (measured on
-        `sample` -- a device tensor of N keys -- or on a synthetic input of
-        `kind`; among choices within 3% of the fastest, the one with the
-        fewest rounds), from the cache when present."""
+        `sample` -- a device tensor of N keys, with `payload` when the keys
+        carry one -- or on a synthetic input of `kind`; among choices within
+        3% of the fastest, the one with the fewest rounds), from the cache
+        when present."""
         import torch
         key = cache_key(N, p, key_type, kind)
         with self._lock:
@@ -131,15 +145,15 @@ class Tuner:
         results = []
         try:
             # stage 1: oversampling x tiling with the default histogram form and driver
-            for s, (cm, ci, ck) in itertools.product(over, tiles):
-                c = Choice(oversample=s, chip_max_keys=cm, child_interp=ci, child_bucket_keys=ck)
-                ms, rounds = self._time_sort(sample, p, eps, seed, c, trials, key_type)
+            for s, tiling in itertools.product(over, tiles):
+                c = Choice(oversample=s, **_tiling_fields(tiling))
+                ms, rounds = self._time_sort(sample, p, eps, seed, c, trials, key_type, payload)
                 results.append((ms, rounds, c))
             best = min(results, key=lambda r: r[0])[2]
             # stage 2: histogram form and round driver around the best
             for hf, hr in ((hss.FLAG_HIST_PROBE, 0), (hss.FLAG_HIST_STAGED, 0), (0, 1)):
                 c = Choice(**{**asdict(best), "hist_flags": hf, "host_rounds": hr})
-                ms, rounds = self._time_sort(sample, p, eps, seed, c, trials, key_type)
+                ms, rounds = self._time_sort(sample, p, eps, seed, c, trials, key_type, payload)
                 results.append((ms, rounds, c))
         finally:
             hss.reset_tuning()
@@ -173,8 +187,8 @@ class Tuner:
         over, tiles = default_space(max(sps))
         results = []
         try:
-            for s, (cm, ci, ck) in itertools.product(over, tiles[:3]):
-                c = Choice(oversample=s, chip_max_keys=cm, child_interp=ci, child_bucket_keys=ck)
+            for s, tiling in itertools.product(over, tiles[:3]):
+                c = Choice(oversample=s, **_tiling_fields(tiling))
                 so, _ = c.apply()
                 out = torch.empty_like(sub)
                 hss.sort_batch(sub, ssz, sps, eps, seed, oversample=so, key_type=key_type, out=out)
