@@ -1811,7 +1811,10 @@ __global__ __launch_bounds__(256) void k_msd_prep(const uint64_t* __restrict__ s
                                                   uint64_t* __restrict__ cmin, uint64_t* __restrict__ cmax,
                                                   uint32_t level_chip_max, uint32_t pack_keys,
                                                   const uint8_t* __restrict__ spl_mode) {
-    __shared__ uint32_t s_c[kRadix], s_x[kRadix], s_warp[32], s_end[kRadix];
+    __shared__ uint32_t s_c[kRadix], s_x[kRadix + 1], s_warp[32], s_end[kRadix];
+    __shared__ uint16_t s_jump[8][kRadix + 1];  // packing: 2^i packs ahead of each sub-bucket
+    __shared__ uint32_t s_big[8];               // packing: sub-buckets split again, one bit each
+    __shared__ uint8_t s_first[kRadix];         // packing: the sub-bucket starts a pack
     const uint32_t id = blockIdx.x;
     if (id >= counters[19]) return;
     const uint32_t s = large_seg[id];
@@ -1851,31 +1854,54 @@ __global__ __launch_bounds__(256) void k_msd_prep(const uint64_t* __restrict__ s
     // (uniform keys: none do, and the serial walk below is skipped).
     const bool pair_fits = d + 1 < (uint32_t)kRadix && total + s_c[d + 1] <= pack_keys && total + s_c[d + 1] > 0u;
     const bool packable = __syncthreads_or(pair_fits) != 0;
-    if (packable && d == 0) {
-        uint32_t start = 0, acc = 0;
-        bool open = false;
-        for (uint32_t k = 0; k < (uint32_t)kRadix; ++k) {
-            const uint32_t c = s_c[k];
-            if (c > level_chip_max) {
-                if (open) s_end[start] = s_x[k];
-                open = false;
-                s_end[k] = s_x[k] + c;
-                continue;
+    if (packable) {  // uniform per CTA
+        // The greedy walk over the sub-buckets in order (a sub-bucket split
+        // again stands alone; otherwise a pack takes sub-buckets while they
+        // add up to at most pack_keys), computed in parallel: next[d], the
+        // sub-bucket after the pack that would start at d, by a bit search
+        // and a binary search; the packs reachable from sub-bucket 0 by
+        // pointer doubling (thread m finds the m-th pack's start).
+        const bool big = total > level_chip_max;
+        const uint32_t bal = __ballot_sync(0xffffffffu, big);
+        if ((d & 31) == 0) s_big[d >> 5] = bal;
+        if (d == 0) s_x[kRadix] = s_x[kRadix - 1] + s_c[kRadix - 1];
+        __syncthreads();
+        uint32_t nxt;
+        if (big) {
+            nxt = d + 1;
+        } else {
+            uint32_t fb = kRadix;  // the first sub-bucket after d split again
+            for (uint32_t wd = (d + 1) >> 5; wd < 8; ++wd) {
+                const uint32_t m = s_big[wd] & (wd == ((d + 1) >> 5) ? ~0u << ((d + 1) & 31) : ~0u);
+                if ((d + 1) < (uint32_t)kRadix && m) { fb = wd * 32 + (uint32_t)(__ffs(m) - 1); break; }
             }
-            if (open && acc + c > pack_keys) {
-                s_end[start] = s_x[k];
-                open = false;
+            // the first j > d whose keys would take the pack past pack_keys:
+            // the first m >= d + 2 with s_x[m] > s_x[d] + pack_keys, j = m - 1
+            const uint32_t lim = x + pack_keys;
+            uint32_t lo = d + 2, hi = kRadix + 1;  // search m in [lo, hi)
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (s_x[mid] > lim) hi = mid; else lo = mid + 1;
             }
-            if (!open) {
-                start = k;
-                acc = 0;
-                open = true;
-            } else {
-                s_end[k] = ~0u;
-            }
-            acc += c;
+            const uint32_t fs = lo <= (uint32_t)kRadix ? lo - 1 : (uint32_t)kRadix;
+            nxt = min(fb, fs);
         }
-        if (open) s_end[start] = s_x[kRadix - 1] + s_c[kRadix - 1];
+        s_jump[0][d] = (uint16_t)nxt;
+        if (d == 0) s_jump[0][kRadix] = (uint16_t)kRadix;
+        s_first[d] = 0;
+        __syncthreads();
+        for (int i = 1; i < 8; ++i) {
+            const uint32_t a = s_jump[i - 1][d];
+            s_jump[i][d] = a < (uint32_t)kRadix ? s_jump[i - 1][a] : (uint16_t)kRadix;
+            if (d == 0) s_jump[i][kRadix] = (uint16_t)kRadix;
+            __syncthreads();
+        }
+        uint32_t pos = 0;  // start of pack number d
+        for (int i = 0; i < 8 && pos < (uint32_t)kRadix; ++i)
+            if ((d >> i) & 1u) pos = s_jump[i][pos];
+        if (pos < (uint32_t)kRadix) s_first[pos] = 1;
+        __syncthreads();
+        s_end[d] = s_first[d] ? s_x[nxt] : ~0u;
     }
     if (!packable) s_end[d] = x + total;
     __syncthreads();
