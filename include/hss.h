@@ -514,9 +514,11 @@ typedef struct {
     /* First split of each segment of a local sort: 0 (default) on its top
      * varying byte; 1 samples the segment first and, when the sample's top
      * varying byte crowds its keys into few values (Gaussian clusters, heavy
-     * duplicates), splits on 255 splitters taken from the sorted sample (a
-     * binary search per key: measured slower than the extra split level it
-     * saves, so off by default). */
+     * duplicates, spatially clustered Morton codes), splits on 255 splitters
+     * taken from the sorted sample (a binary search per key) and packs those
+     * sub-buckets by at most 256 keys.  Faster on the clustered Morton
+     * payload workload, slower on the Gaussian mixture and Zipf keys: off by
+     * default, left to the autotuner. */
     uint32_t first_split;
     /* How the split pass writes a tile: 0 stages the tile in shared memory in
      * digit order and writes each digit's run with consecutive stores; 1

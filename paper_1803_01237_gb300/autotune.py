@@ -65,10 +65,10 @@ def default_space(p: int):
     the histogram form and the round driver around the best of those.  A
     tiling is (chip_max_keys, child_interp, child_bucket_keys[, pack_keys,
     first_split]); the last one splits each segment first on sampled
-    splitters with small packs (spatially clustered keys, e.g. Morton codes of
-    a Plummer sphere, need one split level instead of three)."""
+    splitters (spatially clustered keys, e.g. Morton codes of a Plummer
+    sphere, need one split level instead of three)."""
     over = [3.0, 5.0, 8.0, 12.0]
-    tiles = [(4096, 0, 384), (14336, 0, 384), (4096, 1, 384), (4096, 1, 768), (4096, 0, 384, 256, 1)]
+    tiles = [(4096, 0, 384), (14336, 0, 384), (4096, 1, 384), (4096, 1, 768), (4096, 0, 384, 1024, 1)]
     return over, tiles
 
 

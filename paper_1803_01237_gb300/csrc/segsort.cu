@@ -2526,7 +2526,9 @@ static cudaError_t segsort_t(const uint64_t* src, uint64_t* dst, uint64_t* tmp, 
         HSS_LAUNCH(k_msd_prep, n_large, 256, 0, st, L.seg_lo, ws.large_seg, ws.counters, ws.tile_start, ws.tile_hist,
                    ws.vor, ws.vand, L.hint_lo, L.hint_mult, ws.msd_base, ws.msd_mult, ws.msd_shift[buf], ws.spec,
                    ws.direct, ws.sub_lo[buf], ws.sub_hi[buf], ws.tile_off, child_interp ? chip_max : 0xffffffffu,
-                   ws.large_mask, ws.any_large, ws.cmin[buf], ws.cmax[buf], chip_max, std::min(pack_keys, chip_max),
+                   ws.large_mask, ws.any_large, ws.cmin[buf], ws.cmax[buf], chip_max,
+                   // sampled-splitter sub-buckets (about 256 keys, unevenly wide) pack at most 256 keys
+                   std::min(bysplit_level ? std::min(pack_keys, 256u) : pack_keys, chip_max),
                    bysplit_level ? ws.spl_mode : nullptr);
         // The split pass: level buffers alternate tmp, dst, tmp, ... after src.
         uint64_t* next = (L.depth & 1) ? dst : tmp;
