@@ -342,7 +342,10 @@ def run_gpu(args):
         e2e = {"value": world * N / e2e_s, "unit": "keys/s", "h2d_bytes_per_step": 8 * N,
                "d2h_bytes_per_step": 8 * N + 16 * (P - 1) + 8 * (P + 1), "ms_per_step": 1000 * e2e_s,
                "api": "hss_sort_host (pinned host buffers, copies inside the call)", "input": "uniform",
-               "calls_ms": calls_ms}
+               "calls_ms": calls_ms, "median_call_ms": sorted(calls_ms)[len(calls_ms) // 2],
+               "note": "value and ms_per_step are the mean over the calls; on this shared host single calls "
+                       "sometimes take 3-4 times the median while the device phases keep their times "
+                       "(the host copies slow down)"}
         del hk, ho
 
     if rank != 0:
