@@ -40,3 +40,20 @@ def test_choice_flags_and_cache_file(tmp_path):
     t2 = autotune.Tuner(str(path))
     assert t2.cache == json.load(open(path))
     assert autotune.Choice(**t2.cache["GPU|u64|n20|p6|uniform"]["choice"]).child_interp == 1
+
+
+def test_default_space_tilings_map_to_choices():
+    """Every tiling of the search space becomes a Choice whose knobs the C ABI
+    accepts (3-tuples leave packing and the first split at their defaults)."""
+    from paper_1803_01237_gb300 import autotune
+    over, tiles = autotune.default_space(1024)
+    assert 5.0 in over
+    for t in tiles:
+        c = autotune.Choice(oversample=5.0, **autotune._tiling_fields(t))
+        assert (c.chip_max_keys, c.child_interp, c.child_bucket_keys) == tuple(t[:3])
+        if len(t) > 3:
+            assert (c.pack_keys, c.first_split) == tuple(t[3:5])
+        s, flags = c.apply()
+        assert hss.get_tuning()["first_split"] == c.first_split
+        hss.reset_tuning()
+    assert any(len(t) > 4 and t[4] == 1 for t in tiles)  # the sampled-splitter first split is searched
