@@ -568,3 +568,40 @@ def test_equal_schedule_expected_probes_per_interval(gen):
                 pooled_mean += mean
                 pooled_var += var
     assert abs(pooled_got - pooled_mean) <= 4.0 * math.sqrt(pooled_var) + 1.0
+
+
+@pytest.mark.parametrize("gen,max_rounds", [("uniform", 1), ("uniform", 2), ("zipf", 1)])
+def test_final_choice_is_closest_seen_cut(gen, max_rounds):
+    """Sec. 4.2.2 step 5: each splitter is the seen cut ranked closest to t_i,
+    over every probe of every round; with a round limit most splitters stay
+    unresolved, so the choice (and its tie rule, equal distance -> L_i) is
+    exercised.  Ranks of the probes are taken by brute force; the sentinels
+    (rank 0 with no probe below, rank N with none above) are reported with
+    seg -2 / -3."""
+    N, p = 1 << 12, 16
+    gens = {"uniform": inputs.uniform, "zipf": lambda n, s: inputs.zipf(n, s, distinct=200)}
+    ties = 0
+    for seed in range(60):
+        keys = gens[gen](N, seed)
+        res = oracle.hss(keys, p, 0.002, seed=seed, oversample=1.0, max_rounds=max_rounds, trace=True)
+        assert res.rounds <= max_rounds
+        order, rank_of = _global_order(keys, p)
+        _, idx = _sorted_pos_to_input_index(keys, p)
+        seen = np.array([rank_of[idx[int(sg)][int(sp)]] for r in range(res.rounds)
+                         for _, sg, sp in res.samples[r]], dtype=np.int64)
+        for i in range(p - 1):
+            t = ((i + 1) * N) // p
+            below, above = seen[seen <= t], seen[seen >= t]
+            lo = int(below.max()) if below.size else 0
+            hi = int(above.min()) if above.size else N
+            want = lo if t - lo <= hi - t else hi
+            ties += int(lo != hi and t - lo == hi - t)
+            assert int(res.offsets[i + 1]) == want
+            if want == 0 and not below.size:
+                assert int(res.splitter_seg[i]) == -2
+            elif want == N and not above.size:
+                assert int(res.splitter_seg[i]) == -3
+            else:
+                e = idx[int(res.splitter_seg[i])][int(res.splitter_spos[i])]
+                assert int(rank_of[e]) == want and keys[e] == res.splitter_key[i]
+    assert ties >= 1  # the tie rule was reached
