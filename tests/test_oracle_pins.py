@@ -605,3 +605,44 @@ def test_final_choice_is_closest_seen_cut(gen, max_rounds):
                 e = idx[int(res.splitter_seg[i])][int(res.splitter_spos[i])]
                 assert int(rank_of[e]) == want and keys[e] == res.splitter_key[i]
     assert ties >= 1  # the tie rule was reached
+
+
+@pytest.mark.parametrize("gen", ["uniform", "zipf"])
+def test_resolution_rule_against_brute_force(gen):
+    """Sec. 4.2.2 step 3: after every round, splitter i counts as resolved
+    exactly when the best probe seen so far below or above t_i (brute-force
+    ranks) lies within tol = floor(N eps / 2p) of it, the bound inclusive;
+    the per-round unresolved counts follow, and the rounds stop at the first
+    round that leaves none.  Cases where only the equality |rank - t_i| = tol
+    resolves a splitter occur and are checked."""
+    N, p, eps = 1 << 13, 16, 0.02
+    tol = (N * 2 // 100) // (2 * p)  # floor(N eps / 2p) in integers: eps = 2/100
+    assert tol == 5
+    gens = {"uniform": inputs.uniform, "zipf": lambda n, s: inputs.zipf(n, s, distinct=300)}
+    decisive = 0
+    for seed in range(20):
+        keys = gens[gen](N, seed)
+        res = oracle.hss(keys, p, eps, seed=seed, trace=True)
+        assert res.tol == tol
+        _, rank_of = _global_order(keys, p)
+        _, idx = _sorted_pos_to_input_index(keys, p)
+        seen = np.zeros(0, dtype=np.int64)
+        for r in range(res.rounds + 1):
+            if r:
+                seen = np.concatenate([seen, np.array([rank_of[idx[int(sg)][int(sp)]]
+                                                       for _, sg, sp in res.samples[r - 1]], dtype=np.int64)])
+            open_ = 0
+            for i in range(p - 1):
+                t = ((i + 1) * N) // p
+                below, above = seen[seen <= t], seen[seen >= t]
+                dl = t - (int(below.max()) if below.size else 0)
+                du = (int(above.min()) if above.size else N) - t
+                ok = dl <= tol or du <= tol
+                decisive += int(ok and min(dl, du) == tol)
+                assert bool(res.trace_resolved[r, i] & 1) == ok
+                assert bool(res.trace_resolved[r, i] & 2) == bool(below.size)  # L is an input key
+                assert bool(res.trace_resolved[r, i] & 4) == bool(above.size)  # U is an input key
+                open_ += int(not ok)
+            assert int(res.unresolved[r]) == open_
+            assert (open_ == 0) == (r == res.rounds)
+    assert decisive >= 1
