@@ -159,3 +159,28 @@ def test_two_stage_with_r_equal_p():
     res = oracle.hss_two_stage(keys, p, p, eps, 3)
     assert np.array_equal(res.out_keys, np.sort(keys, kind="stable"))
     assert np.array_equal(res.offsets, res.stage1.offsets)
+
+
+def test_paper_two_stage_round_counts():
+    """Sec. 7.3: two stages at p = 8192 and 16384 with 128 groups and eps = 1%
+    per stage took 6 rounds per stage.  Soft check (window of the fixture) on
+    the oracle's full-size record of 2^30 Morton keys at p = 16384, r = 128,
+    and on live runs of 2^21 uniform keys at both processor counts: stage 1 and
+    every group of stage 2 converge, within the window of the paper's count."""
+    import json
+    import os
+    golden = os.path.join(os.path.dirname(__file__), "golden")
+    with open(os.path.join(golden, "paper_round_counts.json")) as f:
+        g = json.load(f)["two_stage_iterations"]
+    want, win, r, eps = g["iterations"], g["window"], g["groups"], g["eps"]
+    with open(os.path.join(golden, "fullsize_two_stage.json")) as f:
+        rec = json.load(f)
+    assert rec["config"]["p"] in g["p"] and rec["config"]["groups"] == r and rec["config"]["eps"] == eps
+    stages = [rec["stage1"]] + rec["groups"]
+    assert len(stages) == r + 1
+    for st in stages:
+        assert st["status"] == 0 and abs(st["rounds"] - want) <= win, st["rounds"]
+    for p in g["p"]:
+        ref = oracle.hss_two_stage(inputs.uniform(1 << 21, 3), p, r, eps, 3)
+        for st in [ref.stage1] + list(ref.stage2):
+            assert st.status == 0 and abs(st.rounds - want) <= win, (p, st.rounds)
