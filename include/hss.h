@@ -375,8 +375,13 @@ int hss_partition_batch_seeded(const void* d_keys, int key_type, const uint64_t*
  *
  * Requirements (else HSS_ERR_INVALID before any device work): 2 <= r <= p,
  * r divides p, p / r <= 65536, N >= 2p, the proportional schedule, u64 or
- * i64 keys.  If stage 1 leaves a group with fewer than p / r keys (only when
- * it did not balance) the call returns HSS_ERR_INVALID after stage 1.
+ * i64 keys; and every group stays below 2^30 keys at its balance bound
+ * (N / r + 2 floor(N eps / (2r)) + 2 < 2^30) as every stage-1 segment
+ * (ceil(N / p) < 2^30).  If stage 1 leaves a group with fewer than p / r keys
+ * (only when it did not balance) the call returns HSS_ERR_INVALID after
+ * stage 1.  d_work holds at least hss_two_stage_workspace_bytes(...) bytes
+ * of the same arguments (else HSS_ERR_WORKSPACE); its contents are undefined
+ * afterwards.
  *
  * Outputs (device): d_keys_out[N] (d_payload_out[N] when d_payload is set),
  * d_group_splitters[r - 1] (stage-1 cuts: seg / spos name an input processor
