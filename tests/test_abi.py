@@ -175,6 +175,9 @@ def test_two_stage_arguments_rejected_without_device(lib):
     for n, p, r, kw in [(N, 256, 1, {}), (N, 256, 24, {}), (N, 256, 512, {}), (300, 256, 16, {}),
                         (N, 256, 16, {"schedule": 1}), (N, 256, 16, {"eps": 0.0}), (N, 1 << 18, 2, {})]:
         assert L.hss_two_stage_workspace_bytes(n, ctypes.byref(prm(p, **kw)), r, 0, 0) == 0
+    # a group at its balance bound reaches 2^30 keys with 2^31 keys in 2 groups, not in 8
+    assert L.hss_two_stage_workspace_bytes(1 << 31, ctypes.byref(prm(8)), 2, 0, 0) == 0
+    assert L.hss_two_stage_workspace_bytes(1 << 31, ctypes.byref(prm(8)), 8, 0, 0) > 0
     P = ctypes.c_void_p
     L.hss_sort_two_stage.restype = ctypes.c_int
     L.hss_sort_two_stage.argtypes = [P, P, ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(hss.Params), ctypes.c_uint32,
