@@ -85,3 +85,47 @@ def test_delta_scales_with_job_size():
     d = serve.Server._dkw
     assert d(1 << 16) == pytest.approx(math.sqrt(math.log(200.0) / 2.0 ** 17))
     assert d(1 << 20) == pytest.approx(d(1 << 16) / 4)
+
+
+def _bare_server(budget, reserve=0, available=0, slots=2):
+    """A Server with only the fields admission reads (no device, no streams)."""
+    from paper_1803_01237_gb300 import serve
+    s = object.__new__(serve.Server)
+    s.hbm_budget, s.hbm_reserve, s.pending_bytes, s.bytes_in_flight = budget, reserve, 0, 0
+    s.slot_ws = [None] * slots
+    s._available_bytes = lambda: available
+    return s
+
+
+class _Ws:
+    def __init__(self, n):
+        self.n = n
+
+    def numel(self):
+        return self.n
+
+
+def test_admission_by_memory():
+    """Admission rules of the server, on the host: no budget admits every
+    request; a fixed budget counts the bytes of the requests in flight; the
+    "free" budget compares what the request would allocate now (the slot's
+    workspace growth plus its outputs) and what earlier admissions have yet to
+    allocate with the device's available bytes less the reserve."""
+    from paper_1803_01237_gb300 import serve
+    import torch
+    req = serve.Request(rid=0, arrival=0.0, keys=torch.zeros(1 << 20, dtype=torch.int64), p=256, eps=0.02, seed=1)
+    nb = serve.Server.request_bytes(1 << 20, 256)
+    need = nb + 4096  # outputs beyond the workspace
+    assert _bare_server(None)._fits(0, req, need)
+    s = _bare_server(need + 100)
+    assert s._fits(0, req, need)
+    s.bytes_in_flight = 101
+    assert not s._fits(0, req, need)
+    s = _bare_server("free", reserve=1000, available=need + 1000)
+    assert s._growth(0, req, need) == need and s._fits(0, req, need)
+    s.pending_bytes = 1
+    assert not s._fits(0, req, need)
+    s.slot_ws[1] = _Ws(nb)  # a slot whose cached workspace is large enough grows by the outputs only
+    assert s._growth(1, req, need) == 4096 and s._fits(1, req, need)
+    s.slot_ws[1] = _Ws(nb // 2)
+    assert s._growth(1, req, need) == nb - nb // 2 + 4096
