@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -188,3 +189,28 @@ def test_two_stage_arguments_rejected_without_device(lib):
                                work, ctypes.byref(st), None, None)
     assert L.hss_sort_two_stage(*args(256, 24, 1 << 40)) == -1
     assert L.hss_sort_two_stage(*args(256, 16, 16)) == -2
+
+
+def test_cut_records_match_the_c_layout():
+    """The binding's packed (n, 2) int64 cut tensors hold hss_cut records
+    byte for byte (u64 key, i32 seg, u32 spos: 16 bytes, little-endian), the
+    special segs -1/-2/-3 and positions above 2^31 included, both ways."""
+    import torch
+    from paper_1803_01237_gb300 import hss
+
+    class Cut(ctypes.Structure):
+        _fields_ = [("key", ctypes.c_uint64), ("seg", ctypes.c_int32), ("spos", ctypes.c_uint32)]
+
+    assert ctypes.sizeof(Cut) == 16
+    vals = [(0, 0, 0), ((1 << 64) - 1, 7, (1 << 32) - 1), (5, -1, 0), (0, -2, 0), (0, -3, 0),
+            (1 << 63, (1 << 31) - 1, 1 << 31), (12345, 3, 99)]
+    arr = (Cut * len(vals))(*[Cut(*v) for v in vals])
+    raw = bytes(arr)
+    key = np.array([v[0] for v in vals], dtype=np.uint64)
+    seg = np.array([v[1] for v in vals], dtype=np.int32)
+    spos = np.array([v[2] for v in vals], dtype=np.uint32)
+    packed = hss.cuts_from_numpy(key, seg, spos, "cpu")
+    assert packed.shape == (len(vals), 2) and packed.dtype == torch.int64
+    assert packed.numpy().tobytes() == raw
+    k, s, sp = hss.cuts_to_numpy(torch.from_numpy(np.frombuffer(raw, dtype=np.int64).copy()).reshape(-1, 2))
+    assert np.array_equal(k.view(np.uint64), key) and np.array_equal(s, seg) and np.array_equal(sp, spos)
