@@ -214,3 +214,30 @@ def test_cut_records_match_the_c_layout():
     assert packed.numpy().tobytes() == raw
     k, s, sp = hss.cuts_to_numpy(torch.from_numpy(np.frombuffer(raw, dtype=np.int64).copy()).reshape(-1, 2))
     assert np.array_equal(k.view(np.uint64), key) and np.array_equal(s, seg) and np.array_equal(sp, spos)
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every struct the binding mirrors with ctypes has the size and field
+    offsets that a C compiler gives the header's declaration (gcc, host ABI)."""
+    import subprocess
+    from paper_1803_01237_gb300 import hss
+    mirrors = {"hss_params": hss.Params, "hss_stats": hss.Stats, "hss_tuning": hss.Tuning,
+               "hss_job_stats": hss.JobStats, "hss_batch_stats": hss.BatchStats,
+               "hss_two_stage_stats": hss.TwoStageStats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "hss.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in py._fields_:
+            lines.append(f'    printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ["    return 0;", "}"]
+    src, exe = tmp_path / "layout.c", tmp_path / "layout"
+    src.write_text("\n".join(lines) + "\n")
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    got = {}
+    for line in subprocess.check_output([str(exe)], text=True).splitlines():
+        cname, field, v = line.split()
+        got[(cname, field)] = int(v)
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f in py._fields_:
+            assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])
