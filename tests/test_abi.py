@@ -229,6 +229,10 @@ def test_binding_structs_match_the_header(tmp_path):
         lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
         for f in py._fields_:
             lines.append(f'    printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    # CDFModel reads theta at byte 0 and the Adam step counter at byte 12 NPARAM of hss_cdf_model
+    lines.append('    printf("hss_cdf_model size %zu\\n", sizeof(hss_cdf_model));')
+    for fld in ("theta", "step"):
+        lines.append(f'    printf("hss_cdf_model {fld} %zu\\n", offsetof(hss_cdf_model, {fld}));')
     lines += ["    return 0;", "}"]
     src, exe = tmp_path / "layout.c", tmp_path / "layout"
     src.write_text("\n".join(lines) + "\n")
@@ -241,3 +245,7 @@ def test_binding_structs_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f in py._fields_:
             assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])
+    lib = hss.load()
+    lib.hss_cdf_model_bytes.restype = ctypes.c_size_t
+    assert got[("hss_cdf_model", "size")] == lib.hss_cdf_model_bytes()
+    assert got[("hss_cdf_model", "theta")] == 0 and got[("hss_cdf_model", "step")] == 12 * hss.CDF_NPARAM
