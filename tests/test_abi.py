@@ -249,3 +249,34 @@ def test_binding_structs_match_the_header(tmp_path):
     lib.hss_cdf_model_bytes.restype = ctypes.c_size_t
     assert got[("hss_cdf_model", "size")] == lib.hss_cdf_model_bytes()
     assert got[("hss_cdf_model", "theta")] == 0 and got[("hss_cdf_model", "step")] == 12 * hss.CDF_NPARAM
+
+
+def test_binding_constants_match_the_header():
+    """Error codes, key types, operations, flags, limits, schedules and the
+    CDF network's constants in the binding equal the header's #defines."""
+    from paper_1803_01237_gb300 import hss
+    defs = {}
+    for m in re.finditer(r"^#define\s+(HSS_\w+)\s+\(?(-?\d+)u?\)?", open(HEADER).read(), re.M):
+        defs[m.group(1)] = int(m.group(2))
+    want = {"HSS_ERR_INVALID": hss.ERR_INVALID, "HSS_ERR_WORKSPACE": hss.ERR_WORKSPACE,
+            "HSS_ERR_ROUND_LIMIT": hss.ERR_ROUND_LIMIT, "HSS_ERR_TIMEOUT": hss.ERR_TIMEOUT,
+            "HSS_ERR_CUDA": hss.ERR_CUDA, "HSS_ERR_CAPACITY": hss.ERR_CAPACITY,
+            "HSS_FLAG_SYNC": hss.FLAG_SYNC, "HSS_FLAG_TIMING": hss.FLAG_TIMING,
+            "HSS_FLAG_HIST_PROBE": hss.FLAG_HIST_PROBE, "HSS_FLAG_HIST_STAGED": hss.FLAG_HIST_STAGED,
+            "HSS_FLAG_HOST_ROUNDS": hss.FLAG_HOST_ROUNDS, "HSS_FLAG_DEVICE_ROUNDS": hss.FLAG_DEVICE_ROUNDS,
+            "HSS_MAX_ROUNDS": hss.MAX_ROUNDS, "HSS_NUM_PHASES": hss.NUM_PHASES, "HSS_CDF_NPARAM": hss.CDF_NPARAM,
+            "HSS_KEY_U64": hss.KEY_TYPES["u64"], "HSS_KEY_I64": hss.KEY_TYPES["i64"],
+            "HSS_CDF_LINEAR": hss.CDF_FEATURES["linear"], "HSS_CDF_LOG": hss.CDF_FEATURES["log"],
+            "HSS_CDF_W_FP32": hss.CDF_WEIGHTS["fp32"], "HSS_CDF_W_BF16": hss.CDF_WEIGHTS["bf16"]}
+    for name, op in [("SORT", "sort"), ("PARTITION", "partition"), ("LOCAL_SORT", "local_sort"),
+                     ("MERGE", "merge"), ("EXCHANGE", "exchange"), ("SORT_HOST", "sort_host")]:
+        want["HSS_OP_" + name] = hss.OP[op]
+    for name in ("PROPORTIONAL", "THEORY", "EQUAL"):
+        want["HSS_SCHEDULE_" + name] = hss.SCHEDULES[name.lower()]
+    want["HSS_OK"] = hss.HSS_OK
+    for name, v in want.items():
+        assert defs[name] == v, name
+    codes = {v: k for k, v in defs.items() if k.startswith("HSS_ERR_")}
+    for code, name in codes.items():
+        assert hss.ERRORS[code] == name
+    assert set(hss.ERRORS) == set(codes)
