@@ -280,3 +280,29 @@ def test_binding_constants_match_the_header():
     for code, name in codes.items():
         assert hss.ERRORS[code] == name
     assert set(hss.ERRORS) == set(codes)
+
+
+def _header_arity():
+    """Number of parameters of every hss_* prototype in the header."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(hss_\w+)\s*\(([^;{}]*?)\)\s*;", text, re.S):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_argtypes_match_header_arity():
+    """Every entry point whose argument types the binding declares at load
+    time takes as many arguments as the header's prototype."""
+    from paper_1803_01237_gb300 import hss
+    lib = hss.load()
+    arity = _header_arity()
+    assert len(arity) >= 30
+    checked = 0
+    for name, n in arity.items():
+        fn = getattr(lib, name, None)
+        if fn is not None and fn.argtypes is not None:
+            assert len(fn.argtypes) == n, (name, len(fn.argtypes), n)
+            checked += 1
+    assert checked >= 20
