@@ -304,16 +304,21 @@ def partition_async(keys, p: int, eps: float, seed: int, oversample: float = 5.0
     return spl[:p - 1], off, ws
 
 
-def call_stats(op: str, N: int, p: int, eps: float, seed: int, ws: torch.Tensor, oversample: float = 5.0,
-               max_rounds: int = 0, key_type: str = "u64", payload: bool = False, flags: int = 0, stream=None):
-    """hss_call_stats: (status, Stats) of the last call on workspace ws."""
-    lib = load()
+def _bind_call_stats(lib):
+    """Argument types of hss_call_stats (bound on first use)."""
     if not hasattr(lib, "_call_stats_bound"):
         P = ctypes.c_void_p
         lib.hss_call_stats.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(Params), ctypes.c_int,
                                        ctypes.c_int, P, ctypes.c_size_t, ctypes.POINTER(Stats), P]
         lib.hss_call_stats.restype = ctypes.c_int
         lib._call_stats_bound = True
+    return lib
+
+
+def call_stats(op: str, N: int, p: int, eps: float, seed: int, ws: torch.Tensor, oversample: float = 5.0,
+               max_rounds: int = 0, key_type: str = "u64", payload: bool = False, flags: int = 0, stream=None):
+    """hss_call_stats: (status, Stats) of the last call on workspace ws."""
+    lib = _bind_call_stats(load())
     prm = _params(p, eps, seed, oversample, max_rounds, flags)
     st = Stats()
     rc = lib.hss_call_stats(OP[op], N, ctypes.byref(prm), KEY_TYPES[key_type], int(payload), _ptr(ws), ws.numel(),
@@ -639,9 +644,8 @@ class BatchResult:
         return self.splitters[o:o + self.ps[j] - 1]
 
 
-def _batch(keys, sizes, ps, eps, seed, payload, oversample, max_rounds, key_type, flags, sort, out, out_payload,
-           stream, seeds=None, ws=None):
-    lib = load()
+def _bind_batch(lib):
+    """Argument types of the batched entry points (bound on first use)."""
     if not hasattr(lib, "_batch_bound"):
         P, U64, U32, I32, SZ = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_size_t
         lib.hss_batch_workspace_bytes.argtypes = [P, P, U32, ctypes.POINTER(Params), I32, I32, I32]
@@ -659,6 +663,12 @@ def _batch(keys, sizes, ps, eps, seed, payload, oversample, max_rounds, key_type
                                                    ctypes.POINTER(BatchStats), P, P]
         lib.hss_partition_batch_seeded.restype = I32
         lib._batch_bound = True
+    return lib
+
+
+def _batch(keys, sizes, ps, eps, seed, payload, oversample, max_rounds, key_type, flags, sort, out, out_payload,
+           stream, seeds=None, ws=None):
+    lib = _bind_batch(load())
     keys = _as_key_tensor(keys)
     sizes = np.ascontiguousarray(np.asarray(sizes, dtype=np.uint64))
     ps = np.ascontiguousarray(np.asarray(ps, dtype=np.uint32))
@@ -775,13 +785,8 @@ class TwoStageResult:
         return self.splitters[g * (pg - 1):(g + 1) * (pg - 1)]
 
 
-def sort_two_stage(keys, p: int, groups: int, eps: float, seed: int, payload=None, oversample: float = 5.0,
-                   max_rounds: int = 0, key_type: str = "u64", flags: int = 0, out=None, out_payload=None,
-                   stream=None) -> TwoStageResult:
-    """Two-stage HSS (hss_sort_two_stage): the p processors' keys split into
-    `groups` groups, then each group sorted over its p / groups processors
-    with seed + 1 + g."""
-    lib = load()
+def _bind_two_stage(lib):
+    """Argument types of the two-stage entry points (bound on first use)."""
     if not hasattr(lib, "_two_stage_bound"):
         P, U64, U32, I32, SZ = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_size_t
         lib.hss_two_stage_workspace_bytes.argtypes = [U64, ctypes.POINTER(Params), U32, I32, I32]
@@ -790,6 +795,16 @@ def sort_two_stage(keys, p: int, groups: int, eps: float, seed: int, payload=Non
                                            ctypes.POINTER(TwoStageStats), P, P]
         lib.hss_sort_two_stage.restype = I32
         lib._two_stage_bound = True
+    return lib
+
+
+def sort_two_stage(keys, p: int, groups: int, eps: float, seed: int, payload=None, oversample: float = 5.0,
+                   max_rounds: int = 0, key_type: str = "u64", flags: int = 0, out=None, out_payload=None,
+                   stream=None) -> TwoStageResult:
+    """Two-stage HSS (hss_sort_two_stage): the p processors' keys split into
+    `groups` groups, then each group sorted over its p / groups processors
+    with seed + 1 + g."""
+    lib = _bind_two_stage(load())
     keys = _as_key_tensor(keys)
     N = keys.numel()
     r = int(groups)
