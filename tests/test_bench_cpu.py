@@ -80,3 +80,31 @@ def test_max_over_ranks_gloo():
     assert res == {0: 11.0, 1: 11.0}
     import bench  # noqa: E402  (single process: the value itself)
     assert bench._max_over_ranks(3.5, None, "cpu") == 3.5
+
+
+def test_split_traffic_record_rule():
+    """The roofline's DRAM traffic comes from a committed capture that is
+    void once the split pass's sources change: the hash moves with an edit
+    inside them, not with one elsewhere in segsort.cu, is None when a marker
+    is gone, and the full-size bytes are the capture's scaled by the keys."""
+    sys.path.insert(0, ROOT)
+    import bench
+    csrc = os.path.join(ROOT, "paper_1803_01237_gb300", "csrc")
+    cu, cuh, internal = (open(os.path.join(csrc, n)).read() for n in ("segsort.cu", "segsort.cuh", "hss_internal.cuh"))
+    h = bench.split_source_hash(cu, cuh, internal)
+    assert h is not None and len(h) == 16
+    start = cu.find("struct SplitArgs {")
+    inside = cu[:start + 18] + " " + cu[start + 18:]
+    assert bench.split_source_hash(inside, cuh, internal) != h
+    assert bench.split_source_hash(cu + "\n// trailing note\n", cuh, internal) == h
+    assert bench.split_source_hash(cu.replace("struct SplitArgs {", "struct Split {"), cuh, internal) is None
+    assert bench.split_source_hash(cu, cuh, internal + " ") != h
+    rec = {}
+    for line in open(os.path.join(ROOT, "profiles", "k_split_traffic.txt")):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.strip().split("=", 1)
+            rec[k] = v
+    full = int(rec["dram_bytes_per_launch_capture"]) * (1 << bench.LOG2N) // int(rec["keys_capture"])
+    assert int(float(rec["dram_bytes_per_launch_full_size"])) == full
+    got = bench._traffic_record()
+    assert got is None if rec["split_source_sha"] != h else got == float(full)
