@@ -146,8 +146,16 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.f.close()
-        rows = [ln.split(",") for ln in open(self.path).read().strip().splitlines() if ln.strip()]
+        with open(self.path) as f:
+            text = f.read()
         os.unlink(self.path)
+        return self.summarize(text)
+
+    @staticmethod
+    def summarize(text: str):
+        """Median SM clock, maximum clock and the throttle reasons seen
+        active in nvidia-smi's CSV samples (None without a valid sample)."""
+        rows = [ln.split(",") for ln in text.strip().splitlines() if ln.strip()]
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:

@@ -108,3 +108,25 @@ def test_split_traffic_record_rule():
     assert int(float(rec["dram_bytes_per_launch_full_size"])) == full
     got = bench._traffic_record()
     assert got is None if rec["split_source_sha"] != h else got == float(full)
+
+
+def test_clock_summary_of_nvidia_smi_samples():
+    """The bench's clock record: median SM clock over the samples, the
+    maximum clock, and every throttle reason seen active; malformed or
+    partial lines are skipped and no valid sample gives None."""
+    sys.path.insert(0, ROOT)
+    import bench
+    text = "\n".join([
+        "0, 1965, 2070, 900.1, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2032, 2070, 850.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 870.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070, 870.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 1990, 2070",
+        "",
+    ])
+    got = bench.ClockSampler.summarize(text)
+    assert got == {"sm_mhz": 1980.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    hot = "0, 1500, 2070, 1400, 0x8, Active, Not Active, Active, Not Active\n"
+    assert bench.ClockSampler.summarize(hot)["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    assert bench.ClockSampler.summarize("") is None
+    assert bench.ClockSampler.summarize("0, [N/A], [N/A], 0, 0x0, a, b, c, d\n") is None
